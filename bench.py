@@ -1,0 +1,297 @@
+#!/usr/bin/env python
+"""Benchmark of the Clifford circuit-cutting hot path on one GB300.
+
+Workload (default): 100 qubits, depth-20 random Clifford brickwork, 10 T gates
+in two non-Clifford regions of 9 wires, 4 wire cuts -> 3 fragments (86-wire
+Clifford body with 144 variants, two 9-wire statevector fragments with 12),
+10^4 Philox shots per Clifford variant, 12-qubit marginal + 64 Z-strings.
+One step = one pass of the whole path: tableau evolution, outcome spaces,
+sampling, statevectors, fold, recombination.
+
+value   Clifford variant-shots/s, plan resident on the device, one CUDA-graph
+        replay + device-side recombination per step, L2 flushed between steps.
+e2e     the same metric through the public C ABI from host buffers: plan build
+        (host compile + upload), evaluation, recombination into host memory.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Clifford variant-shots/s and circuits/s end-to-end; % of HBM/tensor roofline"
+UNIT = "variant-shots/s"
+SEED = (0x9E3779B9, 0x7F4A7C15)
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def workload(name):
+    import workloads as W
+    if name == "config2":
+        return W.config2()
+    if name == "config1":
+        return W.config1()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def describe(w):
+    return (f"{w.name}: {w.circuit.n_qubits} qubits, {len(w.circuit.gates)} gates, {w.circuit.n_t} T, "
+            f"{len(w.cuts)} cuts, {w.shots} shots/Clifford variant, {len(w.marginal)}-qubit marginal, "
+            f"{len(w.zstrings)} Z-strings")
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = [l.split(",") for l in open(self.f.name).read().splitlines() if l.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1])); mx = max(mx, float(r[2]))
+                for n, v in zip(names, r[5:9]):
+                    if v.strip() == "Active":
+                        reasons.add(n)
+            except Exception:
+                pass
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_baseline(w, seconds_hint=""):
+    """The CPU oracle on one full circuit of the workload (all variants)."""
+    from oracle.pipeline import evaluate_workload
+    t0 = time.perf_counter()
+    r = evaluate_workload(w, mode="sampled", seed_lo=SEED[0], seed_hi=SEED[1], keep_tableaus=False)
+    dt = time.perf_counter() - t0
+    ncl = sum(f.n_variants for f in r.fragments if f.clifford)
+    return {"value": ncl * w.shots / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one full circuit of the workload ({ncl} Clifford variants x {w.shots} shots, "
+                      f"all statevector variants, fold and recombination), {dt:.1f} s single-threaded",
+            "circuits_per_s": 1.0 / dt}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the CPU oracle, timed on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    from oracle.pipeline import evaluate_workload
+    from oracle.cutting import fragment_circuit
+    w = workload(args.workload)
+    frags, _ = fragment_circuit(w.circuit, w.cuts, w.marginal)
+    body = max(range(len(frags)), key=lambda i: frags[i].n if frags[i].clifford else -1)
+    nsamp = 8
+    vs = list(range(0, frags[body].n_variants, max(1, frags[body].n_variants // nsamp)))[:nsamp]
+
+    def step():
+        evaluate_workload(w, mode="sampled", seed_lo=SEED[0], seed_hi=SEED[1],
+                          variants_only={body: vs}, keep_tableaus=False)
+
+    for _ in range(args.warmup):
+        step()
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter(); step(); times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    units = len(vs) * w.shots * args.steps
+    val = units / tot
+    line = {"metric": METRIC, "value": val, "unit": UNIT, "impl": "reference", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8/f64",
+            "data": "synthetic", "config": {"workload": describe(w), "parallelism": "none (CPU oracle)"},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": val, "unit": UNIT,
+                             "sample": f"per step: {len(vs)} body variants x {w.shots} shots"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2303_10788_gb300 import ccs
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    w = workload(args.workload)
+    seed = (SEED[0] + rank, SEED[1])
+    ctx = ccs.ccs_create(local_rank)
+    plan = ccs.ccs_build_fragments(ctx, [w])
+    infos = [ccs.ccs_fragment_info_get(ctx, plan, 0, f) for f in range(ccs.ccs_plan_counts(ctx, plan, 0)[0])]
+    n_cliff_var = sum(i["n_variants"] for i in infos if i["clifford"])
+    units_per_step = n_cliff_var * w.shots
+    marg = torch.zeros(1 << len(w.marginal), dtype=torch.float64, device="cuda")
+    zexp = torch.zeros(max(1, len(w.zstrings)), dtype=torch.float64, device="cuda")
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")      # > 129 MB L2
+    res = ccs.ccs_eval_variants(ctx, plan, mode=ccs.CCS_SAMPLED, shots=w.shots, seed_lo=seed[0],
+                                seed_hi=seed[1], use_graph=True)
+
+    def step():
+        ccs.ccs_eval_variants(ctx, plan, mode=ccs.CCS_SAMPLED, shots=w.shots, seed_lo=seed[0],
+                              seed_hi=seed[1], use_graph=True, res=res)
+        ccs.ccs_recombine(ctx, plan, res, marginal_out=marg, zexp_out=zexp)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    stream = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    clk = Clocks(local_rank)
+    for i in range(args.steps):
+        flush.zero_()
+        evs[i][0].record(stream)
+        step()
+        evs[i][1].record(stream)
+    barrier()
+    clocks = clk.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    t_tot = sum(step_ms) / 1e3
+    if dist is not None:
+        tt = torch.tensor([t_tot], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_tot = float(tt.item())
+    value = units_per_step * args.steps * world / t_tot
+
+    # --- per-stage kernel times (profiled pass, same work, no graph) ----------
+    ccs.ccs_set_profiling(ctx, True)
+    acc = {}
+    for _ in range(args.steps):
+        flush.zero_()
+        ccs.ccs_eval_variants(ctx, plan, mode=ccs.CCS_SAMPLED, shots=w.shots, seed_lo=seed[0],
+                              seed_hi=seed[1], res=res)
+        ccs.ccs_recombine(ctx, plan, res, marginal_out=marg, zexp_out=zexp)
+        for k, v in ccs.ccs_get_stage_times(ctx).items():
+            acc.setdefault(k, []).append(v)
+    ccs.ccs_set_profiling(ctx, False)
+    stage = {k: statistics.mean(v) for k, v in acc.items()}
+    dom = max(stage, key=stage.get)
+
+    # --- end to end through the C ABI from host buffers ------------------------
+    e2e_times = []
+    for i in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        p2 = ccs.ccs_build_fragments(ctx, [w])
+        r2 = ccs.ccs_eval_variants(ctx, p2, mode=ccs.CCS_SAMPLED, shots=w.shots, seed_lo=seed[0],
+                                   seed_hi=seed[1])
+        m_host, z_host = ccs.ccs_recombine(ctx, p2, r2)
+        e2e_times.append(time.perf_counter() - t0)
+        del r2, p2
+    e2e_s = statistics.mean(e2e_times)
+    h2d = sum(24 * len(x.circuit.gates) + 8 * len(x.cuts) + 4 * len(x.marginal) +
+              4 * sum(len(z) + 1 for z in x.zstrings) for x in [w])
+    d2h = 8 * ((1 << len(w.marginal)) + len(w.zstrings))
+
+    pk, pk_kind = peaks()
+    roof = roofline(dom, stage[dom], w, infos, pk, pk_kind)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64/f32", "data": "synthetic",
+            "config": {"workload": describe(w), "variant_shots_per_step": units_per_step,
+                       "l2": "flushed between steps (512 MB write, outside the step events)",
+                       "parallelism": f"{world} independent replicas (no collective)",
+                       "launch": "one CUDA-graph replay (eval) + recombination per step"},
+            "circuits_per_s": world * args.steps / t_tot,
+            "stage_ms": stage, "roofline": roof,
+            "e2e": {"value": units_per_step * world / e2e_s, "unit": UNIT, "circuits_per_s": world / e2e_s,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": 7 * args.steps, "clocks": clocks}
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_baseline(w)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def roofline(stage, ms, w, infos, pk, pk_kind):
+    """Roofline of the dominant stage (algorithmic units per launch / time)."""
+    sm_mhz = pk.get("sm_max_mhz", 2070.0)
+    n_sm = 152
+    cl = [i for i in infos if i["clifford"]]
+    if stage == "sample":
+        shots = sum(i["n_variants"] for i in cl) * w.shots
+        # Philox4x32-10: 20 32x32->64-bit multiplies per shot; IMAD at 64/clk/SM
+        achieved = shots * 20 / (ms * 1e-3) / 1e12
+        peak = n_sm * 64 * sm_mhz * 1e6 / 1e12
+        return {"bound": "alu", "stage": stage, "achieved": achieved, "peak": peak,
+                "unit": "T int-mul/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": f"derived: {n_sm} SMs x 64 IMAD/clk x {sm_mhz:.0f} MHz"}
+    if stage == "clifford":
+        # bit-sliced CHP: per fused 2-qubit op per 64-row word, 4 columns read
+        # and written (64 B of shared memory); shared memory 128 B/clk/SM
+        ops = sum(i["n_variants"] * i["n_ops"] * 2 * ((i["n_wires"] + 63) // 64) for i in cl)
+        achieved = ops * 64 / (ms * 1e-3) / 1e9
+        peak = n_sm * 128 * sm_mhz * 1e6 / 1e9
+        return {"bound": "smem", "stage": stage, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": f"derived: {n_sm} SMs x 128 B/clk x {sm_mhz:.0f} MHz"}
+    hbm = pk["hbm_gbs"]
+    return {"bound": "hbm", "stage": stage, "achieved": None, "peak": hbm, "unit": "GB/s",
+            "frac": None, "traffic": None, "peak_source": pk_kind}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="config2")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", args.gpus if args.gpus == 1 else 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,238 @@
+/*
+ * ccs.h -- C ABI of the GB300 (sm_103a) Clifford circuit-cutting hot path.
+ *
+ * The method is Clifford-based circuit cutting ("Clifford-based Circuit
+ * Cutting for Quantum Simulation", Smith, Perlin et al.): a near-Clifford
+ * circuit is cut into Clifford and small non-Clifford fragments (Sec. V-A),
+ * every fragment *variant* -- one choice of prepared state at each quantum
+ * input and of measurement basis at each quantum output (Sec. V-B) -- is
+ * simulated, Clifford ones by a stabilizer tableau and the others by an exact
+ * statevector (Sec. V-B), and the distribution of the uncut circuit is
+ * rebuilt by a contraction over the 4^k cut terms (Sec. III-B, Sec. V-C).
+ *
+ * Three calls carry the path:
+ *   ccs_build_fragments  circuit(s) -> fragments + variant plan      (Sec. V-A)
+ *   ccs_eval_variants    plan -> per-variant outcome data on the GPU (Sec. V-B)
+ *   ccs_recombine        per-variant data -> marginal + <Z_S> values (Sec. V-C)
+ *
+ * Conventions (fixed by this interface; the paper leaves them open):
+ *   - qubits start in |0>, outputs are measured in Z (Sec. V-B);
+ *   - a cut {qubit, gate_index} splits the qubit's wire just before gate
+ *     gate_index of the flat gate list; cuts are ordered by (gate_index, qubit);
+ *   - a fragment's wires are the wire segments it owns, ordered by
+ *     (qubit, segment); fragments are ordered by their first wire;
+ *   - preparations 0..3 = |0>,|1>,|+>,|+i>; bases 0..2 = X,Y,Z;
+ *   - variant id = mixed radix: quantum inputs first (radix 4, first input
+ *     least significant), then quantum outputs (radix 3), both in cut order;
+ *   - measured list A_f = the fragment's marginal wires (in the caller's
+ *     marginal order) then its quantum-output wires (cut order); bit j of an
+ *     outcome y is wire A_f[j];
+ *   - bit j of a marginal index is the j-th qubit of the caller's marginal.
+ *
+ * Ownership: every pointer passed in belongs to the caller and is only read
+ * during the call (host memory unless stated).  Plans, results and contexts
+ * belong to the library and are released by their *_free / ccs_destroy.
+ * Device memory is taken from the context's allocator (see ccs_allocator).
+ *
+ * Errors: every int-returning call returns CCS_OK (0) or a negative
+ * CCS_ERR_* code and leaves a message in ccs_last_error(ctx).  No exception
+ * crosses the ABI.  A context must be used by one host thread at a time.
+ */
+#ifndef CCS_ABI_H_
+#define CCS_ABI_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CCS_OK 0
+#define CCS_ERR_INVALID_ARG (-1)
+#define CCS_ERR_UNSUPPORTED_GATE (-2)
+#define CCS_ERR_TOO_MANY_CUTS (-3)
+#define CCS_ERR_NC_TOO_WIDE (-4)
+#define CCS_ERR_OOM (-5)
+#define CCS_ERR_CUDA (-6)
+#define CCS_ERR_TIMEOUT (-7)
+#define CCS_ERR_UNSUPPORTED (-8)
+#define CCS_ERR_DEVICE_CHECK (-9)
+
+/* Gate opcodes (Sec. II-A, II-C): Paulis, S = Z^{1/2}, H, CX, CZ; T = Z^{1/4}
+ * and its inverse are the non-Clifford gates. */
+enum {
+  CCS_H = 0, CCS_S = 1, CCS_SDG = 2, CCS_X = 3, CCS_Y = 4, CCS_Z = 5,
+  CCS_CX = 6, CCS_CZ = 7, CCS_T = 8, CCS_TDG = 9
+};
+
+/* One gate.  q[1] is the target of CX (q[0] the control) and is ignored for
+ * one-qubit gates.  nq, flags and param are reserved (set to 0). */
+typedef struct {
+  uint8_t op;
+  uint8_t nq;
+  uint16_t flags;
+  uint32_t q[2];
+  double param;
+} ccs_gate;
+
+typedef struct {
+  uint32_t qubit;
+  uint32_t gate_index;
+} ccs_cut;
+
+/* One problem: a circuit, its cuts and what to report.
+ *   cuts/n_cuts   explicit wire cuts; n_cuts < 0 asks ccs_build_fragments to
+ *                 search for a cut set (greedy, or the learned scorer);
+ *   marginal      output qubits of the reported marginal (<= 24 of them);
+ *   zstring_*     CSR list of Z-strings S (sets of qubits): <Z_S> is
+ *                 reported for each. */
+typedef struct {
+  uint32_t n_qubits;
+  uint32_t n_gates;
+  const ccs_gate* gates;
+  int32_t n_cuts;
+  const ccs_cut* cuts;
+  uint32_t n_marginal;
+  const uint32_t* marginal;
+  uint32_t n_zstrings;
+  const uint32_t* zstring_offsets;   /* n_zstrings + 1 entries */
+  const uint32_t* zstring_qubits;
+} ccs_problem;
+
+typedef struct ccs_ctx_s* ccs_ctx;
+typedef struct ccs_plan_s* ccs_plan;
+typedef struct ccs_res_s* ccs_res;
+
+/* Device allocator: alloc returns device memory of `bytes` usable on
+ * `stream` (NULL on failure); free releases it.  Passing NULL to ccs_create
+ * uses cudaMallocAsync / cudaFreeAsync on the context's stream. */
+typedef void* (*ccs_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void (*ccs_free_fn)(void* ptr, size_t bytes, void* stream, void* user);
+typedef struct {
+  ccs_alloc_fn alloc;
+  ccs_free_fn free;
+  void* user;
+} ccs_allocator;
+
+/* Create a context on CUDA device `device`, issuing all work on
+ * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).
+ * device < 0 creates a host-only context: plans can be built and inspected
+ * (fragments, cuts, variant counts) without a GPU; ccs_eval_variants and
+ * ccs_recombine then return CCS_ERR_UNSUPPORTED. */
+int ccs_create(ccs_ctx* out, int device, void* cuda_stream, const ccs_allocator* alloc);
+void ccs_destroy(ccs_ctx ctx);
+const char* ccs_last_error(ccs_ctx ctx);
+/* Library version string (static storage). */
+const char* ccs_version(void);
+
+/* --- cutting (Sec. V-A) --------------------------------------------------- */
+typedef struct {
+  int32_t max_cuts;        /* reject / bound searched cut sets (default 12) */
+  int32_t max_nc_width;    /* widest non-Clifford fragment allowed (<= 12) */
+  int32_t use_learned;     /* 1: let the learned scorer pick among candidates */
+} ccs_cut_opts;
+
+/* Split each problem's circuit at its cuts into fragments, build every
+ * fragment's variant list, compile its gates into moments of fused one- and
+ * two-qubit Clifford updates (Clifford fragments) or 2x2 / 4x4 unitaries
+ * (non-Clifford fragments), and upload the plan to the device.
+ * Errors: INVALID_ARG (bad qubit index, cut position, marginal),
+ * UNSUPPORTED_GATE, TOO_MANY_CUTS, NC_TOO_WIDE, UNSUPPORTED (a cut whose two
+ * ends lie in the same fragment), OOM, CUDA. */
+int ccs_build_fragments(ccs_ctx ctx, const ccs_problem* problems, int n_problems,
+                        const ccs_cut_opts* opts, ccs_plan* out);
+void ccs_plan_free(ccs_plan plan);
+
+/* --- variant evaluation (Sec. V-B) ---------------------------------------- */
+#define CCS_EXACT 0
+#define CCS_SAMPLED 1
+typedef struct {
+  int32_t mode;            /* CCS_EXACT: closed-form 2^-rank per Clifford variant;
+                              CCS_SAMPLED: `shots` Philox shots per Clifford variant */
+  uint32_t shots;
+  uint32_t seed_lo, seed_hi;   /* Philox4x32-10 key */
+  int32_t keep_tableaus;   /* 1: keep every final tableau for ccs_get_tableau */
+  int32_t use_graph;       /* 1: capture the launches in a CUDA graph and replay */
+} ccs_eval_opts;
+
+/* Evaluate every variant of every fragment of the plan on the GPU: tableau
+ * evolution, GF(2) reduction to the affine outcome space, Philox sampling
+ * (Clifford) or complex64 statevectors (non-Clifford), then the fold of the
+ * variant data into one tensor per fragment.  Shot s of variant v of
+ * fragment f of problem c uses Philox counter (s, v, f, c).  If *res is NULL
+ * a result is created, else its buffers are reused (same plan only).  The
+ * call is asynchronous on the context stream; getters synchronise. */
+int ccs_eval_variants(ccs_ctx ctx, ccs_plan plan, const ccs_eval_opts* opts, ccs_res* res);
+void ccs_res_free(ccs_res res);
+
+/* --- recombination (Sec. V-C) --------------------------------------------- */
+#define CCS_FP32 0
+#define CCS_BF16 1
+typedef struct {
+  int32_t precision;          /* CCS_FP32 or CCS_BF16 operands of the 4^k contraction */
+  int32_t outputs_on_device;  /* 1: marginal_out / zexp_out are device pointers */
+} ccs_recomb_opts;
+
+/* p(o) = 2^-k sum_{P in {I,X,Y,Z}^k} prod_f T_f(o_f, P|f) for every problem,
+ * written to marginal_out (problems back to back, 2^n_marginal doubles each)
+ * and <Z_S> to zexp_out (n_zstrings doubles each).  Partial sums over the
+ * cut index are combined in FP64.  Synchronises the context stream unless
+ * outputs_on_device is set.  Errors: UNSUPPORTED for a problem whose
+ * fragments do not form a star (one fragment on every cut). */
+int ccs_recombine(ccs_ctx ctx, ccs_plan plan, ccs_res res, const ccs_recomb_opts* opts,
+                  double* marginal_out, double* zexp_out);
+
+/* --- plan inspection -------------------------------------------------------- */
+typedef struct {
+  int32_t n_wires;
+  int32_t clifford;
+  int32_t n_variants;
+  int32_t n_qin, n_qout;
+  int32_t n_marg;           /* marginal bits owned by this fragment */
+  int32_t n_meas;           /* |A_f| = n_marg + n_qout */
+  int32_t n_slots;          /* cuts incident to the fragment */
+  int32_t n_ops, n_moments; /* compiled gate stream */
+} ccs_fragment_info;
+
+int ccs_plan_counts(ccs_ctx ctx, ccs_plan plan, int problem, int* n_fragments, int* n_cuts);
+int ccs_fragment_info_get(ccs_ctx ctx, ccs_plan plan, int problem, int fragment,
+                          ccs_fragment_info* out);
+/* The cut set used for a problem (after search), in cut order. */
+int ccs_plan_cuts(ccs_ctx ctx, ccs_plan plan, int problem, ccs_cut* out, int cap);
+/* Wires of a fragment as (qubit, segment) pairs, 2*n_wires uint32. */
+int ccs_fragment_wires(ccs_ctx ctx, ccs_plan plan, int problem, int fragment, uint32_t* out);
+
+/* --- stage timing ------------------------------------------------------------ */
+/* With profiling on, ccs_eval_variants runs without a CUDA graph and records
+ * CUDA events on the context stream around each kernel stage; recombination
+ * does the same.  ccs_get_stage_times synchronises the stream and writes the
+ * last recorded duration of each stage in milliseconds (-1 if the stage did
+ * not run) to ms[0..4]: 0 tableau evolution + outcome space + Z values
+ * (one persistent kernel), 1 Philox sampling, 2 statevectors, 3 fold,
+ * 4 recombination.  Returns the number of stages (5) or an error; cap >= 5. */
+int ccs_set_profiling(ccs_ctx ctx, int on);
+int ccs_get_stage_times(ccs_ctx ctx, double* ms, int cap);
+
+/* --- result getters (parity; caller-owned host buffers) ------------------ */
+/* Final tableau of a Clifford variant (needs keep_tableaus): uint8
+ * [2n][2n+1], row i = x_0..x_{n-1}, z_0..z_{n-1}, r; rows 0..n-1 are
+ * destabilizers, n..2n-1 stabilizers. */
+int ccs_get_tableau(ccs_ctx ctx, ccs_res res, int problem, int fragment, int variant, uint8_t* out);
+/* Canonical affine outcome space of a Clifford variant: outcomes are
+ * off ^ span(basis[0..rank)), basis in reduced row-echelon form with the
+ * pivot (lowest set bit) ascending; off has every pivot bit clear. */
+int ccs_get_outcome_space(ccs_ctx ctx, ccs_res res, int problem, int fragment, int variant,
+                          uint64_t* off, uint64_t* basis, int* rank);
+/* Shot counts of a sampled Clifford variant, 2^|A_f| uint32. */
+int ccs_get_counts(ccs_ctx ctx, ccs_res res, int problem, int fragment, int variant, uint32_t* out);
+/* Probabilities of a variant over 2^|A_f| outcomes (float32): exact ones for
+ * non-Clifford variants and exact-mode Clifford variants. */
+int ccs_get_dist(ccs_ctx ctx, ccs_res res, int problem, int fragment, int variant, float* out);
+/* Folded fragment tensor T_f[o][P] (float32, 2^n_marg x 4^n_slots, row-major). */
+int ccs_get_tensor(ccs_ctx ctx, ccs_res res, int problem, int fragment, float* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CCS_ABI_H_ */

@@ -88,11 +88,12 @@ def evaluate(circuit, cuts, marginal, zstrings=(), mode="sampled", shots=1024,
                 else:
                     counts = sample_counts(off, B, len(A), shots, v, fi, circuit_id, seed_lo, seed_hi)
                     dist = counts / float(shots)
+                supp = tb.support(tab) if len(zstrings) else None
                 for si, zs in enumerate(zstrings):
                     base = [out_wire[q][1] for q in zs if out_wire[q][0] == fi]
                     for u in range(1 << len(f.qout)):
                         ws = base + [w for j, (_, w) in enumerate(f.qout) if (u >> j) & 1]
-                        zv[si, u] = tb.z_expectation(tab, ws)
+                        zv[si, u] = tb.z_expectation(tab, ws, supp)
                 rs.append(VariantResult(dist, tb.tableau_bits(tab) if keep_tableaus else None,
                                         off, B, counts, zv))
             else:

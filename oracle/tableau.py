@@ -197,9 +197,11 @@ def outcome_space(tab, A):
     return off, B, len(B)
 
 
-def z_expectation(tab, wires):
-    """<Z_wires> of the state: (-1)^{mask.x0} if mask is orthogonal to D, else 0."""
-    x0, D = support(tab)
+def z_expectation(tab, wires, supp=None):
+    """<Z_wires> of the state: (-1)^{mask.x0} if mask is orthogonal to D, else 0.
+
+    ``supp`` may pass a precomputed ``support(tab)``."""
+    x0, D = support(tab) if supp is None else supp
     mask = np.zeros(tab.n, np.uint8)
     for w in wires:
         mask[w] ^= 1

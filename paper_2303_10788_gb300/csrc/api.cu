@@ -1,0 +1,702 @@
+// C ABI of the circuit-cutting hot path (declared in include/ccs.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+#include "plan.hpp"
+
+using namespace ccs;
+
+struct ccs_ctx_s {
+  int device = 0;
+  bool host_only = false;   // device < 0: planning only, no GPU work
+  cudaStream_t stream = nullptr;
+  ccs_allocator alloc{nullptr, nullptr, nullptr};
+  bool own_alloc = true;
+  int sm_count = 0;
+  size_t smem_optin = 0;
+  std::string err;
+  // stage timing (CUDA events around each launch on the context stream)
+  bool profiling = false;
+  cudaEvent_t ev[16] = {};
+  int n_ev = 0;
+  float stage_ms[8] = {};
+  int stage_mask = 0;   // stages recorded by the last profiled call
+};
+
+namespace {
+enum Stage { ST_CLIFFORD = 0, ST_SAMPLE = 1, ST_STATEVEC = 2, ST_FOLD = 3, ST_RECOMB = 4, ST_N = 5 };
+void stage_begin(ccs_ctx c, int st) {
+  if (!c->profiling) return;
+  if (!c->ev[2 * st]) { cudaEventCreate(&c->ev[2 * st]); cudaEventCreate(&c->ev[2 * st + 1]); }
+  cudaEventRecord(c->ev[2 * st], c->stream);
+}
+void stage_end(ccs_ctx c, int st) {
+  if (!c->profiling) return;
+  cudaEventRecord(c->ev[2 * st + 1], c->stream);
+  c->stage_mask |= 1 << st;
+}
+}  // namespace
+
+namespace {
+
+int fail(ccs_ctx c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+int cuda_fail(ccs_ctx c, cudaError_t e, const char* where) {
+  return fail(c, CCS_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+void* dalloc(ccs_ctx c, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~size_t(255);
+  if (!c->own_alloc) return c->alloc.alloc(bytes, (void*)c->stream, c->alloc.user);
+  void* p = nullptr;
+  if (cudaMallocAsync(&p, bytes, c->stream) != cudaSuccess) return nullptr;
+  return p;
+}
+
+void dfree(ccs_ctx c, void* p, size_t bytes) {
+  if (!p) return;
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~size_t(255);
+  if (!c->own_alloc) c->alloc.free(p, bytes, (void*)c->stream, c->alloc.user);
+  else cudaFreeAsync(p, c->stream);
+}
+
+struct Allocs {
+  ccs_ctx ctx = nullptr;
+  std::vector<std::pair<void*, size_t>> list;
+  template <class T>
+  T* get(size_t count) {
+    const size_t bytes = count * sizeof(T);
+    void* p = dalloc(ctx, bytes);
+    if (p) list.push_back({p, bytes});
+    return (T*)p;
+  }
+  void release() {
+    for (auto& a : list) dfree(ctx, a.first, a.second);
+    list.clear();
+  }
+};
+
+template <class T>
+bool upload(ccs_ctx c, Allocs& A, const std::vector<T>& h, T** out) {
+  *out = A.get<T>(std::max<size_t>(h.size(), 1));
+  if (!*out) return false;
+  if (!h.empty() &&
+      cudaMemcpyAsync(*out, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+    return false;
+  return true;
+}
+
+}  // namespace
+
+struct ccs_plan_s {
+  ccs_ctx ctx = nullptr;
+  bool host_only = false;
+  std::vector<Problem> problems;
+  std::vector<Frag> frags;
+  std::vector<FragDev> fdev;
+  std::vector<ProblemDev> pdev;
+  DevPlan dp{};
+  Allocs A;
+  long long n_spaces = 0, n_counts = 0, n_dist = 0, n_zval = 0, n_tab = 0, n_T = 0, n_TZ = 0;
+  long long n_marg = 0, n_zexp = 0;
+  std::vector<long long> t_prefix, tz_prefix, out_prefix, z_prefix;
+  long long* d_t_prefix = nullptr;
+  long long* d_tz_prefix = nullptr;
+  long long* d_out_prefix = nullptr;
+  long long* d_z_prefix = nullptr;
+  int cliff_smem_words = 0, max_nc_n = 1;
+  bool all_star = true;
+  ~ccs_plan_s() { A.release(); }
+};
+
+struct ccs_res_s {
+  ccs_plan plan = nullptr;
+  DevRes dr{};
+  EvalParams ep{};
+  bool have_tabs = false;
+  bool have_counts = false;
+  Allocs A;
+  cudaGraphExec_t graph = nullptr;
+  EvalParams graph_key{};
+  int graph_valid = 0;
+  int cliff_threads = 256;
+  int sample_spc = 4096;
+  ~ccs_res_s() {
+    if (graph) cudaGraphExecDestroy(graph);
+    A.release();
+  }
+};
+
+extern "C" {
+
+const char* ccs_version(void) { return "ccs 0.1 (sm_103a)"; }
+
+int ccs_create(ccs_ctx* out, int device, void* cuda_stream, const ccs_allocator* alloc) {
+  if (!out) return CCS_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (device < 0) {   // host-only context: fragments and plans can be built and inspected
+    ccs_ctx c = new ccs_ctx_s();
+    c->device = -1;
+    c->host_only = true;
+    c->smem_optin = 227 * 1024;
+    *out = c;
+    return CCS_OK;
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return CCS_ERR_CUDA;
+  ccs_ctx c = new ccs_ctx_s();
+  c->device = device;
+  c->stream = (cudaStream_t)cuda_stream;
+  if (alloc && alloc->alloc && alloc->free) {
+    c->alloc = *alloc;
+    c->own_alloc = false;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) { delete c; return CCS_ERR_CUDA; }
+  cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  c->smem_optin = (size_t)optin;
+  *out = c;
+  return CCS_OK;
+}
+
+void ccs_destroy(ccs_ctx c) {
+  if (!c) return;
+  for (auto& e : c->ev)
+    if (e) cudaEventDestroy(e);
+  delete c;
+}
+
+int ccs_set_profiling(ccs_ctx c, int on) {
+  if (!c) return CCS_ERR_INVALID_ARG;
+  if (c->host_only) return fail(c, CCS_ERR_UNSUPPORTED, "host-only context");
+  c->profiling = on != 0;
+  c->stage_mask = 0;
+  return CCS_OK;
+}
+
+int ccs_get_stage_times(ccs_ctx c, double* ms, int cap) {
+  if (!c || !ms || cap < ST_N) return fail(c, CCS_ERR_INVALID_ARG, "bad arguments");
+  if (c->host_only || !c->profiling) return fail(c, CCS_ERR_UNSUPPORTED, "profiling is off");
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "synchronize");
+  for (int st = 0; st < ST_N; ++st) {
+    ms[st] = -1.0;
+    if (c->stage_mask & (1 << st)) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, c->ev[2 * st], c->ev[2 * st + 1]) == cudaSuccess) ms[st] = t;
+    }
+  }
+  return ST_N;
+}
+
+const char* ccs_last_error(ccs_ctx c) { return c ? c->err.c_str() : "null context"; }
+
+int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, const ccs_cut_opts* opts,
+                        ccs_plan* out) {
+  if (!c || !out || (n_problems > 0 && !probs) || n_problems < 0) return fail(c, CCS_ERR_INVALID_ARG, "bad arguments");
+  *out = nullptr;
+  if (!c->host_only) cudaSetDevice(c->device);
+  ccs_cut_opts o{kMaxCuts, 10, 0};
+  if (opts) o = *opts;
+  auto plan = new ccs_plan_s();
+  plan->ctx = c;
+  plan->A.ctx = c;
+  std::string err;
+  for (int pi = 0; pi < n_problems; ++pi) {
+    const ccs_problem& q = probs[pi];
+    Problem P;
+    P.n_qubits = q.n_qubits;
+    if (q.n_qubits == 0 || (q.n_gates && !q.gates)) { delete plan; return fail(c, CCS_ERR_INVALID_ARG, "empty circuit"); }
+    for (uint32_t g = 0; g < q.n_gates; ++g) {
+      const ccs_gate& G = q.gates[g];
+      P.gates.push_back({(int)G.op, (int)G.q[0], (G.op == CCS_CX || G.op == CCS_CZ) ? (int)G.q[1] : -1});
+    }
+    P.marginal.assign(q.marginal, q.marginal + q.n_marginal);
+    for (uint32_t z = 0; z < q.n_zstrings; ++z)
+      P.zstrings.emplace_back(q.zstring_qubits + q.zstring_offsets[z], q.zstring_qubits + q.zstring_offsets[z + 1]);
+    if (q.n_cuts >= 0) {
+      if (q.n_cuts > 0 && !q.cuts) { delete plan; return fail(c, CCS_ERR_INVALID_ARG, "null cut list"); }
+      P.cuts.assign(q.cuts, q.cuts + q.n_cuts);
+      if ((int)P.cuts.size() > o.max_cuts) { delete plan; return fail(c, CCS_ERR_TOO_MANY_CUTS, "too many cuts"); }
+    } else {
+      CutSearchOpts so;
+      so.max_cuts = std::min(o.max_cuts, kMaxCuts);
+      so.max_nc_width = std::min(o.max_nc_width > 0 ? o.max_nc_width : 10, kMaxNCWidth);
+      std::vector<CutCandidate> cands;
+      int rc = greedy_cuts(P, so, cands, err);
+      if (rc != CCS_OK) { delete plan; return fail(c, rc, err); }
+      P.cuts = cands.front().cuts;
+    }
+    int rc = fragment_problem(P, pi, plan->frags, err);
+    if (rc != CCS_OK) { delete plan; return fail(c, rc, "problem " + std::to_string(pi) + ": " + err); }
+    plan->problems.push_back(std::move(P));
+  }
+
+  // --- flatten ---------------------------------------------------------------
+  std::vector<CliffordOp> cops;
+  std::vector<NCOp> nops;
+  std::vector<int> moments, wires, zoffs;
+  std::vector<int2> items_c, items_nc;
+  std::vector<long long> cost_c, cost_nc;
+  for (auto& f : plan->frags) {
+    if (f.clifford) compile_clifford(f);
+    else compile_nc(f);
+  }
+  for (size_t fi = 0; fi < plan->frags.size(); ++fi) {
+    Frag& f = plan->frags[fi];
+    FragDev d{};
+    d.n = f.n();
+    d.Wh = (d.n + 63) / 64;
+    d.W = 2 * d.Wh;
+    d.nA = f.n_meas();
+    d.m = (int)f.marg_wire.size();
+    d.qin = (int)f.qin_wire.size();
+    d.qout = (int)f.qout_wire.size();
+    d.nv = f.n_variants();
+    d.clifford = f.clifford ? 1 : 0;
+    d.problem = f.problem;
+    d.findex = f.index;
+    d.ops_off = f.clifford ? (int)cops.size() : (int)nops.size();
+    d.mom_off = (int)moments.size();
+    d.n_moments = f.n_moments();
+    for (int x : f.moment_start) moments.push_back(x);
+    if (f.clifford) cops.insert(cops.end(), f.cops.begin(), f.cops.end());
+    else nops.insert(nops.end(), f.nops.begin(), f.nops.end());
+    d.A_off = (int)wires.size();
+    for (int w : f.marg_wire) wires.push_back(w);
+    for (int w : f.qout_wire) wires.push_back(w);
+    d.qin_off = (int)wires.size();
+    for (int w : f.qin_wire) wires.push_back(w);
+    d.qout_off = (int)wires.size();
+    for (int w : f.qout_wire) wires.push_back(w);
+    d.nz = (int)f.zwires.size();
+    d.zw_off = (int)zoffs.size();
+    for (auto& zw : f.zwires) {
+      zoffs.push_back((int)wires.size());
+      for (int w : zw) wires.push_back(w);
+    }
+    zoffs.push_back((int)wires.size());
+    d.n_slots = (int)f.slots.size();
+    for (int j = 0; j < d.n_slots; ++j) {
+      d.slot_code[j] = (f.slot_kind[j] << 8) | f.slot_idx[j];
+      d.slot_cut[j] = f.slots[j];
+    }
+    for (int j = 0; j < d.m; ++j) d.marg_pos[j] = f.marg_pos[j];
+    const long long outs = 1ll << d.nA;
+    if (f.clifford) {
+      d.space_off = plan->n_spaces;
+      plan->n_spaces += d.nv;
+      d.counts_off = plan->n_counts;
+      plan->n_counts += (long long)d.nv * outs;
+      d.tab_off = plan->n_tab;
+      plan->n_tab += (long long)d.nv * (2 * d.n + 3) * d.W;
+      const int words = (2 * d.n + 3) * d.W + (d.n + 1) / 2 + 2;
+      plan->cliff_smem_words = std::max(plan->cliff_smem_words, words);
+      for (int v = 0; v < d.nv; ++v) {
+        items_c.push_back(make_int2((int)fi, v));
+        cost_c.push_back((long long)d.W * (d.n_moments + 4) * std::max(1, d.n / 16) + d.nz * 4 + d.nA * d.n);
+      }
+    } else {
+      d.space_off = d.counts_off = d.tab_off = -1;
+      plan->max_nc_n = std::max(plan->max_nc_n, d.n);
+      for (int v = 0; v < d.nv; ++v) {
+        items_nc.push_back(make_int2((int)fi, v));
+        cost_nc.push_back((1ll << d.n) * ((long long)f.nops.size() + 4));
+      }
+    }
+    d.dist_off = plan->n_dist;
+    plan->n_dist += (long long)d.nv * outs;
+    d.zval_off = plan->n_zval;
+    plan->n_zval += (long long)d.nv * d.nz * (1ll << d.qout);
+    d.T_off = plan->n_T;
+    plan->n_T += (1ll << d.m) * (1ll << (2 * d.n_slots));
+    d.TZ_off = plan->n_TZ;
+    plan->n_TZ += (long long)d.nz * (1ll << (2 * d.n_slots));
+    plan->fdev.push_back(d);
+  }
+  if ((size_t)plan->cliff_smem_words * 8 > c->smem_optin && !items_c.empty()) {
+    delete plan;
+    return fail(c, CCS_ERR_UNSUPPORTED, "Clifford fragment does not fit in shared memory");
+  }
+  auto sort_items = [](std::vector<int2>& it, std::vector<long long>& cost) {
+    std::vector<size_t> idx(it.size());
+    for (size_t i = 0; i < idx.size(); ++i) idx[i] = i;
+    std::stable_sort(idx.begin(), idx.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
+    std::vector<int2> out(it.size());
+    for (size_t i = 0; i < idx.size(); ++i) out[i] = it[idx[i]];
+    it.swap(out);
+  };
+  sort_items(items_c, cost_c);
+  sort_items(items_nc, cost_nc);
+
+  int f0 = 0;
+  plan->t_prefix.push_back(0);
+  plan->tz_prefix.push_back(0);
+  plan->out_prefix.push_back(0);
+  plan->z_prefix.push_back(0);
+  for (auto& f : plan->fdev) {
+    plan->t_prefix.push_back(plan->t_prefix.back() + (1ll << f.m) * (1ll << (2 * f.n_slots)));
+    plan->tz_prefix.push_back(plan->tz_prefix.back() + (long long)f.nz * (1ll << (2 * f.n_slots)));
+  }
+  for (auto& P : plan->problems) {
+    ProblemDev d{};
+    d.k = (int)P.cuts.size();
+    d.n_frags = (int)P.frag_ids.size();
+    d.frag0 = f0;
+    d.hub = P.hub;
+    d.n_marg = (int)P.marginal.size();
+    d.nz = (int)P.zstrings.size();
+    d.marg_off = plan->n_marg;
+    d.zexp_off = plan->n_zexp;
+    plan->n_marg += 1ll << d.n_marg;
+    plan->n_zexp += d.nz;
+    plan->out_prefix.push_back(plan->n_marg);
+    plan->z_prefix.push_back(plan->n_zexp);
+    if (P.hub < 0) plan->all_star = false;
+    f0 += d.n_frags;
+    plan->pdev.push_back(d);
+  }
+
+  std::vector<CliffordOp> prep(4), basis(3);
+  std::vector<float> prepm(32), basism(24);
+  for (int s = 0; s < 4; ++s) { prep[s] = prep_op(s); prep_matrix(s, &prepm[8 * s]); }
+  for (int b = 0; b < 3; ++b) { basis[b] = basis_op(b); basis_matrix(b, &basism[8 * b]); }
+
+  if (c->host_only) {
+    plan->dp.n_items_cliff = (int)items_c.size();
+    plan->dp.n_items_nc = (int)items_nc.size();
+    *out = plan;
+    return CCS_OK;
+  }
+  DevPlan& dp = plan->dp;
+  FragDev* dfr; CliffordOp* dco; NCOp* dno; int* dmo; int* dwi; int* dzo; int2* dic; int2* din;
+  ProblemDev* dpr; CliffordOp* dpo; CliffordOp* dbo; float* dpm; float* dbm;
+  bool ok = upload(c, plan->A, plan->fdev, &dfr) && upload(c, plan->A, cops, &dco) &&
+            upload(c, plan->A, nops, &dno) && upload(c, plan->A, moments, &dmo) &&
+            upload(c, plan->A, wires, &dwi) && upload(c, plan->A, zoffs, &dzo) &&
+            upload(c, plan->A, items_c, &dic) && upload(c, plan->A, items_nc, &din) &&
+            upload(c, plan->A, plan->pdev, &dpr) && upload(c, plan->A, prep, &dpo) &&
+            upload(c, plan->A, basis, &dbo) && upload(c, plan->A, prepm, &dpm) &&
+            upload(c, plan->A, basism, &dbm) &&
+            upload(c, plan->A, plan->t_prefix, &plan->d_t_prefix) &&
+            upload(c, plan->A, plan->tz_prefix, &plan->d_tz_prefix) &&
+            upload(c, plan->A, plan->out_prefix, &plan->d_out_prefix) &&
+            upload(c, plan->A, plan->z_prefix, &plan->d_z_prefix);
+  if (!ok) { delete plan; return fail(c, CCS_ERR_OOM, "plan upload failed"); }
+  dp.frags = dfr; dp.cops = dco; dp.nops = dno; dp.moments = dmo; dp.wires = dwi; dp.zoffs = dzo;
+  dp.items_cliff = dic; dp.items_nc = din;
+  dp.n_items_cliff = (int)items_c.size(); dp.n_items_nc = (int)items_nc.size();
+  dp.problems = dpr; dp.n_problems = (int)plan->pdev.size();
+  dp.prep_ops = dpo; dp.basis_ops = dbo; dp.prep_mats = dpm; dp.basis_mats = dbm;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) { delete plan; return cuda_fail(c, e, "plan upload"); }
+  *out = plan;
+  return CCS_OK;
+}
+
+void ccs_plan_free(ccs_plan p) { delete p; }
+
+static int enqueue_eval(ccs_ctx c, ccs_plan p, ccs_res r) {
+  cudaStream_t s = c->stream;
+  const EvalParams& e = r->ep;
+  cudaError_t err;
+  if ((err = cudaMemsetAsync(r->dr.work, 0, 4 * sizeof(unsigned), s)) != cudaSuccess) return cuda_fail(c, err, "memset");
+  if (e.mode == CCS_SAMPLED && p->n_counts)
+    if ((err = cudaMemsetAsync(r->dr.counts, 0, p->n_counts * sizeof(uint32_t), s)) != cudaSuccess)
+      return cuda_fail(c, err, "memset counts");
+  if (e.mode == CCS_EXACT && p->n_dist)
+    if ((err = cudaMemsetAsync(r->dr.dist, 0, p->n_dist * sizeof(float), s)) != cudaSuccess)
+      return cuda_fail(c, err, "memset dist");
+  const DevPlan& dp = p->dp;
+  if (dp.n_items_cliff) {
+    const int threads = r->cliff_threads;
+    const size_t smem = (size_t)p->cliff_smem_words * 8;
+    int per_sm = (int)std::max<size_t>(1, std::min<size_t>(2048 / threads, (c->smem_optin + 1024) / (smem + 2048)));
+    int grid = std::min(dp.n_items_cliff, c->sm_count * per_sm);
+    stage_begin(c, ST_CLIFFORD);
+    if ((err = launch_clifford(dp, r->dr, e, threads, p->cliff_smem_words, grid, s)) != cudaSuccess)
+      return cuda_fail(c, err, "clifford kernel");
+    stage_end(c, ST_CLIFFORD);
+    if (e.mode == CCS_SAMPLED) {
+      stage_begin(c, ST_SAMPLE);
+      if ((err = launch_sample(dp, r->dr, e, r->sample_spc, 256, s)) != cudaSuccess)
+        return cuda_fail(c, err, "sample kernel");
+      stage_end(c, ST_SAMPLE);
+    }
+  }
+  if (dp.n_items_nc) {
+    int grid = std::min(dp.n_items_nc, c->sm_count * 4);
+    int threads = std::min(256, std::max(32, 1 << std::max(0, p->max_nc_n - 2)));
+    stage_begin(c, ST_STATEVEC);
+    if ((err = launch_statevector(dp, r->dr, p->max_nc_n, threads, grid, s)) != cudaSuccess)
+      return cuda_fail(c, err, "statevector kernel");
+    stage_end(c, ST_STATEVEC);
+  }
+  stage_begin(c, ST_FOLD);
+  if ((err = launch_fold(dp, r->dr, e, p->d_t_prefix, (int)p->fdev.size(), p->n_T, p->d_tz_prefix, p->n_TZ, s)) !=
+      cudaSuccess)
+    return cuda_fail(c, err, "fold kernel");
+  stage_end(c, ST_FOLD);
+  return CCS_OK;
+}
+
+int ccs_eval_variants(ccs_ctx c, ccs_plan p, const ccs_eval_opts* opts, ccs_res* res) {
+  if (!c || !p || !opts || !res) return fail(c, CCS_ERR_INVALID_ARG, "bad arguments");
+  if (opts->mode != CCS_EXACT && opts->mode != CCS_SAMPLED) return fail(c, CCS_ERR_INVALID_ARG, "bad mode");
+  if (opts->mode == CCS_SAMPLED && opts->shots == 0) return fail(c, CCS_ERR_INVALID_ARG, "zero shots");
+  if (c->host_only) return fail(c, CCS_ERR_UNSUPPORTED, "host-only context cannot evaluate");
+  cudaSetDevice(c->device);
+  ccs_res r = *res;
+  if (r && r->plan != p) return fail(c, CCS_ERR_INVALID_ARG, "result belongs to another plan");
+  if (!r) {
+    r = new ccs_res_s();
+    r->plan = p;
+    r->A.ctx = c;
+    DevRes& d = r->dr;
+    d.spaces = r->A.get<SpaceRec>(std::max<long long>(p->n_spaces, 1));
+    d.dist = r->A.get<float>(std::max<long long>(p->n_dist, 1));
+    d.zval = r->A.get<float>(std::max<long long>(p->n_zval, 1));
+    d.T = r->A.get<float>(std::max<long long>(p->n_T, 1));
+    d.TZ = r->A.get<float>(std::max<long long>(p->n_TZ, 1));
+    d.marg = r->A.get<double>(std::max<long long>(p->n_marg, 1));
+    d.zexp = r->A.get<double>(std::max<long long>(p->n_zexp, 1));
+    d.work = r->A.get<unsigned>(4);
+    d.status = r->A.get<unsigned>(4);
+    if (!d.spaces || !d.dist || !d.zval || !d.T || !d.TZ || !d.marg || !d.zexp || !d.work || !d.status) {
+      delete r;
+      return fail(c, CCS_ERR_OOM, "result allocation failed");
+    }
+    cudaMemsetAsync(d.status, 0, 4 * sizeof(unsigned), c->stream);
+    *res = r;
+  }
+  if (opts->mode == CCS_SAMPLED && !r->have_counts && p->n_counts) {
+    r->dr.counts = r->A.get<uint32_t>(p->n_counts);
+    if (!r->dr.counts) return fail(c, CCS_ERR_OOM, "counts allocation failed");
+    r->have_counts = true;
+  }
+  if (opts->keep_tableaus && !r->have_tabs && p->n_tab) {
+    r->dr.tabs = r->A.get<unsigned long long>(p->n_tab);
+    if (!r->dr.tabs) return fail(c, CCS_ERR_OOM, "tableau allocation failed");
+    r->have_tabs = true;
+  }
+  EvalParams e{};
+  e.mode = opts->mode;
+  e.shots = opts->mode == CCS_SAMPLED ? opts->shots : 0;
+  e.seed_lo = opts->seed_lo;
+  e.seed_hi = opts->seed_hi;
+  e.keep_tableaus = opts->keep_tableaus && r->have_tabs;
+  e.inv_shots = e.shots ? 1.0 / (double)e.shots : 0.0;
+  r->ep = e;
+  if (!opts->use_graph || c->profiling) {
+    c->stage_mask = 0;
+    return enqueue_eval(c, p, r);
+  }
+  const bool same = r->graph && r->graph_key.mode == e.mode && r->graph_key.shots == e.shots &&
+                    r->graph_key.seed_lo == e.seed_lo && r->graph_key.seed_hi == e.seed_hi &&
+                    r->graph_key.keep_tableaus == e.keep_tableaus;
+  if (!same) {
+    if (r->graph) { cudaGraphExecDestroy(r->graph); r->graph = nullptr; }
+    cudaStream_t s = c->stream;
+    bool tmp_stream = false;
+    if (s == nullptr) {   // the legacy stream cannot be captured
+      if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return fail(c, CCS_ERR_CUDA, "stream");
+      tmp_stream = true;
+    }
+    cudaStream_t saved = c->stream;
+    c->stream = s;
+    cudaGraph_t g;
+    cudaError_t err = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (err != cudaSuccess) { c->stream = saved; return cuda_fail(c, err, "begin capture"); }
+    int rc = enqueue_eval(c, p, r);
+    err = cudaStreamEndCapture(s, &g);
+    c->stream = saved;
+    if (tmp_stream) cudaStreamDestroy(s);
+    if (rc != CCS_OK) return rc;
+    if (err != cudaSuccess) return cuda_fail(c, err, "end capture");
+    err = cudaGraphInstantiate(&r->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (err != cudaSuccess) return cuda_fail(c, err, "graph instantiate");
+    r->graph_key = e;
+  }
+  cudaError_t err = cudaGraphLaunch(r->graph, c->stream);
+  if (err != cudaSuccess) return cuda_fail(c, err, "graph launch");
+  return CCS_OK;
+}
+
+void ccs_res_free(ccs_res r) { delete r; }
+
+static int check_status(ccs_ctx c, ccs_res r) {
+  unsigned st[4];
+  cudaError_t e = cudaMemcpyAsync(st, r->dr.status, sizeof(st), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "synchronize");
+  if (st[0]) return fail(c, CCS_ERR_DEVICE_CHECK, "device consistency check failed (code " + std::to_string(st[0]) + ")");
+  return CCS_OK;
+}
+
+int ccs_recombine(ccs_ctx c, ccs_plan p, ccs_res r, const ccs_recomb_opts* opts, double* marginal_out,
+                  double* zexp_out) {
+  if (!c || !p || !r || r->plan != p) return fail(c, CCS_ERR_INVALID_ARG, "bad arguments");
+  if (c->host_only) return fail(c, CCS_ERR_UNSUPPORTED, "host-only context cannot recombine");
+  if (!p->all_star) return fail(c, CCS_ERR_UNSUPPORTED, "fragments do not form a star");
+  const int prec = opts ? opts->precision : CCS_FP32;
+  const bool on_dev = opts && opts->outputs_on_device;
+  if (prec != CCS_FP32 && prec != CCS_BF16) return fail(c, CCS_ERR_INVALID_ARG, "bad precision");
+  cudaSetDevice(c->device);
+  stage_begin(c, ST_RECOMB);
+  cudaError_t e = launch_recombine(p->dp, r->dr, prec, p->d_out_prefix, p->n_marg, p->d_z_prefix, p->n_zexp,
+                                   c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "recombine kernel");
+  stage_end(c, ST_RECOMB);
+  const cudaMemcpyKind kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (marginal_out && p->n_marg)
+    if ((e = cudaMemcpyAsync(marginal_out, r->dr.marg, p->n_marg * sizeof(double), kind, c->stream)) != cudaSuccess)
+      return cuda_fail(c, e, "copy marginal");
+  if (zexp_out && p->n_zexp)
+    if ((e = cudaMemcpyAsync(zexp_out, r->dr.zexp, p->n_zexp * sizeof(double), kind, c->stream)) != cudaSuccess)
+      return cuda_fail(c, e, "copy zexp");
+  if (on_dev) return CCS_OK;
+  return check_status(c, r);
+}
+
+// --- inspection -------------------------------------------------------------
+static const Frag* find_frag(ccs_plan p, int problem, int fragment, int* global) {
+  if (problem < 0 || problem >= (int)p->problems.size()) return nullptr;
+  const Problem& P = p->problems[problem];
+  if (fragment < 0 || fragment >= (int)P.frag_ids.size()) return nullptr;
+  *global = P.frag_ids[fragment];
+  return &p->frags[*global];
+}
+
+int ccs_plan_counts(ccs_ctx c, ccs_plan p, int problem, int* nf, int* nc) {
+  if (!p || problem < 0 || problem >= (int)p->problems.size()) return fail(c, CCS_ERR_INVALID_ARG, "bad problem");
+  if (nf) *nf = (int)p->problems[problem].frag_ids.size();
+  if (nc) *nc = (int)p->problems[problem].cuts.size();
+  return CCS_OK;
+}
+
+int ccs_fragment_info_get(ccs_ctx c, ccs_plan p, int problem, int fragment, ccs_fragment_info* out) {
+  int g;
+  const Frag* f = p ? find_frag(p, problem, fragment, &g) : nullptr;
+  if (!f || !out) return fail(c, CCS_ERR_INVALID_ARG, "bad fragment");
+  out->n_wires = f->n();
+  out->clifford = f->clifford;
+  out->n_variants = f->n_variants();
+  out->n_qin = (int)f->qin_wire.size();
+  out->n_qout = (int)f->qout_wire.size();
+  out->n_marg = (int)f->marg_wire.size();
+  out->n_meas = f->n_meas();
+  out->n_slots = (int)f->slots.size();
+  out->n_ops = f->clifford ? (int)f->cops.size() : (int)f->nops.size();
+  out->n_moments = f->n_moments();
+  return CCS_OK;
+}
+
+int ccs_plan_cuts(ccs_ctx c, ccs_plan p, int problem, ccs_cut* out, int cap) {
+  if (!p || problem < 0 || problem >= (int)p->problems.size()) return fail(c, CCS_ERR_INVALID_ARG, "bad problem");
+  const auto& cuts = p->problems[problem].cuts;
+  if (cap < (int)cuts.size()) return fail(c, CCS_ERR_INVALID_ARG, "buffer too small");
+  for (size_t i = 0; i < cuts.size(); ++i) out[i] = cuts[i];
+  return (int)cuts.size();
+}
+
+int ccs_fragment_wires(ccs_ctx c, ccs_plan p, int problem, int fragment, uint32_t* out) {
+  int g;
+  const Frag* f = p ? find_frag(p, problem, fragment, &g) : nullptr;
+  if (!f || !out) return fail(c, CCS_ERR_INVALID_ARG, "bad fragment");
+  for (int i = 0; i < f->n(); ++i) { out[2 * i] = f->wires[i].first; out[2 * i + 1] = f->wires[i].second; }
+  return CCS_OK;
+}
+
+static int locate(ccs_ctx c, ccs_res r, int problem, int fragment, int variant, const FragDev** fd) {
+  if (!c || !r) return fail(c, CCS_ERR_INVALID_ARG, "bad arguments");
+  int g;
+  const Frag* f = find_frag(r->plan, problem, fragment, &g);
+  if (!f) return fail(c, CCS_ERR_INVALID_ARG, "bad fragment");
+  if (variant < -1 || variant >= f->n_variants()) return fail(c, CCS_ERR_INVALID_ARG, "bad variant");
+  *fd = &r->plan->fdev[g];
+  cudaSetDevice(c->device);
+  return check_status(c, r);
+}
+
+int ccs_get_tableau(ccs_ctx c, ccs_res r, int problem, int fragment, int variant, uint8_t* out) {
+  const FragDev* d;
+  int rc = locate(c, r, problem, fragment, variant, &d);
+  if (rc) return rc;
+  if (!d->clifford || !r->ep.keep_tableaus || variant < 0) return fail(c, CCS_ERR_INVALID_ARG, "no tableau kept");
+  const int n = d->n, W = d->W, Wh = d->Wh, ncol = 2 * n + 3;
+  std::vector<unsigned long long> h((size_t)ncol * W);
+  cudaError_t e = cudaMemcpy(h.data(), r->dr.tabs + d->tab_off + (long long)variant * ncol * W,
+                             h.size() * 8, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "copy tableau");
+  auto bit = [&](int col, int row) -> uint8_t {
+    const int word = row < n ? row / 64 : Wh + (row - n) / 64;
+    const int b = row < n ? row % 64 : (row - n) % 64;
+    return (uint8_t)((h[(size_t)col * W + word] >> b) & 1ull);
+  };
+  for (int row = 0; row < 2 * n; ++row) {
+    uint8_t* o = out + (size_t)row * (2 * n + 1);
+    for (int j = 0; j < n; ++j) { o[j] = bit(j, row); o[n + j] = bit(n + 1 + j, row); }
+    o[2 * n] = bit(2 * (n + 1), row);
+  }
+  return CCS_OK;
+}
+
+int ccs_get_outcome_space(ccs_ctx c, ccs_res r, int problem, int fragment, int variant, uint64_t* off,
+                          uint64_t* basis, int* rank) {
+  const FragDev* d;
+  int rc = locate(c, r, problem, fragment, variant, &d);
+  if (rc) return rc;
+  if (!d->clifford || variant < 0) return fail(c, CCS_ERR_INVALID_ARG, "not a Clifford variant");
+  SpaceRec s;
+  cudaError_t e = cudaMemcpy(&s, r->dr.spaces + d->space_off + variant, sizeof(s), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "copy space");
+  if (off) *off = s.off;
+  if (rank) *rank = s.rank;
+  if (basis)
+    for (int i = 0; i < s.rank; ++i) basis[i] = s.basis[i];
+  return CCS_OK;
+}
+
+int ccs_get_counts(ccs_ctx c, ccs_res r, int problem, int fragment, int variant, uint32_t* out) {
+  const FragDev* d;
+  int rc = locate(c, r, problem, fragment, variant, &d);
+  if (rc) return rc;
+  if (!d->clifford || r->ep.mode != CCS_SAMPLED || variant < 0) return fail(c, CCS_ERR_INVALID_ARG, "no counts");
+  cudaError_t e = cudaMemcpy(out, r->dr.counts + d->counts_off + ((long long)variant << d->nA),
+                             sizeof(uint32_t) << d->nA, cudaMemcpyDeviceToHost);
+  return e == cudaSuccess ? CCS_OK : cuda_fail(c, e, "copy counts");
+}
+
+int ccs_get_dist(ccs_ctx c, ccs_res r, int problem, int fragment, int variant, float* out) {
+  const FragDev* d;
+  int rc = locate(c, r, problem, fragment, variant, &d);
+  if (rc) return rc;
+  if ((d->clifford && r->ep.mode != CCS_EXACT) || variant < 0) return fail(c, CCS_ERR_INVALID_ARG, "no distribution");
+  cudaError_t e = cudaMemcpy(out, r->dr.dist + d->dist_off + ((long long)variant << d->nA),
+                             sizeof(float) << d->nA, cudaMemcpyDeviceToHost);
+  return e == cudaSuccess ? CCS_OK : cuda_fail(c, e, "copy dist");
+}
+
+int ccs_get_tensor(ccs_ctx c, ccs_res r, int problem, int fragment, float* out) {
+  const FragDev* d;
+  int rc = locate(c, r, problem, fragment, -1, &d);
+  if (rc) return rc;
+  const long long cnt = (1ll << d->m) << (2 * d->n_slots);
+  cudaError_t e = cudaMemcpy(out, r->dr.T + d->T_off, cnt * sizeof(float), cudaMemcpyDeviceToHost);
+  return e == cudaSuccess ? CCS_OK : cuda_fail(c, e, "copy tensor");
+}
+
+}  // extern "C"

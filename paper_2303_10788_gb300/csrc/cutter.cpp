@@ -1,0 +1,315 @@
+// Greedy cut search (Sec. V-A): the cutter tags non-Clifford operations and
+// places wire cuts that isolate them into small non-Clifford fragments, the
+// rest of the circuit staying Clifford.  The paper gives no search algorithm;
+// this one grows regions from the non-Clifford gates:
+//
+//   * a region is a set of wire windows (qubit q, gate positions [a, b) of
+//     q's gate list); its gates are those inside every window they touch, and
+//     it is closed: a two-qubit gate inside one window is inside its partner's
+//     window too;
+//   * each window costs a cut before it (a > 0) and after it (b < len);
+//   * every non-Clifford gate seeds a one-gate window; overlapping regions
+//     are merged;
+//   * moves: widen a window by one gate, widen it to the start or end of its
+//     wire or to the whole wire, or merge two regions (each followed by
+//     closure); a beam of the cheapest states by estimated cost is expanded
+//     (uphill moves allowed) until the best valid candidate stops improving;
+//   * cost = sum over fragments of variants x per-variant work + 4^k 2^|o|
+//     recombination work, with region width capped at max_nc_width.
+// Every visited state that is a valid star (one Clifford fragment on every
+// cut) within the cut budget is kept as a candidate, cheapest first.
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <set>
+
+#include "plan.hpp"
+
+namespace ccs {
+
+namespace {
+
+struct Window {
+  int q, a, b;
+};
+using Region = std::vector<Window>;   // sorted by qubit, one window per qubit
+
+struct Ctx {
+  const Problem* P;
+  int n;
+  std::vector<std::vector<int>> ops_on;      // gate indices per qubit
+  std::vector<std::array<int, 2>> pos_of;    // position of gate g in ops_on[q0], ops_on[q1]
+  std::vector<int> nonclifford;
+};
+
+bool two_qubit(int op) { return op == CCS_CX || op == CCS_CZ; }
+
+Window* find_w(Region& r, int q) {
+  for (auto& w : r)
+    if (w.q == q) return &w;
+  return nullptr;
+}
+
+// Close a region under two-qubit gates.
+void close_region(const Ctx& C, Region& r) {
+  bool changed = true;
+  while (changed) {
+    changed = false;
+    for (size_t i = 0; i < r.size(); ++i) {
+      const Window w = r[i];
+      for (int pos = w.a; pos < w.b; ++pos) {
+        const int g = C.ops_on[w.q][pos];
+        const auto& G = C.P->gates[g];
+        if (!two_qubit(G[0])) continue;
+        const int p = G[1] == w.q ? G[2] : G[1];
+        const int pp = C.pos_of[g][G[1] == w.q ? 1 : 0];
+        Window* o = find_w(r, p);
+        if (!o) {
+          r.push_back({p, pp, pp + 1});
+          changed = true;
+        } else if (pp < o->a || pp >= o->b) {
+          o->a = std::min(o->a, pp);
+          o->b = std::max(o->b, pp + 1);
+          changed = true;
+        }
+      }
+    }
+  }
+  std::sort(r.begin(), r.end(), [](const Window& x, const Window& y) { return x.q < y.q; });
+}
+
+bool overlap(const Region& x, const Region& y) {
+  for (auto& a : x)
+    for (auto& b : y)
+      if (a.q == b.q && a.a < b.b && b.a < a.b) return true;
+  return false;
+}
+
+Region merge(const Region& x, const Region& y) {
+  Region r = x;
+  for (auto& w : y) {
+    Window* o = find_w(r, w.q);
+    if (!o) r.push_back(w);
+    else { o->a = std::min(o->a, w.a); o->b = std::max(o->b, w.b); }
+  }
+  return r;
+}
+
+// Merge overlapping regions and re-close until stable.
+void normalise(const Ctx& C, std::vector<Region>& rs) {
+  for (auto& r : rs) close_region(C, r);
+  bool changed = true;
+  while (changed) {
+    changed = false;
+    for (size_t i = 0; i < rs.size() && !changed; ++i)
+      for (size_t j = i + 1; j < rs.size() && !changed; ++j)
+        if (overlap(rs[i], rs[j])) {
+          rs[i] = merge(rs[i], rs[j]);
+          close_region(C, rs[i]);
+          rs.erase(rs.begin() + j);
+          changed = true;
+        }
+  }
+  std::sort(rs.begin(), rs.end(), [](const Region& x, const Region& y) {
+    return std::make_pair(x[0].q, x[0].a) < std::make_pair(y[0].q, y[0].a);
+  });
+}
+
+std::vector<ccs_cut> cuts_of(const Ctx& C, const std::vector<Region>& rs) {
+  std::vector<ccs_cut> cuts;
+  for (auto& r : rs)
+    for (auto& w : r) {
+      const int len = (int)C.ops_on[w.q].size();
+      if (w.a > 0) cuts.push_back({(uint32_t)w.q, (uint32_t)C.ops_on[w.q][w.a]});
+      if (w.b < len) cuts.push_back({(uint32_t)w.q, (uint32_t)C.ops_on[w.q][w.b]});
+    }
+  std::sort(cuts.begin(), cuts.end(), [](const ccs_cut& x, const ccs_cut& y) {
+    return x.gate_index != y.gate_index ? x.gate_index < y.gate_index : x.qubit < y.qubit;
+  });
+  cuts.erase(std::unique(cuts.begin(), cuts.end(), [](const ccs_cut& x, const ccs_cut& y) {
+               return x.qubit == y.qubit && x.gate_index == y.gate_index;
+             }), cuts.end());
+  return cuts;
+}
+
+// Estimated work of a state straight from its windows (the Clifford rest is
+// taken as one fragment).
+double estimate(const Ctx& C, const std::vector<Region>& rs, int max_width, bool* ok) {
+  *ok = true;
+  const int n = C.n;
+  long long nc_gates_total = 0;
+  double cost = 0.0;
+  int k = 0, body_qin = 0, body_qout = 0, body_wires = n, body_marg = 0, nc_marg = 0;
+  std::set<int> marg(C.P->marginal.begin(), C.P->marginal.end());
+  for (auto& r : rs) {
+    int width = (int)r.size(), qin = 0, qout = 0;
+    long long gates = 0;
+    std::set<int> inside;
+    for (auto& w : r)
+      for (int p = w.a; p < w.b; ++p) inside.insert(C.ops_on[w.q][p]);
+    gates = (long long)inside.size();
+    for (auto& w : r) {
+      const int len = (int)C.ops_on[w.q].size();
+      const bool pre = w.a > 0, post = w.b < len;
+      qin += pre;
+      qout += post;
+      body_wires += (pre && post) ? 1 : (!pre && !post) ? -1 : 0;
+      if (!post && marg.count(w.q)) ++nc_marg;
+    }
+    if (width > max_width) *ok = false;
+    k += qin + qout;
+    body_qin += qout;
+    body_qout += qin;
+    nc_gates_total += gates;
+    cost += std::pow(4.0, qin) * std::pow(3.0, qout) * (double)gates * std::ldexp(1.0, width) / 64.0;
+  }
+  body_marg = (int)marg.size() - nc_marg;
+  const long long body_gates = (long long)C.P->gates.size() - nc_gates_total;
+  const double W = 2.0 * std::ceil(std::max(1, body_wires) / 64.0);
+  cost += std::pow(4.0, body_qin) * std::pow(3.0, body_qout) * ((double)body_gates / 6.0 * W + 1024.0);
+  cost += std::pow(4.0, k) * std::ldexp(1.0, body_marg + nc_marg) / 16.0;
+  (void)body_marg;
+  return cost;
+}
+
+}  // namespace
+
+double plan_cost(const Problem& p, const std::vector<ccs_cut>& cuts, bool* ok) {
+  Problem q = p;
+  q.cuts = cuts;
+  std::vector<Frag> frags;
+  std::string err;
+  if (fragment_problem(q, 0, frags, err) != CCS_OK || q.hub < 0) {
+    if (ok) *ok = false;
+    return INFINITY;
+  }
+  double cost = 0.0;
+  for (auto& f : frags) {
+    const double nv = (double)f.n_variants();
+    if (f.clifford) cost += nv * ((double)f.gates.size() / 6.0 * 2.0 * std::ceil(f.n() / 64.0) + 1024.0);
+    else cost += nv * (double)f.gates.size() * std::ldexp(1.0, f.n()) / 64.0;
+  }
+  cost += std::pow(4.0, (double)cuts.size()) * std::ldexp(1.0, (int)p.marginal.size()) / 16.0;
+  if (ok) *ok = true;
+  return cost;
+}
+
+int greedy_cuts(const Problem& p, const CutSearchOpts& o, std::vector<CutCandidate>& cands, std::string& err) {
+  Ctx C;
+  C.P = &p;
+  C.n = (int)p.n_qubits;
+  C.ops_on.assign(C.n, {});
+  C.pos_of.assign(p.gates.size(), {-1, -1});
+  for (int g = 0; g < (int)p.gates.size(); ++g) {
+    const auto& G = p.gates[g];
+    if (G[1] < 0 || G[1] >= C.n || (two_qubit(G[0]) && (G[2] < 0 || G[2] >= C.n))) {
+      err = "gate qubit out of range";
+      return CCS_ERR_INVALID_ARG;
+    }
+    C.pos_of[g][0] = (int)C.ops_on[G[1]].size();
+    C.ops_on[G[1]].push_back(g);
+    if (two_qubit(G[0])) {
+      C.pos_of[g][1] = (int)C.ops_on[G[2]].size();
+      C.ops_on[G[2]].push_back(g);
+    }
+    if (G[0] == CCS_T || G[0] == CCS_TDG) C.nonclifford.push_back(g);
+  }
+  cands.clear();
+  if (C.nonclifford.empty()) {
+    cands.push_back({{}, 0.0, {}});
+    return CCS_OK;
+  }
+  std::vector<Region> state;
+  for (int g : C.nonclifford) {
+    const int q = p.gates[g][1];
+    state.push_back({{q, C.pos_of[g][0], C.pos_of[g][0] + 1}});
+  }
+  normalise(C, state);
+  std::map<std::vector<std::pair<int, int>>, double> seen;
+  auto key_of = [&](const std::vector<Region>& s) {
+    std::vector<std::pair<int, int>> key;
+    for (auto& r : s) {
+      for (auto& w : r) key.push_back({w.q * 4 + 0, w.a}), key.push_back({w.q * 4 + 1, w.b});
+      key.push_back({-1, -1});
+    }
+    return key;
+  };
+  std::set<std::vector<std::pair<int, int>>> cut_seen;
+  auto record = [&](const std::vector<Region>& s) {
+    for (auto& r : s)
+      if ((int)r.size() > o.max_nc_width) return;
+    auto cuts = cuts_of(C, s);
+    if ((int)cuts.size() > o.max_cuts) return;
+    std::vector<std::pair<int, int>> key;
+    for (auto& c : cuts) key.push_back({(int)c.qubit, (int)c.gate_index});
+    if (!cut_seen.insert(key).second) return;
+    bool valid;
+    const double cost = plan_cost(p, cuts, &valid);
+    if (valid) cands.push_back({cuts, cost, {}});
+  };
+  // Beam search over region states (uphill moves allowed, so closures that
+  // first add cuts and then remove them are found).
+  struct Item { double cost; std::vector<Region> s; };
+  const int beam = 6;
+  bool ok;
+  std::vector<Item> frontier{{estimate(C, state, o.max_nc_width, &ok), state}};
+  record(state);
+  double best_valid = INFINITY;
+  int stale = 0;
+  for (int iter = 0; iter < 2 * C.n + 64 && stale < 12; ++iter) {
+    std::vector<Item> next;
+    std::set<std::vector<std::pair<int, int>>> in_next;
+    auto consider = [&](std::vector<Region> s) {
+      normalise(C, s);
+      bool ok2;
+      const double c2 = estimate(C, s, o.max_nc_width, &ok2);
+      if (!ok2) return;
+      auto key = key_of(s);
+      if (seen.count(key)) return;
+      seen[key] = c2;
+      if (!in_next.insert(key).second) return;
+      next.push_back({c2, std::move(s)});
+    };
+    for (auto& it : frontier) {
+      const auto& st = it.s;
+      for (size_t ri = 0; ri < st.size(); ++ri) {
+        for (size_t wi = 0; wi < st[ri].size(); ++wi) {
+          const Window w = st[ri][wi];
+          const int len = (int)C.ops_on[w.q].size();
+          if (w.a > 0) {
+            auto s1 = st; s1[ri][wi].a = w.a - 1; consider(s1);
+            if (w.a > 1) { auto s2 = st; s2[ri][wi].a = 0; consider(s2); }
+          }
+          if (w.b < len) {
+            auto s1 = st; s1[ri][wi].b = w.b + 1; consider(s1);
+            if (w.b < len - 1) { auto s2 = st; s2[ri][wi].b = len; consider(s2); }
+          }
+          if (w.a > 0 && w.b < len) { auto s3 = st; s3[ri][wi].a = 0; s3[ri][wi].b = len; consider(s3); }
+        }
+        for (size_t rj = ri + 1; rj < st.size(); ++rj) {
+          auto s4 = st;
+          s4[ri] = merge(s4[ri], s4[rj]);
+          s4.erase(s4.begin() + rj);
+          consider(s4);
+        }
+      }
+    }
+    if (next.empty()) break;
+    std::stable_sort(next.begin(), next.end(), [](const Item& x, const Item& y) { return x.cost < y.cost; });
+    if ((int)next.size() > beam) next.resize(beam);
+    for (auto& it : next) record(it.s);
+    double bv = INFINITY;
+    for (auto& c : cands) bv = std::min(bv, c.cost);
+    if (bv < best_valid) { best_valid = bv; stale = 0; } else { ++stale; }
+    frontier.swap(next);
+  }
+  if (cands.empty()) {
+    err = "no valid cut set within the cut and width limits";
+    return CCS_ERR_TOO_MANY_CUTS;
+  }
+  std::stable_sort(cands.begin(), cands.end(),
+                   [](const CutCandidate& x, const CutCandidate& y) { return x.cost < y.cost; });
+  return CCS_OK;
+}
+
+}  // namespace ccs

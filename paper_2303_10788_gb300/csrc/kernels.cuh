@@ -1,0 +1,103 @@
+// Device-side plan records and kernel launchers of the circuit-cutting hot path.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "plan.hpp"
+
+namespace ccs {
+
+// One fragment as the kernels see it (all offsets index flat device arrays).
+struct FragDev {
+  int n, W, Wh;            // wires; tableau words per column (2*Wh) and per half
+  int nA, m, qin, qout;    // |A_f|, marginal bits, quantum inputs / outputs
+  int nv, clifford;        // variants; 1 = tableau, 0 = statevector
+  int problem, findex;     // Philox counter words 3 and 2
+  int ops_off, mom_off, n_moments;
+  int A_off, qin_off, qout_off;   // into the wire-list array
+  int nz, zw_off;          // Z-strings: nz+1 offsets at zoffs[zw_off..] into the wire-list array
+  int n_slots;
+  int slot_code[kMaxCuts]; // (kind << 8) | index into qin/qout
+  int slot_cut[kMaxCuts];  // cut id within the problem
+  int marg_pos[kMaxMarginal];
+  long long space_off;     // SpaceRec index of variant 0
+  long long counts_off;    // uint32 index of variant 0 (2^nA each)
+  long long dist_off;      // float index of variant 0 (2^nA each)
+  long long zval_off;      // float index of variant 0 (nz * 2^qout each)
+  long long tab_off;       // uint64 index of variant 0 ((2n+3)*W each), -1 if not kept
+  long long T_off;         // float index of T_f (2^m x 4^n_slots)
+  long long TZ_off;        // float index of T_f^S (nz x 4^n_slots)
+};
+
+// Canonical affine outcome space of a Clifford variant.
+struct SpaceRec {
+  uint32_t off;
+  int32_t rank;
+  uint32_t basis[kMaxMeas];
+  uint32_t flags;          // nonzero: a device-side consistency check failed
+  uint32_t pad;
+};
+
+struct ProblemDev {
+  int k, n_frags, frag0;   // cuts, fragments, first FragDev index
+  int hub;                 // local index of the star's hub
+  int n_marg, nz;
+  long long marg_off, zexp_off;   // double indices into the outputs
+};
+
+// Device views of a plan + result.
+struct DevPlan {
+  const FragDev* frags;
+  const CliffordOp* cops;
+  const NCOp* nops;
+  const int* moments;
+  const int* wires;
+  const int* zoffs;
+  const int2* items_cliff;    // (frag, variant), costliest first
+  const int2* items_nc;
+  int n_items_cliff, n_items_nc;
+  const ProblemDev* problems;
+  int n_problems;
+  const CliffordOp* prep_ops;  // 4
+  const CliffordOp* basis_ops; // 3
+  const float* prep_mats;      // 4 x 8
+  const float* basis_mats;     // 3 x 8
+};
+
+struct DevRes {
+  SpaceRec* spaces;
+  uint32_t* counts;
+  float* dist;
+  float* zval;
+  unsigned long long* tabs;
+  float* T;
+  float* TZ;
+  double* marg;
+  double* zexp;
+  unsigned int* work;         // persistent-kernel work counters
+  unsigned int* status;       // device-side error word
+};
+
+struct EvalParams {
+  int mode;                   // CCS_EXACT / CCS_SAMPLED
+  uint32_t shots, seed_lo, seed_hi;
+  int keep_tableaus;
+  double inv_shots;
+};
+
+// Kernel launchers (stream-ordered; return cudaError_t of the launch).
+cudaError_t launch_clifford(const DevPlan& p, const DevRes& r, const EvalParams& e,
+                            int threads, int smem_words, int grid, cudaStream_t s);
+cudaError_t launch_sample(const DevPlan& p, const DevRes& r, const EvalParams& e,
+                          int shots_per_cta, int threads, cudaStream_t s);
+cudaError_t launch_statevector(const DevPlan& p, const DevRes& r, int max_n, int threads,
+                               int grid, cudaStream_t s);
+cudaError_t launch_fold(const DevPlan& p, const DevRes& r, const EvalParams& e,
+                        const long long* t_prefix, int n_frags_total, long long total,
+                        const long long* tz_prefix, long long total_z, cudaStream_t s);
+cudaError_t launch_recombine(const DevPlan& p, const DevRes& r, int precision,
+                             const long long* out_prefix, long long total_out,
+                             const long long* z_prefix, long long total_z, cudaStream_t s);
+
+}  // namespace ccs

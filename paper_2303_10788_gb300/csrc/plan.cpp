@@ -1,0 +1,399 @@
+// Fragmenting (Sec. V-A), variant bookkeeping (Sec. V-B) and gate-stream
+// compilation for the device kernels.
+#include "plan.hpp"
+
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <numeric>
+
+namespace ccs {
+
+namespace {
+
+bool is_two_qubit(int op) { return op == CCS_CX || op == CCS_CZ; }
+bool is_clifford_op(int op) { return op >= CCS_H && op <= CCS_CZ; }
+
+struct UF {
+  std::vector<int> p;
+  explicit UF(int n) : p(n) { std::iota(p.begin(), p.end(), 0); }
+  int find(int x) {
+    while (p[x] != x) { p[x] = p[p[x]]; x = p[x]; }
+    return x;
+  }
+  void join(int a, int b) {
+    a = find(a); b = find(b);
+    if (a != b) p[std::max(a, b)] = std::min(a, b);
+  }
+};
+
+// CHP update of one local Pauli pattern (x_a, z_a, x_b, z_b) and its sign.
+void chp_local(int op, int ra, int rb, int x[2], int z[2], int& flip) {
+  switch (op) {
+    case CCS_H: flip ^= x[ra] & z[ra]; std::swap(x[ra], z[ra]); break;
+    case CCS_S: flip ^= x[ra] & z[ra]; z[ra] ^= x[ra]; break;
+    case CCS_SDG: flip ^= x[ra] & (z[ra] ^ 1); z[ra] ^= x[ra]; break;
+    case CCS_X: flip ^= z[ra]; break;
+    case CCS_Y: flip ^= x[ra] ^ z[ra]; break;
+    case CCS_Z: flip ^= x[ra]; break;
+    case CCS_CX:
+      flip ^= x[ra] & z[rb] & (x[rb] ^ z[ra] ^ 1);
+      x[rb] ^= x[ra];
+      z[ra] ^= z[rb];
+      break;
+    case CCS_CZ:
+      flip ^= x[ra] & x[rb] & (z[ra] ^ z[rb]);
+      z[ra] ^= x[rb];
+      z[rb] ^= x[ra];
+      break;
+    default: break;
+  }
+}
+
+// (M, anf) of a gate word acting on roles 0 (= a) and 1 (= b).
+CliffordOp clifford_from_word(const std::vector<std::array<int, 3>>& word) {
+  int u[16], f[16];
+  for (int v = 0; v < 16; ++v) {
+    int x[2] = {v & 1, (v >> 2) & 1};
+    int z[2] = {(v >> 1) & 1, (v >> 3) & 1};
+    int flip = 0;
+    for (auto& g : word) chp_local(g[0], g[1], g[2], x, z, flip);
+    u[v] = x[0] | (z[0] << 1) | (x[1] << 2) | (z[1] << 3);
+    f[v] = flip;
+  }
+  CliffordOp op{0, 0, 0, 0};
+  for (int j = 0; j < 4; ++j)
+    for (int i = 0; i < 4; ++i)
+      if ((u[1 << j] >> i) & 1) op.M |= (uint16_t)(1u << (4 * i + j));
+  int a[16];
+  for (int s = 0; s < 16; ++s) a[s] = f[s];
+  for (int i = 0; i < 4; ++i)
+    for (int s = 0; s < 16; ++s)
+      if (s & (1 << i)) a[s] ^= a[s ^ (1 << i)];
+  for (int s = 0; s < 16; ++s)
+    if (a[s]) op.anf |= (uint16_t)(1u << s);
+  return op;
+}
+
+using cd = std::complex<double>;
+
+void gate_matrix_1q(int op, cd m[4]) {
+  const double r = 1.0 / std::sqrt(2.0);
+  const cd I(0, 1);
+  cd id[4] = {1, 0, 0, 1};
+  for (int i = 0; i < 4; ++i) m[i] = id[i];
+  switch (op) {
+    case CCS_H: m[0] = r; m[1] = r; m[2] = r; m[3] = -r; break;
+    case CCS_S: m[3] = I; break;
+    case CCS_SDG: m[3] = -I; break;
+    case CCS_X: m[0] = 0; m[1] = 1; m[2] = 1; m[3] = 0; break;
+    case CCS_Y: m[0] = 0; m[1] = -I; m[2] = I; m[3] = 0; break;
+    case CCS_Z: m[3] = -1; break;
+    case CCS_T: m[3] = std::polar(1.0, M_PI / 4); break;
+    case CCS_TDG: m[3] = std::polar(1.0, -M_PI / 4); break;
+    default: break;
+  }
+}
+
+// 4x4 (index = bit_a + 2 bit_b) matrix of a gate on roles (ra, rb).
+void gate_matrix_2(int op, int ra, int rb, cd m[16]) {
+  for (int i = 0; i < 16; ++i) m[i] = 0;
+  if (op == CCS_CX || op == CCS_CZ) {
+    for (int j = 0; j < 4; ++j) {
+      int bits[2] = {j & 1, (j >> 1) & 1};
+      if (op == CCS_CX) {
+        int out[2] = {bits[0], bits[1]};
+        out[rb] ^= bits[ra];
+        m[(out[0] | out[1] << 1) * 4 + j] = 1;
+      } else {
+        m[j * 4 + j] = (bits[0] & bits[1]) ? -1.0 : 1.0;
+      }
+    }
+    return;
+  }
+  cd g[4];
+  gate_matrix_1q(op, g);
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      int ia = (ra == 0) ? (i & 1) : (i >> 1), ja = (ra == 0) ? (j & 1) : (j >> 1);
+      int ib = (ra == 0) ? (i >> 1) : (i & 1), jb = (ra == 0) ? (j >> 1) : (j & 1);
+      m[i * 4 + j] = (ib == jb) ? g[ia * 2 + ja] : cd(0);
+    }
+}
+
+struct Fused {
+  int a, b;                                   // b < 0: one-qubit op
+  std::vector<std::array<int, 3>> word;       // (op, role_a, role_b)
+  bool dead = false;
+};
+
+// Fuse consecutive gates per qubit (pair) and assign ASAP moments.
+std::vector<std::vector<const Fused*>> fuse_and_layer(const Frag& f, std::vector<Fused>& ops) {
+  const int n = f.n();
+  std::vector<int> last(n, -1);
+  for (auto& g : f.gates) {
+    int op = g[0], a = g[1], b = g[2];
+    if (!is_two_qubit(op)) {
+      if (last[a] >= 0) {
+        Fused& F = ops[last[a]];
+        F.word.push_back({op, F.a == a ? 0 : 1, -1});
+      } else {
+        ops.push_back({a, -1, {{op, 0, -1}}});
+        last[a] = (int)ops.size() - 1;
+      }
+      continue;
+    }
+    int la = last[a], lb = last[b];
+    if (la >= 0 && la == lb) {
+      Fused& F = ops[la];
+      int ra = F.a == a ? 0 : 1;
+      F.word.push_back({op, ra, 1 - ra});
+      continue;
+    }
+    Fused nf{a, b, {}};
+    for (int side = 0; side < 2; ++side) {
+      int lq = side == 0 ? la : lb;
+      if (lq >= 0 && ops[lq].b < 0) {     // absorb a trailing one-qubit op
+        for (auto& w : ops[lq].word) nf.word.push_back({w[0], side, -1});
+        ops[lq].dead = true;
+        ops[lq].word.clear();
+      }
+    }
+    nf.word.push_back({op, 0, 1});
+    ops.push_back(nf);
+    last[a] = last[b] = (int)ops.size() - 1;
+  }
+  std::vector<int> layer_of_q(n, -1);
+  std::vector<std::vector<const Fused*>> layers;
+  for (auto& F : ops) {
+    if (F.dead) continue;
+    int L = layer_of_q[F.a];
+    if (F.b >= 0) L = std::max(L, layer_of_q[F.b]);
+    L += 1;
+    layer_of_q[F.a] = L;
+    if (F.b >= 0) layer_of_q[F.b] = L;
+    if ((int)layers.size() <= L) layers.resize(L + 1);
+    layers[L].push_back(&F);
+  }
+  return layers;
+}
+
+}  // namespace
+
+int fragment_problem(Problem& p, int pi, std::vector<Frag>& out, std::string& err) {
+  const int n = (int)p.n_qubits;
+  const int ng = (int)p.gates.size();
+  for (int gi = 0; gi < ng; ++gi) {
+    auto& g = p.gates[gi];
+    if (g[0] < 0 || g[0] > CCS_TDG) { err = "unknown gate opcode"; return CCS_ERR_UNSUPPORTED_GATE; }
+    if (g[1] < 0 || g[1] >= n) { err = "gate qubit out of range"; return CCS_ERR_INVALID_ARG; }
+    if (is_two_qubit(g[0]) && (g[2] < 0 || g[2] >= n || g[2] == g[1])) {
+      err = "bad two-qubit gate operands"; return CCS_ERR_INVALID_ARG;
+    }
+  }
+  for (auto& c : p.cuts)
+    if ((int)c.qubit >= n || (int)c.gate_index > ng) { err = "cut out of range"; return CCS_ERR_INVALID_ARG; }
+  std::sort(p.cuts.begin(), p.cuts.end(), [](const ccs_cut& x, const ccs_cut& y) {
+    return x.gate_index != y.gate_index ? x.gate_index < y.gate_index : x.qubit < y.qubit;
+  });
+  for (size_t i = 1; i < p.cuts.size(); ++i)
+    if (p.cuts[i].qubit == p.cuts[i - 1].qubit && p.cuts[i].gate_index == p.cuts[i - 1].gate_index) {
+      err = "duplicate cut"; return CCS_ERR_INVALID_ARG;
+    }
+  if ((int)p.cuts.size() > kMaxCuts) { err = "too many cuts"; return CCS_ERR_TOO_MANY_CUTS; }
+  if (p.marginal.size() > (size_t)kMaxMarginal) { err = "marginal too wide"; return CCS_ERR_INVALID_ARG; }
+  for (auto q : p.marginal)
+    if ((int)q >= n) { err = "marginal qubit out of range"; return CCS_ERR_INVALID_ARG; }
+  for (size_t i = 0; i < p.marginal.size(); ++i)
+    for (size_t j = 0; j < i; ++j)
+      if (p.marginal[i] == p.marginal[j]) { err = "repeated marginal qubit"; return CCS_ERR_INVALID_ARG; }
+
+  std::vector<std::vector<int>> pos(n);
+  for (auto& c : p.cuts) pos[c.qubit].push_back((int)c.gate_index);
+  std::vector<int> base(n + 1, 0);
+  for (int q = 0; q < n; ++q) base[q + 1] = base[q] + (int)pos[q].size() + 1;
+  auto seg = [&](int q, int g) {
+    return (int)(std::upper_bound(pos[q].begin(), pos[q].end(), g) - pos[q].begin());
+  };
+  UF uf(base[n]);
+  for (int gi = 0; gi < ng; ++gi) {
+    auto& g = p.gates[gi];
+    if (is_two_qubit(g[0])) uf.join(base[g[1]] + seg(g[1], gi), base[g[2]] + seg(g[2], gi));
+  }
+  // fragments ordered by first wire; wires by (qubit, segment) = segment id
+  std::map<int, int> root_to_frag;
+  std::vector<std::pair<int, int>> where(base[n]);
+  const int first = (int)out.size();
+  for (int s = 0; s < base[n]; ++s) {
+    int r = uf.find(s);
+    auto it = root_to_frag.find(r);
+    if (it == root_to_frag.end()) {
+      it = root_to_frag.emplace(r, (int)out.size()).first;
+      Frag f;
+      f.problem = pi;
+      f.index = (int)out.size() - first;
+      out.push_back(f);
+    }
+    Frag& f = out[it->second];
+    int q = (int)(std::upper_bound(base.begin(), base.end(), s) - base.begin()) - 1;
+    where[s] = {it->second, f.n()};
+    f.wires.push_back({(uint32_t)q, (uint32_t)(s - base[q])});
+  }
+  for (int gi = 0; gi < ng; ++gi) {
+    auto& g = p.gates[gi];
+    auto wa = where[base[g[1]] + seg(g[1], gi)];
+    Frag& f = out[wa.first];
+    if (is_two_qubit(g[0])) {
+      auto wb = where[base[g[2]] + seg(g[2], gi)];
+      f.gates.push_back({g[0], wa.second, wb.second});
+    } else {
+      f.gates.push_back({g[0], wa.second, -1});
+      if (!is_clifford_op(g[0])) f.clifford = false;
+    }
+  }
+  for (int ci = 0; ci < (int)p.cuts.size(); ++ci) {
+    int q = p.cuts[ci].qubit;
+    int k = (int)(std::find(pos[q].begin(), pos[q].end(), (int)p.cuts[ci].gate_index) - pos[q].begin()) + 1;
+    auto up = where[base[q] + k - 1], dn = where[base[q] + k];
+    if (up.first == dn.first) {
+      err = "a cut whose two ends lie in one fragment is not supported";
+      return CCS_ERR_UNSUPPORTED;
+    }
+    out[up.first].qout_cut.push_back(ci);
+    out[up.first].qout_wire.push_back(up.second);
+    out[dn.first].qin_cut.push_back(ci);
+    out[dn.first].qin_wire.push_back(dn.second);
+  }
+  for (int mi = 0; mi < (int)p.marginal.size(); ++mi) {
+    int q = p.marginal[mi];
+    auto w = where[base[q] + (int)pos[q].size()];
+    out[w.first].marg_pos.push_back(mi);
+    out[w.first].marg_wire.push_back(w.second);
+  }
+  for (int fi = first; fi < (int)out.size(); ++fi) {
+    Frag& f = out[fi];
+    f.zwires.assign(p.zstrings.size(), {});
+    std::vector<std::pair<int, std::pair<int, int>>> sl;
+    for (size_t j = 0; j < f.qin_cut.size(); ++j) sl.push_back({f.qin_cut[j], {0, (int)j}});
+    for (size_t j = 0; j < f.qout_cut.size(); ++j) sl.push_back({f.qout_cut[j], {1, (int)j}});
+    std::sort(sl.begin(), sl.end());
+    for (auto& e : sl) {
+      f.slots.push_back(e.first);
+      f.slot_kind.push_back(e.second.first);
+      f.slot_idx.push_back(e.second.second);
+    }
+  }
+  for (size_t si = 0; si < p.zstrings.size(); ++si)
+    for (auto q : p.zstrings[si]) {
+      if ((int)q >= n) { err = "Z-string qubit out of range"; return CCS_ERR_INVALID_ARG; }
+      auto w = where[base[q] + (int)pos[q].size()];
+      out[w.first].zwires[si].push_back(w.second);
+    }
+  p.frag_ids.clear();
+  for (int fi = first; fi < (int)out.size(); ++fi) {
+    Frag& f = out[fi];
+    if (!f.clifford && f.n() > kMaxNCWidth) { err = "non-Clifford fragment too wide"; return CCS_ERR_NC_TOO_WIDE; }
+    if (f.clifford && f.n() > kMaxTableauQubits) { err = "Clifford fragment too wide"; return CCS_ERR_UNSUPPORTED; }
+    if (f.n_meas() > kMaxMeas) { err = "fragment measures too many wires"; return CCS_ERR_UNSUPPORTED; }
+    p.frag_ids.push_back(fi);
+  }
+  // star: one fragment on every cut
+  const int nf = (int)out.size() - first;
+  p.hub = -1;
+  if (p.cuts.empty()) {
+    p.hub = 0;
+  } else {
+    for (int h = 0; h < nf && p.hub < 0; ++h)
+      if ((int)out[first + h].slots.size() == (int)p.cuts.size()) p.hub = h;
+  }
+  return CCS_OK;
+}
+
+void compile_clifford(Frag& f) {
+  std::vector<Fused> ops;
+  ops.reserve(f.gates.size());
+  auto layers = fuse_and_layer(f, ops);
+  f.cops.clear();
+  f.moment_start.assign(1, 0);
+  const uint16_t dummy = (uint16_t)f.n();
+  for (auto& L : layers) {
+    for (auto* F : L) {
+      CliffordOp op = clifford_from_word(F->word);
+      op.qa = (uint16_t)F->a;
+      op.qb = F->b >= 0 ? (uint16_t)F->b : dummy;
+      f.cops.push_back(op);
+    }
+    f.moment_start.push_back((int)f.cops.size());
+  }
+}
+
+void compile_nc(Frag& f) {
+  std::vector<Fused> ops;
+  ops.reserve(f.gates.size());
+  auto layers = fuse_and_layer(f, ops);
+  f.nops.clear();
+  f.moment_start.assign(1, 0);
+  for (auto& L : layers) {
+    for (auto* F : L) {
+      NCOp o{};
+      o.a = F->a;
+      o.b = F->b;
+      if (F->b < 0) {
+        cd U[4] = {1, 0, 0, 1};
+        for (auto& g : F->word) {
+          cd G[4], R[4];
+          gate_matrix_1q(g[0], G);
+          for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 2; ++j) R[i * 2 + j] = G[i * 2] * U[j] + G[i * 2 + 1] * U[2 + j];
+          for (int i = 0; i < 4; ++i) U[i] = R[i];
+        }
+        for (int i = 0; i < 4; ++i) { o.m[2 * i] = (float)U[i].real(); o.m[2 * i + 1] = (float)U[i].imag(); }
+      } else {
+        cd U[16], G[16], R[16];
+        for (int i = 0; i < 16; ++i) U[i] = (i % 5 == 0) ? 1.0 : 0.0;
+        for (auto& g : F->word) {
+          gate_matrix_2(g[0], g[1], g[2] < 0 ? 1 - g[1] : g[2], G);
+          for (int i = 0; i < 4; ++i)
+            for (int j = 0; j < 4; ++j) {
+              cd s = 0;
+              for (int k = 0; k < 4; ++k) s += G[i * 4 + k] * U[k * 4 + j];
+              R[i * 4 + j] = s;
+            }
+          for (int i = 0; i < 16; ++i) U[i] = R[i];
+        }
+        for (int i = 0; i < 16; ++i) { o.m[2 * i] = (float)U[i].real(); o.m[2 * i + 1] = (float)U[i].imag(); }
+      }
+      f.nops.push_back(o);
+    }
+    f.moment_start.push_back((int)f.nops.size());
+  }
+}
+
+static const std::vector<std::vector<int>> kPrepWords = {{}, {CCS_X}, {CCS_H}, {CCS_H, CCS_S}};
+static const std::vector<std::vector<int>> kBasisWords = {{CCS_H}, {CCS_SDG, CCS_H}, {}};
+
+static CliffordOp one_qubit_op(const std::vector<int>& w) {
+  std::vector<std::array<int, 3>> word;
+  for (int g : w) word.push_back({g, 0, -1});
+  return clifford_from_word(word);
+}
+
+CliffordOp prep_op(int s) { return one_qubit_op(kPrepWords[s]); }
+CliffordOp basis_op(int b) { return one_qubit_op(kBasisWords[b]); }
+
+static void one_qubit_matrix(const std::vector<int>& w, float out[8]) {
+  cd U[4] = {1, 0, 0, 1};
+  for (int g : w) {
+    cd G[4], R[4];
+    gate_matrix_1q(g, G);
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 2; ++j) R[i * 2 + j] = G[i * 2] * U[j] + G[i * 2 + 1] * U[2 + j];
+    for (int i = 0; i < 4; ++i) U[i] = R[i];
+  }
+  for (int i = 0; i < 4; ++i) { out[2 * i] = (float)U[i].real(); out[2 * i + 1] = (float)U[i].imag(); }
+}
+
+void prep_matrix(int s, float out[8]) { one_qubit_matrix(kPrepWords[s], out); }
+void basis_matrix(int b, float out[8]) { one_qubit_matrix(kBasisWords[b], out); }
+
+}  // namespace ccs

@@ -1,0 +1,149 @@
+// Non-Clifford fragments (K4): one complex64 statevector of 2^n amplitudes per
+// variant in shared memory (the paper hands these fragments to an exact
+// statevector simulator, Sec. V-B).  Gates arrive fused into 2x2 / 4x4
+// unitaries; each is applied by all threads, one amplitude pair or quad per
+// thread, with a barrier between ops.  Outputs: the exact marginal on A_f and
+// the Z-string values, both reduced in a fixed order (deterministic).
+#include "kernels.cuh"
+
+namespace ccs {
+
+namespace {
+
+__device__ __forceinline__ unsigned insert_zero(unsigned t, int pos) {
+  return ((t >> pos) << (pos + 1)) | (t & ((1u << pos) - 1u));
+}
+
+__device__ __forceinline__ float2 cmul(float re, float im, float2 a) {
+  return make_float2(re * a.x - im * a.y, re * a.y + im * a.x);
+}
+
+__device__ void apply_1q(float2* psi, int n, int a, const float* m) {
+  const unsigned half = 1u << (n - 1);
+  for (unsigned t = threadIdx.x; t < half; t += blockDim.x) {
+    const unsigned i0 = insert_zero(t, a), i1 = i0 | (1u << a);
+    const float2 a0 = psi[i0], a1 = psi[i1];
+    const float2 p = cmul(m[0], m[1], a0), q = cmul(m[2], m[3], a1);
+    const float2 r = cmul(m[4], m[5], a0), s = cmul(m[6], m[7], a1);
+    psi[i0] = make_float2(p.x + q.x, p.y + q.y);
+    psi[i1] = make_float2(r.x + s.x, r.y + s.y);
+  }
+}
+
+__device__ void apply_2q(float2* psi, int n, int a, int b, const float* m) {
+  const unsigned quarter = 1u << (n - 2);
+  const int lo = a < b ? a : b, hi = a < b ? b : a;
+  for (unsigned t = threadIdx.x; t < quarter; t += blockDim.x) {
+    const unsigned i00 = insert_zero(insert_zero(t, lo), hi);
+    unsigned idx[4] = {i00, i00 | (1u << a), i00 | (1u << b), i00 | (1u << a) | (1u << b)};
+    float2 in[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) in[k] = psi[idx[k]];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const float2 t2 = cmul(m[2 * (r * 4 + c)], m[2 * (r * 4 + c) + 1], in[c]);
+        acc.x += t2.x;
+        acc.y += t2.y;
+      }
+      psi[idx[r]] = acc;
+    }
+  }
+}
+
+__device__ __forceinline__ int digit_in(int v, int i) {
+  for (int t = 0; t < i; ++t) v /= 4;
+  return v % 4;
+}
+__device__ __forceinline__ int digit_out(int v, int qin, int i) {
+  for (int t = 0; t < qin; ++t) v /= 4;
+  for (int t = 0; t < i; ++t) v /= 3;
+  return v % 3;
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(256) statevector_kernel(DevPlan P, DevRes R) {
+  extern __shared__ float2 psi[];
+  __shared__ int s_item;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  for (;;) {
+    if (tid == 0) s_item = (int)atomicAdd(&R.work[1], 1u);
+    __syncthreads();
+    const int item = s_item;
+    __syncthreads();
+    if (item >= P.n_items_nc) break;
+    const int2 it = P.items_nc[item];
+    const FragDev& F = P.frags[it.x];
+    const int v = it.y, n = F.n;
+    const unsigned N = 1u << n;
+    for (unsigned i = tid; i < N; i += blockDim.x) psi[i] = make_float2(i == 0 ? 1.f : 0.f, 0.f);
+    __syncthreads();
+    for (int o = 0; o < F.qin; ++o) {
+      apply_1q(psi, n, P.wires[F.qin_off + o], P.prep_mats + 8 * digit_in(v, o));
+      __syncthreads();
+    }
+    const int op0 = P.moments[F.mom_off], op1 = P.moments[F.mom_off + F.n_moments];
+    for (int o = op0; o < op1; ++o) {
+      const NCOp& op = P.nops[F.ops_off + o];
+      if (op.b < 0) apply_1q(psi, n, op.a, op.m);
+      else apply_2q(psi, n, op.a, op.b, op.m);
+      __syncthreads();
+    }
+    for (int o = 0; o < F.qout; ++o) {
+      apply_1q(psi, n, P.wires[F.qout_off + o], P.basis_mats + 8 * digit_out(v, F.qin, o));
+      __syncthreads();
+    }
+    // marginal on A: each output sums its completions in index order
+    const int nA = F.nA;
+    unsigned amask = 0;
+    for (int j = 0; j < nA; ++j) amask |= 1u << P.wires[F.A_off + j];
+    float* d = R.dist + F.dist_off + ((long long)v << nA);
+    for (unsigned y = tid; y < (1u << nA); y += blockDim.x) {
+      unsigned base = 0;
+      for (int j = 0; j < nA; ++j)
+        if ((y >> j) & 1u) base |= 1u << P.wires[F.A_off + j];
+      float acc = 0.f;
+      const unsigned rest = (N - 1) & ~amask;
+      for (unsigned c = 0;; c = (c - rest) & rest) {     // subsets of `rest`, ascending
+        const float2 a = psi[base | c];
+        acc += a.x * a.x + a.y * a.y;
+        if (c == rest) break;
+      }
+      d[y] = acc;
+    }
+    // Z-string values: <Z on (string wires + selected quantum outputs)>
+    const int nzu = F.nz << F.qout;
+    for (int ev = warp; ev < nzu; ev += nwarps) {
+      const int zi = ev >> F.qout, u = ev & ((1 << F.qout) - 1);
+      unsigned zm = 0;
+      for (int q = P.zoffs[F.zw_off + zi]; q < P.zoffs[F.zw_off + zi + 1]; ++q) zm ^= 1u << P.wires[q];
+      for (int o = 0; o < F.qout; ++o)
+        if ((u >> o) & 1) zm ^= 1u << P.wires[F.qout_off + o];
+      float acc = 0.f;
+      for (unsigned x = lane; x < N; x += 32) {
+        const float2 a = psi[x];
+        const float pr = a.x * a.x + a.y * a.y;
+        acc += (__popc(x & zm) & 1) ? -pr : pr;
+      }
+      for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) R.zval[F.zval_off + ((long long)v * F.nz + zi) * (1 << F.qout) + u] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+cudaError_t launch_statevector(const DevPlan& p, const DevRes& r, int max_n, int threads, int grid,
+                               cudaStream_t s) {
+  if (p.n_items_nc == 0) return cudaSuccess;
+  const size_t smem = (size_t)8 << max_n;
+  cudaError_t err = cudaFuncSetAttribute(statevector_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+  if (err != cudaSuccess) return err;
+  statevector_kernel<<<grid, threads, smem, s>>>(p, r);
+  return cudaGetLastError();
+}
+
+}  // namespace ccs

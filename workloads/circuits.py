@@ -9,8 +9,8 @@ The partition is fixed first (a "star"): each non-Clifford region is a set of
 full qubits plus a time window of one boundary qubit, i.e. two wire cuts per
 region, the boundary qubit being cut out of the middle of the Clifford body
 (Sec. III-B, Fig. 2 caption).  Brickwork pairs that straddle a fragment
-boundary at their layer are dropped, so the intended cut set isolates every
-T gate.
+boundary are never formed: at each layer brickwork pairs are drawn within
+each fragment's qubits, so the intended cut set isolates every T gate.
 
 Uniform random two-qubit Cliffords are drawn with the double-coset form
 C2 = U (C1 x C1) g_c (C1 x C1) over the four local-equivalence classes
@@ -112,6 +112,10 @@ def _frag_of(q, layer, regions):
 def brickwork_star(n, depth, regions, seed):
     """Brickwork of random C2 elements with the star partition fixed first.
 
+    At each layer the qubits are grouped by the fragment they belong to
+    (body or a region); within each group consecutive members (in qubit
+    order) are paired, alternating the pairing parity between layers.  So a
+    region never splits the body's chain, and no gate straddles fragments.
     Returns ``(circuit, cuts)``; the cuts are the two wire cuts per region on
     its boundary qubit, at the first gate of layers t_a and t_b.
     """
@@ -134,9 +138,15 @@ def brickwork_star(n, depth, regions, seed):
         for r in regions:
             if layer in (r.t_a, r.t_b):
                 cuts.append((r.boundary, len(c.gates)))
-        for i in range(layer % 2, n - 1, 2):
-            if _frag_of(i, layer, regions) == _frag_of(i + 1, layer, regions):
-                c.gates += random_c2_word(rng, i, i + 1)
+        groups = {}
+        for q in range(n):
+            groups.setdefault(_frag_of(q, layer, regions), []).append(q)
+        pairs = []
+        for members in groups.values():
+            for j in range(layer % 2, len(members) - 1, 2):
+                pairs.append((members[j], members[j + 1]))
+        for a, b in sorted(pairs):
+            c.gates += random_c2_word(rng, a, b)
         for q in range(n):
             if (layer, q) in t_slots:
                 c.add(T, q)
