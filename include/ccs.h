@@ -144,6 +144,17 @@ int ccs_build_fragments(ccs_ctx ctx, const ccs_problem* problems, int n_problems
                         const ccs_cut_opts* opts, ccs_plan* out);
 void ccs_plan_free(ccs_plan plan);
 
+/* Candidate cut sets of one problem from the cut search (its cuts field is
+ * ignored), cheapest first by the search's work estimate: a greedy beam over
+ * regions grown from the non-Clifford gates (Sec. V-A: cuts isolate the
+ * non-Clifford operations).  Candidate i's cuts are
+ * cuts_out[offsets[i] .. offsets[i+1]) in cut order, its estimate costs[i].
+ * Returns the number of candidates written (<= cap_cands; offsets needs
+ * cap_cands + 1 entries) or an error (TOO_MANY_CUTS when no candidate fits
+ * the limits).  Works on host-only contexts. */
+int ccs_cut_candidates(ccs_ctx ctx, const ccs_problem* problem, const ccs_cut_opts* opts,
+                       ccs_cut* cuts_out, int cap_cuts, int* offsets, double* costs, int cap_cands);
+
 /* --- variant evaluation (Sec. V-B) ---------------------------------------- */
 #define CCS_EXACT 0
 #define CCS_SAMPLED 1

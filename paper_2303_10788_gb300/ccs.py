@@ -27,7 +27,7 @@ EXPORTS = ["ccs_version", "ccs_create", "ccs_destroy", "ccs_last_error", "ccs_bu
            "ccs_plan_free", "ccs_eval_variants", "ccs_res_free", "ccs_recombine", "ccs_plan_counts",
            "ccs_fragment_info_get", "ccs_plan_cuts", "ccs_fragment_wires", "ccs_get_tableau",
            "ccs_get_outcome_space", "ccs_get_counts", "ccs_get_dist", "ccs_get_tensor",
-           "ccs_set_profiling", "ccs_get_stage_times"]
+           "ccs_set_profiling", "ccs_get_stage_times", "ccs_cut_candidates"]
 STAGES = ["clifford", "sample", "statevector", "fold", "recombine"]
 
 
@@ -111,6 +111,8 @@ def lib():
             "ccs_get_dist": ([P, P, C.c_int, C.c_int, C.c_int, P], C.c_int),
             "ccs_get_tensor": ([P, P, C.c_int, C.c_int, P], C.c_int),
             "ccs_set_profiling": ([P, C.c_int], C.c_int),
+            "ccs_cut_candidates": ([P, C.POINTER(ccs_problem), C.POINTER(ccs_cut_opts), C.POINTER(ccs_cut),
+                                    C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_int], C.c_int),
             "ccs_get_stage_times": ([P, C.POINTER(C.c_double), C.c_int], C.c_int),
         }
         for name, (args, res) in sig.items():
@@ -371,3 +373,16 @@ def ccs_get_stage_times(ctx):
     buf = (C.c_double * 8)()
     n = ctx.check(lib().ccs_get_stage_times(ctx.h, buf, 8), "ccs_get_stage_times")
     return {STAGES[i]: buf[i] for i in range(n) if buf[i] >= 0}
+
+
+def ccs_cut_candidates(ctx, problem, max_cuts=12, max_nc_width=10, cap=64):
+    """[(cuts, estimated cost)] from the cut search, cheapest first."""
+    p, keep = _pack_problem(problem)
+    opts = ccs_cut_opts(max_cuts, max_nc_width, 0)
+    cuts = (ccs_cut * (cap * 16))()
+    offs = (C.c_int * (cap + 1))()
+    costs = (C.c_double * cap)()
+    n = ctx.check(lib().ccs_cut_candidates(ctx.h, C.byref(p), C.byref(opts), cuts, cap * 16, offs, costs, cap),
+                  "ccs_cut_candidates")
+    return [([(cuts[j].qubit, cuts[j].gate_index) for j in range(offs[i], offs[i + 1])], costs[i])
+            for i in range(n)]

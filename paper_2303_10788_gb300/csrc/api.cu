@@ -408,6 +408,37 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
 
 void ccs_plan_free(ccs_plan p) { delete p; }
 
+int ccs_cut_candidates(ccs_ctx c, const ccs_problem* q, const ccs_cut_opts* opts, ccs_cut* cuts_out,
+                       int cap_cuts, int* offsets, double* costs, int cap_cands) {
+  if (!c || !q || !cuts_out || !offsets || cap_cands < 1) return fail(c, CCS_ERR_INVALID_ARG, "bad arguments");
+  ccs_cut_opts o{kMaxCuts, 10, 0};
+  if (opts) o = *opts;
+  Problem P;
+  P.n_qubits = q->n_qubits;
+  for (uint32_t g = 0; g < q->n_gates; ++g) {
+    const ccs_gate& G = q->gates[g];
+    if (G.op > CCS_TDG) return fail(c, CCS_ERR_UNSUPPORTED_GATE, "unknown gate opcode");
+    P.gates.push_back({(int)G.op, (int)G.q[0], (G.op == CCS_CX || G.op == CCS_CZ) ? (int)G.q[1] : -1});
+  }
+  P.marginal.assign(q->marginal, q->marginal + q->n_marginal);
+  CutSearchOpts so;
+  so.max_cuts = std::min(o.max_cuts, kMaxCuts);
+  so.max_nc_width = std::min(o.max_nc_width > 0 ? o.max_nc_width : 10, kMaxNCWidth);
+  std::vector<CutCandidate> cands;
+  std::string err;
+  int rc = greedy_cuts(P, so, cands, err);
+  if (rc != CCS_OK) return fail(c, rc, err);
+  int n = 0, used = 0;
+  offsets[0] = 0;
+  for (auto& cd : cands) {
+    if (n >= cap_cands || used + (int)cd.cuts.size() > cap_cuts) break;
+    for (auto& x : cd.cuts) cuts_out[used++] = x;
+    if (costs) costs[n] = cd.cost;
+    offsets[++n] = used;
+  }
+  return n;
+}
+
 static int enqueue_eval(ccs_ctx c, ccs_plan p, ccs_res r) {
   cudaStream_t s = c->stream;
   const EvalParams& e = r->ep;

@@ -8,10 +8,12 @@
 //     it is closed: a two-qubit gate inside one window is inside its partner's
 //     window too;
 //   * each window costs a cut before it (a > 0) and after it (b < len);
+//     windows absorb runs of one-qubit gates at their edges;
 //   * every non-Clifford gate seeds a one-gate window; overlapping regions
 //     are merged;
 //   * moves: widen a window by one gate, widen it to the start or end of its
-//     wire or to the whole wire, or merge two regions (each followed by
+//     wire or to the whole wire, saturate a region (make its windows whole
+//     wires while the closure fits the width cap), or merge two regions (each followed by
 //     closure); a beam of the cheapest states by estimated cost is expanded
 //     (uphill moves allowed) until the best valid candidate stops improving;
 //   * cost = sum over fragments of variants x per-variant work + 4^k 2^|o|
@@ -20,6 +22,8 @@
 // cut) within the cut budget is kept as a candidate, cheapest first.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <map>
 #include <set>
 
@@ -50,11 +54,18 @@ Window* find_w(Region& r, int q) {
   return nullptr;
 }
 
-// Close a region under two-qubit gates.
+// Close a region under two-qubit gates.  Windows also absorb the runs of
+// one-qubit gates at their edges: that pulls in no new qubit and lets a
+// window reach the end of its wire, which removes a cut.
 void close_region(const Ctx& C, Region& r) {
   bool changed = true;
   while (changed) {
     changed = false;
+    for (auto& w : r) {
+      const auto& ops = C.ops_on[w.q];
+      while (w.a > 0 && !two_qubit(C.P->gates[ops[w.a - 1]][0])) --w.a;
+      while (w.b < (int)ops.size() && !two_qubit(C.P->gates[ops[w.b]][0])) ++w.b;
+    }
     for (size_t i = 0; i < r.size(); ++i) {
       const Window w = r[i];
       for (int pos = w.a; pos < w.b; ++pos) {
@@ -113,6 +124,29 @@ void normalise(const Ctx& C, std::vector<Region>& rs) {
   std::sort(rs.begin(), rs.end(), [](const Region& x, const Region& y) {
     return std::make_pair(x[0].q, x[0].a) < std::make_pair(y[0].q, y[0].a);
   });
+}
+
+// Make windows whole wires one at a time, keeping each change whose closure
+// still fits the width cap, until nothing changes.
+Region saturate(const Ctx& C, Region r, int max_width) {
+  bool changed = true;
+  while (changed) {
+    changed = false;
+    for (size_t i = 0; i < r.size(); ++i) {
+      const int len = (int)C.ops_on[r[i].q].size();
+      if (r[i].a == 0 && r[i].b == len) continue;
+      Region t = r;
+      t[i].a = 0;
+      t[i].b = len;
+      close_region(C, t);
+      if ((int)t.size() <= max_width) {
+        r = t;
+        changed = true;
+        break;
+      }
+    }
+  }
+  return r;
 }
 
 std::vector<ccs_cut> cuts_of(const Ctx& C, const std::vector<Region>& rs) {
@@ -286,6 +320,11 @@ int greedy_cuts(const Problem& p, const CutSearchOpts& o, std::vector<CutCandida
           }
           if (w.a > 0 && w.b < len) { auto s3 = st; s3[ri][wi].a = 0; s3[ri][wi].b = len; consider(s3); }
         }
+        {
+          auto s5 = st;
+          s5[ri] = saturate(C, s5[ri], o.max_nc_width);
+          consider(s5);
+        }
         for (size_t rj = ri + 1; rj < st.size(); ++rj) {
           auto s4 = st;
           s4[ri] = merge(s4[ri], s4[rj]);
@@ -296,6 +335,13 @@ int greedy_cuts(const Problem& p, const CutSearchOpts& o, std::vector<CutCandida
     }
     if (next.empty()) break;
     std::stable_sort(next.begin(), next.end(), [](const Item& x, const Item& y) { return x.cost < y.cost; });
+    if (std::getenv("CCS_DEBUG_CUTTER")) {
+      const auto& b = next.front();
+      std::fprintf(stderr, "iter %d: %zu states, best est %.3g, regions %zu, cuts %zu, widths:", iter, next.size(),
+                   b.cost, b.s.size(), cuts_of(C, b.s).size());
+      for (auto& r : b.s) std::fprintf(stderr, " %zu", r.size());
+      std::fprintf(stderr, "\n");
+    }
     if ((int)next.size() > beam) next.resize(beam);
     for (auto& it : next) record(it.s);
     double bv = INFINITY;
