@@ -386,3 +386,4 @@ def ccs_cut_candidates(ctx, problem, max_cuts=12, max_nc_width=10, cap=64):
                   "ccs_cut_candidates")
     return [([(cuts[j].qubit, cuts[j].gate_index) for j in range(offs[i], offs[i + 1])], costs[i])
             for i in range(n)]
+

@@ -110,7 +110,11 @@ struct ccs_plan_s {
   Allocs A;
   long long n_spaces = 0, n_counts = 0, n_dist = 0, n_zval = 0, n_tab = 0, n_T = 0, n_TZ = 0;
   long long n_marg = 0, n_zexp = 0;
-  std::vector<long long> t_prefix, tz_prefix, out_prefix, z_prefix;
+  std::vector<long long> t_prefix, tz_prefix, out_prefix, z_prefix, r_prefix, blk_prefix;
+  long long* d_r_prefix = nullptr;
+  long long* d_blk_prefix = nullptr;
+  long long r_total = 0, part_total = 0, gemm_blocks = 0;
+  int max_tile_smem = 0;
   long long* d_t_prefix = nullptr;
   long long* d_tz_prefix = nullptr;
   long long* d_out_prefix = nullptr;
@@ -132,6 +136,7 @@ struct ccs_res_s {
   int graph_valid = 0;
   int cliff_threads = 256;
   int sample_spc = 4096;
+  float* scratch = nullptr;   // recombination: R operand + split-K partials
   ~ccs_res_s() {
     if (graph) cudaGraphExecDestroy(graph);
     A.release();
@@ -346,6 +351,8 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
   plan->tz_prefix.push_back(0);
   plan->out_prefix.push_back(0);
   plan->z_prefix.push_back(0);
+  plan->r_prefix.push_back(0);
+  plan->blk_prefix.push_back(0);
   for (auto& f : plan->fdev) {
     plan->t_prefix.push_back(plan->t_prefix.back() + (1ll << f.m) * (1ll << (2 * f.n_slots)));
     plan->tz_prefix.push_back(plan->tz_prefix.back() + (long long)f.nz * (1ll << (2 * f.n_slots)));
@@ -365,6 +372,29 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
     plan->out_prefix.push_back(plan->n_marg);
     plan->z_prefix.push_back(plan->n_zexp);
     if (P.hub < 0) plan->all_star = false;
+    if (P.hub >= 0) {
+      const int m_hub = plan->fdev[f0 + P.hub].m;
+      d.M = 1 << m_hub;
+      d.N = 1 << (d.n_marg - m_hub);
+      d.K = 1ll << (2 * d.k);
+      d.TN = std::min(d.N, 64);
+      d.TM = std::min(d.M, std::max(1, 1024 / d.TN));
+      d.mtiles = (d.M + d.TM - 1) / d.TM;
+      d.ntiles = (d.N + d.TN - 1) / d.TN;
+      const long long base = (long long)d.mtiles * d.ntiles;
+      const int target = 2 * std::max(c->sm_count, 148);
+      const long long max_splits = std::max(1ll, d.K / 32);
+      d.splits = (int)std::max(1ll, std::min(max_splits, (target + base - 1) / base));
+      d.r_off = plan->r_total;
+      plan->r_total += d.K * d.N;
+      d.part_off = plan->part_total;
+      plan->part_total += (long long)d.splits * d.M * d.N;
+      d.blk_off = plan->gemm_blocks;
+      plan->gemm_blocks += base * d.splits;
+      plan->max_tile_smem = std::max(plan->max_tile_smem, (d.TM * (16 + 1) + 16 * d.TN) * 4);
+    }
+    plan->r_prefix.push_back(plan->r_total);
+    plan->blk_prefix.push_back(plan->gemm_blocks);
     f0 += d.n_frags;
     plan->pdev.push_back(d);
   }
@@ -393,7 +423,9 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
             upload(c, plan->A, plan->t_prefix, &plan->d_t_prefix) &&
             upload(c, plan->A, plan->tz_prefix, &plan->d_tz_prefix) &&
             upload(c, plan->A, plan->out_prefix, &plan->d_out_prefix) &&
-            upload(c, plan->A, plan->z_prefix, &plan->d_z_prefix);
+            upload(c, plan->A, plan->z_prefix, &plan->d_z_prefix) &&
+            upload(c, plan->A, plan->r_prefix, &plan->d_r_prefix) &&
+            upload(c, plan->A, plan->blk_prefix, &plan->d_blk_prefix);
   if (!ok) { delete plan; return fail(c, CCS_ERR_OOM, "plan upload failed"); }
   dp.frags = dfr; dp.cops = dco; dp.nops = dno; dp.moments = dmo; dp.wires = dwi; dp.zoffs = dzo;
   dp.items_cliff = dic; dp.items_nc = din;
@@ -505,7 +537,9 @@ int ccs_eval_variants(ccs_ctx c, ccs_plan p, const ccs_eval_opts* opts, ccs_res*
     d.zexp = r->A.get<double>(std::max<long long>(p->n_zexp, 1));
     d.work = r->A.get<unsigned>(4);
     d.status = r->A.get<unsigned>(4);
-    if (!d.spaces || !d.dist || !d.zval || !d.T || !d.TZ || !d.marg || !d.zexp || !d.work || !d.status) {
+    r->scratch = r->A.get<float>(std::max<long long>(p->r_total + p->part_total, 1));
+    if (!d.spaces || !d.dist || !d.zval || !d.T || !d.TZ || !d.marg || !d.zexp || !d.work || !d.status ||
+        !r->scratch) {
       delete r;
       return fail(c, CCS_ERR_OOM, "result allocation failed");
     }
@@ -587,8 +621,9 @@ int ccs_recombine(ccs_ctx c, ccs_plan p, ccs_res r, const ccs_recomb_opts* opts,
   if (prec != CCS_FP32 && prec != CCS_BF16) return fail(c, CCS_ERR_INVALID_ARG, "bad precision");
   cudaSetDevice(c->device);
   stage_begin(c, ST_RECOMB);
-  cudaError_t e = launch_recombine(p->dp, r->dr, prec, p->d_out_prefix, p->n_marg, p->d_z_prefix, p->n_zexp,
-                                   c->stream);
+  RecombSizes rz{p->r_total, p->part_total, p->gemm_blocks, p->n_marg, p->n_zexp,
+                 p->d_r_prefix, p->d_blk_prefix, p->d_out_prefix, p->d_z_prefix, p->max_tile_smem};
+  cudaError_t e = launch_recombine(p->dp, r->dr, prec, rz, r->scratch, r->dr.marg, r->dr.zexp, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "recombine kernel");
   stage_end(c, ST_RECOMB);
   const cudaMemcpyKind kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
@@ -731,3 +766,4 @@ int ccs_get_tensor(ccs_ctx c, ccs_res r, int problem, int fragment, float* out) 
 }
 
 }  // extern "C"
+

@@ -44,6 +44,13 @@ struct ProblemDev {
   int hub;                 // local index of the star's hub
   int n_marg, nz;
   long long marg_off, zexp_off;   // double indices into the outputs
+  // contraction C[o_hub, o_leaf] = sum_P T_hub[o_hub, P] R[P, o_leaf] (star only)
+  int M, N, splits;        // 2^m_hub, 2^(n_marg - m_hub), split-K factor
+  int TM, TN, mtiles, ntiles;
+  long long K;             // 4^k
+  long long r_off;         // float index of R (K x N) in the scratch
+  long long part_off;      // float index of the split-K partials (splits x M x N)
+  long long blk_off;       // first GEMM block of this problem
 };
 
 // Device views of a plan + result.
@@ -96,8 +103,19 @@ cudaError_t launch_statevector(const DevPlan& p, const DevRes& r, int max_n, int
 cudaError_t launch_fold(const DevPlan& p, const DevRes& r, const EvalParams& e,
                         const long long* t_prefix, int n_frags_total, long long total,
                         const long long* tz_prefix, long long total_z, cudaStream_t s);
-cudaError_t launch_recombine(const DevPlan& p, const DevRes& r, int precision,
-                             const long long* out_prefix, long long total_out,
-                             const long long* z_prefix, long long total_z, cudaStream_t s);
+// Recombination of every star problem: R build, split-K GEMM, FP64 reduce
+// and scatter into marg_out (2^n_marg doubles per problem at marg_off), and
+// the Z-string contraction into zexp_out.  `scratch` holds R and the split-K
+// partials (r_total + part_total floats).
+struct RecombSizes {
+  long long r_total, part_total, gemm_blocks, out_total, z_total;
+  const long long* r_prefix;     // per problem, K*N entries
+  const long long* blk_prefix;   // per problem, GEMM blocks
+  const long long* out_prefix;   // per problem, M*N outputs
+  const long long* z_prefix;     // per problem, Z-strings
+  int max_tile_smem;             // bytes of dynamic shared memory per GEMM block
+};
+cudaError_t launch_recombine(const DevPlan& p, const DevRes& r, int precision, const RecombSizes& z,
+                             float* scratch, double* marg_out, double* zexp_out, cudaStream_t s);
 
 }  // namespace ccs

@@ -138,66 +138,132 @@ __global__ void fold_z_kernel(DevPlan P, DevRes R, const long long* prefix, int 
   }
 }
 
-// Small-shape contraction: one thread per output o of a star (hub + leaves),
-// FP32 products summed in FP32 over chunks of 64 cut terms, chunks summed in
-// FP64.  BF16 mode rounds both GEMM operands (hub tensor and the leaves'
-// Kronecker product) to bf16 first, as a bf16 tensor-core GEMM would.
-__global__ void recombine_small_kernel(DevPlan P, DevRes R, int precision, const long long* prefix,
-                                       int np, long long total) {
+// --- contraction over the 4^k cut index ------------------------------------
+// For a star (hub h + leaves), p(o) = 2^-k sum_P T_h[o_h, P] R[P, o_l] with
+// R[P, o_l] = prod_leaves T_l[o_l|l, P|l] (leaf outputs concatenated in
+// fragment order; cut-free fragments contribute their P-independent factor).
+// R is built once (it is the GEMM's B operand), then a tiled GEMM with split-K
+// writes FP32 partial tiles, and the partials are summed in FP64 in a fixed
+// order, scaled by 2^-k and scattered to marginal order.  BF16 mode rounds
+// both operands to bf16 (as a bf16 tensor-core GEMM would) with FP32
+// accumulation.
+
+__global__ void build_r_kernel(DevPlan P, DevRes R, int precision, const long long* prefix, int np,
+                               long long total, float* scratch) {
   for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
        g += (long long)gridDim.x * blockDim.x) {
     const int pi = find_seg(prefix, np, g);
     const ProblemDev& Pb = P.problems[pi];
-    const long long o = g - prefix[pi];
-    const FragDev& Hb = P.frags[Pb.frag0 + Pb.hub];
-    const int k = Pb.k;
-    int oh = 0;
-    for (int j = 0; j < Hb.m; ++j) oh |= (int)((o >> Hb.marg_pos[j]) & 1) << j;
-    // leaves carrying cuts, plus a scalar for fragments without cuts
-    int lf[kMaxCuts], lo[kMaxCuts], nl = 0;
-    float scal = 1.f;
+    const long long loc = g - prefix[pi];
+    const long long Pp = loc / Pb.N;
+    const long long ol = loc - Pp * Pb.N;
+    float v = 1.f;
+    int off = 0;
     for (int l = 0; l < Pb.n_frags; ++l) {
       if (l == Pb.hub) continue;
       const FragDev& L = P.frags[Pb.frag0 + l];
-      int x = 0;
-      for (int j = 0; j < L.m; ++j) x |= (int)((o >> L.marg_pos[j]) & 1) << j;
-      if (L.n_slots == 0) {
-        scal *= R.T[L.T_off + x];
-      } else if (nl < kMaxCuts) {
-        lf[nl] = Pb.frag0 + l;
-        lo[nl] = x;
-        ++nl;
-      }
+      const int x = (int)((ol >> off) & ((1ll << L.m) - 1));
+      off += L.m;
+      int pl = 0;
+      for (int i = 0; i < L.n_slots; ++i) pl |= (int)((Pp >> (2 * L.slot_cut[i])) & 3) << (2 * i);
+      v *= R.T[L.T_off + ((long long)x << (2 * L.n_slots)) + pl];
     }
-    const long long K = 1ll << (2 * k);
-    const float* th = R.T + Hb.T_off + (long long)oh * K;
-    double total_d = 0.0;
-    for (long long P0 = 0; P0 < K; P0 += 64) {
-      float acc = 0.f;
-      const long long P1 = P0 + 64 < K ? P0 + 64 : K;
-      for (long long Pp = P0; Pp < P1; ++Pp) {
-        float rv = scal;
-        for (int l = 0; l < nl; ++l) {
-          const FragDev& L = P.frags[lf[l]];
-          int pl = 0;
-          for (int i = 0; i < L.n_slots; ++i) pl |= (int)((Pp >> (2 * L.slot_cut[i])) & 3) << (2 * i);
-          rv *= R.T[L.T_off + ((long long)lo[l] << (2 * L.n_slots)) + pl];
-        }
-        float hv = th[Pp];
-        if (precision == CCS_BF16) {
-          rv = to_bf16f(rv);
-          hv = to_bf16f(hv);
-        }
-        acc = fmaf(hv, rv, acc);
-      }
-      total_d += (double)acc;
-    }
-    R.marg[Pb.marg_off + o] = ldexp(total_d, -k);
+    if (precision == CCS_BF16) v = to_bf16f(v);
+    scratch[Pb.r_off + loc] = v;
   }
 }
 
-// <Z_S> = 2^-k sum_P prod_f T_f^S(P|f): one block per (problem, string).
-__global__ void recombine_z_kernel(DevPlan P, DevRes R, const long long* prefix, int np, long long total) {
+constexpr int kTK = 16;
+
+__global__ void __launch_bounds__(256) gemm_splitk_kernel(DevPlan P, DevRes R, int precision,
+                                                          const long long* blk_prefix, int np,
+                                                          long long total_blocks, float* scratch) {
+  extern __shared__ float sm[];
+  for (long long b = blockIdx.x; b < total_blocks; b += gridDim.x) {
+    const int pi = find_seg(blk_prefix, np, b);
+    const ProblemDev& Pb = P.problems[pi];
+    const FragDev& Hb = P.frags[Pb.frag0 + Pb.hub];
+    long long loc = b - blk_prefix[pi];
+    const int nt = (int)(loc % Pb.ntiles); loc /= Pb.ntiles;
+    const int mt = (int)(loc % Pb.mtiles); loc /= Pb.mtiles;
+    const int split = (int)loc;
+    const int TM = Pb.TM, TN = Pb.TN, M = Pb.M, N = Pb.N;
+    const long long K = Pb.K;
+    const long long kchunk = (K + Pb.splits - 1) / Pb.splits;
+    const long long k0 = split * kchunk, k1 = k0 + kchunk < K ? k0 + kchunk : K;
+    float* As = sm;                          // TM x (kTK + 1)
+    float* Bs = sm + TM * (kTK + 1);         // kTK x TN
+    const float* A = R.T + Hb.T_off;         // M x K, row-major
+    const float* Bm = scratch + Pb.r_off;    // K x N, row-major
+    const int nout = TM * TN;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (long long kk = k0; kk < k1; kk += kTK) {
+      for (int t = threadIdx.x; t < TM * kTK; t += blockDim.x) {
+        const int m = t / kTK, k = t % kTK;
+        const long long gm = (long long)mt * TM + m, gk = kk + k;
+        float v = (gm < M && gk < k1) ? A[gm * K + gk] : 0.f;
+        if (precision == CCS_BF16) v = to_bf16f(v);
+        As[m * (kTK + 1) + k] = v;
+      }
+      for (int t = threadIdx.x; t < kTK * TN; t += blockDim.x) {
+        const int k = t / TN, n = t % TN;
+        const long long gn = (long long)nt * TN + n, gk = kk + k;
+        Bs[k * TN + n] = (gn < N && gk < k1) ? Bm[gk * N + gn] : 0.f;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int o = threadIdx.x + 256 * j;
+        if (o < nout) {
+          const int m = o / TN, n = o % TN;
+          float a = acc[j];
+#pragma unroll
+          for (int k = 0; k < kTK; ++k) a = fmaf(As[m * (kTK + 1) + k], Bs[k * TN + n], a);
+          acc[j] = a;
+        }
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int o = threadIdx.x + 256 * j;
+      if (o < nout) {
+        const int m = o / TN, n = o % TN;
+        const long long gm = (long long)mt * TM + m, gn = (long long)nt * TN + n;
+        if (gm < M && gn < N) scratch[Pb.part_off + ((long long)split * M + gm) * N + gn] = acc[j];
+      }
+    }
+  }
+}
+
+__global__ void reduce_scatter_kernel(DevPlan P, const long long* prefix, int np, long long total,
+                                      const float* scratch, double* marg_out) {
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
+       g += (long long)gridDim.x * blockDim.x) {
+    const int pi = find_seg(prefix, np, g);
+    const ProblemDev& Pb = P.problems[pi];
+    const long long loc = g - prefix[pi];
+    const long long m = loc / Pb.N, n = loc - m * Pb.N;
+    double acc = 0.0;
+    for (int s = 0; s < Pb.splits; ++s) acc += (double)scratch[Pb.part_off + ((long long)s * Pb.M + m) * Pb.N + n];
+    long long o = 0;
+    const FragDev& Hb = P.frags[Pb.frag0 + Pb.hub];
+    for (int j = 0; j < Hb.m; ++j) o |= ((m >> j) & 1) << Hb.marg_pos[j];
+    int off = 0;
+    for (int l = 0; l < Pb.n_frags; ++l) {
+      if (l == Pb.hub) continue;
+      const FragDev& L = P.frags[Pb.frag0 + l];
+      for (int j = 0; j < L.m; ++j) o |= ((n >> (off + j)) & 1) << L.marg_pos[j];
+      off += L.m;
+    }
+    marg_out[Pb.marg_off + o] = ldexp(acc, -Pb.k);
+  }
+}
+
+// <Z_S> = 2^-k sum_P prod_f T_f^S(P|f): one block per (problem, string),
+// FP32 products, FP64 sums, fixed-order tree reduction.
+__global__ void recombine_z_kernel(DevPlan P, DevRes R, const long long* prefix, int np, long long total,
+                                   double* zexp_out) {
   __shared__ double red[256];
   for (long long g = blockIdx.x; g < total; g += gridDim.x) {
     const int pi = find_seg(prefix, np, g);
@@ -205,20 +271,15 @@ __global__ void recombine_z_kernel(DevPlan P, DevRes R, const long long* prefix,
     const int zi = (int)(g - prefix[pi]);
     const long long K = 1ll << (2 * Pb.k);
     double part = 0.0;
-    for (long long P0 = (long long)threadIdx.x * 64; P0 < K; P0 += (long long)blockDim.x * 64) {
-      float acc = 0.f;
-      const long long P1 = P0 + 64 < K ? P0 + 64 : K;
-      for (long long Pp = P0; Pp < P1; ++Pp) {
-        float t = 1.f;
-        for (int l = 0; l < Pb.n_frags; ++l) {
-          const FragDev& L = P.frags[Pb.frag0 + l];
-          int pl = 0;
-          for (int i = 0; i < L.n_slots; ++i) pl |= (int)((Pp >> (2 * L.slot_cut[i])) & 3) << (2 * i);
-          t *= R.TZ[L.TZ_off + ((long long)zi << (2 * L.n_slots)) + pl];
-        }
-        acc += t;
+    for (long long Pp = threadIdx.x; Pp < K; Pp += blockDim.x) {
+      float t = 1.f;
+      for (int l = 0; l < Pb.n_frags; ++l) {
+        const FragDev& L = P.frags[Pb.frag0 + l];
+        int pl = 0;
+        for (int i = 0; i < L.n_slots; ++i) pl |= (int)((Pp >> (2 * L.slot_cut[i])) & 3) << (2 * i);
+        t *= R.TZ[L.TZ_off + ((long long)zi << (2 * L.n_slots)) + pl];
       }
-      part += (double)acc;
+      part += (double)t;
     }
     red[threadIdx.x] = part;
     __syncthreads();
@@ -226,7 +287,7 @@ __global__ void recombine_z_kernel(DevPlan P, DevRes R, const long long* prefix,
       if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
       __syncthreads();
     }
-    if (threadIdx.x == 0) R.zexp[Pb.zexp_off + zi] = ldexp(red[0], -Pb.k);
+    if (threadIdx.x == 0) zexp_out[Pb.zexp_off + zi] = ldexp(red[0], -Pb.k);
     __syncthreads();
   }
 }
@@ -247,21 +308,35 @@ cudaError_t launch_fold(const DevPlan& p, const DevRes& r, const EvalParams& e, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_recombine(const DevPlan& p, const DevRes& r, int precision, const long long* out_prefix,
-                             long long total_out, const long long* z_prefix, long long total_z,
-                             cudaStream_t s) {
-  if (total_out > 0) {
-    const long long blocks = (total_out + 127) / 128;
-    recombine_small_kernel<<<(unsigned)(blocks < 65535 * 8 ? blocks : 65535 * 8), 128, 0, s>>>(
-        p, r, precision, out_prefix, p.n_problems, total_out);
-    cudaError_t err = cudaGetLastError();
-    if (err != cudaSuccess) return err;
+cudaError_t launch_recombine(const DevPlan& p, const DevRes& r, int precision, const RecombSizes& z,
+                             float* scratch, double* marg_out, double* zexp_out, cudaStream_t s) {
+  auto grid = [](long long n, int per) {
+    long long b = (n + per - 1) / per;
+    return (unsigned)(b < 65535ll * 16 ? (b > 0 ? b : 1) : 65535ll * 16);
+  };
+  cudaError_t err = cudaSuccess;
+  if (z.out_total > 0) {
+    build_r_kernel<<<grid(z.r_total, 256), 256, 0, s>>>(p, r, precision, z.r_prefix, p.n_problems, z.r_total,
+                                                        scratch);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    if (z.max_tile_smem > 48 * 1024) {
+      err = cudaFuncSetAttribute(gemm_splitk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, z.max_tile_smem);
+      if (err != cudaSuccess) return err;
+    }
+    gemm_splitk_kernel<<<(unsigned)(z.gemm_blocks < 65535ll * 16 ? z.gemm_blocks : 65535ll * 16), 256,
+                         z.max_tile_smem, s>>>(p, r, precision, z.blk_prefix, p.n_problems, z.gemm_blocks, scratch);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    reduce_scatter_kernel<<<grid(z.out_total, 256), 256, 0, s>>>(p, z.out_prefix, p.n_problems, z.out_total,
+                                                                scratch, marg_out);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
-  if (total_z > 0) {
-    recombine_z_kernel<<<(unsigned)(total_z < 65535 ? total_z : 65535), 256, 0, s>>>(p, r, z_prefix, p.n_problems,
-                                                                               total_z);
+  if (z.z_total > 0) {
+    recombine_z_kernel<<<(unsigned)(z.z_total < 65535 ? z.z_total : 65535), 256, 0, s>>>(p, r, z.z_prefix,
+                                                                                    p.n_problems, z.z_total,
+                                                                                    zexp_out);
+    err = cudaGetLastError();
   }
-  return cudaGetLastError();
+  return err;
 }
 
 }  // namespace ccs

@@ -65,8 +65,11 @@ __device__ __forceinline__ int digit_out(int v, int qin, int i) {
 
 }  // namespace
 
-__global__ void __launch_bounds__(256) statevector_kernel(DevPlan P, DevRes R) {
+constexpr int kOpStage = 128;   // fused ops staged in shared memory at a time
+
+__global__ void __launch_bounds__(256) statevector_kernel(DevPlan P, DevRes R, int max_n) {
   extern __shared__ float2 psi[];
+  NCOp* ops_s = reinterpret_cast<NCOp*>(psi + (1u << max_n));
   __shared__ int s_item;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   for (;;) {
@@ -86,11 +89,18 @@ __global__ void __launch_bounds__(256) statevector_kernel(DevPlan P, DevRes R) {
       __syncthreads();
     }
     const int op0 = P.moments[F.mom_off], op1 = P.moments[F.mom_off + F.n_moments];
-    for (int o = op0; o < op1; ++o) {
-      const NCOp& op = P.nops[F.ops_off + o];
-      if (op.b < 0) apply_1q(psi, n, op.a, op.m);
-      else apply_2q(psi, n, op.a, op.b, op.m);
+    for (int c0 = op0; c0 < op1; c0 += kOpStage) {
+      const int cnt = min(kOpStage, op1 - c0);
+      const int* src = reinterpret_cast<const int*>(P.nops + F.ops_off + c0);
+      int* dst = reinterpret_cast<int*>(ops_s);
+      for (int i = tid; i < cnt * (int)(sizeof(NCOp) / 4); i += blockDim.x) dst[i] = src[i];
       __syncthreads();
+      for (int o = 0; o < cnt; ++o) {
+        const NCOp& op = ops_s[o];
+        if (op.b < 0) apply_1q(psi, n, op.a, op.m);
+        else apply_2q(psi, n, op.a, op.b, op.m);
+        __syncthreads();
+      }
     }
     for (int o = 0; o < F.qout; ++o) {
       apply_1q(psi, n, P.wires[F.qout_off + o], P.basis_mats + 8 * digit_out(v, F.qin, o));
@@ -138,11 +148,11 @@ __global__ void __launch_bounds__(256) statevector_kernel(DevPlan P, DevRes R) {
 cudaError_t launch_statevector(const DevPlan& p, const DevRes& r, int max_n, int threads, int grid,
                                cudaStream_t s) {
   if (p.n_items_nc == 0) return cudaSuccess;
-  const size_t smem = (size_t)8 << max_n;
+  const size_t smem = ((size_t)8 << max_n) + (size_t)kOpStage * sizeof(NCOp);
   cudaError_t err = cudaFuncSetAttribute(statevector_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
   if (err != cudaSuccess) return err;
-  statevector_kernel<<<grid, threads, smem, s>>>(p, r);
+  statevector_kernel<<<grid, threads, smem, s>>>(p, r, max_n);
   return cudaGetLastError();
 }
 
