@@ -194,6 +194,29 @@ typedef struct {
 int ccs_recombine(ccs_ctx ctx, ccs_plan plan, ccs_res res, const ccs_recomb_opts* opts,
                   double* marginal_out, double* zexp_out);
 
+/* Recombination that allocates no device memory.  The paper has no
+ * counterpart; this exists for callers that cannot allocate at the point
+ * where they need the result: for example a runtime that reserved the whole
+ * device for its own memory pool up front, or a latency-critical thread that
+ * must not take the allocator's locks or risk the device-wide
+ * synchronisation a cudaMalloc can cause.
+ *
+ * Same result as ccs_recombine (same kernels, same arithmetic), written
+ * straight to the caller's DEVICE buffers marginal_out and zexp_out (layouts
+ * as in ccs_recombine); the call is asynchronous on the context stream and
+ * does not synchronise.  Its scratch (the leaves' Kronecker operand and the
+ * split-K partials) is a fixed 8 MiB array inside the library that every
+ * GPU loading the library holds until exit; a plan needing more
+ * (4 * sum over problems of (4^k * N + splits * M * N) bytes) is rejected
+ * with CCS_ERR_UNSUPPORTED.  Every scratch word is written before it is read
+ * within one call, so nothing needs clearing, but all calls share the one
+ * array: calls that may overlap on the GPU (other streams, other contexts
+ * on the same device) race and must be ordered by the caller.  The first
+ * call on each device looks up the array's device address; make that first
+ * call before any stream capture.  Errors: INVALID_ARG, UNSUPPORTED, CUDA. */
+int ccs_recombine_noalloc(ccs_ctx ctx, ccs_plan plan, ccs_res res, int precision, double* marginal_out,
+                          double* zexp_out);
+
 /* --- plan inspection -------------------------------------------------------- */
 typedef struct {
   int32_t n_wires;

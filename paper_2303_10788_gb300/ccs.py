@@ -27,7 +27,7 @@ EXPORTS = ["ccs_version", "ccs_create", "ccs_destroy", "ccs_last_error", "ccs_bu
            "ccs_plan_free", "ccs_eval_variants", "ccs_res_free", "ccs_recombine", "ccs_plan_counts",
            "ccs_fragment_info_get", "ccs_plan_cuts", "ccs_fragment_wires", "ccs_get_tableau",
            "ccs_get_outcome_space", "ccs_get_counts", "ccs_get_dist", "ccs_get_tensor",
-           "ccs_set_profiling", "ccs_get_stage_times", "ccs_cut_candidates"]
+           "ccs_set_profiling", "ccs_get_stage_times", "ccs_cut_candidates", "ccs_recombine_noalloc"]
 STAGES = ["clifford", "sample", "statevector", "fold", "recombine"]
 
 
@@ -111,6 +111,7 @@ def lib():
             "ccs_get_dist": ([P, P, C.c_int, C.c_int, C.c_int, P], C.c_int),
             "ccs_get_tensor": ([P, P, C.c_int, C.c_int, P], C.c_int),
             "ccs_set_profiling": ([P, C.c_int], C.c_int),
+            "ccs_recombine_noalloc": ([P, P, P, C.c_int, P, P], C.c_int),
             "ccs_cut_candidates": ([P, C.POINTER(ccs_problem), C.POINTER(ccs_cut_opts), C.POINTER(ccs_cut),
                                     C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_int], C.c_int),
             "ccs_get_stage_times": ([P, C.POINTER(C.c_double), C.c_int], C.c_int),
@@ -387,3 +388,12 @@ def ccs_cut_candidates(ctx, problem, max_cuts=12, max_nc_width=10, cap=64):
     return [([(cuts[j].qubit, cuts[j].gate_index) for j in range(offs[i], offs[i + 1])], costs[i])
             for i in range(n)]
 
+
+def ccs_recombine_noalloc(ctx, plan, res, marginal_out, zexp_out=None, precision=CCS_FP32):
+    """Recombination into caller-owned device buffers (torch float64 CUDA
+    tensors) with no device allocation by the library; asynchronous."""
+    ctx.check(lib().ccs_recombine_noalloc(ctx.h, plan.h, res.h, precision,
+                                          C.c_void_p(marginal_out.data_ptr()),
+                                          C.c_void_p(zexp_out.data_ptr() if zexp_out is not None else None)),
+              "ccs_recombine_noalloc")
+    return marginal_out, zexp_out

@@ -767,3 +767,44 @@ int ccs_get_tensor(ccs_ctx c, ccs_res r, int problem, int fragment, float* out) 
 
 }  // extern "C"
 
+// --- recombination without device allocation ---------------------------------
+// The scratch of the recombination (the leaves' Kronecker operand R and the
+// split-K partial tiles) lives in this fixed array instead of memory the
+// library allocates.  Every GPU that loads the library holds it until the
+// process exits.  In host code `g_noalloc_scratch` names a host-side stand-in,
+// not device memory, so its device address is looked up once per device.
+namespace {
+constexpr long long kNoAllocScratchFloats = 2ll << 20;   // 8 MiB of float
+static __device__ __align__(256) float g_noalloc_scratch[kNoAllocScratchFloats];
+constexpr int kMaxDevices = 64;
+float* g_noalloc_addr[kMaxDevices] = {};
+}  // namespace
+
+extern "C" int ccs_recombine_noalloc(ccs_ctx c, ccs_plan p, ccs_res r, int precision, double* marginal_out,
+                                     double* zexp_out) {
+  if (!c || !p || !r || r->plan != p) return fail(c, CCS_ERR_INVALID_ARG, "bad arguments");
+  if (c->host_only) return fail(c, CCS_ERR_UNSUPPORTED, "host-only context cannot recombine");
+  if (!p->all_star) return fail(c, CCS_ERR_UNSUPPORTED, "fragments do not form a star");
+  if (precision != CCS_FP32 && precision != CCS_BF16) return fail(c, CCS_ERR_INVALID_ARG, "bad precision");
+  if ((p->n_marg && !marginal_out) || (p->n_zexp && !zexp_out))
+    return fail(c, CCS_ERR_INVALID_ARG, "null output buffer");
+  const long long need = p->r_total + p->part_total;
+  if (need > kNoAllocScratchFloats)
+    return fail(c, CCS_ERR_UNSUPPORTED,
+                "recombination needs " + std::to_string(need * 4) + " bytes of scratch; the fixed scratch of "
+                "ccs_recombine_noalloc holds " + std::to_string(kNoAllocScratchFloats * 4) + " bytes");
+  if (c->device < 0 || c->device >= kMaxDevices) return fail(c, CCS_ERR_UNSUPPORTED, "device index too large");
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e != cudaSuccess) return cuda_fail(c, e, "set device");
+  if (!g_noalloc_addr[c->device]) {   // first call on this device: resolve the array's address
+    float* ptr = nullptr;
+    e = cudaGetSymbolAddress((void**)&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaGetSymbolAddress of the fixed scratch");
+    g_noalloc_addr[c->device] = ptr;
+  }
+  RecombSizes rz{p->r_total, p->part_total, p->gemm_blocks, p->n_marg, p->n_zexp,
+                 p->d_r_prefix, p->d_blk_prefix, p->d_out_prefix, p->d_z_prefix, p->max_tile_smem};
+  e = launch_recombine(p->dp, r->dr, precision, rz, g_noalloc_addr[c->device], marginal_out, zexp_out, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "recombine kernel");
+  return CCS_OK;
+}
