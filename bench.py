@@ -39,19 +39,30 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def workload(name):
+def workloads_for(name):
+    """The batch of circuits one step processes."""
     import workloads as W
-    if name == "config2":
-        return W.config2()
     if name == "config1":
-        return W.config1()
+        return [W.config1()]
+    if name == "config2":
+        return [W.config2()]
+    if name == "config3":
+        return [W.config3()]
+    if name == "config4":
+        return W.config4(256)
     raise SystemExit(f"unknown workload {name}")
 
 
-def describe(w):
-    return (f"{w.name}: {w.circuit.n_qubits} qubits, {len(w.circuit.gates)} gates, {w.circuit.n_t} T, "
-            f"{len(w.cuts)} cuts, {w.shots} shots/Clifford variant, {len(w.marginal)}-qubit marginal, "
-            f"{len(w.zstrings)} Z-strings")
+def describe(ws):
+    w = ws[0]
+    if len(ws) == 1:
+        return (f"{w.name}: {w.circuit.n_qubits} qubits, {len(w.circuit.gates)} gates, {w.circuit.n_t} T, "
+                f"{len(w.cuts)} cuts, {w.shots} shots/Clifford variant, {len(w.marginal)}-qubit marginal, "
+                f"{len(w.zstrings)} Z-strings")
+    nq = [x.circuit.n_qubits for x in ws]
+    return (f"{w.name.split('_')[0]}: {len(ws)} circuits of {min(nq)}-{max(nq)} qubits, "
+            f"{min(len(x.cuts) for x in ws)}-{max(len(x.cuts) for x in ws)} cuts, {w.shots} shots/Clifford "
+            f"variant, {len(w.marginal)}-qubit marginal each, one plan and one launch sequence per step")
 
 
 class Clocks:
@@ -64,7 +75,7 @@ class Clocks:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={q}",
-                                       "--format=csv,noheader,nounits", "-lms", "50"],
+                                       "--format=csv,noheader,nounits", "-lms", "10"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
@@ -96,17 +107,34 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def oracle_baseline(w, seconds_hint=""):
-    """The CPU oracle on one full circuit of the workload (all variants)."""
+def oracle_baseline(ws, budget_s=20.0):
+    """The CPU oracle on a bounded sample of the workload: whole circuits when
+    one fits the budget, else a sample of Clifford variants of the first one."""
     from oracle.pipeline import evaluate_workload
-    t0 = time.perf_counter()
-    r = evaluate_workload(w, mode="sampled", seed_lo=SEED[0], seed_hi=SEED[1], keep_tableaus=False)
-    dt = time.perf_counter() - t0
-    ncl = sum(f.n_variants for f in r.fragments if f.clifford)
-    return {"value": ncl * w.shots / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one full circuit of the workload ({ncl} Clifford variants x {w.shots} shots, "
-                      f"all statevector variants, fold and recombination), {dt:.1f} s single-threaded",
-            "circuits_per_s": 1.0 / dt}
+    from oracle.cutting import fragment_circuit
+    w = ws[0]
+    frags, _ = fragment_circuit(w.circuit, w.cuts, w.marginal)
+    ncl = sum(f.n_variants for f in frags if f.clifford)
+    if ncl <= 400:
+        t0 = time.perf_counter()
+        evaluate_workload(w, mode="sampled", seed_lo=SEED[0], seed_hi=SEED[1], keep_tableaus=False)
+        dt = time.perf_counter() - t0
+        return {"value": ncl * w.shots / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": f"one full circuit of the workload ({ncl} Clifford variants x {w.shots} shots, "
+                          f"all statevector variants, fold and recombination), {dt:.1f} s single-threaded",
+                "circuits_per_s": 1.0 / dt}
+    body = max(range(len(frags)), key=lambda i: frags[i].n if frags[i].clifford else -1)
+    vs, t_tot = [], 0.0
+    while t_tot < budget_s and len(vs) < frags[body].n_variants:
+        v = len(vs) * 97 % frags[body].n_variants
+        t0 = time.perf_counter()
+        evaluate_workload(w, mode="sampled", seed_lo=SEED[0], seed_hi=SEED[1], keep_tableaus=False,
+                          variants_only={body: [v]})
+        t_tot += time.perf_counter() - t0
+        vs.append(v)
+    return {"value": len(vs) * w.shots / t_tot, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{len(vs)} body variants x {w.shots} shots of the first circuit ({t_tot:.1f} s "
+                      f"single-threaded; a whole circuit has {ncl} Clifford variants)"}
 
 
 def run_reference(args, rank, world):
@@ -115,7 +143,8 @@ def run_reference(args, rank, world):
         return
     from oracle.pipeline import evaluate_workload
     from oracle.cutting import fragment_circuit
-    w = workload(args.workload)
+    ws = workloads_for(args.workload)
+    w = ws[0]
     frags, _ = fragment_circuit(w.circuit, w.cuts, w.marginal)
     body = max(range(len(frags)), key=lambda i: frags[i].n if frags[i].clifford else -1)
     nsamp = 8
@@ -136,7 +165,7 @@ def run_reference(args, rank, world):
     line = {"metric": METRIC, "value": val, "unit": UNIT, "impl": "reference", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8/f64",
-            "data": "synthetic", "config": {"workload": describe(w), "parallelism": "none (CPU oracle)"},
+            "data": "synthetic", "config": {"workload": describe(ws), "parallelism": "none (CPU oracle)"},
             "cpu_baseline": {"kind": "oracle", "cores": 1, "value": val, "unit": UNIT,
                              "sample": f"per step: {len(vs)} body variants x {w.shots} shots"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -157,15 +186,18 @@ def run_ours(args, rank, world, local_rank):
             dist.barrier()
         torch.cuda.synchronize()
 
-    w = workload(args.workload)
+    ws = workloads_for(args.workload)
+    w = ws[0]
     seed = (SEED[0] + rank, SEED[1])
     ctx = ccs.ccs_create(local_rank)
-    plan = ccs.ccs_build_fragments(ctx, [w])
-    infos = [ccs.ccs_fragment_info_get(ctx, plan, 0, f) for f in range(ccs.ccs_plan_counts(ctx, plan, 0)[0])]
+    plan = ccs.ccs_build_fragments(ctx, ws)
+    infos = []
+    for pi in range(len(ws)):
+        infos += [ccs.ccs_fragment_info_get(ctx, plan, pi, f) for f in range(ccs.ccs_plan_counts(ctx, plan, pi)[0])]
     n_cliff_var = sum(i["n_variants"] for i in infos if i["clifford"])
     units_per_step = n_cliff_var * w.shots
-    marg = torch.zeros(1 << len(w.marginal), dtype=torch.float64, device="cuda")
-    zexp = torch.zeros(max(1, len(w.zstrings)), dtype=torch.float64, device="cuda")
+    marg = torch.zeros(sum(1 << len(x.marginal) for x in ws), dtype=torch.float64, device="cuda")
+    zexp = torch.zeros(max(1, sum(len(x.zstrings) for x in ws)), dtype=torch.float64, device="cuda")
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")      # > 129 MB L2
     res = ccs.ccs_eval_variants(ctx, plan, mode=ccs.CCS_SAMPLED, shots=w.shots, seed_lo=seed[0],
                                 seed_hi=seed[1], use_graph=True)
@@ -215,7 +247,7 @@ def run_ours(args, rank, world, local_rank):
     for i in range(args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        p2 = ccs.ccs_build_fragments(ctx, [w])
+        p2 = ccs.ccs_build_fragments(ctx, ws)
         r2 = ccs.ccs_eval_variants(ctx, p2, mode=ccs.CCS_SAMPLED, shots=w.shots, seed_lo=seed[0],
                                    seed_hi=seed[1])
         m_host, z_host = ccs.ccs_recombine(ctx, p2, r2)
@@ -223,56 +255,81 @@ def run_ours(args, rank, world, local_rank):
         del r2, p2
     e2e_s = statistics.mean(e2e_times)
     h2d = sum(24 * len(x.circuit.gates) + 8 * len(x.cuts) + 4 * len(x.marginal) +
-              4 * sum(len(z) + 1 for z in x.zstrings) for x in [w])
-    d2h = 8 * ((1 << len(w.marginal)) + len(w.zstrings))
+              4 * sum(len(z) + 1 for z in x.zstrings) for x in ws)
+    d2h = 8 * sum((1 << len(x.marginal)) + len(x.zstrings) for x in ws)
 
     pk, pk_kind = peaks()
-    roof = roofline(dom, stage[dom], w, infos, pk, pk_kind)
+    roofs = stage_rooflines(stage, w, ws, infos, pk, pk_kind)
+    roof = dict(roofs[dom], stage=dom)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64/f32", "data": "synthetic",
-            "config": {"workload": describe(w), "variant_shots_per_step": units_per_step,
+            "config": {"workload": describe(ws), "variant_shots_per_step": units_per_step,
                        "l2": "flushed between steps (512 MB write, outside the step events)",
                        "parallelism": f"{world} independent replicas (no collective)",
                        "launch": "one CUDA-graph replay (eval) + recombination per step"},
-            "circuits_per_s": world * args.steps / t_tot,
-            "stage_ms": stage, "roofline": roof,
-            "e2e": {"value": units_per_step * world / e2e_s, "unit": UNIT, "circuits_per_s": world / e2e_s,
+            "circuits_per_s": world * len(ws) * args.steps / t_tot,
+            "stage_ms": stage, "roofline": roof, "stage_roofline": roofs,
+            "e2e": {"value": units_per_step * world / e2e_s, "unit": UNIT, "circuits_per_s": world * len(ws) / e2e_s,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": 7 * args.steps, "clocks": clocks}
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = oracle_baseline(w)
+        line["cpu_baseline"] = oracle_baseline(ws)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
 
 
-def roofline(stage, ms, w, infos, pk, pk_kind):
-    """Roofline of the dominant stage (algorithmic units per launch / time)."""
-    sm_mhz = pk.get("sm_max_mhz", 2070.0)
-    n_sm = 152
+N_SM = 152
+
+
+def stage_rooflines(stage, w, ws, infos, pk, pk_kind):
+    """Roofline of every stage: algorithmic work per launch / live duration.
+
+    clifford    alu: each fused 2-qubit Clifford update of one 64-row word is
+                70 64-bit logic ops (4x4 GF(2) map + sign polynomial) =
+                140 32-bit lane ops; peak = SMs x 128 lanes x clock
+    sample      alu: Philox4x32-10 = 20 32x32->64-bit multiplies per shot;
+                peak = SMs x 64 multiplies/clk x clock
+    statevector alu: a fused 4x4 complex op costs 128 FP32 flops per amplitude
+                quad (2x2: 32 per pair); peak = SMs x 128 FMA x 2 x clock
+    fold, operands, recombine
+                hbm: bytes of variant data / tensors read and written once;
+                peak = measured copy bandwidth
+    """
+    clk = pk.get("sm_max_mhz", 2070.0) * 1e6
     cl = [i for i in infos if i["clifford"]]
-    if stage == "sample":
-        shots = sum(i["n_variants"] for i in cl) * w.shots
-        # Philox4x32-10: 20 32x32->64-bit multiplies per shot; IMAD at 64/clk/SM
-        achieved = shots * 20 / (ms * 1e-3) / 1e12
-        peak = n_sm * 64 * sm_mhz * 1e6 / 1e12
-        return {"bound": "alu", "stage": stage, "achieved": achieved, "peak": peak,
-                "unit": "T int-mul/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": f"derived: {n_sm} SMs x 64 IMAD/clk x {sm_mhz:.0f} MHz"}
-    if stage == "clifford":
-        # bit-sliced CHP: per fused 2-qubit op per 64-row word, 4 columns read
-        # and written (64 B of shared memory); shared memory 128 B/clk/SM
-        ops = sum(i["n_variants"] * i["n_ops"] * 2 * ((i["n_wires"] + 63) // 64) for i in cl)
-        achieved = ops * 64 / (ms * 1e-3) / 1e9
-        peak = n_sm * 128 * sm_mhz * 1e6 / 1e9
-        return {"bound": "smem", "stage": stage, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None,
-                "peak_source": f"derived: {n_sm} SMs x 128 B/clk x {sm_mhz:.0f} MHz"}
-    hbm = pk["hbm_gbs"]
-    return {"bound": "hbm", "stage": stage, "achieved": None, "peak": hbm, "unit": "GB/s",
-            "frac": None, "traffic": None, "peak_source": pk_kind}
+    nc = [i for i in infos if not i["clifford"]]
+    out = {}
+    for st, ms in stage.items():
+        t = ms * 1e-3
+        if st == "clifford":
+            ops = sum(i["n_variants"] * i["n_ops"] * 2 * ((i["n_wires"] + 63) // 64) for i in cl)
+            a, p = ops * 140 / t / 1e12, N_SM * 128 * clk / 1e12
+            out[st] = {"bound": "alu", "achieved": a, "peak": p, "unit": "T lane-op/s",
+                       "peak_source": f"derived: {N_SM} SMs x 128 lanes x {clk/1e6:.0f} MHz"}
+        elif st == "sample":
+            shots = sum(i["n_variants"] for i in cl) * w.shots
+            a, p = shots * 20 / t / 1e12, N_SM * 64 * clk / 1e12
+            out[st] = {"bound": "alu", "achieved": a, "peak": p, "unit": "T int-mul/s",
+                       "peak_source": f"derived: {N_SM} SMs x 64 IMAD/clk x {clk/1e6:.0f} MHz"}
+        elif st == "statevector":
+            fl = sum(i["n_variants"] * i["n_ops"] * 32 * (1 << i["n_wires"]) for i in nc)
+            a, p = fl / t / 1e12, N_SM * 256 * clk / 1e12
+            out[st] = {"bound": "alu", "achieved": a, "peak": p, "unit": "TFLOP/s",
+                       "peak_source": f"derived: {N_SM} SMs x 128 FP32 FMA x 2 x {clk/1e6:.0f} MHz"}
+        else:
+            if st == "recombine":
+                by = sum(4 * (1 << len(x.marginal)) * 4 ** len(x.cuts) for x in ws)   # hub operand read once
+            else:
+                by = sum(i["n_variants"] * 4 * (1 << i["n_meas"]) for i in infos)       # variant data read once
+            a, p = by / t / 1e9, pk["hbm_gbs"]
+            out[st] = {"bound": "hbm", "achieved": a, "peak": p, "unit": "GB/s", "peak_source": pk_kind}
+        out[st]["frac"] = out[st]["achieved"] / out[st]["peak"]
+        out[st]["traffic"] = None
+        out[st]["ms"] = ms
+    return out
 
 
 def main():

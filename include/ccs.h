@@ -163,8 +163,12 @@ typedef struct {
                               CCS_SAMPLED: `shots` Philox shots per Clifford variant */
   uint32_t shots;
   uint32_t seed_lo, seed_hi;   /* Philox4x32-10 key */
-  int32_t keep_tableaus;   /* 1: keep every final tableau for ccs_get_tableau */
+  int32_t keep_tableaus;   /* 1: keep every final tableau (ccs_get_tableau) and the
+                              star hub's dense shot counts (ccs_get_counts) */
   int32_t use_graph;       /* 1: capture the launches in a CUDA graph and replay */
+  int32_t autotune;        /* 1: before the first launch of this result, time the
+                              candidate launch shapes on this plan and keep the
+                              fastest (cached in the context per shape bucket) */
 } ccs_eval_opts;
 
 /* Evaluate every variant of every fragment of the plan on the GPU: tableau
@@ -176,6 +180,10 @@ typedef struct {
  * call is asynchronous on the context stream; getters synchronise. */
 int ccs_eval_variants(ccs_ctx ctx, ccs_plan plan, const ccs_eval_opts* opts, ccs_res* res);
 void ccs_res_free(ccs_res res);
+/* Launch shape in use for a result (after autotuning, if any): threads per
+ * tableau CTA, 64-row words of one fused op per thread, shots per sampling
+ * CTA. */
+int ccs_get_tuning(ccs_ctx ctx, ccs_res res, int* cliff_threads, int* words_per_op, int* shots_per_cta);
 
 /* --- recombination (Sec. V-C) --------------------------------------------- */
 #define CCS_FP32 0
@@ -183,6 +191,8 @@ void ccs_res_free(ccs_res res);
 typedef struct {
   int32_t precision;          /* CCS_FP32 or CCS_BF16 operands of the 4^k contraction */
   int32_t outputs_on_device;  /* 1: marginal_out / zexp_out are device pointers */
+  int32_t no_tensor_cores;    /* 1: BF16 contractions on CUDA cores even where the
+                                 tcgen05 GEMM applies (0: use it, the default) */
 } ccs_recomb_opts;
 
 /* p(o) = 2^-k sum_{P in {I,X,Y,Z}^k} prod_f T_f(o_f, P|f) for every problem,
@@ -242,9 +252,11 @@ int ccs_fragment_wires(ccs_ctx ctx, ccs_plan plan, int problem, int fragment, ui
  * CUDA events on the context stream around each kernel stage; recombination
  * does the same.  ccs_get_stage_times synchronises the stream and writes the
  * last recorded duration of each stage in milliseconds (-1 if the stage did
- * not run) to ms[0..4]: 0 tableau evolution + outcome space + Z values
- * (one persistent kernel), 1 Philox sampling, 2 statevectors, 3 fold,
- * 4 recombination.  Returns the number of stages (5) or an error; cap >= 5. */
+ * not run) to ms[0..5]: 0 tableau evolution + outcome space + Z values
+ * (one persistent kernel), 1 Philox sampling, 2 statevectors, 3 fold of the
+ * Clifford fragments, 4 recombination, 5 contraction operands (the hub's
+ * output-folded Q and the other fragments' preparation-weighted T').
+ * Returns the number of stages (6) or an error; cap >= 6. */
 int ccs_set_profiling(ccs_ctx ctx, int on);
 int ccs_get_stage_times(ccs_ctx ctx, double* ms, int cap);
 
@@ -263,7 +275,16 @@ int ccs_get_counts(ccs_ctx ctx, ccs_res res, int problem, int fragment, int vari
 /* Probabilities of a variant over 2^|A_f| outcomes (float32): exact ones for
  * non-Clifford variants and exact-mode Clifford variants. */
 int ccs_get_dist(ccs_ctx ctx, ccs_res res, int problem, int fragment, int variant, float* out);
-/* Folded fragment tensor T_f[o][P] (float32, 2^n_marg x 4^n_slots, row-major). */
+/* Contraction operand of a fragment of a star (float32, 2^n_marg x 4^n_slots):
+ * for the hub Q[o][d] with d's digit at each cut = the preparation index where
+ * the hub has a quantum input and the Pauli index where it has a quantum
+ * output; for the other fragments T'[o][d] = T_f with the preparation weights
+ * applied at the cuts where the fragment feeds the hub.  Then
+ * p(o) = 2^-k sum_d Q[o_hub][d] prod T'[o_f][d|f]. */
+int ccs_get_operand(ccs_ctx ctx, ccs_res res, int problem, int fragment, float* out);
+/* Folded fragment tensor T_f[o][P] (float32, 2^n_marg x 4^n_slots, row-major).
+ * For the hub of a star this is computed on request (the contraction uses
+ * the hub's output-folded data directly). */
 int ccs_get_tensor(ccs_ctx ctx, ccs_res res, int problem, int fragment, float* out);
 
 #ifdef __cplusplus

@@ -27,8 +27,9 @@ EXPORTS = ["ccs_version", "ccs_create", "ccs_destroy", "ccs_last_error", "ccs_bu
            "ccs_plan_free", "ccs_eval_variants", "ccs_res_free", "ccs_recombine", "ccs_plan_counts",
            "ccs_fragment_info_get", "ccs_plan_cuts", "ccs_fragment_wires", "ccs_get_tableau",
            "ccs_get_outcome_space", "ccs_get_counts", "ccs_get_dist", "ccs_get_tensor",
-           "ccs_set_profiling", "ccs_get_stage_times", "ccs_cut_candidates", "ccs_recombine_noalloc"]
-STAGES = ["clifford", "sample", "statevector", "fold", "recombine"]
+           "ccs_set_profiling", "ccs_get_stage_times", "ccs_cut_candidates", "ccs_recombine_noalloc",
+           "ccs_get_tuning", "ccs_get_operand"]
+STAGES = ["clifford", "sample", "statevector", "fold", "recombine", "operands"]
 
 
 class ccs_gate(C.Structure):
@@ -54,11 +55,12 @@ class ccs_cut_opts(C.Structure):
 
 class ccs_eval_opts(C.Structure):
     _fields_ = [("mode", C.c_int32), ("shots", C.c_uint32), ("seed_lo", C.c_uint32),
-                ("seed_hi", C.c_uint32), ("keep_tableaus", C.c_int32), ("use_graph", C.c_int32)]
+                ("seed_hi", C.c_uint32), ("keep_tableaus", C.c_int32), ("use_graph", C.c_int32),
+                ("autotune", C.c_int32)]
 
 
 class ccs_recomb_opts(C.Structure):
-    _fields_ = [("precision", C.c_int32), ("outputs_on_device", C.c_int32)]
+    _fields_ = [("precision", C.c_int32), ("outputs_on_device", C.c_int32), ("no_tensor_cores", C.c_int32)]
 
 
 class ccs_fragment_info(C.Structure):
@@ -110,8 +112,10 @@ def lib():
             "ccs_get_counts": ([P, P, C.c_int, C.c_int, C.c_int, P], C.c_int),
             "ccs_get_dist": ([P, P, C.c_int, C.c_int, C.c_int, P], C.c_int),
             "ccs_get_tensor": ([P, P, C.c_int, C.c_int, P], C.c_int),
+            "ccs_get_operand": ([P, P, C.c_int, C.c_int, P], C.c_int),
             "ccs_set_profiling": ([P, C.c_int], C.c_int),
             "ccs_recombine_noalloc": ([P, P, P, C.c_int, P, P], C.c_int),
+            "ccs_get_tuning": ([P, P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
             "ccs_cut_candidates": ([P, C.POINTER(ccs_problem), C.POINTER(ccs_cut_opts), C.POINTER(ccs_cut),
                                     C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_int], C.c_int),
             "ccs_get_stage_times": ([P, C.POINTER(C.c_double), C.c_int], C.c_int),
@@ -265,8 +269,8 @@ def ccs_build_fragments(ctx, problems, max_cuts=12, max_nc_width=10, use_learned
 
 
 def ccs_eval_variants(ctx, plan, mode=CCS_SAMPLED, shots=1024, seed_lo=0x1234, seed_hi=0x5678,
-                      keep_tableaus=False, use_graph=False, res=None):
-    opts = ccs_eval_opts(mode, shots, seed_lo, seed_hi, int(keep_tableaus), int(use_graph))
+                      keep_tableaus=False, use_graph=False, res=None, autotune=False):
+    opts = ccs_eval_opts(mode, shots, seed_lo, seed_hi, int(keep_tableaus), int(use_graph), int(autotune))
     h = C.c_void_p(res.h.value if res is not None else None)
     ctx.check(lib().ccs_eval_variants(ctx.h, plan.h, C.byref(opts), C.byref(h)), "ccs_eval_variants")
     if res is not None:
@@ -274,13 +278,13 @@ def ccs_eval_variants(ctx, plan, mode=CCS_SAMPLED, shots=1024, seed_lo=0x1234, s
     return Res(ctx, plan, h)
 
 
-def ccs_recombine(ctx, plan, res, precision=CCS_FP32, marginal_out=None, zexp_out=None):
+def ccs_recombine(ctx, plan, res, precision=CCS_FP32, marginal_out=None, zexp_out=None, tensor_cores=True):
     """Host mode (default): returns (marginal, zexp) float64 numpy arrays with
     all problems back to back.  Device mode: pass torch float64 CUDA tensors
     as ``marginal_out`` / ``zexp_out``; the call does not synchronise."""
     on_dev = marginal_out is not None and hasattr(marginal_out, "data_ptr")
     if on_dev:
-        opts = ccs_recomb_opts(precision, 1)
+        opts = ccs_recomb_opts(precision, 1, 0 if tensor_cores else 1)
         ctx.check(lib().ccs_recombine(ctx.h, plan.h, res.h, C.byref(opts),
                                       C.c_void_p(marginal_out.data_ptr()),
                                       C.c_void_p(zexp_out.data_ptr() if zexp_out is not None else None)),
@@ -290,7 +294,7 @@ def ccs_recombine(ctx, plan, res, precision=CCS_FP32, marginal_out=None, zexp_ou
     nz = sum(len(getattr(p, "zstrings", []) or []) for p in plan.problems)
     marg = np.zeros(max(nm, 1))
     zexp = np.zeros(max(nz, 1))
-    opts = ccs_recomb_opts(precision, 0)
+    opts = ccs_recomb_opts(precision, 0, 0 if tensor_cores else 1)
     ctx.check(lib().ccs_recombine(ctx.h, plan.h, res.h, C.byref(opts),
                                   marg.ctypes.data_as(C.c_void_p), zexp.ctypes.data_as(C.c_void_p)),
               "ccs_recombine")
@@ -397,3 +401,18 @@ def ccs_recombine_noalloc(ctx, plan, res, marginal_out, zexp_out=None, precision
                                           C.c_void_p(zexp_out.data_ptr() if zexp_out is not None else None)),
               "ccs_recombine_noalloc")
     return marginal_out, zexp_out
+
+
+def ccs_get_tuning(ctx, res):
+    """(threads per tableau CTA, words per op per thread, shots per sampling CTA)."""
+    t, wpo, spc = C.c_int(), C.c_int(), C.c_int()
+    ctx.check(lib().ccs_get_tuning(ctx.h, res.h, C.byref(t), C.byref(wpo), C.byref(spc)), "ccs_get_tuning")
+    return t.value, wpo.value, spc.value
+
+
+def ccs_get_operand(ctx, res, problem, fragment):
+    info = ccs_fragment_info_get(ctx, res.plan, problem, fragment)
+    out = np.zeros((1 << info["n_marg"], 4 ** info["n_slots"]), np.float32)
+    ctx.check(lib().ccs_get_operand(ctx.h, res.h, problem, fragment, out.ctypes.data_as(C.c_void_p)),
+              "ccs_get_operand")
+    return out

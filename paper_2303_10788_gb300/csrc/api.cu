@@ -4,7 +4,9 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "kernels.cuh"
@@ -21,6 +23,11 @@ struct ccs_ctx_s {
   int sm_count = 0;
   size_t smem_optin = 0;
   std::string err;
+  // autotuner results: shape bucket -> (Clifford threads per CTA, shots per sampler CTA)
+  std::map<std::tuple<int, int, unsigned, int>, std::tuple<int, int, int>> tuned;
+  // second stream for the statevector branch (forked from / joined into `stream`)
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   // stage timing (CUDA events around each launch on the context stream)
   bool profiling = false;
   cudaEvent_t ev[16] = {};
@@ -30,7 +37,7 @@ struct ccs_ctx_s {
 };
 
 namespace {
-enum Stage { ST_CLIFFORD = 0, ST_SAMPLE = 1, ST_STATEVEC = 2, ST_FOLD = 3, ST_RECOMB = 4, ST_N = 5 };
+enum Stage { ST_CLIFFORD = 0, ST_SAMPLE = 1, ST_STATEVEC = 2, ST_FOLD = 3, ST_RECOMB = 4, ST_OPERANDS = 5, ST_N = 6 };
 void stage_begin(ccs_ctx c, int st) {
   if (!c->profiling) return;
   if (!c->ev[2 * st]) { cudaEventCreate(&c->ev[2 * st]); cudaEventCreate(&c->ev[2 * st + 1]); }
@@ -113,13 +120,18 @@ struct ccs_plan_s {
   std::vector<long long> t_prefix, tz_prefix, out_prefix, z_prefix, r_prefix, blk_prefix;
   long long* d_r_prefix = nullptr;
   long long* d_blk_prefix = nullptr;
-  long long r_total = 0, part_total = 0, gemm_blocks = 0;
+  long long r_total = 0, part_total = 0, gemm_blocks = 0, rt_total = 0;
   int max_tile_smem = 0;
   long long* d_t_prefix = nullptr;
   long long* d_tz_prefix = nullptr;
   long long* d_out_prefix = nullptr;
   long long* d_z_prefix = nullptr;
   int cliff_smem_words = 0, max_nc_n = 1;
+  FoldSet fold_cliff{}, fold_nc{}, fold_hubs{}, fold_hubs_nc{}, fold_others{};
+  int2* d_items_hub = nullptr;      // Clifford hub variants (fused sampler)
+  int2* d_items_plain = nullptr;    // other Clifford variants (sampler -> counts)
+  int n_items_hub = 0, n_items_plain = 0, max_hub_nA = 0;
+  long long n_counts_plain = 0;     // counts of non-hub Clifford fragments come first
   bool all_star = true;
   ~ccs_plan_s() { A.release(); }
 };
@@ -135,8 +147,10 @@ struct ccs_res_s {
   EvalParams graph_key{};
   int graph_valid = 0;
   int cliff_threads = 256;
+  int cliff_words = 1;        // words per op per thread in the tableau kernel
   int sample_spc = 4096;
   float* scratch = nullptr;   // recombination: R operand + split-K partials
+  uint16_t* rt_scratch = nullptr;   // bf16 R'^T of tensor-core-eligible problems
   ~ccs_res_s() {
     if (graph) cudaGraphExecDestroy(graph);
     A.release();
@@ -169,6 +183,12 @@ int ccs_create(ccs_ctx* out, int device, void* cuda_stream, const ccs_allocator*
   }
   if (cudaSetDevice(device) != cudaSuccess) { delete c; return CCS_ERR_CUDA; }
   cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+  if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming) != cudaSuccess) {
+    delete c;
+    return CCS_ERR_CUDA;
+  }
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
   c->smem_optin = (size_t)optin;
@@ -180,6 +200,9 @@ void ccs_destroy(ccs_ctx c) {
   if (!c) return;
   for (auto& e : c->ev)
     if (e) cudaEventDestroy(e);
+  if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+  if (c->join_ev) cudaEventDestroy(c->join_ev);
+  if (c->side) cudaStreamDestroy(c->side);
   delete c;
 }
 
@@ -308,7 +331,9 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
       d.tab_off = plan->n_tab;
       plan->n_tab += (long long)d.nv * (2 * d.n + 3) * d.W;
       const int words = (2 * d.n + 3) * d.W + (d.n + 1) / 2 + 2;
-      plan->cliff_smem_words = std::max(plan->cliff_smem_words, words);
+      const int staged = words + (int)f.cops.size() + (d.n_moments + 2) / 2 + 2;   // + op stream
+      plan->cliff_smem_words =
+          std::max(plan->cliff_smem_words, (size_t)staged * 8 <= c->smem_optin ? staged : words);
       for (int v = 0; v < d.nv; ++v) {
         items_c.push_back(make_int2((int)fi, v));
         cost_c.push_back((long long)d.W * (d.n_moments + 4) * std::max(1, d.n / 16) + d.nz * 4 + d.nA * d.n);
@@ -325,8 +350,8 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
     plan->n_dist += (long long)d.nv * outs;
     d.zval_off = plan->n_zval;
     plan->n_zval += (long long)d.nv * d.nz * (1ll << d.qout);
-    d.T_off = plan->n_T;
-    plan->n_T += (1ll << d.m) * (1ll << (2 * d.n_slots));
+    d.T_off = (plan->n_T + 63) & ~63ll;     // 256-byte aligned (TMA needs 16)
+    plan->n_T = d.T_off + (1ll << d.m) * (1ll << (2 * d.n_slots));
     d.TZ_off = plan->n_TZ;
     plan->n_TZ += (long long)d.nz * (1ll << (2 * d.n_slots));
     plan->fdev.push_back(d);
@@ -357,6 +382,50 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
     plan->t_prefix.push_back(plan->t_prefix.back() + (1ll << f.m) * (1ll << (2 * f.n_slots)));
     plan->tz_prefix.push_back(plan->tz_prefix.back() + (long long)f.nz * (1ll << (2 * f.n_slots)));
   }
+  // roles in star problems: the hub's contraction operand is Q, the others' T'
+  {
+    int f0r = 0;
+    for (auto& P : plan->problems) {
+      const int nfr = (int)P.frag_ids.size();
+      if (P.hub >= 0)
+        for (int l = 0; l < nfr; ++l) plan->fdev[f0r + l].role = (l == P.hub) ? 1 : 2;
+      f0r += nfr;
+    }
+  }
+  // shot counts: non-hub Clifford fragments first (they are zeroed before
+  // sampling), hub fragments after (written whole by the fused sampler)
+  {
+    long long off = 0;
+    for (auto& f : plan->fdev)
+      if (f.clifford && f.role != 1) { f.counts_off = off; off += (long long)f.nv << f.nA; }
+    plan->n_counts_plain = off;
+    for (auto& f : plan->fdev)
+      if (f.clifford && f.role == 1) { f.counts_off = off; off += (long long)f.nv << f.nA; }
+  }
+  std::vector<int2> items_hub, items_plain;
+  for (auto& it : items_c) {
+    const FragDev& f = plan->fdev[it.x];
+    if (f.role == 1) { items_hub.push_back(it); plan->max_hub_nA = std::max(plan->max_hub_nA, f.nA); }
+    else items_plain.push_back(it);
+  }
+  plan->n_items_hub = (int)items_hub.size();
+  plan->n_items_plain = (int)items_plain.size();
+  // fold sets: T of non-hub Clifford fragments (main stream) and non-hub
+  // statevector fragments (side branch); T^S of every fragment; then the
+  // contraction operands Q (hubs) and T' (the others)
+  std::vector<int> fidx_c, fidx_nc, fidx_h, fidx_hn, fidx_o;
+  std::vector<long long> tp_c{0}, tzp_c{0}, tp_nc{0}, tzp_nc{0}, tp_h{0}, tp_hn{0}, tp_o{0};
+  std::vector<long long> zero_h{0}, zero_hn{0}, zero_o{0};
+  for (int fi = 0; fi < (int)plan->fdev.size(); ++fi) {
+    const FragDev& f = plan->fdev[fi];
+    const long long t = (1ll << f.m) * (1ll << (2 * f.n_slots)), tz = (long long)f.nz * (1ll << (2 * f.n_slots));
+    const long long tf = f.role == 1 ? 0 : t;    // hubs: T only on request
+    if (f.clifford) { fidx_c.push_back(fi); tp_c.push_back(tp_c.back() + tf); tzp_c.push_back(tzp_c.back() + tz); }
+    else { fidx_nc.push_back(fi); tp_nc.push_back(tp_nc.back() + tf); tzp_nc.push_back(tzp_nc.back() + tz); }
+    if (f.role == 1) { fidx_h.push_back(fi); tp_h.push_back(tp_h.back() + t); zero_h.push_back(0); }
+    if (f.role == 1 && !f.clifford) { fidx_hn.push_back(fi); tp_hn.push_back(tp_hn.back() + t); zero_hn.push_back(0); }
+    if (f.role == 2) { fidx_o.push_back(fi); tp_o.push_back(tp_o.back() + t); zero_o.push_back(0); }
+  }
   for (auto& P : plan->problems) {
     ProblemDev d{};
     d.k = (int)P.cuts.size();
@@ -377,8 +446,9 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
       d.M = 1 << m_hub;
       d.N = 1 << (d.n_marg - m_hub);
       d.K = 1ll << (2 * d.k);
-      d.TN = std::min(d.N, 64);
-      d.TM = std::min(d.M, std::max(1, 1024 / d.TN));
+      auto up4 = [](int x) { return (x + 3) & ~3; };
+      d.TN = std::min(up4(d.N), 64);                          // tile: TM x TN, 4x4 per thread,
+      d.TM = std::min(up4(d.M), 4096 / d.TN);                 // at most 256 threads
       d.mtiles = (d.M + d.TM - 1) / d.TM;
       d.ntiles = (d.N + d.TN - 1) / d.TN;
       const long long base = (long long)d.mtiles * d.ntiles;
@@ -391,7 +461,13 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
       plan->part_total += (long long)d.splits * d.M * d.N;
       d.blk_off = plan->gemm_blocks;
       plan->gemm_blocks += base * d.splits;
-      plan->max_tile_smem = std::max(plan->max_tile_smem, (d.TM * (16 + 1) + 16 * d.TN) * 4);
+      plan->max_tile_smem = std::max(plan->max_tile_smem, 16 * (d.TM + d.TN) * 4);
+      d.hub_T_off = plan->fdev[f0 + P.hub].T_off;
+      d.tc = (gemm_tc_supported(d.M, d.N, d.K) && d.K >= 4096 && d.M >= 128) ? 1 : 0;
+      if (d.tc) {
+        d.rt_off = (plan->rt_total + 63) & ~63ll;
+        plan->rt_total = d.rt_off + d.K * d.N;
+      }
     }
     plan->r_prefix.push_back(plan->r_total);
     plan->blk_prefix.push_back(plan->gemm_blocks);
@@ -399,11 +475,32 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
     plan->pdev.push_back(d);
   }
 
+  // the scratch holds every problem's R operand first, then the split-K partials
+  for (auto& d : plan->pdev) d.part_off += plan->r_total;
   std::vector<CliffordOp> prep(4), basis(3);
   std::vector<float> prepm(32), basism(24);
   for (int s = 0; s < 4; ++s) { prep[s] = prep_op(s); prep_matrix(s, &prepm[8 * s]); }
   for (int b = 0; b < 3; ++b) { basis[b] = basis_op(b); basis_matrix(b, &basism[8 * b]); }
 
+  int *d_fidx_c, *d_fidx_nc, *d_fidx_h, *d_fidx_hn, *d_fidx_o;
+  long long *d_tp_c, *d_tzp_c, *d_tp_nc, *d_tzp_nc, *d_tp_h, *d_tp_hn, *d_tp_o, *d_zh, *d_zhn, *d_zo;
+  if (!c->host_only) {
+    bool okf = upload(c, plan->A, fidx_c, &d_fidx_c) && upload(c, plan->A, fidx_nc, &d_fidx_nc) &&
+               upload(c, plan->A, tp_c, &d_tp_c) && upload(c, plan->A, tzp_c, &d_tzp_c) &&
+               upload(c, plan->A, tp_nc, &d_tp_nc) && upload(c, plan->A, tzp_nc, &d_tzp_nc) &&
+               upload(c, plan->A, fidx_h, &d_fidx_h) && upload(c, plan->A, fidx_o, &d_fidx_o) &&
+               upload(c, plan->A, tp_h, &d_tp_h) && upload(c, plan->A, tp_o, &d_tp_o) &&
+               upload(c, plan->A, zero_h, &d_zh) && upload(c, plan->A, zero_o, &d_zo) &&
+               upload(c, plan->A, fidx_hn, &d_fidx_hn) && upload(c, plan->A, tp_hn, &d_tp_hn) &&
+               upload(c, plan->A, zero_hn, &d_zhn) && upload(c, plan->A, items_hub, &plan->d_items_hub) &&
+               upload(c, plan->A, items_plain, &plan->d_items_plain);
+    if (!okf) { delete plan; return fail(c, CCS_ERR_OOM, "plan upload failed"); }
+    plan->fold_cliff = FoldSet{d_fidx_c, d_tp_c, d_tzp_c, (int)fidx_c.size(), tp_c.back(), tzp_c.back()};
+    plan->fold_nc = FoldSet{d_fidx_nc, d_tp_nc, d_tzp_nc, (int)fidx_nc.size(), tp_nc.back(), tzp_nc.back()};
+    plan->fold_hubs = FoldSet{d_fidx_h, d_tp_h, d_zh, (int)fidx_h.size(), tp_h.back(), 0};
+    plan->fold_hubs_nc = FoldSet{d_fidx_hn, d_tp_hn, d_zhn, (int)fidx_hn.size(), tp_hn.back(), 0};
+    plan->fold_others = FoldSet{d_fidx_o, d_tp_o, d_zo, (int)fidx_o.size(), tp_o.back(), 0};
+  }
   if (c->host_only) {
     plan->dp.n_items_cliff = (int)items_c.size();
     plan->dp.n_items_nc = (int)items_nc.size();
@@ -471,47 +568,134 @@ int ccs_cut_candidates(ccs_ctx c, const ccs_problem* q, const ccs_cut_opts* opts
   return n;
 }
 
+// Evaluation as two branches: Clifford variants (tableaus -> spaces/Z-values
+// -> sampling -> fold) on the context stream, statevector variants (+ their
+// fold) on the side stream, forked after the memsets and joined at the end.
+// With profiling on, everything runs on the context stream so each stage's
+// events bracket one kernel.
 static int enqueue_eval(ccs_ctx c, ccs_plan p, ccs_res r) {
   cudaStream_t s = c->stream;
   const EvalParams& e = r->ep;
   cudaError_t err;
   if ((err = cudaMemsetAsync(r->dr.work, 0, 4 * sizeof(unsigned), s)) != cudaSuccess) return cuda_fail(c, err, "memset");
-  if (e.mode == CCS_SAMPLED && p->n_counts)
-    if ((err = cudaMemsetAsync(r->dr.counts, 0, p->n_counts * sizeof(uint32_t), s)) != cudaSuccess)
+  if (e.mode == CCS_SAMPLED && p->n_counts_plain)
+    if ((err = cudaMemsetAsync(r->dr.counts, 0, p->n_counts_plain * sizeof(uint32_t), s)) != cudaSuccess)
       return cuda_fail(c, err, "memset counts");
   if (e.mode == CCS_EXACT && p->n_dist)
     if ((err = cudaMemsetAsync(r->dr.dist, 0, p->n_dist * sizeof(float), s)) != cudaSuccess)
       return cuda_fail(c, err, "memset dist");
   const DevPlan& dp = p->dp;
+  const bool fork = dp.n_items_nc > 0 && !c->profiling;
+  cudaStream_t s2 = fork ? c->side : s;
+  if (fork) {
+    if ((err = cudaEventRecord(c->fork_ev, s)) != cudaSuccess) return cuda_fail(c, err, "fork");
+    if ((err = cudaStreamWaitEvent(s2, c->fork_ev, 0)) != cudaSuccess) return cuda_fail(c, err, "fork wait");
+  }
+  if (dp.n_items_nc) {
+    int grid = std::min(dp.n_items_nc, c->sm_count * 4);
+    int threads = std::min(256, std::max(32, 1 << std::max(0, p->max_nc_n - 2)));
+    stage_begin(c, ST_STATEVEC);
+    if ((err = launch_statevector(dp, r->dr, p->max_nc_n, threads, grid, s2)) != cudaSuccess)
+      return cuda_fail(c, err, "statevector kernel");
+    stage_end(c, ST_STATEVEC);
+    if ((err = launch_fold(dp, r->dr, e, p->fold_nc, s2)) != cudaSuccess) return cuda_fail(c, err, "fold kernel");
+  }
   if (dp.n_items_cliff) {
     const int threads = r->cliff_threads;
     const size_t smem = (size_t)p->cliff_smem_words * 8;
     int per_sm = (int)std::max<size_t>(1, std::min<size_t>(2048 / threads, (c->smem_optin + 1024) / (smem + 2048)));
     int grid = std::min(dp.n_items_cliff, c->sm_count * per_sm);
     stage_begin(c, ST_CLIFFORD);
-    if ((err = launch_clifford(dp, r->dr, e, threads, p->cliff_smem_words, grid, s)) != cudaSuccess)
+    if ((err = launch_clifford(dp, r->dr, e, threads, r->cliff_words, p->cliff_smem_words, grid, s)) != cudaSuccess)
       return cuda_fail(c, err, "clifford kernel");
     stage_end(c, ST_CLIFFORD);
     if (e.mode == CCS_SAMPLED) {
       stage_begin(c, ST_SAMPLE);
-      if ((err = launch_sample(dp, r->dr, e, r->sample_spc, 256, s)) != cudaSuccess)
+      if ((err = launch_sample_hub(dp, r->dr, e, p->d_items_hub, p->n_items_hub, p->max_hub_nA, e.keep_tableaus,
+                                   s)) != cudaSuccess)
+        return cuda_fail(c, err, "hub sample kernel");
+      if ((err = launch_sample(dp, r->dr, e, p->d_items_plain, p->n_items_plain, r->sample_spc, 256, s)) !=
+          cudaSuccess)
         return cuda_fail(c, err, "sample kernel");
       stage_end(c, ST_SAMPLE);
     }
+    stage_begin(c, ST_FOLD);
+    if ((err = launch_fold(dp, r->dr, e, p->fold_cliff, s)) != cudaSuccess) return cuda_fail(c, err, "fold kernel");
+    stage_end(c, ST_FOLD);
   }
-  if (dp.n_items_nc) {
-    int grid = std::min(dp.n_items_nc, c->sm_count * 4);
-    int threads = std::min(256, std::max(32, 1 << std::max(0, p->max_nc_n - 2)));
-    stage_begin(c, ST_STATEVEC);
-    if ((err = launch_statevector(dp, r->dr, p->max_nc_n, threads, grid, s)) != cudaSuccess)
-      return cuda_fail(c, err, "statevector kernel");
-    stage_end(c, ST_STATEVEC);
+  if (fork) {
+    if ((err = cudaEventRecord(c->join_ev, s2)) != cudaSuccess) return cuda_fail(c, err, "join");
+    if ((err = cudaStreamWaitEvent(s, c->join_ev, 0)) != cudaSuccess) return cuda_fail(c, err, "join wait");
   }
-  stage_begin(c, ST_FOLD);
-  if ((err = launch_fold(dp, r->dr, e, p->d_t_prefix, (int)p->fdev.size(), p->n_T, p->d_tz_prefix, p->n_TZ, s)) !=
-      cudaSuccess)
-    return cuda_fail(c, err, "fold kernel");
-  stage_end(c, ST_FOLD);
+  stage_begin(c, ST_OPERANDS);
+  // hubs: Clifford hubs in sampled mode already have Q from the fused sampler
+  const FoldSet& hubs = e.mode == CCS_SAMPLED ? p->fold_hubs_nc : p->fold_hubs;
+  if ((err = launch_operands(dp, r->dr, e, hubs, p->fold_others, s)) != cudaSuccess)
+    return cuda_fail(c, err, "operand kernels");
+  stage_end(c, ST_OPERANDS);
+  return CCS_OK;
+}
+
+// Autotuner: time every (Clifford threads per CTA, shots per sampler CTA)
+// candidate on this plan with CUDA events (one warm-up + three timed
+// evaluations each) and keep the fastest; cached per shape bucket (widest
+// Clifford fragment rounded up to 64 wires, Clifford variant count rounded up
+// to a power of two, shots, mode).
+static int autotune(ccs_ctx c, ccs_plan p, ccs_res r) {
+  int max_n = 0;
+  for (auto& f : p->fdev)
+    if (f.clifford) max_n = std::max(max_n, f.n);
+  int items = 1;
+  while (items < p->dp.n_items_cliff) items <<= 1;
+  const auto key = std::make_tuple((max_n + 63) / 64, items, r->ep.shots, r->ep.mode);
+  auto it = c->tuned.find(key);
+  if (it != c->tuned.end()) {
+    std::tie(r->cliff_threads, r->cliff_words, r->sample_spc) = it->second;
+    return CCS_OK;
+  }
+  const int threads_c[] = {128, 256, 512};
+  const int spc_c[] = {1024, 2048, 4096, 8192};
+  const int words_c[] = {1, 2, 4, 8};
+  const int n_spc = r->ep.mode == CCS_SAMPLED ? 4 : 1;
+  const int max_w = 2 * ((max_n + 63) / 64);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return fail(c, CCS_ERR_CUDA, "autotune events");
+  float best = 1e30f;
+  std::tuple<int, int, int> choice{r->cliff_threads, r->cliff_words, r->sample_spc};
+  int rc = CCS_OK;
+  for (int ti = 0; ti < 3 && rc == CCS_OK; ++ti)
+    for (int wi = 0; wi < 4 && rc == CCS_OK; ++wi)
+    for (int si = 0; si < n_spc && rc == CCS_OK; ++si) {
+      if (words_c[wi] > max_w) continue;
+      r->cliff_threads = threads_c[ti];
+      r->cliff_words = words_c[wi];
+      r->sample_spc = spc_c[si];
+      rc = enqueue_eval(c, p, r);
+      if (rc != CCS_OK) break;
+      cudaEventRecord(e0, c->stream);
+      for (int rep = 0; rep < 3 && rc == CCS_OK; ++rep) rc = enqueue_eval(c, p, r);
+      cudaEventRecord(e1, c->stream);
+      float ms = 0.f;
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        rc = fail(c, CCS_ERR_CUDA, "autotune timing");
+        break;
+      }
+      if (ms < best) { best = ms; choice = {threads_c[ti], words_c[wi], spc_c[si]}; }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != CCS_OK) return rc;
+  std::tie(r->cliff_threads, r->cliff_words, r->sample_spc) = choice;
+  c->tuned[key] = choice;
+  return CCS_OK;
+}
+
+int ccs_get_tuning(ccs_ctx c, ccs_res r, int* cliff_threads, int* words_per_op, int* shots_per_cta) {
+  if (!c || !r) return fail(c, CCS_ERR_INVALID_ARG, "bad arguments");
+  if (cliff_threads) *cliff_threads = r->cliff_threads;
+  if (words_per_op) *words_per_op = r->cliff_words;
+  if (shots_per_cta) *shots_per_cta = r->sample_spc;
   return CCS_OK;
 }
 
@@ -519,6 +703,8 @@ int ccs_eval_variants(ccs_ctx c, ccs_plan p, const ccs_eval_opts* opts, ccs_res*
   if (!c || !p || !opts || !res) return fail(c, CCS_ERR_INVALID_ARG, "bad arguments");
   if (opts->mode != CCS_EXACT && opts->mode != CCS_SAMPLED) return fail(c, CCS_ERR_INVALID_ARG, "bad mode");
   if (opts->mode == CCS_SAMPLED && opts->shots == 0) return fail(c, CCS_ERR_INVALID_ARG, "zero shots");
+  if (opts->mode == CCS_SAMPLED && opts->shots > 0xffffu && p->max_hub_nA > 15)
+    return fail(c, CCS_ERR_UNSUPPORTED, "more than 65535 shots with a 16-bit hub outcome space");
   if (c->host_only) return fail(c, CCS_ERR_UNSUPPORTED, "host-only context cannot evaluate");
   cudaSetDevice(c->device);
   ccs_res r = *res;
@@ -532,14 +718,27 @@ int ccs_eval_variants(ccs_ctx c, ccs_plan p, const ccs_eval_opts* opts, ccs_res*
     d.dist = r->A.get<float>(std::max<long long>(p->n_dist, 1));
     d.zval = r->A.get<float>(std::max<long long>(p->n_zval, 1));
     d.T = r->A.get<float>(std::max<long long>(p->n_T, 1));
+    d.TQ = r->A.get<float>(std::max<long long>(p->n_T, 1));
     d.TZ = r->A.get<float>(std::max<long long>(p->n_TZ, 1));
     d.marg = r->A.get<double>(std::max<long long>(p->n_marg, 1));
     d.zexp = r->A.get<double>(std::max<long long>(p->n_zexp, 1));
     d.work = r->A.get<unsigned>(4);
     d.status = r->A.get<unsigned>(4);
     r->scratch = r->A.get<float>(std::max<long long>(p->r_total + p->part_total, 1));
-    if (!d.spaces || !d.dist || !d.zval || !d.T || !d.TZ || !d.marg || !d.zexp || !d.work || !d.status ||
-        !r->scratch) {
+    {   // default launch shape before any tuning: wide tableaus take 8 words per op, 512 threads
+      int max_n = 0;
+      for (auto& f : p->fdev)
+        if (f.clifford) max_n = std::max(max_n, f.n);
+      const int W = 2 * ((max_n + 63) / 64);
+      r->cliff_words = W >= 16 ? 8 : W >= 8 ? 4 : 1;
+      r->cliff_threads = max_n > 256 ? 512 : 256;
+    }
+    if (p->rt_total) {
+      d.TQh = r->A.get<uint16_t>(p->n_T);
+      r->rt_scratch = r->A.get<uint16_t>(p->rt_total);
+    }
+    if (!d.spaces || !d.dist || !d.zval || !d.T || !d.TQ || !d.TZ || !d.marg || !d.zexp || !d.work || !d.status ||
+        !r->scratch || (p->rt_total && (!d.TQh || !r->rt_scratch))) {
       delete r;
       return fail(c, CCS_ERR_OOM, "result allocation failed");
     }
@@ -564,6 +763,13 @@ int ccs_eval_variants(ccs_ctx c, ccs_plan p, const ccs_eval_opts* opts, ccs_res*
   e.keep_tableaus = opts->keep_tableaus && r->have_tabs;
   e.inv_shots = e.shots ? 1.0 / (double)e.shots : 0.0;
   r->ep = e;
+  if (opts->autotune && !r->graph) {
+    const bool prof = c->profiling;
+    c->profiling = false;
+    int rc = autotune(c, p, r);
+    c->profiling = prof;
+    if (rc != CCS_OK) return rc;
+  }
   if (!opts->use_graph || c->profiling) {
     c->stage_mask = 0;
     return enqueue_eval(c, p, r);
@@ -622,7 +828,8 @@ int ccs_recombine(ccs_ctx c, ccs_plan p, ccs_res r, const ccs_recomb_opts* opts,
   cudaSetDevice(c->device);
   stage_begin(c, ST_RECOMB);
   RecombSizes rz{p->r_total, p->part_total, p->gemm_blocks, p->n_marg, p->n_zexp,
-                 p->d_r_prefix, p->d_blk_prefix, p->d_out_prefix, p->d_z_prefix, p->max_tile_smem};
+                 p->d_r_prefix, p->d_blk_prefix, p->d_out_prefix, p->d_z_prefix, p->max_tile_smem,
+                 (opts && opts->no_tensor_cores) ? nullptr : p->pdev.data(), (int)p->pdev.size(), r->rt_scratch};
   cudaError_t e = launch_recombine(p->dp, r->dr, prec, rz, r->scratch, r->dr.marg, r->dr.zexp, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "recombine kernel");
   stage_end(c, ST_RECOMB);
@@ -741,6 +948,7 @@ int ccs_get_counts(ccs_ctx c, ccs_res r, int problem, int fragment, int variant,
   int rc = locate(c, r, problem, fragment, variant, &d);
   if (rc) return rc;
   if (!d->clifford || r->ep.mode != CCS_SAMPLED || variant < 0) return fail(c, CCS_ERR_INVALID_ARG, "no counts");
+  if (d->role == 1 && !r->ep.keep_tableaus) return fail(c, CCS_ERR_INVALID_ARG, "hub counts are kept only with keep_tableaus");
   cudaError_t e = cudaMemcpy(out, r->dr.counts + d->counts_off + ((long long)variant << d->nA),
                              sizeof(uint32_t) << d->nA, cudaMemcpyDeviceToHost);
   return e == cudaSuccess ? CCS_OK : cuda_fail(c, e, "copy counts");
@@ -756,11 +964,39 @@ int ccs_get_dist(ccs_ctx c, ccs_res r, int problem, int fragment, int variant, f
   return e == cudaSuccess ? CCS_OK : cuda_fail(c, e, "copy dist");
 }
 
+int ccs_get_operand(ccs_ctx c, ccs_res r, int problem, int fragment, float* out) {
+  const FragDev* d;
+  int rc = locate(c, r, problem, fragment, -1, &d);
+  if (rc) return rc;
+  if (d->role == 0) return fail(c, CCS_ERR_INVALID_ARG, "not part of a star contraction");
+  const long long cnt = (1ll << d->m) << (2 * d->n_slots);
+  cudaError_t e = cudaMemcpy(out, r->dr.TQ + d->T_off, cnt * sizeof(float), cudaMemcpyDeviceToHost);
+  return e == cudaSuccess ? CCS_OK : cuda_fail(c, e, "copy operand");
+}
+
 int ccs_get_tensor(ccs_ctx c, ccs_res r, int problem, int fragment, float* out) {
   const FragDev* d;
   int rc = locate(c, r, problem, fragment, -1, &d);
   if (rc) return rc;
   const long long cnt = (1ll << d->m) << (2 * d->n_slots);
+  if (d->role == 1 && d->clifford && r->ep.mode == CCS_SAMPLED && !r->ep.keep_tableaus)
+    return fail(c, CCS_ERR_INVALID_ARG, "a sampled hub's tensor needs its counts (keep_tableaus)");
+  if (d->role == 1) {   // a hub's T is not formed on the hot path: fold it now
+    const int g = (int)(d - r->plan->fdev.data());
+    std::vector<int> fi{g};
+    std::vector<long long> tp{0, cnt}, tz{0, 0};
+    Allocs tmp;
+    tmp.ctx = c;
+    int* dfi; long long *dtp, *dtz;
+    if (!upload(c, tmp, fi, &dfi) || !upload(c, tmp, tp, &dtp) || !upload(c, tmp, tz, &dtz)) {
+      tmp.release();
+      return fail(c, CCS_ERR_OOM, "tensor fold buffers");
+    }
+    cudaError_t e2 = launch_fold(r->plan->dp, r->dr, r->ep, FoldSet{dfi, dtp, dtz, 1, cnt, 0}, c->stream);
+    if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(c->stream);
+    tmp.release();
+    if (e2 != cudaSuccess) return cuda_fail(c, e2, "tensor fold");
+  }
   cudaError_t e = cudaMemcpy(out, r->dr.T + d->T_off, cnt * sizeof(float), cudaMemcpyDeviceToHost);
   return e == cudaSuccess ? CCS_OK : cuda_fail(c, e, "copy tensor");
 }
@@ -803,7 +1039,8 @@ extern "C" int ccs_recombine_noalloc(ccs_ctx c, ccs_plan p, ccs_res r, int preci
     g_noalloc_addr[c->device] = ptr;
   }
   RecombSizes rz{p->r_total, p->part_total, p->gemm_blocks, p->n_marg, p->n_zexp,
-                 p->d_r_prefix, p->d_blk_prefix, p->d_out_prefix, p->d_z_prefix, p->max_tile_smem};
+                 p->d_r_prefix, p->d_blk_prefix, p->d_out_prefix, p->d_z_prefix, p->max_tile_smem,
+                 nullptr, 0, nullptr};
   e = launch_recombine(p->dp, r->dr, precision, rz, g_noalloc_addr[c->device], marginal_out, zexp_out, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "recombine kernel");
   return CCS_OK;

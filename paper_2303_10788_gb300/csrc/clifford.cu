@@ -9,6 +9,8 @@
 // [0, Wh), stabilizer rows in words [Wh, 2Wh), so destabilizer i and
 // stabilizer i share a bit position.  A gate therefore touches whole 64-row
 // words of a few columns (Gottesman-Knill / CHP, Sec. II-C and III-B).
+#include <cuda_bf16.h>
+
 #include "kernels.cuh"
 
 namespace ccs {
@@ -19,30 +21,32 @@ namespace {
 
 __device__ __forceinline__ uint64_t bm(unsigned v, int bit) { return 0ull - (uint64_t)((v >> bit) & 1u); }
 
-// Apply one fused Clifford op to word w of its four columns.
-__device__ __forceinline__ void apply_op(CliffordOp op, uint64_t* tab, int W, int zb, int w,
-                                         uint64_t& rdelta) {
-  uint64_t* pxa = tab + (size_t)op.qa * W + w;
-  uint64_t* pza = tab + (size_t)(zb + op.qa) * W + w;
-  uint64_t* pxb = tab + (size_t)op.qb * W + w;
-  uint64_t* pzb = tab + (size_t)(zb + op.qb) * W + w;
-  const uint64_t v0 = *pxa, v1 = *pza, v2 = *pxb, v3 = *pzb;
+// Apply one fused Clifford op to G consecutive words starting at w0 (words
+// >= W are skipped): the op's 31 bit masks are expanded once for all G.
+template <int G>
+__device__ __forceinline__ void apply_op_g(CliffordOp op, uint64_t* tab, int W, int zb, int w0, uint64_t (&rd)[G]) {
   const unsigned M = op.M, A = op.anf;
-  const uint64_t u0 = (v0 & bm(M, 0)) ^ (v1 & bm(M, 1)) ^ (v2 & bm(M, 2)) ^ (v3 & bm(M, 3));
-  const uint64_t u1 = (v0 & bm(M, 4)) ^ (v1 & bm(M, 5)) ^ (v2 & bm(M, 6)) ^ (v3 & bm(M, 7));
-  const uint64_t u2 = (v0 & bm(M, 8)) ^ (v1 & bm(M, 9)) ^ (v2 & bm(M, 10)) ^ (v3 & bm(M, 11));
-  const uint64_t u3 = (v0 & bm(M, 12)) ^ (v1 & bm(M, 13)) ^ (v2 & bm(M, 14)) ^ (v3 & bm(M, 15));
-  const uint64_t v01 = v0 & v1, v23 = v2 & v3;
-  uint64_t f = (v0 & bm(A, 1)) ^ (v1 & bm(A, 2)) ^ (v01 & bm(A, 3)) ^ (v2 & bm(A, 4)) ^
-               ((v0 & v2) & bm(A, 5)) ^ ((v1 & v2) & bm(A, 6)) ^ ((v01 & v2) & bm(A, 7)) ^
-               (v3 & bm(A, 8)) ^ ((v0 & v3) & bm(A, 9)) ^ ((v1 & v3) & bm(A, 10)) ^
-               ((v01 & v3) & bm(A, 11)) ^ (v23 & bm(A, 12)) ^ ((v0 & v23) & bm(A, 13)) ^
-               ((v1 & v23) & bm(A, 14)) ^ ((v01 & v23) & bm(A, 15));
-  rdelta ^= f;
-  *pxa = u0;
-  *pza = u1;
-  *pxb = u2;
-  *pzb = u3;
+  uint64_t m[16], a[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) { m[i] = bm(M, i); a[i] = bm(A, i); }
+  uint64_t* pxa = tab + (size_t)op.qa * W;
+  uint64_t* pza = tab + (size_t)(zb + op.qa) * W;
+  uint64_t* pxb = tab + (size_t)op.qb * W;
+  uint64_t* pzb = tab + (size_t)(zb + op.qb) * W;
+#pragma unroll
+  for (int k = 0; k < G; ++k) {
+    const int w = w0 + k;
+    if (G > 1 && w >= W) break;
+    const uint64_t v0 = pxa[w], v1 = pza[w], v2 = pxb[w], v3 = pzb[w];
+    const uint64_t v01 = v0 & v1, v23 = v2 & v3;
+    rd[k] ^= (v0 & a[1]) ^ (v1 & a[2]) ^ (v01 & a[3]) ^ (v2 & a[4]) ^ ((v0 & v2) & a[5]) ^ ((v1 & v2) & a[6]) ^
+             ((v01 & v2) & a[7]) ^ (v3 & a[8]) ^ ((v0 & v3) & a[9]) ^ ((v1 & v3) & a[10]) ^ ((v01 & v3) & a[11]) ^
+             (v23 & a[12]) ^ ((v0 & v23) & a[13]) ^ ((v1 & v23) & a[14]) ^ ((v01 & v23) & a[15]);
+    pxa[w] = (v0 & m[0]) ^ (v1 & m[1]) ^ (v2 & m[2]) ^ (v3 & m[3]);
+    pza[w] = (v0 & m[4]) ^ (v1 & m[5]) ^ (v2 & m[6]) ^ (v3 & m[7]);
+    pxb[w] = (v0 & m[8]) ^ (v1 & m[9]) ^ (v2 & m[10]) ^ (v3 & m[11]);
+    pzb[w] = (v0 & m[12]) ^ (v1 & m[13]) ^ (v2 & m[14]) ^ (v3 & m[15]);
+  }
 }
 
 // XOR of the bits strictly below each position.
@@ -118,9 +122,12 @@ __device__ __forceinline__ int variant_out_digit(int v, int qin, int i) {
 
 }  // namespace
 
-__global__ void __launch_bounds__(512) clifford_kernel(DevPlan P, DevRes R, EvalParams E) {
+// G = words of one op per thread (the op's masks are expanded once per G).
+template <int G>
+__global__ void __launch_bounds__(512) clifford_kernel(DevPlan P, DevRes R, EvalParams E, int smem_words) {
   extern __shared__ unsigned long long smem_u64[];
   uint64_t* tab = reinterpret_cast<uint64_t*>(smem_u64);
+  __shared__ FragDev sF;
   __shared__ int s_item;
   __shared__ int s_rank;
   __shared__ uint32_t s_off;
@@ -141,11 +148,30 @@ __global__ void __launch_bounds__(512) clifford_kernel(DevPlan P, DevRes R, Eval
     __syncthreads();
     if (item >= P.n_items_cliff) break;
     const int2 it = P.items_cliff[item];
-    const FragDev& F = P.frags[it.x];
+    {   // the fragment record, once per item, into shared memory
+      const int* src = reinterpret_cast<const int*>(P.frags + it.x);
+      int* dst = reinterpret_cast<int*>(&sF);
+      for (int i = tid; i < (int)(sizeof(FragDev) / 4); i += nt) dst[i] = src[i];
+    }
+    __syncthreads();
+    const FragDev& F = sF;
     const int v = it.y;
     const int n = F.n, W = F.W, Wh = F.Wh, zb = n + 1, rcol = 2 * (n + 1);
     const int ncol = 2 * n + 3;
     uint32_t* rows = reinterpret_cast<uint32_t*>(tab + (size_t)ncol * W);
+    // op stream and moment offsets staged after the tableau when they fit
+    const int base_words = ncol * W + (n + 1) / 2 + 2;
+    const int n_ops = P.moments[F.mom_off + F.n_moments];
+    const bool staged = base_words + n_ops + (F.n_moments + 2) / 2 + 2 <= smem_words;
+    CliffordOp* ops_s = reinterpret_cast<CliffordOp*>(tab + base_words);
+    int* mom_s = reinterpret_cast<int*>(tab + base_words + n_ops);
+    const CliffordOp* ops = staged ? ops_s : P.cops + F.ops_off;
+    const int* mom = staged ? mom_s : P.moments + F.mom_off;
+    if (staged) {
+      const unsigned long long* src = reinterpret_cast<const unsigned long long*>(P.cops + F.ops_off);
+      for (int i = tid; i < n_ops; i += nt) reinterpret_cast<unsigned long long*>(ops_s)[i] = src[i];
+      for (int i = tid; i <= F.n_moments; i += nt) mom_s[i] = P.moments[F.mom_off + i];
+    }
 
     // --- K1: initial tableau (destabilizer i = X_i, stabilizer i = Z_i) ---
     for (int i = tid; i < ncol * W; i += nt) tab[i] = 0ull;
@@ -156,23 +182,26 @@ __global__ void __launch_bounds__(512) clifford_kernel(DevPlan P, DevRes R, Eval
     }
     __syncthreads();
 
-    const int J = nt / W;                  // op slots per word
-    const int w = tid % W, jslot = tid / W;
+    const int ngrp = (W + G - 1) / G;       // word groups of G words
+    const int J = nt / ngrp;                 // op slots per word group
+    const int w0 = (tid % ngrp) * G, jslot = tid / ngrp;
     const bool active = jslot < J;
-    uint64_t rdelta = 0;
+    uint64_t rd[G];
+#pragma unroll
+    for (int k = 0; k < G; ++k) rd[k] = 0;
     if (active) {                          // preparations at quantum inputs
       for (int o = jslot; o < F.qin; o += J) {
         CliffordOp op = P.prep_ops[variant_in_digit(v, o)];
         op.qa = (uint16_t)P.wires[F.qin_off + o];
         op.qb = (uint16_t)n;
-        apply_op(op, tab, W, zb, w, rdelta);
+        apply_op_g<G>(op, tab, W, zb, w0, rd);
       }
     }
     __syncthreads();
     for (int mm = 0; mm < F.n_moments; ++mm) {
-      const int b0 = P.moments[F.mom_off + mm], b1 = P.moments[F.mom_off + mm + 1];
+      const int b0 = mom[mm], b1 = mom[mm + 1];
       if (active)
-        for (int o = b0 + jslot; o < b1; o += J) apply_op(P.cops[F.ops_off + o], tab, W, zb, w, rdelta);
+        for (int o = b0 + jslot; o < b1; o += J) apply_op_g<G>(ops[o], tab, W, zb, w0, rd);
       __syncthreads();
     }
     if (active) {                          // basis changes at quantum outputs
@@ -180,10 +209,13 @@ __global__ void __launch_bounds__(512) clifford_kernel(DevPlan P, DevRes R, Eval
         CliffordOp op = P.basis_ops[variant_out_digit(v, F.qin, o)];
         op.qa = (uint16_t)P.wires[F.qout_off + o];
         op.qb = (uint16_t)n;
-        apply_op(op, tab, W, zb, w, rdelta);
+        apply_op_g<G>(op, tab, W, zb, w0, rd);
       }
-      atomicXor(reinterpret_cast<unsigned long long*>(&tab[(size_t)rcol * W + w]),
-                (unsigned long long)rdelta);
+#pragma unroll
+      for (int k = 0; k < G; ++k)
+        if (w0 + k < W)
+          atomicXor(reinterpret_cast<unsigned long long*>(&tab[(size_t)rcol * W + w0 + k]),
+                    (unsigned long long)rd[k]);
     }
     __syncthreads();
 
@@ -315,12 +347,12 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 
 constexpr int kHistSmem = 8192;   // dense per-CTA histogram up to |A| = 13
 
-__global__ void __launch_bounds__(256) sample_kernel(DevPlan P, DevRes R, EvalParams E, int spc,
+__global__ void __launch_bounds__(256) sample_kernel(DevPlan P, DevRes R, EvalParams E, const int2* items, int spc,
                                                      int chunks) {
   __shared__ uint32_t tbl[3][256];
   __shared__ uint32_t hist[kHistSmem];
   const int item = blockIdx.x / chunks, chunk = blockIdx.x % chunks;
-  const int2 it = P.items_cliff[item];
+  const int2 it = items[item];
   const FragDev& F = P.frags[it.x];
   const int v = it.y;
   const SpaceRec& sp = R.spaces[F.space_off + v];
@@ -357,24 +389,143 @@ __global__ void __launch_bounds__(256) sample_kernel(DevPlan P, DevRes R, EvalPa
   }
 }
 
-cudaError_t launch_clifford(const DevPlan& p, const DevRes& r, const EvalParams& e, int threads,
-                            int smem_words, int grid, cudaStream_t s) {
-  if (p.n_items_cliff == 0) return cudaSuccess;
-  const size_t smem = (size_t)smem_words * 8;
-  cudaError_t err = cudaFuncSetAttribute(clifford_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+// --- K3 + K5 fused for the hub of a star --------------------------------
+// One CTA per hub variant: all its shots into a shared-memory histogram
+// (16-bit counters packed in pairs, so |A| <= 16 fits 128 KB), then the
+// variant's slice of the hub operand
+//   Q[o, (s, P_out)] = sum_b prod_j lambda(P_out_j, b_j) count(o, b) / shots
+// for every P_out with beta(P_out) = the variant's bases.  Dense counts are
+// written only when kept for inspection.
+__global__ void __launch_bounds__(512) sample_hub_kernel(DevPlan P, DevRes R, EvalParams E, const int2* items,
+                                                         int keep_counts, int wide) {
+  extern __shared__ uint32_t hist2[];
+  __shared__ uint32_t tbl[3][256];
+  __shared__ FragDev sF;
+  const int2 it = items[blockIdx.x];
+  {
+    const int* src = reinterpret_cast<const int*>(P.frags + it.x);
+    int* dst = reinterpret_cast<int*>(&sF);
+    for (int i = threadIdx.x; i < (int)(sizeof(FragDev) / 4); i += blockDim.x) dst[i] = src[i];
+  }
+  __syncthreads();
+  const FragDev& F = sF;
+  const int v = it.y, nA = F.nA;
+  const SpaceRec& sp = R.spaces[F.space_off + v];
+  const int rank = sp.rank;
+  const uint32_t off = sp.off;
+  for (int t = threadIdx.x; t < 3 * 256; t += blockDim.x) {
+    const int k = t >> 8, byte = t & 255;
+    uint32_t acc = 0;
+    for (int b = 0; b < 8; ++b) {
+      const int j = 8 * k + b;
+      if (j < rank && ((byte >> b) & 1)) acc ^= sp.basis[j];
+    }
+    tbl[k][byte] = acc;
+  }
+  const int nwords = wide ? (1 << nA) : ((1 << nA) > 1 ? (1 << (nA - 1)) : 1);
+  for (int i = threadIdx.x; i < nwords; i += blockDim.x) hist2[i] = 0u;
+  __syncthreads();
+  const uint32_t cmask = rank >= 32 ? 0xffffffffu : ((1u << rank) - 1u);
+  for (uint32_t s = threadIdx.x; s < E.shots; s += blockDim.x) {
+    const uint4 o = philox4x32_10(make_uint4(s, (uint32_t)v, (uint32_t)F.findex, (uint32_t)F.problem),
+                                  E.seed_lo, E.seed_hi);
+    const uint32_t c = o.x & cmask;
+    const uint32_t y = off ^ tbl[0][c & 255] ^ tbl[1][(c >> 8) & 255] ^ tbl[2][(c >> 16) & 255];
+    if (wide) atomicAdd(&hist2[y], 1u);
+    else atomicAdd(&hist2[y >> 1], 1u << ((y & 1u) << 4));
+  }
+  __syncthreads();
+  auto count = [&](uint32_t y) -> uint32_t {
+    return wide ? hist2[y] : (hist2[y >> 1] >> ((y & 1u) << 4)) & 0xffffu;
+  };
+  if (keep_counts) {
+    uint32_t* g = R.counts + F.counts_off + ((long long)v << nA);
+    for (uint32_t y = threadIdx.x; y < (1u << nA); y += blockDim.x) g[y] = count(y);
+  }
+  // the variant's digits: preparations at input slots, bases at output slots
+  int beta[kMaxCuts];
+  {
+    int t = v;
+    for (int i = 0; i < F.qin; ++i) t /= 4;
+    for (int j = 0; j < F.qout; ++j) { beta[j] = t % 3; t /= 3; }
+  }
+  int zpos[kMaxCuts], nz = 0;
+  int Dbase = 0;
+  for (int j = 0; j < F.n_slots; ++j) {
+    const int code = F.slot_code[j], idx = code & 255;
+    if ((code >> 8) == 0) {
+      int t = v;
+      for (int i = 0; i < idx; ++i) t /= 4;
+      Dbase |= (t % 4) << (2 * j);
+    } else if (beta[idx] == 2) {
+      zpos[nz++] = j;                         // Z basis: P_out in {I, Z}
+    } else {
+      Dbase |= (beta[idx] == 0 ? 1 : 2) << (2 * j);   // X basis -> X, Y basis -> Y
+    }
+  }
+  const int m = F.m, S2 = 2 * F.n_slots;
+  const double inv = E.inv_shots;
+  const int n_items = (1 << m) << nz;
+  for (int t = threadIdx.x; t < n_items; t += blockDim.x) {
+    const int o = t >> nz, cz = t & ((1 << nz) - 1);
+    int D = Dbase, smask = 0;   // smask: quantum outputs whose outcome flips the sign
+    for (int i = 0; i < nz; ++i)
+      if ((cz >> i) & 1) D |= 3 << (2 * zpos[i]);
+    for (int j = 0; j < F.n_slots; ++j) {
+      const int code = F.slot_code[j];
+      if ((code >> 8) == 1 && ((D >> (2 * j)) & 3) != 0) smask |= 1 << (code & 255);
+    }
+    long long acc = 0;
+    for (int b = 0; b < (1 << F.qout); ++b) {
+      const long long cnt = count((uint32_t)o | ((uint32_t)b << m));
+      acc += (__popc(b & smask) & 1) ? -cnt : cnt;
+    }
+    const float qv = (float)((double)acc * inv);
+    R.TQ[F.T_off + ((long long)o << S2) + D] = qv;
+    if (R.TQh) reinterpret_cast<__nv_bfloat16*>(R.TQh)[F.T_off + ((long long)o << S2) + D] = __float2bfloat16_rn(qv);
+  }
+}
+
+cudaError_t launch_sample_hub(const DevPlan& p, const DevRes& r, const EvalParams& e, const int2* items, int n_items,
+                              int max_nA, int keep_counts, cudaStream_t s) {
+  if (n_items == 0 || e.shots == 0) return cudaSuccess;
+  const int wide = e.shots > 0xffffu ? 1 : 0;     // 32-bit counters when 16 bits could overflow
+  const size_t smem = (size_t)4 * (wide ? (1 << max_nA) : ((1 << max_nA) > 1 ? (1 << (max_nA - 1)) : 1));
+  cudaError_t err = cudaFuncSetAttribute(sample_hub_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  clifford_kernel<<<grid, threads, smem, s>>>(p, r, e);
+  sample_hub_kernel<<<n_items, 512, smem, s>>>(p, r, e, items, keep_counts, wide);
   return cudaGetLastError();
 }
 
-cudaError_t launch_sample(const DevPlan& p, const DevRes& r, const EvalParams& e, int spc, int threads,
-                          cudaStream_t s) {
-  if (p.n_items_cliff == 0 || e.shots == 0) return cudaSuccess;
+template <int G>
+static cudaError_t launch_clifford_g(const DevPlan& p, const DevRes& r, const EvalParams& e, int threads,
+                                     int smem_words, int grid, cudaStream_t s) {
+  const size_t smem = (size_t)smem_words * 8;
+  cudaError_t err = cudaFuncSetAttribute(clifford_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+  if (err != cudaSuccess) return err;
+  clifford_kernel<G><<<grid, threads, smem, s>>>(p, r, e, smem_words);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_clifford(const DevPlan& p, const DevRes& r, const EvalParams& e, int threads, int words_per_op,
+                            int smem_words, int grid, cudaStream_t s) {
+  if (p.n_items_cliff == 0) return cudaSuccess;
+  switch (words_per_op) {
+    case 8: return launch_clifford_g<8>(p, r, e, threads, smem_words, grid, s);
+    case 4: return launch_clifford_g<4>(p, r, e, threads, smem_words, grid, s);
+    case 2: return launch_clifford_g<2>(p, r, e, threads, smem_words, grid, s);
+    default: return launch_clifford_g<1>(p, r, e, threads, smem_words, grid, s);
+  }
+}
+
+cudaError_t launch_sample(const DevPlan& p, const DevRes& r, const EvalParams& e, const int2* items, int n_items,
+                          int spc, int threads, cudaStream_t s) {
+  if (n_items == 0 || e.shots == 0) return cudaSuccess;
   const int chunks = (int)((e.shots + spc - 1) / spc);
-  const long long grid = (long long)p.n_items_cliff * chunks;
+  const long long grid = (long long)n_items * chunks;
   if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-  sample_kernel<<<(unsigned)grid, threads, 0, s>>>(p, r, e, spc, chunks);
+  sample_kernel<<<(unsigned)grid, threads, 0, s>>>(p, r, e, items, spc, chunks);
   return cudaGetLastError();
 }
 

@@ -26,7 +26,8 @@ struct FragDev {
   long long dist_off;      // float index of variant 0 (2^nA each)
   long long zval_off;      // float index of variant 0 (nz * 2^qout each)
   long long tab_off;       // uint64 index of variant 0 ((2n+3)*W each), -1 if not kept
-  long long T_off;         // float index of T_f (2^m x 4^n_slots)
+  long long T_off;         // float index of T_f (2^m x 4^n_slots); also indexes TQ
+  int role;                // 0 plain, 1 hub of a star (TQ = Q), 2 other fragment of a star (TQ = T')
   long long TZ_off;        // float index of T_f^S (nz x 4^n_slots)
 };
 
@@ -49,8 +50,11 @@ struct ProblemDev {
   int TM, TN, mtiles, ntiles;
   long long K;             // 4^k
   long long r_off;         // float index of R (K x N) in the scratch
-  long long part_off;      // float index of the split-K partials (splits x M x N)
+  long long part_off;      // float index of the split-K partials (splits x M x N), after all R
   long long blk_off;       // first GEMM block of this problem
+  long long rt_off;        // bf16 index of R'^T (N x K) in the bf16 scratch (tensor-core path)
+  long long hub_T_off;     // T_off of the hub
+  int tc;                  // 1: eligible for the tensor-core GEMM in BF16 mode
 };
 
 // Device views of a plan + result.
@@ -79,6 +83,8 @@ struct DevRes {
   float* zval;
   unsigned long long* tabs;
   float* T;
+  float* TQ;               // contraction operands: Q for hubs, T' for the other fragments
+  uint16_t* TQh;           // bf16 copy of the hubs' Q (tensor-core path), may be null
   float* TZ;
   double* marg;
   double* zexp;
@@ -94,15 +100,32 @@ struct EvalParams {
 };
 
 // Kernel launchers (stream-ordered; return cudaError_t of the launch).
+// words_per_op: 64-row words of one fused op a thread updates (1, 2, 4 or 8)
 cudaError_t launch_clifford(const DevPlan& p, const DevRes& r, const EvalParams& e,
-                            int threads, int smem_words, int grid, cudaStream_t s);
-cudaError_t launch_sample(const DevPlan& p, const DevRes& r, const EvalParams& e,
-                          int shots_per_cta, int threads, cudaStream_t s);
+                            int threads, int words_per_op, int smem_words, int grid, cudaStream_t s);
+cudaError_t launch_sample(const DevPlan& p, const DevRes& r, const EvalParams& e, const int2* items,
+                          int n_items, int shots_per_cta, int threads, cudaStream_t s);
+// Sampling + output fold of star hubs (one CTA per hub variant); writes the
+// hub's contraction operand Q into TQ, and dense counts if keep_counts.
+cudaError_t launch_sample_hub(const DevPlan& p, const DevRes& r, const EvalParams& e, const int2* items,
+                              int n_items, int max_nA, int keep_counts, cudaStream_t s);
 cudaError_t launch_statevector(const DevPlan& p, const DevRes& r, int max_n, int threads,
                                int grid, cudaStream_t s);
-cudaError_t launch_fold(const DevPlan& p, const DevRes& r, const EvalParams& e,
-                        const long long* t_prefix, int n_frags_total, long long total,
-                        const long long* tz_prefix, long long total_z, cudaStream_t s);
+// A subset of fragments to fold: fidx[i] is the FragDev index of segment i;
+// t_prefix / tz_prefix (nf + 1 entries) count T_f and T_f^S entries.
+struct FoldSet {
+  const int* fidx;
+  const long long* t_prefix;
+  const long long* tz_prefix;
+  int nf;
+  long long total, total_z;
+};
+cudaError_t launch_fold(const DevPlan& p, const DevRes& r, const EvalParams& e, const FoldSet& f,
+                        cudaStream_t s);
+// Contraction operands of star problems: Q of each hub from its variant data
+// (set `hubs`) and T' of every other fragment from its T (set `others`).
+cudaError_t launch_operands(const DevPlan& p, const DevRes& r, const EvalParams& e, const FoldSet& hubs,
+                            const FoldSet& others, cudaStream_t s);
 // Recombination of every star problem: R build, split-K GEMM, FP64 reduce
 // and scatter into marg_out (2^n_marg doubles per problem at marg_off), and
 // the Z-string contraction into zexp_out.  `scratch` holds R and the split-K
@@ -114,8 +137,16 @@ struct RecombSizes {
   const long long* out_prefix;   // per problem, M*N outputs
   const long long* z_prefix;     // per problem, Z-strings
   int max_tile_smem;             // bytes of dynamic shared memory per GEMM block
+  // tensor-core path (BF16 only; null host list disables it)
+  const ProblemDev* host_problems;
+  int n_problems;
+  uint16_t* rt_scratch;          // bf16 R'^T of eligible problems
 };
 cudaError_t launch_recombine(const DevPlan& p, const DevRes& r, int precision, const RecombSizes& z,
                              float* scratch, double* marg_out, double* zexp_out, cudaStream_t s);
+// tcgen05 GEMM (gemm_tc.cu): partials[split][m][n] of A (M x K) x Bt^T (Bt: N x K), bf16
+bool gemm_tc_supported(int M, int N, long long K);
+cudaError_t launch_gemm_tc(const void* A, const void* Bt, int M, int N, long long K, int splits, float* partials,
+                           unsigned* status, cudaStream_t s);
 
 }  // namespace ccs

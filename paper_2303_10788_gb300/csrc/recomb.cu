@@ -73,13 +73,13 @@ __device__ __forceinline__ float to_bf16f(float x) { return __bfloat162float(__f
 
 }  // namespace
 
-__global__ void fold_kernel(DevPlan P, DevRes R, EvalParams E, const long long* prefix, int nf,
-                            long long total) {
+__global__ void fold_kernel(DevPlan P, DevRes R, EvalParams E, const int* fidx, const long long* prefix,
+                            int nf, long long total) {
   for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
        g += (long long)gridDim.x * blockDim.x) {
-    const int f = find_seg(prefix, nf, g);
-    const FragDev& F = P.frags[f];
-    const long long loc = g - prefix[f];
+    const int fs = find_seg(prefix, nf, g);
+    const FragDev& F = P.frags[fidx[fs]];
+    const long long loc = g - prefix[fs];
     const int S2 = 2 * F.n_slots;
     const int o = (int)(loc >> S2), Pi = (int)(loc & ((1ll << S2) - 1));
     PauliSplit ps;
@@ -110,12 +110,108 @@ __global__ void fold_kernel(DevPlan P, DevRes R, EvalParams E, const long long* 
   }
 }
 
-__global__ void fold_z_kernel(DevPlan P, DevRes R, const long long* prefix, int nf, long long total) {
+// Contraction operands.  Writing the hub's tensor through its preparations,
+//   T_h(o, P) = sum_s prod_{input cuts i} mu(P_i, s_i) Q_h(o, s, P_out),
+//   Q_h(o, s, P_out) = sum_b prod_j lambda(P_out_j, b_j) p_(s, beta(P_out))(o, b),
+// moves the mu weights onto the fragment upstream of each hub input cut:
+//   p(o) = 2^-k sum_{s, P_out} Q_h(o, s, P_out) prod_l T'_l,
+//   T'_l(o_l, ...) = sum over P at the cuts where l feeds the hub of
+//                    prod mu(P_i, s_i) T_l(o_l, P).
+// Q_h reads one variant per entry (no sum over preparations) and T'_l is
+// small, so the large hub tensor is never formed.
+__global__ void qfold_kernel(DevPlan P, DevRes R, EvalParams E, const int* fidx, const long long* prefix, int nf,
+                             long long total) {
   for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
        g += (long long)gridDim.x * blockDim.x) {
-    const int f = find_seg(prefix, nf, g);
-    const FragDev& F = P.frags[f];
-    const long long loc = g - prefix[f];
+    const int fs = find_seg(prefix, nf, g);
+    const FragDev& F = P.frags[fidx[fs]];
+    const long long loc = g - prefix[fs];
+    const int S2 = 2 * F.n_slots;
+    const int o = (int)(loc >> S2), D = (int)(loc & ((1ll << S2) - 1));
+    int pout[kMaxCuts];
+    long long vin = 0;
+    for (int j = 0; j < F.n_slots; ++j) {
+      const int d = (D >> (2 * j)) & 3, code = F.slot_code[j], idx = code & 255;
+      if ((code >> 8) == 0) vin += (long long)d << (2 * idx);
+      else pout[idx] = d;
+    }
+    long long vout = 0, mul = 1;
+    for (int j = 0; j < F.qout; ++j) {
+      vout += (pout[j] == 1 ? 0 : pout[j] == 2 ? 1 : 2) * mul;
+      mul *= 3;
+    }
+    const long long v = vin + (vout << (2 * F.qin));
+    const bool use_counts = F.clifford && E.mode == CCS_SAMPLED;
+    double acc = 0.0;
+    for (int b = 0; b < (1 << F.qout); ++b) {
+      int neg = 0;
+      for (int j = 0; j < F.qout; ++j) neg ^= (pout[j] != 0) & ((b >> j) & 1);
+      const long long y = (v << F.nA) | ((long long)b << F.m) | o;
+      const double val = use_counts ? (double)R.counts[F.counts_off + y] * E.inv_shots : (double)R.dist[F.dist_off + y];
+      acc += neg ? -val : val;
+    }
+    R.TQ[F.T_off + loc] = (float)acc;
+    if (R.TQh) reinterpret_cast<__nv_bfloat16*>(R.TQh)[F.T_off + loc] = __float2bfloat16_rn((float)acc);
+  }
+}
+
+__global__ void prime_kernel(DevPlan P, DevRes R, const int* fidx, const long long* prefix, int nf,
+                             long long total) {
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
+       g += (long long)gridDim.x * blockDim.x) {
+    const int fs = find_seg(prefix, nf, g);
+    const FragDev& F = P.frags[fidx[fs]];
+    const long long loc = g - prefix[fs];
+    const int S2 = 2 * F.n_slots;
+    const long long row = (loc >> S2) << S2;
+    const int D = (int)(loc & ((1ll << S2) - 1));
+    // slots where this fragment feeds the hub (its quantum outputs) carry a
+    // preparation digit s; expand each into the Paulis with mu(P, s) != 0
+    int outs[kMaxCuts], nout = 0, base = D;
+    for (int j = 0; j < F.n_slots; ++j)
+      if ((F.slot_code[j] >> 8) == 1) {
+        outs[nout++] = j;
+        base &= ~(3 << (2 * j));
+      }
+    int total_c = 1;
+    int cnt[kMaxCuts];
+    for (int t = 0; t < nout; ++t) {
+      const int sdig = (D >> (2 * outs[t])) & 3;
+      cnt[t] = sdig < 2 ? 4 : 1;
+      total_c *= cnt[t];
+    }
+    double acc = 0.0;
+    for (int c = 0; c < total_c; ++c) {
+      int rem = c, Pidx = base;
+      double coef = 1.0;
+      for (int t = 0; t < nout; ++t) {
+        const int sdig = (D >> (2 * outs[t])) & 3;
+        int pj;
+        double w;
+        if (sdig < 2) {
+          pj = rem % 4;
+          rem /= 4;
+          w = (pj == 0) ? 1.0 : (pj == 3) ? (sdig == 0 ? 1.0 : -1.0) : -1.0;   // I, X, Y, Z
+        } else {
+          pj = sdig == 2 ? 1 : 2;    // |+> -> X, |+i> -> Y, weight 2
+          w = 2.0;
+        }
+        Pidx |= pj << (2 * outs[t]);
+        coef *= w;
+      }
+      acc += coef * (double)R.T[F.T_off + row + Pidx];
+    }
+    R.TQ[F.T_off + loc] = (float)acc;
+  }
+}
+
+__global__ void fold_z_kernel(DevPlan P, DevRes R, const int* fidx, const long long* prefix, int nf,
+                              long long total) {
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
+       g += (long long)gridDim.x * blockDim.x) {
+    const int fs = find_seg(prefix, nf, g);
+    const FragDev& F = P.frags[fidx[fs]];
+    const long long loc = g - prefix[fs];
     const int S2 = 2 * F.n_slots;
     const int zi = (int)(loc >> S2), Pi = (int)(loc & ((1ll << S2) - 1));
     PauliSplit ps;
@@ -138,6 +234,25 @@ __global__ void fold_z_kernel(DevPlan P, DevRes R, const long long* prefix, int 
   }
 }
 
+cudaError_t launch_operands(const DevPlan& p, const DevRes& r, const EvalParams& e, const FoldSet& hubs,
+                            const FoldSet& others, cudaStream_t s) {
+  if (hubs.total > 0) {
+    const long long blocks = (hubs.total + 255) / 256;
+    qfold_kernel<<<(unsigned)(blocks < 65535 * 16 ? blocks : 65535 * 16), 256, 0, s>>>(p, r, e, hubs.fidx,
+                                                                                 hubs.t_prefix, hubs.nf,
+                                                                                 hubs.total);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+  }
+  if (others.total > 0) {
+    const long long blocks = (others.total + 255) / 256;
+    prime_kernel<<<(unsigned)(blocks < 65535 * 16 ? blocks : 65535 * 16), 256, 0, s>>>(p, r, others.fidx,
+                                                                                 others.t_prefix, others.nf,
+                                                                                 others.total);
+  }
+  return cudaGetLastError();
+}
+
 // --- contraction over the 4^k cut index ------------------------------------
 // For a star (hub h + leaves), p(o) = 2^-k sum_P T_h[o_h, P] R[P, o_l] with
 // R[P, o_l] = prod_leaves T_l[o_l|l, P|l] (leaf outputs concatenated in
@@ -149,7 +264,7 @@ __global__ void fold_z_kernel(DevPlan P, DevRes R, const long long* prefix, int 
 // accumulation.
 
 __global__ void build_r_kernel(DevPlan P, DevRes R, int precision, const long long* prefix, int np,
-                               long long total, float* scratch) {
+                               long long total, float* scratch, uint16_t* rt_scratch) {
   for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
        g += (long long)gridDim.x * blockDim.x) {
     const int pi = find_seg(prefix, np, g);
@@ -166,22 +281,28 @@ __global__ void build_r_kernel(DevPlan P, DevRes R, int precision, const long lo
       off += L.m;
       int pl = 0;
       for (int i = 0; i < L.n_slots; ++i) pl |= (int)((Pp >> (2 * L.slot_cut[i])) & 3) << (2 * i);
-      v *= R.T[L.T_off + ((long long)x << (2 * L.n_slots)) + pl];
+      v *= R.TQ[L.T_off + ((long long)x << (2 * L.n_slots)) + pl];
     }
     if (precision == CCS_BF16) v = to_bf16f(v);
     scratch[Pb.r_off + loc] = v;
+    if (precision == CCS_BF16 && Pb.tc && rt_scratch)   // R'^T for the tensor-core GEMM
+      reinterpret_cast<__nv_bfloat16*>(rt_scratch)[Pb.rt_off + ol * Pb.K + Pp] = __float2bfloat16_rn(v);
   }
 }
 
 constexpr int kTK = 16;
 
+// Split-K GEMM tile: TM x TN outputs (multiples of 4), one 4x4 register
+// micro-tile per thread, A staged k-major and B row-major in shared memory so
+// each k step is two float4 reads and 16 FMAs.
 __global__ void __launch_bounds__(256) gemm_splitk_kernel(DevPlan P, DevRes R, int precision,
                                                           const long long* blk_prefix, int np,
-                                                          long long total_blocks, float* scratch) {
-  extern __shared__ float sm[];
+                                                          long long total_blocks, float* scratch, int skip_tc) {
+  extern __shared__ __align__(16) float sm[];
   for (long long b = blockIdx.x; b < total_blocks; b += gridDim.x) {
     const int pi = find_seg(blk_prefix, np, b);
     const ProblemDev& Pb = P.problems[pi];
+    if (skip_tc && Pb.tc) continue;          // done by the tensor-core GEMM
     const FragDev& Hb = P.frags[Pb.frag0 + Pb.hub];
     long long loc = b - blk_prefix[pi];
     const int nt = (int)(loc % Pb.ntiles); loc /= Pb.ntiles;
@@ -191,19 +312,25 @@ __global__ void __launch_bounds__(256) gemm_splitk_kernel(DevPlan P, DevRes R, i
     const long long K = Pb.K;
     const long long kchunk = (K + Pb.splits - 1) / Pb.splits;
     const long long k0 = split * kchunk, k1 = k0 + kchunk < K ? k0 + kchunk : K;
-    float* As = sm;                          // TM x (kTK + 1)
-    float* Bs = sm + TM * (kTK + 1);         // kTK x TN
-    const float* A = R.T + Hb.T_off;         // M x K, row-major
+    float* As = sm;                  // kTK x TM
+    float* Bs = sm + kTK * TM;       // kTK x TN
+    const float* A = R.TQ + Hb.T_off;        // M x K, row-major (the hub's Q)
     const float* Bm = scratch + Pb.r_off;    // K x N, row-major
-    const int nout = TM * TN;
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    const int tn4 = TN >> 2;
+    const bool act = (int)threadIdx.x < (TM >> 2) * tn4;
+    const int mi = act ? ((int)threadIdx.x / tn4) * 4 : 0, ni = act ? ((int)threadIdx.x % tn4) * 4 : 0;
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
     for (long long kk = k0; kk < k1; kk += kTK) {
       for (int t = threadIdx.x; t < TM * kTK; t += blockDim.x) {
         const int m = t / kTK, k = t % kTK;
         const long long gm = (long long)mt * TM + m, gk = kk + k;
         float v = (gm < M && gk < k1) ? A[gm * K + gk] : 0.f;
         if (precision == CCS_BF16) v = to_bf16f(v);
-        As[m * (kTK + 1) + k] = v;
+        As[k * TM + m] = v;
       }
       for (int t = threadIdx.x; t < kTK * TN; t += blockDim.x) {
         const int k = t / TN, n = t % TN;
@@ -211,27 +338,28 @@ __global__ void __launch_bounds__(256) gemm_splitk_kernel(DevPlan P, DevRes R, i
         Bs[k * TN + n] = (gn < N && gk < k1) ? Bm[gk * N + gn] : 0.f;
       }
       __syncthreads();
+      if (act) {
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int o = threadIdx.x + 256 * j;
-        if (o < nout) {
-          const int m = o / TN, n = o % TN;
-          float a = acc[j];
+        for (int k = 0; k < kTK; ++k) {
+          const float4 av = *reinterpret_cast<const float4*>(As + k * TM + mi);
+          const float4 bv = *reinterpret_cast<const float4*>(Bs + k * TN + ni);
+          const float a4[4] = {av.x, av.y, av.z, av.w}, b4[4] = {bv.x, bv.y, bv.z, bv.w};
 #pragma unroll
-          for (int k = 0; k < kTK; ++k) a = fmaf(As[m * (kTK + 1) + k], Bs[k * TN + n], a);
-          acc[j] = a;
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a4[i], b4[j], acc[i][j]);
         }
       }
       __syncthreads();
     }
+    if (act) {
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int o = threadIdx.x + 256 * j;
-      if (o < nout) {
-        const int m = o / TN, n = o % TN;
-        const long long gm = (long long)mt * TM + m, gn = (long long)nt * TN + n;
-        if (gm < M && gn < N) scratch[Pb.part_off + ((long long)split * M + gm) * N + gn] = acc[j];
-      }
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const long long gm = (long long)mt * TM + mi + i, gn = (long long)nt * TN + ni + j;
+          if (gm < M && gn < N) scratch[Pb.part_off + ((long long)split * M + gm) * N + gn] = acc[i][j];
+        }
     }
   }
 }
@@ -292,18 +420,19 @@ __global__ void recombine_z_kernel(DevPlan P, DevRes R, const long long* prefix,
   }
 }
 
-cudaError_t launch_fold(const DevPlan& p, const DevRes& r, const EvalParams& e, const long long* t_prefix,
-                        int nf, long long total, const long long* tz_prefix, long long total_z,
+cudaError_t launch_fold(const DevPlan& p, const DevRes& r, const EvalParams& e, const FoldSet& f,
                         cudaStream_t s) {
-  if (total > 0) {
-    const long long blocks = (total + 255) / 256;
-    fold_kernel<<<(unsigned)(blocks < 65535 * 8 ? blocks : 65535 * 8), 256, 0, s>>>(p, r, e, t_prefix, nf, total);
+  if (f.total > 0) {
+    const long long blocks = (f.total + 255) / 256;
+    fold_kernel<<<(unsigned)(blocks < 65535 * 8 ? blocks : 65535 * 8), 256, 0, s>>>(p, r, e, f.fidx, f.t_prefix,
+                                                                              f.nf, f.total);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
   }
-  if (total_z > 0) {
-    const long long blocks = (total_z + 255) / 256;
-    fold_z_kernel<<<(unsigned)(blocks < 65535 * 8 ? blocks : 65535 * 8), 256, 0, s>>>(p, r, tz_prefix, nf, total_z);
+  if (f.total_z > 0) {
+    const long long blocks = (f.total_z + 255) / 256;
+    fold_z_kernel<<<(unsigned)(blocks < 65535 * 8 ? blocks : 65535 * 8), 256, 0, s>>>(p, r, f.fidx, f.tz_prefix,
+                                                                                f.nf, f.total_z);
   }
   return cudaGetLastError();
 }
@@ -316,16 +445,27 @@ cudaError_t launch_recombine(const DevPlan& p, const DevRes& r, int precision, c
   };
   cudaError_t err = cudaSuccess;
   if (z.out_total > 0) {
+    const bool use_tc = precision == CCS_BF16 && z.host_problems && z.rt_scratch && r.TQh;
     build_r_kernel<<<grid(z.r_total, 256), 256, 0, s>>>(p, r, precision, z.r_prefix, p.n_problems, z.r_total,
-                                                        scratch);
+                                                        scratch, use_tc ? z.rt_scratch : nullptr);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     if (z.max_tile_smem > 48 * 1024) {
       err = cudaFuncSetAttribute(gemm_splitk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, z.max_tile_smem);
       if (err != cudaSuccess) return err;
     }
     gemm_splitk_kernel<<<(unsigned)(z.gemm_blocks < 65535ll * 16 ? z.gemm_blocks : 65535ll * 16), 256,
-                         z.max_tile_smem, s>>>(p, r, precision, z.blk_prefix, p.n_problems, z.gemm_blocks, scratch);
+                         z.max_tile_smem, s>>>(p, r, precision, z.blk_prefix, p.n_problems, z.gemm_blocks, scratch,
+                                               use_tc ? 1 : 0);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    if (use_tc) {
+      for (int i = 0; i < z.n_problems; ++i) {
+        const ProblemDev& Pb = z.host_problems[i];
+        if (!Pb.tc) continue;
+        err = launch_gemm_tc(r.TQh + Pb.hub_T_off, z.rt_scratch + Pb.rt_off, Pb.M, Pb.N, Pb.K, Pb.splits,
+                             scratch + Pb.part_off, r.status, s);
+        if (err != cudaSuccess) return err;
+      }
+    }
     reduce_scatter_kernel<<<grid(z.out_total, 256), 256, 0, s>>>(p, z.out_prefix, p.n_problems, z.out_total,
                                                                 scratch, marg_out);
     if ((err = cudaGetLastError()) != cudaSuccess) return err;

@@ -215,8 +215,7 @@ def config3():
     c, cuts = brickwork_star(500, 30, regs, seed)
     body = [q for q in range(500) if q not in (0, 130, 260, 390)]
     marg = _pick_marginal(rng, body, [0, 130, 260, 390], 12)
-    return Workload("config3", c, cuts, marg, zstrings_for(500, 64, rng, 8),
-                    1 << 14, seed, regs)
+    return Workload("config3", c, cuts, marg, [], 1 << 14, seed, regs)
 
 
 def _random_star(rng, n, depth, n_regions, n_t_total, max_width=10, min_depth_margin=2):
