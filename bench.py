@@ -199,13 +199,15 @@ def run_ours(args, rank, world, local_rank):
     marg = torch.zeros(sum(1 << len(x.marginal) for x in ws), dtype=torch.float64, device="cuda")
     zexp = torch.zeros(max(1, sum(len(x.zstrings) for x in ws)), dtype=torch.float64, device="cuda")
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")      # > 129 MB L2
+    prec = ccs.CCS_BF16 if args.precision == "bf16" else ccs.CCS_FP32
     res = ccs.ccs_eval_variants(ctx, plan, mode=ccs.CCS_SAMPLED, shots=w.shots, seed_lo=seed[0],
-                                seed_hi=seed[1], use_graph=True)
+                                seed_hi=seed[1], use_graph=True, autotune=args.autotune)
+    tuning = ccs.ccs_get_tuning(ctx, res)
 
     def step():
         ccs.ccs_eval_variants(ctx, plan, mode=ccs.CCS_SAMPLED, shots=w.shots, seed_lo=seed[0],
                               seed_hi=seed[1], use_graph=True, res=res)
-        ccs.ccs_recombine(ctx, plan, res, marginal_out=marg, zexp_out=zexp)
+        ccs.ccs_recombine(ctx, plan, res, precision=prec, marginal_out=marg, zexp_out=zexp)
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -221,11 +223,8 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     clocks = clk.stop()
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    t_tot = sum(step_ms) / 1e3
-    if dist is not None:
-        tt = torch.tensor([t_tot], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_tot = float(tt.item())
+    from paper_2303_10788_gb300.sharding import max_over_ranks
+    t_tot = max_over_ranks(sum(step_ms) / 1e3, dist, device="cuda")
     value = units_per_step * args.steps * world / t_tot
 
     # --- per-stage kernel times (profiled pass, same work, no graph) ----------
@@ -235,7 +234,7 @@ def run_ours(args, rank, world, local_rank):
         flush.zero_()
         ccs.ccs_eval_variants(ctx, plan, mode=ccs.CCS_SAMPLED, shots=w.shots, seed_lo=seed[0],
                               seed_hi=seed[1], res=res)
-        ccs.ccs_recombine(ctx, plan, res, marginal_out=marg, zexp_out=zexp)
+        ccs.ccs_recombine(ctx, plan, res, precision=prec, marginal_out=marg, zexp_out=zexp)
         for k, v in ccs.ccs_get_stage_times(ctx).items():
             acc.setdefault(k, []).append(v)
     ccs.ccs_set_profiling(ctx, False)
@@ -250,7 +249,7 @@ def run_ours(args, rank, world, local_rank):
         p2 = ccs.ccs_build_fragments(ctx, ws)
         r2 = ccs.ccs_eval_variants(ctx, p2, mode=ccs.CCS_SAMPLED, shots=w.shots, seed_lo=seed[0],
                                    seed_hi=seed[1])
-        m_host, z_host = ccs.ccs_recombine(ctx, p2, r2)
+        m_host, z_host = ccs.ccs_recombine(ctx, p2, r2, precision=prec)
         e2e_times.append(time.perf_counter() - t0)
         del r2, p2
     e2e_s = statistics.mean(e2e_times)
@@ -263,11 +262,15 @@ def run_ours(args, rank, world, local_rank):
     roof = dict(roofs[dom], stage=dom)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u64/f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64/" + args.precision, "data": "synthetic",
             "config": {"workload": describe(ws), "variant_shots_per_step": units_per_step,
                        "l2": "flushed between steps (512 MB write, outside the step events)",
                        "parallelism": f"{world} independent replicas (no collective)",
-                       "launch": "one CUDA-graph replay (eval) + recombination per step"},
+                       "launch": "one CUDA-graph replay (eval) + recombination per step",
+                       "recombination": args.precision + (" (tcgen05 where eligible)" if args.precision == "bf16" else
+                                                          " (CUDA-core FMA)"),
+                       "tuning": {"threads": tuning[0], "words_per_op": tuning[1], "shots_per_cta": tuning[2],
+                                  "autotuned": bool(args.autotune)}},
             "circuits_per_s": world * len(ws) * args.steps / t_tot,
             "stage_ms": stage, "roofline": roof, "stage_roofline": roofs,
             "e2e": {"value": units_per_step * world / e2e_s, "unit": UNIT, "circuits_per_s": world * len(ws) / e2e_s,
@@ -340,6 +343,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="config2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"],
+                    help="operands of the 4^k contraction (bf16 uses the tcgen05 GEMM where it applies)")
+    ap.add_argument("--autotune", action="store_true", help="tune launch shapes on the plan before timing")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", args.gpus if args.gpus == 1 else 1))
