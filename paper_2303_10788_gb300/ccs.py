@@ -28,13 +28,21 @@ EXPORTS = ["ccs_version", "ccs_create", "ccs_destroy", "ccs_last_error", "ccs_bu
            "ccs_fragment_info_get", "ccs_plan_cuts", "ccs_fragment_wires", "ccs_get_tableau",
            "ccs_get_outcome_space", "ccs_get_counts", "ccs_get_dist", "ccs_get_tensor",
            "ccs_set_profiling", "ccs_get_stage_times", "ccs_cut_candidates", "ccs_recombine_noalloc",
-           "ccs_get_tuning", "ccs_get_operand"]
+           "ccs_get_tuning", "ccs_get_operand", "ccs_launch_count"]
 STAGES = ["clifford", "sample", "statevector", "fold", "recombine", "operands"]
 
 
 class ccs_gate(C.Structure):
     _fields_ = [("op", C.c_uint8), ("nq", C.c_uint8), ("flags", C.c_uint16),
                 ("q", C.c_uint32 * 2), ("param", C.c_double)]
+
+
+# numpy twin of ccs_gate (same offsets), for packing whole circuits at once
+_GATE_DTYPE = np.dtype({"names": ["op", "nq", "flags", "q", "param"],
+                        "formats": [np.uint8, np.uint8, np.uint16, (np.uint32, 2), np.float64],
+                        "offsets": [ccs_gate.op.offset, ccs_gate.nq.offset, ccs_gate.flags.offset,
+                                    ccs_gate.q.offset, ccs_gate.param.offset],
+                        "itemsize": C.sizeof(ccs_gate)})
 
 
 class ccs_cut(C.Structure):
@@ -56,7 +64,7 @@ class ccs_cut_opts(C.Structure):
 class ccs_eval_opts(C.Structure):
     _fields_ = [("mode", C.c_int32), ("shots", C.c_uint32), ("seed_lo", C.c_uint32),
                 ("seed_hi", C.c_uint32), ("keep_tableaus", C.c_int32), ("use_graph", C.c_int32),
-                ("autotune", C.c_int32)]
+                ("autotune", C.c_int32), ("per_variant_body", C.c_int32)]
 
 
 class ccs_recomb_opts(C.Structure):
@@ -233,11 +241,14 @@ def _pack_problem(prob):
     """prob: object with .circuit (n_qubits, gates=[(op,q0,q1)]), .cuts (or None),
     .marginal, .zstrings."""
     circ = prob.circuit
-    gates = (ccs_gate * max(1, len(circ.gates)))()
-    for i, (op, a, b) in enumerate(circ.gates):
-        gates[i].op = op
-        gates[i].q[0] = a
-        gates[i].q[1] = b if b >= 0 else 0
+    ng = len(circ.gates)
+    arr = np.zeros(max(1, ng), dtype=_GATE_DTYPE)
+    if ng:
+        g = np.asarray(circ.gates, dtype=np.int64).reshape(ng, 3)
+        arr["op"][:ng] = g[:, 0]
+        arr["q"][:ng, 0] = g[:, 1]
+        arr["q"][:ng, 1] = np.maximum(g[:, 2], 0)
+    gates = (ccs_gate * max(1, ng)).from_buffer(arr)
     cuts = getattr(prob, "cuts", None)
     ccuts = (ccs_cut * max(1, len(cuts) if cuts else 1))()
     if cuts:
@@ -254,23 +265,40 @@ def _pack_problem(prob):
     zq = (C.c_uint32 * max(1, len(flat)))(*flat)
     p = ccs_problem(circ.n_qubits, len(circ.gates), gates, -1 if cuts is None else len(cuts), ccuts,
                     len(prob.marginal), marg, len(zs), zo, zq)
-    keep = (gates, ccuts, marg, zo, zq)
+    keep = (arr, gates, ccuts, marg, zo, zq)
     return p, keep
 
 
+class PackedProblems:
+    """Problems marshalled once into ccs_problem structs (host buffers the
+    C ABI reads); pass to ccs_build_fragments in place of the list."""
+
+    def __init__(self, problems):
+        self.problems = list(problems)
+        self._keep = [_pack_problem(p) for p in self.problems]
+        self.arr = (ccs_problem * len(self._keep))(*[p for p, _ in self._keep])
+
+    def __len__(self):
+        return len(self.problems)
+
+
+def pack_problems(problems):
+    return PackedProblems(problems)
+
+
 def ccs_build_fragments(ctx, problems, max_cuts=12, max_nc_width=10, use_learned=0):
-    packed = [_pack_problem(p) for p in problems]
-    arr = (ccs_problem * len(packed))(*[p for p, _ in packed])
+    pk = problems if isinstance(problems, PackedProblems) else PackedProblems(problems)
     opts = ccs_cut_opts(max_cuts, max_nc_width, use_learned)
     h = C.c_void_p()
-    ctx.check(lib().ccs_build_fragments(ctx.h, arr, len(packed), C.byref(opts), C.byref(h)),
+    ctx.check(lib().ccs_build_fragments(ctx.h, pk.arr, len(pk), C.byref(opts), C.byref(h)),
               "ccs_build_fragments")
-    return Plan(ctx, h, problems)
+    return Plan(ctx, h, pk.problems)
 
 
 def ccs_eval_variants(ctx, plan, mode=CCS_SAMPLED, shots=1024, seed_lo=0x1234, seed_hi=0x5678,
-                      keep_tableaus=False, use_graph=False, res=None, autotune=False):
-    opts = ccs_eval_opts(mode, shots, seed_lo, seed_hi, int(keep_tableaus), int(use_graph), int(autotune))
+                      keep_tableaus=False, use_graph=False, res=None, autotune=False, per_variant_body=False):
+    opts = ccs_eval_opts(mode, shots, seed_lo, seed_hi, int(keep_tableaus), int(use_graph), int(autotune),
+                         int(per_variant_body))
     h = C.c_void_p(res.h.value if res is not None else None)
     ctx.check(lib().ccs_eval_variants(ctx.h, plan.h, C.byref(opts), C.byref(h)), "ccs_eval_variants")
     if res is not None:
@@ -416,3 +444,159 @@ def ccs_get_operand(ctx, res, problem, fragment):
     ctx.check(lib().ccs_get_operand(ctx.h, res.h, problem, fragment, out.ctypes.data_as(C.c_void_p)),
               "ccs_get_operand")
     return out
+
+
+# --- learned cut scorer --------------------------------------------------------
+class ccs_graph_batch(C.Structure):
+    _fields_ = [("n_nodes", C.c_int32), ("n_graphs", C.c_int32), ("x", C.POINTER(C.c_float)),
+                ("rowptr", C.POINTER(C.c_int32)), ("col", C.POINTER(C.c_int32)), ("val", C.POINTER(C.c_float)),
+                ("val_t", C.POINTER(C.c_float)), ("graph_off", C.POINTER(C.c_int32)),
+                ("glob", C.POINTER(C.c_float))]
+
+
+_MPNN_SIGS = {
+    "ccs_mpnn_num_params": ([], C.c_int),
+    "ccs_mpnn_create": ([C.c_void_p, C.c_uint64, C.POINTER(C.c_void_p)], C.c_int),
+    "ccs_mpnn_free": ([C.c_void_p], None),
+    "ccs_mpnn_params": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "ccs_mpnn_set_params": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "ccs_mpnn_forward": ([C.c_void_p, C.c_void_p, C.POINTER(ccs_graph_batch), C.c_void_p], C.c_int),
+    "ccs_mpnn_gradient": ([C.c_void_p, C.c_void_p, C.POINTER(ccs_graph_batch), C.c_void_p, C.c_void_p,
+                           C.c_void_p], C.c_int),
+    "ccs_mpnn_train_step": ([C.c_void_p, C.c_void_p, C.POINTER(ccs_graph_batch), C.c_void_p, C.c_float,
+                             C.c_void_p], C.c_int),
+    "ccs_featurize": ([C.c_void_p, C.POINTER(ccs_problem), C.POINTER(ccs_cut), C.c_int, C.c_void_p, C.c_void_p,
+                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p], C.c_int),
+    "ccs_set_cut_model": ([C.c_void_p, C.c_void_p], C.c_int),
+}
+EXPORTS += list(_MPNN_SIGS)
+
+
+def _mpnn_lib():
+    L = lib()
+    if not getattr(L, "_mpnn_bound", False):
+        for name, (args, res) in _MPNN_SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        L._mpnn_bound = True
+    return L
+
+
+class Graph:
+    """Features of one circuit under one cut set (numpy arrays)."""
+
+    def __init__(self, x, rowptr, col, val, val_t, glob):
+        self.x, self.rowptr, self.col, self.val, self.val_t, self.glob = x, rowptr, col, val, val_t, glob
+
+
+def ccs_featurize(ctx, problem, cuts):
+    p, keep = _pack_problem(problem)
+    n = problem.circuit.n_qubits
+    cap = max(16, 2 * sum(1 for g in problem.circuit.gates if g[0] in (6, 7)))
+    x = np.zeros((n, 8), np.float32)
+    rowptr = np.zeros(n + 1, np.int32)
+    col = np.zeros(cap, np.int32)
+    val = np.zeros(cap, np.float32)
+    val_t = np.zeros(cap, np.float32)
+    glob = np.zeros(8, np.float32)
+    cc = (ccs_cut * max(1, len(cuts)))(*[ccs_cut(q, g) for q, g in cuts])
+    f = lambda a: a.ctypes.data_as(C.c_void_p)
+    nnz = ctx.check(_mpnn_lib().ccs_featurize(ctx.h, C.byref(p), cc, len(cuts), f(x), f(rowptr), f(col), f(val),
+                                              f(val_t), cap, f(glob)), "ccs_featurize")
+    return Graph(x, rowptr, col[:nnz].copy(), val[:nnz].copy(), val_t[:nnz].copy(), glob)
+
+
+def make_batch(graphs):
+    """Concatenate graphs into block-diagonal batch arrays (kept alive on the struct)."""
+    xs, rps, cols, vals, vts, gl, goff = [], [0], [], [], [], [], [0]
+    for g in graphs:
+        base, e0 = goff[-1], rps[-1]
+        xs.append(g.x)
+        rps += list(e0 + g.rowptr[1:])
+        cols.append(g.col + base)
+        vals.append(g.val)
+        vts.append(g.val_t)
+        gl.append(g.glob)
+        goff.append(base + g.x.shape[0])
+    arrs = dict(x=np.ascontiguousarray(np.concatenate(xs), np.float32), rowptr=np.asarray(rps, np.int32),
+                col=np.ascontiguousarray(np.concatenate(cols), np.int32),
+                val=np.ascontiguousarray(np.concatenate(vals), np.float32),
+                val_t=np.ascontiguousarray(np.concatenate(vts), np.float32),
+                graph_off=np.asarray(goff, np.int32), glob=np.ascontiguousarray(np.stack(gl), np.float32))
+    P = lambda a, t: a.ctypes.data_as(C.POINTER(t))
+    b = ccs_graph_batch(goff[-1], len(graphs), P(arrs["x"], C.c_float), P(arrs["rowptr"], C.c_int32),
+                        P(arrs["col"], C.c_int32), P(arrs["val"], C.c_float), P(arrs["val_t"], C.c_float),
+                        P(arrs["graph_off"], C.c_int32), P(arrs["glob"], C.c_float))
+    b._arrays = arrs
+    return b
+
+
+class Mpnn:
+    def __init__(self, ctx, h):
+        self.ctx, self.h = ctx, h
+
+    def __del__(self):
+        try:
+            if self.h:
+                _mpnn_lib().ccs_mpnn_free(self.h)
+        except Exception:
+            pass
+
+
+def ccs_mpnn_num_params():
+    return _mpnn_lib().ccs_mpnn_num_params()
+
+
+def ccs_mpnn_create(ctx, seed=0):
+    h = C.c_void_p()
+    ctx.check(_mpnn_lib().ccs_mpnn_create(ctx.h, seed, C.byref(h)), "ccs_mpnn_create")
+    return Mpnn(ctx, h)
+
+
+def ccs_mpnn_params(ctx, net):
+    out = np.zeros(ccs_mpnn_num_params(), np.float32)
+    ctx.check(_mpnn_lib().ccs_mpnn_params(ctx.h, net.h, out.ctypes.data_as(C.c_void_p)), "ccs_mpnn_params")
+    return out
+
+
+def ccs_mpnn_set_params(ctx, net, params):
+    p = np.ascontiguousarray(params, np.float32)
+    ctx.check(_mpnn_lib().ccs_mpnn_set_params(ctx.h, net.h, p.ctypes.data_as(C.c_void_p)), "ccs_mpnn_set_params")
+
+
+def ccs_mpnn_forward(ctx, net, batch):
+    out = np.zeros(batch.n_graphs, np.float32)
+    ctx.check(_mpnn_lib().ccs_mpnn_forward(ctx.h, net.h, C.byref(batch), out.ctypes.data_as(C.c_void_p)),
+              "ccs_mpnn_forward")
+    return out
+
+
+def ccs_mpnn_gradient(ctx, net, batch, target):
+    t = np.ascontiguousarray(target, np.float32)
+    loss = np.zeros(1, np.float32)
+    grad = np.zeros(ccs_mpnn_num_params(), np.float32)
+    ctx.check(_mpnn_lib().ccs_mpnn_gradient(ctx.h, net.h, C.byref(batch), t.ctypes.data_as(C.c_void_p),
+                                            loss.ctypes.data_as(C.c_void_p), grad.ctypes.data_as(C.c_void_p)),
+              "ccs_mpnn_gradient")
+    return float(loss[0]), grad
+
+
+def ccs_mpnn_train_step(ctx, net, batch, target, lr=1e-3):
+    t = np.ascontiguousarray(target, np.float32)
+    loss = np.zeros(1, np.float32)
+    ctx.check(_mpnn_lib().ccs_mpnn_train_step(ctx.h, net.h, C.byref(batch), t.ctypes.data_as(C.c_void_p), lr,
+                                              loss.ctypes.data_as(C.c_void_p)), "ccs_mpnn_train_step")
+    return float(loss[0])
+
+
+def ccs_set_cut_model(ctx, net):
+    ctx.check(_mpnn_lib().ccs_set_cut_model(ctx.h, net.h if net is not None else None), "ccs_set_cut_model")
+
+
+def ccs_launch_count():
+    """Kernels the library has launched in this process (graph replays count their nodes)."""
+    L = lib()
+    L.ccs_launch_count.restype = C.c_longlong
+    L.ccs_launch_count.argtypes = []
+    return int(L.ccs_launch_count())

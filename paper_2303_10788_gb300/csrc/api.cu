@@ -1,3 +1,4 @@
+#include <atomic>
 // C ABI of the circuit-cutting hot path (declared in include/ccs.h).
 #include <cuda_runtime.h>
 
@@ -23,6 +24,7 @@ struct ccs_ctx_s {
   int sm_count = 0;
   size_t smem_optin = 0;
   std::string err;
+  ccs_mpnn cut_model = nullptr;   // learned cut scorer (not owned)
   // autotuner results: shape bucket -> (Clifford threads per CTA, shots per sampler CTA)
   std::map<std::tuple<int, int, unsigned, int>, std::tuple<int, int, int>> tuned;
   // second stream for the statevector branch (forked from / joined into `stream`)
@@ -35,6 +37,8 @@ struct ccs_ctx_s {
   float stage_ms[8] = {};
   int stage_mask = 0;   // stages recorded by the last profiled call
 };
+
+cudaStream_t ccs::c_stream(ccs_ctx c) { return c->stream; }
 
 namespace {
 enum Stage { ST_CLIFFORD = 0, ST_SAMPLE = 1, ST_STATEVEC = 2, ST_FOLD = 3, ST_RECOMB = 4, ST_OPERANDS = 5, ST_N = 6 };
@@ -115,7 +119,7 @@ struct ccs_plan_s {
   std::vector<ProblemDev> pdev;
   DevPlan dp{};
   Allocs A;
-  long long n_spaces = 0, n_counts = 0, n_dist = 0, n_zval = 0, n_tab = 0, n_T = 0, n_TZ = 0;
+  long long n_spaces = 0, n_counts = 0, n_dist = 0, n_zval = 0, n_tab = 0, n_T = 0, n_TZ = 0, n_body = 0;
   long long n_marg = 0, n_zexp = 0;
   std::vector<long long> t_prefix, tz_prefix, out_prefix, z_prefix, r_prefix, blk_prefix;
   long long* d_r_prefix = nullptr;
@@ -127,6 +131,7 @@ struct ccs_plan_s {
   long long* d_out_prefix = nullptr;
   long long* d_z_prefix = nullptr;
   int cliff_smem_words = 0, max_nc_n = 1;
+  int body_smem_words = 0;          // variant kernel started from a shared body (no op staging)
   FoldSet fold_cliff{}, fold_nc{}, fold_hubs{}, fold_hubs_nc{}, fold_others{};
   int2* d_items_hub = nullptr;      // Clifford hub variants (fused sampler)
   int2* d_items_plain = nullptr;    // other Clifford variants (sampler -> counts)
@@ -144,6 +149,7 @@ struct ccs_res_s {
   bool have_counts = false;
   Allocs A;
   cudaGraphExec_t graph = nullptr;
+  long long graph_launches = 0;   // kernel nodes of the captured graph
   EvalParams graph_key{};
   int graph_valid = 0;
   int cliff_threads = 256;
@@ -157,7 +163,77 @@ struct ccs_res_s {
   }
 };
 
+// Score up to 16 candidate cut sets with the learned model; index of the
+// smallest predicted time.
+namespace ccs {
+static std::atomic<long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void note_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace ccs
+
+static int learned_pick(ccs_ctx c, const Problem& P, const std::vector<CutCandidate>& cands, int* pick) {
+  const int nc = (int)std::min<size_t>(cands.size(), 16);
+  std::vector<float> X, val, valt, glob;
+  std::vector<int> rowptr{0}, col, goff{0};
+  std::string err;
+  for (int i = 0; i < nc; ++i) {
+    std::vector<float> x1, v1, vt1, g1;
+    std::vector<int> rp1, c1;
+    int rc = featurize(P, cands[i].cuts, x1, rp1, c1, v1, vt1, g1, err);
+    if (rc != CCS_OK) return fail(c, rc, err);
+    const int base = goff.back(), e0 = rowptr.back();
+    X.insert(X.end(), x1.begin(), x1.end());
+    for (size_t r = 1; r < rp1.size(); ++r) rowptr.push_back(e0 + rp1[r]);
+    for (int cc : c1) col.push_back(base + cc);
+    val.insert(val.end(), v1.begin(), v1.end());
+    valt.insert(valt.end(), vt1.begin(), vt1.end());
+    glob.insert(glob.end(), g1.begin(), g1.end());
+    goff.push_back(base + (int)P.n_qubits);
+  }
+  ccs_graph_batch b{goff.back(), nc, X.data(), rowptr.data(), col.data(), val.data(), valt.data(), goff.data(),
+                    glob.data()};
+  std::vector<float> pred(nc);
+  if (mpnn_predict(c->cut_model, &b, pred.data()) != CCS_OK) return fail(c, CCS_ERR_CUDA, "cut model forward");
+  *pick = (int)(std::min_element(pred.begin(), pred.end()) - pred.begin());
+  return CCS_OK;
+}
+
 extern "C" {
+
+int ccs_set_cut_model(ccs_ctx c, ccs_mpnn net) {
+  if (!c) return CCS_ERR_INVALID_ARG;
+  c->cut_model = net;
+  return CCS_OK;
+}
+
+int ccs_featurize(ccs_ctx c, const ccs_problem* q, const ccs_cut* cuts, int n_cuts, float* x, int32_t* rowptr,
+                  int32_t* col, float* val, float* val_t, int cap_nnz, float* glob) {
+  if (!c || !q || (n_cuts > 0 && !cuts) || !x || !rowptr || !glob) return fail(c, CCS_ERR_INVALID_ARG, "bad arguments");
+  Problem P;
+  P.n_qubits = q->n_qubits;
+  for (uint32_t g = 0; g < q->n_gates; ++g) {
+    const ccs_gate& G = q->gates[g];
+    P.gates.push_back({(int)G.op, (int)G.q[0], (G.op == CCS_CX || G.op == CCS_CZ) ? (int)G.q[1] : -1});
+  }
+  P.marginal.assign(q->marginal, q->marginal + q->n_marginal);
+  std::vector<ccs_cut> cs(cuts, cuts + std::max(0, n_cuts));
+  std::vector<float> X, v, vt, g;
+  std::vector<int> rp, cl;
+  std::string err;
+  int rc = featurize(P, cs, X, rp, cl, v, vt, g, err);
+  if (rc != CCS_OK) return fail(c, rc, err);
+  if ((int)cl.size() > cap_nnz) return fail(c, CCS_ERR_INVALID_ARG, "edge buffer too small");
+  std::copy(X.begin(), X.end(), x);
+  std::copy(rp.begin(), rp.end(), rowptr);
+  std::copy(cl.begin(), cl.end(), col);
+  if (val) std::copy(v.begin(), v.end(), val);
+  if (val_t) std::copy(vt.begin(), vt.end(), val_t);
+  std::copy(g.begin(), g.end(), glob);
+  return (int)cl.size();
+}
+
+long long ccs_launch_count(void) { return launch_count(); }
 
 const char* ccs_version(void) { return "ccs 0.1 (sm_103a)"; }
 
@@ -266,6 +342,13 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
       int rc = greedy_cuts(P, so, cands, err);
       if (rc != CCS_OK) { delete plan; return fail(c, rc, err); }
       P.cuts = cands.front().cuts;
+      if (o.use_learned && c->cut_model && cands.size() > 1 && !c->host_only) {
+        int pick = 0;
+        rc = learned_pick(c, P, cands, &pick);
+        if (rc != CCS_OK) { delete plan; return rc; }
+        // the greedy estimate judges the pick: far worse estimates are refused
+        if (cands[pick].cost <= 16.0 * cands.front().cost) P.cuts = cands[pick].cuts;
+      }
     }
     int rc = fragment_problem(P, pi, plan->frags, err);
     if (rc != CCS_OK) { delete plan; return fail(c, rc, "problem " + std::to_string(pi) + ": " + err); }
@@ -276,7 +359,8 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
   std::vector<CliffordOp> cops;
   std::vector<NCOp> nops;
   std::vector<int> moments, wires, zoffs;
-  std::vector<int2> items_c, items_nc;
+  std::vector<int2> items_c, items_nc, items_b;
+  int max_body_cols = 0;
   std::vector<long long> cost_c, cost_nc;
   for (auto& f : plan->frags) {
     if (f.clifford) compile_clifford(f);
@@ -330,16 +414,21 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
       plan->n_counts += (long long)d.nv * outs;
       d.tab_off = plan->n_tab;
       plan->n_tab += (long long)d.nv * (2 * d.n + 3) * d.W;
+      d.body_off = plan->n_body;      // even: (2n+3)*W is even, so 16-byte aligned
+      plan->n_body += (long long)(2 * d.n + 3) * d.W;
+      for (int w = 0; w < d.W; ++w) items_b.push_back(make_int2((int)fi, w));
+      max_body_cols = std::max(max_body_cols, 2 * d.n + 3);
       const int words = (2 * d.n + 3) * d.W + (d.n + 1) / 2 + 2;
       const int staged = words + (int)f.cops.size() + (d.n_moments + 2) / 2 + 2;   // + op stream
       plan->cliff_smem_words =
           std::max(plan->cliff_smem_words, (size_t)staged * 8 <= c->smem_optin ? staged : words);
+      plan->body_smem_words = std::max(plan->body_smem_words, words);
       for (int v = 0; v < d.nv; ++v) {
         items_c.push_back(make_int2((int)fi, v));
         cost_c.push_back((long long)d.W * (d.n_moments + 4) * std::max(1, d.n / 16) + d.nz * 4 + d.nA * d.n);
       }
     } else {
-      d.space_off = d.counts_off = d.tab_off = -1;
+      d.space_off = d.counts_off = d.tab_off = d.body_off = -1;
       plan->max_nc_n = std::max(plan->max_nc_n, d.n);
       for (int v = 0; v < d.nv; ++v) {
         items_nc.push_back(make_int2((int)fi, v));
@@ -508,12 +597,13 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
     return CCS_OK;
   }
   DevPlan& dp = plan->dp;
-  FragDev* dfr; CliffordOp* dco; NCOp* dno; int* dmo; int* dwi; int* dzo; int2* dic; int2* din;
+  FragDev* dfr; CliffordOp* dco; NCOp* dno; int* dmo; int* dwi; int* dzo; int2* dic; int2* din; int2* dib;
   ProblemDev* dpr; CliffordOp* dpo; CliffordOp* dbo; float* dpm; float* dbm;
   bool ok = upload(c, plan->A, plan->fdev, &dfr) && upload(c, plan->A, cops, &dco) &&
             upload(c, plan->A, nops, &dno) && upload(c, plan->A, moments, &dmo) &&
             upload(c, plan->A, wires, &dwi) && upload(c, plan->A, zoffs, &dzo) &&
             upload(c, plan->A, items_c, &dic) && upload(c, plan->A, items_nc, &din) &&
+            upload(c, plan->A, items_b, &dib) &&
             upload(c, plan->A, plan->pdev, &dpr) && upload(c, plan->A, prep, &dpo) &&
             upload(c, plan->A, basis, &dbo) && upload(c, plan->A, prepm, &dpm) &&
             upload(c, plan->A, basism, &dbm) &&
@@ -527,6 +617,7 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
   dp.frags = dfr; dp.cops = dco; dp.nops = dno; dp.moments = dmo; dp.wires = dwi; dp.zoffs = dzo;
   dp.items_cliff = dic; dp.items_nc = din;
   dp.n_items_cliff = (int)items_c.size(); dp.n_items_nc = (int)items_nc.size();
+  dp.items_body = dib; dp.n_items_body = (int)items_b.size(); dp.max_body_cols = max_body_cols;
   dp.problems = dpr; dp.n_problems = (int)plan->pdev.size();
   dp.prep_ops = dpo; dp.basis_ops = dbo; dp.prep_mats = dpm; dp.basis_mats = dbm;
   cudaError_t e = cudaStreamSynchronize(c->stream);
@@ -602,11 +693,14 @@ static int enqueue_eval(ccs_ctx c, ccs_plan p, ccs_res r) {
   }
   if (dp.n_items_cliff) {
     const int threads = r->cliff_threads;
-    const size_t smem = (size_t)p->cliff_smem_words * 8;
+    const int smem_words = e.shared_body ? p->body_smem_words : p->cliff_smem_words;
+    const size_t smem = (size_t)smem_words * 8;
     int per_sm = (int)std::max<size_t>(1, std::min<size_t>(2048 / threads, (c->smem_optin + 1024) / (smem + 2048)));
     int grid = std::min(dp.n_items_cliff, c->sm_count * per_sm);
     stage_begin(c, ST_CLIFFORD);
-    if ((err = launch_clifford(dp, r->dr, e, threads, r->cliff_words, p->cliff_smem_words, grid, s)) != cudaSuccess)
+    if (e.shared_body && (err = launch_body(dp, r->dr, s)) != cudaSuccess) return cuda_fail(c, err, "body kernel");
+    if ((err = launch_clifford(dp, r->dr, e, threads, e.shared_body ? 1 : r->cliff_words, smem_words, grid, s)) !=
+        cudaSuccess)
       return cuda_fail(c, err, "clifford kernel");
     stage_end(c, ST_CLIFFORD);
     if (e.mode == CCS_SAMPLED) {
@@ -647,7 +741,7 @@ static int autotune(ccs_ctx c, ccs_plan p, ccs_res r) {
     if (f.clifford) max_n = std::max(max_n, f.n);
   int items = 1;
   while (items < p->dp.n_items_cliff) items <<= 1;
-  const auto key = std::make_tuple((max_n + 63) / 64, items, r->ep.shots, r->ep.mode);
+  const auto key = std::make_tuple((max_n + 63) / 64, items, r->ep.shots, r->ep.mode * 2 + r->ep.shared_body);
   auto it = c->tuned.find(key);
   if (it != c->tuned.end()) {
     std::tie(r->cliff_threads, r->cliff_words, r->sample_spc) = it->second;
@@ -667,7 +761,7 @@ static int autotune(ccs_ctx c, ccs_plan p, ccs_res r) {
   for (int ti = 0; ti < 3 && rc == CCS_OK; ++ti)
     for (int wi = 0; wi < 4 && rc == CCS_OK; ++wi)
     for (int si = 0; si < n_spc && rc == CCS_OK; ++si) {
-      if (words_c[wi] > max_w) continue;
+      if (words_c[wi] > max_w || (r->ep.shared_body && words_c[wi] != 1)) continue;
       r->cliff_threads = threads_c[ti];
       r->cliff_words = words_c[wi];
       r->sample_spc = spc_c[si];
@@ -694,7 +788,7 @@ static int autotune(ccs_ctx c, ccs_plan p, ccs_res r) {
 int ccs_get_tuning(ccs_ctx c, ccs_res r, int* cliff_threads, int* words_per_op, int* shots_per_cta) {
   if (!c || !r) return fail(c, CCS_ERR_INVALID_ARG, "bad arguments");
   if (cliff_threads) *cliff_threads = r->cliff_threads;
-  if (words_per_op) *words_per_op = r->cliff_words;
+  if (words_per_op) *words_per_op = r->ep.shared_body ? 1 : r->cliff_words;
   if (shots_per_cta) *shots_per_cta = r->sample_spc;
   return CCS_OK;
 }
@@ -723,6 +817,7 @@ int ccs_eval_variants(ccs_ctx c, ccs_plan p, const ccs_eval_opts* opts, ccs_res*
     d.marg = r->A.get<double>(std::max<long long>(p->n_marg, 1));
     d.zexp = r->A.get<double>(std::max<long long>(p->n_zexp, 1));
     d.work = r->A.get<unsigned>(4);
+    d.body = r->A.get<unsigned long long>(std::max<long long>(p->n_body, 2));
     d.status = r->A.get<unsigned>(4);
     r->scratch = r->A.get<float>(std::max<long long>(p->r_total + p->part_total, 1));
     {   // default launch shape before any tuning: wide tableaus take 8 words per op, 512 threads
@@ -738,6 +833,7 @@ int ccs_eval_variants(ccs_ctx c, ccs_plan p, const ccs_eval_opts* opts, ccs_res*
       r->rt_scratch = r->A.get<uint16_t>(p->rt_total);
     }
     if (!d.spaces || !d.dist || !d.zval || !d.T || !d.TQ || !d.TZ || !d.marg || !d.zexp || !d.work || !d.status ||
+        !d.body ||
         !r->scratch || (p->rt_total && (!d.TQh || !r->rt_scratch))) {
       delete r;
       return fail(c, CCS_ERR_OOM, "result allocation failed");
@@ -761,6 +857,7 @@ int ccs_eval_variants(ccs_ctx c, ccs_plan p, const ccs_eval_opts* opts, ccs_res*
   e.seed_lo = opts->seed_lo;
   e.seed_hi = opts->seed_hi;
   e.keep_tableaus = opts->keep_tableaus && r->have_tabs;
+  e.shared_body = opts->per_variant_body ? 0 : 1;
   e.inv_shots = e.shots ? 1.0 / (double)e.shots : 0.0;
   r->ep = e;
   if (opts->autotune && !r->graph) {
@@ -776,7 +873,7 @@ int ccs_eval_variants(ccs_ctx c, ccs_plan p, const ccs_eval_opts* opts, ccs_res*
   }
   const bool same = r->graph && r->graph_key.mode == e.mode && r->graph_key.shots == e.shots &&
                     r->graph_key.seed_lo == e.seed_lo && r->graph_key.seed_hi == e.seed_hi &&
-                    r->graph_key.keep_tableaus == e.keep_tableaus;
+                    r->graph_key.keep_tableaus == e.keep_tableaus && r->graph_key.shared_body == e.shared_body;
   if (!same) {
     if (r->graph) { cudaGraphExecDestroy(r->graph); r->graph = nullptr; }
     cudaStream_t s = c->stream;
@@ -790,7 +887,10 @@ int ccs_eval_variants(ccs_ctx c, ccs_plan p, const ccs_eval_opts* opts, ccs_res*
     cudaGraph_t g;
     cudaError_t err = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
     if (err != cudaSuccess) { c->stream = saved; return cuda_fail(c, err, "begin capture"); }
+    const long long before = launch_count();
     int rc = enqueue_eval(c, p, r);
+    r->graph_launches = launch_count() - before;
+    note_launches(-r->graph_launches);      // captured, not launched
     err = cudaStreamEndCapture(s, &g);
     c->stream = saved;
     if (tmp_stream) cudaStreamDestroy(s);
@@ -803,6 +903,7 @@ int ccs_eval_variants(ccs_ctx c, ccs_plan p, const ccs_eval_opts* opts, ccs_res*
   }
   cudaError_t err = cudaGraphLaunch(r->graph, c->stream);
   if (err != cudaSuccess) return cuda_fail(c, err, "graph launch");
+  note_launches(r->graph_launches);
   return CCS_OK;
 }
 

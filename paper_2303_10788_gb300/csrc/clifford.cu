@@ -21,10 +21,13 @@ namespace {
 
 __device__ __forceinline__ uint64_t bm(unsigned v, int bit) { return 0ull - (uint64_t)((v >> bit) & 1u); }
 
-// Apply one fused Clifford op to G consecutive words starting at w0 (words
+// Apply one fused Clifford op to this thread's G words wk[0..G) (entries
 // >= W are skipped): the op's 31 bit masks are expanded once for all G.
+// The words are spread so that one load instruction of a warp touches each
+// shared-memory bank pair at most twice (see word_map below).
 template <int G>
-__device__ __forceinline__ void apply_op_g(CliffordOp op, uint64_t* tab, int W, int zb, int w0, uint64_t (&rd)[G]) {
+__device__ __forceinline__ void apply_op_g(CliffordOp op, uint64_t* tab, int W, int zb, const int (&wk)[G],
+                                           uint64_t (&rd)[G]) {
   const unsigned M = op.M, A = op.anf;
   uint64_t m[16], a[16];
 #pragma unroll
@@ -35,8 +38,8 @@ __device__ __forceinline__ void apply_op_g(CliffordOp op, uint64_t* tab, int W, 
   uint64_t* pzb = tab + (size_t)(zb + op.qb) * W;
 #pragma unroll
   for (int k = 0; k < G; ++k) {
-    const int w = w0 + k;
-    if (G > 1 && w >= W) break;
+    const int w = wk[k];
+    if (G > 1 && w >= W) continue;
     const uint64_t v0 = pxa[w], v1 = pza[w], v2 = pxb[w], v3 = pzb[w];
     const uint64_t v01 = v0 & v1, v23 = v2 & v3;
     rd[k] ^= (v0 & a[1]) ^ (v1 & a[2]) ^ (v01 & a[3]) ^ (v2 & a[4]) ^ ((v0 & v2) & a[5]) ^ ((v1 & v2) & a[6]) ^
@@ -120,12 +123,130 @@ __device__ __forceinline__ int variant_out_digit(int v, int qin, int i) {
   return v % 3;
 }
 
+// Phase exponent g of the product of two single-qubit Paulis (x1,z1)(x2,z2)
+// = i^g (x1^x2, z1^z2), with (1,1) meaning Y (Aaronson-Gottesman, Sec. III).
+__device__ __forceinline__ int pauli_g(unsigned x1, unsigned z1, unsigned x2, unsigned z2) {
+  if (x1 & z1) return (int)z2 - (int)x2;
+  if (x1) return (int)(z2 & 1u) * (2 * (int)x2 - 1);
+  if (z1) return (int)x2 * (1 - 2 * (int)z2);
+  return 0;
+}
+
+// Start a variant from its fragment's body tableau.  The body B is the gate
+// sequence U applied to the identity tableau, so its destabilizer row i is
+// U X_i U^+ and its stabilizer row i is U Z_i U^+.  Preparing input wire i
+// with a one-qubit Clifford C before U turns those rows into
+// U (C X_i C^+) U^+ and U (C Z_i C^+) U^+, where C X C^+ and C Z C^+ are
+// signed X, Y or Z read off the preparation's fused op (its M columns for x
+// and z, its sign polynomial's linear terms).  The image of Y_i = i X_i Z_i
+// is i times the product of the two body rows, whose sign follows from the
+// summed phase exponents (Sec. III of Aaronson-Gottesman).  Conjugation is
+// exact and row-wise, so the result equals simulating C then U bit for bit.
+// Phase 1 (one warp per Y-valued input) sums the exponents; phase 2 (one
+// thread per column) rewrites the two rows of every input in that column.
+__device__ void prep_rows_from_body(const DevPlan& P, const FragDev& F, int v, uint64_t* tab, int tid, int nt,
+                                    int* s_code, int* s_ry) {
+  const int n = F.n, W = F.W, Wh = F.Wh, zb = n + 1, rcol = 2 * (n + 1), ncol = 2 * n + 3;
+  const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
+  for (int o = tid; o < F.qin; o += nt) {
+    const CliffordOp op = P.prep_ops[variant_in_digit(v, o)];
+    const unsigned M = op.M, A = op.anf;
+    // 2-bit Pauli codes (bit 0 = x, bit 1 = z) and sign bits of the two images
+    const int dc = (int)((M >> 0) & 1u) | (int)(((M >> 4) & 1u) << 1);
+    const int sc = (int)((M >> 1) & 1u) | (int)(((M >> 5) & 1u) << 1);
+    s_code[o] = dc | (sc << 2) | (int)(((A >> 1) & 1u) << 4) | (int)(((A >> 2) & 1u) << 5);
+  }
+  __syncthreads();
+  for (int o = warp; o < F.qin; o += nwarps) {
+    const int code = s_code[o];
+    if ((code & 3) != 3 && ((code >> 2) & 3) != 3) continue;   // no Y image
+    const int i = P.wires[F.qin_off + o];
+    const int wd = i >> 6, b = i & 63;
+    int g = 0;
+    for (int j = lane; j < n; j += 32) {
+      const unsigned xd = (unsigned)(tab[(size_t)j * W + wd] >> b) & 1u;
+      const unsigned zd = (unsigned)(tab[(size_t)(zb + j) * W + wd] >> b) & 1u;
+      const unsigned xs = (unsigned)(tab[(size_t)j * W + Wh + wd] >> b) & 1u;
+      const unsigned zs = (unsigned)(tab[(size_t)(zb + j) * W + Wh + wd] >> b) & 1u;
+      g += pauli_g(xd, zd, xs, zs);
+    }
+    for (int off = 16; off; off >>= 1) g += __shfl_xor_sync(0xffffffffu, g, off);
+    if (lane == 0) {
+      const unsigned rd = (unsigned)(tab[(size_t)rcol * W + wd] >> b) & 1u;
+      const unsigned rs = (unsigned)(tab[(size_t)rcol * W + Wh + wd] >> b) & 1u;
+      const int e = ((1 + g) % 4 + 4) % 4;      // 0 or 2: i D S is Hermitian
+      s_ry[o] = (int)(rd ^ rs ^ (e == 2 ? 1u : 0u));
+    }
+  }
+  __syncthreads();
+  for (int c = tid; c < ncol; c += nt) {
+    uint64_t* col = tab + (size_t)c * W;
+    for (int o = 0; o < F.qin; ++o) {
+      const int code = s_code[o];
+      if (code == (1 | (2 << 2))) continue;      // X -> X, Z -> Z, no signs: unchanged
+      const int i = P.wires[F.qin_off + o];
+      const int wd = i >> 6, b = i & 63;
+      const unsigned db = (unsigned)(col[wd] >> b) & 1u, sb = (unsigned)(col[Wh + wd] >> b) & 1u;
+      unsigned nd, ns;
+      auto img = [&](int pc) -> unsigned {
+        if (c == rcol) return pc == 1 ? db : pc == 2 ? sb : (unsigned)s_ry[o];
+        return pc == 1 ? db : pc == 2 ? sb : (db ^ sb);
+      };
+      nd = img(code & 3);
+      ns = img((code >> 2) & 3);
+      if (c == rcol) {
+        nd ^= (unsigned)(code >> 4) & 1u;
+        ns ^= (unsigned)(code >> 5) & 1u;
+      }
+      col[wd] = (col[wd] & ~(1ull << b)) | ((uint64_t)nd << b);
+      col[Wh + wd] = (col[Wh + wd] & ~(1ull << b)) | ((uint64_t)ns << b);
+    }
+  }
+  __syncthreads();
+}
+
+}  // namespace
+
+// --- shared body: one CTA per (Clifford fragment, 64-row word) -------------
+// Rows evolve independently under conjugation, so each word of every column
+// is an independent problem: the CTA keeps one word per column in shared
+// memory and applies the whole op stream to it, moment by moment.
+__global__ void __launch_bounds__(256) body_kernel(DevPlan P, DevRes R) {
+  extern __shared__ __align__(16) unsigned long long smem_u64[];
+  uint64_t* tab = reinterpret_cast<uint64_t*>(smem_u64);
+  const int2 it = P.items_body[blockIdx.x];
+  const FragDev& F = P.frags[it.x];
+  const int n = F.n, W = F.W, Wh = F.Wh, zb = n + 1, rcol = 2 * (n + 1), ncol = 2 * n + 3;
+  const int w = it.y, tid = threadIdx.x, nt = blockDim.x;
+  for (int c = tid; c < ncol; c += nt) tab[c] = 0ull;
+  __syncthreads();
+  {   // identity: destabilizer i = X_i (words [0, Wh)), stabilizer i = Z_i
+    const int half = w < Wh ? 0 : 1, i0 = 64 * (w - half * Wh);
+    for (int i = i0 + tid; i < min(n, i0 + 64); i += nt) tab[half ? zb + i : i] = 1ull << (i & 63);
+  }
+  __syncthreads();
+  const CliffordOp* ops = P.cops + F.ops_off;
+  const int* mom = P.moments + F.mom_off;
+  const int wk[1] = {0};
+  uint64_t rd[1] = {0ull};
+  for (int mm = 0; mm < F.n_moments; ++mm) {
+    const int b0 = mom[mm], b1 = mom[mm + 1];
+    for (int o = b0 + tid; o < b1; o += nt) apply_op_g<1>(ops[o], tab, 1, zb, wk, rd);
+    __syncthreads();
+  }
+  atomicXor(reinterpret_cast<unsigned long long*>(&tab[rcol]), (unsigned long long)rd[0]);
+  __syncthreads();
+  unsigned long long* dst = R.body + F.body_off;
+  for (int c = tid; c < ncol; c += nt) dst[(size_t)c * W + w] = tab[c];
+}
+
+namespace {
 }  // namespace
 
 // G = words of one op per thread (the op's masks are expanded once per G).
 template <int G>
 __global__ void __launch_bounds__(512) clifford_kernel(DevPlan P, DevRes R, EvalParams E, int smem_words) {
-  extern __shared__ unsigned long long smem_u64[];
+  extern __shared__ __align__(16) unsigned long long smem_u64[];
   uint64_t* tab = reinterpret_cast<uint64_t*>(smem_u64);
   __shared__ FragDev sF;
   __shared__ int s_item;
@@ -137,6 +258,7 @@ __global__ void __launch_bounds__(512) clifford_kernel(DevPlan P, DevRes R, Eval
   __shared__ int s_nonpiv[kMaxMeas];
   __shared__ int s_n_nonpiv;
   __shared__ uint64_t s_sel[16][kMaxWh];
+  __shared__ int s_code[kMaxCuts], s_ry[kMaxCuts];
 
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
@@ -159,62 +281,79 @@ __global__ void __launch_bounds__(512) clifford_kernel(DevPlan P, DevRes R, Eval
     const int n = F.n, W = F.W, Wh = F.Wh, zb = n + 1, rcol = 2 * (n + 1);
     const int ncol = 2 * n + 3;
     uint32_t* rows = reinterpret_cast<uint32_t*>(tab + (size_t)ncol * W);
-    // op stream and moment offsets staged after the tableau when they fit
-    const int base_words = ncol * W + (n + 1) / 2 + 2;
-    const int n_ops = P.moments[F.mom_off + F.n_moments];
-    const bool staged = base_words + n_ops + (F.n_moments + 2) / 2 + 2 <= smem_words;
-    CliffordOp* ops_s = reinterpret_cast<CliffordOp*>(tab + base_words);
-    int* mom_s = reinterpret_cast<int*>(tab + base_words + n_ops);
-    const CliffordOp* ops = staged ? ops_s : P.cops + F.ops_off;
-    const int* mom = staged ? mom_s : P.moments + F.mom_off;
-    if (staged) {
-      const unsigned long long* src = reinterpret_cast<const unsigned long long*>(P.cops + F.ops_off);
-      for (int i = tid; i < n_ops; i += nt) reinterpret_cast<unsigned long long*>(ops_s)[i] = src[i];
-      for (int i = tid; i <= F.n_moments; i += nt) mom_s[i] = P.moments[F.mom_off + i];
-    }
-
-    // --- K1: initial tableau (destabilizer i = X_i, stabilizer i = Z_i) ---
-    for (int i = tid; i < ncol * W; i += nt) tab[i] = 0ull;
-    __syncthreads();
-    for (int j = tid; j < n; j += nt) {
-      tab[(size_t)j * W + (j >> 6)] = 1ull << (j & 63);
-      tab[(size_t)(zb + j) * W + Wh + (j >> 6)] = 1ull << (j & 63);
-    }
-    __syncthreads();
-
-    const int ngrp = (W + G - 1) / G;       // word groups of G words
-    const int J = nt / ngrp;                 // op slots per word group
-    const int w0 = (tid % ngrp) * G, jslot = tid / ngrp;
+    // Word map: an op is applied by ngrp = ceil(W/G) threads; thread g of op
+    // slot j owns words g + ngrp*((k + j) mod G), k < G.  For a fixed k the
+    // slots of a warp cycle through the G blocks of ngrp words, so when W is
+    // a multiple of 16 (every column starts at bank pair 0) each 64-bit bank
+    // pair sees exactly two accesses per load: conflict-free.
+    const int ngrp = (W + G - 1) / G;
+    const int J = nt / ngrp;                 // op slots
+    const int gidx = tid % ngrp, jslot = tid / ngrp;
     const bool active = jslot < J;
+    int wk[G];
+#pragma unroll
+    for (int k = 0; k < G; ++k) wk[k] = gidx + ngrp * ((k + jslot) % G);
     uint64_t rd[G];
 #pragma unroll
     for (int k = 0; k < G; ++k) rd[k] = 0;
-    if (active) {                          // preparations at quantum inputs
-      for (int o = jslot; o < F.qin; o += J) {
-        CliffordOp op = P.prep_ops[variant_in_digit(v, o)];
-        op.qa = (uint16_t)P.wires[F.qin_off + o];
-        op.qb = (uint16_t)n;
-        apply_op_g<G>(op, tab, W, zb, w0, rd);
-      }
-    }
-    __syncthreads();
-    for (int mm = 0; mm < F.n_moments; ++mm) {
-      const int b0 = mom[mm], b1 = mom[mm + 1];
-      if (active)
-        for (int o = b0 + jslot; o < b1; o += J) apply_op_g<G>(ops[o], tab, W, zb, w0, rd);
+    if (E.shared_body) {
+      // --- K1 from the fragment's shared body: copy it, rewrite the input rows ---
+      const ulonglong2* src = reinterpret_cast<const ulonglong2*>(R.body + F.body_off);
+      ulonglong2* dst2 = reinterpret_cast<ulonglong2*>(tab);
+      for (int i = tid; i < ncol * W / 2; i += nt) dst2[i] = src[i];
       __syncthreads();
+      prep_rows_from_body(P, F, v, tab, tid, nt, s_code, s_ry);
+    } else {
+      // op stream and moment offsets staged after the tableau when they fit
+      const int base_words = ncol * W + (n + 1) / 2 + 2;
+      const int n_ops = P.moments[F.mom_off + F.n_moments];
+      const bool staged = base_words + n_ops + (F.n_moments + 2) / 2 + 2 <= smem_words;
+      CliffordOp* ops_s = reinterpret_cast<CliffordOp*>(tab + base_words);
+      int* mom_s = reinterpret_cast<int*>(tab + base_words + n_ops);
+      const CliffordOp* ops = staged ? ops_s : P.cops + F.ops_off;
+      const int* mom = staged ? mom_s : P.moments + F.mom_off;
+      if (staged) {
+        const unsigned long long* src = reinterpret_cast<const unsigned long long*>(P.cops + F.ops_off);
+        for (int i = tid; i < n_ops; i += nt) reinterpret_cast<unsigned long long*>(ops_s)[i] = src[i];
+        for (int i = tid; i <= F.n_moments; i += nt) mom_s[i] = P.moments[F.mom_off + i];
+      }
+
+      // --- K1: initial tableau (destabilizer i = X_i, stabilizer i = Z_i) ---
+      for (int i = tid; i < ncol * W; i += nt) tab[i] = 0ull;
+      __syncthreads();
+      for (int j = tid; j < n; j += nt) {
+        tab[(size_t)j * W + (j >> 6)] = 1ull << (j & 63);
+        tab[(size_t)(zb + j) * W + Wh + (j >> 6)] = 1ull << (j & 63);
+      }
+      __syncthreads();
+
+      if (active) {                          // preparations at quantum inputs
+        for (int o = jslot; o < F.qin; o += J) {
+          CliffordOp op = P.prep_ops[variant_in_digit(v, o)];
+          op.qa = (uint16_t)P.wires[F.qin_off + o];
+          op.qb = (uint16_t)n;
+          apply_op_g<G>(op, tab, W, zb, wk, rd);
+        }
+      }
+      __syncthreads();
+      for (int mm = 0; mm < F.n_moments; ++mm) {
+        const int b0 = mom[mm], b1 = mom[mm + 1];
+        if (active)
+          for (int o = b0 + jslot; o < b1; o += J) apply_op_g<G>(ops[o], tab, W, zb, wk, rd);
+        __syncthreads();
+      }
     }
     if (active) {                          // basis changes at quantum outputs
       for (int o = jslot; o < F.qout; o += J) {
         CliffordOp op = P.basis_ops[variant_out_digit(v, F.qin, o)];
         op.qa = (uint16_t)P.wires[F.qout_off + o];
         op.qb = (uint16_t)n;
-        apply_op_g<G>(op, tab, W, zb, w0, rd);
+        apply_op_g<G>(op, tab, W, zb, wk, rd);
       }
 #pragma unroll
       for (int k = 0; k < G; ++k)
-        if (w0 + k < W)
-          atomicXor(reinterpret_cast<unsigned long long*>(&tab[(size_t)rcol * W + w0 + k]),
+        if (wk[k] < W)
+          atomicXor(reinterpret_cast<unsigned long long*>(&tab[(size_t)rcol * W + wk[k]]),
                     (unsigned long long)rd[k]);
     }
     __syncthreads();
@@ -493,7 +632,7 @@ cudaError_t launch_sample_hub(const DevPlan& p, const DevRes& r, const EvalParam
   const size_t smem = (size_t)4 * (wide ? (1 << max_nA) : ((1 << max_nA) > 1 ? (1 << (max_nA - 1)) : 1));
   cudaError_t err = cudaFuncSetAttribute(sample_hub_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  sample_hub_kernel<<<n_items, 512, smem, s>>>(p, r, e, items, keep_counts, wide);
+  sample_hub_kernel<<<n_items, 512, smem, s>>>(p, r, e, items, keep_counts, wide); note_launch();
   return cudaGetLastError();
 }
 
@@ -504,7 +643,7 @@ static cudaError_t launch_clifford_g(const DevPlan& p, const DevRes& r, const Ev
   cudaError_t err = cudaFuncSetAttribute(clifford_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
   if (err != cudaSuccess) return err;
-  clifford_kernel<G><<<grid, threads, smem, s>>>(p, r, e, smem_words);
+  clifford_kernel<G><<<grid, threads, smem, s>>>(p, r, e, smem_words); note_launch();
   return cudaGetLastError();
 }
 
@@ -519,13 +658,20 @@ cudaError_t launch_clifford(const DevPlan& p, const DevRes& r, const EvalParams&
   }
 }
 
+cudaError_t launch_body(const DevPlan& p, const DevRes& r, cudaStream_t s) {
+  if (p.n_items_body == 0) return cudaSuccess;
+  const size_t smem = (size_t)p.max_body_cols * 8;
+  body_kernel<<<p.n_items_body, 256, smem, s>>>(p, r); note_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_sample(const DevPlan& p, const DevRes& r, const EvalParams& e, const int2* items, int n_items,
                           int spc, int threads, cudaStream_t s) {
   if (n_items == 0 || e.shots == 0) return cudaSuccess;
   const int chunks = (int)((e.shots + spc - 1) / spc);
   const long long grid = (long long)n_items * chunks;
   if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-  sample_kernel<<<(unsigned)grid, threads, 0, s>>>(p, r, e, items, spc, chunks);
+  sample_kernel<<<(unsigned)grid, threads, 0, s>>>(p, r, e, items, spc, chunks); note_launch();
   return cudaGetLastError();
 }
 

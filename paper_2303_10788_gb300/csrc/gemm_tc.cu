@@ -308,7 +308,7 @@ cudaError_t launch_gemm_tc(const void* A, const void* Bt, int M, int N, long lon
   const size_t smem = gemm_tc_smem(N);
   cudaError_t e = cudaFuncSetAttribute(gemm_bf16_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  gemm_bf16_tc_kernel<<<mtiles * splits, 192, smem, s>>>(ta, tb, M, N, k_tiles, per, mtiles, partials, status);
+  gemm_bf16_tc_kernel<<<mtiles * splits, 192, smem, s>>>(ta, tb, M, N, k_tiles, per, mtiles, partials, status); note_launch();
   return cudaGetLastError();
 }
 

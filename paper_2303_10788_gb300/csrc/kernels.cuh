@@ -29,6 +29,7 @@ struct FragDev {
   long long T_off;         // float index of T_f (2^m x 4^n_slots); also indexes TQ
   int role;                // 0 plain, 1 hub of a star (TQ = Q), 2 other fragment of a star (TQ = T')
   long long TZ_off;        // float index of T_f^S (nz x 4^n_slots)
+  long long body_off;      // uint64 index of the shared body tableau ((2n+3)*W words), Clifford only
 };
 
 // Canonical affine outcome space of a Clifford variant.
@@ -68,6 +69,8 @@ struct DevPlan {
   const int2* items_cliff;    // (frag, variant), costliest first
   const int2* items_nc;
   int n_items_cliff, n_items_nc;
+  const int2* items_body;     // (frag, 64-row word) of every Clifford fragment's body
+  int n_items_body, max_body_cols;
   const ProblemDev* problems;
   int n_problems;
   const CliffordOp* prep_ops;  // 4
@@ -82,6 +85,7 @@ struct DevRes {
   float* dist;
   float* zval;
   unsigned long long* tabs;
+  unsigned long long* body;   // body tableaus, one per Clifford fragment
   float* T;
   float* TQ;               // contraction operands: Q for hubs, T' for the other fragments
   uint16_t* TQh;           // bf16 copy of the hubs' Q (tensor-core path), may be null
@@ -96,11 +100,21 @@ struct EvalParams {
   int mode;                   // CCS_EXACT / CCS_SAMPLED
   uint32_t shots, seed_lo, seed_hi;
   int keep_tableaus;
+  int shared_body;            // 1: variants start from their fragment's body tableau
   double inv_shots;
 };
 
+// Kernels the library has launched in this process; a replayed CUDA graph
+// adds its kernel nodes once per replay.
+void note_launch();
+void note_launches(long long n);
+long long launch_count();
+
 // Kernel launchers (stream-ordered; return cudaError_t of the launch).
 // words_per_op: 64-row words of one fused op a thread updates (1, 2, 4 or 8)
+// Body tableau of every Clifford fragment (identity evolved by the gate
+// sequence, no preparations or basis changes), one CTA per 64-row word.
+cudaError_t launch_body(const DevPlan& p, const DevRes& r, cudaStream_t s);
 cudaError_t launch_clifford(const DevPlan& p, const DevRes& r, const EvalParams& e,
                             int threads, int words_per_op, int smem_words, int grid, cudaStream_t s);
 cudaError_t launch_sample(const DevPlan& p, const DevRes& r, const EvalParams& e, const int2* items,
@@ -144,6 +158,12 @@ struct RecombSizes {
 };
 cudaError_t launch_recombine(const DevPlan& p, const DevRes& r, int precision, const RecombSizes& z,
                              float* scratch, double* marg_out, double* zexp_out, cudaStream_t s);
+// context stream; learned scorer helpers (mpnn.cu, features.cpp)
+cudaStream_t c_stream(ccs_ctx c);
+int mpnn_predict(ccs_mpnn n, const ccs_graph_batch* b, float* pred);
+int featurize(const Problem& p, const std::vector<ccs_cut>& cuts, std::vector<float>& x, std::vector<int>& rowptr,
+              std::vector<int>& col, std::vector<float>& val, std::vector<float>& val_t, std::vector<float>& glob,
+              std::string& err);
 // tcgen05 GEMM (gemm_tc.cu): partials[split][m][n] of A (M x K) x Bt^T (Bt: N x K), bf16
 bool gemm_tc_supported(int M, int N, long long K);
 cudaError_t launch_gemm_tc(const void* A, const void* Bt, int M, int N, long long K, int splits, float* partials,

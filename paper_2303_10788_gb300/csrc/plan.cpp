@@ -27,17 +27,20 @@ struct UF {
   }
 };
 
-// CHP update of one local Pauli pattern (x_a, z_a, x_b, z_b) and its sign.
-void chp_local(int op, int ra, int rb, int x[2], int z[2], int& flip) {
+// CHP update (Sec. III of Aaronson-Gottesman) of the local Pauli patterns
+// (x_a, z_a, x_b, z_b) and their signs, 16 patterns at once: bit v of each
+// plane is the x_a, z_a, x_b, z_b or sign bit of pattern v.
+void chp_planes(int op, int ra, int rb, uint32_t x[2], uint32_t z[2], uint32_t& flip) {
+  const uint32_t ONE = 0xffffu;
   switch (op) {
     case CCS_H: flip ^= x[ra] & z[ra]; std::swap(x[ra], z[ra]); break;
     case CCS_S: flip ^= x[ra] & z[ra]; z[ra] ^= x[ra]; break;
-    case CCS_SDG: flip ^= x[ra] & (z[ra] ^ 1); z[ra] ^= x[ra]; break;
+    case CCS_SDG: flip ^= x[ra] & (z[ra] ^ ONE); z[ra] ^= x[ra]; break;
     case CCS_X: flip ^= z[ra]; break;
     case CCS_Y: flip ^= x[ra] ^ z[ra]; break;
     case CCS_Z: flip ^= x[ra]; break;
     case CCS_CX:
-      flip ^= x[ra] & z[rb] & (x[rb] ^ z[ra] ^ 1);
+      flip ^= x[ra] & z[rb] & (x[rb] ^ z[ra] ^ ONE);
       x[rb] ^= x[ra];
       z[ra] ^= z[rb];
       break;
@@ -52,14 +55,14 @@ void chp_local(int op, int ra, int rb, int x[2], int z[2], int& flip) {
 
 // (M, anf) of a gate word acting on roles 0 (= a) and 1 (= b).
 CliffordOp clifford_from_word(const std::vector<std::array<int, 3>>& word) {
+  // pattern v: x_a = bit 0, z_a = bit 1, x_b = bit 2, z_b = bit 3 of v
+  uint32_t x[2] = {0xaaaau, 0xf0f0u}, z[2] = {0xccccu, 0xff00u}, flip = 0;
+  for (auto& g : word) chp_planes(g[0], g[1], g[2] < 0 ? 1 - g[1] : g[2], x, z, flip);
   int u[16], f[16];
   for (int v = 0; v < 16; ++v) {
-    int x[2] = {v & 1, (v >> 2) & 1};
-    int z[2] = {(v >> 1) & 1, (v >> 3) & 1};
-    int flip = 0;
-    for (auto& g : word) chp_local(g[0], g[1], g[2], x, z, flip);
-    u[v] = x[0] | (z[0] << 1) | (x[1] << 2) | (z[1] << 3);
-    f[v] = flip;
+    u[v] = (int)(((x[0] >> v) & 1u) | (((z[0] >> v) & 1u) << 1) | (((x[1] >> v) & 1u) << 2) |
+                 (((z[1] >> v) & 1u) << 3));
+    f[v] = (int)((flip >> v) & 1u);
   }
   CliffordOp op{0, 0, 0, 0};
   for (int j = 0; j < 4; ++j)

@@ -240,7 +240,7 @@ cudaError_t launch_operands(const DevPlan& p, const DevRes& r, const EvalParams&
     const long long blocks = (hubs.total + 255) / 256;
     qfold_kernel<<<(unsigned)(blocks < 65535 * 16 ? blocks : 65535 * 16), 256, 0, s>>>(p, r, e, hubs.fidx,
                                                                                  hubs.t_prefix, hubs.nf,
-                                                                                 hubs.total);
+                                                                                 hubs.total); note_launch();
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
   }
@@ -248,7 +248,7 @@ cudaError_t launch_operands(const DevPlan& p, const DevRes& r, const EvalParams&
     const long long blocks = (others.total + 255) / 256;
     prime_kernel<<<(unsigned)(blocks < 65535 * 16 ? blocks : 65535 * 16), 256, 0, s>>>(p, r, others.fidx,
                                                                                  others.t_prefix, others.nf,
-                                                                                 others.total);
+                                                                                 others.total); note_launch();
   }
   return cudaGetLastError();
 }
@@ -425,14 +425,14 @@ cudaError_t launch_fold(const DevPlan& p, const DevRes& r, const EvalParams& e, 
   if (f.total > 0) {
     const long long blocks = (f.total + 255) / 256;
     fold_kernel<<<(unsigned)(blocks < 65535 * 8 ? blocks : 65535 * 8), 256, 0, s>>>(p, r, e, f.fidx, f.t_prefix,
-                                                                              f.nf, f.total);
+                                                                              f.nf, f.total); note_launch();
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
   }
   if (f.total_z > 0) {
     const long long blocks = (f.total_z + 255) / 256;
     fold_z_kernel<<<(unsigned)(blocks < 65535 * 8 ? blocks : 65535 * 8), 256, 0, s>>>(p, r, f.fidx, f.tz_prefix,
-                                                                                f.nf, f.total_z);
+                                                                                f.nf, f.total_z); note_launch();
   }
   return cudaGetLastError();
 }
@@ -447,7 +447,7 @@ cudaError_t launch_recombine(const DevPlan& p, const DevRes& r, int precision, c
   if (z.out_total > 0) {
     const bool use_tc = precision == CCS_BF16 && z.host_problems && z.rt_scratch && r.TQh;
     build_r_kernel<<<grid(z.r_total, 256), 256, 0, s>>>(p, r, precision, z.r_prefix, p.n_problems, z.r_total,
-                                                        scratch, use_tc ? z.rt_scratch : nullptr);
+                                                        scratch, use_tc ? z.rt_scratch : nullptr); note_launch();
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     if (z.max_tile_smem > 48 * 1024) {
       err = cudaFuncSetAttribute(gemm_splitk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, z.max_tile_smem);
@@ -455,7 +455,7 @@ cudaError_t launch_recombine(const DevPlan& p, const DevRes& r, int precision, c
     }
     gemm_splitk_kernel<<<(unsigned)(z.gemm_blocks < 65535ll * 16 ? z.gemm_blocks : 65535ll * 16), 256,
                          z.max_tile_smem, s>>>(p, r, precision, z.blk_prefix, p.n_problems, z.gemm_blocks, scratch,
-                                               use_tc ? 1 : 0);
+                                               use_tc ? 1 : 0); note_launch();
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
     if (use_tc) {
       for (int i = 0; i < z.n_problems; ++i) {
@@ -467,13 +467,13 @@ cudaError_t launch_recombine(const DevPlan& p, const DevRes& r, int precision, c
       }
     }
     reduce_scatter_kernel<<<grid(z.out_total, 256), 256, 0, s>>>(p, z.out_prefix, p.n_problems, z.out_total,
-                                                                scratch, marg_out);
+                                                                scratch, marg_out); note_launch();
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
   if (z.z_total > 0) {
     recombine_z_kernel<<<(unsigned)(z.z_total < 65535 ? z.z_total : 65535), 256, 0, s>>>(p, r, z.z_prefix,
                                                                                     p.n_problems, z.z_total,
-                                                                                    zexp_out);
+                                                                                    zexp_out); note_launch();
     err = cudaGetLastError();
   }
   return err;

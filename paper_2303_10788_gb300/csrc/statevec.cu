@@ -152,7 +152,7 @@ cudaError_t launch_statevector(const DevPlan& p, const DevRes& r, int max_n, int
   cudaError_t err = cudaFuncSetAttribute(statevector_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
   if (err != cudaSuccess) return err;
-  statevector_kernel<<<grid, threads, smem, s>>>(p, r, max_n);
+  statevector_kernel<<<grid, threads, smem, s>>>(p, r, max_n); note_launch();
   return cudaGetLastError();
 }
 
