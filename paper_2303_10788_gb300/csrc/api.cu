@@ -1071,8 +1071,18 @@ int ccs_get_operand(ccs_ctx c, ccs_res r, int problem, int fragment, float* out)
   if (rc) return rc;
   if (d->role == 0) return fail(c, CCS_ERR_INVALID_ARG, "not part of a star contraction");
   const long long cnt = (1ll << d->m) << (2 * d->n_slots);
-  cudaError_t e = cudaMemcpy(out, r->dr.TQ + d->T_off, cnt * sizeof(float), cudaMemcpyDeviceToHost);
-  return e == cudaSuccess ? CCS_OK : cuda_fail(c, e, "copy operand");
+  if (d->role != 1) {
+    cudaError_t e = cudaMemcpy(out, r->dr.TQ + d->T_off, cnt * sizeof(float), cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? CCS_OK : cuda_fail(c, e, "copy operand");
+  }
+  // the hub's Q is stored transposed on the device ([d][o]); return [o][d]
+  std::vector<float> t(cnt);
+  cudaError_t e = cudaMemcpy(t.data(), r->dr.TQ + d->T_off, cnt * sizeof(float), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "copy operand");
+  const long long M = 1ll << d->m, K = 1ll << (2 * d->n_slots);
+  for (long long k = 0; k < K; ++k)
+    for (long long o = 0; o < M; ++o) out[o * K + k] = t[k * M + o];
+  return CCS_OK;
 }
 
 int ccs_get_tensor(ccs_ctx c, ccs_res r, int problem, int fragment, float* out) {

@@ -144,12 +144,12 @@ __device__ __forceinline__ int pauli_g(unsigned x1, unsigned z1, unsigned x2, un
 // exact and row-wise, so the result equals simulating C then U bit for bit.
 // Phase 1 (one warp per Y-valued input) sums the exponents; phase 2 (one
 // thread per column) rewrites the two rows of every input in that column.
-__device__ void prep_rows_from_body(const DevPlan& P, const FragDev& F, int v, uint64_t* tab, int tid, int nt,
-                                    int* s_code, int* s_ry) {
+__device__ void prep_rows_from_body(const CliffordOp* s_prep, const int* s_qin, const FragDev& F, int v,
+                                    uint64_t* tab, int tid, int nt, int* s_code, int* s_ry) {
   const int n = F.n, W = F.W, Wh = F.Wh, zb = n + 1, rcol = 2 * (n + 1), ncol = 2 * n + 3;
   const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
   for (int o = tid; o < F.qin; o += nt) {
-    const CliffordOp op = P.prep_ops[variant_in_digit(v, o)];
+    const CliffordOp op = s_prep[variant_in_digit(v, o)];
     const unsigned M = op.M, A = op.anf;
     // 2-bit Pauli codes (bit 0 = x, bit 1 = z) and sign bits of the two images
     const int dc = (int)((M >> 0) & 1u) | (int)(((M >> 4) & 1u) << 1);
@@ -160,7 +160,7 @@ __device__ void prep_rows_from_body(const DevPlan& P, const FragDev& F, int v, u
   for (int o = warp; o < F.qin; o += nwarps) {
     const int code = s_code[o];
     if ((code & 3) != 3 && ((code >> 2) & 3) != 3) continue;   // no Y image
-    const int i = P.wires[F.qin_off + o];
+    const int i = s_qin[o];
     const int wd = i >> 6, b = i & 63;
     int g = 0;
     for (int j = lane; j < n; j += 32) {
@@ -184,7 +184,7 @@ __device__ void prep_rows_from_body(const DevPlan& P, const FragDev& F, int v, u
     for (int o = 0; o < F.qin; ++o) {
       const int code = s_code[o];
       if (code == (1 | (2 << 2))) continue;      // X -> X, Z -> Z, no signs: unchanged
-      const int i = P.wires[F.qin_off + o];
+      const int i = s_qin[o];
       const int wd = i >> 6, b = i & 63;
       const unsigned db = (unsigned)(col[wd] >> b) & 1u, sb = (unsigned)(col[Wh + wd] >> b) & 1u;
       unsigned nd, ns;
@@ -259,9 +259,16 @@ __global__ void __launch_bounds__(512) clifford_kernel(DevPlan P, DevRes R, Eval
   __shared__ int s_n_nonpiv;
   __shared__ uint64_t s_sel[16][kMaxWh];
   __shared__ int s_code[kMaxCuts], s_ry[kMaxCuts];
+  __shared__ int s_A[kMaxMeas];                  // local wires of the measured set A
+  __shared__ int s_qin[kMaxCuts], s_qout[kMaxCuts];   // local wires of the quantum inputs / outputs
+  __shared__ CliffordOp s_prep[4], s_bops[3];    // preparation and basis-change ops
+  __shared__ uint32_t s_wb[16][32];              // K2: a warp's basis vectors by pivot
+  __shared__ uint32_t s_wh[16];                  // K2: that warp's pivot set
 
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
+  if (tid < 4) s_prep[tid] = P.prep_ops[tid];
+  else if (tid < 7) s_bops[tid - 4] = P.basis_ops[tid - 4];   // ordered by the loop's first barrier
 
   for (;;) {
     if (tid == 0) s_item = (int)atomicAdd(&R.work[0], 1u);
@@ -278,9 +285,11 @@ __global__ void __launch_bounds__(512) clifford_kernel(DevPlan P, DevRes R, Eval
     __syncthreads();
     const FragDev& F = sF;
     const int v = it.y;
+    for (int j = tid; j < F.nA; j += nt) s_A[j] = P.wires[F.A_off + j];   // ordered by the next barrier
+    if (tid < F.qin) s_qin[tid] = P.wires[F.qin_off + tid];
+    else if (tid >= 32 && tid - 32 < F.qout) s_qout[tid - 32] = P.wires[F.qout_off + tid - 32];
     const int n = F.n, W = F.W, Wh = F.Wh, zb = n + 1, rcol = 2 * (n + 1);
     const int ncol = 2 * n + 3;
-    uint32_t* rows = reinterpret_cast<uint32_t*>(tab + (size_t)ncol * W);
     // Word map: an op is applied by ngrp = ceil(W/G) threads; thread g of op
     // slot j owns words g + ngrp*((k + j) mod G), k < G.  For a fixed k the
     // slots of a warp cycle through the G blocks of ngrp words, so when W is
@@ -302,7 +311,7 @@ __global__ void __launch_bounds__(512) clifford_kernel(DevPlan P, DevRes R, Eval
       ulonglong2* dst2 = reinterpret_cast<ulonglong2*>(tab);
       for (int i = tid; i < ncol * W / 2; i += nt) dst2[i] = src[i];
       __syncthreads();
-      prep_rows_from_body(P, F, v, tab, tid, nt, s_code, s_ry);
+      prep_rows_from_body(s_prep, s_qin, F, v, tab, tid, nt, s_code, s_ry);
     } else {
       // op stream and moment offsets staged after the tableau when they fit
       const int base_words = ncol * W + (n + 1) / 2 + 2;
@@ -329,8 +338,8 @@ __global__ void __launch_bounds__(512) clifford_kernel(DevPlan P, DevRes R, Eval
 
       if (active) {                          // preparations at quantum inputs
         for (int o = jslot; o < F.qin; o += J) {
-          CliffordOp op = P.prep_ops[variant_in_digit(v, o)];
-          op.qa = (uint16_t)P.wires[F.qin_off + o];
+          CliffordOp op = s_prep[variant_in_digit(v, o)];
+          op.qa = (uint16_t)s_qin[o];
           op.qb = (uint16_t)n;
           apply_op_g<G>(op, tab, W, zb, wk, rd);
         }
@@ -345,8 +354,8 @@ __global__ void __launch_bounds__(512) clifford_kernel(DevPlan P, DevRes R, Eval
     }
     if (active) {                          // basis changes at quantum outputs
       for (int o = jslot; o < F.qout; o += J) {
-        CliffordOp op = P.basis_ops[variant_out_digit(v, F.qin, o)];
-        op.qa = (uint16_t)P.wires[F.qout_off + o];
+        CliffordOp op = s_bops[variant_out_digit(v, F.qin, o)];
+        op.qa = (uint16_t)s_qout[o];
         op.qb = (uint16_t)n;
         apply_op_g<G>(op, tab, W, zb, wk, rd);
       }
@@ -364,37 +373,72 @@ __global__ void __launch_bounds__(512) clifford_kernel(DevPlan P, DevRes R, Eval
     }
 
     // --- K2: basis B = RREF of the stabilizer X-block on the columns A ---
+    // Every warp takes its stabilizer rows (lane = row, bits = A columns) and
+    // builds an echelon basis of them with ballots (pivot = lowest set bit,
+    // lane p keeps the vector with pivot p).  The warp bases are merged in a
+    // binary tree (the partner's vectors are reduced by the own pivots, then
+    // eliminated among themselves), and warp 0 back-substitutes the final
+    // basis into the unique reduced form, in pivot order.
     const int nA = F.nA;
-    for (int i = tid; i < n; i += nt) {
-      uint32_t row = 0;
-      for (int j = 0; j < nA; ++j) {
-        const int a = P.wires[F.A_off + j];
-        row |= (uint32_t)((tab[(size_t)a * W + Wh + (i >> 6)] >> (i & 63)) & 1ull) << j;
-      }
-      rows[i] = row;
-    }
     if (tid == 0) s_off = 0;
-    __syncthreads();
-    if (warp == 0) {
-      int cnt = 0;
-      for (int p = 0; p < nA; ++p) {
-        int cand = 0x7fffffff;
-        for (int i = lane; i < n; i += 32)
-          if ((rows[i] >> p) & 1u) { cand = i; break; }
-        for (int o = 16; o; o >>= 1) cand = min(cand, __shfl_xor_sync(0xffffffffu, cand, o));
-        if (cand == 0x7fffffff) continue;
-        const uint32_t prow = rows[cand];
-        __syncwarp();
-        if (lane == 0) rows[cand] = 0;
-        __syncwarp();
-        for (int i = lane; i < n; i += 32)
-          if ((rows[i] >> p) & 1u) rows[i] ^= prow;
-        if (lane < cnt && ((s_basis[lane] >> p) & 1u)) s_basis[lane] ^= prow;
-        __syncwarp();
-        if (lane == 0) { s_basis[cnt] = prow; s_piv[cnt] = p; }
-        ++cnt;
-        __syncwarp();
+    const unsigned FULLW = 0xffffffffu;
+    uint32_t mine = 0, have = 0;
+    auto absorb = [&](uint32_t row) {
+      for (uint32_t h = have; h; h &= h - 1) {
+        const int p = __ffs(h) - 1;
+        const uint32_t bp = __shfl_sync(FULLW, mine, p);
+        if ((row >> p) & 1u) row ^= bp;
       }
+      for (int p = 0; p < nA; ++p) {
+        if ((have >> p) & 1u) continue;
+        const unsigned msk = __ballot_sync(FULLW, (row >> p) & 1u);
+        if (!msk) continue;
+        const int leader = __ffs(msk) - 1;
+        const uint32_t prow = __shfl_sync(FULLW, row, leader);
+        if (lane == leader) row = 0;
+        else if ((row >> p) & 1u) row ^= prow;
+        if (lane == p) mine = prow;
+        have |= 1u << p;
+      }
+    };
+    for (int i0 = warp * 32; i0 < n; i0 += nt) {
+      const int i = i0 + lane;
+      uint32_t row = 0;
+      if (i < n) {
+        const size_t w = (size_t)Wh + (i >> 6);
+        const int b = i & 63;
+        for (int j = 0; j < nA; ++j) row |= (uint32_t)((tab[(size_t)s_A[j] * W + w] >> b) & 1ull) << j;
+      }
+      absorb(row);
+    }
+    for (int stride = 1; stride < nwarps; stride <<= 1) {
+      const bool top = (warp % (2 * stride)) == 0 && warp + stride < nwarps;
+      const bool give = (warp % (2 * stride)) == stride;
+      if (give) {
+        s_wb[warp][lane] = mine;
+        if (lane == 0) s_wh[warp] = have;
+      }
+      __syncthreads();
+      if (top) {
+        const int pw = warp + stride;
+        absorb(((s_wh[pw] >> lane) & 1u) ? s_wb[pw][lane] : 0u);
+      }
+      __syncthreads();
+    }
+    if (warp == 0) {
+      uint32_t vec = ((have >> lane) & 1u) ? mine : 0u;
+      for (int q = nA - 1; q > 0; --q) {
+        if (!((have >> q) & 1u)) continue;
+        const uint32_t bq = __shfl_sync(FULLW, vec, q);
+        if (lane < q && ((vec >> q) & 1u)) vec ^= bq;
+      }
+      const int cnt = __popc(have);
+      if (lane < nA && ((have >> lane) & 1u)) {
+        const int pos = __popc(have & ((1u << lane) - 1u));
+        s_basis[pos] = vec;
+        s_piv[pos] = lane;
+      }
+      __syncwarp();
       if (lane == 0) {
         s_rank = cnt;
         int m = 0, pi = 0;
@@ -437,7 +481,7 @@ __global__ void __launch_bounds__(512) clifford_kernel(DevPlan P, DevRes R, Eval
           const int q0 = P.zoffs[F.zw_off + zi], q1 = P.zoffs[F.zw_off + zi + 1];
           for (int q = q0; q < q1; ++q) acc ^= tab[(size_t)P.wires[q] * W + lane];
           for (int o = 0; o < F.qout; ++o)
-            if ((u >> o) & 1) acc ^= tab[(size_t)P.wires[F.qout_off + o] * W + lane];
+            if ((u >> o) & 1) acc ^= tab[(size_t)s_qout[o] * W + lane];
         }
         const int z = zexp_from_acc(tab, n, W, Wh, acc, lane, s_sel[warp], R.status);
         if (lane == 0)
@@ -533,8 +577,9 @@ __global__ void __launch_bounds__(256) sample_kernel(DevPlan P, DevRes R, EvalPa
 // (16-bit counters packed in pairs, so |A| <= 16 fits 128 KB), then the
 // variant's slice of the hub operand
 //   Q[o, (s, P_out)] = sum_b prod_j lambda(P_out_j, b_j) count(o, b) / shots
-// for every P_out with beta(P_out) = the variant's bases.  Dense counts are
-// written only when kept for inspection.
+// for every P_out with beta(P_out) = the variant's bases, written to the
+// transposed store Q^T.  Dense counts are written only when kept for
+// inspection.
 __global__ void __launch_bounds__(512) sample_hub_kernel(DevPlan P, DevRes R, EvalParams E, const int2* items,
                                                          int keep_counts, int wide) {
   extern __shared__ uint32_t hist2[];
@@ -588,8 +633,8 @@ __global__ void __launch_bounds__(512) sample_hub_kernel(DevPlan P, DevRes R, Ev
     for (int i = 0; i < F.qin; ++i) t /= 4;
     for (int j = 0; j < F.qout; ++j) { beta[j] = t % 3; t /= 3; }
   }
-  int zpos[kMaxCuts], nz = 0;
-  int Dbase = 0;
+  int zpos[kMaxCuts], zout[kMaxCuts], nz = 0;
+  int Dbase = 0, fixed_mask = 0;   // fixed_mask: X/Y-basis outputs, whose outcome always flips the sign
   for (int j = 0; j < F.n_slots; ++j) {
     const int code = F.slot_code[j], idx = code & 255;
     if ((code >> 8) == 0) {
@@ -597,31 +642,47 @@ __global__ void __launch_bounds__(512) sample_hub_kernel(DevPlan P, DevRes R, Ev
       for (int i = 0; i < idx; ++i) t /= 4;
       Dbase |= (t % 4) << (2 * j);
     } else if (beta[idx] == 2) {
-      zpos[nz++] = j;                         // Z basis: P_out in {I, Z}
+      zpos[nz] = j;                           // Z basis: P_out in {I, Z}
+      zout[nz++] = idx;
     } else {
       Dbase |= (beta[idx] == 0 ? 1 : 2) << (2 * j);   // X basis -> X, Y basis -> Y
+      fixed_mask |= 1 << idx;
     }
   }
-  const int m = F.m, S2 = 2 * F.n_slots;
-  const double inv = E.inv_shots;
-  const int n_items = (1 << m) << nz;
-  for (int t = threadIdx.x; t < n_items; t += blockDim.x) {
-    const int o = t >> nz, cz = t & ((1 << nz) - 1);
-    int D = Dbase, smask = 0;   // smask: quantum outputs whose outcome flips the sign
-    for (int i = 0; i < nz; ++i)
-      if ((cz >> i) & 1) D |= 3 << (2 * zpos[i]);
-    for (int j = 0; j < F.n_slots; ++j) {
-      const int code = F.slot_code[j];
-      if ((code >> 8) == 1 && ((D >> (2 * j)) & 3) != 0) smask |= 1 << (code & 255);
+  // Q is stored transposed, Q^T[D][o] (o fastest), so each D of the variant
+  // is one coalesced row of 2^m floats.
+  const int m = F.m, M = 1 << m, nb = 1 << F.qout;
+  const float inv = (float)E.inv_shots;
+  float* QT = R.TQ + F.T_off;
+  if (F.qout <= 4 && E.shots <= (1u << 26)) {     // |acc| <= 16 shots fits an int
+    for (int o = threadIdx.x; o < M; o += blockDim.x) {
+      int c[16];
+#pragma unroll
+      for (int b = 0; b < 16; ++b) c[b] = b < nb ? (int)count((uint32_t)o | ((uint32_t)b << m)) : 0;
+      for (int cz = 0; cz < (1 << nz); ++cz) {
+        int D = Dbase, smask = fixed_mask;
+        for (int i = 0; i < nz; ++i)
+          if ((cz >> i) & 1) { D |= 3 << (2 * zpos[i]); smask |= 1 << zout[i]; }
+        int acc = 0;
+#pragma unroll
+        for (int b = 0; b < 16; ++b) acc += (__popc(b & smask) & 1) ? -c[b] : c[b];
+        QT[(long long)D * M + o] = (float)acc * inv;
+      }
     }
-    long long acc = 0;
-    for (int b = 0; b < (1 << F.qout); ++b) {
-      const long long cnt = count((uint32_t)o | ((uint32_t)b << m));
-      acc += (__popc(b & smask) & 1) ? -cnt : cnt;
+  } else {
+    for (int cz = 0; cz < (1 << nz); ++cz) {
+      int D = Dbase, smask = fixed_mask;
+      for (int i = 0; i < nz; ++i)
+        if ((cz >> i) & 1) { D |= 3 << (2 * zpos[i]); smask |= 1 << zout[i]; }
+      for (int o = threadIdx.x; o < M; o += blockDim.x) {
+        long long acc = 0;
+        for (int b = 0; b < nb; ++b) {
+          const long long cnt = count((uint32_t)o | ((uint32_t)b << m));
+          acc += (__popc(b & smask) & 1) ? -cnt : cnt;
+        }
+        QT[(long long)D * M + o] = (float)((double)acc * E.inv_shots);
+      }
     }
-    const float qv = (float)((double)acc * inv);
-    R.TQ[F.T_off + ((long long)o << S2) + D] = qv;
-    if (R.TQh) reinterpret_cast<__nv_bfloat16*>(R.TQh)[F.T_off + ((long long)o << S2) + D] = __float2bfloat16_rn(qv);
   }
 }
 

@@ -125,9 +125,8 @@ __global__ void qfold_kernel(DevPlan P, DevRes R, EvalParams E, const int* fidx,
        g += (long long)gridDim.x * blockDim.x) {
     const int fs = find_seg(prefix, nf, g);
     const FragDev& F = P.frags[fidx[fs]];
-    const long long loc = g - prefix[fs];
-    const int S2 = 2 * F.n_slots;
-    const int o = (int)(loc >> S2), D = (int)(loc & ((1ll << S2) - 1));
+    const long long loc = g - prefix[fs];     // hub operand stored transposed: loc = D * 2^m + o
+    const int o = (int)(loc & ((1ll << F.m) - 1)), D = (int)(loc >> F.m);
     int pout[kMaxCuts];
     long long vin = 0;
     for (int j = 0; j < F.n_slots; ++j) {
@@ -151,7 +150,6 @@ __global__ void qfold_kernel(DevPlan P, DevRes R, EvalParams E, const int* fidx,
       acc += neg ? -val : val;
     }
     R.TQ[F.T_off + loc] = (float)acc;
-    if (R.TQh) reinterpret_cast<__nv_bfloat16*>(R.TQh)[F.T_off + loc] = __float2bfloat16_rn((float)acc);
   }
 }
 
@@ -314,7 +312,7 @@ __global__ void __launch_bounds__(256) gemm_splitk_kernel(DevPlan P, DevRes R, i
     const long long k0 = split * kchunk, k1 = k0 + kchunk < K ? k0 + kchunk : K;
     float* As = sm;                  // kTK x TM
     float* Bs = sm + kTK * TM;       // kTK x TN
-    const float* A = R.TQ + Hb.T_off;        // M x K, row-major (the hub's Q)
+    const float* At = R.TQ + Hb.T_off;       // the hub's Q stored transposed: K x M, row-major
     const float* Bm = scratch + Pb.r_off;    // K x N, row-major
     const int tn4 = TN >> 2;
     const bool act = (int)threadIdx.x < (TM >> 2) * tn4;
@@ -326,9 +324,9 @@ __global__ void __launch_bounds__(256) gemm_splitk_kernel(DevPlan P, DevRes R, i
       for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
     for (long long kk = k0; kk < k1; kk += kTK) {
       for (int t = threadIdx.x; t < TM * kTK; t += blockDim.x) {
-        const int m = t / kTK, k = t % kTK;
+        const int m = t % TM, k = t / TM;
         const long long gm = (long long)mt * TM + m, gk = kk + k;
-        float v = (gm < M && gk < k1) ? A[gm * K + gk] : 0.f;
+        float v = (gm < M && gk < k1) ? At[gk * M + gm] : 0.f;
         if (precision == CCS_BF16) v = to_bf16f(v);
         As[k * TM + m] = v;
       }
@@ -361,6 +359,34 @@ __global__ void __launch_bounds__(256) gemm_splitk_kernel(DevPlan P, DevRes R, i
           if (gm < M && gn < N) scratch[Pb.part_off + ((long long)split * M + gm) * N + gn] = acc[i][j];
         }
     }
+  }
+}
+
+// BF16 K-major copy of a hub operand for the tensor-core GEMM:
+// Qh[o][D] = bf16(Q^T[D][o]), through 64 x 32 shared-memory tiles so both
+// the read (o fastest) and the write (D fastest, 128 B per row) coalesce.
+__global__ void __launch_bounds__(256) hub_bf16_kernel(const float* __restrict__ QT, __nv_bfloat16* __restrict__ Qh,
+                                                       int M, long long K) {
+  __shared__ float tile[64][33];
+  const long long tiles_d = (K + 63) / 64, tiles_o = (M + 31) / 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+  for (long long t = blockIdx.x; t < tiles_d * tiles_o; t += gridDim.x) {
+    const long long d0 = (t / tiles_o) * 64;
+    const int o0 = (int)(t % tiles_o) * 32;
+    for (int r = ty; r < 64; r += 8) {
+      const long long d = d0 + r;
+      const int o = o0 + tx;
+      tile[r][tx] = (d < K && o < M) ? QT[d * M + o] : 0.f;
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+      const int o = o0 + r;
+      for (int c = tx; c < 64; c += 32) {
+        const long long d = d0 + c;
+        if (o < M && d < K) Qh[(long long)o * K + d] = __float2bfloat16_rn(tile[c][r]);
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -461,6 +487,12 @@ cudaError_t launch_recombine(const DevPlan& p, const DevRes& r, int precision, c
       for (int i = 0; i < z.n_problems; ++i) {
         const ProblemDev& Pb = z.host_problems[i];
         if (!Pb.tc) continue;
+        {
+          const long long tiles = ((Pb.K + 63) / 64) * ((Pb.M + 31) / 32);
+          hub_bf16_kernel<<<(unsigned)(tiles < 152 * 16 ? tiles : 152 * 16), 256, 0, s>>>(
+              r.TQ + Pb.hub_T_off, reinterpret_cast<__nv_bfloat16*>(r.TQh) + Pb.hub_T_off, Pb.M, Pb.K); note_launch();
+          if ((err = cudaGetLastError()) != cudaSuccess) return err;
+        }
         err = launch_gemm_tc(r.TQh + Pb.hub_T_off, z.rt_scratch + Pb.rt_off, Pb.M, Pb.N, Pb.K, Pb.splits,
                              scratch + Pb.part_off, r.status, s);
         if (err != cudaSuccess) return err;
