@@ -360,6 +360,7 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
   std::vector<NCOp> nops;
   std::vector<int> moments, wires, zoffs;
   std::vector<int2> items_c, items_nc, items_b;
+  std::vector<int> cliff_frags;
   int max_body_cols = 0;
   std::vector<long long> cost_c, cost_nc;
   for (auto& f : plan->frags) {
@@ -416,6 +417,8 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
       plan->n_tab += (long long)d.nv * (2 * d.n + 3) * d.W;
       d.body_off = plan->n_body;      // even: (2n+3)*W is even, so 16-byte aligned
       plan->n_body += (long long)(2 * d.n + 3) * d.W;
+      d.rb_off = 65ll * (long long)cliff_frags.size();
+      cliff_frags.push_back((int)fi);
       for (int w = 0; w < d.W; ++w) items_b.push_back(make_int2((int)fi, w));
       max_body_cols = std::max(max_body_cols, 2 * d.n + 3);
       const int words = (2 * d.n + 3) * d.W + (d.n + 1) / 2 + 2;
@@ -428,7 +431,7 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
         cost_c.push_back((long long)d.W * (d.n_moments + 4) * std::max(1, d.n / 16) + d.nz * 4 + d.nA * d.n);
       }
     } else {
-      d.space_off = d.counts_off = d.tab_off = d.body_off = -1;
+      d.space_off = d.counts_off = d.tab_off = d.body_off = d.rb_off = -1;
       plan->max_nc_n = std::max(plan->max_nc_n, d.n);
       for (int v = 0; v < d.nv; ++v) {
         items_nc.push_back(make_int2((int)fi, v));
@@ -597,13 +600,13 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
     return CCS_OK;
   }
   DevPlan& dp = plan->dp;
-  FragDev* dfr; CliffordOp* dco; NCOp* dno; int* dmo; int* dwi; int* dzo; int2* dic; int2* din; int2* dib;
+  FragDev* dfr; CliffordOp* dco; NCOp* dno; int* dmo; int* dwi; int* dzo; int2* dic; int2* din; int2* dib; int* dcf;
   ProblemDev* dpr; CliffordOp* dpo; CliffordOp* dbo; float* dpm; float* dbm;
   bool ok = upload(c, plan->A, plan->fdev, &dfr) && upload(c, plan->A, cops, &dco) &&
             upload(c, plan->A, nops, &dno) && upload(c, plan->A, moments, &dmo) &&
             upload(c, plan->A, wires, &dwi) && upload(c, plan->A, zoffs, &dzo) &&
             upload(c, plan->A, items_c, &dic) && upload(c, plan->A, items_nc, &din) &&
-            upload(c, plan->A, items_b, &dib) &&
+            upload(c, plan->A, items_b, &dib) && upload(c, plan->A, cliff_frags, &dcf) &&
             upload(c, plan->A, plan->pdev, &dpr) && upload(c, plan->A, prep, &dpo) &&
             upload(c, plan->A, basis, &dbo) && upload(c, plan->A, prepm, &dpm) &&
             upload(c, plan->A, basism, &dbm) &&
@@ -618,6 +621,7 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
   dp.items_cliff = dic; dp.items_nc = din;
   dp.n_items_cliff = (int)items_c.size(); dp.n_items_nc = (int)items_nc.size();
   dp.items_body = dib; dp.n_items_body = (int)items_b.size(); dp.max_body_cols = max_body_cols;
+  dp.cliff_frags = dcf; dp.n_cliff_frags = (int)cliff_frags.size();
   dp.problems = dpr; dp.n_problems = (int)plan->pdev.size();
   dp.prep_ops = dpo; dp.basis_ops = dbo; dp.prep_mats = dpm; dp.basis_mats = dbm;
   cudaError_t e = cudaStreamSynchronize(c->stream);
@@ -698,7 +702,10 @@ static int enqueue_eval(ccs_ctx c, ccs_plan p, ccs_res r) {
     int per_sm = (int)std::max<size_t>(1, std::min<size_t>(2048 / threads, (c->smem_optin + 1024) / (smem + 2048)));
     int grid = std::min(dp.n_items_cliff, c->sm_count * per_sm);
     stage_begin(c, ST_CLIFFORD);
-    if (e.shared_body && (err = launch_body(dp, r->dr, s)) != cudaSuccess) return cuda_fail(c, err, "body kernel");
+    if (e.shared_body) {
+      if ((err = launch_body(dp, r->dr, s)) != cudaSuccess) return cuda_fail(c, err, "body kernel");
+      if ((err = launch_screen(dp, r->dr, e, c->sm_count, s)) != cudaSuccess) return cuda_fail(c, err, "screen kernel");
+    }
     if ((err = launch_clifford(dp, r->dr, e, threads, e.shared_body ? 1 : r->cliff_words, smem_words, grid, s)) !=
         cudaSuccess)
       return cuda_fail(c, err, "clifford kernel");
@@ -818,6 +825,8 @@ int ccs_eval_variants(ccs_ctx c, ccs_plan p, const ccs_eval_opts* opts, ccs_res*
     d.zexp = r->A.get<double>(std::max<long long>(p->n_zexp, 1));
     d.work = r->A.get<unsigned>(4);
     d.body = r->A.get<unsigned long long>(std::max<long long>(p->n_body, 2));
+    d.rowbasis = r->A.get<unsigned long long>(std::max<long long>(65ll * p->dp.n_cliff_frags, 1));
+    d.slow_items = r->A.get<int2>(std::max<long long>(p->dp.n_items_cliff, 1));
     d.status = r->A.get<unsigned>(4);
     r->scratch = r->A.get<float>(std::max<long long>(p->r_total + p->part_total, 1));
     {   // default launch shape before any tuning: wide tableaus take 8 words per op, 512 threads
@@ -833,7 +842,7 @@ int ccs_eval_variants(ccs_ctx c, ccs_plan p, const ccs_eval_opts* opts, ccs_res*
       r->rt_scratch = r->A.get<uint16_t>(p->rt_total);
     }
     if (!d.spaces || !d.dist || !d.zval || !d.T || !d.TQ || !d.TZ || !d.marg || !d.zexp || !d.work || !d.status ||
-        !d.body ||
+        !d.body || !d.rowbasis || !d.slow_items ||
         !r->scratch || (p->rt_total && (!d.TQh || !r->rt_scratch))) {
       delete r;
       return fail(c, CCS_ERR_OOM, "result allocation failed");

@@ -243,6 +243,188 @@ __global__ void __launch_bounds__(256) body_kernel(DevPlan P, DevRes R) {
 namespace {
 }  // namespace
 
+// --- shared-row basis: one CTA per Clifford fragment ----------------------
+// Every variant of a fragment keeps the body's stabilizer rows outside its
+// quantum inputs; only the input rows and the output columns change.  The
+// rank of a variant's measured set A therefore follows from the span of
+// those shared rows, taken as extended vectors e_i = (X bits on A, Z bits on
+// the quantum outputs) so that any output basis change maps them linearly.
+// This kernel stores an echelon basis of that span (pivot = lowest set bit)
+// in 64 pivot slots plus the pivot mask.
+namespace {
+// Fold `row` into the warp's echelon basis eb[] (pivot slots) / have.
+__device__ __forceinline__ void absorb64(unsigned long long row, unsigned long long* eb, unsigned long long& have,
+                                         int ne, int lane) {
+  for (unsigned long long h = have; h; h &= h - 1) {
+    const int p = __ffsll((long long)h) - 1;
+    if ((row >> p) & 1ull) row ^= eb[p];
+  }
+  for (int p = 0; p < ne; ++p) {
+    if ((have >> p) & 1ull) continue;
+    const unsigned msk = __ballot_sync(0xffffffffu, (unsigned)((row >> p) & 1ull));
+    if (!msk) continue;
+    const int leader = __ffs(msk) - 1;
+    const unsigned long long prow = __shfl_sync(0xffffffffu, row, leader);
+    if (lane == leader) row = 0ull;
+    else if ((row >> p) & 1ull) row ^= prow;
+    if (lane == 0) eb[p] = prow;
+    have |= 1ull << p;
+    __syncwarp();
+  }
+}
+}  // namespace
+
+__global__ void __launch_bounds__(512) body_basis_kernel(DevPlan P, DevRes R) {
+  __shared__ unsigned long long s_eb[16][64];
+  __shared__ unsigned long long s_eh[16];
+  __shared__ int s_col[64];
+  __shared__ int s_in[kMaxCuts];
+  const FragDev& F = P.frags[P.cliff_frags[blockIdx.x]];
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
+  const int n = F.n, W = F.W, Wh = F.Wh, zb = n + 1, nA = F.nA, ne = F.nA + F.qout;
+  for (int j = tid; j < ne; j += nt) s_col[j] = j < nA ? P.wires[F.A_off + j] : zb + P.wires[F.qout_off + j - nA];
+  if (tid < F.qin) s_in[tid] = P.wires[F.qin_off + tid];
+  __syncthreads();
+  const unsigned long long* body = R.body + F.body_off;
+  unsigned long long have = 0ull;
+  for (int i0 = warp * 32; i0 < n; i0 += nt) {
+    const int i = i0 + lane;
+    bool shared_row = i < n;
+    for (int k = 0; k < F.qin; ++k) shared_row = shared_row && s_in[k] != i;
+    unsigned long long row = 0ull;
+    if (shared_row) {
+      const size_t w = (size_t)Wh + (i >> 6);
+      const int b = i & 63;
+      for (int j = 0; j < ne; ++j) row |= ((body[(size_t)s_col[j] * W + w] >> b) & 1ull) << j;
+    }
+    absorb64(row, s_eb[warp], have, ne, lane);
+  }
+  for (int stride = 1; stride < nwarps; stride <<= 1) {
+    const bool top = (warp % (2 * stride)) == 0 && warp + stride < nwarps;
+    const bool give = (warp % (2 * stride)) == stride;
+    if (give && lane == 0) s_eh[warp] = have;
+    __syncthreads();
+    if (top) {
+      const int pw = warp + stride;
+      const unsigned long long ph = s_eh[pw];
+      absorb64(((ph >> lane) & 1ull) ? s_eb[pw][lane] : 0ull, s_eb[warp], have, ne, lane);
+      absorb64(((ph >> (lane + 32)) & 1ull) ? s_eb[pw][lane + 32] : 0ull, s_eb[warp], have, ne, lane);
+    }
+    __syncthreads();
+  }
+  if (warp == 0) {
+    unsigned long long* out = R.rowbasis + F.rb_off;
+    for (int p = lane; p < 64; p += 32) out[p] = ((have >> p) & 1ull) ? s_eb[0][p] : 0ull;
+    if (lane == 0) out[64] = have;
+  }
+}
+
+// --- screen: one warp per Clifford variant ---------------------------------
+// The variant's rows on A are the shared rows mapped through its output
+// basis changes (X bit of an output wire becomes m0 x + m1 z, read off the
+// basis op's matrix) plus its new input rows (the image of C Z_i C^+ under
+// the body: D_i, S_i or their product, bits only).  Ballot elimination of
+// those <= 48 vectors gives the rank; at full rank the canonical space is
+// (off 0, identity-reduced basis) and no tableau is needed.  Otherwise, or
+// when Z-strings or tableaus are wanted, the variant is queued.
+__global__ void __launch_bounds__(256) screen_kernel(DevPlan P, DevRes R, EvalParams E) {
+  __shared__ unsigned long long s_dummy;
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int tw = (gridDim.x * blockDim.x) >> 5;
+  const unsigned FULLW = 0xffffffffu;
+  (void)s_dummy;
+  for (int item = gw; item < P.n_items_cliff; item += tw) {
+    const int2 it = P.items_cliff[item];
+    const FragDev& F = P.frags[it.x];
+    const int v = it.y;
+    const int nA = F.nA, m = F.m, qout = F.qout;
+    bool slow = E.keep_tableaus || F.nz > 0 || nA > 31;
+    uint32_t have = 0, mine = 0;
+    if (!slow) {
+      // output basis maps: keepX / fromZ masks over A bits m..m+qout-1
+      uint32_t keepX = (1u << m) - 1u, fromZ = 0u;
+      for (int o = 0; o < qout; ++o) {
+        const unsigned M = P.basis_ops[variant_out_digit(v, F.qin, o)].M;
+        if (M & 1u) keepX |= 1u << (m + o);
+        if ((M >> 1) & 1u) fromZ |= 1u << (m + o);
+      }
+      auto project = [&](unsigned long long e) -> uint32_t {
+        const uint32_t x = (uint32_t)(e & ((1ull << nA) - 1ull));
+        const uint32_t z = (uint32_t)((e >> nA) << m);
+        return (x & keepX) ^ (z & fromZ);
+      };
+      auto absorb = [&](uint32_t row) {
+        for (uint32_t h = have; h; h &= h - 1) {
+          const int p = __ffs(h) - 1;
+          const uint32_t bp = __shfl_sync(FULLW, mine, p);
+          if ((row >> p) & 1u) row ^= bp;
+        }
+        for (int p = 0; p < nA; ++p) {
+          if ((have >> p) & 1u) continue;
+          const unsigned msk = __ballot_sync(FULLW, (row >> p) & 1u);
+          if (!msk) continue;
+          const int leader = __ffs(msk) - 1;
+          const uint32_t prow = __shfl_sync(FULLW, row, leader);
+          if (lane == leader) row = 0;
+          else if ((row >> p) & 1u) row ^= prow;
+          if (lane == p) mine = prow;
+          have |= 1u << p;
+        }
+      };
+      const unsigned long long* rb = R.rowbasis + F.rb_off;
+      const unsigned long long sh = rb[64];
+      absorb(((sh >> lane) & 1ull) ? project(rb[lane]) : 0u);
+      absorb(((sh >> (lane + 32)) & 1ull) ? project(rb[lane + 32]) : 0u);
+      // new stabilizer rows of the quantum inputs (bits only)
+      uint32_t row = 0;
+      if (lane < F.qin) {
+        const unsigned M = P.prep_ops[variant_in_digit(v, lane)].M;
+        const int sc = (int)((M >> 1) & 1u) | (int)(((M >> 5) & 1u) << 1);   // image of Z: 1 X, 2 Z, 3 Y
+        const int i = P.wires[F.qin_off + lane];
+        const int wd = i >> 6, b = i & 63;
+        const int n = F.n, W = F.W, Wh = F.Wh, zb = n + 1, ne = nA + qout;
+        const unsigned long long* body = R.body + F.body_off;
+        unsigned long long e = 0ull;
+        for (int j = 0; j < ne; ++j) {
+          const int col = j < nA ? P.wires[F.A_off + j] : zb + P.wires[F.qout_off + j - nA];
+          const unsigned long long d = (body[(size_t)col * W + wd] >> b) & 1ull;
+          const unsigned long long st = (body[(size_t)col * W + Wh + wd] >> b) & 1ull;
+          e |= ((sc & 1 ? d : 0ull) ^ (sc & 2 ? st : 0ull)) << j;
+        }
+        row = project(e);
+      }
+      absorb(row);
+      slow = __popc(have) != nA;
+    }
+    if (slow) {
+      if (lane == 0) {
+        const unsigned pos = atomicAdd(&R.work[2], 1u);
+        R.slow_items[pos] = it;
+      }
+      continue;
+    }
+    // full rank: reduce to the canonical form and record the space
+    uint32_t vec = ((have >> lane) & 1u) ? mine : 0u;
+    for (int q = nA - 1; q > 0; --q) {
+      const uint32_t bq = __shfl_sync(FULLW, vec, q);
+      if (lane < q && ((vec >> q) & 1u)) vec ^= bq;
+    }
+    SpaceRec& sp = R.spaces[F.space_off + v];
+    if (lane < kMaxMeas) sp.basis[lane] = lane < nA ? vec : 0u;
+    if (lane == 0) {
+      sp.off = 0u;
+      sp.rank = nA;
+      sp.flags = 0u;
+    }
+    if (E.mode == CCS_EXACT) {
+      const float pr = ldexpf(1.0f, -nA);
+      float* d = R.dist + F.dist_off + ((long long)v << nA);
+      for (int y = lane; y < (1 << nA); y += 32) d[y] = pr;
+    }
+  }
+}
+
 // G = words of one op per thread (the op's masks are expanded once per G).
 template <int G>
 __global__ void __launch_bounds__(512) clifford_kernel(DevPlan P, DevRes R, EvalParams E, int smem_words) {
@@ -275,8 +457,10 @@ __global__ void __launch_bounds__(512) clifford_kernel(DevPlan P, DevRes R, Eval
     __syncthreads();
     const int item = s_item;
     __syncthreads();
-    if (item >= P.n_items_cliff) break;
-    const int2 it = P.items_cliff[item];
+    // with shared bodies only the variants the screen queued come here
+    const int n_items = E.shared_body ? (int)*reinterpret_cast<volatile unsigned*>(&R.work[2]) : P.n_items_cliff;
+    if (item >= n_items) break;
+    const int2 it = E.shared_body ? R.slow_items[item] : P.items_cliff[item];
     {   // the fragment record, once per item, into shared memory
       const int* src = reinterpret_cast<const int*>(P.frags + it.x);
       int* dst = reinterpret_cast<int*>(&sF);
@@ -723,6 +907,18 @@ cudaError_t launch_body(const DevPlan& p, const DevRes& r, cudaStream_t s) {
   if (p.n_items_body == 0) return cudaSuccess;
   const size_t smem = (size_t)p.max_body_cols * 8;
   body_kernel<<<p.n_items_body, 256, smem, s>>>(p, r); note_launch();
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess || p.n_cliff_frags == 0) return err;
+  body_basis_kernel<<<p.n_cliff_frags, 512, 0, s>>>(p, r); note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_screen(const DevPlan& p, const DevRes& r, const EvalParams& e, int sm_count, cudaStream_t s) {
+  if (p.n_items_cliff == 0) return cudaSuccess;
+  const int warps = 8;
+  const long long need = (p.n_items_cliff + warps - 1) / warps;
+  const int grid = (int)(need < (long long)sm_count * 8 ? need : (long long)sm_count * 8);
+  screen_kernel<<<grid, 32 * warps, 0, s>>>(p, r, e); note_launch();
   return cudaGetLastError();
 }
 

@@ -30,6 +30,7 @@ struct FragDev {
   int role;                // 0 plain, 1 hub of a star (TQ = Q), 2 other fragment of a star (TQ = T')
   long long TZ_off;        // float index of T_f^S (nz x 4^n_slots)
   long long body_off;      // uint64 index of the shared body tableau ((2n+3)*W words), Clifford only
+  long long rb_off;        // uint64 index of the shared-row basis (64 slots + pivot mask), Clifford only
 };
 
 // Canonical affine outcome space of a Clifford variant.
@@ -71,6 +72,8 @@ struct DevPlan {
   int n_items_cliff, n_items_nc;
   const int2* items_body;     // (frag, 64-row word) of every Clifford fragment's body
   int n_items_body, max_body_cols;
+  const int* cliff_frags;     // every Clifford fragment (shared-row bases)
+  int n_cliff_frags;
   const ProblemDev* problems;
   int n_problems;
   const CliffordOp* prep_ops;  // 4
@@ -86,6 +89,8 @@ struct DevRes {
   float* zval;
   unsigned long long* tabs;
   unsigned long long* body;   // body tableaus, one per Clifford fragment
+  unsigned long long* rowbasis;   // shared-row bases, 65 words per Clifford fragment
+  int2* slow_items;           // variants the screen could not finish (count in work[2])
   float* T;
   float* TQ;               // contraction operands: Q for hubs, T' for the other fragments
   uint16_t* TQh;           // bf16 copy of the hubs' Q (tensor-core path), may be null
@@ -115,6 +120,10 @@ long long launch_count();
 // Body tableau of every Clifford fragment (identity evolved by the gate
 // sequence, no preparations or basis changes), one CTA per 64-row word.
 cudaError_t launch_body(const DevPlan& p, const DevRes& r, cudaStream_t s);
+// Screen of every Clifford variant from its fragment's shared-row basis: a
+// variant whose measured set has full rank (no Z-strings, no tableau kept)
+// is finished here; the others are queued for the tableau kernel.
+cudaError_t launch_screen(const DevPlan& p, const DevRes& r, const EvalParams& e, int sm_count, cudaStream_t s);
 cudaError_t launch_clifford(const DevPlan& p, const DevRes& r, const EvalParams& e,
                             int threads, int words_per_op, int smem_words, int grid, cudaStream_t s);
 cudaError_t launch_sample(const DevPlan& p, const DevRes& r, const EvalParams& e, const int2* items,

@@ -50,3 +50,51 @@ def test_shared_body_bit_exact(ctx, ws):
                 assert np.array_equal(ccs.ccs_get_counts(ctx, ra, pi, f, v), ccs.ccs_get_counts(ctx, rb, pi, f, v))
                 checked += 1
     assert checked >= 5
+
+
+@pytest.mark.parametrize("ws", [
+    [small_star(n=12, depth=9, region_full=(0, 1, 2, 3), boundary=4, window=(2, 6), n_z=0)],
+    config4(64)[:24],
+], ids=["star12", "config4x24"])
+def test_screen_matches_tableau_kernel(ctx, ws):
+    """Variants finished by the rank screen (no tableau) carry the same
+    outcome spaces and give the same marginals as the tableau kernel, which
+    every variant takes when tableaus are kept."""
+    plan = ccs.ccs_build_fragments(ctx, ws)
+    kw = dict(mode=ccs.CCS_SAMPLED, shots=ws[0].shots, seed_lo=SEED[0], seed_hi=SEED[1])
+    ra = ccs.ccs_eval_variants(ctx, plan, **kw)
+    rb = ccs.ccs_eval_variants(ctx, plan, keep_tableaus=True, **kw)
+    ma, _ = ccs.ccs_recombine(ctx, plan, ra)
+    mb, _ = ccs.ccs_recombine(ctx, plan, rb)
+    assert np.array_equal(ma, mb)
+    n = 0
+    for pi in range(len(ws)):
+        nf, _ = ccs.ccs_plan_counts(ctx, plan, pi)
+        for f in range(nf):
+            info = ccs.ccs_fragment_info_get(ctx, plan, pi, f)
+            if not info["clifford"]:
+                continue
+            for v in range(info["n_variants"]):
+                assert ccs.ccs_get_outcome_space(ctx, ra, pi, f, v) == ccs.ccs_get_outcome_space(ctx, rb, pi, f, v)
+                n += 1
+    assert n >= 10
+
+
+def test_screen_config3_all_variants(ctx):
+    """Config 3's 20736 body variants: spaces from the screen equal those of
+    the tableau kernel, variant by variant."""
+    from workloads import config3
+    w = config3()
+    plan = ccs.ccs_build_fragments(ctx, [w])
+    kw = dict(mode=ccs.CCS_SAMPLED, shots=w.shots, seed_lo=SEED[0], seed_hi=SEED[1])
+    ra = ccs.ccs_eval_variants(ctx, plan, **kw)
+    rb = ccs.ccs_eval_variants(ctx, plan, keep_tableaus=True, **kw)
+    nf, _ = ccs.ccs_plan_counts(ctx, plan, 0)
+    for f in range(nf):
+        info = ccs.ccs_fragment_info_get(ctx, plan, 0, f)
+        if info["clifford"]:
+            for v in range(info["n_variants"]):
+                assert ccs.ccs_get_outcome_space(ctx, ra, 0, f, v) == ccs.ccs_get_outcome_space(ctx, rb, 0, f, v), v
+    ma, _ = ccs.ccs_recombine(ctx, plan, ra, precision=ccs.CCS_FP32)
+    mb, _ = ccs.ccs_recombine(ctx, plan, rb, precision=ccs.CCS_FP32)
+    assert np.array_equal(ma, mb)
