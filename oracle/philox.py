@@ -41,9 +41,10 @@ def philox4x32_10(c0, c1, c2, c3, k0, k1):
 
 
 def shot_words(n_shots, variant, fragment, circuit, seed_lo, seed_hi):
-    """64 random bits per shot: key = (seed_lo, seed_hi),
-    counter = (shot, variant, fragment, circuit); bits = w0 | w1 << 32."""
-    s = np.arange(n_shots, dtype=np.uint64)
-    w0, w1, _, _ = philox4x32_10(s, np.full_like(s, variant), np.full_like(s, fragment),
-                                 np.full_like(s, circuit), seed_lo, seed_hi)
-    return w0 | (w1 << np.uint64(32))
+    """32 random bits per shot: key = (seed_lo, seed_hi); shot s takes output
+    word s mod 4 of the block with counter (s div 4, variant, fragment,
+    circuit), so one generator call serves four consecutive shots."""
+    g = np.arange((n_shots + 3) // 4, dtype=np.uint64)
+    w = philox4x32_10(g, np.full_like(g, variant), np.full_like(g, fragment),
+                      np.full_like(g, circuit), seed_lo, seed_hi)
+    return np.stack(w, axis=1).reshape(-1)[:n_shots]

@@ -50,7 +50,9 @@ class OracleResult:
 
 
 def sample_counts(off, B, nbits, shots, variant, fragment, circuit, seed_lo, seed_hi):
-    """Counts of y = off ^ XOR_{j: c_j = 1} B_j with c = low rho bits of Philox."""
+    """Counts of y = off ^ XOR_{j: c_j = 1} B_j with c = low rho bits of the
+    shot's 32-bit Philox word (rho <= 32)."""
+    assert len(B) <= 32
     bits = shot_words(shots, variant, fragment, circuit, seed_lo, seed_hi)
     y = np.full(shots, off, np.int64)
     for j, b in enumerate(B):

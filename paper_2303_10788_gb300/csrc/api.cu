@@ -361,6 +361,7 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
   std::vector<int> moments, wires, zoffs;
   std::vector<int2> items_c, items_nc, items_b;
   std::vector<int> cliff_frags;
+  int max_body_stage = 0;
   int max_body_cols = 0;
   std::vector<long long> cost_c, cost_nc;
   for (auto& f : plan->frags) {
@@ -417,8 +418,13 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
       plan->n_tab += (long long)d.nv * (2 * d.n + 3) * d.W;
       d.body_off = plan->n_body;      // even: (2n+3)*W is even, so 16-byte aligned
       plan->n_body += (long long)(2 * d.n + 3) * d.W;
-      d.rb_off = 65ll * (long long)cliff_frags.size();
-      cliff_frags.push_back((int)fi);
+      if (d.nz == 0) {   // screenable: no Z-strings need the tableau
+        d.rb_off = 65ll * (long long)cliff_frags.size();
+        cliff_frags.push_back((int)fi);
+      } else {
+        d.rb_off = -1;
+      }
+      max_body_stage = std::max(max_body_stage, 2 * d.n + 3 + (int)f.cops.size() + (d.n_moments + 2) / 2 + 1);
       for (int w = 0; w < d.W; ++w) items_b.push_back(make_int2((int)fi, w));
       max_body_cols = std::max(max_body_cols, 2 * d.n + 3);
       const int words = (2 * d.n + 3) * d.W + (d.n + 1) / 2 + 2;
@@ -622,6 +628,7 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
   dp.n_items_cliff = (int)items_c.size(); dp.n_items_nc = (int)items_nc.size();
   dp.items_body = dib; dp.n_items_body = (int)items_b.size(); dp.max_body_cols = max_body_cols;
   dp.cliff_frags = dcf; dp.n_cliff_frags = (int)cliff_frags.size();
+  dp.max_body_stage_words = max_body_stage;
   dp.problems = dpr; dp.n_problems = (int)plan->pdev.size();
   dp.prep_ops = dpo; dp.basis_ops = dbo; dp.prep_mats = dpm; dp.basis_mats = dbm;
   cudaError_t e = cudaStreamSynchronize(c->stream);
@@ -703,8 +710,10 @@ static int enqueue_eval(ccs_ctx c, ccs_plan p, ccs_res r) {
     int grid = std::min(dp.n_items_cliff, c->sm_count * per_sm);
     stage_begin(c, ST_CLIFFORD);
     if (e.shared_body) {
-      if ((err = launch_body(dp, r->dr, s)) != cudaSuccess) return cuda_fail(c, err, "body kernel");
-      if ((err = launch_screen(dp, r->dr, e, c->sm_count, s)) != cudaSuccess) return cuda_fail(c, err, "screen kernel");
+      if ((err = launch_body(dp, r->dr, (int)c->smem_optin, e.screen != 0, s)) != cudaSuccess)
+        return cuda_fail(c, err, "body kernel");
+      if (e.screen && (err = launch_screen(dp, r->dr, e, c->sm_count, s)) != cudaSuccess)
+        return cuda_fail(c, err, "screen kernel");
     }
     if ((err = launch_clifford(dp, r->dr, e, threads, e.shared_body ? 1 : r->cliff_words, smem_words, grid, s)) !=
         cudaSuccess)
@@ -867,6 +876,7 @@ int ccs_eval_variants(ccs_ctx c, ccs_plan p, const ccs_eval_opts* opts, ccs_res*
   e.seed_hi = opts->seed_hi;
   e.keep_tableaus = opts->keep_tableaus && r->have_tabs;
   e.shared_body = opts->per_variant_body ? 0 : 1;
+  e.screen = e.shared_body && p->dp.n_cliff_frags > 0 && !e.keep_tableaus;
   e.inv_shots = e.shots ? 1.0 / (double)e.shots : 0.0;
   r->ep = e;
   if (opts->autotune && !r->graph) {

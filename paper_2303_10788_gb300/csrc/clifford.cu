@@ -11,11 +11,14 @@
 // words of a few columns (Gottesman-Knill / CHP, Sec. II-C and III-B).
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "kernels.cuh"
 
 namespace ccs {
 
 constexpr int kMaxWh = (kMaxTableauQubits + 63) / 64;
+constexpr int kZOffStage = 257, kZWireStage = 1024;
 
 namespace {
 
@@ -211,13 +214,23 @@ __device__ void prep_rows_from_body(const CliffordOp* s_prep, const int* s_qin, 
 // Rows evolve independently under conjugation, so each word of every column
 // is an independent problem: the CTA keeps one word per column in shared
 // memory and applies the whole op stream to it, moment by moment.
-__global__ void __launch_bounds__(256) body_kernel(DevPlan P, DevRes R) {
+__global__ void __launch_bounds__(256) body_kernel(DevPlan P, DevRes R, int smem_words) {
   extern __shared__ __align__(16) unsigned long long smem_u64[];
   uint64_t* tab = reinterpret_cast<uint64_t*>(smem_u64);
   const int2 it = P.items_body[blockIdx.x];
   const FragDev& F = P.frags[it.x];
   const int n = F.n, W = F.W, Wh = F.Wh, zb = n + 1, rcol = 2 * (n + 1), ncol = 2 * n + 3;
   const int w = it.y, tid = threadIdx.x, nt = blockDim.x;
+  // the op stream and moment offsets follow the column words when they fit
+  const int n_ops = P.moments[F.mom_off + F.n_moments];
+  const bool staged = ncol + n_ops + (F.n_moments + 2) / 2 + 1 <= smem_words;
+  CliffordOp* ops_s = reinterpret_cast<CliffordOp*>(tab + ncol);
+  int* mom_s = reinterpret_cast<int*>(tab + ncol + n_ops);
+  if (staged) {
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(P.cops + F.ops_off);
+    for (int i = tid; i < n_ops; i += nt) reinterpret_cast<unsigned long long*>(ops_s)[i] = src[i];
+    for (int i = tid; i <= F.n_moments; i += nt) mom_s[i] = P.moments[F.mom_off + i];
+  }
   for (int c = tid; c < ncol; c += nt) tab[c] = 0ull;
   __syncthreads();
   {   // identity: destabilizer i = X_i (words [0, Wh)), stabilizer i = Z_i
@@ -225,8 +238,8 @@ __global__ void __launch_bounds__(256) body_kernel(DevPlan P, DevRes R) {
     for (int i = i0 + tid; i < min(n, i0 + 64); i += nt) tab[half ? zb + i : i] = 1ull << (i & 63);
   }
   __syncthreads();
-  const CliffordOp* ops = P.cops + F.ops_off;
-  const int* mom = P.moments + F.mom_off;
+  const CliffordOp* ops = staged ? ops_s : P.cops + F.ops_off;
+  const int* mom = staged ? mom_s : P.moments + F.mom_off;
   const int wk[1] = {0};
   uint64_t rd[1] = {0ull};
   for (int mm = 0; mm < F.n_moments; ++mm) {
@@ -279,6 +292,7 @@ __global__ void __launch_bounds__(512) body_basis_kernel(DevPlan P, DevRes R) {
   __shared__ unsigned long long s_eh[16];
   __shared__ int s_col[64];
   __shared__ int s_in[kMaxCuts];
+  __shared__ unsigned long long s_cw[64][kMaxWh];   // stabilizer halves of the extended columns
   const FragDev& F = P.frags[P.cliff_frags[blockIdx.x]];
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
   const int n = F.n, W = F.W, Wh = F.Wh, zb = n + 1, nA = F.nA, ne = F.nA + F.qout;
@@ -286,6 +300,8 @@ __global__ void __launch_bounds__(512) body_basis_kernel(DevPlan P, DevRes R) {
   if (tid < F.qin) s_in[tid] = P.wires[F.qin_off + tid];
   __syncthreads();
   const unsigned long long* body = R.body + F.body_off;
+  for (int t = tid; t < ne * Wh; t += nt) s_cw[t / Wh][t % Wh] = body[(size_t)s_col[t / Wh] * W + Wh + t % Wh];
+  __syncthreads();
   unsigned long long have = 0ull;
   for (int i0 = warp * 32; i0 < n; i0 += nt) {
     const int i = i0 + lane;
@@ -293,9 +309,8 @@ __global__ void __launch_bounds__(512) body_basis_kernel(DevPlan P, DevRes R) {
     for (int k = 0; k < F.qin; ++k) shared_row = shared_row && s_in[k] != i;
     unsigned long long row = 0ull;
     if (shared_row) {
-      const size_t w = (size_t)Wh + (i >> 6);
-      const int b = i & 63;
-      for (int j = 0; j < ne; ++j) row |= ((body[(size_t)s_col[j] * W + w] >> b) & 1ull) << j;
+      const int w = i >> 6, b = i & 63;
+      for (int j = 0; j < ne; ++j) row |= ((s_cw[j][w] >> b) & 1ull) << j;
     }
     absorb64(row, s_eb[warp], have, ne, lane);
   }
@@ -442,6 +457,8 @@ __global__ void __launch_bounds__(512) clifford_kernel(DevPlan P, DevRes R, Eval
   __shared__ uint64_t s_sel[16][kMaxWh];
   __shared__ int s_code[kMaxCuts], s_ry[kMaxCuts];
   __shared__ int s_A[kMaxMeas];                  // local wires of the measured set A
+  __shared__ int s_zo[kZOffStage], s_zw[kZWireStage];   // Z-string wire lists (staged when they fit)
+  __shared__ bool s_zstaged;
   __shared__ int s_qin[kMaxCuts], s_qout[kMaxCuts];   // local wires of the quantum inputs / outputs
   __shared__ CliffordOp s_prep[4], s_bops[3];    // preparation and basis-change ops
   __shared__ uint32_t s_wb[16][32];              // K2: a warp's basis vectors by pivot
@@ -457,10 +474,10 @@ __global__ void __launch_bounds__(512) clifford_kernel(DevPlan P, DevRes R, Eval
     __syncthreads();
     const int item = s_item;
     __syncthreads();
-    // with shared bodies only the variants the screen queued come here
-    const int n_items = E.shared_body ? (int)*reinterpret_cast<volatile unsigned*>(&R.work[2]) : P.n_items_cliff;
+    // after the rank screen only the variants it queued come here
+    const int n_items = E.screen ? (int)*reinterpret_cast<volatile unsigned*>(&R.work[2]) : P.n_items_cliff;
     if (item >= n_items) break;
-    const int2 it = E.shared_body ? R.slow_items[item] : P.items_cliff[item];
+    const int2 it = E.screen ? R.slow_items[item] : P.items_cliff[item];
     {   // the fragment record, once per item, into shared memory
       const int* src = reinterpret_cast<const int*>(P.frags + it.x);
       int* dst = reinterpret_cast<int*>(&sF);
@@ -472,6 +489,15 @@ __global__ void __launch_bounds__(512) clifford_kernel(DevPlan P, DevRes R, Eval
     for (int j = tid; j < F.nA; j += nt) s_A[j] = P.wires[F.A_off + j];   // ordered by the next barrier
     if (tid < F.qin) s_qin[tid] = P.wires[F.qin_off + tid];
     else if (tid >= 32 && tid - 32 < F.qout) s_qout[tid - 32] = P.wires[F.qout_off + tid - 32];
+    if (F.nz > 0) {   // Z-string wire lists, when they fit
+      const int zb0 = P.zoffs[F.zw_off], ztot = P.zoffs[F.zw_off + F.nz] - zb0;
+      const bool fit = F.nz + 1 <= kZOffStage && ztot <= kZWireStage;
+      if (tid == 0) s_zstaged = fit;
+      if (fit) {
+        for (int k = tid; k <= F.nz; k += nt) s_zo[k] = P.zoffs[F.zw_off + k] - zb0;
+        for (int t = tid; t < ztot; t += nt) s_zw[t] = P.wires[zb0 + t];
+      }
+    }
     const int n = F.n, W = F.W, Wh = F.Wh, zb = n + 1, rcol = 2 * (n + 1);
     const int ncol = 2 * n + 3;
     // Word map: an op is applied by ngrp = ceil(W/G) threads; thread g of op
@@ -643,16 +669,16 @@ __global__ void __launch_bounds__(512) clifford_kernel(DevPlan P, DevRes R, Eval
     // A non-pivot bit y_j is fixed by the pivot bits: y_j = off_j ^ sum_i
     // B_i[j] y_{piv_i}, so off_j is the sign of <Z_{A_j} prod Z_{A_piv_i}>.
     const int nnp = s_n_nonpiv;
-    const int nzu = F.nz << F.qout;
-    for (int ev = warp; ev < nnp + nzu; ev += nwarps) {
-      uint64_t acc = 0;
+    const int nzs = F.nz;
+    for (int ev = warp; ev < nnp + nzs; ev += nwarps) {
       if (ev < nnp) {
+        uint64_t acc = 0;
         const int j = s_nonpiv[ev];
         const uint32_t mask = s_nonpiv_mask[ev];
         if (lane < W) {
-          acc = tab[(size_t)P.wires[F.A_off + j] * W + lane];
+          acc = tab[(size_t)s_A[j] * W + lane];
           for (int i = 0; i < s_rank; ++i)
-            if ((mask >> i) & 1u) acc ^= tab[(size_t)P.wires[F.A_off + s_piv[i]] * W + lane];
+            if ((mask >> i) & 1u) acc ^= tab[(size_t)s_A[s_piv[i]] * W + lane];
         }
         const int z = zexp_from_acc(tab, n, W, Wh, acc, lane, s_sel[warp], R.status);
         if (lane == 0) {
@@ -660,16 +686,25 @@ __global__ void __launch_bounds__(512) clifford_kernel(DevPlan P, DevRes R, Eval
           if (z < 0) atomicOr(&s_off, 1u << j);
         }
       } else {
-        const int zi = (ev - nnp) >> F.qout, u = (ev - nnp) & ((1 << F.qout) - 1);
+        // Z-string zi: its own columns once, then every subset u of the outputs
+        const int zi = ev - nnp;
+        uint64_t acc0 = 0;
         if (lane < W) {
-          const int q0 = P.zoffs[F.zw_off + zi], q1 = P.zoffs[F.zw_off + zi + 1];
-          for (int q = q0; q < q1; ++q) acc ^= tab[(size_t)P.wires[q] * W + lane];
-          for (int o = 0; o < F.qout; ++o)
-            if ((u >> o) & 1) acc ^= tab[(size_t)s_qout[o] * W + lane];
+          if (s_zstaged) {
+            for (int q = s_zo[zi]; q < s_zo[zi + 1]; ++q) acc0 ^= tab[(size_t)s_zw[q] * W + lane];
+          } else {
+            const int q0 = P.zoffs[F.zw_off + zi], q1 = P.zoffs[F.zw_off + zi + 1];
+            for (int q = q0; q < q1; ++q) acc0 ^= tab[(size_t)P.wires[q] * W + lane];
+          }
         }
-        const int z = zexp_from_acc(tab, n, W, Wh, acc, lane, s_sel[warp], R.status);
-        if (lane == 0)
-          R.zval[F.zval_off + ((long long)v * F.nz + zi) * (1 << F.qout) + u] = (float)z;
+        for (int u = 0; u < (1 << F.qout); ++u) {
+          uint64_t acc = acc0;
+          if (lane < W)
+            for (int o = 0; o < F.qout; ++o)
+              if ((u >> o) & 1) acc ^= tab[(size_t)s_qout[o] * W + lane];
+          const int z = zexp_from_acc(tab, n, W, Wh, acc, lane, s_sel[warp], R.status);
+          if (lane == 0) R.zval[F.zval_off + ((long long)v * F.nz + zi) * (1 << F.qout) + u] = (float)z;
+        }
       }
     }
     __syncthreads();
@@ -740,14 +775,20 @@ __global__ void __launch_bounds__(256) sample_kernel(DevPlan P, DevRes R, EvalPa
   __syncthreads();
   uint32_t* gcounts = R.counts + F.counts_off + ((long long)v << nA);
   const uint32_t cmask = rank >= 32 ? 0xffffffffu : ((1u << rank) - 1u);
+  // shot 4g+j takes output word j of the generator at counter (g, v, f, problem)
   const uint32_t s_end = min((uint32_t)E.shots, (uint32_t)(chunk + 1) * (uint32_t)spc);
-  for (uint32_t s = (uint32_t)chunk * spc + threadIdx.x; s < s_end; s += blockDim.x) {
-    const uint4 o = philox4x32_10(make_uint4(s, (uint32_t)v, (uint32_t)F.findex, (uint32_t)F.problem),
+  for (uint32_t g = ((uint32_t)chunk * spc >> 2) + threadIdx.x; 4 * g < s_end; g += blockDim.x) {
+    const uint4 o = philox4x32_10(make_uint4(g, (uint32_t)v, (uint32_t)F.findex, (uint32_t)F.problem),
                                   E.seed_lo, E.seed_hi);
-    const uint32_t c = o.x & cmask;
-    const uint32_t y = off ^ tbl[0][c & 255] ^ tbl[1][(c >> 8) & 255] ^ tbl[2][(c >> 16) & 255];
-    if (smem_hist) atomicAdd(&hist[y], 1u);
-    else atomicAdd(&gcounts[y], 1u);
+    const uint32_t w4[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (4 * g + j >= s_end) break;
+      const uint32_t c = w4[j] & cmask;
+      const uint32_t y = off ^ tbl[0][c & 255] ^ tbl[1][(c >> 8) & 255] ^ tbl[2][(c >> 16) & 255];
+      if (smem_hist) atomicAdd(&hist[y], 1u);
+      else atomicAdd(&gcounts[y], 1u);
+    }
   }
   if (smem_hist) {
     __syncthreads();
@@ -794,13 +835,18 @@ __global__ void __launch_bounds__(512) sample_hub_kernel(DevPlan P, DevRes R, Ev
   for (int i = threadIdx.x; i < nwords; i += blockDim.x) hist2[i] = 0u;
   __syncthreads();
   const uint32_t cmask = rank >= 32 ? 0xffffffffu : ((1u << rank) - 1u);
-  for (uint32_t s = threadIdx.x; s < E.shots; s += blockDim.x) {
-    const uint4 o = philox4x32_10(make_uint4(s, (uint32_t)v, (uint32_t)F.findex, (uint32_t)F.problem),
+  for (uint32_t g = threadIdx.x; 4 * g < E.shots; g += blockDim.x) {   // shot 4g+j: word j
+    const uint4 o = philox4x32_10(make_uint4(g, (uint32_t)v, (uint32_t)F.findex, (uint32_t)F.problem),
                                   E.seed_lo, E.seed_hi);
-    const uint32_t c = o.x & cmask;
-    const uint32_t y = off ^ tbl[0][c & 255] ^ tbl[1][(c >> 8) & 255] ^ tbl[2][(c >> 16) & 255];
-    if (wide) atomicAdd(&hist2[y], 1u);
-    else atomicAdd(&hist2[y >> 1], 1u << ((y & 1u) << 4));
+    const uint32_t w4[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (4 * g + j >= E.shots) break;
+      const uint32_t c = w4[j] & cmask;
+      const uint32_t y = off ^ tbl[0][c & 255] ^ tbl[1][(c >> 8) & 255] ^ tbl[2][(c >> 16) & 255];
+      if (wide) atomicAdd(&hist2[y], 1u);
+      else atomicAdd(&hist2[y >> 1], 1u << ((y & 1u) << 4));
+    }
   }
   __syncthreads();
   auto count = [&](uint32_t y) -> uint32_t {
@@ -903,11 +949,14 @@ cudaError_t launch_clifford(const DevPlan& p, const DevRes& r, const EvalParams&
   }
 }
 
-cudaError_t launch_body(const DevPlan& p, const DevRes& r, cudaStream_t s) {
+cudaError_t launch_body(const DevPlan& p, const DevRes& r, int smem_optin, bool basis, cudaStream_t s) {
   if (p.n_items_body == 0) return cudaSuccess;
-  const size_t smem = (size_t)p.max_body_cols * 8;
-  body_kernel<<<p.n_items_body, 256, smem, s>>>(p, r); note_launch();
-  cudaError_t err = cudaGetLastError();
+  const int words = std::max(p.max_body_cols, std::min(p.max_body_stage_words, smem_optin / 8));
+  cudaError_t err = cudaFuncSetAttribute(body_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, words * 8);
+  if (err != cudaSuccess) return err;
+  body_kernel<<<p.n_items_body, 256, (size_t)words * 8, s>>>(p, r, words); note_launch();
+  err = cudaGetLastError();
+  if (!basis) return err;
   if (err != cudaSuccess || p.n_cliff_frags == 0) return err;
   body_basis_kernel<<<p.n_cliff_frags, 512, 0, s>>>(p, r); note_launch();
   return cudaGetLastError();

@@ -72,6 +72,7 @@ struct DevPlan {
   int n_items_cliff, n_items_nc;
   const int2* items_body;     // (frag, 64-row word) of every Clifford fragment's body
   int n_items_body, max_body_cols;
+  int max_body_stage_words;   // body kernel shared memory with the op stream staged
   const int* cliff_frags;     // every Clifford fragment (shared-row bases)
   int n_cliff_frags;
   const ProblemDev* problems;
@@ -106,6 +107,7 @@ struct EvalParams {
   uint32_t shots, seed_lo, seed_hi;
   int keep_tableaus;
   int shared_body;            // 1: variants start from their fragment's body tableau
+  int screen;                 // 1: the rank screen runs; the tableau kernel takes its queue
   double inv_shots;
 };
 
@@ -119,7 +121,7 @@ long long launch_count();
 // words_per_op: 64-row words of one fused op a thread updates (1, 2, 4 or 8)
 // Body tableau of every Clifford fragment (identity evolved by the gate
 // sequence, no preparations or basis changes), one CTA per 64-row word.
-cudaError_t launch_body(const DevPlan& p, const DevRes& r, cudaStream_t s);
+cudaError_t launch_body(const DevPlan& p, const DevRes& r, int smem_optin, bool basis, cudaStream_t s);
 // Screen of every Clifford variant from its fragment's shared-row basis: a
 // variant whose measured set has full rank (no Z-strings, no tableau kept)
 // is finished here; the others are queued for the tableau kernel.

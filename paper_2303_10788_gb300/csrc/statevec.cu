@@ -66,11 +66,15 @@ __device__ __forceinline__ int digit_out(int v, int qin, int i) {
 }  // namespace
 
 constexpr int kOpStage = 128;   // fused ops staged in shared memory at a time
+constexpr int kZChunk = 256;    // Z-string masks built per pass
 
 __global__ void __launch_bounds__(256) statevector_kernel(DevPlan P, DevRes R, int max_n) {
   extern __shared__ float2 psi[];
   NCOp* ops_s = reinterpret_cast<NCOp*>(psi + (1u << max_n));
   __shared__ int s_item;
+  __shared__ unsigned s_abit[kMaxMeas];     // bit of each A wire in the amplitude index
+  __shared__ unsigned s_zm[kZChunk];        // Z masks of a chunk of Z-strings
+  __shared__ unsigned s_qm[kMaxCuts];       // bit of each quantum output
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   for (;;) {
     if (tid == 0) s_item = (int)atomicAdd(&R.work[1], 1u);
@@ -108,13 +112,16 @@ __global__ void __launch_bounds__(256) statevector_kernel(DevPlan P, DevRes R, i
     }
     // marginal on A: each output sums its completions in index order
     const int nA = F.nA;
+    for (int j = tid; j < nA; j += blockDim.x) s_abit[j] = 1u << P.wires[F.A_off + j];
+    for (int o = tid; o < F.qout; o += blockDim.x) s_qm[o] = 1u << P.wires[F.qout_off + o];
+    __syncthreads();
     unsigned amask = 0;
-    for (int j = 0; j < nA; ++j) amask |= 1u << P.wires[F.A_off + j];
+    for (int j = 0; j < nA; ++j) amask |= s_abit[j];
     float* d = R.dist + F.dist_off + ((long long)v << nA);
     for (unsigned y = tid; y < (1u << nA); y += blockDim.x) {
       unsigned base = 0;
       for (int j = 0; j < nA; ++j)
-        if ((y >> j) & 1u) base |= 1u << P.wires[F.A_off + j];
+        if ((y >> j) & 1u) base |= s_abit[j];
       float acc = 0.f;
       const unsigned rest = (N - 1) & ~amask;
       for (unsigned c = 0;; c = (c - rest) & rest) {     // subsets of `rest`, ascending
@@ -124,22 +131,32 @@ __global__ void __launch_bounds__(256) statevector_kernel(DevPlan P, DevRes R, i
       }
       d[y] = acc;
     }
-    // Z-string values: <Z on (string wires + selected quantum outputs)>
-    const int nzu = F.nz << F.qout;
-    for (int ev = warp; ev < nzu; ev += nwarps) {
-      const int zi = ev >> F.qout, u = ev & ((1 << F.qout) - 1);
-      unsigned zm = 0;
-      for (int q = P.zoffs[F.zw_off + zi]; q < P.zoffs[F.zw_off + zi + 1]; ++q) zm ^= 1u << P.wires[q];
-      for (int o = 0; o < F.qout; ++o)
-        if ((u >> o) & 1) zm ^= 1u << P.wires[F.qout_off + o];
-      float acc = 0.f;
-      for (unsigned x = lane; x < N; x += 32) {
-        const float2 a = psi[x];
-        const float pr = a.x * a.x + a.y * a.y;
-        acc += (__popc(x & zm) & 1) ? -pr : pr;
+    // Z-string values: <Z on (string wires + selected quantum outputs)>; the
+    // strings' masks are built a chunk at a time, one thread per string
+    for (int z0 = 0; z0 < F.nz; z0 += kZChunk) {
+      const int zc = min(kZChunk, F.nz - z0);
+      for (int k = tid; k < zc; k += blockDim.x) {
+        unsigned zm = 0;
+        for (int q = P.zoffs[F.zw_off + z0 + k]; q < P.zoffs[F.zw_off + z0 + k + 1]; ++q) zm ^= 1u << P.wires[q];
+        s_zm[k] = zm;
       }
-      for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) R.zval[F.zval_off + ((long long)v * F.nz + zi) * (1 << F.qout) + u] = acc;
+      __syncthreads();
+      const int nzu = zc << F.qout;
+      for (int ev = warp; ev < nzu; ev += nwarps) {
+        const int k = ev >> F.qout, u = ev & ((1 << F.qout) - 1);
+        unsigned zm = s_zm[k];
+        for (int o = 0; o < F.qout; ++o)
+          if ((u >> o) & 1) zm ^= s_qm[o];
+        float acc = 0.f;
+        for (unsigned x = lane; x < N; x += 32) {
+          const float2 a = psi[x];
+          const float pr = a.x * a.x + a.y * a.y;
+          acc += (__popc(x & zm) & 1) ? -pr : pr;
+        }
+        for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) R.zval[F.zval_off + ((long long)v * F.nz + z0 + k) * (1 << F.qout) + u] = acc;
+      }
+      __syncthreads();
     }
     __syncthreads();
   }

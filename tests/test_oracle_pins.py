@@ -243,3 +243,16 @@ def test_shot_words_keying():
     b = shot_words(8, 1, 2, 3, 10, 21)
     c = shot_words(8, 2, 2, 3, 10, 20)
     assert len(set(a.tolist())) == 8 and not np.array_equal(a, b) and not np.array_equal(a, c)
+
+
+def test_shot_words_layout():
+    """Shot 4k+j is output word j of the generator at counter (k, v, f, c);
+    a ragged shot count takes a prefix (the counter layout is this
+    implementation's choice: the paper fixes none)."""
+    w = shot_words(11, 5, 6, 7, 0xA, 0xB)
+    for k in range(3):
+        out = philox4x32_10(k, 5, 6, 7, 0xA, 0xB)
+        for j in range(4):
+            if 4 * k + j < 11:
+                assert int(w[4 * k + j]) == int(out[j])
+    assert np.array_equal(shot_words(7, 5, 6, 7, 0xA, 0xB), w[:7])
