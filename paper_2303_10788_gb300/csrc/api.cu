@@ -815,6 +815,8 @@ int ccs_eval_variants(ccs_ctx c, ccs_plan p, const ccs_eval_opts* opts, ccs_res*
   if (opts->mode == CCS_SAMPLED && opts->shots == 0) return fail(c, CCS_ERR_INVALID_ARG, "zero shots");
   if (opts->mode == CCS_SAMPLED && opts->shots > 0xffffu && p->max_hub_nA > 15)
     return fail(c, CCS_ERR_UNSUPPORTED, "more than 65535 shots with a 16-bit hub outcome space");
+  if (opts->mode == CCS_SAMPLED && p->max_hub_nA > 16)   // the hub histogram lives in shared memory
+    return fail(c, CCS_ERR_UNSUPPORTED, "hub measured set wider than 16 bits in sampled mode");
   if (c->host_only) return fail(c, CCS_ERR_UNSUPPORTED, "host-only context cannot evaluate");
   cudaSetDevice(c->device);
   ccs_res r = *res;

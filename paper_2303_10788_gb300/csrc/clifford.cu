@@ -806,10 +806,11 @@ __global__ void __launch_bounds__(256) sample_kernel(DevPlan P, DevRes R, EvalPa
 // transposed store Q^T.  Dense counts are written only when kept for
 // inspection.
 __global__ void __launch_bounds__(512) sample_hub_kernel(DevPlan P, DevRes R, EvalParams E, const int2* items,
-                                                         int keep_counts, int wide) {
+                                                         int keep_counts, int wide, int hist_words) {
   extern __shared__ uint32_t hist2[];
   __shared__ uint32_t tbl[3][256];
   __shared__ FragDev sF;
+  __shared__ int s_czD[16], s_czS[16];
   const int2 it = items[blockIdx.x];
   {
     const int* src = reinterpret_cast<const int*>(P.frags + it.x);
@@ -884,7 +885,52 @@ __global__ void __launch_bounds__(512) sample_hub_kernel(DevPlan P, DevRes R, Ev
   const int m = F.m, M = 1 << m, nb = 1 << F.qout;
   const float inv = (float)E.inv_shots;
   float* QT = R.TQ + F.T_off;
-  if (F.qout <= 4 && E.shots <= (1u << 26)) {     // |acc| <= 16 shots fits an int
+  if (!wide && m >= 1 && F.qout <= 4 && E.shots <= (1u << 26)) {
+    // Pairs of outputs (o, o+1) share the packed counter words.  Per pair,
+    // a 16-point Walsh-Hadamard transform over the output bits gives the
+    // signed sum for every sign mask at once; each thread parks it in its
+    // own 33-int slot after the histogram and picks the variant's masks.
+    if ((int)threadIdx.x < (1 << nz)) {
+      int D = Dbase, smask = fixed_mask;
+      for (int i = 0; i < nz; ++i)
+        if ((threadIdx.x >> i) & 1) { D |= 3 << (2 * zpos[i]); smask |= 1 << zout[i]; }
+      s_czD[threadIdx.x] = D;
+      s_czS[threadIdx.x] = smask;
+    }
+    __syncthreads();
+    int* wht = reinterpret_cast<int*>(hist2 + hist_words) + threadIdx.x * 33;   // odd stride: no bank conflicts
+    for (int o2 = threadIdx.x; o2 < (M >> 1); o2 += blockDim.x) {
+      const int o = 2 * o2;
+      int a[16], c[16];
+#pragma unroll
+      for (int b = 0; b < 16; ++b) {
+        const uint32_t w = b < nb ? hist2[((uint32_t)o | ((uint32_t)b << m)) >> 1] : 0u;
+        a[b] = (int)(w & 0xffffu);
+        c[b] = (int)(w >> 16);
+      }
+#pragma unroll
+      for (int h = 1; h < 16; h <<= 1)
+#pragma unroll
+        for (int b = 0; b < 16; ++b)
+          if (!(b & h)) {
+            const int x0 = a[b], y0 = a[b | h], x1 = c[b], y1 = c[b | h];
+            a[b] = x0 + y0;
+            a[b | h] = x0 - y0;
+            c[b] = x1 + y1;
+            c[b | h] = x1 - y1;
+          }
+#pragma unroll
+      for (int b = 0; b < 16; ++b) {
+        wht[b] = a[b];
+        wht[16 + b] = c[b];
+      }
+      for (int cz = 0; cz < (1 << nz); ++cz) {
+        const int sm = s_czS[cz];
+        *reinterpret_cast<float2*>(QT + (long long)s_czD[cz] * M + o) =
+            make_float2((float)wht[sm] * inv, (float)wht[16 + sm] * inv);
+      }
+    }
+  } else if (F.qout <= 4 && E.shots <= (1u << 26)) {     // |acc| <= 16 shots fits an int
     for (int o = threadIdx.x; o < M; o += blockDim.x) {
       int c[16];
 #pragma unroll
@@ -920,10 +966,12 @@ cudaError_t launch_sample_hub(const DevPlan& p, const DevRes& r, const EvalParam
                               int max_nA, int keep_counts, cudaStream_t s) {
   if (n_items == 0 || e.shots == 0) return cudaSuccess;
   const int wide = e.shots > 0xffffu ? 1 : 0;     // 32-bit counters when 16 bits could overflow
-  const size_t smem = (size_t)4 * (wide ? (1 << max_nA) : ((1 << max_nA) > 1 ? (1 << (max_nA - 1)) : 1));
+  const int hist_words = wide ? (1 << max_nA) : ((1 << max_nA) > 1 ? (1 << (max_nA - 1)) : 1);
+  // packed counters, then 33 ints per thread for the transform of the 16-bit path
+  const size_t smem = (size_t)4 * hist_words + (wide ? 0 : (size_t)512 * 33 * 4);
   cudaError_t err = cudaFuncSetAttribute(sample_hub_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  sample_hub_kernel<<<n_items, 512, smem, s>>>(p, r, e, items, keep_counts, wide); note_launch();
+  sample_hub_kernel<<<n_items, 512, smem, s>>>(p, r, e, items, keep_counts, wide, hist_words); note_launch();
   return cudaGetLastError();
 }
 
