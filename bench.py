@@ -191,9 +191,9 @@ def run_ours(args, rank, world, local_rank):
     seed = (SEED[0] + rank, SEED[1])
     ctx = ccs.ccs_create(local_rank)
     plan = ccs.ccs_build_fragments(ctx, ws)
-    infos = []
-    for pi in range(len(ws)):
-        infos += [ccs.ccs_fragment_info_get(ctx, plan, pi, f) for f in range(ccs.ccs_plan_counts(ctx, plan, pi)[0])]
+    prob_infos = [[ccs.ccs_fragment_info_get(ctx, plan, pi, f) for f in range(ccs.ccs_plan_counts(ctx, plan, pi)[0])]
+                  for pi in range(len(ws))]
+    infos = [i for pi in prob_infos for i in pi]
     n_cliff_var = sum(i["n_variants"] for i in infos if i["clifford"])
     units_per_step = n_cliff_var * w.shots
     marg = torch.zeros(sum(1 << len(x.marginal) for x in ws), dtype=torch.float64, device="cuda")
@@ -263,7 +263,7 @@ def run_ours(args, rank, world, local_rank):
     d2h = 8 * sum((1 << len(x.marginal)) + len(x.zstrings) for x in ws)
 
     pk, pk_kind = peaks()
-    roofs = stage_rooflines(stage, w, ws, infos, pk, pk_kind)
+    roofs = stage_rooflines(stage, w, ws, prob_infos, pk, pk_kind, args.precision)
     roof = dict(roofs[dom], stage=dom)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / args.steps, "higher_is_better": True,
@@ -292,48 +292,78 @@ def run_ours(args, rank, world, local_rank):
 N_SM = 152
 
 
-def stage_rooflines(stage, w, ws, infos, pk, pk_kind):
+def stage_rooflines(stage, w, ws, prob_infos, pk, pk_kind, precision):
     """Roofline of every stage: algorithmic work per launch / live duration.
 
-    clifford    alu: each fused 2-qubit Clifford update of one 64-row word is
-                70 64-bit logic ops (4x4 GF(2) map + sign polynomial) =
-                140 32-bit lane ops; peak = SMs x 128 lanes x clock
-    sample      alu: Philox4x32-10 = 20 32x32->64-bit multiplies per shot;
-                peak = SMs x 64 multiplies/clk x clock
-    statevector alu: a fused 4x4 complex op costs 128 FP32 flops per amplitude
-                quad (2x2: 32 per pair); peak = SMs x 128 FMA x 2 x clock
+    Lane-op peak = SMs x 128 lanes x clock (one 32-bit integer/logic op per
+    lane per clock); FP32 peak = SMs x 128 FMA x 2 x clock; HBM peak = the
+    measured copy bandwidth.
+
+    clifford    alu: body evolution, once per Clifford fragment: 140 lane ops
+                per fused op and 64-row word (4x4 GF(2) map + sign polynomial
+                on 64-bit words); per variant, either the rank screen
+                (elimination of n_meas + n_qout + n_qin vectors over n_meas
+                bits, 4 lane ops per vector-bit) or, for problems with
+                Z-strings, the tableau kernel: copy of the (2n+3)W body words
+                plus 8 lane ops per word per Z-string evaluation
+    sample      alu: 25 lane ops per shot (a quarter of one Philox4x32-10 call:
+                10 rounds x 6 ops / 4, + mask, 3 table lookups, 2 xors, atomic)
+                and, for a star's hub, 60 lane ops per output (packed counter
+                loads, 16-point Walsh-Hadamard transform, operand stores)
+    statevector alu: a fused 4x4 complex op costs 32 FP32 flops per amplitude
     fold, operands, recombine
-                hbm: bytes of variant data / tensors read and written once;
-                peak = measured copy bandwidth
+                hbm: fold/operands: variant data read once and fragment
+                tensors written once; recombine: the hub operand read once by
+                the GEMM (plus its BF16 transpose: 4 B read + 2 B written per
+                element) and the leaves' operand
     """
     clk = pk.get("sm_max_mhz", 2070.0) * 1e6
-    cl = [i for i in infos if i["clifford"]]
-    nc = [i for i in infos if not i["clifford"]]
+    lanes = N_SM * 128 * clk
     out = {}
     for st, ms in stage.items():
         t = ms * 1e-3
-        if st == "clifford":
-            ops = sum(i["n_variants"] * i["n_ops"] * 2 * ((i["n_wires"] + 63) // 64) for i in cl)
-            a, p = ops * 140 / t / 1e12, N_SM * 128 * clk / 1e12
-            out[st] = {"bound": "alu", "achieved": a, "peak": p, "unit": "T lane-op/s",
+        if st in ("clifford", "sample"):
+            ops = 0
+            for x, infos in zip(ws, prob_infos):
+                for i in infos:
+                    if not i["clifford"]:
+                        continue
+                    W = 2 * ((i["n_wires"] + 63) // 64)
+                    if st == "clifford":
+                        ops += i["n_ops"] * W * 140
+                        if x.zstrings:
+                            ops += i["n_variants"] * ((2 * i["n_wires"] + 3) * W +
+                                                      8 * W * len(x.zstrings) * (1 << i["n_qout"]))
+                        else:
+                            ops += i["n_variants"] * (i["n_meas"] + i["n_qout"] + i["n_qin"]) * i["n_meas"] * 4
+                    else:
+                        ops += i["n_variants"] * x.shots * 25
+                        if i["n_slots"] == len(x.cuts):   # hub of the star (one slot per cut)
+                            ops += i["n_variants"] * (1 << i["n_marg"]) * 60
+            out[st] = {"bound": "alu", "achieved": ops / t / 1e12, "peak": lanes / 1e12, "unit": "T lane-op/s",
                        "peak_source": f"derived: {N_SM} SMs x 128 lanes x {clk/1e6:.0f} MHz"}
-        elif st == "sample":
-            shots = sum(i["n_variants"] for i in cl) * w.shots
-            a, p = shots * 20 / t / 1e12, N_SM * 64 * clk / 1e12
-            out[st] = {"bound": "alu", "achieved": a, "peak": p, "unit": "T int-mul/s",
-                       "peak_source": f"derived: {N_SM} SMs x 64 IMAD/clk x {clk/1e6:.0f} MHz"}
         elif st == "statevector":
-            fl = sum(i["n_variants"] * i["n_ops"] * 32 * (1 << i["n_wires"]) for i in nc)
-            a, p = fl / t / 1e12, N_SM * 256 * clk / 1e12
-            out[st] = {"bound": "alu", "achieved": a, "peak": p, "unit": "TFLOP/s",
-                       "peak_source": f"derived: {N_SM} SMs x 128 FP32 FMA x 2 x {clk/1e6:.0f} MHz"}
+            fl = sum(i["n_variants"] * i["n_ops"] * 32 * (1 << i["n_wires"])
+                     for infos in prob_infos for i in infos if not i["clifford"])
+            out[st] = {"bound": "alu", "achieved": fl / t / 1e12, "peak": N_SM * 256 * clk / 1e12,
+                       "unit": "TFLOP/s", "peak_source": f"derived: {N_SM} SMs x 128 FP32 FMA x 2 x {clk/1e6:.0f} MHz"}
         else:
-            if st == "recombine":
-                by = sum(4 * (1 << len(x.marginal)) * 4 ** len(x.cuts) for x in ws)   # hub operand read once
-            else:
-                by = sum(i["n_variants"] * 4 * (1 << i["n_meas"]) for i in infos)       # variant data read once
-            a, p = by / t / 1e9, pk["hbm_gbs"]
-            out[st] = {"bound": "hbm", "achieved": a, "peak": p, "unit": "GB/s", "peak_source": pk_kind}
+            by = 0
+            for x, infos in zip(ws, prob_infos):
+                k = len(x.cuts)
+                if st == "recombine":
+                    M = 1 << max([i["n_marg"] for i in infos if i["n_slots"] == k] or [0])
+                    N = (1 << len(x.marginal)) // M
+                    by += (4 ** k) * M * (8 if precision == "bf16" else 4) + (4 ** k) * N * 4
+                else:
+                    for i in infos:
+                        hub = i["n_slots"] == k
+                        if st == "fold" and not (hub and i["clifford"]):
+                            by += i["n_variants"] * 4 * (1 << i["n_meas"]) + 4 * (1 << i["n_marg"]) * 4 ** i["n_slots"]
+                        if st == "operands" and not hub:
+                            by += 8 * (1 << i["n_marg"]) * 4 ** i["n_slots"]
+            out[st] = {"bound": "hbm", "achieved": by / t / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                       "peak_source": pk_kind}
         out[st]["frac"] = out[st]["achieved"] / out[st]["peak"]
         out[st]["traffic"] = None
         out[st]["ms"] = ms
