@@ -600,3 +600,10 @@ def ccs_launch_count():
     L.ccs_launch_count.restype = C.c_longlong
     L.ccs_launch_count.argtypes = []
     return int(L.ccs_launch_count())
+
+
+def load_cut_scorer(ctx, path):
+    """A scorer with the parameters saved by learned_cuts (npz 'params')."""
+    net = ccs_mpnn_create(ctx)
+    ccs_mpnn_set_params(ctx, net, np.load(path)["params"])
+    return net

@@ -172,12 +172,20 @@ void note_launches(long long n) { g_launches.fetch_add(n, std::memory_order_rela
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 }  // namespace ccs
 
+// The learned choice among the greedy candidates the greedy estimate allows
+// (at most 16x the cheapest estimate, at most 16 of them): featurize each,
+// one scorer forward on the GPU, take the smallest predicted log time.
 static int learned_pick(ccs_ctx c, const Problem& P, const std::vector<CutCandidate>& cands, int* pick) {
-  const int nc = (int)std::min<size_t>(cands.size(), 16);
+  std::vector<int> idx;
+  for (int i = 0; i < (int)cands.size() && (int)idx.size() < 16; ++i)
+    if (cands[i].cost <= 16.0 * cands.front().cost) idx.push_back(i);
+  *pick = 0;
+  if (idx.size() < 2) return CCS_OK;
+  const int nc = (int)idx.size();
   std::vector<float> X, val, valt, glob;
   std::vector<int> rowptr{0}, col, goff{0};
   std::string err;
-  for (int i = 0; i < nc; ++i) {
+  for (int i : idx) {
     std::vector<float> x1, v1, vt1, g1;
     std::vector<int> rp1, c1;
     int rc = featurize(P, cands[i].cuts, x1, rp1, c1, v1, vt1, g1, err);
@@ -195,7 +203,7 @@ static int learned_pick(ccs_ctx c, const Problem& P, const std::vector<CutCandid
                     glob.data()};
   std::vector<float> pred(nc);
   if (mpnn_predict(c->cut_model, &b, pred.data()) != CCS_OK) return fail(c, CCS_ERR_CUDA, "cut model forward");
-  *pick = (int)(std::min_element(pred.begin(), pred.end()) - pred.begin());
+  *pick = idx[std::min_element(pred.begin(), pred.end()) - pred.begin()];
   return CCS_OK;
 }
 
@@ -346,8 +354,7 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
         int pick = 0;
         rc = learned_pick(c, P, cands, &pick);
         if (rc != CCS_OK) { delete plan; return rc; }
-        // the greedy estimate judges the pick: far worse estimates are refused
-        if (cands[pick].cost <= 16.0 * cands.front().cost) P.cuts = cands[pick].cuts;
+        P.cuts = cands[pick].cuts;
       }
     }
     int rc = fragment_problem(P, pi, plan->frags, err);
