@@ -1,3 +1,4 @@
+#include <thread>
 #include <atomic>
 // C ABI of the circuit-cutting hot path (declared in include/ccs.h).
 #include <cuda_runtime.h>
@@ -36,6 +37,9 @@ struct ccs_ctx_s {
   int n_ev = 0;
   float stage_ms[8] = {};
   int stage_mask = 0;   // stages recorded by the last profiled call
+  // pinned staging buffer for plan uploads (one host->device copy per batch)
+  char* pinned = nullptr;
+  size_t pinned_bytes = 0;
 };
 
 cudaStream_t ccs::c_stream(ccs_ctx c) { return c->stream; }
@@ -82,19 +86,89 @@ void dfree(ccs_ctx c, void* p, size_t bytes) {
   else cudaFreeAsync(p, c->stream);
 }
 
+// Device memory of one plan or result.  Small requests are carved, 256-byte
+// aligned, out of 1 MiB blocks so a plan or result costs a handful of
+// allocator calls; large ones get their own block.
 struct Allocs {
+  static constexpr size_t kBlock = 1 << 20, kSmall = 128 << 10;
   ccs_ctx ctx = nullptr;
   std::vector<std::pair<void*, size_t>> list;
+  char* cur = nullptr;
+  size_t left = 0;
   template <class T>
   T* get(size_t count) {
-    const size_t bytes = count * sizeof(T);
-    void* p = dalloc(ctx, bytes);
-    if (p) list.push_back({p, bytes});
-    return (T*)p;
+    const size_t bytes = (std::max<size_t>(count * sizeof(T), 1) + 255) & ~(size_t)255;
+    if (bytes > kSmall) {
+      void* p = dalloc(ctx, bytes);
+      if (p) list.push_back({p, bytes});
+      return (T*)p;
+    }
+    if (bytes > left) {
+      void* p = dalloc(ctx, kBlock);
+      if (!p) return nullptr;
+      list.push_back({p, kBlock});
+      cur = (char*)p;
+      left = kBlock;
+    }
+    T* p = (T*)cur;
+    cur += bytes;
+    left -= bytes;
+    return p;
   }
   void release() {
     for (auto& a : list) dfree(ctx, a.first, a.second);
     list.clear();
+    cur = nullptr;
+    left = 0;
+  }
+};
+
+// f(0..n-1) on up to hardware_concurrency host threads (inline for n = 1).
+template <class F>
+void parallel_for(int n, F&& f) {
+  const int T = std::min<int>(n, std::max(1u, std::min(32u, std::thread::hardware_concurrency())));
+  if (T <= 1) {
+    for (int i = 0; i < n; ++i) f(i);
+    return;
+  }
+  std::atomic<int> next{0};
+  std::vector<std::thread> th;
+  for (int t = 0; t < T; ++t)
+    th.emplace_back([&] {
+      for (int i = next.fetch_add(1); i < n; i = next.fetch_add(1)) f(i);
+    });
+  for (auto& x : th) x.join();
+}
+
+// Host arrays gathered into one pinned buffer and sent with one copy.
+struct Staging {
+  struct Item { const void* src; size_t bytes, off; void** out; };
+  std::vector<Item> items;
+  size_t total = 0;
+  template <class T>
+  void add(const std::vector<T>& h, T** out) {
+    const size_t bytes = h.size() * sizeof(T);
+    items.push_back({h.data(), bytes, total, reinterpret_cast<void**>(out)});
+    total += (std::max<size_t>(bytes, 1) + 255) & ~(size_t)255;
+  }
+  bool commit(ccs_ctx c, Allocs& A) {
+    if (items.empty()) return true;
+    char* d = A.get<char>(total);
+    if (!d) return false;
+    // the previous copy out of the staging buffer must be done before reuse
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return false;
+    if (c->pinned_bytes < total) {
+      if (c->pinned) cudaFreeHost(c->pinned);
+      c->pinned = nullptr;
+      c->pinned_bytes = 0;
+      if (cudaMallocHost(&c->pinned, total) != cudaSuccess) return false;
+      c->pinned_bytes = total;
+    }
+    for (auto& it : items) {
+      if (it.bytes) std::memcpy(c->pinned + it.off, it.src, it.bytes);
+      *it.out = d + it.off;
+    }
+    return cudaMemcpyAsync(d, c->pinned, total, cudaMemcpyHostToDevice, c->stream) == cudaSuccess;
   }
 };
 
@@ -287,6 +361,7 @@ void ccs_destroy(ccs_ctx c) {
   if (c->fork_ev) cudaEventDestroy(c->fork_ev);
   if (c->join_ev) cudaEventDestroy(c->join_ev);
   if (c->side) cudaStreamDestroy(c->side);
+  if (c->pinned) cudaFreeHost(c->pinned);
   delete c;
 }
 
@@ -326,11 +401,21 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
   plan->ctx = c;
   plan->A.ctx = c;
   std::string err;
-  for (int pi = 0; pi < n_problems; ++pi) {
+  // Per problem, on host threads: parse, cut search (if asked), fragment
+  // and compile.  Results are joined in problem order, so the plan does not
+  // depend on the thread count.
+  const int np = n_problems;
+  std::vector<Problem> pr(np);
+  std::vector<std::vector<Frag>> pf(np);
+  std::vector<std::vector<CutCandidate>> pc(np);
+  std::vector<int> prc(np, CCS_OK);
+  std::vector<std::string> perr(np);
+  parallel_for(np, [&](int pi) {
     const ccs_problem& q = probs[pi];
-    Problem P;
+    Problem& P = pr[pi];
     P.n_qubits = q.n_qubits;
-    if (q.n_qubits == 0 || (q.n_gates && !q.gates)) { delete plan; return fail(c, CCS_ERR_INVALID_ARG, "empty circuit"); }
+    if (q.n_qubits == 0 || (q.n_gates && !q.gates)) { prc[pi] = CCS_ERR_INVALID_ARG; perr[pi] = "empty circuit"; return; }
+    P.gates.reserve(q.n_gates);
     for (uint32_t g = 0; g < q.n_gates; ++g) {
       const ccs_gate& G = q.gates[g];
       P.gates.push_back({(int)G.op, (int)G.q[0], (G.op == CCS_CX || G.op == CCS_CZ) ? (int)G.q[1] : -1});
@@ -339,27 +424,44 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
     for (uint32_t z = 0; z < q.n_zstrings; ++z)
       P.zstrings.emplace_back(q.zstring_qubits + q.zstring_offsets[z], q.zstring_qubits + q.zstring_offsets[z + 1]);
     if (q.n_cuts >= 0) {
-      if (q.n_cuts > 0 && !q.cuts) { delete plan; return fail(c, CCS_ERR_INVALID_ARG, "null cut list"); }
+      if (q.n_cuts > 0 && !q.cuts) { prc[pi] = CCS_ERR_INVALID_ARG; perr[pi] = "null cut list"; return; }
       P.cuts.assign(q.cuts, q.cuts + q.n_cuts);
-      if ((int)P.cuts.size() > o.max_cuts) { delete plan; return fail(c, CCS_ERR_TOO_MANY_CUTS, "too many cuts"); }
+      if ((int)P.cuts.size() > o.max_cuts) { prc[pi] = CCS_ERR_TOO_MANY_CUTS; perr[pi] = "too many cuts"; return; }
     } else {
       CutSearchOpts so;
       so.max_cuts = std::min(o.max_cuts, kMaxCuts);
       so.max_nc_width = std::min(o.max_nc_width > 0 ? o.max_nc_width : 10, kMaxNCWidth);
-      std::vector<CutCandidate> cands;
-      int rc = greedy_cuts(P, so, cands, err);
-      if (rc != CCS_OK) { delete plan; return fail(c, rc, err); }
-      P.cuts = cands.front().cuts;
-      if (o.use_learned && c->cut_model && cands.size() > 1 && !c->host_only) {
-        int pick = 0;
-        rc = learned_pick(c, P, cands, &pick);
-        if (rc != CCS_OK) { delete plan; return rc; }
-        P.cuts = cands[pick].cuts;
-      }
+      prc[pi] = greedy_cuts(P, so, pc[pi], perr[pi]);
+      if (prc[pi] != CCS_OK) return;
+      P.cuts = pc[pi].front().cuts;
     }
-    int rc = fragment_problem(P, pi, plan->frags, err);
-    if (rc != CCS_OK) { delete plan; return fail(c, rc, "problem " + std::to_string(pi) + ": " + err); }
-    plan->problems.push_back(std::move(P));
+  });
+  for (int pi = 0; pi < np; ++pi)
+    if (prc[pi] != CCS_OK) { delete plan; return fail(c, prc[pi], perr[pi]); }
+  // the learned choice runs the scorer on the GPU: one problem at a time
+  if (o.use_learned && c->cut_model && !c->host_only)
+    for (int pi = 0; pi < np; ++pi)
+      if (pc[pi].size() > 1) {
+        int pick = 0;
+        int rc = learned_pick(c, pr[pi], pc[pi], &pick);
+        if (rc != CCS_OK) { delete plan; return rc; }
+        pr[pi].cuts = pc[pi][pick].cuts;
+      }
+  parallel_for(np, [&](int pi) {
+    prc[pi] = fragment_problem(pr[pi], pi, pf[pi], perr[pi]);
+    if (prc[pi] != CCS_OK) return;
+    for (auto& f : pf[pi]) {
+      if (f.clifford) compile_clifford(f);
+      else compile_nc(f);
+    }
+  });
+  for (int pi = 0; pi < np; ++pi)
+    if (prc[pi] != CCS_OK) { delete plan; return fail(c, prc[pi], "problem " + std::to_string(pi) + ": " + perr[pi]); }
+  for (int pi = 0; pi < np; ++pi) {
+    const int base = (int)plan->frags.size();      // fragment ids become plan-global
+    for (auto& id : pr[pi].frag_ids) id += base;
+    for (auto& f : pf[pi]) plan->frags.push_back(std::move(f));
+    plan->problems.push_back(std::move(pr[pi]));
   }
 
   // --- flatten ---------------------------------------------------------------
@@ -371,10 +473,6 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
   int max_body_stage = 0;
   int max_body_cols = 0;
   std::vector<long long> cost_c, cost_nc;
-  for (auto& f : plan->frags) {
-    if (f.clifford) compile_clifford(f);
-    else compile_nc(f);
-  }
   for (size_t fi = 0; fi < plan->frags.size(); ++fi) {
     Frag& f = plan->frags[fi];
     FragDev d{};
@@ -590,15 +688,13 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
   int *d_fidx_c, *d_fidx_nc, *d_fidx_h, *d_fidx_hn, *d_fidx_o;
   long long *d_tp_c, *d_tzp_c, *d_tp_nc, *d_tzp_nc, *d_tp_h, *d_tp_hn, *d_tp_o, *d_zh, *d_zhn, *d_zo;
   if (!c->host_only) {
-    bool okf = upload(c, plan->A, fidx_c, &d_fidx_c) && upload(c, plan->A, fidx_nc, &d_fidx_nc) &&
-               upload(c, plan->A, tp_c, &d_tp_c) && upload(c, plan->A, tzp_c, &d_tzp_c) &&
-               upload(c, plan->A, tp_nc, &d_tp_nc) && upload(c, plan->A, tzp_nc, &d_tzp_nc) &&
-               upload(c, plan->A, fidx_h, &d_fidx_h) && upload(c, plan->A, fidx_o, &d_fidx_o) &&
-               upload(c, plan->A, tp_h, &d_tp_h) && upload(c, plan->A, tp_o, &d_tp_o) &&
-               upload(c, plan->A, zero_h, &d_zh) && upload(c, plan->A, zero_o, &d_zo) &&
-               upload(c, plan->A, fidx_hn, &d_fidx_hn) && upload(c, plan->A, tp_hn, &d_tp_hn) &&
-               upload(c, plan->A, zero_hn, &d_zhn) && upload(c, plan->A, items_hub, &plan->d_items_hub) &&
-               upload(c, plan->A, items_plain, &plan->d_items_plain);
+    Staging st;
+    st.add(fidx_c, &d_fidx_c); st.add(fidx_nc, &d_fidx_nc); st.add(tp_c, &d_tp_c); st.add(tzp_c, &d_tzp_c);
+    st.add(tp_nc, &d_tp_nc); st.add(tzp_nc, &d_tzp_nc); st.add(fidx_h, &d_fidx_h); st.add(fidx_o, &d_fidx_o);
+    st.add(tp_h, &d_tp_h); st.add(tp_o, &d_tp_o); st.add(zero_h, &d_zh); st.add(zero_o, &d_zo);
+    st.add(fidx_hn, &d_fidx_hn); st.add(tp_hn, &d_tp_hn); st.add(zero_hn, &d_zhn);
+    st.add(items_hub, &plan->d_items_hub); st.add(items_plain, &plan->d_items_plain);
+    bool okf = st.commit(c, plan->A);
     if (!okf) { delete plan; return fail(c, CCS_ERR_OOM, "plan upload failed"); }
     plan->fold_cliff = FoldSet{d_fidx_c, d_tp_c, d_tzp_c, (int)fidx_c.size(), tp_c.back(), tzp_c.back()};
     plan->fold_nc = FoldSet{d_fidx_nc, d_tp_nc, d_tzp_nc, (int)fidx_nc.size(), tp_nc.back(), tzp_nc.back()};
@@ -615,20 +711,15 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
   DevPlan& dp = plan->dp;
   FragDev* dfr; CliffordOp* dco; NCOp* dno; int* dmo; int* dwi; int* dzo; int2* dic; int2* din; int2* dib; int* dcf;
   ProblemDev* dpr; CliffordOp* dpo; CliffordOp* dbo; float* dpm; float* dbm;
-  bool ok = upload(c, plan->A, plan->fdev, &dfr) && upload(c, plan->A, cops, &dco) &&
-            upload(c, plan->A, nops, &dno) && upload(c, plan->A, moments, &dmo) &&
-            upload(c, plan->A, wires, &dwi) && upload(c, plan->A, zoffs, &dzo) &&
-            upload(c, plan->A, items_c, &dic) && upload(c, plan->A, items_nc, &din) &&
-            upload(c, plan->A, items_b, &dib) && upload(c, plan->A, cliff_frags, &dcf) &&
-            upload(c, plan->A, plan->pdev, &dpr) && upload(c, plan->A, prep, &dpo) &&
-            upload(c, plan->A, basis, &dbo) && upload(c, plan->A, prepm, &dpm) &&
-            upload(c, plan->A, basism, &dbm) &&
-            upload(c, plan->A, plan->t_prefix, &plan->d_t_prefix) &&
-            upload(c, plan->A, plan->tz_prefix, &plan->d_tz_prefix) &&
-            upload(c, plan->A, plan->out_prefix, &plan->d_out_prefix) &&
-            upload(c, plan->A, plan->z_prefix, &plan->d_z_prefix) &&
-            upload(c, plan->A, plan->r_prefix, &plan->d_r_prefix) &&
-            upload(c, plan->A, plan->blk_prefix, &plan->d_blk_prefix);
+  Staging st;
+  st.add(plan->fdev, &dfr); st.add(cops, &dco); st.add(nops, &dno); st.add(moments, &dmo); st.add(wires, &dwi);
+  st.add(zoffs, &dzo); st.add(items_c, &dic); st.add(items_nc, &din); st.add(items_b, &dib);
+  st.add(cliff_frags, &dcf); st.add(plan->pdev, &dpr); st.add(prep, &dpo); st.add(basis, &dbo);
+  st.add(prepm, &dpm); st.add(basism, &dbm); st.add(plan->t_prefix, &plan->d_t_prefix);
+  st.add(plan->tz_prefix, &plan->d_tz_prefix); st.add(plan->out_prefix, &plan->d_out_prefix);
+  st.add(plan->z_prefix, &plan->d_z_prefix); st.add(plan->r_prefix, &plan->d_r_prefix);
+  st.add(plan->blk_prefix, &plan->d_blk_prefix);
+  bool ok = st.commit(c, plan->A);
   if (!ok) { delete plan; return fail(c, CCS_ERR_OOM, "plan upload failed"); }
   dp.frags = dfr; dp.cops = dco; dp.nops = dno; dp.moments = dmo; dp.wires = dwi; dp.zoffs = dzo;
   dp.items_cliff = dic; dp.items_nc = din;

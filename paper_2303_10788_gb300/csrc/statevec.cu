@@ -131,32 +131,50 @@ __global__ void __launch_bounds__(256) statevector_kernel(DevPlan P, DevRes R, i
       }
       d[y] = acc;
     }
-    // Z-string values: <Z on (string wires + selected quantum outputs)>; the
-    // strings' masks are built a chunk at a time, one thread per string
-    for (int z0 = 0; z0 < F.nz; z0 += kZChunk) {
-      const int zc = min(kZChunk, F.nz - z0);
-      for (int k = tid; k < zc; k += blockDim.x) {
-        unsigned zm = 0;
-        for (int q = P.zoffs[F.zw_off + z0 + k]; q < P.zoffs[F.zw_off + z0 + k + 1]; ++q) zm ^= 1u << P.wires[q];
-        s_zm[k] = zm;
-      }
-      __syncthreads();
-      const int nzu = zc << F.qout;
-      for (int ev = warp; ev < nzu; ev += nwarps) {
-        const int k = ev >> F.qout, u = ev & ((1 << F.qout) - 1);
-        unsigned zm = s_zm[k];
-        for (int o = 0; o < F.qout; ++o)
-          if ((u >> o) & 1) zm ^= s_qm[o];
-        float acc = 0.f;
-        for (unsigned x = lane; x < N; x += 32) {
-          const float2 a = psi[x];
-          const float pr = a.x * a.x + a.y * a.y;
-          acc += (__popc(x & zm) & 1) ? -pr : pr;
+    // Z-string values <Z_S> = sum_x (-1)^{|x & S|} p(x): the Walsh-Hadamard
+    // transform of the probabilities, in place over the amplitude buffer
+    if (F.nz > 0) {
+      // psi -> p into the low half of the same buffer: block-wide rounds (a
+      // uniform barrier count); round b writes floats [b, b + blockDim), i.e.
+      // amplitudes below b + blockDim, all read before the round's barrier
+      float* pr = reinterpret_cast<float*>(psi);
+      for (unsigned b0 = 0; b0 < N; b0 += blockDim.x) {
+        const unsigned i = b0 + tid;
+        float pv = 0.f;
+        if (i < N) {
+          const float2 a = psi[i];
+          pv = a.x * a.x + a.y * a.y;
         }
-        for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) R.zval[F.zval_off + ((long long)v * F.nz + z0 + k) * (1 << F.qout) + u] = acc;
+        __syncthreads();
+        if (i < N) pr[i] = pv;
+        __syncthreads();
       }
-      __syncthreads();
+      for (int h = 0; h < n; ++h) {
+        for (unsigned t = tid; t < (N >> 1); t += blockDim.x) {
+          const unsigned i0 = insert_zero(t, h), i1 = i0 | (1u << h);
+          const float x0 = pr[i0], x1 = pr[i1];
+          pr[i0] = x0 + x1;
+          pr[i1] = x0 - x1;
+        }
+        __syncthreads();
+      }
+      for (int z0 = 0; z0 < F.nz; z0 += kZChunk) {
+        const int zc = min(kZChunk, F.nz - z0);
+        for (int k = tid; k < zc; k += blockDim.x) {
+          unsigned zm = 0;
+          for (int q = P.zoffs[F.zw_off + z0 + k]; q < P.zoffs[F.zw_off + z0 + k + 1]; ++q) zm ^= 1u << P.wires[q];
+          s_zm[k] = zm;
+        }
+        __syncthreads();
+        for (int ev = tid; ev < (zc << F.qout); ev += blockDim.x) {
+          const int k = ev >> F.qout, u = ev & ((1 << F.qout) - 1);
+          unsigned zm = s_zm[k];
+          for (int o = 0; o < F.qout; ++o)
+            if ((u >> o) & 1) zm ^= s_qm[o];
+          R.zval[F.zval_off + ((long long)v * F.nz + z0 + k) * (1 << F.qout) + u] = pr[zm];
+        }
+        __syncthreads();
+      }
     }
     __syncthreads();
   }
@@ -165,6 +183,7 @@ __global__ void __launch_bounds__(256) statevector_kernel(DevPlan P, DevRes R, i
 cudaError_t launch_statevector(const DevPlan& p, const DevRes& r, int max_n, int threads, int grid,
                                cudaStream_t s) {
   if (p.n_items_nc == 0) return cudaSuccess;
+
   const size_t smem = ((size_t)8 << max_n) + (size_t)kOpStage * sizeof(NCOp);
   cudaError_t err = cudaFuncSetAttribute(statevector_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);

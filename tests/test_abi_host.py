@@ -126,3 +126,19 @@ def test_host_only_context_cannot_evaluate(hctx):
     with pytest.raises(ccs.CCSError) as e:
         ccs.ccs_eval_variants(hctx, plan)
     assert "UNSUPPORTED" in str(e.value)
+
+
+def test_batched_plan_equals_single_plans():
+    """Problems planned together (on host threads) give the same fragments
+    as each problem planned alone."""
+    from workloads import config4
+    hctx = ccs.ccs_create(-1)
+    ws = config4(64)[:16]
+    plan = ccs.ccs_build_fragments(hctx, ws)
+    for pi, w in enumerate(ws):
+        one = ccs.ccs_build_fragments(hctx, [w])
+        assert ccs.ccs_plan_counts(hctx, plan, pi) == ccs.ccs_plan_counts(hctx, one, 0)
+        nf, _ = ccs.ccs_plan_counts(hctx, one, 0)
+        for f in range(nf):
+            assert ccs.ccs_fragment_info_get(hctx, plan, pi, f) == ccs.ccs_fragment_info_get(hctx, one, 0, f)
+            assert ccs.ccs_fragment_wires(hctx, plan, pi, f) == ccs.ccs_fragment_wires(hctx, one, 0, f)
