@@ -199,15 +199,18 @@ def run_ours(args, rank, world, local_rank):
     marg = torch.zeros(sum(1 << len(x.marginal) for x in ws), dtype=torch.float64, device="cuda")
     zexp = torch.zeros(max(1, sum(len(x.zstrings) for x in ws)), dtype=torch.float64, device="cuda")
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")      # > 129 MB L2
+    if args.plain:
+        args.precision = "fp32"
     prec = ccs.CCS_BF16 if args.precision == "bf16" else ccs.CCS_FP32
-    pvb = bool(args.per_variant_body)
+    pvb = bool(args.per_variant_body or args.plain)
+    graph = not args.plain
     res = ccs.ccs_eval_variants(ctx, plan, mode=ccs.CCS_SAMPLED, shots=w.shots, seed_lo=seed[0],
-                                seed_hi=seed[1], use_graph=True, autotune=args.autotune, per_variant_body=pvb)
+                                seed_hi=seed[1], use_graph=graph, autotune=args.autotune and not args.plain, per_variant_body=pvb)
     tuning = ccs.ccs_get_tuning(ctx, res)
 
     def step():
         ccs.ccs_eval_variants(ctx, plan, mode=ccs.CCS_SAMPLED, shots=w.shots, seed_lo=seed[0],
-                              seed_hi=seed[1], use_graph=True, res=res, per_variant_body=pvb)
+                              seed_hi=seed[1], use_graph=graph, res=res, per_variant_body=pvb)
         ccs.ccs_recombine(ctx, plan, res, precision=prec, marginal_out=marg, zexp_out=zexp)
 
     for _ in range(max(3, args.warmup)):
@@ -271,7 +274,8 @@ def run_ours(args, rank, world, local_rank):
             "config": {"workload": describe(ws), "variant_shots_per_step": units_per_step,
                        "l2": "flushed between steps (512 MB write, outside the step events)",
                        "parallelism": f"{world} independent replicas (no collective)",
-                       "launch": "one CUDA-graph replay (eval) + recombination per step",
+                       "launch": ("plain: per-variant simulation, stream launches" if args.plain else
+                                  "one CUDA-graph replay (eval) + recombination per step"),
                        "recombination": args.precision + (" (tcgen05 where eligible)" if args.precision == "bf16" else
                                                           " (CUDA-core FMA)"),
                        "tuning": {"threads": tuning[0], "words_per_op": tuning[1], "shots_per_cta": tuning[2],
@@ -383,6 +387,8 @@ def main():
     ap.add_argument("--autotune", action="store_true", help="tune launch shapes on the plan before timing")
     ap.add_argument("--per-variant-body", action="store_true",
                     help="simulate every variant's whole circuit (no shared fragment body)")
+    ap.add_argument("--plain", action="store_true",
+                    help="the plain GPU form: per-variant simulation, no CUDA graph, FP32, no autotuning")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", args.gpus if args.gpus == 1 else 1))

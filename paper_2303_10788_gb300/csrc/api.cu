@@ -126,7 +126,12 @@ struct Allocs {
 // f(0..n-1) on up to hardware_concurrency host threads (inline for n = 1).
 template <class F>
 void parallel_for(int n, F&& f) {
-  const int T = std::min<int>(n, std::max(1u, std::min(32u, std::thread::hardware_concurrency())));
+  if (n <= 1) {
+    if (n == 1) f(0);
+    return;
+  }
+  static const unsigned hw = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+  const int T = std::min<int>(n, (int)hw);
   if (T <= 1) {
     for (int i = 0; i < n; ++i) f(i);
     return;
