@@ -211,7 +211,7 @@ def run_ours(args, rank, world, local_rank):
     def step():
         ccs.ccs_eval_variants(ctx, plan, mode=ccs.CCS_SAMPLED, shots=w.shots, seed_lo=seed[0],
                               seed_hi=seed[1], use_graph=graph, res=res, per_variant_body=pvb)
-        ccs.ccs_recombine(ctx, plan, res, precision=prec, marginal_out=marg, zexp_out=zexp)
+        ccs.ccs_recombine(ctx, plan, res, precision=prec, marginal_out=marg, zexp_out=zexp, use_graph=graph)
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -275,7 +275,7 @@ def run_ours(args, rank, world, local_rank):
                        "l2": "flushed between steps (512 MB write, outside the step events)",
                        "parallelism": f"{world} independent replicas (no collective)",
                        "launch": ("plain: per-variant simulation, stream launches" if args.plain else
-                                  "one CUDA-graph replay (eval) + recombination per step"),
+                                  "two CUDA-graph replays per step (evaluation, recombination)"),
                        "recombination": args.precision + (" (tcgen05 where eligible)" if args.precision == "bf16" else
                                                           " (CUDA-core FMA)"),
                        "tuning": {"threads": tuning[0], "words_per_op": tuning[1], "shots_per_cta": tuning[2],

@@ -200,6 +200,9 @@ typedef struct {
   int32_t outputs_on_device;  /* 1: marginal_out / zexp_out are device pointers */
   int32_t no_tensor_cores;    /* 1: BF16 contractions on CUDA cores even where the
                                  tcgen05 GEMM applies (0: use it, the default) */
+  int32_t use_graph;          /* 1: capture the contraction launches in a CUDA graph
+                                 kept on the result (per precision and tensor-core
+                                 choice) and replay it */
 } ccs_recomb_opts;
 
 /* p(o) = 2^-k sum_{P in {I,X,Y,Z}^k} prod_f T_f(o_f, P|f) for every problem,

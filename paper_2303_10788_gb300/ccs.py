@@ -68,7 +68,8 @@ class ccs_eval_opts(C.Structure):
 
 
 class ccs_recomb_opts(C.Structure):
-    _fields_ = [("precision", C.c_int32), ("outputs_on_device", C.c_int32), ("no_tensor_cores", C.c_int32)]
+    _fields_ = [("precision", C.c_int32), ("outputs_on_device", C.c_int32), ("no_tensor_cores", C.c_int32),
+                ("use_graph", C.c_int32)]
 
 
 class ccs_fragment_info(C.Structure):
@@ -306,13 +307,14 @@ def ccs_eval_variants(ctx, plan, mode=CCS_SAMPLED, shots=1024, seed_lo=0x1234, s
     return Res(ctx, plan, h)
 
 
-def ccs_recombine(ctx, plan, res, precision=CCS_FP32, marginal_out=None, zexp_out=None, tensor_cores=True):
+def ccs_recombine(ctx, plan, res, precision=CCS_FP32, marginal_out=None, zexp_out=None, tensor_cores=True,
+                  use_graph=False):
     """Host mode (default): returns (marginal, zexp) float64 numpy arrays with
     all problems back to back.  Device mode: pass torch float64 CUDA tensors
     as ``marginal_out`` / ``zexp_out``; the call does not synchronise."""
     on_dev = marginal_out is not None and hasattr(marginal_out, "data_ptr")
     if on_dev:
-        opts = ccs_recomb_opts(precision, 1, 0 if tensor_cores else 1)
+        opts = ccs_recomb_opts(precision, 1, 0 if tensor_cores else 1, int(use_graph))
         ctx.check(lib().ccs_recombine(ctx.h, plan.h, res.h, C.byref(opts),
                                       C.c_void_p(marginal_out.data_ptr()),
                                       C.c_void_p(zexp_out.data_ptr() if zexp_out is not None else None)),
@@ -322,7 +324,7 @@ def ccs_recombine(ctx, plan, res, precision=CCS_FP32, marginal_out=None, zexp_ou
     nz = sum(len(getattr(p, "zstrings", []) or []) for p in plan.problems)
     marg = np.zeros(max(nm, 1))
     zexp = np.zeros(max(nz, 1))
-    opts = ccs_recomb_opts(precision, 0, 0 if tensor_cores else 1)
+    opts = ccs_recomb_opts(precision, 0, 0 if tensor_cores else 1, int(use_graph))
     ctx.check(lib().ccs_recombine(ctx.h, plan.h, res.h, C.byref(opts),
                                   marg.ctypes.data_as(C.c_void_p), zexp.ctypes.data_as(C.c_void_p)),
               "ccs_recombine")

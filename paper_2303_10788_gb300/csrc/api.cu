@@ -203,7 +203,9 @@ struct ccs_plan_s {
   std::vector<long long> t_prefix, tz_prefix, out_prefix, z_prefix, r_prefix, blk_prefix;
   long long* d_r_prefix = nullptr;
   long long* d_blk_prefix = nullptr;
-  long long r_total = 0, part_total = 0, gemm_blocks = 0, rt_total = 0;
+  long long r_total = 0, part_total = 0, gemm_blocks = 0, rt_total = 0, small_blocks = 0;
+  std::vector<long long> s_prefix;
+  long long* d_s_prefix = nullptr;
   int max_tile_smem = 0;
   long long* d_t_prefix = nullptr;
   long long* d_tz_prefix = nullptr;
@@ -229,6 +231,9 @@ struct ccs_res_s {
   Allocs A;
   cudaGraphExec_t graph = nullptr;
   long long graph_launches = 0;   // kernel nodes of the captured graph
+  cudaGraphExec_t rgraph = nullptr;   // recombination graph
+  int rgraph_key = -1;
+  long long rgraph_launches = 0;
   EvalParams graph_key{};
   int graph_valid = 0;
   int cliff_threads = 256;
@@ -238,6 +243,7 @@ struct ccs_res_s {
   uint16_t* rt_scratch = nullptr;   // bf16 R'^T of tensor-core-eligible problems
   ~ccs_res_s() {
     if (graph) cudaGraphExecDestroy(graph);
+    if (rgraph) cudaGraphExecDestroy(rgraph);
     A.release();
   }
 };
@@ -586,6 +592,7 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
   plan->z_prefix.push_back(0);
   plan->r_prefix.push_back(0);
   plan->blk_prefix.push_back(0);
+  plan->s_prefix.push_back(0);
   for (auto& f : plan->fdev) {
     plan->t_prefix.push_back(plan->t_prefix.back() + (1ll << f.m) * (1ll << (2 * f.n_slots)));
     plan->tz_prefix.push_back(plan->tz_prefix.back() + (long long)f.nz * (1ll << (2 * f.n_slots)));
@@ -659,19 +666,29 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
       d.TM = std::min(up4(d.M), 4096 / d.TN);                 // at most 256 threads
       d.mtiles = (d.M + d.TM - 1) / d.TM;
       d.ntiles = (d.N + d.TN - 1) / d.TN;
-      const long long base = (long long)d.mtiles * d.ntiles;
-      const int target = 2 * std::max(c->sm_count, 148);
-      const long long max_splits = std::max(1ll, d.K / 32);
-      d.splits = (int)std::max(1ll, std::min(max_splits, (target + base - 1) / base));
-      d.r_off = plan->r_total;
-      plan->r_total += d.K * d.N;
-      d.part_off = plan->part_total;
-      plan->part_total += (long long)d.splits * d.M * d.N;
-      d.blk_off = plan->gemm_blocks;
-      plan->gemm_blocks += base * d.splits;
-      plan->max_tile_smem = std::max(plan->max_tile_smem, 16 * (d.TM + d.TN) * 4);
       d.hub_T_off = plan->fdev[f0 + P.hub].T_off;
       d.tc = (gemm_tc_supported(d.M, d.N, d.K) && d.K >= 4096 && d.M >= 128) ? 1 : 0;
+      // small stars: one pass, R formed on the fly (no R, no split-K partials)
+      d.small = (!d.tc && d.K <= 4096) ? 1 : 0;
+      if (d.small) {
+        d.stn = std::min(up4(d.N), 64);
+        d.stm = std::min(up4(d.M), 4096 / d.stn);
+        d.smt = (d.M + d.stm - 1) / d.stm;
+        d.snt = (d.N + d.stn - 1) / d.stn;
+        plan->small_blocks += (long long)d.smt * d.snt;
+      } else {
+        const long long base = (long long)d.mtiles * d.ntiles;
+        const int target = 2 * std::max(c->sm_count, 148);
+        const long long max_splits = std::max(1ll, d.K / 32);
+        d.splits = (int)std::max(1ll, std::min(max_splits, (target + base - 1) / base));
+        d.r_off = plan->r_total;
+        plan->r_total += d.K * d.N;
+        d.part_off = plan->part_total;
+        plan->part_total += (long long)d.splits * d.M * d.N;
+        d.blk_off = plan->gemm_blocks;
+        plan->gemm_blocks += base * d.splits;
+        plan->max_tile_smem = std::max(plan->max_tile_smem, 16 * (d.TM + d.TN) * 4);
+      }
       if (d.tc) {
         d.rt_off = (plan->rt_total + 63) & ~63ll;
         plan->rt_total = d.rt_off + d.K * d.N;
@@ -679,6 +696,7 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
     }
     plan->r_prefix.push_back(plan->r_total);
     plan->blk_prefix.push_back(plan->gemm_blocks);
+    plan->s_prefix.push_back(plan->small_blocks);
     f0 += d.n_frags;
     plan->pdev.push_back(d);
   }
@@ -723,7 +741,7 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
   st.add(prepm, &dpm); st.add(basism, &dbm); st.add(plan->t_prefix, &plan->d_t_prefix);
   st.add(plan->tz_prefix, &plan->d_tz_prefix); st.add(plan->out_prefix, &plan->d_out_prefix);
   st.add(plan->z_prefix, &plan->d_z_prefix); st.add(plan->r_prefix, &plan->d_r_prefix);
-  st.add(plan->blk_prefix, &plan->d_blk_prefix);
+  st.add(plan->blk_prefix, &plan->d_blk_prefix); st.add(plan->s_prefix, &plan->d_s_prefix);
   bool ok = st.commit(c, plan->A);
   if (!ok) { delete plan; return fail(c, CCS_ERR_OOM, "plan upload failed"); }
   dp.frags = dfr; dp.cops = dco; dp.nops = dno; dp.moments = dmo; dp.wires = dwi; dp.zoffs = dzo;
@@ -1051,13 +1069,48 @@ int ccs_recombine(ccs_ctx c, ccs_plan p, ccs_res r, const ccs_recomb_opts* opts,
   const bool on_dev = opts && opts->outputs_on_device;
   if (prec != CCS_FP32 && prec != CCS_BF16) return fail(c, CCS_ERR_INVALID_ARG, "bad precision");
   cudaSetDevice(c->device);
-  stage_begin(c, ST_RECOMB);
+  const bool tc = !(opts && opts->no_tensor_cores);
   RecombSizes rz{p->r_total, p->part_total, p->gemm_blocks, p->n_marg, p->n_zexp,
                  p->d_r_prefix, p->d_blk_prefix, p->d_out_prefix, p->d_z_prefix, p->max_tile_smem,
-                 (opts && opts->no_tensor_cores) ? nullptr : p->pdev.data(), (int)p->pdev.size(), r->rt_scratch};
-  cudaError_t e = launch_recombine(p->dp, r->dr, prec, rz, r->scratch, r->dr.marg, r->dr.zexp, c->stream);
-  if (e != cudaSuccess) return cuda_fail(c, e, "recombine kernel");
-  stage_end(c, ST_RECOMB);
+                 tc ? p->pdev.data() : nullptr, (int)p->pdev.size(), r->rt_scratch, p->small_blocks,
+                 p->d_s_prefix};
+  cudaError_t e;
+  if (opts && opts->use_graph && !c->profiling) {
+    const int key = prec * 2 + (tc ? 1 : 0);
+    if (!r->rgraph || r->rgraph_key != key) {
+      if (r->rgraph) { cudaGraphExecDestroy(r->rgraph); r->rgraph = nullptr; }
+      cudaStream_t s = c->stream;
+      bool tmp_stream = false;
+      if (s == nullptr) {   // the legacy stream cannot be captured
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return fail(c, CCS_ERR_CUDA, "stream");
+        tmp_stream = true;
+      }
+      cudaGraph_t g;
+      if ((e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+        if (tmp_stream) cudaStreamDestroy(s);
+        return cuda_fail(c, e, "begin capture");
+      }
+      const long long before = launch_count();
+      cudaError_t le = launch_recombine(p->dp, r->dr, prec, rz, r->scratch, r->dr.marg, r->dr.zexp, s);
+      r->rgraph_launches = launch_count() - before;
+      note_launches(-r->rgraph_launches);      // captured, not launched
+      e = cudaStreamEndCapture(s, &g);
+      if (tmp_stream) cudaStreamDestroy(s);
+      if (le != cudaSuccess) return cuda_fail(c, le, "recombine kernel");
+      if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
+      e = cudaGraphInstantiate(&r->rgraph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
+      r->rgraph_key = key;
+    }
+    if ((e = cudaGraphLaunch(r->rgraph, c->stream)) != cudaSuccess) return cuda_fail(c, e, "graph launch");
+    note_launches(r->rgraph_launches);
+  } else {
+    stage_begin(c, ST_RECOMB);
+    e = launch_recombine(p->dp, r->dr, prec, rz, r->scratch, r->dr.marg, r->dr.zexp, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "recombine kernel");
+    stage_end(c, ST_RECOMB);
+  }
   const cudaMemcpyKind kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   if (marginal_out && p->n_marg)
     if ((e = cudaMemcpyAsync(marginal_out, r->dr.marg, p->n_marg * sizeof(double), kind, c->stream)) != cudaSuccess)
@@ -1275,7 +1328,7 @@ extern "C" int ccs_recombine_noalloc(ccs_ctx c, ccs_plan p, ccs_res r, int preci
   }
   RecombSizes rz{p->r_total, p->part_total, p->gemm_blocks, p->n_marg, p->n_zexp,
                  p->d_r_prefix, p->d_blk_prefix, p->d_out_prefix, p->d_z_prefix, p->max_tile_smem,
-                 nullptr, 0, nullptr};
+                 nullptr, 0, nullptr, p->small_blocks, p->d_s_prefix};
   e = launch_recombine(p->dp, r->dr, precision, rz, g_noalloc_addr[c->device], marginal_out, zexp_out, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "recombine kernel");
   return CCS_OK;

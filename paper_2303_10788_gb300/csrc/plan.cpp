@@ -53,11 +53,11 @@ void chp_planes(int op, int ra, int rb, uint32_t x[2], uint32_t z[2], uint32_t& 
   }
 }
 
-// (M, anf) of a gate word acting on roles 0 (= a) and 1 (= b).
-CliffordOp clifford_from_word(const std::vector<std::array<int, 3>>& word) {
-  // pattern v: x_a = bit 0, z_a = bit 1, x_b = bit 2, z_b = bit 3 of v
-  uint32_t x[2] = {0xaaaau, 0xf0f0u}, z[2] = {0xccccu, 0xff00u}, flip = 0;
-  for (auto& g : word) chp_planes(g[0], g[1], g[2] < 0 ? 1 - g[1] : g[2], x, z, flip);
+// Identity planes: pattern v has x_a = bit 0, z_a = bit 1, x_b = bit 2, z_b = bit 3 of v.
+constexpr uint32_t kPX0 = 0xaaaau, kPX1 = 0xf0f0u, kPZ0 = 0xccccu, kPZ1 = 0xff00u;
+
+// (M, anf) of the Clifford update given by its 16-pattern planes.
+CliffordOp clifford_from_planes(const uint32_t x[2], const uint32_t z[2], uint32_t flip) {
   int u[16], f[16];
   for (int v = 0; v < 16; ++v) {
     u[v] = (int)(((x[0] >> v) & 1u) | (((z[0] >> v) & 1u) << 1) | (((x[1] >> v) & 1u) << 2) |
@@ -76,6 +76,13 @@ CliffordOp clifford_from_word(const std::vector<std::array<int, 3>>& word) {
   for (int s = 0; s < 16; ++s)
     if (a[s]) op.anf |= (uint16_t)(1u << s);
   return op;
+}
+
+// (M, anf) of a gate word acting on roles 0 (= a) and 1 (= b).
+CliffordOp clifford_from_word(const std::vector<std::array<int, 3>>& word) {
+  uint32_t x[2] = {kPX0, kPX1}, z[2] = {kPZ0, kPZ1}, flip = 0;
+  for (auto& g : word) chp_planes(g[0], g[1], g[2] < 0 ? 1 - g[1] : g[2], x, z, flip);
+  return clifford_from_planes(x, z, flip);
 }
 
 using cd = std::complex<double>;
@@ -124,14 +131,22 @@ void gate_matrix_2(int op, int ra, int rb, cd m[16]) {
     }
 }
 
+// A fused op: statevector fragments keep the gate word (for the unitary);
+// Clifford fragments apply each gate to the op's 16-pattern planes as it
+// arrives, so no word is stored.
 struct Fused {
   int a, b;                                   // b < 0: one-qubit op
-  std::vector<std::array<int, 3>> word;       // (op, role_a, role_b)
+  std::vector<std::array<int, 3>> word;       // (op, role_a, role_b), statevector fragments only
+  uint32_t px[2] = {kPX0, kPX1}, pz[2] = {kPZ0, kPZ1}, pf = 0;
   bool dead = false;
+  void add(int op, int ra, int rb, bool planes) {
+    if (planes) chp_planes(op, ra, rb < 0 ? 1 - ra : rb, px, pz, pf);
+    else word.push_back({op, ra, rb});
+  }
 };
 
 // Fuse consecutive gates per qubit (pair) and assign ASAP moments.
-std::vector<std::vector<const Fused*>> fuse_and_layer(const Frag& f, std::vector<Fused>& ops) {
+std::vector<std::vector<const Fused*>> fuse_and_layer(const Frag& f, std::vector<Fused>& ops, bool planes) {
   const int n = f.n();
   std::vector<int> last(n, -1);
   for (auto& g : f.gates) {
@@ -139,9 +154,10 @@ std::vector<std::vector<const Fused*>> fuse_and_layer(const Frag& f, std::vector
     if (!is_two_qubit(op)) {
       if (last[a] >= 0) {
         Fused& F = ops[last[a]];
-        F.word.push_back({op, F.a == a ? 0 : 1, -1});
+        F.add(op, F.a == a ? 0 : 1, -1, planes);
       } else {
-        ops.push_back({a, -1, {{op, 0, -1}}});
+        ops.push_back(Fused{a, -1});
+        ops.back().add(op, 0, -1, planes);
         last[a] = (int)ops.size() - 1;
       }
       continue;
@@ -150,19 +166,40 @@ std::vector<std::vector<const Fused*>> fuse_and_layer(const Frag& f, std::vector
     if (la >= 0 && la == lb) {
       Fused& F = ops[la];
       int ra = F.a == a ? 0 : 1;
-      F.word.push_back({op, ra, 1 - ra});
+      F.add(op, ra, 1 - ra, planes);
       continue;
     }
-    Fused nf{a, b, {}};
+    Fused nf{a, b};
+    const Fused* g1[2] = {nullptr, nullptr};
     for (int side = 0; side < 2; ++side) {
       int lq = side == 0 ? la : lb;
       if (lq >= 0 && ops[lq].b < 0) {     // absorb a trailing one-qubit op
-        for (auto& w : ops[lq].word) nf.word.push_back({w[0], side, -1});
+        if (!planes)
+          for (auto& w : ops[lq].word) nf.word.push_back({w[0], side, -1});
+        g1[side] = &ops[lq];
         ops[lq].dead = true;
-        ops[lq].word.clear();
       }
     }
-    nf.word.push_back({op, 0, 1});
+    if (planes && (g1[0] || g1[1])) {   // nf = (g1[0] on role 0) x (g1[1] on role 1), then the gate
+      uint32_t x[2] = {0, 0}, z[2] = {0, 0}, fl = 0;
+      for (int v = 0; v < 16; ++v)
+        for (int side = 0; side < 2; ++side) {
+          const int w = (v >> (2 * side)) & 3;            // this role's (x, z) as a one-qubit pattern
+          unsigned xo = w & 1, zo = (w >> 1) & 1, fo = 0;
+          if (g1[side]) {
+            xo = (g1[side]->px[0] >> w) & 1u;
+            zo = (g1[side]->pz[0] >> w) & 1u;
+            fo = (g1[side]->pf >> w) & 1u;
+          }
+          x[side] |= xo << v;
+          z[side] |= zo << v;
+          fl ^= fo << v;
+        }
+      nf.px[0] = x[0]; nf.px[1] = x[1]; nf.pz[0] = z[0]; nf.pz[1] = z[1]; nf.pf = fl;
+    }
+    for (int side = 0; side < 2; ++side)
+      if (g1[side]) const_cast<Fused*>(g1[side])->word.clear();
+    nf.add(op, 0, 1, planes);
     ops.push_back(nf);
     last[a] = last[b] = (int)ops.size() - 1;
   }
@@ -315,13 +352,13 @@ int fragment_problem(Problem& p, int pi, std::vector<Frag>& out, std::string& er
 void compile_clifford(Frag& f) {
   std::vector<Fused> ops;
   ops.reserve(f.gates.size());
-  auto layers = fuse_and_layer(f, ops);
+  auto layers = fuse_and_layer(f, ops, true);
   f.cops.clear();
   f.moment_start.assign(1, 0);
   const uint16_t dummy = (uint16_t)f.n();
   for (auto& L : layers) {
     for (auto* F : L) {
-      CliffordOp op = clifford_from_word(F->word);
+      CliffordOp op = clifford_from_planes(F->px, F->pz, F->pf);
       op.qa = (uint16_t)F->a;
       op.qb = F->b >= 0 ? (uint16_t)F->b : dummy;
       f.cops.push_back(op);
@@ -333,7 +370,7 @@ void compile_clifford(Frag& f) {
 void compile_nc(Frag& f) {
   std::vector<Fused> ops;
   ops.reserve(f.gates.size());
-  auto layers = fuse_and_layer(f, ops);
+  auto layers = fuse_and_layer(f, ops, false);
   f.nops.clear();
   f.moment_start.assign(1, 0);
   for (auto& L : layers) {

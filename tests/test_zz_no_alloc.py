@@ -36,17 +36,19 @@ def test_noalloc_matches_recombine_twice(ctx, make):
 
 def test_noalloc_rejects_plans_beyond_its_scratch(ctx):
     import torch
-    # three leaves carrying the whole 12-qubit marginal and 6 cuts: the
-    # Kronecker operand alone is 4^6 x 2^12 floats (64 MiB) > 8 MiB
-    regs = [Region([0, 1, 2, 3], 4, 2, 6, [0, 1, 2, 3], 1),
-            Region([10, 11, 12, 13], 14, 2, 6, [10, 11, 12, 13], 1),
-            Region([20, 21, 22, 23], 24, 2, 6, [20, 21, 22, 23], 1)]
-    c, cuts = brickwork_star(30, 9, regs, seed=1)
-    w = Workload("big", c, cuts, [0, 1, 2, 3, 10, 11, 12, 13, 20, 21, 22, 23], [], 256, 1)
+    # four leaves carrying the whole 12-qubit marginal and 8 cuts: the
+    # Kronecker operand alone is 4^8 x 2^12 floats (1 GiB) > 8 MiB (stars with
+    # K <= 4096 are contracted in one pass and need no scratch at all)
+    regs = [Region([0, 1, 2], 3, 2, 6, [0, 1, 2], 1),
+            Region([10, 11, 12], 13, 2, 6, [10, 11, 12], 1),
+            Region([20, 21, 22], 23, 2, 6, [20, 21, 22], 1),
+            Region([30, 31, 32], 33, 2, 6, [30, 31, 32], 1)]
+    c, cuts = brickwork_star(40, 9, regs, seed=1)
+    w = Workload("big", c, cuts, [0, 1, 2, 10, 11, 12, 20, 21, 22, 30, 31, 32], [], 256, 1)
     plan = ccs.ccs_build_fragments(ctx, [w])
     nf, nc = ccs.ccs_plan_counts(ctx, plan, 0)
     slots = [ccs.ccs_fragment_info_get(ctx, plan, 0, f)["n_slots"] for f in range(nf)]
-    assert nc == 6 and max(slots) == 6          # a star: the body carries every cut
+    assert nc == 8 and max(slots) == 8          # a star: the body carries every cut
     res = ccs.ccs_eval_variants(ctx, plan, mode=ccs.CCS_SAMPLED, shots=256)
     m = torch.zeros(1 << 12, dtype=torch.float64, device="cuda")
     with pytest.raises(ccs.CCSError) as e:
