@@ -203,7 +203,7 @@ struct ccs_plan_s {
   std::vector<long long> t_prefix, tz_prefix, out_prefix, z_prefix, r_prefix, blk_prefix;
   long long* d_r_prefix = nullptr;
   long long* d_blk_prefix = nullptr;
-  long long r_total = 0, part_total = 0, gemm_blocks = 0, rt_total = 0, small_blocks = 0;
+  long long r_total = 0, part_total = 0, gemm_blocks = 0, rt_total = 0;
   std::vector<long long> s_prefix;
   long long* d_s_prefix = nullptr;
   int max_tile_smem = 0;
@@ -481,7 +481,7 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
   std::vector<int> moments, wires, zoffs;
   std::vector<int2> items_c, items_nc, items_b;
   std::vector<int> cliff_frags;
-  int max_body_stage = 0;
+  int max_body_stage = 0, max_moment_ops = 1;
   int max_body_cols = 0;
   std::vector<long long> cost_c, cost_nc;
   for (size_t fi = 0; fi < plan->frags.size(); ++fi) {
@@ -541,6 +541,8 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
         d.rb_off = -1;
       }
       max_body_stage = std::max(max_body_stage, 2 * d.n + 3 + (int)f.cops.size() + (d.n_moments + 2) / 2 + 1);
+      for (int mm = 0; mm < f.n_moments(); ++mm)
+        max_moment_ops = std::max(max_moment_ops, f.moment_start[mm + 1] - f.moment_start[mm]);
       for (int w = 0; w < d.W; ++w) items_b.push_back(make_int2((int)fi, w));
       max_body_cols = std::max(max_body_cols, 2 * d.n + 3);
       const int words = (2 * d.n + 3) * d.W + (d.n + 1) / 2 + 2;
@@ -592,7 +594,6 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
   plan->z_prefix.push_back(0);
   plan->r_prefix.push_back(0);
   plan->blk_prefix.push_back(0);
-  plan->s_prefix.push_back(0);
   for (auto& f : plan->fdev) {
     plan->t_prefix.push_back(plan->t_prefix.back() + (1ll << f.m) * (1ll << (2 * f.n_slots)));
     plan->tz_prefix.push_back(plan->tz_prefix.back() + (long long)f.nz * (1ll << (2 * f.n_slots)));
@@ -668,27 +669,17 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
       d.ntiles = (d.N + d.TN - 1) / d.TN;
       d.hub_T_off = plan->fdev[f0 + P.hub].T_off;
       d.tc = (gemm_tc_supported(d.M, d.N, d.K) && d.K >= 4096 && d.M >= 128) ? 1 : 0;
-      // small stars: one pass, R formed on the fly (no R, no split-K partials)
-      d.small = (!d.tc && d.K <= 4096) ? 1 : 0;
-      if (d.small) {
-        d.stn = std::min(up4(d.N), 64);
-        d.stm = std::min(up4(d.M), 4096 / d.stn);
-        d.smt = (d.M + d.stm - 1) / d.stm;
-        d.snt = (d.N + d.stn - 1) / d.stn;
-        plan->small_blocks += (long long)d.smt * d.snt;
-      } else {
-        const long long base = (long long)d.mtiles * d.ntiles;
-        const int target = 2 * std::max(c->sm_count, 148);
-        const long long max_splits = std::max(1ll, d.K / 32);
-        d.splits = (int)std::max(1ll, std::min(max_splits, (target + base - 1) / base));
-        d.r_off = plan->r_total;
-        plan->r_total += d.K * d.N;
-        d.part_off = plan->part_total;
-        plan->part_total += (long long)d.splits * d.M * d.N;
-        d.blk_off = plan->gemm_blocks;
-        plan->gemm_blocks += base * d.splits;
-        plan->max_tile_smem = std::max(plan->max_tile_smem, 16 * (d.TM + d.TN) * 4);
-      }
+      const long long base = (long long)d.mtiles * d.ntiles;
+      const int target = 2 * std::max(c->sm_count, 148);
+      const long long max_splits = std::max(1ll, d.K / 32);
+      d.splits = (int)std::max(1ll, std::min(max_splits, (target + base - 1) / base));
+      d.r_off = plan->r_total;
+      plan->r_total += d.K * d.N;
+      d.part_off = plan->part_total;
+      plan->part_total += (long long)d.splits * d.M * d.N;
+      d.blk_off = plan->gemm_blocks;
+      plan->gemm_blocks += base * d.splits;
+      plan->max_tile_smem = std::max(plan->max_tile_smem, 16 * (d.TM + d.TN) * 4);
       if (d.tc) {
         d.rt_off = (plan->rt_total + 63) & ~63ll;
         plan->rt_total = d.rt_off + d.K * d.N;
@@ -696,7 +687,6 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
     }
     plan->r_prefix.push_back(plan->r_total);
     plan->blk_prefix.push_back(plan->gemm_blocks);
-    plan->s_prefix.push_back(plan->small_blocks);
     f0 += d.n_frags;
     plan->pdev.push_back(d);
   }
@@ -741,7 +731,7 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
   st.add(prepm, &dpm); st.add(basism, &dbm); st.add(plan->t_prefix, &plan->d_t_prefix);
   st.add(plan->tz_prefix, &plan->d_tz_prefix); st.add(plan->out_prefix, &plan->d_out_prefix);
   st.add(plan->z_prefix, &plan->d_z_prefix); st.add(plan->r_prefix, &plan->d_r_prefix);
-  st.add(plan->blk_prefix, &plan->d_blk_prefix); st.add(plan->s_prefix, &plan->d_s_prefix);
+  st.add(plan->blk_prefix, &plan->d_blk_prefix);
   bool ok = st.commit(c, plan->A);
   if (!ok) { delete plan; return fail(c, CCS_ERR_OOM, "plan upload failed"); }
   dp.frags = dfr; dp.cops = dco; dp.nops = dno; dp.moments = dmo; dp.wires = dwi; dp.zoffs = dzo;
@@ -750,6 +740,7 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
   dp.items_body = dib; dp.n_items_body = (int)items_b.size(); dp.max_body_cols = max_body_cols;
   dp.cliff_frags = dcf; dp.n_cliff_frags = (int)cliff_frags.size();
   dp.max_body_stage_words = max_body_stage;
+  dp.max_moment_ops = max_moment_ops;
   dp.problems = dpr; dp.n_problems = (int)plan->pdev.size();
   dp.prep_ops = dpo; dp.basis_ops = dbo; dp.prep_mats = dpm; dp.basis_mats = dbm;
   cudaError_t e = cudaStreamSynchronize(c->stream);
@@ -1072,8 +1063,7 @@ int ccs_recombine(ccs_ctx c, ccs_plan p, ccs_res r, const ccs_recomb_opts* opts,
   const bool tc = !(opts && opts->no_tensor_cores);
   RecombSizes rz{p->r_total, p->part_total, p->gemm_blocks, p->n_marg, p->n_zexp,
                  p->d_r_prefix, p->d_blk_prefix, p->d_out_prefix, p->d_z_prefix, p->max_tile_smem,
-                 tc ? p->pdev.data() : nullptr, (int)p->pdev.size(), r->rt_scratch, p->small_blocks,
-                 p->d_s_prefix};
+                 tc ? p->pdev.data() : nullptr, (int)p->pdev.size(), r->rt_scratch};
   cudaError_t e;
   if (opts && opts->use_graph && !c->profiling) {
     const int key = prec * 2 + (tc ? 1 : 0);
@@ -1328,7 +1318,7 @@ extern "C" int ccs_recombine_noalloc(ccs_ctx c, ccs_plan p, ccs_res r, int preci
   }
   RecombSizes rz{p->r_total, p->part_total, p->gemm_blocks, p->n_marg, p->n_zexp,
                  p->d_r_prefix, p->d_blk_prefix, p->d_out_prefix, p->d_z_prefix, p->max_tile_smem,
-                 nullptr, 0, nullptr, p->small_blocks, p->d_s_prefix};
+                 nullptr, 0, nullptr};
   e = launch_recombine(p->dp, r->dr, precision, rz, g_noalloc_addr[c->device], marginal_out, zexp_out, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "recombine kernel");
   return CCS_OK;

@@ -1002,7 +1002,10 @@ cudaError_t launch_body(const DevPlan& p, const DevRes& r, int smem_optin, bool 
   const int words = std::max(p.max_body_cols, std::min(p.max_body_stage_words, smem_optin / 8));
   cudaError_t err = cudaFuncSetAttribute(body_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, words * 8);
   if (err != cudaSuccess) return err;
-  body_kernel<<<p.n_items_body, 256, (size_t)words * 8, s>>>(p, r, words); note_launch();
+  // one thread per op of the widest moment (whole warps, 32..256): fewer
+  // idle warps at each moment's barrier
+  const int threads = std::min(256, std::max(32, (p.max_moment_ops + 31) / 32 * 32));
+  body_kernel<<<p.n_items_body, threads, (size_t)words * 8, s>>>(p, r, words); note_launch();
   err = cudaGetLastError();
   if (!basis) return err;
   if (err != cudaSuccess || p.n_cliff_frags == 0) return err;

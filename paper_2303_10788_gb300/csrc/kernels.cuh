@@ -57,9 +57,6 @@ struct ProblemDev {
   long long rt_off;        // bf16 index of R'^T (N x K) in the bf16 scratch (tensor-core path)
   long long hub_T_off;     // T_off of the hub
   int tc;                  // 1: eligible for the tensor-core GEMM in BF16 mode
-  int small;               // 1: contracted by the one-pass kernel (R formed on the fly)
-  int stm, stn;            // its output tile (<= 64 x 64) and tile counts
-  int smt, snt;
 };
 
 // Device views of a plan + result.
@@ -76,6 +73,7 @@ struct DevPlan {
   const int2* items_body;     // (frag, 64-row word) of every Clifford fragment's body
   int n_items_body, max_body_cols;
   int max_body_stage_words;   // body kernel shared memory with the op stream staged
+  int max_moment_ops;         // widest gate moment of any Clifford fragment
   const int* cliff_frags;     // every Clifford fragment (shared-row bases)
   int n_cliff_frags;
   const ProblemDev* problems;
@@ -169,8 +167,6 @@ struct RecombSizes {
   const ProblemDev* host_problems;
   int n_problems;
   uint16_t* rt_scratch;          // bf16 R'^T of eligible problems
-  long long small_blocks;        // blocks of the one-pass contraction
-  const long long* s_prefix;     // per problem, one-pass blocks
 };
 cudaError_t launch_recombine(const DevPlan& p, const DevRes& r, int precision, const RecombSizes& z,
                              float* scratch, double* marg_out, double* zexp_out, cudaStream_t s);

@@ -390,117 +390,12 @@ __global__ void __launch_bounds__(256) hub_bf16_kernel(const float* __restrict__
   }
 }
 
-// One-pass contraction of a small star (K <= 4096): each block owns a tile
-// of at most 64 x 64 outputs and walks the whole cut index in chunks of 64:
-// the hub operand rows come from Q^T, the leaves' Kronecker operand R is
-// formed on the fly in shared memory, products and sums within a chunk are
-// FP32 and the chunks are added in FP64; the outputs go straight to their
-// marginal positions.  No R or split-K partials touch HBM.
-constexpr int kSK = 64;
-
-__device__ __forceinline__ long long marg_index(const DevPlan& P, const ProblemDev& Pb, long long m, long long n) {
-  long long o = 0;
-  const FragDev& Hb = P.frags[Pb.frag0 + Pb.hub];
-  for (int j = 0; j < Hb.m; ++j) o |= ((m >> j) & 1) << Hb.marg_pos[j];
-  int off = 0;
-  for (int l = 0; l < Pb.n_frags; ++l) {
-    if (l == Pb.hub) continue;
-    const FragDev& L = P.frags[Pb.frag0 + l];
-    for (int j = 0; j < L.m; ++j) o |= ((n >> (off + j)) & 1) << L.marg_pos[j];
-    off += L.m;
-  }
-  return o;
-}
-
-__global__ void __launch_bounds__(256) contract_small_kernel(DevPlan P, DevRes R, int precision,
-                                                             const long long* s_prefix, int np, long long total,
-                                                             double* marg_out) {
-  __shared__ __align__(16) float Qs[kSK][64];
-  __shared__ __align__(16) float Rs[kSK][64];
-  for (long long b = blockIdx.x; b < total; b += gridDim.x) {
-    const int pi = find_seg(s_prefix, np, b);
-    const ProblemDev& Pb = P.problems[pi];
-    const long long loc = b - s_prefix[pi];
-    const int mt = (int)(loc / Pb.snt), nt = (int)(loc % Pb.snt);
-    const int M = Pb.M, N = Pb.N, TM = Pb.stm, TN = Pb.stn;
-    const int m0 = mt * TM, n0 = nt * TN;
-    const long long K = Pb.K;
-    const float* QT = R.TQ + Pb.hub_T_off;
-    const int tn4 = TN >> 2;
-    const bool act = (int)threadIdx.x < (TM >> 2) * tn4;
-    const int mi = act ? ((int)threadIdx.x / tn4) * 4 : 0, ni = act ? ((int)threadIdx.x % tn4) * 4 : 0;
-    double acc64[4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) acc64[i][j] = 0.0;
-    for (long long k0 = 0; k0 < K; k0 += kSK) {
-      for (int t = threadIdx.x; t < kSK * TM; t += blockDim.x) {
-        const int k = t / TM, m = t % TM;
-        float v = (k0 + k < K && m0 + m < M) ? QT[(k0 + k) * M + m0 + m] : 0.f;
-        if (precision == CCS_BF16) v = to_bf16f(v);
-        Qs[k][m] = v;
-      }
-      for (int t = threadIdx.x; t < kSK * TN; t += blockDim.x) {
-        const int k = t / TN, n = t % TN;
-        const long long Pp = k0 + k, ol = n0 + n;
-        float v = 0.f;
-        if (Pp < K && ol < N) {
-          v = 1.f;
-          int off = 0;
-          for (int l = 0; l < Pb.n_frags; ++l) {
-            if (l == Pb.hub) continue;
-            const FragDev& L = P.frags[Pb.frag0 + l];
-            const int x = (int)((ol >> off) & ((1ll << L.m) - 1));
-            off += L.m;
-            int pl = 0;
-            for (int i = 0; i < L.n_slots; ++i) pl |= (int)((Pp >> (2 * L.slot_cut[i])) & 3) << (2 * i);
-            v *= R.TQ[L.T_off + ((long long)x << (2 * L.n_slots)) + pl];
-          }
-          if (precision == CCS_BF16) v = to_bf16f(v);
-        }
-        Rs[k][n] = v;
-      }
-      __syncthreads();
-      if (act) {
-        float acc[4][4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-#pragma unroll 8
-        for (int k = 0; k < kSK; ++k) {
-          const float4 av = *reinterpret_cast<const float4*>(&Qs[k][mi]);
-          const float4 bv = *reinterpret_cast<const float4*>(&Rs[k][ni]);
-          const float a4[4] = {av.x, av.y, av.z, av.w}, b4[4] = {bv.x, bv.y, bv.z, bv.w};
-#pragma unroll
-          for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a4[i], b4[j], acc[i][j]);
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) acc64[i][j] += (double)acc[i][j];
-      }
-      __syncthreads();
-    }
-    if (act)
-      for (int i = 0; i < 4; ++i)
-        for (int j = 0; j < 4; ++j) {
-          const long long m = m0 + mi + i, n = n0 + ni + j;
-          if (m < M && n < N) marg_out[Pb.marg_off + marg_index(P, Pb, m, n)] = ldexp(acc64[i][j], -Pb.k);
-        }
-  }
-}
-
 __global__ void reduce_scatter_kernel(DevPlan P, const long long* prefix, int np, long long total,
                                       const float* scratch, double* marg_out) {
   for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
        g += (long long)gridDim.x * blockDim.x) {
     const int pi = find_seg(prefix, np, g);
     const ProblemDev& Pb = P.problems[pi];
-    if (Pb.small) continue;                      // written by the one-pass kernel
     const long long loc = g - prefix[pi];
     const long long m = loc / Pb.N, n = loc - m * Pb.N;
     double acc = 0.0;
@@ -607,12 +502,7 @@ cudaError_t launch_recombine(const DevPlan& p, const DevRes& r, int precision, c
         if (err != cudaSuccess) return err;
       }
     }
-    if (z.small_blocks > 0) {
-      contract_small_kernel<<<(unsigned)(z.small_blocks < 65535ll * 16 ? z.small_blocks : 65535ll * 16), 256, 0, s>>>(
-          p, r, precision, z.s_prefix, p.n_problems, z.small_blocks, marg_out); note_launch();
-      if ((err = cudaGetLastError()) != cudaSuccess) return err;
-    }
-    if (z.gemm_blocks > 0) {   // some problem takes the split-K / tensor-core path
+    {
       reduce_scatter_kernel<<<grid(z.out_total, 256), 256, 0, s>>>(p, z.out_prefix, p.n_problems, z.out_total,
                                                                   scratch, marg_out); note_launch();
       if ((err = cudaGetLastError()) != cudaSuccess) return err;

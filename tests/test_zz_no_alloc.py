@@ -37,8 +37,7 @@ def test_noalloc_matches_recombine_twice(ctx, make):
 def test_noalloc_rejects_plans_beyond_its_scratch(ctx):
     import torch
     # four leaves carrying the whole 12-qubit marginal and 8 cuts: the
-    # Kronecker operand alone is 4^8 x 2^12 floats (1 GiB) > 8 MiB (stars with
-    # K <= 4096 are contracted in one pass and need no scratch at all)
+    # Kronecker operand alone is 4^8 x 2^12 floats (1 GiB) > 8 MiB
     regs = [Region([0, 1, 2], 3, 2, 6, [0, 1, 2], 1),
             Region([10, 11, 12], 13, 2, 6, [10, 11, 12], 1),
             Region([20, 21, 22], 23, 2, 6, [20, 21, 22], 1),
