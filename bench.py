@@ -279,6 +279,7 @@ def run_ours(args, rank, world, local_rank):
                        "recombination": args.precision + (" (tcgen05 where eligible)" if args.precision == "bf16" else
                                                           " (CUDA-core FMA)"),
                        "tuning": {"threads": tuning[0], "words_per_op": tuning[1], "shots_per_cta": tuning[2],
+                                  "hub_threads": tuning[3],
                                   "autotuned": bool(args.autotune)}},
             "circuits_per_s": world * len(ws) * args.steps / t_tot,
             "stage_ms": stage, "roofline": roof, "stage_roofline": roofs,

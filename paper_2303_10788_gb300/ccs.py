@@ -64,7 +64,7 @@ class ccs_cut_opts(C.Structure):
 class ccs_eval_opts(C.Structure):
     _fields_ = [("mode", C.c_int32), ("shots", C.c_uint32), ("seed_lo", C.c_uint32),
                 ("seed_hi", C.c_uint32), ("keep_tableaus", C.c_int32), ("use_graph", C.c_int32),
-                ("autotune", C.c_int32), ("per_variant_body", C.c_int32)]
+                ("autotune", C.c_int32), ("per_variant_body", C.c_int32), ("hub_sampler", C.c_int32)]
 
 
 class ccs_recomb_opts(C.Structure):
@@ -124,7 +124,8 @@ def lib():
             "ccs_get_operand": ([P, P, C.c_int, C.c_int, P], C.c_int),
             "ccs_set_profiling": ([P, C.c_int], C.c_int),
             "ccs_recombine_noalloc": ([P, P, P, C.c_int, P, P], C.c_int),
-            "ccs_get_tuning": ([P, P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
+            "ccs_get_tuning": ([P, P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                C.POINTER(C.c_int)], C.c_int),
             "ccs_cut_candidates": ([P, C.POINTER(ccs_problem), C.POINTER(ccs_cut_opts), C.POINTER(ccs_cut),
                                     C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_int], C.c_int),
             "ccs_get_stage_times": ([P, C.POINTER(C.c_double), C.c_int], C.c_int),
@@ -297,9 +298,10 @@ def ccs_build_fragments(ctx, problems, max_cuts=12, max_nc_width=10, use_learned
 
 
 def ccs_eval_variants(ctx, plan, mode=CCS_SAMPLED, shots=1024, seed_lo=0x1234, seed_hi=0x5678,
-                      keep_tableaus=False, use_graph=False, res=None, autotune=False, per_variant_body=False):
+                      keep_tableaus=False, use_graph=False, res=None, autotune=False, per_variant_body=False,
+                      hub_sampler=0):
     opts = ccs_eval_opts(mode, shots, seed_lo, seed_hi, int(keep_tableaus), int(use_graph), int(autotune),
-                         int(per_variant_body))
+                         int(per_variant_body), int(hub_sampler))
     h = C.c_void_p(res.h.value if res is not None else None)
     ctx.check(lib().ccs_eval_variants(ctx.h, plan.h, C.byref(opts), C.byref(h)), "ccs_eval_variants")
     if res is not None:
@@ -434,10 +436,12 @@ def ccs_recombine_noalloc(ctx, plan, res, marginal_out, zexp_out=None, precision
 
 
 def ccs_get_tuning(ctx, res):
-    """(threads per tableau CTA, words per op per thread, shots per sampling CTA)."""
-    t, wpo, spc = C.c_int(), C.c_int(), C.c_int()
-    ctx.check(lib().ccs_get_tuning(ctx.h, res.h, C.byref(t), C.byref(wpo), C.byref(spc)), "ccs_get_tuning")
-    return t.value, wpo.value, spc.value
+    """(threads per tableau CTA, words per op per thread, shots per sampling CTA,
+    threads per hub-sampler CTA)."""
+    t, wpo, spc, hub = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+    ctx.check(lib().ccs_get_tuning(ctx.h, res.h, C.byref(t), C.byref(wpo), C.byref(spc), C.byref(hub)),
+              "ccs_get_tuning")
+    return t.value, wpo.value, spc.value, hub.value
 
 
 def ccs_get_operand(ctx, res, problem, fragment):

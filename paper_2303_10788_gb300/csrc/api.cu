@@ -27,7 +27,7 @@ struct ccs_ctx_s {
   std::string err;
   ccs_mpnn cut_model = nullptr;   // learned cut scorer (not owned)
   // autotuner results: shape bucket -> (Clifford threads per CTA, shots per sampler CTA)
-  std::map<std::tuple<int, int, unsigned, int>, std::tuple<int, int, int>> tuned;
+  std::map<std::tuple<int, int, unsigned, int>, std::tuple<int, int, int, int>> tuned;
   // second stream for the statevector branch (forked from / joined into `stream`)
   cudaStream_t side = nullptr;
   cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
@@ -217,6 +217,7 @@ struct ccs_plan_s {
   int2* d_items_hub = nullptr;      // Clifford hub variants (fused sampler)
   int2* d_items_plain = nullptr;    // other Clifford variants (sampler -> counts)
   int n_items_hub = 0, n_items_plain = 0, max_hub_nA = 0;
+  bool hub_bytes_ok = true;         // every hub fits the byte-counter sampler
   long long n_counts_plain = 0;     // counts of non-hub Clifford fragments come first
   bool all_star = true;
   ~ccs_plan_s() { A.release(); }
@@ -239,6 +240,8 @@ struct ccs_res_s {
   int cliff_threads = 256;
   int cliff_words = 1;        // words per op per thread in the tableau kernel
   int sample_spc = 4096;
+  int hub_threads = 512;      // threads of the fused hub sampler CTA (16-bit counters)
+  bool hub_bytes = false;     // use the byte-counter hub sampler (256 threads, two CTAs per SM)
   float* scratch = nullptr;   // recombination: R operand + split-K partials
   uint16_t* rt_scratch = nullptr;   // bf16 R'^T of tensor-core-eligible problems
   ~ccs_res_s() {
@@ -621,7 +624,11 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
   std::vector<int2> items_hub, items_plain;
   for (auto& it : items_c) {
     const FragDev& f = plan->fdev[it.x];
-    if (f.role == 1) { items_hub.push_back(it); plan->max_hub_nA = std::max(plan->max_hub_nA, f.nA); }
+    if (f.role == 1) {
+      items_hub.push_back(it);
+      plan->max_hub_nA = std::max(plan->max_hub_nA, f.nA);
+      if (f.m < 2 || f.qout > 4 || f.nA > 16) plan->hub_bytes_ok = false;
+    }
     else items_plain.push_back(it);
   }
   plan->n_items_hub = (int)items_hub.size();
@@ -833,7 +840,8 @@ static int enqueue_eval(ccs_ctx c, ccs_plan p, ccs_res r) {
     stage_end(c, ST_CLIFFORD);
     if (e.mode == CCS_SAMPLED) {
       stage_begin(c, ST_SAMPLE);
-      if ((err = launch_sample_hub(dp, r->dr, e, p->d_items_hub, p->n_items_hub, p->max_hub_nA, e.keep_tableaus,
+      if ((err = launch_sample_hub(dp, r->dr, e, p->d_items_hub, p->n_items_hub, p->max_hub_nA, r->hub_threads,
+                                   e.keep_tableaus, p->hub_bytes_ok && r->hub_bytes,
                                    s)) != cudaSuccess)
         return cuda_fail(c, err, "hub sample kernel");
       if ((err = launch_sample(dp, r->dr, e, p->d_items_plain, p->n_items_plain, r->sample_spc, 256, s)) !=
@@ -872,49 +880,69 @@ static int autotune(ccs_ctx c, ccs_plan p, ccs_res r) {
   const auto key = std::make_tuple((max_n + 63) / 64, items, r->ep.shots, r->ep.mode * 2 + r->ep.shared_body);
   auto it = c->tuned.find(key);
   if (it != c->tuned.end()) {
-    std::tie(r->cliff_threads, r->cliff_words, r->sample_spc) = it->second;
+    std::tie(r->cliff_threads, r->cliff_words, r->sample_spc, r->hub_threads) = it->second;
+    r->hub_bytes = r->hub_threads == 256;
     return CCS_OK;
   }
-  const int threads_c[] = {128, 256, 512};
-  const int spc_c[] = {1024, 2048, 4096, 8192};
-  const int words_c[] = {1, 2, 4, 8};
-  const int n_spc = r->ep.mode == CCS_SAMPLED ? 4 : 1;
-  const int max_w = 2 * ((max_n + 63) / 64);
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     return fail(c, CCS_ERR_CUDA, "autotune events");
-  float best = 1e30f;
-  std::tuple<int, int, int> choice{r->cliff_threads, r->cliff_words, r->sample_spc};
+  // one warm-up and three timed evaluations of the current shape
+  auto time_it = [&](float* ms) -> int {
+    int rc = enqueue_eval(c, p, r);
+    if (rc != CCS_OK) return rc;
+    cudaEventRecord(e0, c->stream);
+    for (int rep = 0; rep < 3 && rc == CCS_OK; ++rep) rc = enqueue_eval(c, p, r);
+    cudaEventRecord(e1, c->stream);
+    if (rc != CCS_OK) return rc;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(ms, e0, e1) != cudaSuccess)
+      return fail(c, CCS_ERR_CUDA, "autotune timing");
+    return CCS_OK;
+  };
+  // coordinate descent: tableau CTA shape, then plain-sampler chunk, then hub-sampler CTA
+  const int threads_c[] = {128, 256, 512};
+  const int words_c[] = {1, 2, 4, 8};
+  const int spc_c[] = {1024, 2048, 4096, 8192};
+  const int hub_c[] = {128, 512, 256};      // 256: the byte-counter kernel
+  const int max_w = 2 * ((max_n + 63) / 64);
+  const bool sampled = r->ep.mode == CCS_SAMPLED;
   int rc = CCS_OK;
+  float best = 1e30f, ms = 0.f;
+  int bt = r->cliff_threads, bw = r->cliff_words, bs = r->sample_spc, bh = r->hub_threads;
   for (int ti = 0; ti < 3 && rc == CCS_OK; ++ti)
-    for (int wi = 0; wi < 4 && rc == CCS_OK; ++wi)
-    for (int si = 0; si < n_spc && rc == CCS_OK; ++si) {
+    for (int wi = 0; wi < 4 && rc == CCS_OK; ++wi) {
       if (words_c[wi] > max_w || (r->ep.shared_body && words_c[wi] != 1)) continue;
       r->cliff_threads = threads_c[ti];
       r->cliff_words = words_c[wi];
-      r->sample_spc = spc_c[si];
-      rc = enqueue_eval(c, p, r);
-      if (rc != CCS_OK) break;
-      cudaEventRecord(e0, c->stream);
-      for (int rep = 0; rep < 3 && rc == CCS_OK; ++rep) rc = enqueue_eval(c, p, r);
-      cudaEventRecord(e1, c->stream);
-      float ms = 0.f;
-      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-        rc = fail(c, CCS_ERR_CUDA, "autotune timing");
-        break;
-      }
-      if (ms < best) { best = ms; choice = {threads_c[ti], words_c[wi], spc_c[si]}; }
+      if ((rc = time_it(&ms)) == CCS_OK && ms < best) { best = ms; bt = threads_c[ti]; bw = words_c[wi]; }
     }
+  r->cliff_threads = bt;
+  r->cliff_words = bw;
+  for (int si = 0; sampled && p->n_items_plain && si < 4 && rc == CCS_OK; ++si) {
+    r->sample_spc = spc_c[si];
+    if ((rc = time_it(&ms)) == CCS_OK && ms < best) { best = ms; bs = spc_c[si]; }
+  }
+  r->sample_spc = bs;
+  bool bb = r->hub_bytes;
+  for (int hi = 0; sampled && p->n_items_hub && hi < 3 && rc == CCS_OK; ++hi) {
+    if (hi == 2 && !p->hub_bytes_ok) continue;
+    r->hub_bytes = hi == 2;
+    r->hub_threads = hub_c[hi];
+    if ((rc = time_it(&ms)) == CCS_OK && ms < best) { best = ms; bh = hub_c[hi]; bb = hi == 2; }
+  }
+  r->hub_threads = bh;
+  r->hub_bytes = bb;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc != CCS_OK) return rc;
-  std::tie(r->cliff_threads, r->cliff_words, r->sample_spc) = choice;
-  c->tuned[key] = choice;
+  c->tuned[key] = std::make_tuple(bt, bw, bs, bh);
   return CCS_OK;
 }
 
-int ccs_get_tuning(ccs_ctx c, ccs_res r, int* cliff_threads, int* words_per_op, int* shots_per_cta) {
+int ccs_get_tuning(ccs_ctx c, ccs_res r, int* cliff_threads, int* words_per_op, int* shots_per_cta,
+                   int* hub_threads) {
   if (!c || !r) return fail(c, CCS_ERR_INVALID_ARG, "bad arguments");
+  if (hub_threads) *hub_threads = (r->hub_bytes && r->plan->hub_bytes_ok) ? 256 : r->hub_threads;
   if (cliff_threads) *cliff_threads = r->cliff_threads;
   if (words_per_op) *words_per_op = r->ep.shared_body ? 1 : r->cliff_words;
   if (shots_per_cta) *shots_per_cta = r->sample_spc;
@@ -959,6 +987,10 @@ int ccs_eval_variants(ccs_ctx c, ccs_plan p, const ccs_eval_opts* opts, ccs_res*
       const int W = 2 * ((max_n + 63) / 64);
       r->cliff_words = W >= 16 ? 8 : W >= 8 ? 4 : 1;
       r->cliff_threads = max_n > 256 ? 512 : 256;
+      // small hub CTAs when a variant has few shots and few outputs (more CTAs per SM);
+      // byte counters when the histogram would otherwise fill an SM's shared memory
+      r->hub_threads = (p->max_hub_nA <= 12 && opts->shots <= 4096) ? 128 : 512;
+      r->hub_bytes = p->hub_bytes_ok && p->max_hub_nA >= 13;
     }
     if (p->rt_total) {
       d.TQh = r->A.get<uint16_t>(p->n_T);
@@ -991,9 +1023,13 @@ int ccs_eval_variants(ccs_ctx c, ccs_plan p, const ccs_eval_opts* opts, ccs_res*
   e.keep_tableaus = opts->keep_tableaus && r->have_tabs;
   e.shared_body = opts->per_variant_body ? 0 : 1;
   e.screen = e.shared_body && p->dp.n_cliff_frags > 0 && !e.keep_tableaus;
+  if (opts->hub_sampler < 0 || opts->hub_sampler > 2) return fail(c, CCS_ERR_INVALID_ARG, "bad hub sampler");
+  e.hub_sampler = opts->hub_sampler;
+  if (opts->hub_sampler == 1) r->hub_bytes = false;
+  if (opts->hub_sampler == 2) r->hub_bytes = p->hub_bytes_ok;
   e.inv_shots = e.shots ? 1.0 / (double)e.shots : 0.0;
   r->ep = e;
-  if (opts->autotune && !r->graph) {
+  if (opts->autotune && !r->graph && opts->hub_sampler == 0) {
     const bool prof = c->profiling;
     c->profiling = false;
     int rc = autotune(c, p, r);
@@ -1006,7 +1042,8 @@ int ccs_eval_variants(ccs_ctx c, ccs_plan p, const ccs_eval_opts* opts, ccs_res*
   }
   const bool same = r->graph && r->graph_key.mode == e.mode && r->graph_key.shots == e.shots &&
                     r->graph_key.seed_lo == e.seed_lo && r->graph_key.seed_hi == e.seed_hi &&
-                    r->graph_key.keep_tableaus == e.keep_tableaus && r->graph_key.shared_body == e.shared_body;
+                    r->graph_key.keep_tableaus == e.keep_tableaus && r->graph_key.shared_body == e.shared_body &&
+                    r->graph_key.hub_sampler == e.hub_sampler;
   if (!same) {
     if (r->graph) { cudaGraphExecDestroy(r->graph); r->graph = nullptr; }
     cudaStream_t s = c->stream;

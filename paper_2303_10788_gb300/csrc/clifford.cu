@@ -962,16 +962,211 @@ __global__ void __launch_bounds__(512) sample_hub_kernel(DevPlan P, DevRes R, Ev
   }
 }
 
+// --- the hub sampler with byte counters (two CTAs per SM) -----------------
+// Same result as sample_hub_kernel, for hubs with |A| <= 16, at least two
+// marginal bits and at most four quantum outputs, below 65536 shots.  The
+// histogram holds 8-bit counters (2^16 of them in 64 KB) so two CTAs fit on
+// an SM.  Counts stay exact: a variant whose expected count per outcome is
+// above 64 (shots > 64 * 2^rank), or whose counting overflowed a byte
+// (the atomic's old value tells), is counted again with 16-bit counters in
+// two passes, each over the outputs o of one half (top marginal bit).
+namespace {
+// signed sums of the counts c[b] (b = output bits) for every sign mask by a
+// 16-point Walsh-Hadamard transform, for the outputs o and o+1 (a, c), then
+// the variant's operand rows Q^T[D][o..o+1]
+__device__ __forceinline__ void hub_pair_out(int (&a)[16], int (&c)[16], int* wht, const int* s_czD,
+                                             const int* s_czS, int nz, float* QT, int M, int o, float inv) {
+#pragma unroll
+  for (int h = 1; h < 16; h <<= 1)
+#pragma unroll
+    for (int b = 0; b < 16; ++b)
+      if (!(b & h)) {
+        const int x0 = a[b], y0 = a[b | h], x1 = c[b], y1 = c[b | h];
+        a[b] = x0 + y0;
+        a[b | h] = x0 - y0;
+        c[b] = x1 + y1;
+        c[b | h] = x1 - y1;
+      }
+#pragma unroll
+  for (int b = 0; b < 16; ++b) {
+    wht[b] = a[b];
+    wht[16 + b] = c[b];
+  }
+  for (int cz = 0; cz < (1 << nz); ++cz) {
+    const int sm = s_czS[cz];
+    *reinterpret_cast<float2*>(QT + (long long)s_czD[cz] * M + o) =
+        make_float2((float)wht[sm] * inv, (float)wht[16 + sm] * inv);
+  }
+}
+}  // namespace
+
+__global__ void __launch_bounds__(256) sample_hub8_kernel(DevPlan P, DevRes R, EvalParams E, const int2* items,
+                                                          int keep_counts, int hist_words) {
+  extern __shared__ uint32_t h32[];
+  __shared__ uint32_t tbl[3][256];
+  __shared__ FragDev sF;
+  __shared__ int s_czD[16], s_czS[16];
+  __shared__ int s_over;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int2 it = items[blockIdx.x];
+  {
+    const int* src = reinterpret_cast<const int*>(P.frags + it.x);
+    int* dst = reinterpret_cast<int*>(&sF);
+    for (int i = tid; i < (int)(sizeof(FragDev) / 4); i += nt) dst[i] = src[i];
+  }
+  if (tid == 0) s_over = 0;
+  __syncthreads();
+  const FragDev& F = sF;
+  const int v = it.y, nA = F.nA, m = F.m, M = 1 << m, nb = 1 << F.qout;
+  const SpaceRec& sp = R.spaces[F.space_off + v];
+  const int rank = sp.rank;
+  const uint32_t off = sp.off;
+  for (int t = tid; t < 3 * 256; t += nt) {
+    const int k = t >> 8, byte = t & 255;
+    uint32_t acc = 0;
+    for (int b = 0; b < 8; ++b) {
+      const int j = 8 * k + b;
+      if (j < rank && ((byte >> b) & 1)) acc ^= sp.basis[j];
+    }
+    tbl[k][byte] = acc;
+  }
+  // the variant's operand columns: one D and sign mask per Z-basis choice
+  int nz = 0;
+  {
+    int beta[kMaxCuts], zpos[kMaxCuts], zout[kMaxCuts];
+    int t = v;
+    for (int i = 0; i < F.qin; ++i) t /= 4;
+    for (int j = 0; j < F.qout; ++j) { beta[j] = t % 3; t /= 3; }
+    int Dbase = 0, fixed_mask = 0;
+    for (int j = 0; j < F.n_slots; ++j) {
+      const int code = F.slot_code[j], idx = code & 255;
+      if ((code >> 8) == 0) {
+        int u = v;
+        for (int i = 0; i < idx; ++i) u /= 4;
+        Dbase |= (u % 4) << (2 * j);
+      } else if (beta[idx] == 2) {
+        zpos[nz] = j;
+        zout[nz++] = idx;
+      } else {
+        Dbase |= (beta[idx] == 0 ? 1 : 2) << (2 * j);
+        fixed_mask |= 1 << idx;
+      }
+    }
+    if (tid < (1 << nz)) {
+      int D = Dbase, smask = fixed_mask;
+      for (int i = 0; i < nz; ++i)
+        if ((tid >> i) & 1) { D |= 3 << (2 * zpos[i]); smask |= 1 << zout[i]; }
+      s_czD[tid] = D;
+      s_czS[tid] = smask;
+    }
+  }
+  const uint32_t cmask = rank >= 32 ? 0xffffffffu : ((1u << rank) - 1u);
+  const float inv = (float)E.inv_shots;
+  float* QT = R.TQ + F.T_off;
+  int* wht = reinterpret_cast<int*>(h32 + hist_words) + tid * 33;
+  uint32_t* gcount = R.counts + F.counts_off + ((long long)v << nA);
+  auto sample_y = [&](uint32_t w) -> uint32_t {
+    const uint32_t c = w & cmask;
+    return off ^ tbl[0][c & 255] ^ tbl[1][(c >> 8) & 255] ^ tbl[2][(c >> 16) & 255];
+  };
+  bool narrow = (unsigned long long)E.shots <= (64ull << rank);
+  if (narrow) {
+    for (int i = tid; i < (1 << nA) / 4; i += nt) h32[i] = 0u;
+    __syncthreads();
+    for (uint32_t g = tid; 4 * g < E.shots; g += nt) {   // shot 4g+j: word j
+      const uint4 o = philox4x32_10(make_uint4(g, (uint32_t)v, (uint32_t)F.findex, (uint32_t)F.problem),
+                                    E.seed_lo, E.seed_hi);
+      const uint32_t w4[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (4 * g + j >= E.shots) break;
+        const uint32_t y = sample_y(w4[j]), sh = (y & 3u) << 3;
+        const uint32_t old = atomicAdd(&h32[y >> 2], 1u << sh);
+        if (((old >> sh) & 0xffu) == 0xffu) s_over = 1;     // a byte wrapped: recount wider
+      }
+    }
+    __syncthreads();
+    narrow = s_over == 0;
+    if (narrow) {
+      if (keep_counts)
+        for (uint32_t y = tid; y < (1u << nA); y += nt) gcount[y] = (h32[y >> 2] >> ((y & 3u) << 3)) & 0xffu;
+      for (int q = tid; q < (M >> 2); q += nt) {       // outputs o..o+3 share a counter word
+        const int o = 4 * q;
+        uint32_t w[16];
+#pragma unroll
+        for (int b = 0; b < 16; ++b) w[b] = b < nb ? h32[((uint32_t)o | ((uint32_t)b << m)) >> 2] : 0u;
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+          int a[16], c[16];
+#pragma unroll
+          for (int b = 0; b < 16; ++b) {
+            a[b] = (int)((w[b] >> (16 * half)) & 0xffu);
+            c[b] = (int)((w[b] >> (16 * half + 8)) & 0xffu);
+          }
+          hub_pair_out(a, c, wht, s_czD, s_czS, nz, QT, M, o + 2 * half, inv);
+        }
+      }
+    }
+  }
+  if (!narrow) {   // 16-bit counters, outputs of one half (top marginal bit) per pass
+    const int mh = m - 1, Mh = M >> 1;
+    for (int h = 0; h < 2; ++h) {
+      __syncthreads();
+      for (int i = tid; i < (1 << (nA - 1)) / 2; i += nt) h32[i] = 0u;
+      __syncthreads();
+      for (uint32_t g = tid; 4 * g < E.shots; g += nt) {
+        const uint4 o = philox4x32_10(make_uint4(g, (uint32_t)v, (uint32_t)F.findex, (uint32_t)F.problem),
+                                      E.seed_lo, E.seed_hi);
+        const uint32_t w4[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          if (4 * g + j >= E.shots) break;
+          const uint32_t y = sample_y(w4[j]);
+          if ((int)((y >> mh) & 1u) != h) continue;
+          const uint32_t yh = (y & (uint32_t)(Mh - 1)) | ((y >> m) << mh);
+          atomicAdd(&h32[yh >> 1], 1u << ((yh & 1u) << 4));
+        }
+      }
+      __syncthreads();
+      if (keep_counts)
+        for (uint32_t yh = tid; yh < (1u << (nA - 1)); yh += nt) {
+          const uint32_t y = (yh & (uint32_t)(Mh - 1)) | ((uint32_t)h << mh) | ((yh >> mh) << m);
+          gcount[y] = (h32[yh >> 1] >> ((yh & 1u) << 4)) & 0xffffu;
+        }
+      for (int o2 = tid; o2 < (Mh >> 1); o2 += nt) {    // pairs of outputs within the half
+        const int ol = 2 * o2;
+        int a[16], c[16];
+#pragma unroll
+        for (int b = 0; b < 16; ++b) {
+          const uint32_t w = b < nb ? h32[((uint32_t)ol | ((uint32_t)b << mh)) >> 1] : 0u;
+          a[b] = (int)(w & 0xffffu);
+          c[b] = (int)(w >> 16);
+        }
+        hub_pair_out(a, c, wht, s_czD, s_czS, nz, QT, M, h * Mh + ol, inv);
+      }
+    }
+  }
+}
+
 cudaError_t launch_sample_hub(const DevPlan& p, const DevRes& r, const EvalParams& e, const int2* items, int n_items,
-                              int max_nA, int keep_counts, cudaStream_t s) {
+                              int max_nA, int threads, int keep_counts, bool bytes_ok, cudaStream_t s) {
   if (n_items == 0 || e.shots == 0) return cudaSuccess;
+  if (bytes_ok && e.shots <= 0xffffu && max_nA >= 2 && max_nA <= 16) {   // byte counters, 256 threads
+    const int hist_words = (1 << max_nA) / 4;
+    const size_t smem = (size_t)4 * hist_words + (size_t)256 * 33 * 4;
+    cudaError_t err = cudaFuncSetAttribute(sample_hub8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    sample_hub8_kernel<<<n_items, 256, smem, s>>>(p, r, e, items, keep_counts, hist_words); note_launch();
+    return cudaGetLastError();
+  }
   const int wide = e.shots > 0xffffu ? 1 : 0;     // 32-bit counters when 16 bits could overflow
   const int hist_words = wide ? (1 << max_nA) : ((1 << max_nA) > 1 ? (1 << (max_nA - 1)) : 1);
   // packed counters, then 33 ints per thread for the transform of the 16-bit path
-  const size_t smem = (size_t)4 * hist_words + (wide ? 0 : (size_t)512 * 33 * 4);
+  threads = threads >= 512 ? 512 : threads >= 256 ? 256 : 128;
+  const size_t smem = (size_t)4 * hist_words + (wide ? 0 : (size_t)threads * 33 * 4);
   cudaError_t err = cudaFuncSetAttribute(sample_hub_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  sample_hub_kernel<<<n_items, 512, smem, s>>>(p, r, e, items, keep_counts, wide, hist_words); note_launch();
+  sample_hub_kernel<<<n_items, threads, smem, s>>>(p, r, e, items, keep_counts, wide, hist_words); note_launch();
   return cudaGetLastError();
 }
 

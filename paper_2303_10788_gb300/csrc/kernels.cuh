@@ -109,6 +109,7 @@ struct EvalParams {
   int keep_tableaus;
   int shared_body;            // 1: variants start from their fragment's body tableau
   int screen;                 // 1: the rank screen runs; the tableau kernel takes its queue
+  int hub_sampler;            // host only: the caller's hub sampler choice (0 automatic)
   double inv_shots;
 };
 
@@ -133,8 +134,10 @@ cudaError_t launch_sample(const DevPlan& p, const DevRes& r, const EvalParams& e
                           int n_items, int shots_per_cta, int threads, cudaStream_t s);
 // Sampling + output fold of star hubs (one CTA per hub variant); writes the
 // hub's contraction operand Q into TQ, and dense counts if keep_counts.
+// bytes_ok: every hub has >= 2 marginal bits, <= 4 quantum outputs and |A| <= 16
+// (the byte-counter kernel applies)
 cudaError_t launch_sample_hub(const DevPlan& p, const DevRes& r, const EvalParams& e, const int2* items,
-                              int n_items, int max_nA, int keep_counts, cudaStream_t s);
+                              int n_items, int max_nA, int threads, int keep_counts, bool bytes_ok, cudaStream_t s);
 cudaError_t launch_statevector(const DevPlan& p, const DevRes& r, int max_n, int threads,
                                int grid, cudaStream_t s);
 // A subset of fragments to fold: fidx[i] is the FragDev index of segment i;
