@@ -219,6 +219,7 @@ struct ccs_plan_s {
   int n_items_hub = 0, n_items_plain = 0, max_hub_nA = 0;
   bool hub_bytes_ok = true;         // every hub fits the byte-counter sampler
   long long n_counts_plain = 0;     // counts of non-hub Clifford fragments come first
+  long long n_dist_nc = 0;          // distributions of statevector fragments come first
   bool all_star = true;
   ~ccs_plan_s() { A.release(); }
 };
@@ -229,6 +230,8 @@ struct ccs_res_s {
   EvalParams ep{};
   bool have_tabs = false;
   bool have_counts = false;
+  bool counts_full = false;   // counts include the hubs' (kept for inspection)
+  bool dist_full = false;     // distributions include the Clifford fragments' (exact mode)
   Allocs A;
   cudaGraphExec_t graph = nullptr;
   long long graph_launches = 0;   // kernel nodes of the captured graph
@@ -574,6 +577,14 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
     d.TZ_off = plan->n_TZ;
     plan->n_TZ += (long long)d.nz * (1ll << (2 * d.n_slots));
     plan->fdev.push_back(d);
+  }
+  {   // distributions: statevector fragments first (all a sampled evaluation needs), then Clifford
+    long long off = 0;
+    for (auto& f : plan->fdev)
+      if (!f.clifford) { f.dist_off = off; off += (long long)f.nv << f.nA; }
+    plan->n_dist_nc = off;
+    for (auto& f : plan->fdev)
+      if (f.clifford) { f.dist_off = off; off += (long long)f.nv << f.nA; }
   }
   if ((size_t)plan->cliff_smem_words * 8 > c->smem_optin && !items_c.empty()) {
     delete plan;
@@ -967,7 +978,7 @@ int ccs_eval_variants(ccs_ctx c, ccs_plan p, const ccs_eval_opts* opts, ccs_res*
     r->A.ctx = c;
     DevRes& d = r->dr;
     d.spaces = r->A.get<SpaceRec>(std::max<long long>(p->n_spaces, 1));
-    d.dist = r->A.get<float>(std::max<long long>(p->n_dist, 1));
+    d.dist = r->A.get<float>(std::max<long long>(p->n_dist_nc, 1));   // exact mode widens it
     d.zval = r->A.get<float>(std::max<long long>(p->n_zval, 1));
     d.T = r->A.get<float>(std::max<long long>(p->n_T, 1));
     d.TQ = r->A.get<float>(std::max<long long>(p->n_T, 1));
@@ -1005,10 +1016,23 @@ int ccs_eval_variants(ccs_ctx c, ccs_plan p, const ccs_eval_opts* opts, ccs_res*
     cudaMemsetAsync(d.status, 0, 4 * sizeof(unsigned), c->stream);
     *res = r;
   }
-  if (opts->mode == CCS_SAMPLED && !r->have_counts && p->n_counts) {
-    r->dr.counts = r->A.get<uint32_t>(p->n_counts);
+  // buffers a mode needs are added on first use; a replaced buffer drops the captured graph
+  auto drop_graph = [&]() {
+    if (r->graph) { cudaGraphExecDestroy(r->graph); r->graph = nullptr; }
+  };
+  const bool want_full_counts = opts->keep_tableaus && p->n_counts > p->n_counts_plain;
+  if (opts->mode == CCS_SAMPLED && p->n_counts && (!r->have_counts || (want_full_counts && !r->counts_full))) {
+    r->dr.counts = r->A.get<uint32_t>(want_full_counts ? p->n_counts : std::max<long long>(p->n_counts_plain, 1));
     if (!r->dr.counts) return fail(c, CCS_ERR_OOM, "counts allocation failed");
     r->have_counts = true;
+    r->counts_full = want_full_counts;
+    drop_graph();
+  }
+  if (opts->mode == CCS_EXACT && !r->dist_full && p->n_dist > p->n_dist_nc) {
+    r->dr.dist = r->A.get<float>(p->n_dist);
+    if (!r->dr.dist) return fail(c, CCS_ERR_OOM, "distribution allocation failed");
+    r->dist_full = true;
+    drop_graph();
   }
   if (opts->keep_tableaus && !r->have_tabs && p->n_tab) {
     r->dr.tabs = r->A.get<unsigned long long>(p->n_tab);

@@ -363,27 +363,34 @@ __global__ void __launch_bounds__(256) gemm_splitk_kernel(DevPlan P, DevRes R, i
 }
 
 // BF16 K-major copy of a hub operand for the tensor-core GEMM:
-// Qh[o][D] = bf16(Q^T[D][o]), through 64 x 32 shared-memory tiles so both
-// the read (o fastest) and the write (D fastest, 128 B per row) coalesce.
+// Qh[o][D] = bf16(Q^T[D][o]), through 64 x 64 shared-memory tiles: each
+// warp reads 256 contiguous bytes of a Q^T row (o fastest) and writes 128
+// contiguous bytes of a Qh row as bf16 pairs (D fastest).
 __global__ void __launch_bounds__(256) hub_bf16_kernel(const float* __restrict__ QT, __nv_bfloat16* __restrict__ Qh,
                                                        int M, long long K) {
-  __shared__ float tile[64][33];
-  const long long tiles_d = (K + 63) / 64, tiles_o = (M + 31) / 32;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+  __shared__ float tile[64][65];
+  const long long tiles_d = (K + 63) / 64, tiles_o = (M + 63) / 64;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;   // 8 warps
   for (long long t = blockIdx.x; t < tiles_d * tiles_o; t += gridDim.x) {
     const long long d0 = (t / tiles_o) * 64;
-    const int o0 = (int)(t % tiles_o) * 32;
-    for (int r = ty; r < 64; r += 8) {
+    const int o0 = (int)(t % tiles_o) * 64;
+    for (int r = warp; r < 64; r += 8) {            // rows of Q^T: 64 floats each, two per lane
       const long long d = d0 + r;
-      const int o = o0 + tx;
-      tile[r][tx] = (d < K && o < M) ? QT[d * M + o] : 0.f;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int o = o0 + lane + 32 * h;
+        tile[r][lane + 32 * h] = (d < K && o < M) ? QT[d * M + o] : 0.f;
+      }
     }
     __syncthreads();
-    for (int r = ty; r < 32; r += 8) {
+    for (int r = warp; r < 64; r += 8) {            // rows of Qh: 64 bf16 each, one pair per lane
       const int o = o0 + r;
-      for (int c = tx; c < 64; c += 32) {
-        const long long d = d0 + c;
-        if (o < M && d < K) Qh[(long long)o * K + d] = __float2bfloat16_rn(tile[c][r]);
+      const long long d = d0 + 2 * lane;
+      if (o < M && d + 1 < K) {
+        *reinterpret_cast<__nv_bfloat162*>(Qh + (long long)o * K + d) =
+            __floats2bfloat162_rn(tile[2 * lane][r], tile[2 * lane + 1][r]);
+      } else if (o < M && d < K) {
+        Qh[(long long)o * K + d] = __float2bfloat16_rn(tile[2 * lane][r]);
       }
     }
     __syncthreads();
@@ -492,8 +499,8 @@ cudaError_t launch_recombine(const DevPlan& p, const DevRes& r, int precision, c
         const ProblemDev& Pb = z.host_problems[i];
         if (!Pb.tc) continue;
         {
-          const long long tiles = ((Pb.K + 63) / 64) * ((Pb.M + 31) / 32);
-          hub_bf16_kernel<<<(unsigned)(tiles < 152 * 16 ? tiles : 152 * 16), 256, 0, s>>>(
+          const long long tiles = ((Pb.K + 63) / 64) * ((Pb.M + 63) / 64);
+          hub_bf16_kernel<<<(unsigned)(tiles < 152 * 32 ? tiles : 152 * 32), 256, 0, s>>>(
               r.TQ + Pb.hub_T_off, reinterpret_cast<__nv_bfloat16*>(r.TQh) + Pb.hub_T_off, Pb.M, Pb.K); note_launch();
           if ((err = cudaGetLastError()) != cudaSuccess) return err;
         }
