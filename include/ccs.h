@@ -300,6 +300,7 @@ typedef struct {
   int32_t n_meas;           /* |A_f| = n_marg + n_qout */
   int32_t n_slots;          /* cuts incident to the fragment */
   int32_t n_ops, n_moments; /* compiled gate stream */
+  int32_t n_zstrings;       /* the problem's Z-strings (each restricted to the fragment) */
 } ccs_fragment_info;
 
 int ccs_plan_counts(ccs_ctx ctx, ccs_plan plan, int problem, int* n_fragments, int* n_cuts);
@@ -338,6 +339,11 @@ int ccs_get_counts(ccs_ctx ctx, ccs_res res, int problem, int fragment, int vari
 /* Probabilities of a variant over 2^|A_f| outcomes (float32): exact ones for
  * non-Clifford variants and exact-mode Clifford variants. */
 int ccs_get_dist(ccs_ctx ctx, ccs_res res, int problem, int fragment, int variant, float* out);
+/* Z-string values of a variant (float32, nz x 2^n_qout, row-major): entry
+ * [s][u] is <Z_S prod_{o in u} M_o> of the fragment's final state, S the
+ * string's wires in the fragment, M_o the observable measured at quantum
+ * output o (the cut identity, Sec. IV); +-1 or 0 for Clifford variants. */
+int ccs_get_zvals(ccs_ctx ctx, ccs_res res, int problem, int fragment, int variant, float* out);
 /* Contraction operand of a fragment of a star (float32, 2^n_marg x 4^n_slots):
  * for the hub Q[o][d] with d's digit at each cut = the preparation index where
  * the hub has a quantum input and the Pauli index where it has a quantum

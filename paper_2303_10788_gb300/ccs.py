@@ -26,7 +26,7 @@ CCS_FP32, CCS_BF16 = 0, 1
 EXPORTS = ["ccs_version", "ccs_create", "ccs_destroy", "ccs_last_error", "ccs_build_fragments",
            "ccs_plan_free", "ccs_eval_variants", "ccs_res_free", "ccs_recombine", "ccs_plan_counts",
            "ccs_fragment_info_get", "ccs_plan_cuts", "ccs_fragment_wires", "ccs_get_tableau",
-           "ccs_get_outcome_space", "ccs_get_counts", "ccs_get_dist", "ccs_get_tensor",
+           "ccs_get_outcome_space", "ccs_get_counts", "ccs_get_dist", "ccs_get_zvals", "ccs_get_tensor",
            "ccs_set_profiling", "ccs_get_stage_times", "ccs_cut_candidates", "ccs_recombine_noalloc",
            "ccs_get_tuning", "ccs_get_operand", "ccs_launch_count"]
 STAGES = ["clifford", "sample", "statevector", "fold", "recombine", "operands"]
@@ -74,7 +74,8 @@ class ccs_recomb_opts(C.Structure):
 
 class ccs_fragment_info(C.Structure):
     _fields_ = [(n, C.c_int32) for n in ("n_wires", "clifford", "n_variants", "n_qin", "n_qout",
-                                           "n_marg", "n_meas", "n_slots", "n_ops", "n_moments")]
+                                           "n_marg", "n_meas", "n_slots", "n_ops", "n_moments",
+                                           "n_zstrings")]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -120,6 +121,7 @@ def lib():
                                        C.POINTER(C.c_uint64), C.POINTER(C.c_int)], C.c_int),
             "ccs_get_counts": ([P, P, C.c_int, C.c_int, C.c_int, P], C.c_int),
             "ccs_get_dist": ([P, P, C.c_int, C.c_int, C.c_int, P], C.c_int),
+            "ccs_get_zvals": ([P, P, C.c_int, C.c_int, C.c_int, P], C.c_int),
             "ccs_get_tensor": ([P, P, C.c_int, C.c_int, P], C.c_int),
             "ccs_get_operand": ([P, P, C.c_int, C.c_int, P], C.c_int),
             "ccs_set_profiling": ([P, C.c_int], C.c_int),
@@ -390,6 +392,15 @@ def ccs_get_dist(ctx, res, problem, fragment, variant):
     out = np.zeros(1 << nA, np.float32)
     ctx.check(lib().ccs_get_dist(ctx.h, res.h, problem, fragment, variant,
                                  out.ctypes.data_as(C.c_void_p)), "ccs_get_dist")
+    return out
+
+
+def ccs_get_zvals(ctx, res, problem, fragment, variant):
+    """Z-string values of one variant: [string][subset of quantum outputs]."""
+    info = ccs_fragment_info_get(ctx, res.plan, problem, fragment)
+    out = np.zeros((info["n_zstrings"], 1 << info["n_qout"]), np.float32)
+    ctx.check(lib().ccs_get_zvals(ctx.h, res.h, problem, fragment, variant, out.ctypes.data_as(C.c_void_p)),
+              "ccs_get_zvals")
     return out
 
 

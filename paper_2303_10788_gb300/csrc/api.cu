@@ -199,6 +199,7 @@ struct ccs_plan_s {
   DevPlan dp{};
   Allocs A;
   long long n_spaces = 0, n_counts = 0, n_dist = 0, n_zval = 0, n_tab = 0, n_T = 0, n_TZ = 0, n_body = 0;
+  long long n_zimg = 0;             // uint64 words of Z images
   long long n_marg = 0, n_zexp = 0;
   std::vector<long long> t_prefix, tz_prefix, out_prefix, z_prefix, r_prefix, blk_prefix;
   long long* d_r_prefix = nullptr;
@@ -485,8 +486,9 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
   std::vector<CliffordOp> cops;
   std::vector<NCOp> nops;
   std::vector<int> moments, wires, zoffs;
-  std::vector<int2> items_c, items_nc, items_b;
+  std::vector<int2> items_c, items_nc, items_b, items_z, zblocks;
   std::vector<int> cliff_frags;
+  int img_words_max = 0, body_words_max = 0;
   int max_body_stage = 0, max_moment_ops = 1;
   int max_body_cols = 0;
   std::vector<long long> cost_c, cost_nc;
@@ -540,11 +542,17 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
       plan->n_tab += (long long)d.nv * (2 * d.n + 3) * d.W;
       d.body_off = plan->n_body;      // even: (2n+3)*W is even, so 16-byte aligned
       plan->n_body += (long long)(2 * d.n + 3) * d.W;
-      if (d.nz == 0) {   // screenable: no Z-strings need the tableau
-        d.rb_off = 65ll * (long long)cliff_frags.size();
-        cliff_frags.push_back((int)fi);
-      } else {
-        d.rb_off = -1;
+      d.rb_off = 65ll * (long long)cliff_frags.size();
+      cliff_frags.push_back((int)fi);
+      {   // Z images: every string, X, Y, Z of every quantum output, Z of every marginal wire
+        const int ni = d.nz + 3 * d.qout + d.m;
+        d.zimg_off = plan->n_zimg;
+        plan->n_zimg += (long long)ni * (2 * d.Wh + 1);
+        img_words_max = std::max(img_words_max, ni * (2 * d.Wh + 1));
+        body_words_max = std::max(body_words_max, (2 * d.n + 3) * d.W);
+        for (int k = 0; k < ni; k += 16) items_z.push_back(make_int2((int)fi, k));
+        if (d.nz > 0)
+          for (int v = 0; v < d.nv; v += zblock_variants(d.nz)) zblocks.push_back(make_int2((int)fi, v));
       }
       max_body_stage = std::max(max_body_stage, 2 * d.n + 3 + (int)f.cops.size() + (d.n_moments + 2) / 2 + 1);
       for (int mm = 0; mm < f.n_moments(); ++mm)
@@ -561,7 +569,7 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
         cost_c.push_back((long long)d.W * (d.n_moments + 4) * std::max(1, d.n / 16) + d.nz * 4 + d.nA * d.n);
       }
     } else {
-      d.space_off = d.counts_off = d.tab_off = d.body_off = d.rb_off = -1;
+      d.space_off = d.counts_off = d.tab_off = d.body_off = d.rb_off = d.zimg_off = -1;
       plan->max_nc_n = std::max(plan->max_nc_n, d.n);
       for (int v = 0; v < d.nv; ++v) {
         items_nc.push_back(make_int2((int)fi, v));
@@ -741,11 +749,12 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
   }
   DevPlan& dp = plan->dp;
   FragDev* dfr; CliffordOp* dco; NCOp* dno; int* dmo; int* dwi; int* dzo; int2* dic; int2* din; int2* dib; int* dcf;
+  int2* diz = nullptr; int2* dzb = nullptr;
   ProblemDev* dpr; CliffordOp* dpo; CliffordOp* dbo; float* dpm; float* dbm;
   Staging st;
   st.add(plan->fdev, &dfr); st.add(cops, &dco); st.add(nops, &dno); st.add(moments, &dmo); st.add(wires, &dwi);
   st.add(zoffs, &dzo); st.add(items_c, &dic); st.add(items_nc, &din); st.add(items_b, &dib);
-  st.add(cliff_frags, &dcf); st.add(plan->pdev, &dpr); st.add(prep, &dpo); st.add(basis, &dbo);
+  st.add(cliff_frags, &dcf); st.add(items_z, &diz); st.add(zblocks, &dzb); st.add(plan->pdev, &dpr); st.add(prep, &dpo); st.add(basis, &dbo);
   st.add(prepm, &dpm); st.add(basism, &dbm); st.add(plan->t_prefix, &plan->d_t_prefix);
   st.add(plan->tz_prefix, &plan->d_tz_prefix); st.add(plan->out_prefix, &plan->d_out_prefix);
   st.add(plan->z_prefix, &plan->d_z_prefix); st.add(plan->r_prefix, &plan->d_r_prefix);
@@ -757,6 +766,9 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
   dp.n_items_cliff = (int)items_c.size(); dp.n_items_nc = (int)items_nc.size();
   dp.items_body = dib; dp.n_items_body = (int)items_b.size(); dp.max_body_cols = max_body_cols;
   dp.cliff_frags = dcf; dp.n_cliff_frags = (int)cliff_frags.size();
+  dp.items_zimg = diz; dp.n_items_zimg = (int)items_z.size();
+  dp.zblocks = dzb; dp.n_zblocks = (int)zblocks.size();
+  dp.body_words_max = body_words_max; dp.img_words_max = img_words_max;
   dp.max_body_stage_words = max_body_stage;
   dp.max_moment_ops = max_moment_ops;
   dp.problems = dpr; dp.n_problems = (int)plan->pdev.size();
@@ -842,11 +854,12 @@ static int enqueue_eval(ccs_ctx c, ccs_plan p, ccs_res r) {
     if (e.shared_body) {
       if ((err = launch_body(dp, r->dr, (int)c->smem_optin, e.screen != 0, s)) != cudaSuccess)
         return cuda_fail(c, err, "body kernel");
-      if (e.screen && (err = launch_screen(dp, r->dr, e, c->sm_count, s)) != cudaSuccess)
+      if (e.screen && (err = launch_screen(dp, r->dr, e, c->sm_count, (int)c->smem_optin, s)) != cudaSuccess)
         return cuda_fail(c, err, "screen kernel");
     }
-    if ((err = launch_clifford(dp, r->dr, e, threads, e.shared_body ? 1 : r->cliff_words, smem_words, grid, s)) !=
-        cudaSuccess)
+    if (!e.screen &&
+        (err = launch_clifford(dp, r->dr, e, threads, e.shared_body ? 1 : r->cliff_words, smem_words, grid, s)) !=
+            cudaSuccess)
       return cuda_fail(c, err, "clifford kernel");
     stage_end(c, ST_CLIFFORD);
     if (e.mode == CCS_SAMPLED) {
@@ -888,7 +901,8 @@ static int autotune(ccs_ctx c, ccs_plan p, ccs_res r) {
     if (f.clifford) max_n = std::max(max_n, f.n);
   int items = 1;
   while (items < p->dp.n_items_cliff) items <<= 1;
-  const auto key = std::make_tuple((max_n + 63) / 64, items, r->ep.shots, r->ep.mode * 2 + r->ep.shared_body);
+  const auto key =
+      std::make_tuple((max_n + 63) / 64, items, r->ep.shots, r->ep.mode * 4 + r->ep.shared_body * 2 + r->ep.screen);
   auto it = c->tuned.find(key);
   if (it != c->tuned.end()) {
     std::tie(r->cliff_threads, r->cliff_words, r->sample_spc, r->hub_threads) = it->second;
@@ -920,9 +934,12 @@ static int autotune(ccs_ctx c, ccs_plan p, ccs_res r) {
   int rc = CCS_OK;
   float best = 1e30f, ms = 0.f;
   int bt = r->cliff_threads, bw = r->cliff_words, bs = r->sample_spc, bh = r->hub_threads;
-  for (int ti = 0; ti < 3 && rc == CCS_OK; ++ti)
+  // (the tableau kernel does not run after the screen: one baseline timing)
+  const int n_ti = r->ep.screen ? 1 : 3;
+  for (int ti = 0; ti < n_ti && rc == CCS_OK; ++ti)
     for (int wi = 0; wi < 4 && rc == CCS_OK; ++wi) {
       if (words_c[wi] > max_w || (r->ep.shared_body && words_c[wi] != 1)) continue;
+      if (r->ep.screen) { if ((rc = time_it(&ms)) == CCS_OK) best = ms; break; }
       r->cliff_threads = threads_c[ti];
       r->cliff_words = words_c[wi];
       if ((rc = time_it(&ms)) == CCS_OK && ms < best) { best = ms; bt = threads_c[ti]; bw = words_c[wi]; }
@@ -988,7 +1005,7 @@ int ccs_eval_variants(ccs_ctx c, ccs_plan p, const ccs_eval_opts* opts, ccs_res*
     d.work = r->A.get<unsigned>(4);
     d.body = r->A.get<unsigned long long>(std::max<long long>(p->n_body, 2));
     d.rowbasis = r->A.get<unsigned long long>(std::max<long long>(65ll * p->dp.n_cliff_frags, 1));
-    d.slow_items = r->A.get<int2>(std::max<long long>(p->dp.n_items_cliff, 1));
+    d.zimg = r->A.get<unsigned long long>(std::max<long long>(p->n_zimg, 1));
     d.status = r->A.get<unsigned>(4);
     r->scratch = r->A.get<float>(std::max<long long>(p->r_total + p->part_total, 1));
     {   // default launch shape before any tuning: wide tableaus take 8 words per op, 512 threads
@@ -1008,7 +1025,7 @@ int ccs_eval_variants(ccs_ctx c, ccs_plan p, const ccs_eval_opts* opts, ccs_res*
       r->rt_scratch = r->A.get<uint16_t>(p->rt_total);
     }
     if (!d.spaces || !d.dist || !d.zval || !d.T || !d.TQ || !d.TZ || !d.marg || !d.zexp || !d.work || !d.status ||
-        !d.body || !d.rowbasis || !d.slow_items ||
+        !d.body || !d.rowbasis || !d.zimg ||
         !r->scratch || (p->rt_total && (!d.TQh || !r->rt_scratch))) {
       delete r;
       return fail(c, CCS_ERR_OOM, "result allocation failed");
@@ -1203,6 +1220,7 @@ int ccs_fragment_info_get(ccs_ctx c, ccs_plan p, int problem, int fragment, ccs_
   out->n_slots = (int)f->slots.size();
   out->n_ops = f->clifford ? (int)f->cops.size() : (int)f->nops.size();
   out->n_moments = f->n_moments();
+  out->n_zstrings = (int)f->zwires.size();
   return CCS_OK;
 }
 
@@ -1291,6 +1309,18 @@ int ccs_get_dist(ccs_ctx c, ccs_res r, int problem, int fragment, int variant, f
   cudaError_t e = cudaMemcpy(out, r->dr.dist + d->dist_off + ((long long)variant << d->nA),
                              sizeof(float) << d->nA, cudaMemcpyDeviceToHost);
   return e == cudaSuccess ? CCS_OK : cuda_fail(c, e, "copy dist");
+}
+
+int ccs_get_zvals(ccs_ctx c, ccs_res r, int problem, int fragment, int variant, float* out) {
+  const FragDev* d;
+  int rc = locate(c, r, problem, fragment, variant, &d);
+  if (rc) return rc;
+  if (variant < 0) return fail(c, CCS_ERR_INVALID_ARG, "no variant");
+  const long long cnt = (long long)d->nz << d->qout;
+  if (cnt == 0) return CCS_OK;
+  cudaError_t e = cudaMemcpy(out, r->dr.zval + d->zval_off + (long long)variant * cnt, cnt * sizeof(float),
+                             cudaMemcpyDeviceToHost);
+  return e == cudaSuccess ? CCS_OK : cuda_fail(c, e, "copy Z values");
 }
 
 int ccs_get_operand(ccs_ctx c, ccs_res r, int problem, int fragment, float* out) {

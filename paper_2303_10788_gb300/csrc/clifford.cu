@@ -256,15 +256,178 @@ __global__ void __launch_bounds__(256) body_kernel(DevPlan P, DevRes R, int smem
 namespace {
 }  // namespace
 
-// --- shared-row basis: one CTA per Clifford fragment ----------------------
-// Every variant of a fragment keeps the body's stabilizer rows outside its
-// quantum inputs; only the input rows and the output columns change.  The
-// rank of a variant's measured set A therefore follows from the span of
-// those shared rows, taken as extended vectors e_i = (X bits on A, Z bits on
-// the quantum outputs) so that any output basis change maps them linearly.
-// This kernel stores an echelon basis of that span (pivot = lowest set bit)
-// in 64 pivot slots plus the pivot mask.
+// --- Z images -------------------------------------------------------------
+// Pauli expectations of a variant without its tableau.  With the body's rows
+// D_j = U X_j U^+ and S_j = U Z_j U^+ (signs included), every Pauli Q on the
+// output side decomposes as Q = i^-e (prod_j D_j^a_j)(prod_j S_j^b_j), where
+// a_j / b_j say whether Q anticommutes with S_j / D_j (the rows form a
+// symplectic basis) and i^e is the phase of that ordered product of rows.
+// (D_j commutes with every S_k, k != j, so this order equals the interleaved
+// one.)  Conjugating back, U^+ Q U = i^-e X^a Z^b: the backward image.  A
+// variant prepares the product state |psi> = (x)_j C_j|0> and measures
+// O_o = C'^+ Z C' at quantum output o, so the expectation of a product of
+// such Paulis on distinct wires is <psi| prod U^+ Q U |psi>: a product of
+// backward images, evaluated on a product state (Aaronson-Gottesman, Sec.
+// III, for the row products; the cut identity of Sec. IV for the states and
+// observables).  Z-string values and the offsets of rank-deficient outcome
+// spaces are both such expectations.
+//
+// Records of a fragment (2 Wh + 1 words each: a in [0, Wh), b in [Wh, 2Wh),
+// the phase exponent -e mod 4 last): k < nz is Z-string k; k = nz + 3 o + d
+// is the observable of quantum output o in basis d (0 X, 1 Y, 2 Z: the basis
+// changes H, S^+ then H, and none); k = nz + 3 qout + t is Z on marginal
+// wire t.
 namespace {
+
+__device__ __forceinline__ unsigned long long warp_xor64(unsigned long long x) {
+  for (int o = 16; o; o >>= 1) x ^= __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// One record, by one warp.  tab: the fragment's body tableau (shared or
+// global memory); scratch: 4 kMaxWh words of the warp's shared memory.
+__device__ void z_image(const DevPlan& P, const DevRes& R, const FragDev& F, int k, const unsigned long long* tab,
+                        int lane, unsigned long long* scratch) {
+  const int n = F.n, W = F.W, Wh = F.Wh, zb = n + 1, rcol = 2 * (n + 1);
+  unsigned long long* sel = scratch;                  // W words: rows of the product
+  unsigned long long* ex = scratch + 2 * kMaxWh;      // expected x bits of Q
+  unsigned long long* ez = scratch + 3 * kMaxWh;      // expected z bits of Q
+  if (lane < Wh) { ex[lane] = 0ull; ez[lane] = 0ull; }
+  __syncwarp();
+  unsigned long long acc = 0ull;        // lane w < W: anticommutation bits of the rows in word w
+  if (k < F.nz) {
+    // Z_S: the x-columns of the string's wires, XORed (lanes over wires)
+    const int q0 = P.zoffs[F.zw_off + k], q1 = P.zoffs[F.zw_off + k + 1];
+    for (int t0 = q0; t0 < q1; t0 += 32) {
+      const int wq = t0 + lane < q1 ? P.wires[t0 + lane] : -1;
+      if (wq >= 0) atomicXor(&ez[wq >> 6], 1ull << (wq & 63));
+      for (int w = 0; w < W; ++w) {
+        const unsigned long long x = warp_xor64(wq >= 0 ? tab[(size_t)wq * W + w] : 0ull);
+        if (lane == w) acc ^= x;
+      }
+    }
+  } else {
+    int wq;
+    bool ox, oz;
+    if (k < F.nz + 3 * F.qout) {
+      const int o = (k - F.nz) / 3, d = (k - F.nz) % 3;
+      wq = P.wires[F.qout_off + o];
+      ox = d != 2;                     // X, Y or Z on wire wq
+      oz = d != 0;
+    } else {
+      wq = P.wires[F.A_off + (k - F.nz - 3 * F.qout)];
+      ox = false;
+      oz = true;
+    }
+    if (lane < W) {
+      if (ox) acc ^= tab[(size_t)(zb + wq) * W + lane];
+      if (oz) acc ^= tab[(size_t)wq * W + lane];
+    }
+    if (lane == 0) {
+      if (ox) ex[wq >> 6] = 1ull << (wq & 63);
+      if (oz) ez[wq >> 6] = 1ull << (wq & 63);
+    }
+  }
+  // destabilizer rows are selected by a (stabilizer-half bits), stabilizer rows by b
+  if (lane < W) sel[lane < Wh ? lane + Wh : lane - Wh] = acc;
+  __syncwarp();
+  int e = 0;
+  unsigned bad = 0;
+  for (int j = lane; j < n; j += 32) {
+    unsigned cx = 0, cz = 0;
+    for (int w = 0; w < W; ++w) {
+      const unsigned long long sw = sel[w];
+      const unsigned long long x = tab[(size_t)j * W + w] & sw;
+      const unsigned long long z = tab[(size_t)(zb + j) * W + w] & sw;
+      const unsigned long long px = prefix_xor_excl(x) ^ (cx ? ~0ull : 0ull);
+      const unsigned long long pz = prefix_xor_excl(z) ^ (cz ? ~0ull : 0ull);
+      const unsigned long long X1 = px & ~pz, Y1 = px & pz, Z1 = ~px & pz;
+      const unsigned long long X2 = x & ~z, Y2 = x & z, Z2 = ~x & z;
+      const unsigned long long plus = (X1 & Y2) | (Y1 & Z2) | (Z1 & X2);
+      const unsigned long long minus = (X1 & Z2) | (Y1 & X2) | (Z1 & Y2);
+      e += __popcll(plus) - __popcll(minus);
+      cx ^= __popcll(x) & 1;
+      cz ^= __popcll(z) & 1;
+    }
+    // the product must be Q itself up to phase
+    if (cx != (unsigned)((ex[j >> 6] >> (j & 63)) & 1ull) || cz != (unsigned)((ez[j >> 6] >> (j & 63)) & 1ull))
+      bad = 1;
+  }
+  if (lane < W) e += 2 * __popcll(tab[(size_t)rcol * W + lane] & sel[lane]);
+  for (int o = 16; o; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(R.status, 1u);
+  unsigned long long* out = R.zimg + F.zimg_off + (long long)k * (2 * Wh + 1);
+  if (lane < W) out[lane] = sel[lane];   // a = sel[0, Wh), b = sel[Wh, 2 Wh)
+  if (lane == 0) out[2 * Wh] = (unsigned long long)(((-e) % 4 + 4) % 4);
+}
+
+// Expectation in {-1, 0, 1} of a variant (preparation digits `pin`, basis
+// digits `pout`, two bits each) for the product of record zi (a Z-string;
+// -1 for none) and the measured Paulis M_t, t in `amask` (t < m: Z on
+// marginal wire t; t >= m: the observable of output t - m).  The images
+// multiply as U^+ Q U = i^E X^A Z^B; then A must vanish off the quantum
+// inputs and on input j the pattern (A_j, B_j) must be the prepared state's
+// stabilizer (|0>: Z, |1>: -Z, |+>: X, |+i>: Y = i XZ).
+__device__ int pauli_value(const unsigned long long* img, const FragDev& F, int zi, uint32_t amask, unsigned pin,
+                           unsigned pout, const int* qw, unsigned* status) {
+  const int Wh = F.Wh, st = 2 * Wh + 1, m = F.m, zo = F.nz, zm = F.nz + 3 * F.qout;
+  auto rec = [&](int t) -> int {
+    return t < m ? zm + t : zo + 3 * (t - m) + (int)((pout >> (2 * (t - m))) & 3u);
+  };
+  int E = zi >= 0 ? (int)img[(size_t)zi * st + 2 * Wh] : 0;
+  for (uint32_t h = amask; h; h &= h - 1) E += (int)img[(size_t)rec(__ffs(h) - 1) * st + 2 * Wh];
+  for (int w = 0; w < Wh; ++w) {
+    unsigned long long A = 0ull, B = 0ull;
+    if (zi >= 0) {
+      A = img[(size_t)zi * st + w];
+      B = img[(size_t)zi * st + Wh + w];
+    }
+    for (uint32_t h = amask; h; h &= h - 1) {
+      const unsigned long long* r = img + (size_t)rec(__ffs(h) - 1) * st;
+      const unsigned long long a = r[w];
+      E += 2 * __popcll(B & a);
+      A ^= a;
+      B ^= r[Wh + w];
+    }
+    for (int i = 0; i < F.qin; ++i) {
+      const int q = qw[i];
+      if ((q >> 6) != w) continue;
+      const unsigned code = (unsigned)((A >> (q & 63)) & 1ull) | ((unsigned)((B >> (q & 63)) & 1ull) << 1);
+      A &= ~(1ull << (q & 63));
+      if (code == 0) continue;
+      const unsigned s = (pin >> (2 * i)) & 3u;       // 0 |0>, 1 |1>, 2 |+>, 3 |+i>
+      const unsigned want = s < 2 ? 2u : s == 2 ? 1u : 3u;
+      if (code != want) return 0;
+      E += s == 1 ? 2 : s == 3 ? 3 : 0;
+    }
+    if (A) return 0;                                   // X or Y on a |0> input
+  }
+  E &= 3;
+  if (E & 1) {
+    atomicOr(status, 1u);
+    return 0;
+  }
+  return E ? -1 : 1;
+}
+
+__device__ __forceinline__ unsigned pack_in_digits(int v, int qin) {
+  unsigned p = 0;
+  for (int i = 0; i < qin; ++i) {
+    p |= (unsigned)(v % 4) << (2 * i);
+    v /= 4;
+  }
+  return p;
+}
+__device__ __forceinline__ unsigned pack_out_digits(int v, int qin, int qout) {
+  for (int i = 0; i < qin; ++i) v /= 4;
+  unsigned p = 0;
+  for (int o = 0; o < qout; ++o) {
+    p |= (unsigned)(v % 3) << (2 * o);
+    v /= 3;
+  }
+  return p;
+}
+
 // Fold `row` into the warp's echelon basis eb[] (pivot slots) / have.
 __device__ __forceinline__ void absorb64(unsigned long long row, unsigned long long* eb, unsigned long long& have,
                                          int ne, int lane) {
@@ -287,14 +450,41 @@ __device__ __forceinline__ void absorb64(unsigned long long row, unsigned long l
 }
 }  // namespace
 
-__global__ void __launch_bounds__(512) body_basis_kernel(DevPlan P, DevRes R) {
+// --- shared-row basis and Z images ----------------------------------------
+// CTAs [0, n_cliff_frags): one per Clifford fragment.  Every variant keeps
+// the body's stabilizer rows outside its quantum inputs; only the input rows
+// and the output columns change.  The rank of a variant's measured set A
+// therefore follows from the span of those shared rows, taken as extended
+// vectors e_i = (X bits on A, Z bits on the quantum outputs) so that any
+// output basis change maps them linearly.  The CTA stores an echelon basis
+// of that span (pivot = lowest set bit) in 64 pivot slots plus the pivot mask.
+// CTAs after those: 16 Z-image records of one fragment each, one per warp,
+// from the body staged in shared memory when it fits (stage_words).
+__global__ void __launch_bounds__(512) body_basis_kernel(DevPlan P, DevRes R, int stage_words) {
+  extern __shared__ __align__(16) unsigned long long s_body[];
   __shared__ unsigned long long s_eb[16][64];
   __shared__ unsigned long long s_eh[16];
   __shared__ int s_col[64];
   __shared__ int s_in[kMaxCuts];
   __shared__ unsigned long long s_cw[64][kMaxWh];   // stabilizer halves of the extended columns
-  const FragDev& F = P.frags[P.cliff_frags[blockIdx.x]];
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
+  if ((int)blockIdx.x >= P.n_cliff_frags) {
+    const int2 it = P.items_zimg[(int)blockIdx.x - P.n_cliff_frags];   // (fragment, first record)
+    const FragDev& F = P.frags[it.x];
+    const int words = (2 * F.n + 3) * F.W;
+    const unsigned long long* tab = R.body + F.body_off;
+    if (words <= stage_words) {
+      const ulonglong2* src = reinterpret_cast<const ulonglong2*>(tab);
+      ulonglong2* dst = reinterpret_cast<ulonglong2*>(s_body);
+      for (int i = tid; i < words / 2; i += nt) dst[i] = src[i];   // words is even, body_off even
+      __syncthreads();
+      tab = s_body;
+    }
+    const int k = it.y + warp;
+    if (k < F.nz + 3 * F.qout + F.m) z_image(P, R, F, k, tab, lane, s_eb[warp]);
+    return;
+  }
+  const FragDev& F = P.frags[P.cliff_frags[blockIdx.x]];
   const int n = F.n, W = F.W, Wh = F.Wh, zb = n + 1, nA = F.nA, ne = F.nA + F.qout;
   for (int j = tid; j < ne; j += nt) s_col[j] = j < nA ? P.wires[F.A_off + j] : zb + P.wires[F.qout_off + j - nA];
   if (tid < F.qin) s_in[tid] = P.wires[F.qin_off + tid];
@@ -334,108 +524,160 @@ __global__ void __launch_bounds__(512) body_basis_kernel(DevPlan P, DevRes R) {
   }
 }
 
-// --- screen: one warp per Clifford variant ---------------------------------
-// The variant's rows on A are the shared rows mapped through its output
-// basis changes (X bit of an output wire becomes m0 x + m1 z, read off the
-// basis op's matrix) plus its new input rows (the image of C Z_i C^+ under
-// the body: D_i, S_i or their product, bits only).  Ballot elimination of
-// those <= 48 vectors gives the rank; at full rank the canonical space is
-// (off 0, identity-reduced basis) and no tableau is needed.  Otherwise, or
-// when Z-strings or tableaus are wanted, the variant is queued.
-__global__ void __launch_bounds__(256) screen_kernel(DevPlan P, DevRes R, EvalParams E) {
-  __shared__ unsigned long long s_dummy;
+// --- screen -----------------------------------------------------------------
+// CTAs [0, rank_blocks): one warp per Clifford variant.  The variant's rows
+// on A are the shared rows mapped through its output basis changes (the X
+// bit of output o becomes its observable's anticommutation bit: z for X,
+// x ^ z for Y, x for Z) plus its new input rows (the image of C Z_i C^+
+// under the body: D_i, S_i or their product, bits only).  Ballot
+// elimination of those vectors gives the echelon basis of the variant's
+// outcome space, back-substitution its unique reduced form.  Each non-pivot
+// bit j is fixed by the pivot bits, y_j = off_j ^ sum_i B_i[j] y_piv_i, so
+// off_j is the sign of <M_j prod_i M_piv_i> (B_i[j] set), from the Z images
+// (every bit is 0 at full rank).  No tableau is formed; the tableau kernel
+// runs instead of the screen only when tableaus are kept.
+// CTAs after those: (fragment, first variant) blocks of Z-string values:
+// the fragment's records staged in shared memory (img_words of them at
+// most), one (variant, string) pair per thread, every output subset u.
+__global__ void __launch_bounds__(256) screen_kernel(DevPlan P, DevRes R, EvalParams E, int rank_blocks,
+                                                     int img_words) {
+  extern __shared__ __align__(16) unsigned long long s_img[];
+  __shared__ int s_qw[kMaxCuts];
   const int lane = threadIdx.x & 31;
-  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int tw = (gridDim.x * blockDim.x) >> 5;
   const unsigned FULLW = 0xffffffffu;
-  (void)s_dummy;
+  if ((int)blockIdx.x >= rank_blocks) {
+    const int2 zbk = P.zblocks[(int)blockIdx.x - rank_blocks];
+    const FragDev& F = P.frags[zbk.x];
+    const int nz = F.nz, qout = F.qout, vpb = zblock_variants(nz);
+    const int v0 = zbk.y, vcnt = min(vpb, F.nv - v0);
+    const int words = (nz + 3 * qout + F.m) * (2 * F.Wh + 1);
+    const unsigned long long* img = R.zimg + F.zimg_off;
+    if (words <= img_words) {
+      for (int i = threadIdx.x; i < words; i += blockDim.x) s_img[i] = img[i];
+      img = s_img;
+    }
+    if (threadIdx.x < F.qin) s_qw[threadIdx.x] = P.wires[F.qin_off + threadIdx.x];
+    __syncthreads();
+    const int nq = 1 << qout;
+    for (int idx = threadIdx.x; idx < vcnt * nz; idx += blockDim.x) {
+      const int v = v0 + idx / nz, zi = idx % nz;
+      const unsigned pin = pack_in_digits(v, F.qin), pout = pack_out_digits(v, F.qin, qout);
+      float* zv = R.zval + F.zval_off + ((long long)v * nz + zi) * nq;
+      for (int u = 0; u < nq; ++u)
+        zv[u] = (float)pauli_value(img, F, zi, (uint32_t)u << F.m, pin, pout, s_qw, R.status);
+    }
+    return;
+  }
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int tw = (rank_blocks * blockDim.x) >> 5;
   for (int item = gw; item < P.n_items_cliff; item += tw) {
     const int2 it = P.items_cliff[item];
     const FragDev& F = P.frags[it.x];
     const int v = it.y;
     const int nA = F.nA, m = F.m, qout = F.qout;
-    bool slow = E.keep_tableaus || F.nz > 0 || nA > 31;
+    const unsigned pin = pack_in_digits(v, F.qin), pout = pack_out_digits(v, F.qin, qout);
+    // output basis maps: keepX / fromZ masks over A bits m..m+qout-1
+    uint32_t keepX = (1u << m) - 1u, fromZ = 0u;
+    for (int o = 0; o < qout; ++o) {
+      const unsigned d = (pout >> (2 * o)) & 3u;     // 0 X, 1 Y, 2 Z
+      if (d != 0) keepX |= 1u << (m + o);
+      if (d != 2) fromZ |= 1u << (m + o);
+    }
+    auto project = [&](unsigned long long e) -> uint32_t {
+      const uint32_t x = (uint32_t)(e & ((1ull << nA) - 1ull));
+      const uint32_t z = (uint32_t)((e >> nA) << m);
+      return (x & keepX) ^ (z & fromZ);
+    };
     uint32_t have = 0, mine = 0;
-    if (!slow) {
-      // output basis maps: keepX / fromZ masks over A bits m..m+qout-1
-      uint32_t keepX = (1u << m) - 1u, fromZ = 0u;
-      for (int o = 0; o < qout; ++o) {
-        const unsigned M = P.basis_ops[variant_out_digit(v, F.qin, o)].M;
-        if (M & 1u) keepX |= 1u << (m + o);
-        if ((M >> 1) & 1u) fromZ |= 1u << (m + o);
+    auto absorb = [&](uint32_t row) {
+      for (uint32_t h = have; h; h &= h - 1) {
+        const int p = __ffs(h) - 1;
+        const uint32_t bp = __shfl_sync(FULLW, mine, p);
+        if ((row >> p) & 1u) row ^= bp;
       }
-      auto project = [&](unsigned long long e) -> uint32_t {
-        const uint32_t x = (uint32_t)(e & ((1ull << nA) - 1ull));
-        const uint32_t z = (uint32_t)((e >> nA) << m);
-        return (x & keepX) ^ (z & fromZ);
-      };
-      auto absorb = [&](uint32_t row) {
-        for (uint32_t h = have; h; h &= h - 1) {
-          const int p = __ffs(h) - 1;
-          const uint32_t bp = __shfl_sync(FULLW, mine, p);
-          if ((row >> p) & 1u) row ^= bp;
-        }
-        for (int p = 0; p < nA; ++p) {
-          if ((have >> p) & 1u) continue;
-          const unsigned msk = __ballot_sync(FULLW, (row >> p) & 1u);
-          if (!msk) continue;
-          const int leader = __ffs(msk) - 1;
-          const uint32_t prow = __shfl_sync(FULLW, row, leader);
-          if (lane == leader) row = 0;
-          else if ((row >> p) & 1u) row ^= prow;
-          if (lane == p) mine = prow;
-          have |= 1u << p;
-        }
-      };
-      const unsigned long long* rb = R.rowbasis + F.rb_off;
-      const unsigned long long sh = rb[64];
-      absorb(((sh >> lane) & 1ull) ? project(rb[lane]) : 0u);
-      absorb(((sh >> (lane + 32)) & 1ull) ? project(rb[lane + 32]) : 0u);
-      // new stabilizer rows of the quantum inputs (bits only)
+      for (int p = 0; p < nA; ++p) {
+        if ((have >> p) & 1u) continue;
+        const unsigned msk = __ballot_sync(FULLW, (row >> p) & 1u);
+        if (!msk) continue;
+        const int leader = __ffs(msk) - 1;
+        const uint32_t prow = __shfl_sync(FULLW, row, leader);
+        if (lane == leader) row = 0;
+        else if ((row >> p) & 1u) row ^= prow;
+        if (lane == p) mine = prow;
+        have |= 1u << p;
+      }
+    };
+    const unsigned long long* rb = R.rowbasis + F.rb_off;
+    const unsigned long long sh = rb[64];
+    absorb(((sh >> lane) & 1ull) ? project(rb[lane]) : 0u);
+    absorb(((sh >> (lane + 32)) & 1ull) ? project(rb[lane + 32]) : 0u);
+    {   // new stabilizer rows of the quantum inputs (bits only): lanes over the extended columns
+      const int n = F.n, W = F.W, Wh = F.Wh, zb = n + 1, ne = nA + qout;
+      const unsigned long long* body = R.body + F.body_off;
+      int col0 = -1, col1 = -1;
+      if (lane < ne) col0 = lane < nA ? P.wires[F.A_off + lane] : zb + P.wires[F.qout_off + lane - nA];
+      if (lane + 32 < ne) col1 = zb + P.wires[F.qout_off + lane + 32 - nA];
       uint32_t row = 0;
-      if (lane < F.qin) {
-        const unsigned M = P.prep_ops[variant_in_digit(v, lane)].M;
-        const int sc = (int)((M >> 1) & 1u) | (int)(((M >> 5) & 1u) << 1);   // image of Z: 1 X, 2 Z, 3 Y
-        const int i = P.wires[F.qin_off + lane];
-        const int wd = i >> 6, b = i & 63;
-        const int n = F.n, W = F.W, Wh = F.Wh, zb = n + 1, ne = nA + qout;
-        const unsigned long long* body = R.body + F.body_off;
-        unsigned long long e = 0ull;
-        for (int j = 0; j < ne; ++j) {
-          const int col = j < nA ? P.wires[F.A_off + j] : zb + P.wires[F.qout_off + j - nA];
-          const unsigned long long d = (body[(size_t)col * W + wd] >> b) & 1ull;
-          const unsigned long long st = (body[(size_t)col * W + Wh + wd] >> b) & 1ull;
-          e |= ((sc & 1 ? d : 0ull) ^ (sc & 2 ? st : 0ull)) << j;
-        }
-        row = project(e);
+      for (int i = 0; i < F.qin; ++i) {
+        const int q = P.wires[F.qin_off + i];
+        const int wd = q >> 6, b = q & 63;
+        const unsigned s = (pin >> (2 * i)) & 3u;
+        const int sc = s < 2 ? 2 : s == 2 ? 1 : 3;   // image of Z under the preparation: 1 X, 2 Z, 3 Y
+        auto bit = [&](int col) -> unsigned {
+          if (col < 0) return 0u;
+          const unsigned d = (unsigned)(body[(size_t)col * W + wd] >> b) & 1u;
+          const unsigned st = (unsigned)(body[(size_t)col * W + Wh + wd] >> b) & 1u;
+          return ((sc & 1) ? d : 0u) ^ ((sc & 2) ? st : 0u);
+        };
+        const unsigned long long e =
+            (unsigned long long)__ballot_sync(FULLW, bit(col0)) | ((unsigned long long)__ballot_sync(FULLW, bit(col1)) << 32);
+        if (lane == i) row = project(e);
       }
       absorb(row);
-      slow = __popc(have) != nA;
     }
-    if (slow) {
-      if (lane == 0) {
-        const unsigned pos = atomicAdd(&R.work[2], 1u);
-        R.slow_items[pos] = it;
-      }
-      continue;
-    }
-    // full rank: reduce to the canonical form and record the space
+    // reduced form in pivot order; non-pivot bits' relations by ballot
     uint32_t vec = ((have >> lane) & 1u) ? mine : 0u;
     for (int q = nA - 1; q > 0; --q) {
+      if (!((have >> q) & 1u)) continue;
       const uint32_t bq = __shfl_sync(FULLW, vec, q);
       if (lane < q && ((vec >> q) & 1u)) vec ^= bq;
     }
+    const int rank = __popc(have);
+    uint32_t off = 0;
+    if (rank < nA) {
+      uint32_t amask = 0;
+      for (int j = 0; j < nA; ++j) {
+        if ((have >> j) & 1u) continue;
+        const unsigned bm = __ballot_sync(FULLW, ((have >> lane) & 1u) && ((vec >> j) & 1u));
+        if (lane == j) amask = bm | (1u << j);
+      }
+      int z = 1;
+      if (amask) z = pauli_value(R.zimg + F.zimg_off, F, -1, amask, pin, pout, P.wires + F.qin_off, R.status);
+      if (z == 0) atomicOr(R.status, 2u);
+      off = __ballot_sync(FULLW, z < 0);
+    }
     SpaceRec& sp = R.spaces[F.space_off + v];
-    if (lane < kMaxMeas) sp.basis[lane] = lane < nA ? vec : 0u;
+    if ((have >> lane) & 1u) sp.basis[__popc(have & ((1u << lane) - 1u))] = vec;
+    else if (lane >= rank && lane < kMaxMeas) sp.basis[lane] = 0u;
     if (lane == 0) {
-      sp.off = 0u;
-      sp.rank = nA;
+      sp.off = off;
+      sp.rank = rank;
       sp.flags = 0u;
     }
+    __syncwarp();
     if (E.mode == CCS_EXACT) {
-      const float pr = ldexpf(1.0f, -nA);
+      const float pr = ldexpf(1.0f, -rank);
       float* d = R.dist + F.dist_off + ((long long)v << nA);
-      for (int y = lane; y < (1 << nA); y += 32) d[y] = pr;
+      if (rank == nA) {
+        for (int y = lane; y < (1 << nA); y += 32) d[y] = pr;
+      } else {
+        for (int c = lane; c < (1 << rank); c += 32) {   // off ^ the basis vectors c selects
+          uint32_t y = off;
+          for (int i = 0; i < rank; ++i)
+            if ((c >> i) & 1) y ^= sp.basis[i];
+          d[y] = pr;
+        }
+      }
     }
   }
 }
@@ -474,10 +716,8 @@ __global__ void __launch_bounds__(512) clifford_kernel(DevPlan P, DevRes R, Eval
     __syncthreads();
     const int item = s_item;
     __syncthreads();
-    // after the rank screen only the variants it queued come here
-    const int n_items = E.screen ? (int)*reinterpret_cast<volatile unsigned*>(&R.work[2]) : P.n_items_cliff;
-    if (item >= n_items) break;
-    const int2 it = E.screen ? R.slow_items[item] : P.items_cliff[item];
+    if (item >= P.n_items_cliff) break;
+    const int2 it = P.items_cliff[item];
     {   // the fragment record, once per item, into shared memory
       const int* src = reinterpret_cast<const int*>(P.frags + it.x);
       int* dst = reinterpret_cast<int*>(&sF);
@@ -1204,16 +1444,27 @@ cudaError_t launch_body(const DevPlan& p, const DevRes& r, int smem_optin, bool 
   err = cudaGetLastError();
   if (!basis) return err;
   if (err != cudaSuccess || p.n_cliff_frags == 0) return err;
-  body_basis_kernel<<<p.n_cliff_frags, 512, 0, s>>>(p, r); note_launch();
+  // image CTAs stage their fragment's body when it fits beside the static buffers
+  const int stage = std::min(p.body_words_max, (smem_optin - 20 * 1024) / 8) & ~1;
+  err = cudaFuncSetAttribute(body_basis_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, stage * 8);
+  if (err != cudaSuccess) return err;
+  body_basis_kernel<<<p.n_cliff_frags + p.n_items_zimg, 512, (size_t)stage * 8, s>>>(p, r, stage); note_launch();
   return cudaGetLastError();
 }
 
-cudaError_t launch_screen(const DevPlan& p, const DevRes& r, const EvalParams& e, int sm_count, cudaStream_t s) {
+cudaError_t launch_screen(const DevPlan& p, const DevRes& r, const EvalParams& e, int sm_count, int smem_optin,
+                          cudaStream_t s) {
   if (p.n_items_cliff == 0) return cudaSuccess;
   const int warps = 8;
   const long long need = (p.n_items_cliff + warps - 1) / warps;
-  const int grid = (int)(need < (long long)sm_count * 8 ? need : (long long)sm_count * 8);
-  screen_kernel<<<grid, 32 * warps, 0, s>>>(p, r, e); note_launch();
+  const int rank_blocks = (int)(need < (long long)sm_count * 8 ? need : (long long)sm_count * 8);
+  const int img = p.n_zblocks ? std::min(p.img_words_max, std::min(4096, smem_optin / 8)) : 0;
+  if (img) {
+    cudaError_t err = cudaFuncSetAttribute(screen_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, img * 8);
+    if (err != cudaSuccess) return err;
+  }
+  screen_kernel<<<rank_blocks + p.n_zblocks, 32 * warps, (size_t)img * 8, s>>>(p, r, e, rank_blocks, img);
+  note_launch();
   return cudaGetLastError();
 }
 

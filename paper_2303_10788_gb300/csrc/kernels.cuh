@@ -31,6 +31,7 @@ struct FragDev {
   long long TZ_off;        // float index of T_f^S (nz x 4^n_slots)
   long long body_off;      // uint64 index of the shared body tableau ((2n+3)*W words), Clifford only
   long long rb_off;        // uint64 index of the shared-row basis (64 slots + pivot mask), Clifford only
+  long long zimg_off;      // uint64 index of the Z images (nz + 3 qout + m records of 2 Wh + 1 words)
 };
 
 // Canonical affine outcome space of a Clifford variant.
@@ -76,6 +77,12 @@ struct DevPlan {
   int max_moment_ops;         // widest gate moment of any Clifford fragment
   const int* cliff_frags;     // every Clifford fragment (shared-row bases)
   int n_cliff_frags;
+  const int2* items_zimg;     // (frag, first record) of each block of 16 Z-image records
+  int n_items_zimg;
+  const int2* zblocks;        // (frag, first variant) of each block of Z-string values
+  int n_zblocks;
+  int body_words_max;         // widest Clifford body tableau, uint64 words
+  int img_words_max;          // most Z-image words of one fragment
   const ProblemDev* problems;
   int n_problems;
   const CliffordOp* prep_ops;  // 4
@@ -92,7 +99,7 @@ struct DevRes {
   unsigned long long* tabs;
   unsigned long long* body;   // body tableaus, one per Clifford fragment
   unsigned long long* rowbasis;   // shared-row bases, 65 words per Clifford fragment
-  int2* slow_items;           // variants the screen could not finish (count in work[2])
+  unsigned long long* zimg;   // Z images: backward images of the Z-strings and output observables
   float* T;
   float* TQ;               // contraction operands: Q for hubs, T' for the other fragments
   uint16_t* TQh;           // bf16 copy of the hubs' Q (tensor-core path), may be null
@@ -103,12 +110,15 @@ struct DevRes {
   unsigned int* status;       // device-side error word
 };
 
+// Variants per block of Z-string values (about 256 (variant, string) pairs).
+__host__ __device__ inline int zblock_variants(int nz) { return nz >= 256 ? 1 : 256 / nz; }
+
 struct EvalParams {
   int mode;                   // CCS_EXACT / CCS_SAMPLED
   uint32_t shots, seed_lo, seed_hi;
   int keep_tableaus;
   int shared_body;            // 1: variants start from their fragment's body tableau
-  int screen;                 // 1: the rank screen runs; the tableau kernel takes its queue
+  int screen;                 // 1: the screen finishes every Clifford variant (no tableau kernel)
   int hub_sampler;            // host only: the caller's hub sampler choice (0 automatic)
   double inv_shots;
 };
@@ -123,11 +133,15 @@ long long launch_count();
 // words_per_op: 64-row words of one fused op a thread updates (1, 2, 4 or 8)
 // Body tableau of every Clifford fragment (identity evolved by the gate
 // sequence, no preparations or basis changes), one CTA per 64-row word.
+// With basis set, a second launch writes the shared-row bases and the Z
+// images the screen needs.
 cudaError_t launch_body(const DevPlan& p, const DevRes& r, int smem_optin, bool basis, cudaStream_t s);
-// Screen of every Clifford variant from its fragment's shared-row basis: a
-// variant whose measured set has full rank (no Z-strings, no tableau kept)
-// is finished here; the others are queued for the tableau kernel.
-cudaError_t launch_screen(const DevPlan& p, const DevRes& r, const EvalParams& e, int sm_count, cudaStream_t s);
+// Screen of every Clifford variant from its fragment's shared-row basis and
+// Z images: outcome space (rank, reduced basis, offset) and Z-string values,
+// without a tableau per variant.  Used unless tableaus are kept; then the
+// tableau kernel (launch_clifford) takes every variant instead.
+cudaError_t launch_screen(const DevPlan& p, const DevRes& r, const EvalParams& e, int sm_count, int smem_optin,
+                          cudaStream_t s);
 cudaError_t launch_clifford(const DevPlan& p, const DevRes& r, const EvalParams& e,
                             int threads, int words_per_op, int smem_words, int grid, cudaStream_t s);
 cudaError_t launch_sample(const DevPlan& p, const DevRes& r, const EvalParams& e, const int2* items,

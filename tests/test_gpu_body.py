@@ -11,7 +11,8 @@ import numpy as np
 import pytest
 
 from paper_2303_10788_gb300 import ccs
-from workloads import config2, config4, small_star
+from workloads import Workload, config1, config2, config4, small_star
+from workloads.circuits import zstrings_for
 
 pytestmark = pytest.mark.gpu
 SEED = (0x1234, 0x5678)
@@ -98,3 +99,43 @@ def test_screen_config3_all_variants(ctx):
     ma, _ = ccs.ccs_recombine(ctx, plan, ra, precision=ccs.CCS_FP32)
     mb, _ = ccs.ccs_recombine(ctx, plan, rb, precision=ccs.CCS_FP32)
     assert np.array_equal(ma, mb)
+
+
+def _with_zstrings(ws, count, seed):
+    rng = np.random.default_rng(seed)
+    return [Workload(w.name, w.circuit, w.cuts, w.marginal, zstrings_for(w.circuit.n_qubits, count, rng, 8),
+                     w.shots, w.seed, w.regions) for w in ws]
+
+
+@pytest.mark.parametrize("ws", [
+    [small_star(n=12, depth=9, region_full=(0, 1, 2, 3), boundary=4, window=(2, 6))],
+    [config1()],
+    [config2()],
+    _with_zstrings(config4(64)[:16], 24, 5),
+], ids=["star12", "config1", "config2", "config4x16z"])
+def test_zimages_match_tableau_kernel(ctx, ws):
+    """Z-string values from the fragments' Z images (the default path: no
+    tableau per variant) equal those the tableau kernel derives from each
+    variant's final tableau (taken when tableaus are kept), for every
+    variant, string and output subset; so do the recombined expectations."""
+    plan = ccs.ccs_build_fragments(ctx, ws)
+    kw = dict(mode=ccs.CCS_EXACT, seed_lo=SEED[0], seed_hi=SEED[1])
+    ra = ccs.ccs_eval_variants(ctx, plan, **kw)
+    rb = ccs.ccs_eval_variants(ctx, plan, keep_tableaus=True, **kw)
+    ma, za = ccs.ccs_recombine(ctx, plan, ra)
+    mb, zb = ccs.ccs_recombine(ctx, plan, rb)
+    assert np.array_equal(za, zb) and np.array_equal(ma, mb)
+    n = nonzero = 0
+    for pi in range(len(ws)):
+        nf, _ = ccs.ccs_plan_counts(ctx, plan, pi)
+        for f in range(nf):
+            info = ccs.ccs_fragment_info_get(ctx, plan, pi, f)
+            if not info["clifford"] or info["n_zstrings"] == 0:
+                continue
+            for v in range(info["n_variants"]):
+                a = ccs.ccs_get_zvals(ctx, ra, pi, f, v)
+                b = ccs.ccs_get_zvals(ctx, rb, pi, f, v)
+                assert np.array_equal(a, b), (pi, f, v)
+                n += a.size
+                nonzero += int(np.count_nonzero(a))
+    assert n >= 64 and 0 < nonzero < n
