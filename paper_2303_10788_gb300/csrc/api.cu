@@ -542,7 +542,7 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
       plan->n_tab += (long long)d.nv * (2 * d.n + 3) * d.W;
       d.body_off = plan->n_body;      // even: (2n+3)*W is even, so 16-byte aligned
       plan->n_body += (long long)(2 * d.n + 3) * d.W;
-      d.rb_off = 65ll * (long long)cliff_frags.size();
+      d.rb_off = (long long)kRowBasisWords * (long long)cliff_frags.size();
       cliff_frags.push_back((int)fi);
       {   // Z images: every string, X, Y, Z of every quantum output, Z of every marginal wire
         const int ni = d.nz + 3 * d.qout + d.m;
@@ -550,7 +550,7 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
         plan->n_zimg += (long long)ni * (2 * d.Wh + 1);
         img_words_max = std::max(img_words_max, ni * (2 * d.Wh + 1));
         body_words_max = std::max(body_words_max, (2 * d.n + 3) * d.W);
-        for (int k = 0; k < ni; k += 16) items_z.push_back(make_int2((int)fi, k));
+        for (int k = 0; k < ni; ++k) items_z.push_back(make_int2((int)fi, k));
         if (d.nz > 0)
           for (int v = 0; v < d.nv; v += zblock_variants(d.nz)) zblocks.push_back(make_int2((int)fi, v));
       }
@@ -821,7 +821,8 @@ static int enqueue_eval(ccs_ctx c, ccs_plan p, ccs_res r) {
   cudaStream_t s = c->stream;
   const EvalParams& e = r->ep;
   cudaError_t err;
-  if ((err = cudaMemsetAsync(r->dr.work, 0, 4 * sizeof(unsigned), s)) != cudaSuccess) return cuda_fail(c, err, "memset");
+  if ((err = cudaMemsetAsync(r->dr.work, 0, (4 + (size_t)p->dp.n_cliff_frags) * sizeof(unsigned), s)) != cudaSuccess)
+    return cuda_fail(c, err, "memset");
   if (e.mode == CCS_SAMPLED && p->n_counts_plain)
     if ((err = cudaMemsetAsync(r->dr.counts, 0, p->n_counts_plain * sizeof(uint32_t), s)) != cudaSuccess)
       return cuda_fail(c, err, "memset counts");
@@ -837,7 +838,7 @@ static int enqueue_eval(ccs_ctx c, ccs_plan p, ccs_res r) {
   }
   if (dp.n_items_nc) {
     int grid = std::min(dp.n_items_nc, c->sm_count * 4);
-    int threads = std::min(256, std::max(32, 1 << std::max(0, p->max_nc_n - 2)));
+    int threads = std::min(512, std::max(32, 1 << p->max_nc_n));   // one output amplitude per thread
     stage_begin(c, ST_STATEVEC);
     if ((err = launch_statevector(dp, r->dr, p->max_nc_n, threads, grid, s2)) != cudaSuccess)
       return cuda_fail(c, err, "statevector kernel");
@@ -1002,10 +1003,12 @@ int ccs_eval_variants(ccs_ctx c, ccs_plan p, const ccs_eval_opts* opts, ccs_res*
     d.TZ = r->A.get<float>(std::max<long long>(p->n_TZ, 1));
     d.marg = r->A.get<double>(std::max<long long>(p->n_marg, 1));
     d.zexp = r->A.get<double>(std::max<long long>(p->n_zexp, 1));
-    d.work = r->A.get<unsigned>(4);
+    d.work = r->A.get<unsigned>(4 + (long long)p->dp.n_cliff_frags);   // + per-fragment record counters
+    d.fragcnt = d.work ? d.work + 4 : nullptr;
     d.body = r->A.get<unsigned long long>(std::max<long long>(p->n_body, 2));
-    d.rowbasis = r->A.get<unsigned long long>(std::max<long long>(65ll * p->dp.n_cliff_frags, 1));
+    d.rowbasis = r->A.get<unsigned long long>(std::max<long long>((long long)kRowBasisWords * p->dp.n_cliff_frags, 1));
     d.zimg = r->A.get<unsigned long long>(std::max<long long>(p->n_zimg, 1));
+
     d.status = r->A.get<unsigned>(4);
     r->scratch = r->A.get<float>(std::max<long long>(p->r_total + p->part_total, 1));
     {   // default launch shape before any tuning: wide tableaus take 8 words per op, 512 threads
@@ -1025,7 +1028,7 @@ int ccs_eval_variants(ccs_ctx c, ccs_plan p, const ccs_eval_opts* opts, ccs_res*
       r->rt_scratch = r->A.get<uint16_t>(p->rt_total);
     }
     if (!d.spaces || !d.dist || !d.zval || !d.T || !d.TQ || !d.TZ || !d.marg || !d.zexp || !d.work || !d.status ||
-        !d.body || !d.rowbasis || !d.zimg ||
+        !d.body || !d.rowbasis || !d.zimg || !d.fragcnt ||
         !r->scratch || (p->rt_total && (!d.TQh || !r->rt_scratch))) {
       delete r;
       return fail(c, CCS_ERR_OOM, "result allocation failed");

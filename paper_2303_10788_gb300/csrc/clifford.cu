@@ -284,61 +284,67 @@ __device__ __forceinline__ unsigned long long warp_xor64(unsigned long long x) {
   return x;
 }
 
-// One record, by one warp.  tab: the fragment's body tableau (shared or
-// global memory); scratch: 4 kMaxWh words of the warp's shared memory.
-__device__ void z_image(const DevPlan& P, const DevRes& R, const FragDev& F, int k, const unsigned long long* tab,
-                        int lane, unsigned long long* scratch) {
+// One record, by one CTA: the anticommutation bits (acc, by warp 0), then
+// the ordered row product with its phase, threads over the body's columns.
+// The body stays in global memory: a column's W words share one or two
+// 128-byte lines, so after the first touch they come from L1.
+__device__ void z_image(const DevPlan& P, const DevRes& R, const FragDev& F, int k, unsigned long long* s_sel,
+                        unsigned long long* s_ex, unsigned long long* s_ez, int* s_e, unsigned* s_bad) {
   const int n = F.n, W = F.W, Wh = F.Wh, zb = n + 1, rcol = 2 * (n + 1);
-  unsigned long long* sel = scratch;                  // W words: rows of the product
-  unsigned long long* ex = scratch + 2 * kMaxWh;      // expected x bits of Q
-  unsigned long long* ez = scratch + 3 * kMaxWh;      // expected z bits of Q
-  if (lane < Wh) { ex[lane] = 0ull; ez[lane] = 0ull; }
-  __syncwarp();
-  unsigned long long acc = 0ull;        // lane w < W: anticommutation bits of the rows in word w
-  if (k < F.nz) {
-    // Z_S: the x-columns of the string's wires, XORed (lanes over wires)
-    const int q0 = P.zoffs[F.zw_off + k], q1 = P.zoffs[F.zw_off + k + 1];
-    for (int t0 = q0; t0 < q1; t0 += 32) {
-      const int wq = t0 + lane < q1 ? P.wires[t0 + lane] : -1;
-      if (wq >= 0) atomicXor(&ez[wq >> 6], 1ull << (wq & 63));
-      for (int w = 0; w < W; ++w) {
-        const unsigned long long x = warp_xor64(wq >= 0 ? tab[(size_t)wq * W + w] : 0ull);
-        if (lane == w) acc ^= x;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
+  const unsigned long long* tab = R.body + F.body_off;
+  if (tid < Wh) { s_ex[tid] = 0ull; s_ez[tid] = 0ull; }
+  if (tid == 0) { *s_e = 0; *s_bad = 0u; }
+  __syncthreads();
+  if (tid < 32) {
+    unsigned long long acc = 0ull;      // lane w < W: anticommutation bits of the rows in word w
+    if (k < F.nz) {
+      // Z_S: the x-columns of the string's wires, XORed (lanes over wires)
+      const int q0 = P.zoffs[F.zw_off + k], q1 = P.zoffs[F.zw_off + k + 1];
+      for (int t0 = q0; t0 < q1; t0 += 32) {
+        const int wq = t0 + lane < q1 ? P.wires[t0 + lane] : -1;
+        if (wq >= 0) atomicXor(&s_ez[wq >> 6], 1ull << (wq & 63));
+        for (int w = 0; w < W; ++w) {
+          const unsigned long long x = warp_xor64(wq >= 0 ? tab[(size_t)wq * W + w] : 0ull);
+          if (lane == w) acc ^= x;
+        }
+      }
+    } else {
+      int wq;
+      bool ox, oz;
+      if (k < F.nz + 3 * F.qout) {
+        const int o = (k - F.nz) / 3, d = (k - F.nz) % 3;
+        wq = P.wires[F.qout_off + o];
+        ox = d != 2;                     // X, Y or Z on wire wq
+        oz = d != 0;
+      } else {
+        wq = P.wires[F.A_off + (k - F.nz - 3 * F.qout)];
+        ox = false;
+        oz = true;
+      }
+      if (lane < W) {
+        if (ox) acc ^= tab[(size_t)(zb + wq) * W + lane];
+        if (oz) acc ^= tab[(size_t)wq * W + lane];
+      }
+      if (lane == 0) {
+        if (ox) s_ex[wq >> 6] = 1ull << (wq & 63);
+        if (oz) s_ez[wq >> 6] = 1ull << (wq & 63);
       }
     }
-  } else {
-    int wq;
-    bool ox, oz;
-    if (k < F.nz + 3 * F.qout) {
-      const int o = (k - F.nz) / 3, d = (k - F.nz) % 3;
-      wq = P.wires[F.qout_off + o];
-      ox = d != 2;                     // X, Y or Z on wire wq
-      oz = d != 0;
-    } else {
-      wq = P.wires[F.A_off + (k - F.nz - 3 * F.qout)];
-      ox = false;
-      oz = true;
-    }
-    if (lane < W) {
-      if (ox) acc ^= tab[(size_t)(zb + wq) * W + lane];
-      if (oz) acc ^= tab[(size_t)wq * W + lane];
-    }
-    if (lane == 0) {
-      if (ox) ex[wq >> 6] = 1ull << (wq & 63);
-      if (oz) ez[wq >> 6] = 1ull << (wq & 63);
-    }
+    // destabilizer rows are selected by a (stabilizer-half bits), stabilizer rows by b
+    if (lane < W) s_sel[lane < Wh ? lane + Wh : lane - Wh] = acc;
   }
-  // destabilizer rows are selected by a (stabilizer-half bits), stabilizer rows by b
-  if (lane < W) sel[lane < Wh ? lane + Wh : lane - Wh] = acc;
-  __syncwarp();
+  __syncthreads();
   int e = 0;
   unsigned bad = 0;
-  for (int j = lane; j < n; j += 32) {
+  for (int j = tid; j < n; j += nt) {
     unsigned cx = 0, cz = 0;
+    const unsigned long long* xc = tab + (size_t)j * W;
+    const unsigned long long* zc = tab + (size_t)(zb + j) * W;
     for (int w = 0; w < W; ++w) {
-      const unsigned long long sw = sel[w];
-      const unsigned long long x = tab[(size_t)j * W + w] & sw;
-      const unsigned long long z = tab[(size_t)(zb + j) * W + w] & sw;
+      const unsigned long long sw = s_sel[w];
+      const unsigned long long x = xc[w] & sw;
+      const unsigned long long z = zc[w] & sw;
       const unsigned long long px = prefix_xor_excl(x) ^ (cx ? ~0ull : 0ull);
       const unsigned long long pz = prefix_xor_excl(z) ^ (cz ? ~0ull : 0ull);
       const unsigned long long X1 = px & ~pz, Y1 = px & pz, Z1 = ~px & pz;
@@ -350,15 +356,18 @@ __device__ void z_image(const DevPlan& P, const DevRes& R, const FragDev& F, int
       cz ^= __popcll(z) & 1;
     }
     // the product must be Q itself up to phase
-    if (cx != (unsigned)((ex[j >> 6] >> (j & 63)) & 1ull) || cz != (unsigned)((ez[j >> 6] >> (j & 63)) & 1ull))
+    if (cx != (unsigned)((s_ex[j >> 6] >> (j & 63)) & 1ull) || cz != (unsigned)((s_ez[j >> 6] >> (j & 63)) & 1ull))
       bad = 1;
   }
-  if (lane < W) e += 2 * __popcll(tab[(size_t)rcol * W + lane] & sel[lane]);
+  if (tid < W) e += 2 * __popcll(tab[(size_t)rcol * W + tid] & s_sel[tid]);
   for (int o = 16; o; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
-  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(R.status, 1u);
+  if (lane == 0) atomicAdd(s_e, e);
+  if (bad) atomicOr(s_bad, 1u);
+  __syncthreads();
+  if (tid == 0 && *s_bad) atomicOr(R.status, 1u);
   unsigned long long* out = R.zimg + F.zimg_off + (long long)k * (2 * Wh + 1);
-  if (lane < W) out[lane] = sel[lane];   // a = sel[0, Wh), b = sel[Wh, 2 Wh)
-  if (lane == 0) out[2 * Wh] = (unsigned long long)(((-e) % 4 + 4) % 4);
+  if (tid < W) out[tid] = s_sel[tid];   // a = sel[0, Wh), b = sel[Wh, 2 Wh)
+  if (tid == 0) out[2 * Wh] = (unsigned long long)(((-*s_e) % 4 + 4) % 4);
 }
 
 // Expectation in {-1, 0, 1} of a variant (preparation digits `pin`, basis
@@ -450,7 +459,7 @@ __device__ __forceinline__ void absorb64(unsigned long long row, unsigned long l
 }
 }  // namespace
 
-// --- shared-row basis and Z images ----------------------------------------
+// --- shared-row basis, Z images and offset table ----------------------------
 // CTAs [0, n_cliff_frags): one per Clifford fragment.  Every variant keeps
 // the body's stabilizer rows outside its quantum inputs; only the input rows
 // and the output columns change.  The rank of a variant's measured set A
@@ -458,30 +467,66 @@ __device__ __forceinline__ void absorb64(unsigned long long row, unsigned long l
 // vectors e_i = (X bits on A, Z bits on the quantum outputs) so that any
 // output basis change maps them linearly.  The CTA stores an echelon basis
 // of that span (pivot = lowest set bit) in 64 pivot slots plus the pivot mask.
-// CTAs after those: 16 Z-image records of one fragment each, one per warp,
-// from the body staged in shared memory when it fits (stage_words).
-__global__ void __launch_bounds__(512) body_basis_kernel(DevPlan P, DevRes R, int stage_words) {
-  extern __shared__ __align__(16) unsigned long long s_body[];
-  __shared__ unsigned long long s_eb[16][64];
-  __shared__ unsigned long long s_eh[16];
+// CTAs after those: one Z-image record each.  The last CTA to finish a
+// fragment's measurement records (Z of every marginal wire, X / Y / Z of
+// every quantum output: counted in R.fragcnt) writes the fragment's offset
+// table for rank-deficient variants: record r (r < m: marginal wire r;
+// r = m + 3 o + d: output o in basis d) gets its phase, its (a, b) bits on
+// the quantum inputs, and the parities popc(b_k & a_r) mod 2 for every
+// record k, so that the phase of any product of records needs no vectors.
+__global__ void __launch_bounds__(256) body_basis_kernel(DevPlan P, DevRes R) {
+  __shared__ unsigned long long s_eb[8][64];
+  __shared__ unsigned long long s_eh[8];
   __shared__ int s_col[64];
   __shared__ int s_in[kMaxCuts];
   __shared__ unsigned long long s_cw[64][kMaxWh];   // stabilizer halves of the extended columns
+  __shared__ unsigned long long s_zs[4 * kMaxWh];   // record scratch: sel (2 Wh), expected x, expected z
+  __shared__ int s_e;
+  __shared__ unsigned s_bad, s_last;
+  __shared__ unsigned long long s_ct[64];
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
   if ((int)blockIdx.x >= P.n_cliff_frags) {
-    const int2 it = P.items_zimg[(int)blockIdx.x - P.n_cliff_frags];   // (fragment, first record)
+    const int2 it = P.items_zimg[(int)blockIdx.x - P.n_cliff_frags];   // (fragment, record)
     const FragDev& F = P.frags[it.x];
-    const int words = (2 * F.n + 3) * F.W;
-    const unsigned long long* tab = R.body + F.body_off;
-    if (words <= stage_words) {
-      const ulonglong2* src = reinterpret_cast<const ulonglong2*>(tab);
-      ulonglong2* dst = reinterpret_cast<ulonglong2*>(s_body);
-      for (int i = tid; i < words / 2; i += nt) dst[i] = src[i];   // words is even, body_off even
-      __syncthreads();
-      tab = s_body;
+    z_image(P, R, F, it.y, s_zs, s_zs + 2 * kMaxWh, s_zs + 3 * kMaxWh, &s_e, &s_bad);
+    if (it.y < F.nz) return;                       // string records take no part in the table
+    const int m = F.m, Wh = F.Wh, nrec = m + 3 * F.qout, zm = F.nz + 3 * F.qout, st = 2 * Wh + 1;
+    const int fi = (int)(F.rb_off / kRowBasisWords);
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = atomicAdd(&R.fragcnt[fi], 1u) == (unsigned)(nrec - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (tid < 64) s_ct[tid] = 0ull;
+    if (tid < F.qin) s_in[tid] = P.wires[F.qin_off + tid];
+    __syncthreads();
+    const unsigned long long* img = R.zimg + F.zimg_off;
+    auto recp = [&](int r) { return img + (size_t)(r < m ? zm + r : F.nz + (r - m)) * st; };
+    for (int pr = tid; pr < nrec * nrec; pr += nt) {
+      const int l = pr / nrec, k = pr % nrec;       // bit k of ct[l]: popc(b_k & a_l) mod 2
+      const unsigned long long* ak = recp(k);
+      const unsigned long long* al = recp(l);
+      int c = 0;
+      for (int w = 0; w < Wh; ++w) c += __popcll(__ldcg(ak + Wh + w) & __ldcg(al + w));
+      if (c & 1) atomicOr(&s_ct[l], 1ull << k);
     }
-    const int k = it.y + warp;
-    if (k < F.nz + 3 * F.qout + F.m) z_image(P, R, F, k, tab, lane, s_eb[warp]);
+    __syncthreads();
+    unsigned long long* out = R.rowbasis + F.rb_off;
+    for (int r = tid; r < 64; r += nt) {
+      unsigned long long info = 0ull;
+      if (r < nrec) {
+        const unsigned long long* ar = recp(r);
+        info = __ldcg(ar + 2 * Wh) & 3ull;
+        for (int i = 0; i < F.qin; ++i) {
+          const int q = s_in[i];
+          info |= ((__ldcg(ar + (q >> 6)) >> (q & 63)) & 1ull) << (2 + i);
+          info |= ((__ldcg(ar + Wh + (q >> 6)) >> (q & 63)) & 1ull) << (16 + i);
+        }
+      }
+      out[65 + r] = r < nrec ? s_ct[r] : 0ull;
+      out[129 + r] = info;
+    }
     return;
   }
   const FragDev& F = P.frags[P.cliff_frags[blockIdx.x]];
@@ -651,10 +696,30 @@ __global__ void __launch_bounds__(256) screen_kernel(DevPlan P, DevRes R, EvalPa
         const unsigned bm = __ballot_sync(FULLW, ((have >> lane) & 1u) && ((vec >> j) & 1u));
         if (lane == j) amask = bm | (1u << j);
       }
-      int z = 1;
-      if (amask) z = pauli_value(R.zimg + F.zimg_off, F, -1, amask, pin, pout, P.wires + F.qin_off, R.status);
-      if (z == 0) atomicOr(R.status, 2u);
-      off = __ballot_sync(FULLW, z < 0);
+      // sign of <M_j prod M_piv> from the offset table: phases, pairwise
+      // commutation parities (product in ascending t) and the prepared inputs
+      int E = 0;
+      unsigned qa = 0, qb = 0;
+      unsigned long long S = 0ull;
+      for (uint32_t h = amask; h; h &= h - 1) {
+        const int t = __ffs(h) - 1;
+        const int r = t < m ? t : m + 3 * (t - m) + (int)((pout >> (2 * (t - m))) & 3u);
+        const unsigned long long ct = rb[65 + r], info = rb[129 + r];
+        E += (int)(info & 3ull) + 2 * (__popcll(ct & S) & 1);
+        S |= 1ull << r;
+        qa ^= (unsigned)(info >> 2) & 0x3fffu;
+        qb ^= (unsigned)(info >> 16) & 0x3fffu;
+      }
+      bool bad = false;
+      for (int i = 0; i < F.qin; ++i) {
+        const unsigned code = ((qa >> i) & 1u) | (((qb >> i) & 1u) << 1);
+        if (!code) continue;
+        const unsigned s = (pin >> (2 * i)) & 3u;       // 0 |0>, 1 |1>, 2 |+>, 3 |+i>
+        bad = bad || code != (s < 2 ? 2u : s == 2 ? 1u : 3u);
+        E += s == 1 ? 2 : s == 3 ? 3 : 0;
+      }
+      if (amask && (bad || (E & 1))) atomicOr(R.status, 2u);
+      off = __ballot_sync(FULLW, amask != 0 && (E & 2) != 0);
     }
     SpaceRec& sp = R.spaces[F.space_off + v];
     if ((have >> lane) & 1u) sp.basis[__popc(have & ((1u << lane) - 1u))] = vec;
@@ -1444,11 +1509,8 @@ cudaError_t launch_body(const DevPlan& p, const DevRes& r, int smem_optin, bool 
   err = cudaGetLastError();
   if (!basis) return err;
   if (err != cudaSuccess || p.n_cliff_frags == 0) return err;
-  // image CTAs stage their fragment's body when it fits beside the static buffers
-  const int stage = std::min(p.body_words_max, (smem_optin - 20 * 1024) / 8) & ~1;
-  err = cudaFuncSetAttribute(body_basis_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, stage * 8);
-  if (err != cudaSuccess) return err;
-  body_basis_kernel<<<p.n_cliff_frags + p.n_items_zimg, 512, (size_t)stage * 8, s>>>(p, r, stage); note_launch();
+  // fragments with no measurement record get no table: nothing reads it
+  body_basis_kernel<<<p.n_cliff_frags + p.n_items_zimg, 256, 0, s>>>(p, r); note_launch();
   return cudaGetLastError();
 }
 

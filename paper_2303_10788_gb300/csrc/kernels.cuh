@@ -30,7 +30,7 @@ struct FragDev {
   int role;                // 0 plain, 1 hub of a star (TQ = Q), 2 other fragment of a star (TQ = T')
   long long TZ_off;        // float index of T_f^S (nz x 4^n_slots)
   long long body_off;      // uint64 index of the shared body tableau ((2n+3)*W words), Clifford only
-  long long rb_off;        // uint64 index of the shared-row basis (64 slots + pivot mask), Clifford only
+  long long rb_off;        // uint64 index of the fragment's kRowBasisWords (shared-row basis + offset table)
   long long zimg_off;      // uint64 index of the Z images (nz + 3 qout + m records of 2 Wh + 1 words)
 };
 
@@ -77,7 +77,7 @@ struct DevPlan {
   int max_moment_ops;         // widest gate moment of any Clifford fragment
   const int* cliff_frags;     // every Clifford fragment (shared-row bases)
   int n_cliff_frags;
-  const int2* items_zimg;     // (frag, first record) of each block of 16 Z-image records
+  const int2* items_zimg;     // (frag, record) of every Z-image record
   int n_items_zimg;
   const int2* zblocks;        // (frag, first variant) of each block of Z-string values
   int n_zblocks;
@@ -99,7 +99,8 @@ struct DevRes {
   unsigned long long* tabs;
   unsigned long long* body;   // body tableaus, one per Clifford fragment
   unsigned long long* rowbasis;   // shared-row bases, 65 words per Clifford fragment
-  unsigned long long* zimg;   // Z images: backward images of the Z-strings and output observables
+  unsigned long long* zimg;   // Z images: backward images of the Z-strings and measured Paulis
+  unsigned* fragcnt;          // per Clifford fragment: measurement records done (zeroed per evaluation)
   float* T;
   float* TQ;               // contraction operands: Q for hubs, T' for the other fragments
   uint16_t* TQh;           // bf16 copy of the hubs' Q (tensor-core path), may be null
@@ -109,6 +110,11 @@ struct DevRes {
   unsigned int* work;         // persistent-kernel work counters
   unsigned int* status;       // device-side error word
 };
+
+// Per Clifford fragment: the shared-row basis (64 pivot slots + pivot mask)
+// and the offset table of its measured Paulis (64 commutation-parity words +
+// 64 info words).
+constexpr int kRowBasisWords = 65 + 128;
 
 // Variants per block of Z-string values (about 256 (variant, string) pairs).
 __host__ __device__ inline int zblock_variants(int nz) { return nz >= 256 ? 1 : 256 / nz; }
