@@ -202,6 +202,10 @@ struct ccs_plan_s {
   long long n_zimg = 0;             // uint64 words of Z images
   long long n_marg = 0, n_zexp = 0;
   std::vector<long long> t_prefix, tz_prefix, out_prefix, z_prefix, r_prefix, blk_prefix;
+  std::vector<int> direct_list;     // problems contracted leaf by leaf
+  int* d_direct_list = nullptr;
+  long long direct_stage_floats = 0;
+  int chain = 0;                    // some problem takes the R / GEMM / reduce chain
   long long* d_r_prefix = nullptr;
   long long* d_blk_prefix = nullptr;
   long long r_total = 0, part_total = 0, gemm_blocks = 0, rt_total = 0;
@@ -695,17 +699,41 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
       d.ntiles = (d.N + d.TN - 1) / d.TN;
       d.hub_T_off = plan->fdev[f0 + P.hub].T_off;
       d.tc = (gemm_tc_supported(d.M, d.N, d.K) && d.K >= 4096 && d.M >= 128) ? 1 : 0;
-      const long long base = (long long)d.mtiles * d.ntiles;
-      const int target = 2 * std::max(c->sm_count, 148);
-      const long long max_splits = std::max(1ll, d.K / 32);
-      d.splits = (int)std::max(1ll, std::min(max_splits, (target + base - 1) / base));
-      d.r_off = plan->r_total;
-      plan->r_total += d.K * d.N;
-      d.part_off = plan->part_total;
-      plan->part_total += (long long)d.splits * d.M * d.N;
-      d.blk_off = plan->gemm_blocks;
-      plan->gemm_blocks += base * d.splits;
-      plan->max_tile_smem = std::max(plan->max_tile_smem, 16 * (d.TM + d.TN) * 4);
+      // leaf by leaf in one CTA when every intermediate fits in shared memory
+      long long widest = d.K * d.M, A = d.M, rest = d.K;
+      int slots = 0;
+      for (int l = 0; l < d.n_frags; ++l) {
+        if (l == P.hub) continue;
+        const FragDev& L = plan->fdev[f0 + l];
+        rest >>= 2 * L.n_slots;
+        A <<= L.m;
+        slots += L.n_slots;
+        widest = std::max(widest, rest * A);
+      }
+      widest = std::max(widest, (long long)d.M + d.N);   // the scatter tables share a buffer
+      d.direct = (!d.tc && slots == d.k && widest <= kDirectSmemFloats) ? 1 : 0;
+      if (d.direct) {
+        d.splits = 1;
+        d.r_off = plan->r_total;
+        d.part_off = plan->part_total;
+        d.blk_off = plan->gemm_blocks;
+        plan->direct_list.push_back((int)plan->pdev.size());
+        plan->direct_stage_floats = std::max(plan->direct_stage_floats, widest);
+      }
+      if (!d.direct) {
+        const long long base = (long long)d.mtiles * d.ntiles;
+        const int target = 2 * std::max(c->sm_count, 148);
+        const long long max_splits = std::max(1ll, d.K / 32);
+        d.splits = (int)std::max(1ll, std::min(max_splits, (target + base - 1) / base));
+        plan->chain = 1;
+        d.r_off = plan->r_total;
+        plan->r_total += d.K * d.N;
+        d.part_off = plan->part_total;
+        plan->part_total += (long long)d.splits * d.M * d.N;
+        d.blk_off = plan->gemm_blocks;
+        plan->gemm_blocks += base * d.splits;
+        plan->max_tile_smem = std::max(plan->max_tile_smem, 16 * (d.TM + d.TN) * 4);
+      }
       if (d.tc) {
         d.rt_off = (plan->rt_total + 63) & ~63ll;
         plan->rt_total = d.rt_off + d.K * d.N;
@@ -758,7 +786,7 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
   st.add(prepm, &dpm); st.add(basism, &dbm); st.add(plan->t_prefix, &plan->d_t_prefix);
   st.add(plan->tz_prefix, &plan->d_tz_prefix); st.add(plan->out_prefix, &plan->d_out_prefix);
   st.add(plan->z_prefix, &plan->d_z_prefix); st.add(plan->r_prefix, &plan->d_r_prefix);
-  st.add(plan->blk_prefix, &plan->d_blk_prefix);
+  st.add(plan->blk_prefix, &plan->d_blk_prefix); st.add(plan->direct_list, &plan->d_direct_list);
   bool ok = st.commit(c, plan->A);
   if (!ok) { delete plan; return fail(c, CCS_ERR_OOM, "plan upload failed"); }
   dp.frags = dfr; dp.cops = dco; dp.nops = dno; dp.moments = dmo; dp.wires = dwi; dp.zoffs = dzo;
@@ -1143,6 +1171,7 @@ int ccs_recombine(ccs_ctx c, ccs_plan p, ccs_res r, const ccs_recomb_opts* opts,
   cudaSetDevice(c->device);
   const bool tc = !(opts && opts->no_tensor_cores);
   RecombSizes rz{p->r_total, p->part_total, p->gemm_blocks, p->n_marg, p->n_zexp,
+                 p->d_direct_list, (int)p->direct_list.size(), (int)p->direct_stage_floats, p->chain,
                  p->d_r_prefix, p->d_blk_prefix, p->d_out_prefix, p->d_z_prefix, p->max_tile_smem,
                  tc ? p->pdev.data() : nullptr, (int)p->pdev.size(), r->rt_scratch};
   cudaError_t e;
@@ -1411,6 +1440,7 @@ extern "C" int ccs_recombine_noalloc(ccs_ctx c, ccs_plan p, ccs_res r, int preci
     g_noalloc_addr[c->device] = ptr;
   }
   RecombSizes rz{p->r_total, p->part_total, p->gemm_blocks, p->n_marg, p->n_zexp,
+                 p->d_direct_list, (int)p->direct_list.size(), (int)p->direct_stage_floats, p->chain,
                  p->d_r_prefix, p->d_blk_prefix, p->d_out_prefix, p->d_z_prefix, p->max_tile_smem,
                  nullptr, 0, nullptr};
   e = launch_recombine(p->dp, r->dr, precision, rz, g_noalloc_addr[c->device], marginal_out, zexp_out, c->stream);

@@ -58,6 +58,7 @@ struct ProblemDev {
   long long rt_off;        // bf16 index of R'^T (N x K) in the bf16 scratch (tensor-core path)
   long long hub_T_off;     // T_off of the hub
   int tc;                  // 1: eligible for the tensor-core GEMM in BF16 mode
+  int direct;              // 1: small star: contracted leaf by leaf by one CTA in shared memory
 };
 
 // Device views of a plan + result.
@@ -115,6 +116,10 @@ struct DevRes {
 // and the offset table of its measured Paulis (64 commutation-parity words +
 // 64 info words).
 constexpr int kRowBasisWords = 65 + 128;
+
+// Largest intermediate (floats) of a star contracted leaf by leaf in shared
+// memory; larger stars take the R / GEMM / reduce chain.
+constexpr long long kDirectSmemFloats = 12288;
 
 // Variants per block of Z-string values (about 256 (variant, string) pairs).
 __host__ __device__ inline int zblock_variants(int nz) { return nz >= 256 ? 1 : 256 / nz; }
@@ -181,6 +186,10 @@ cudaError_t launch_operands(const DevPlan& p, const DevRes& r, const EvalParams&
 // partials (r_total + part_total floats).
 struct RecombSizes {
   long long r_total, part_total, gemm_blocks, out_total, z_total;
+  const int* direct_list;        // problems contracted leaf by leaf (one CTA each)
+  int n_direct;
+  int direct_stage_floats;       // floats of each of the two intermediate buffers
+  int chain;                     // 1: some problem takes the R / GEMM / reduce chain
   const long long* r_prefix;     // per problem, K*N entries
   const long long* blk_prefix;   // per problem, GEMM blocks
   const long long* out_prefix;   // per problem, M*N outputs

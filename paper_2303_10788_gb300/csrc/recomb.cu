@@ -403,6 +403,7 @@ __global__ void reduce_scatter_kernel(DevPlan P, const long long* prefix, int np
        g += (long long)gridDim.x * blockDim.x) {
     const int pi = find_seg(prefix, np, g);
     const ProblemDev& Pb = P.problems[pi];
+    if (Pb.direct) continue;                  // written by the one-pass contraction
     const long long loc = g - prefix[pi];
     const long long m = loc / Pb.N, n = loc - m * Pb.N;
     double acc = 0.0;
@@ -421,34 +422,204 @@ __global__ void reduce_scatter_kernel(DevPlan P, const long long* prefix, int np
   }
 }
 
+// Marginal index of output (m, n) of a star: hub bits, then the leaves' bits
+// in fragment order.
+__device__ __forceinline__ long long scatter_index(const DevPlan& P, const ProblemDev& Pb, long long m, long long n) {
+  long long o = 0;
+  const FragDev& Hb = P.frags[Pb.frag0 + Pb.hub];
+  for (int j = 0; j < Hb.m; ++j) o |= ((m >> j) & 1) << Hb.marg_pos[j];
+  int off = 0;
+  for (int l = 0; l < Pb.n_frags; ++l) {
+    if (l == Pb.hub) continue;
+    const FragDev& L = P.frags[Pb.frag0 + l];
+    for (int j = 0; j < L.m; ++j) o |= ((n >> (off + j)) & 1) << L.marg_pos[j];
+    off += L.m;
+  }
+  return o;
+}
+
+// Fragment descriptors of one problem, read once into shared memory so that
+// the per-element loops below do no dependent global loads.
+constexpr int kMaxProblemFrags = kMaxCuts + 1;
+constexpr int kLeafStage = 2048;   // floats of a leaf table staged in shared memory
+struct ProblemShared {
+  int nf, hub, k;
+  int m[kMaxProblemFrags], ns[kMaxProblemFrags];
+  int slot_cut[kMaxProblemFrags][kMaxCuts];
+  int marg_pos[kMaxProblemFrags][kMaxMarginal];
+  long long T_off[kMaxProblemFrags], TZ_off[kMaxProblemFrags];
+};
+
+__device__ void load_problem(const DevPlan& P, const ProblemDev& Pb, ProblemShared& S) {
+  const int t = threadIdx.x;
+  if (t == 0) { S.nf = Pb.n_frags; S.hub = Pb.hub; S.k = Pb.k; }
+  if (t < Pb.n_frags) {
+    const FragDev& L = P.frags[Pb.frag0 + t];
+    S.m[t] = L.m;
+    S.ns[t] = L.n_slots;
+    S.T_off[t] = L.T_off;
+    S.TZ_off[t] = L.TZ_off;
+    for (int i = 0; i < L.n_slots; ++i) S.slot_cut[t][i] = L.slot_cut[i];
+    for (int j = 0; j < L.m; ++j) S.marg_pos[t][j] = L.marg_pos[j];
+  }
+}
+
+// Slot digits of fragment l in cut index Pp.
+__device__ __forceinline__ int frag_digits(const ProblemShared& S, int l, long long Pp) {
+  int pl = 0;
+  for (int i = 0; i < S.ns[l]; ++i) pl |= (int)((Pp >> (2 * S.slot_cut[l][i])) & 3) << (2 * i);
+  return pl;
+}
+
 // <Z_S> = 2^-k sum_P prod_f T_f^S(P|f): one block per (problem, string),
 // FP32 products, FP64 sums, fixed-order tree reduction.
-__global__ void recombine_z_kernel(DevPlan P, DevRes R, const long long* prefix, int np, long long total,
-                                   double* zexp_out) {
-  __shared__ double red[256];
-  for (long long g = blockIdx.x; g < total; g += gridDim.x) {
-    const int pi = find_seg(prefix, np, g);
-    const ProblemDev& Pb = P.problems[pi];
-    const int zi = (int)(g - prefix[pi]);
-    const long long K = 1ll << (2 * Pb.k);
-    double part = 0.0;
-    for (long long Pp = threadIdx.x; Pp < K; Pp += blockDim.x) {
-      float t = 1.f;
-      for (int l = 0; l < Pb.n_frags; ++l) {
-        const FragDev& L = P.frags[Pb.frag0 + l];
-        int pl = 0;
-        for (int i = 0; i < L.n_slots; ++i) pl |= (int)((Pp >> (2 * L.slot_cut[i])) & 3) << (2 * i);
-        t *= R.TZ[L.TZ_off + ((long long)zi << (2 * L.n_slots)) + pl];
-      }
-      part += (double)t;
-    }
-    red[threadIdx.x] = part;
+__device__ void z_string_block(const DevPlan& P, const DevRes& R, const long long* prefix, int np, long long g,
+                               ProblemShared& S, double* red, double* zexp_out) {
+  const int pi = find_seg(prefix, np, g);
+  const ProblemDev& Pb = P.problems[pi];
+  const int zi = (int)(g - prefix[pi]);
+  load_problem(P, Pb, S);
+  __syncthreads();
+  const long long K = 1ll << (2 * S.k);
+  double part = 0.0;
+  for (long long Pp = threadIdx.x; Pp < K; Pp += blockDim.x) {
+    float t = 1.f;
+    for (int l = 0; l < S.nf; ++l)
+      t *= R.TZ[S.TZ_off[l] + ((long long)zi << (2 * S.ns[l])) + frag_digits(S, l, Pp)];
+    part += (double)t;
+  }
+  red[threadIdx.x] = part;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s; s >>= 1) {
+    if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
     __syncthreads();
-    for (int s = blockDim.x / 2; s; s >>= 1) {
-      if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+  }
+  if (threadIdx.x == 0) zexp_out[Pb.zexp_off + zi] = ldexp(red[0], -S.k);
+}
+
+// Contraction of a small star leaf by leaf (the tensor-network order of
+// Sec. V-C), one CTA per problem, every intermediate in shared memory.
+// Each cut belongs to exactly one leaf, so the cut index P splits into the
+// leaves' digit groups g_l (a leaf's digits in its slot order, so g_l is
+// the column index of T'_l).  Start from X[kc][m] = Q^T[P][m], kc the cut
+// index with the groups in leaf order (the first leaf's group lowest); each
+// leaf then replaces its group by its outputs:
+//   Y[rest][outer + A x] = sum_g X[g + G rest][outer] T'_l[x][g],
+// outer = (m, x_1, ..., x_{l-1}) of size A.  After the last leaf
+// X[outer] = C[m][n], scaled by 2^-k and scattered to marginal order.
+// 2^m K sum_l 2^(m_1+..+m_l) / 4^(s_1+..+s_l) multiply-adds instead of
+// the 2^m K 2^(m_1+..+m_L) of the Kronecker GEMM.  Sums are compensated
+// (Neumaier) FP32; operands are rounded to bf16 first in BF16 mode.
+// Blocks after the problems compute the Z-string expectations.
+__global__ void __launch_bounds__(512) contract_kernel(DevPlan P, DevRes R, int precision,
+                                                      const int* direct_list, int n_direct, int stage_floats,
+                                                      const long long* z_prefix, int np, long long z_total,
+                                                      double* marg_out, double* zexp_out) {
+  extern __shared__ __align__(16) float s_buf[];   // two buffers of stage_floats
+  __shared__ double red[512];
+  __shared__ ProblemShared S;
+  __shared__ float s_T[kLeafStage];
+  for (long long b = blockIdx.x; b < n_direct + z_total; b += gridDim.x) {
+    if (b >= n_direct) {
+      z_string_block(P, R, z_prefix, np, b - n_direct, S, red, zexp_out);
       __syncthreads();
+      continue;
     }
-    if (threadIdx.x == 0) zexp_out[Pb.zexp_off + zi] = ldexp(red[0], -Pb.k);
+    const ProblemDev& Pb = P.problems[direct_list[b]];
+    const int M = Pb.M, lm = __ffs(M) - 1;       // every extent here is a power of two
+    const int K = (int)Pb.K;
+    const float* At = R.TQ + Pb.hub_T_off;     // the hub's Q stored transposed: K x M, row-major
+    load_problem(P, Pb, S);
+    __syncthreads();
+    float* X = s_buf;
+    float* Y = s_buf + stage_floats;
+    for (int t0 = threadIdx.x; t0 < K * M; t0 += 8 * blockDim.x) {   // 8 loads in flight per thread
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int t = t0 + u * blockDim.x;
+        if (t < K * M) {
+          const int kc = t >> lm, m = t & (M - 1);
+          int k = 0, rem = kc;                   // compact index -> cut index
+          for (int l = 0; l < S.nf; ++l) {
+            if (l == S.hub) continue;
+            for (int i = 0; i < S.ns[l]; ++i) {
+              k |= (rem & 3) << (2 * S.slot_cut[l][i]);
+              rem >>= 2;
+            }
+          }
+          v[u] = At[(long long)k * M + m];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int t = t0 + u * blockDim.x;
+        if (t < K * M) X[t] = precision == CCS_BF16 ? to_bf16f(v[u]) : v[u];
+      }
+    }
+    int lA = lm, lrest = 2 * S.k;                // log2 of the outer and rest extents
+    for (int l = 0; l < S.nf; ++l) {
+      if (l == S.hub) continue;
+      const int lG = 2 * S.ns[l], G = 1 << lG, Nl = 1 << S.m[l];
+      lrest -= lG;
+      const bool tstaged = Nl * G <= kLeafStage;
+      __syncthreads();                           // X complete; previous s_T consumed
+      if (tstaged)
+        for (int i = threadIdx.x; i < Nl * G; i += blockDim.x) {
+          float v = R.TQ[S.T_off[l] + i];
+          if (precision == CCS_BF16) v = to_bf16f(v);
+          s_T[i] = v;
+        }
+      __syncthreads();
+      const int lout = lA + S.m[l], A = 1 << lA;
+      for (int e = threadIdx.x; e < (1 << (lrest + lout)); e += blockDim.x) {
+        const int r = e >> lout, rm = e & ((1 << lout) - 1);
+        const int x = rm >> lA, outer = rm & (A - 1);
+        const float* xs = X + ((r << lG) << lA) + outer;
+        const float* ts = tstaged ? s_T + x * G : nullptr;
+        float sum = 0.f, comp = 0.f;
+        for (int g = 0; g < G; ++g) {
+          float tv;
+          if (tstaged) tv = ts[g];
+          else {
+            tv = R.TQ[S.T_off[l] + (long long)x * G + g];
+            if (precision == CCS_BF16) tv = to_bf16f(tv);
+          }
+          const float p = xs[g << lA] * tv;
+          const float t2 = sum + p;               // Neumaier: keep the lost low part
+          comp += fabsf(sum) >= fabsf(p) ? (sum - t2) + p : (p - t2) + sum;
+          sum = t2;
+        }
+        Y[e] = sum + comp;
+      }
+      float* tmp = X; X = Y; Y = tmp;
+      lA = lout;
+    }
+    // X[m + M n] = C[m][n]; marginal index = hub bits of m | leaf bits of n,
+    // both tabulated in the free buffer (M + N <= 2 M N entries)
+    const int hub = S.hub, N = 1 << (lA - lm);
+    unsigned* orow = reinterpret_cast<unsigned*>(Y);
+    unsigned* ocol = orow + M;
+    for (int m = threadIdx.x; m < M; m += blockDim.x) {
+      unsigned o = 0;
+      for (int j = 0; j < S.m[hub]; ++j) o |= ((unsigned)(m >> j) & 1u) << S.marg_pos[hub][j];
+      orow[m] = o;
+    }
+    for (int n = threadIdx.x; n < N; n += blockDim.x) {
+      unsigned o = 0;
+      int off = 0;
+      for (int l = 0; l < S.nf; ++l) {
+        if (l == hub) continue;
+        for (int j = 0; j < S.m[l]; ++j) o |= ((unsigned)(n >> (off + j)) & 1u) << S.marg_pos[l][j];
+        off += S.m[l];
+      }
+      ocol[n] = o;
+    }
+    __syncthreads();
+    const double scale = ldexp(1.0, -S.k);       // exact: a power of two
+    double* out = marg_out + Pb.marg_off;
+    for (int t = threadIdx.x; t < (1 << lA); t += blockDim.x)
+      out[orow[t & (M - 1)] | ocol[t >> lm]] = (double)X[t] * scale;
     __syncthreads();
   }
 }
@@ -477,7 +648,7 @@ cudaError_t launch_recombine(const DevPlan& p, const DevRes& r, int precision, c
     return (unsigned)(b < 65535ll * 16 ? (b > 0 ? b : 1) : 65535ll * 16);
   };
   cudaError_t err = cudaSuccess;
-  if (z.out_total > 0) {
+  if (z.out_total > 0 && z.chain) {
     const bool use_tc = precision == CCS_BF16 && z.host_problems && z.rt_scratch && r.TQh;
     if (z.r_total > 0) {
       build_r_kernel<<<grid(z.r_total, 256), 256, 0, s>>>(p, r, precision, z.r_prefix, p.n_problems, z.r_total,
@@ -515,10 +686,17 @@ cudaError_t launch_recombine(const DevPlan& p, const DevRes& r, int precision, c
       if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
   }
-  if (z.z_total > 0) {
-    recombine_z_kernel<<<(unsigned)(z.z_total < 65535 ? z.z_total : 65535), 256, 0, s>>>(p, r, z.z_prefix,
-                                                                                    p.n_problems, z.z_total,
-                                                                                    zexp_out); note_launch();
+  const long long blocks = z.n_direct + z.z_total;
+  if (blocks > 0) {
+    const size_t smem = (size_t)z.direct_stage_floats * 2 * 4;
+    if (smem > 48 * 1024) {
+      err = cudaFuncSetAttribute(contract_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (err != cudaSuccess) return err;
+    }
+    contract_kernel<<<(unsigned)(blocks < 65535ll * 16 ? blocks : 65535ll * 16), 512, smem, s>>>(
+        p, r, precision, z.direct_list, z.n_direct, z.direct_stage_floats, z.z_prefix, p.n_problems, z.z_total,
+        marg_out, zexp_out);
+    note_launch();
     err = cudaGetLastError();
   }
   return err;
