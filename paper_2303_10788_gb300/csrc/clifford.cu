@@ -1303,11 +1303,57 @@ __device__ __forceinline__ void hub_pair_out(int (&a)[16], int (&c)[16], int* wh
         make_float2((float)wht[sm] * inv, (float)wht[16 + sm] * inv);
   }
 }
+// Byte-counter variant of hub_pair_out: p[b] holds the counts of outputs o
+// and o+1 for basis outcome b as two 16-bit lanes; the 16-point transform
+// runs on both lanes at once (|sums| <= 16 * 255 fit in 16 bits).
+__device__ __forceinline__ void hub_pair_out_packed(unsigned (&p)[16], unsigned* wht, const int* s_czD,
+                                                    const int* s_czS, int nz, float* QT, int M, int o,
+                                                    float inv) {
+#pragma unroll
+  for (int h = 1; h < 16; h <<= 1)
+#pragma unroll
+    for (int b = 0; b < 16; ++b)
+      if (!(b & h)) {
+        const unsigned x = p[b], y = p[b | h];
+        p[b] = __vadd2(x, y);
+        p[b | h] = __vsub2(x, y);
+      }
+#pragma unroll
+  for (int b = 0; b < 16; ++b) wht[b] = p[b];
+  for (int cz = 0; cz < (1 << nz); ++cz) {
+    const unsigned w = wht[s_czS[cz]];
+    const int lo = (int)(short)(w & 0xffffu), hi = (int)(short)(w >> 16);
+    *reinterpret_cast<float2*>(QT + (long long)s_czD[cz] * M + o) = make_float2((float)lo * inv, (float)hi * inv);
+  }
+}
+
+// Shots of one variant into byte counters (shot 4g+j = word j of Philox call
+// g); L = table lookups per shot (2 when rank <= 16).  Sets *over when a
+// byte wraps.
+template <int L>
+__device__ __forceinline__ void sample_bytes(uint32_t* h32, const uint32_t (*tbl)[256], uint32_t off, uint32_t cmask,
+                                             uint32_t shots, uint4 ctr, uint32_t k0, uint32_t k1, int* over) {
+  for (uint32_t g = threadIdx.x; 4 * g < shots; g += blockDim.x) {
+    ctr.x = g;
+    const uint4 o = philox4x32_10(ctr, k0, k1);
+    const uint32_t w4[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (4 * g + j >= shots) break;
+      const uint32_t c = w4[j] & cmask;
+      uint32_t y = off ^ tbl[0][c & 255] ^ tbl[1][(c >> 8) & 255];
+      if (L == 3) y ^= tbl[2][(c >> 16) & 255];
+      const uint32_t sh = (y & 3u) << 3;
+      const uint32_t old = atomicAdd(&h32[y >> 2], 1u << sh);
+      if (((old >> sh) & 0xffu) == 0xffu) *over = 1;     // a byte wrapped: recount wider
+    }
+  }
+}
 }  // namespace
 
 __global__ void __launch_bounds__(256) sample_hub8_kernel(DevPlan P, DevRes R, EvalParams E, const int2* items,
                                                           int keep_counts, int hist_words) {
-  extern __shared__ uint32_t h32[];
+  extern __shared__ __align__(16) uint32_t h32[];
   __shared__ uint32_t tbl[3][256];
   __shared__ FragDev sF;
   __shared__ int s_czD[16], s_czS[16];
@@ -1376,25 +1422,21 @@ __global__ void __launch_bounds__(256) sample_hub8_kernel(DevPlan P, DevRes R, E
   };
   bool narrow = (unsigned long long)E.shots <= (64ull << rank);
   if (narrow) {
-    for (int i = tid; i < (1 << nA) / 4; i += nt) h32[i] = 0u;
-    __syncthreads();
-    for (uint32_t g = tid; 4 * g < E.shots; g += nt) {   // shot 4g+j: word j
-      const uint4 o = philox4x32_10(make_uint4(g, (uint32_t)v, (uint32_t)F.findex, (uint32_t)F.problem),
-                                    E.seed_lo, E.seed_hi);
-      const uint32_t w4[4] = {o.x, o.y, o.z, o.w};
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        if (4 * g + j >= E.shots) break;
-        const uint32_t y = sample_y(w4[j]), sh = (y & 3u) << 3;
-        const uint32_t old = atomicAdd(&h32[y >> 2], 1u << sh);
-        if (((old >> sh) & 0xffu) == 0xffu) s_over = 1;     // a byte wrapped: recount wider
-      }
+    {   // zero the histogram, 16 bytes per store
+      uint4* h4 = reinterpret_cast<uint4*>(h32);
+      for (int i = tid; i < (1 << nA) / 16; i += nt) h4[i] = make_uint4(0u, 0u, 0u, 0u);
+      for (int i = 4 * ((1 << nA) / 16) + tid; i < (1 << nA) / 4; i += nt) h32[i] = 0u;
     }
+    __syncthreads();
+    const uint4 ctr = make_uint4(0u, (uint32_t)v, (uint32_t)F.findex, (uint32_t)F.problem);
+    if (rank <= 16) sample_bytes<2>(h32, tbl, off, cmask, E.shots, ctr, E.seed_lo, E.seed_hi, &s_over);
+    else sample_bytes<3>(h32, tbl, off, cmask, E.shots, ctr, E.seed_lo, E.seed_hi, &s_over);
     __syncthreads();
     narrow = s_over == 0;
     if (narrow) {
       if (keep_counts)
         for (uint32_t y = tid; y < (1u << nA); y += nt) gcount[y] = (h32[y >> 2] >> ((y & 3u) << 3)) & 0xffu;
+      unsigned* pw = reinterpret_cast<unsigned*>(wht);
       for (int q = tid; q < (M >> 2); q += nt) {       // outputs o..o+3 share a counter word
         const int o = 4 * q;
         uint32_t w[16];
@@ -1402,13 +1444,10 @@ __global__ void __launch_bounds__(256) sample_hub8_kernel(DevPlan P, DevRes R, E
         for (int b = 0; b < 16; ++b) w[b] = b < nb ? h32[((uint32_t)o | ((uint32_t)b << m)) >> 2] : 0u;
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
-          int a[16], c[16];
+          unsigned pk[16];    // outputs o + 2 half and o + 2 half + 1 as 16-bit lanes
 #pragma unroll
-          for (int b = 0; b < 16; ++b) {
-            a[b] = (int)((w[b] >> (16 * half)) & 0xffu);
-            c[b] = (int)((w[b] >> (16 * half + 8)) & 0xffu);
-          }
-          hub_pair_out(a, c, wht, s_czD, s_czS, nz, QT, M, o + 2 * half, inv);
+          for (int b = 0; b < 16; ++b) pk[b] = __byte_perm(w[b], 0u, half ? 0x4342 : 0x4140);
+          hub_pair_out_packed(pk, pw, s_czD, s_czS, nz, QT, M, o + 2 * half, inv);
         }
       }
     }
