@@ -1102,6 +1102,105 @@ __global__ void __launch_bounds__(256) sample_kernel(DevPlan P, DevRes R, EvalPa
   }
 }
 
+namespace {
+// signed sums of the counts c[b] (b = output bits) for every sign mask by a
+// 16-point Walsh-Hadamard transform, for the outputs o and o+1 (a, c), then
+// the variant's operand rows Q^T[D][o..o+1]
+__device__ __forceinline__ void hub_pair_out(int (&a)[16], int (&c)[16], int* wht, const int* s_czD,
+                                             const int* s_czS, int nz, float* QT, int M, int o, float inv) {
+#pragma unroll
+  for (int h = 1; h < 16; h <<= 1)
+#pragma unroll
+    for (int b = 0; b < 16; ++b)
+      if (!(b & h)) {
+        const int x0 = a[b], y0 = a[b | h], x1 = c[b], y1 = c[b | h];
+        a[b] = x0 + y0;
+        a[b | h] = x0 - y0;
+        c[b] = x1 + y1;
+        c[b | h] = x1 - y1;
+      }
+#pragma unroll
+  for (int b = 0; b < 16; ++b) {
+    wht[b] = a[b];
+    wht[16 + b] = c[b];
+  }
+  for (int cz = 0; cz < (1 << nz); ++cz) {
+    const int sm = s_czS[cz];
+    *reinterpret_cast<float2*>(QT + (long long)s_czD[cz] * M + o) =
+        make_float2((float)wht[sm] * inv, (float)wht[16 + sm] * inv);
+  }
+}
+// Byte-counter variant of hub_pair_out: p[b] holds the counts of outputs o
+// and o+1 for basis outcome b as two 16-bit lanes; the 16-point transform
+// runs on both lanes at once (|sums| <= 16 * 255 fit in 16 bits).
+__device__ __forceinline__ void hub_pair_out_packed(unsigned (&p)[16], unsigned* wht, const int* s_czD,
+                                                    const int* s_czS, int nz, float* QT, int M, int o,
+                                                    float inv) {
+#pragma unroll
+  for (int h = 1; h < 16; h <<= 1)
+#pragma unroll
+    for (int b = 0; b < 16; ++b)
+      if (!(b & h)) {
+        const unsigned x = p[b], y = p[b | h];
+        p[b] = __vadd2(x, y);
+        p[b | h] = __vsub2(x, y);
+      }
+#pragma unroll
+  for (int b = 0; b < 16; ++b) wht[b] = p[b];
+  for (int cz = 0; cz < (1 << nz); ++cz) {
+    const unsigned w = wht[s_czS[cz]];
+    const int lo = (int)(short)(w & 0xffffu), hi = (int)(short)(w >> 16);
+    *reinterpret_cast<float2*>(QT + (long long)s_czD[cz] * M + o) = make_float2((float)lo * inv, (float)hi * inv);
+  }
+}
+
+// Shots of one variant into 16-bit (or, wide, 32-bit) counters; L = table
+// lookups per shot (1 at rank <= 8, 2 at rank <= 16).
+template <int L>
+__device__ __forceinline__ void sample_words(uint32_t* hist2, const uint32_t (*tbl)[256], uint32_t off,
+                                             uint32_t cmask, uint32_t shots, uint4 ctr, uint32_t k0, uint32_t k1,
+                                             int wide) {
+  for (uint32_t g = threadIdx.x; 4 * g < shots; g += blockDim.x) {
+    ctr.x = g;
+    const uint4 o = philox4x32_10(ctr, k0, k1);
+    const uint32_t w4[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (4 * g + j >= shots) break;
+      const uint32_t c = w4[j] & cmask;
+      uint32_t y = off ^ tbl[0][c & 255];
+      if (L >= 2) y ^= tbl[1][(c >> 8) & 255];
+      if (L >= 3) y ^= tbl[2][(c >> 16) & 255];
+      if (wide) atomicAdd(&hist2[y], 1u);
+      else atomicAdd(&hist2[y >> 1], 1u << ((y & 1u) << 4));
+    }
+  }
+}
+
+// Shots of one variant into byte counters (shot 4g+j = word j of Philox call
+// g); L = table lookups per shot (2 when rank <= 16).  Sets *over when a
+// byte wraps.
+template <int L>
+__device__ __forceinline__ void sample_bytes(uint32_t* h32, const uint32_t (*tbl)[256], uint32_t off, uint32_t cmask,
+                                             uint32_t shots, uint4 ctr, uint32_t k0, uint32_t k1, int* over) {
+  for (uint32_t g = threadIdx.x; 4 * g < shots; g += blockDim.x) {
+    ctr.x = g;
+    const uint4 o = philox4x32_10(ctr, k0, k1);
+    const uint32_t w4[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (4 * g + j >= shots) break;
+      const uint32_t c = w4[j] & cmask;
+      uint32_t y = off ^ tbl[0][c & 255] ^ tbl[1][(c >> 8) & 255];
+      if (L == 3) y ^= tbl[2][(c >> 16) & 255];
+      const uint32_t sh = (y & 3u) << 3;
+      const uint32_t old = atomicAdd(&h32[y >> 2], 1u << sh);
+      if (((old >> sh) & 0xffu) == 0xffu) *over = 1;     // a byte wrapped: recount wider
+    }
+  }
+}
+}  // namespace
+
 // --- K3 + K5 fused for the hub of a star --------------------------------
 // One CTA per hub variant: all its shots into a shared-memory histogram
 // (16-bit counters packed in pairs, so |A| <= 16 fits 128 KB), then the
@@ -1112,7 +1211,7 @@ __global__ void __launch_bounds__(256) sample_kernel(DevPlan P, DevRes R, EvalPa
 // inspection.
 __global__ void __launch_bounds__(512) sample_hub_kernel(DevPlan P, DevRes R, EvalParams E, const int2* items,
                                                          int keep_counts, int wide, int hist_words) {
-  extern __shared__ uint32_t hist2[];
+  extern __shared__ __align__(16) uint32_t hist2[];
   __shared__ uint32_t tbl[3][256];
   __shared__ FragDev sF;
   __shared__ int s_czD[16], s_czS[16];
@@ -1138,21 +1237,18 @@ __global__ void __launch_bounds__(512) sample_hub_kernel(DevPlan P, DevRes R, Ev
     tbl[k][byte] = acc;
   }
   const int nwords = wide ? (1 << nA) : ((1 << nA) > 1 ? (1 << (nA - 1)) : 1);
-  for (int i = threadIdx.x; i < nwords; i += blockDim.x) hist2[i] = 0u;
+  {   // zero the histogram, 16 bytes per store
+    uint4* h4 = reinterpret_cast<uint4*>(hist2);
+    for (int i = threadIdx.x; i < nwords / 4; i += blockDim.x) h4[i] = make_uint4(0u, 0u, 0u, 0u);
+    for (int i = 4 * (nwords / 4) + threadIdx.x; i < nwords; i += blockDim.x) hist2[i] = 0u;
+  }
   __syncthreads();
   const uint32_t cmask = rank >= 32 ? 0xffffffffu : ((1u << rank) - 1u);
-  for (uint32_t g = threadIdx.x; 4 * g < E.shots; g += blockDim.x) {   // shot 4g+j: word j
-    const uint4 o = philox4x32_10(make_uint4(g, (uint32_t)v, (uint32_t)F.findex, (uint32_t)F.problem),
-                                  E.seed_lo, E.seed_hi);
-    const uint32_t w4[4] = {o.x, o.y, o.z, o.w};
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      if (4 * g + j >= E.shots) break;
-      const uint32_t c = w4[j] & cmask;
-      const uint32_t y = off ^ tbl[0][c & 255] ^ tbl[1][(c >> 8) & 255] ^ tbl[2][(c >> 16) & 255];
-      if (wide) atomicAdd(&hist2[y], 1u);
-      else atomicAdd(&hist2[y >> 1], 1u << ((y & 1u) << 4));
-    }
+  {   // shot 4g+j: word j of Philox call g
+    const uint4 ctr = make_uint4(0u, (uint32_t)v, (uint32_t)F.findex, (uint32_t)F.problem);
+    if (rank <= 8) sample_words<1>(hist2, tbl, off, cmask, E.shots, ctr, E.seed_lo, E.seed_hi, wide);
+    else if (rank <= 16) sample_words<2>(hist2, tbl, off, cmask, E.shots, ctr, E.seed_lo, E.seed_hi, wide);
+    else sample_words<3>(hist2, tbl, off, cmask, E.shots, ctr, E.seed_lo, E.seed_hi, wide);
   }
   __syncthreads();
   auto count = [&](uint32_t y) -> uint32_t {
@@ -1204,6 +1300,18 @@ __global__ void __launch_bounds__(512) sample_hub_kernel(DevPlan P, DevRes R, Ev
     }
     __syncthreads();
     int* wht = reinterpret_cast<int*>(hist2 + hist_words) + threadIdx.x * 33;   // odd stride: no bank conflicts
+    if (E.shots <= 32767u) {
+      // an output's bins sum to at most the shots, so every transform value
+      // fits a signed 16-bit lane: the counter word (outputs o, o+1) is
+      // transformed as is, two outputs per SIMD add
+      for (int o2 = threadIdx.x; o2 < (M >> 1); o2 += blockDim.x) {
+        const int o = 2 * o2;
+        unsigned pk[16];
+#pragma unroll
+        for (int b = 0; b < 16; ++b) pk[b] = b < nb ? hist2[((uint32_t)o | ((uint32_t)b << m)) >> 1] : 0u;
+        hub_pair_out_packed(pk, reinterpret_cast<unsigned*>(wht), s_czD, s_czS, nz, QT, M, o, inv);
+      }
+    } else
     for (int o2 = threadIdx.x; o2 < (M >> 1); o2 += blockDim.x) {
       const int o = 2 * o2;
       int a[16], c[16];
@@ -1275,82 +1383,6 @@ __global__ void __launch_bounds__(512) sample_hub_kernel(DevPlan P, DevRes R, Ev
 // above 64 (shots > 64 * 2^rank), or whose counting overflowed a byte
 // (the atomic's old value tells), is counted again with 16-bit counters in
 // two passes, each over the outputs o of one half (top marginal bit).
-namespace {
-// signed sums of the counts c[b] (b = output bits) for every sign mask by a
-// 16-point Walsh-Hadamard transform, for the outputs o and o+1 (a, c), then
-// the variant's operand rows Q^T[D][o..o+1]
-__device__ __forceinline__ void hub_pair_out(int (&a)[16], int (&c)[16], int* wht, const int* s_czD,
-                                             const int* s_czS, int nz, float* QT, int M, int o, float inv) {
-#pragma unroll
-  for (int h = 1; h < 16; h <<= 1)
-#pragma unroll
-    for (int b = 0; b < 16; ++b)
-      if (!(b & h)) {
-        const int x0 = a[b], y0 = a[b | h], x1 = c[b], y1 = c[b | h];
-        a[b] = x0 + y0;
-        a[b | h] = x0 - y0;
-        c[b] = x1 + y1;
-        c[b | h] = x1 - y1;
-      }
-#pragma unroll
-  for (int b = 0; b < 16; ++b) {
-    wht[b] = a[b];
-    wht[16 + b] = c[b];
-  }
-  for (int cz = 0; cz < (1 << nz); ++cz) {
-    const int sm = s_czS[cz];
-    *reinterpret_cast<float2*>(QT + (long long)s_czD[cz] * M + o) =
-        make_float2((float)wht[sm] * inv, (float)wht[16 + sm] * inv);
-  }
-}
-// Byte-counter variant of hub_pair_out: p[b] holds the counts of outputs o
-// and o+1 for basis outcome b as two 16-bit lanes; the 16-point transform
-// runs on both lanes at once (|sums| <= 16 * 255 fit in 16 bits).
-__device__ __forceinline__ void hub_pair_out_packed(unsigned (&p)[16], unsigned* wht, const int* s_czD,
-                                                    const int* s_czS, int nz, float* QT, int M, int o,
-                                                    float inv) {
-#pragma unroll
-  for (int h = 1; h < 16; h <<= 1)
-#pragma unroll
-    for (int b = 0; b < 16; ++b)
-      if (!(b & h)) {
-        const unsigned x = p[b], y = p[b | h];
-        p[b] = __vadd2(x, y);
-        p[b | h] = __vsub2(x, y);
-      }
-#pragma unroll
-  for (int b = 0; b < 16; ++b) wht[b] = p[b];
-  for (int cz = 0; cz < (1 << nz); ++cz) {
-    const unsigned w = wht[s_czS[cz]];
-    const int lo = (int)(short)(w & 0xffffu), hi = (int)(short)(w >> 16);
-    *reinterpret_cast<float2*>(QT + (long long)s_czD[cz] * M + o) = make_float2((float)lo * inv, (float)hi * inv);
-  }
-}
-
-// Shots of one variant into byte counters (shot 4g+j = word j of Philox call
-// g); L = table lookups per shot (2 when rank <= 16).  Sets *over when a
-// byte wraps.
-template <int L>
-__device__ __forceinline__ void sample_bytes(uint32_t* h32, const uint32_t (*tbl)[256], uint32_t off, uint32_t cmask,
-                                             uint32_t shots, uint4 ctr, uint32_t k0, uint32_t k1, int* over) {
-  for (uint32_t g = threadIdx.x; 4 * g < shots; g += blockDim.x) {
-    ctr.x = g;
-    const uint4 o = philox4x32_10(ctr, k0, k1);
-    const uint32_t w4[4] = {o.x, o.y, o.z, o.w};
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      if (4 * g + j >= shots) break;
-      const uint32_t c = w4[j] & cmask;
-      uint32_t y = off ^ tbl[0][c & 255] ^ tbl[1][(c >> 8) & 255];
-      if (L == 3) y ^= tbl[2][(c >> 16) & 255];
-      const uint32_t sh = (y & 3u) << 3;
-      const uint32_t old = atomicAdd(&h32[y >> 2], 1u << sh);
-      if (((old >> sh) & 0xffu) == 0xffu) *over = 1;     // a byte wrapped: recount wider
-    }
-  }
-}
-}  // namespace
-
 __global__ void __launch_bounds__(256) sample_hub8_kernel(DevPlan P, DevRes R, EvalParams E, const int2* items,
                                                           int keep_counts, int hist_words) {
   extern __shared__ __align__(16) uint32_t h32[];
