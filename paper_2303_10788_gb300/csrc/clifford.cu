@@ -1035,6 +1035,26 @@ __global__ void __launch_bounds__(512) clifford_kernel(DevPlan P, DevRes R, Eval
   }
 }
 
+// Lookup tables of a variant's affine space: tbl[k][byte] = XOR of the basis
+// vectors 8k + b selected by byte's bits, only for the ceil(rank / 8)
+// groups that exist (entry 0 of the others is 0, which is all a shot of
+// rank-limited coefficients can select there).
+__device__ __forceinline__ void build_tables(uint32_t (*tbl)[256], const SpaceRec& sp, int rank) {
+  const int ntab = rank > 16 ? 3 : rank > 8 ? 2 : 1;
+  for (int t = threadIdx.x; t < ntab * 256; t += blockDim.x) {
+    const int k = t >> 8, byte = t & 255;
+    uint32_t acc = 0;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const int j = 8 * k + b;
+      const uint32_t bj = j < rank ? sp.basis[j] : 0u;
+      if ((byte >> b) & 1) acc ^= bj;
+    }
+    tbl[k][byte] = acc;
+  }
+  if ((int)threadIdx.x < 3 - ntab) tbl[ntab + threadIdx.x][0] = 0u;
+}
+
 // --- K3: Philox4x32-10 counter-based sampling from the affine space -------
 namespace {
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
@@ -1065,15 +1085,7 @@ __global__ void __launch_bounds__(256) sample_kernel(DevPlan P, DevRes R, EvalPa
   const SpaceRec& sp = R.spaces[F.space_off + v];
   const int rank = sp.rank, nA = F.nA;
   const uint32_t off = sp.off;
-  for (int t = threadIdx.x; t < 3 * 256; t += blockDim.x) {
-    const int k = t >> 8, byte = t & 255;
-    uint32_t acc = 0;
-    for (int b = 0; b < 8; ++b) {
-      const int j = 8 * k + b;
-      if (j < rank && ((byte >> b) & 1)) acc ^= sp.basis[j];
-    }
-    tbl[k][byte] = acc;
-  }
+  build_tables(tbl, sp, rank);
   const bool smem_hist = (1 << nA) <= kHistSmem;
   if (smem_hist)
     for (int y = threadIdx.x; y < (1 << nA); y += blockDim.x) hist[y] = 0;
@@ -1227,15 +1239,7 @@ __global__ void __launch_bounds__(512) sample_hub_kernel(DevPlan P, DevRes R, Ev
   const SpaceRec& sp = R.spaces[F.space_off + v];
   const int rank = sp.rank;
   const uint32_t off = sp.off;
-  for (int t = threadIdx.x; t < 3 * 256; t += blockDim.x) {
-    const int k = t >> 8, byte = t & 255;
-    uint32_t acc = 0;
-    for (int b = 0; b < 8; ++b) {
-      const int j = 8 * k + b;
-      if (j < rank && ((byte >> b) & 1)) acc ^= sp.basis[j];
-    }
-    tbl[k][byte] = acc;
-  }
+  build_tables(tbl, sp, rank);
   const int nwords = wide ? (1 << nA) : ((1 << nA) > 1 ? (1 << (nA - 1)) : 1);
   {   // zero the histogram, 16 bytes per store
     uint4* h4 = reinterpret_cast<uint4*>(hist2);
@@ -1404,15 +1408,7 @@ __global__ void __launch_bounds__(256) sample_hub8_kernel(DevPlan P, DevRes R, E
   const SpaceRec& sp = R.spaces[F.space_off + v];
   const int rank = sp.rank;
   const uint32_t off = sp.off;
-  for (int t = tid; t < 3 * 256; t += nt) {
-    const int k = t >> 8, byte = t & 255;
-    uint32_t acc = 0;
-    for (int b = 0; b < 8; ++b) {
-      const int j = 8 * k + b;
-      if (j < rank && ((byte >> b) & 1)) acc ^= sp.basis[j];
-    }
-    tbl[k][byte] = acc;
-  }
+  build_tables(tbl, sp, rank);
   // the variant's operand columns: one D and sign mask per Z-basis choice
   int nz = 0;
   {
