@@ -202,8 +202,8 @@ struct ccs_plan_s {
   long long n_zimg = 0;             // uint64 words of Z images
   long long n_marg = 0, n_zexp = 0;
   std::vector<long long> t_prefix, tz_prefix, out_prefix, z_prefix, r_prefix, blk_prefix;
-  std::vector<int> direct_list;     // problems contracted leaf by leaf
-  int* d_direct_list = nullptr;
+  std::vector<int2> direct_items;   // (problem, hub-output slice) contracted leaf by leaf
+  int2* d_direct_items = nullptr;
   long long direct_stage_floats = 0;
   int chain = 0;                    // some problem takes the R / GEMM / reduce chain
   long long* d_r_prefix = nullptr;
@@ -699,8 +699,11 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
       d.ntiles = (d.N + d.TN - 1) / d.TN;
       d.hub_T_off = plan->fdev[f0 + P.hub].T_off;
       d.tc = (gemm_tc_supported(d.M, d.N, d.K) && d.K >= 4096 && d.M >= 128) ? 1 : 0;
-      // leaf by leaf in one CTA when every intermediate fits in shared memory
-      long long widest = d.K * d.M, A = d.M, rest = d.K;
+      // leaf by leaf in shared memory, the hub outputs in slices of TM (the
+      // contraction never mixes hub outputs), when every intermediate of a
+      // slice fits: per hub output the intermediates hold rest_l x N_1..N_l
+      // floats (the first leaf reads the hub operand from global memory)
+      long long per_m = d.n_frags > 1 ? 1 : d.K, A = 1, rest = d.K;   // the first leaf reads Q^T in place
       int slots = 0;
       for (int l = 0; l < d.n_frags; ++l) {
         if (l == P.hub) continue;
@@ -708,17 +711,30 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
         rest >>= 2 * L.n_slots;
         A <<= L.m;
         slots += L.n_slots;
-        widest = std::max(widest, rest * A);
+        per_m = std::max(per_m, rest * A);
       }
-      widest = std::max(widest, (long long)d.M + d.N);   // the scatter tables share a buffer
-      d.direct = (!d.tc && slots == d.k && widest <= kDirectSmemFloats) ? 1 : 0;
+      auto slice = [&](long long pm) {
+        long long t = 1;
+        while (2 * t <= d.M && 2 * t * pm <= kDirectSmemFloats && 2 * t + d.N <= kDirectSmemFloats) t *= 2;
+        return t;
+      };
+      long long tm = slice(per_m);
+      // staging the operand slice first (coalesced, then every read in shared
+      // memory) when that does not shrink the slice
+      const long long per_m_staged = std::max(per_m, d.K);
+      d.direct_staged = per_m_staged <= kDirectSmemFloats && slice(per_m_staged) == tm;
+      if (d.direct_staged) per_m = per_m_staged;
+      d.direct = (!d.tc && slots == d.k && per_m <= kDirectSmemFloats && tm + d.N <= kDirectSmemFloats) ? 1 : 0;
       if (d.direct) {
         d.splits = 1;
+        d.TM = (int)tm;                      // hub outputs per block
+        d.mtiles = (int)(d.M / tm);
         d.r_off = plan->r_total;
         d.part_off = plan->part_total;
         d.blk_off = plan->gemm_blocks;
-        plan->direct_list.push_back((int)plan->pdev.size());
-        plan->direct_stage_floats = std::max(plan->direct_stage_floats, widest);
+        for (int t = 0; t < d.mtiles; ++t) plan->direct_items.push_back(make_int2((int)plan->pdev.size(), t));
+        plan->direct_stage_floats =
+            std::max(plan->direct_stage_floats, std::max(tm * per_m, tm + (long long)d.N));
       }
       if (!d.direct) {
         const long long base = (long long)d.mtiles * d.ntiles;
@@ -786,7 +802,7 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
   st.add(prepm, &dpm); st.add(basism, &dbm); st.add(plan->t_prefix, &plan->d_t_prefix);
   st.add(plan->tz_prefix, &plan->d_tz_prefix); st.add(plan->out_prefix, &plan->d_out_prefix);
   st.add(plan->z_prefix, &plan->d_z_prefix); st.add(plan->r_prefix, &plan->d_r_prefix);
-  st.add(plan->blk_prefix, &plan->d_blk_prefix); st.add(plan->direct_list, &plan->d_direct_list);
+  st.add(plan->blk_prefix, &plan->d_blk_prefix); st.add(plan->direct_items, &plan->d_direct_items);
   bool ok = st.commit(c, plan->A);
   if (!ok) { delete plan; return fail(c, CCS_ERR_OOM, "plan upload failed"); }
   dp.frags = dfr; dp.cops = dco; dp.nops = dno; dp.moments = dmo; dp.wires = dwi; dp.zoffs = dzo;
@@ -1171,7 +1187,7 @@ int ccs_recombine(ccs_ctx c, ccs_plan p, ccs_res r, const ccs_recomb_opts* opts,
   cudaSetDevice(c->device);
   const bool tc = !(opts && opts->no_tensor_cores);
   RecombSizes rz{p->r_total, p->part_total, p->gemm_blocks, p->n_marg, p->n_zexp,
-                 p->d_direct_list, (int)p->direct_list.size(), (int)p->direct_stage_floats, p->chain,
+                 p->d_direct_items, (int)p->direct_items.size(), (int)p->direct_stage_floats, p->chain,
                  p->d_r_prefix, p->d_blk_prefix, p->d_out_prefix, p->d_z_prefix, p->max_tile_smem,
                  tc ? p->pdev.data() : nullptr, (int)p->pdev.size(), r->rt_scratch};
   cudaError_t e;
@@ -1440,7 +1456,7 @@ extern "C" int ccs_recombine_noalloc(ccs_ctx c, ccs_plan p, ccs_res r, int preci
     g_noalloc_addr[c->device] = ptr;
   }
   RecombSizes rz{p->r_total, p->part_total, p->gemm_blocks, p->n_marg, p->n_zexp,
-                 p->d_direct_list, (int)p->direct_list.size(), (int)p->direct_stage_floats, p->chain,
+                 p->d_direct_items, (int)p->direct_items.size(), (int)p->direct_stage_floats, p->chain,
                  p->d_r_prefix, p->d_blk_prefix, p->d_out_prefix, p->d_z_prefix, p->max_tile_smem,
                  nullptr, 0, nullptr};
   e = launch_recombine(p->dp, r->dr, precision, rz, g_noalloc_addr[c->device], marginal_out, zexp_out, c->stream);

@@ -58,7 +58,8 @@ struct ProblemDev {
   long long rt_off;        // bf16 index of R'^T (N x K) in the bf16 scratch (tensor-core path)
   long long hub_T_off;     // T_off of the hub
   int tc;                  // 1: eligible for the tensor-core GEMM in BF16 mode
-  int direct;              // 1: small star: contracted leaf by leaf by one CTA in shared memory
+  int direct;              // 1: contracted leaf by leaf in shared memory, TM hub outputs per CTA
+  int direct_staged;       // 1: the slice's hub operand (K x TM) is staged first; 0: the first leaf streams it
 };
 
 // Device views of a plan + result.
@@ -186,7 +187,7 @@ cudaError_t launch_operands(const DevPlan& p, const DevRes& r, const EvalParams&
 // partials (r_total + part_total floats).
 struct RecombSizes {
   long long r_total, part_total, gemm_blocks, out_total, z_total;
-  const int* direct_list;        // problems contracted leaf by leaf (one CTA each)
+  const int2* direct_items;      // (problem, hub-output slice) contracted leaf by leaf, one CTA each
   int n_direct;
   int direct_stage_floats;       // floats of each of the two intermediate buffers
   int chain;                     // 1: some problem takes the R / GEMM / reduce chain

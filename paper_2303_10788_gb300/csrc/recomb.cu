@@ -497,8 +497,9 @@ __device__ void z_string_block(const DevPlan& P, const DevRes& R, const long lon
   if (threadIdx.x == 0) zexp_out[Pb.zexp_off + zi] = ldexp(red[0], -S.k);
 }
 
-// Contraction of a small star leaf by leaf (the tensor-network order of
-// Sec. V-C), one CTA per problem, every intermediate in shared memory.
+// Contraction of a star leaf by leaf (the tensor-network order of Sec.
+// V-C), one CTA per slice of TM hub outputs (the contraction never mixes
+// them), every intermediate in shared memory.
 // Each cut belongs to exactly one leaf, so the cut index P splits into the
 // leaves' digit groups g_l (a leaf's digits in its slot order, so g_l is
 // the column index of T'_l).  Start from X[kc][m] = Q^T[P][m], kc the cut
@@ -512,7 +513,7 @@ __device__ void z_string_block(const DevPlan& P, const DevRes& R, const long lon
 // (Neumaier) FP32; operands are rounded to bf16 first in BF16 mode.
 // Blocks after the problems compute the Z-string expectations.
 __global__ void __launch_bounds__(512) contract_kernel(DevPlan P, DevRes R, int precision,
-                                                      const int* direct_list, int n_direct, int stage_floats,
+                                                      const int2* direct_items, int n_direct, int stage_floats,
                                                       const long long* z_prefix, int np, long long z_total,
                                                       double* marg_out, double* zexp_out) {
   extern __shared__ __align__(16) float s_buf[];   // two buffers of stage_floats
@@ -525,40 +526,49 @@ __global__ void __launch_bounds__(512) contract_kernel(DevPlan P, DevRes R, int 
       __syncthreads();
       continue;
     }
-    const ProblemDev& Pb = P.problems[direct_list[b]];
-    const int M = Pb.M, lm = __ffs(M) - 1;       // every extent here is a power of two
+    const int2 di = direct_items[b];
+    const ProblemDev& Pb = P.problems[di.x];
+    const int M = Pb.TM, lm = __ffs(M) - 1;      // this block's hub outputs; extents are powers of two
+    const int m0 = di.y * M, Mfull = Pb.M;
     const int K = (int)Pb.K;
-    const float* At = R.TQ + Pb.hub_T_off;     // the hub's Q stored transposed: K x M, row-major
+    const float* At = R.TQ + Pb.hub_T_off + m0;  // the hub's Q stored transposed: K x Mfull, row-major
     load_problem(P, Pb, S);
     __syncthreads();
     float* X = s_buf;
     float* Y = s_buf + stage_floats;
-    for (int t0 = threadIdx.x; t0 < K * M; t0 += 8 * blockDim.x) {   // 8 loads in flight per thread
-      float v[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int t = t0 + u * blockDim.x;
-        if (t < K * M) {
-          const int kc = t >> lm, m = t & (M - 1);
-          int k = 0, rem = kc;                   // compact index -> cut index
-          for (int l = 0; l < S.nf; ++l) {
-            if (l == S.hub) continue;
-            for (int i = 0; i < S.ns[l]; ++i) {
-              k |= (rem & 3) << (2 * S.slot_cut[l][i]);
-              rem >>= 2;
-            }
-          }
-          v[u] = At[(long long)k * M + m];
+    // compact cut index (groups in leaf order, the first leaf's lowest) ->
+    // cut index, for the digits of leaves from `from` on
+    auto expand = [&](int kc, int from) -> int {
+      int k = 0, rem = kc;
+      for (int l = from; l < S.nf; ++l) {
+        if (l == S.hub) continue;
+        for (int i = 0; i < S.ns[l]; ++i) {
+          k |= (rem & 3) << (2 * S.slot_cut[l][i]);
+          rem >>= 2;
         }
       }
+      return k;
+    };
+    int first = 0;
+    while (first < S.nf && first == S.hub) ++first;
+    const bool staged0 = Pb.direct_staged || first >= S.nf;   // no leaf: the operand is the result
+    if (staged0) {
+      for (int t0 = threadIdx.x; t0 < K * M; t0 += 8 * blockDim.x) {   // 8 loads in flight per thread
+        float v[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int t = t0 + u * blockDim.x;
-        if (t < K * M) X[t] = precision == CCS_BF16 ? to_bf16f(v[u]) : v[u];
+        for (int u = 0; u < 8; ++u) {
+          const int t = t0 + u * blockDim.x;
+          if (t < K * M) v[u] = At[(long long)expand(t >> lm, 0) * Mfull + (t & (M - 1))];
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int t = t0 + u * blockDim.x;
+          if (t < K * M) X[t] = precision == CCS_BF16 ? to_bf16f(v[u]) : v[u];
+        }
       }
     }
     int lA = lm, lrest = 2 * S.k;                // log2 of the outer and rest extents
-    for (int l = 0; l < S.nf; ++l) {
+    for (int l = first; l < S.nf; ++l) {
       if (l == S.hub) continue;
       const int lG = 2 * S.ns[l], G = 1 << lG, Nl = 1 << S.m[l];
       lrest -= lG;
@@ -575,20 +585,42 @@ __global__ void __launch_bounds__(512) contract_kernel(DevPlan P, DevRes R, int 
       for (int e = threadIdx.x; e < (1 << (lrest + lout)); e += blockDim.x) {
         const int r = e >> lout, rm = e & ((1 << lout) - 1);
         const int x = rm >> lA, outer = rm & (A - 1);
-        const float* xs = X + ((r << lG) << lA) + outer;
-        const float* ts = tstaged ? s_T + x * G : nullptr;
         float sum = 0.f, comp = 0.f;
-        for (int g = 0; g < G; ++g) {
-          float tv;
-          if (tstaged) tv = ts[g];
-          else {
-            tv = R.TQ[S.T_off[l] + (long long)x * G + g];
-            if (precision == CCS_BF16) tv = to_bf16f(tv);
+        if (l == first && !staged0) {
+          // the first leaf reads the hub operand in global memory: rows of
+          // the cut index, the block's TM hub outputs contiguous in each
+          const int kr = expand(r << lG, l);     // the other leaves' digits of this row group
+          for (int g = 0; g < G; ++g) {
+            int kg = 0;
+            for (int i = 0; i < S.ns[l]; ++i) kg |= ((g >> (2 * i)) & 3) << (2 * S.slot_cut[l][i]);
+            float a = At[(long long)(kr | kg) * Mfull + outer];
+            if (precision == CCS_BF16) a = to_bf16f(a);
+            float tv;
+            if (tstaged) tv = s_T[x * G + g];
+            else {
+              tv = R.TQ[S.T_off[l] + (long long)x * G + g];
+              if (precision == CCS_BF16) tv = to_bf16f(tv);
+            }
+            const float p = a * tv;
+            const float t2 = sum + p;             // Neumaier: keep the lost low part
+            comp += fabsf(sum) >= fabsf(p) ? (sum - t2) + p : (p - t2) + sum;
+            sum = t2;
           }
-          const float p = xs[g << lA] * tv;
-          const float t2 = sum + p;               // Neumaier: keep the lost low part
-          comp += fabsf(sum) >= fabsf(p) ? (sum - t2) + p : (p - t2) + sum;
-          sum = t2;
+        } else {
+          const float* xs = X + ((r << lG) << lA) + outer;
+          const float* ts = tstaged ? s_T + x * G : nullptr;
+          for (int g = 0; g < G; ++g) {
+            float tv;
+            if (tstaged) tv = ts[g];
+            else {
+              tv = R.TQ[S.T_off[l] + (long long)x * G + g];
+              if (precision == CCS_BF16) tv = to_bf16f(tv);
+            }
+            const float p = xs[g << lA] * tv;
+            const float t2 = sum + p;
+            comp += fabsf(sum) >= fabsf(p) ? (sum - t2) + p : (p - t2) + sum;
+            sum = t2;
+          }
         }
         Y[e] = sum + comp;
       }
@@ -596,13 +628,13 @@ __global__ void __launch_bounds__(512) contract_kernel(DevPlan P, DevRes R, int 
       lA = lout;
     }
     // X[m + M n] = C[m][n]; marginal index = hub bits of m | leaf bits of n,
-    // both tabulated in the free buffer (M + N <= 2 M N entries)
+    // both tabulated in the free buffer (TM + N entries, within its size)
     const int hub = S.hub, N = 1 << (lA - lm);
     unsigned* orow = reinterpret_cast<unsigned*>(Y);
     unsigned* ocol = orow + M;
     for (int m = threadIdx.x; m < M; m += blockDim.x) {
       unsigned o = 0;
-      for (int j = 0; j < S.m[hub]; ++j) o |= ((unsigned)(m >> j) & 1u) << S.marg_pos[hub][j];
+      for (int j = 0; j < S.m[hub]; ++j) o |= ((unsigned)((m0 + m) >> j) & 1u) << S.marg_pos[hub][j];
       orow[m] = o;
     }
     for (int n = threadIdx.x; n < N; n += blockDim.x) {
@@ -694,7 +726,7 @@ cudaError_t launch_recombine(const DevPlan& p, const DevRes& r, int precision, c
       if (err != cudaSuccess) return err;
     }
     contract_kernel<<<(unsigned)(blocks < 65535ll * 16 ? blocks : 65535ll * 16), 512, smem, s>>>(
-        p, r, precision, z.direct_list, z.n_direct, z.direct_stage_floats, z.z_prefix, p.n_problems, z.z_total,
+        p, r, precision, z.direct_items, z.n_direct, z.direct_stage_floats, z.z_prefix, p.n_problems, z.z_total,
         marg_out, zexp_out);
     note_launch();
     err = cudaGetLastError();
