@@ -484,6 +484,7 @@ __global__ void __launch_bounds__(256) body_basis_kernel(DevPlan P, DevRes R) {
   __shared__ int s_e;
   __shared__ unsigned s_bad, s_last;
   __shared__ unsigned long long s_ct[64];
+  __shared__ unsigned long long s_qd[kMaxCuts], s_qs[kMaxCuts];
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
   if ((int)blockIdx.x >= P.n_cliff_frags) {
     const int2 it = P.items_zimg[(int)blockIdx.x - P.n_cliff_frags];   // (fragment, record)
@@ -532,11 +533,26 @@ __global__ void __launch_bounds__(256) body_basis_kernel(DevPlan P, DevRes R) {
   const FragDev& F = P.frags[P.cliff_frags[blockIdx.x]];
   const int n = F.n, W = F.W, Wh = F.Wh, zb = n + 1, nA = F.nA, ne = F.nA + F.qout;
   for (int j = tid; j < ne; j += nt) s_col[j] = j < nA ? P.wires[F.A_off + j] : zb + P.wires[F.qout_off + j - nA];
-  if (tid < F.qin) s_in[tid] = P.wires[F.qin_off + tid];
+  if (tid < F.qin) {
+    s_in[tid] = P.wires[F.qin_off + tid];
+    s_qd[tid] = 0ull;
+    s_qs[tid] = 0ull;
+  }
   __syncthreads();
   const unsigned long long* body = R.body + F.body_off;
   for (int t = tid; t < ne * Wh; t += nt) s_cw[t / Wh][t % Wh] = body[(size_t)s_col[t / Wh] * W + Wh + t % Wh];
+  // each quantum input's destabilizer and stabilizer rows as extended vectors
+  for (int t = tid; t < F.qin * ne; t += nt) {
+    const int i = t / ne, j = t % ne, q = s_in[i];
+    const unsigned long long* col = body + (size_t)s_col[j] * W;
+    if ((col[q >> 6] >> (q & 63)) & 1ull) atomicOr(&s_qd[i], 1ull << j);
+    if ((col[Wh + (q >> 6)] >> (q & 63)) & 1ull) atomicOr(&s_qs[i], 1ull << j);
+  }
   __syncthreads();
+  if (tid < F.qin) {
+    R.rowbasis[F.rb_off + kRbInputRows + tid] = s_qd[tid];
+    R.rowbasis[F.rb_off + kRbInputRows + kMaxCuts + tid] = s_qs[tid];
+  }
   unsigned long long have = 0ull;
   for (int i0 = warp * 32; i0 < n; i0 += nt) {
     const int i = i0 + lane;
@@ -656,27 +672,15 @@ __global__ void __launch_bounds__(256) screen_kernel(DevPlan P, DevRes R, EvalPa
     const unsigned long long sh = rb[64];
     absorb(((sh >> lane) & 1ull) ? project(rb[lane]) : 0u);
     absorb(((sh >> (lane + 32)) & 1ull) ? project(rb[lane + 32]) : 0u);
-    {   // new stabilizer rows of the quantum inputs (bits only): lanes over the extended columns
-      const int n = F.n, W = F.W, Wh = F.Wh, zb = n + 1, ne = nA + qout;
-      const unsigned long long* body = R.body + F.body_off;
-      int col0 = -1, col1 = -1;
-      if (lane < ne) col0 = lane < nA ? P.wires[F.A_off + lane] : zb + P.wires[F.qout_off + lane - nA];
-      if (lane + 32 < ne) col1 = zb + P.wires[F.qout_off + lane + 32 - nA];
+    {   // new stabilizer rows of the quantum inputs (bits only): the image of
+        // C Z C^+ is D, S or their product, from the fragment's input rows
       uint32_t row = 0;
-      for (int i = 0; i < F.qin; ++i) {
-        const int q = P.wires[F.qin_off + i];
-        const int wd = q >> 6, b = q & 63;
-        const unsigned s = (pin >> (2 * i)) & 3u;
+      if (lane < F.qin) {
+        const unsigned s = (pin >> (2 * lane)) & 3u;
         const int sc = s < 2 ? 2 : s == 2 ? 1 : 3;   // image of Z under the preparation: 1 X, 2 Z, 3 Y
-        auto bit = [&](int col) -> unsigned {
-          if (col < 0) return 0u;
-          const unsigned d = (unsigned)(body[(size_t)col * W + wd] >> b) & 1u;
-          const unsigned st = (unsigned)(body[(size_t)col * W + Wh + wd] >> b) & 1u;
-          return ((sc & 1) ? d : 0u) ^ ((sc & 2) ? st : 0u);
-        };
-        const unsigned long long e =
-            (unsigned long long)__ballot_sync(FULLW, bit(col0)) | ((unsigned long long)__ballot_sync(FULLW, bit(col1)) << 32);
-        if (lane == i) row = project(e);
+        const unsigned long long e = ((sc & 1) ? rb[kRbInputRows + lane] : 0ull) ^
+                                     ((sc & 2) ? rb[kRbInputRows + kMaxCuts + lane] : 0ull);
+        row = project(e);
       }
       absorb(row);
     }

@@ -113,10 +113,12 @@ struct DevRes {
   unsigned int* status;       // device-side error word
 };
 
-// Per Clifford fragment: the shared-row basis (64 pivot slots + pivot mask)
-// and the offset table of its measured Paulis (64 commutation-parity words +
-// 64 info words).
-constexpr int kRowBasisWords = 65 + 128;
+// Per Clifford fragment: the shared-row basis (64 pivot slots + pivot mask),
+// the offset table of its measured Paulis (64 commutation-parity words + 64
+// info words), and the extended vectors of each quantum input's body rows
+// (kMaxCuts destabilizer words, then kMaxCuts stabilizer words).
+constexpr int kRowBasisWords = 65 + 128 + 2 * kMaxCuts;
+constexpr int kRbInputRows = 193;
 
 // Largest intermediate (floats) of a star contracted leaf by leaf in shared
 // memory; larger stars take the R / GEMM / reduce chain.

@@ -590,21 +590,31 @@ __global__ void __launch_bounds__(512) contract_kernel(DevPlan P, DevRes R, int 
           // the first leaf reads the hub operand in global memory: rows of
           // the cut index, the block's TM hub outputs contiguous in each
           const int kr = expand(r << lG, l);     // the other leaves' digits of this row group
-          for (int g = 0; g < G; ++g) {
-            int kg = 0;
-            for (int i = 0; i < S.ns[l]; ++i) kg |= ((g >> (2 * i)) & 3) << (2 * S.slot_cut[l][i]);
-            float a = At[(long long)(kr | kg) * Mfull + outer];
-            if (precision == CCS_BF16) a = to_bf16f(a);
-            float tv;
-            if (tstaged) tv = s_T[x * G + g];
-            else {
-              tv = R.TQ[S.T_off[l] + (long long)x * G + g];
-              if (precision == CCS_BF16) tv = to_bf16f(tv);
+          for (int g0 = 0; g0 < G; g0 += 8) {    // 8 loads in flight
+            float a[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const int g = g0 + u;
+              int kg = 0;
+              for (int i = 0; i < S.ns[l]; ++i) kg |= ((g >> (2 * i)) & 3) << (2 * S.slot_cut[l][i]);
+              a[u] = g < G ? At[(long long)(kr | kg) * Mfull + outer] : 0.f;
             }
-            const float p = a * tv;
-            const float t2 = sum + p;             // Neumaier: keep the lost low part
-            comp += fabsf(sum) >= fabsf(p) ? (sum - t2) + p : (p - t2) + sum;
-            sum = t2;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const int g = g0 + u;
+              if (g >= G) break;
+              const float av = precision == CCS_BF16 ? to_bf16f(a[u]) : a[u];
+              float tv;
+              if (tstaged) tv = s_T[x * G + g];
+              else {
+                tv = R.TQ[S.T_off[l] + (long long)x * G + g];
+                if (precision == CCS_BF16) tv = to_bf16f(tv);
+              }
+              const float p = av * tv;
+              const float t2 = sum + p;           // Neumaier: keep the lost low part
+              comp += fabsf(sum) >= fabsf(p) ? (sum - t2) + p : (p - t2) + sum;
+              sum = t2;
+            }
           }
         } else {
           const float* xs = X + ((r << lG) << lA) + outer;
