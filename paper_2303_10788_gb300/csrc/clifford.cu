@@ -1298,7 +1298,8 @@ __global__ void __launch_bounds__(512) sample_hub_kernel(DevPlan P, DevRes R, Ev
     // Pairs of outputs (o, o+1) share the packed counter words.  Per pair,
     // a 16-point Walsh-Hadamard transform over the output bits gives the
     // signed sum for every sign mask at once; each thread parks it in its
-    // own 33-int slot after the histogram and picks the variant's masks.
+    // own slot after the histogram (17 words packed, 33 unpacked: odd
+    // strides, no bank conflicts) and picks the variant's masks.
     if ((int)threadIdx.x < (1 << nz)) {
       int D = Dbase, smask = fixed_mask;
       for (int i = 0; i < nz; ++i)
@@ -1307,7 +1308,7 @@ __global__ void __launch_bounds__(512) sample_hub_kernel(DevPlan P, DevRes R, Ev
       s_czS[threadIdx.x] = smask;
     }
     __syncthreads();
-    int* wht = reinterpret_cast<int*>(hist2 + hist_words) + threadIdx.x * 33;   // odd stride: no bank conflicts
+    int* wht = reinterpret_cast<int*>(hist2 + hist_words) + threadIdx.x * (E.shots <= 32767u ? 17 : 33);
     if (E.shots <= 32767u) {
       // an output's bins sum to at most the shots, so every transform value
       // fits a signed 16-bit lane: the counter word (outputs o, o+1) is
@@ -1446,7 +1447,8 @@ __global__ void __launch_bounds__(256) sample_hub8_kernel(DevPlan P, DevRes R, E
   const uint32_t cmask = rank >= 32 ? 0xffffffffu : ((1u << rank) - 1u);
   const float inv = (float)E.inv_shots;
   float* QT = R.TQ + F.T_off;
-  int* wht = reinterpret_cast<int*>(h32 + hist_words) + tid * 33;
+  const int wstride = E.shots <= 32767u ? 17 : 33;   // packed transforms need 16 words, unpacked 32
+  int* wht = reinterpret_cast<int*>(h32 + hist_words) + tid * wstride;
   uint32_t* gcount = R.counts + F.counts_off + ((long long)v << nA);
   auto sample_y = [&](uint32_t w) -> uint32_t {
     const uint32_t c = w & cmask;
@@ -1511,6 +1513,13 @@ __global__ void __launch_bounds__(256) sample_hub8_kernel(DevPlan P, DevRes R, E
         }
       for (int o2 = tid; o2 < (Mh >> 1); o2 += nt) {    // pairs of outputs within the half
         const int ol = 2 * o2;
+        if (wstride == 17) {                   // an output's bins sum to at most the shots
+          unsigned pk[16];
+#pragma unroll
+          for (int b = 0; b < 16; ++b) pk[b] = b < nb ? h32[((uint32_t)ol | ((uint32_t)b << mh)) >> 1] : 0u;
+          hub_pair_out_packed(pk, reinterpret_cast<unsigned*>(wht), s_czD, s_czS, nz, QT, M, h * Mh + ol, inv);
+          continue;
+        }
         int a[16], c[16];
 #pragma unroll
         for (int b = 0; b < 16; ++b) {
@@ -1529,7 +1538,7 @@ cudaError_t launch_sample_hub(const DevPlan& p, const DevRes& r, const EvalParam
   if (n_items == 0 || e.shots == 0) return cudaSuccess;
   if (bytes_ok && e.shots <= 0xffffu && max_nA >= 2 && max_nA <= 16) {   // byte counters, 256 threads
     const int hist_words = (1 << max_nA) / 4;
-    const size_t smem = (size_t)4 * hist_words + (size_t)256 * 33 * 4;
+    const size_t smem = (size_t)4 * hist_words + (size_t)256 * (e.shots <= 32767u ? 17 : 33) * 4;
     cudaError_t err = cudaFuncSetAttribute(sample_hub8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     sample_hub8_kernel<<<n_items, 256, smem, s>>>(p, r, e, items, keep_counts, hist_words); note_launch();
@@ -1539,7 +1548,7 @@ cudaError_t launch_sample_hub(const DevPlan& p, const DevRes& r, const EvalParam
   const int hist_words = wide ? (1 << max_nA) : ((1 << max_nA) > 1 ? (1 << (max_nA - 1)) : 1);
   // packed counters, then 33 ints per thread for the transform of the 16-bit path
   threads = threads >= 512 ? 512 : threads >= 256 ? 256 : 128;
-  const size_t smem = (size_t)4 * hist_words + (wide ? 0 : (size_t)threads * 33 * 4);
+  const size_t smem = (size_t)4 * hist_words + (wide ? 0 : (size_t)threads * (e.shots <= 32767u ? 17 : 33) * 4);
   cudaError_t err = cudaFuncSetAttribute(sample_hub_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   sample_hub_kernel<<<n_items, threads, smem, s>>>(p, r, e, items, keep_counts, wide, hist_words); note_launch();
