@@ -9,7 +9,8 @@ constants between rounds.  Vectorised over counters with numpy uint64.
 
 The paper itself only states that Clifford fragments are sampled (its sole
 error source is sampling error, Sec. V-C); this counter-based generator is how
-shots are drawn reproducibly, keyed as described in ``shot_words``.
+shots are drawn reproducibly, keyed as described in ``shot_words`` and
+``shot_coeffs``.
 """
 from __future__ import annotations
 
@@ -48,3 +49,23 @@ def shot_words(n_shots, variant, fragment, circuit, seed_lo, seed_hi):
     w = philox4x32_10(g, np.full_like(g, variant), np.full_like(g, fragment),
                       np.full_like(g, circuit), seed_lo, seed_hi)
     return np.stack(w, axis=1).reshape(-1)[:n_shots]
+
+
+def fields_per_word(rank):
+    """Shots one 32-bit output word serves: four 8-bit fields at rank <= 8,
+    two 16-bit fields at rank <= 16, else one (rank <= 24)."""
+    return 4 if rank <= 8 else 2 if rank <= 16 else 1
+
+
+def shot_coeffs(n_shots, rank, variant, fragment, circuit, seed_lo, seed_hi):
+    """Coefficient bits of each shot of a space of the given rank: shot t takes
+    field t mod s (s = fields_per_word(rank), fields from the low bits up, 32/s
+    bits each) of word t div s of the ``shot_words`` stream, and uses its low
+    rank bits."""
+    s = fields_per_word(rank)
+    width = 32 // s
+    words = shot_words((n_shots + s - 1) // s, variant, fragment, circuit, seed_lo, seed_hi)
+    t = np.arange(n_shots, dtype=np.uint64)
+    w = words[(t // np.uint64(s)).astype(np.int64)]
+    f = (w >> (np.uint64(width) * (t % np.uint64(s)))) & np.uint64((1 << width) - 1)
+    return f & np.uint64((1 << rank) - 1)

@@ -25,7 +25,7 @@ import numpy as np
 from . import tableau as tb
 from . import statevector as sv
 from .cutting import fragment_circuit, fold, fold_scalar, recombine, recombine_scalar
-from .philox import shot_words
+from .philox import shot_coeffs
 
 
 @dataclass
@@ -50,10 +50,10 @@ class OracleResult:
 
 
 def sample_counts(off, B, nbits, shots, variant, fragment, circuit, seed_lo, seed_hi):
-    """Counts of y = off ^ XOR_{j: c_j = 1} B_j with c = low rho bits of the
-    shot's 32-bit Philox word (rho <= 32)."""
-    assert len(B) <= 32
-    bits = shot_words(shots, variant, fragment, circuit, seed_lo, seed_hi)
+    """Counts of y = off ^ XOR_{j: c_j = 1} B_j with c = the shot's rho
+    coefficient bits from the Philox stream (``shot_coeffs``, rho <= 24)."""
+    assert len(B) <= 24
+    bits = shot_coeffs(shots, len(B), variant, fragment, circuit, seed_lo, seed_hi)
     y = np.full(shots, off, np.int64)
     for j, b in enumerate(B):
         sel = ((bits >> np.uint64(j)) & np.uint64(1)).astype(bool)

@@ -15,6 +15,8 @@
 
 #include "kernels.cuh"
 
+#include <type_traits>
+
 namespace ccs {
 
 constexpr int kMaxWh = (kMaxTableauQubits + 63) / 64;
@@ -1074,6 +1076,48 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
   }
   return c;
 }
+// Shots [t0, t1) of one variant (t0 a multiple of 4 x fields per word),
+// threads strided over generator calls.  L = table lookups per shot, tied to
+// the rank: a 32-bit output word serves S = 4 / 2 / 1 shots (8-, 16-, 32-bit
+// fields, low bits first) at rank <= 8 / <= 16 / above, so call g (counter
+// (g, variant, fragment, problem)) serves shots 4 S g .. 4 S g + 4 S - 1,
+// word j field h being shot (4 g + j) S + h.  fn receives the shot's rank
+// coefficient bits.
+template <int L, class Fn>
+__device__ __forceinline__ void for_shots(uint32_t t0, uint32_t t1, uint4 ctr, uint32_t k0, uint32_t k1,
+                                          uint32_t cmask, Fn fn) {
+  constexpr int S = L == 1 ? 4 : L == 2 ? 2 : 1, WB = 32 / S;
+  for (uint32_t g = t0 / (4 * S) + threadIdx.x; (unsigned long long)(4 * S) * g < t1; g += blockDim.x) {
+    ctr.x = g;
+    const uint4 o = philox4x32_10(ctr, k0, k1);
+    const uint32_t w4[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int h = 0; h < S; ++h) {
+        const uint32_t t = (4 * g + j) * S + h;
+        if (t < t1) fn((S == 1 ? w4[j] : w4[j] >> (h * WB)) & cmask);
+      }
+  }
+}
+
+// Outcome of coefficient bits c: off ^ the basis vectors c selects.
+template <int L>
+__device__ __forceinline__ uint32_t space_point(const uint32_t (*tbl)[256], uint32_t off, uint32_t c) {
+  uint32_t y = off ^ tbl[0][c & 255];
+  if (L >= 2) y ^= tbl[1][(c >> 8) & 255];
+  if (L >= 3) y ^= tbl[2][(c >> 16) & 255];
+  return y;
+}
+
+// Calls fn with the lookups a rank needs as a compile-time constant.
+template <class Fn>
+__device__ __forceinline__ void by_rank(int rank, Fn fn) {
+  if (rank <= 8) fn(std::integral_constant<int, 1>{});
+  else if (rank <= 16) fn(std::integral_constant<int, 2>{});
+  else fn(std::integral_constant<int, 3>{});
+}
+
 }  // namespace
 
 constexpr int kHistSmem = 8192;   // dense per-CTA histogram up to |A| = 13
@@ -1096,21 +1140,18 @@ __global__ void __launch_bounds__(256) sample_kernel(DevPlan P, DevRes R, EvalPa
   __syncthreads();
   uint32_t* gcounts = R.counts + F.counts_off + ((long long)v << nA);
   const uint32_t cmask = rank >= 32 ? 0xffffffffu : ((1u << rank) - 1u);
-  // shot 4g+j takes output word j of the generator at counter (g, v, f, problem)
-  const uint32_t s_end = min((uint32_t)E.shots, (uint32_t)(chunk + 1) * (uint32_t)spc);
-  for (uint32_t g = ((uint32_t)chunk * spc >> 2) + threadIdx.x; 4 * g < s_end; g += blockDim.x) {
-    const uint4 o = philox4x32_10(make_uint4(g, (uint32_t)v, (uint32_t)F.findex, (uint32_t)F.problem),
-                                  E.seed_lo, E.seed_hi);
-    const uint32_t w4[4] = {o.x, o.y, o.z, o.w};
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      if (4 * g + j >= s_end) break;
-      const uint32_t c = w4[j] & cmask;
-      const uint32_t y = off ^ tbl[0][c & 255] ^ tbl[1][(c >> 8) & 255] ^ tbl[2][(c >> 16) & 255];
+  // this CTA's chunk of shots (spc is a multiple of 16: whole generator calls)
+  const uint32_t t0 = (uint32_t)chunk * (uint32_t)spc;
+  const uint32_t s_end = min((uint32_t)E.shots, t0 + (uint32_t)spc);
+  const uint4 ctr = make_uint4(0u, (uint32_t)v, (uint32_t)F.findex, (uint32_t)F.problem);
+  by_rank(rank, [&](auto lk) {
+    constexpr int L = decltype(lk)::value;
+    for_shots<L>(t0, s_end, ctr, E.seed_lo, E.seed_hi, cmask, [&](uint32_t c) {
+      const uint32_t y = space_point<L>(tbl, off, c);
       if (smem_hist) atomicAdd(&hist[y], 1u);
       else atomicAdd(&gcounts[y], 1u);
-    }
-  }
+    });
+  });
   if (smem_hist) {
     __syncthreads();
     for (int y = threadIdx.x; y < (1 << nA); y += blockDim.x)
@@ -1170,51 +1211,6 @@ __device__ __forceinline__ void hub_pair_out_packed(unsigned (&p)[16], unsigned*
   }
 }
 
-// Shots of one variant into 16-bit (or, wide, 32-bit) counters; L = table
-// lookups per shot (1 at rank <= 8, 2 at rank <= 16).
-template <int L>
-__device__ __forceinline__ void sample_words(uint32_t* hist2, const uint32_t (*tbl)[256], uint32_t off,
-                                             uint32_t cmask, uint32_t shots, uint4 ctr, uint32_t k0, uint32_t k1,
-                                             int wide) {
-  for (uint32_t g = threadIdx.x; 4 * g < shots; g += blockDim.x) {
-    ctr.x = g;
-    const uint4 o = philox4x32_10(ctr, k0, k1);
-    const uint32_t w4[4] = {o.x, o.y, o.z, o.w};
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      if (4 * g + j >= shots) break;
-      const uint32_t c = w4[j] & cmask;
-      uint32_t y = off ^ tbl[0][c & 255];
-      if (L >= 2) y ^= tbl[1][(c >> 8) & 255];
-      if (L >= 3) y ^= tbl[2][(c >> 16) & 255];
-      if (wide) atomicAdd(&hist2[y], 1u);
-      else atomicAdd(&hist2[y >> 1], 1u << ((y & 1u) << 4));
-    }
-  }
-}
-
-// Shots of one variant into byte counters (shot 4g+j = word j of Philox call
-// g); L = table lookups per shot (2 when rank <= 16).  Sets *over when a
-// byte wraps.
-template <int L>
-__device__ __forceinline__ void sample_bytes(uint32_t* h32, const uint32_t (*tbl)[256], uint32_t off, uint32_t cmask,
-                                             uint32_t shots, uint4 ctr, uint32_t k0, uint32_t k1, int* over) {
-  for (uint32_t g = threadIdx.x; 4 * g < shots; g += blockDim.x) {
-    ctr.x = g;
-    const uint4 o = philox4x32_10(ctr, k0, k1);
-    const uint32_t w4[4] = {o.x, o.y, o.z, o.w};
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      if (4 * g + j >= shots) break;
-      const uint32_t c = w4[j] & cmask;
-      uint32_t y = off ^ tbl[0][c & 255] ^ tbl[1][(c >> 8) & 255];
-      if (L == 3) y ^= tbl[2][(c >> 16) & 255];
-      const uint32_t sh = (y & 3u) << 3;
-      const uint32_t old = atomicAdd(&h32[y >> 2], 1u << sh);
-      if (((old >> sh) & 0xffu) == 0xffu) *over = 1;     // a byte wrapped: recount wider
-    }
-  }
-}
 }  // namespace
 
 // --- K3 + K5 fused for the hub of a star --------------------------------
@@ -1252,11 +1248,16 @@ __global__ void __launch_bounds__(512) sample_hub_kernel(DevPlan P, DevRes R, Ev
   }
   __syncthreads();
   const uint32_t cmask = rank >= 32 ? 0xffffffffu : ((1u << rank) - 1u);
-  {   // shot 4g+j: word j of Philox call g
+  {
     const uint4 ctr = make_uint4(0u, (uint32_t)v, (uint32_t)F.findex, (uint32_t)F.problem);
-    if (rank <= 8) sample_words<1>(hist2, tbl, off, cmask, E.shots, ctr, E.seed_lo, E.seed_hi, wide);
-    else if (rank <= 16) sample_words<2>(hist2, tbl, off, cmask, E.shots, ctr, E.seed_lo, E.seed_hi, wide);
-    else sample_words<3>(hist2, tbl, off, cmask, E.shots, ctr, E.seed_lo, E.seed_hi, wide);
+    by_rank(rank, [&](auto lk) {
+      constexpr int L = decltype(lk)::value;
+      for_shots<L>(0u, E.shots, ctr, E.seed_lo, E.seed_hi, cmask, [&](uint32_t c) {
+        const uint32_t y = space_point<L>(tbl, off, c);
+        if (wide) atomicAdd(&hist2[y], 1u);
+        else atomicAdd(&hist2[y >> 1], 1u << ((y & 1u) << 4));
+      });
+    });
   }
   __syncthreads();
   auto count = [&](uint32_t y) -> uint32_t {
@@ -1450,10 +1451,6 @@ __global__ void __launch_bounds__(256) sample_hub8_kernel(DevPlan P, DevRes R, E
   const int wstride = E.shots <= 32767u ? 17 : 33;   // packed transforms need 16 words, unpacked 32
   int* wht = reinterpret_cast<int*>(h32 + hist_words) + tid * wstride;
   uint32_t* gcount = R.counts + F.counts_off + ((long long)v << nA);
-  auto sample_y = [&](uint32_t w) -> uint32_t {
-    const uint32_t c = w & cmask;
-    return off ^ tbl[0][c & 255] ^ tbl[1][(c >> 8) & 255] ^ tbl[2][(c >> 16) & 255];
-  };
   bool narrow = (unsigned long long)E.shots <= (64ull << rank);
   if (narrow) {
     {   // zero the histogram, 16 bytes per store
@@ -1463,8 +1460,14 @@ __global__ void __launch_bounds__(256) sample_hub8_kernel(DevPlan P, DevRes R, E
     }
     __syncthreads();
     const uint4 ctr = make_uint4(0u, (uint32_t)v, (uint32_t)F.findex, (uint32_t)F.problem);
-    if (rank <= 16) sample_bytes<2>(h32, tbl, off, cmask, E.shots, ctr, E.seed_lo, E.seed_hi, &s_over);
-    else sample_bytes<3>(h32, tbl, off, cmask, E.shots, ctr, E.seed_lo, E.seed_hi, &s_over);
+    by_rank(rank, [&](auto lk) {
+      constexpr int L = decltype(lk)::value;
+      for_shots<L>(0u, E.shots, ctr, E.seed_lo, E.seed_hi, cmask, [&](uint32_t c) {
+        const uint32_t y = space_point<L>(tbl, off, c), sh = (y & 3u) << 3;
+        const uint32_t old = atomicAdd(&h32[y >> 2], 1u << sh);
+        if (((old >> sh) & 0xffu) == 0xffu) s_over = 1;     // a byte wrapped: recount wider
+      });
+    });
     __syncthreads();
     narrow = s_over == 0;
     if (narrow) {
@@ -1492,19 +1495,16 @@ __global__ void __launch_bounds__(256) sample_hub8_kernel(DevPlan P, DevRes R, E
       __syncthreads();
       for (int i = tid; i < (1 << (nA - 1)) / 2; i += nt) h32[i] = 0u;
       __syncthreads();
-      for (uint32_t g = tid; 4 * g < E.shots; g += nt) {
-        const uint4 o = philox4x32_10(make_uint4(g, (uint32_t)v, (uint32_t)F.findex, (uint32_t)F.problem),
-                                      E.seed_lo, E.seed_hi);
-        const uint32_t w4[4] = {o.x, o.y, o.z, o.w};
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          if (4 * g + j >= E.shots) break;
-          const uint32_t y = sample_y(w4[j]);
-          if ((int)((y >> mh) & 1u) != h) continue;
+      const uint4 ctr = make_uint4(0u, (uint32_t)v, (uint32_t)F.findex, (uint32_t)F.problem);
+      by_rank(rank, [&](auto lk) {
+        constexpr int L = decltype(lk)::value;
+        for_shots<L>(0u, E.shots, ctr, E.seed_lo, E.seed_hi, cmask, [&](uint32_t c) {
+          const uint32_t y = space_point<L>(tbl, off, c);
+          if ((int)((y >> mh) & 1u) != h) return;
           const uint32_t yh = (y & (uint32_t)(Mh - 1)) | ((y >> m) << mh);
           atomicAdd(&h32[yh >> 1], 1u << ((yh & 1u) << 4));
-        }
-      }
+        });
+      });
       __syncthreads();
       if (keep_counts)
         for (uint32_t yh = tid; yh < (1u << (nA - 1)); yh += nt) {

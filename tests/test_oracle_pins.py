@@ -14,7 +14,7 @@ from workloads import (H, S, SDG, X, Y, Z, CX, CZ, T, Circuit, small_star, confi
 from workloads.circuits import C1_WORDS
 from oracle import tableau as tb
 from oracle import statevector as sv
-from oracle.philox import philox4x32_10, shot_words
+from oracle.philox import philox4x32_10, shot_coeffs, shot_words
 from oracle.pipeline import evaluate, evaluate_workload, brute_force, uncut_clifford, sample_counts
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -256,3 +256,18 @@ def test_shot_words_layout():
             if 4 * k + j < 11:
                 assert int(w[4 * k + j]) == int(out[j])
     assert np.array_equal(shot_words(7, 5, 6, 7, 0xA, 0xB), w[:7])
+
+
+@pytest.mark.parametrize("rank,per_word", [(0, 4), (5, 4), (8, 4), (9, 2), (16, 2), (17, 1), (24, 1)])
+def test_shot_coeffs_layout(rank, per_word):
+    """A word serves four shots at rank <= 8 (bytes, low byte first), two at
+    rank <= 16 (half words), one above; each shot keeps its low rank bits.
+    Checked against the generator's raw output words, shot by shot."""
+    n = 37
+    c = shot_coeffs(n, rank, 5, 6, 7, 0xA, 0xB)
+    width = 32 // per_word
+    for t in range(n):
+        widx = t // per_word
+        word = int(philox4x32_10(widx // 4, 5, 6, 7, 0xA, 0xB)[widx % 4])
+        field = (word >> (width * (t % per_word))) & ((1 << width) - 1)
+        assert int(c[t]) == field & ((1 << rank) - 1), (t, rank)
