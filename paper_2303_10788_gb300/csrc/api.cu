@@ -217,6 +217,7 @@ struct ccs_plan_s {
   long long* d_out_prefix = nullptr;
   long long* d_z_prefix = nullptr;
   int cliff_smem_words = 0, max_nc_n = 1;
+  int nc_basis_chunk = 1;           // basis combinations per statevector item
   int body_smem_words = 0;          // variant kernel started from a shared body (no op staging)
   FoldSet fold_cliff{}, fold_nc{}, fold_hubs{}, fold_hubs_nc{}, fold_others{};
   int2* d_items_hub = nullptr;      // Clifford hub variants (fused sampler)
@@ -491,6 +492,7 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
   std::vector<NCOp> nops;
   std::vector<int> moments, wires, zoffs;
   std::vector<int2> items_c, items_nc, items_b, items_z, zblocks;
+  std::vector<int> nc_frags;
   std::vector<int> cliff_frags;
   int img_words_max = 0, body_words_max = 0;
   int max_body_stage = 0, max_moment_ops = 1;
@@ -575,10 +577,7 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
     } else {
       d.space_off = d.counts_off = d.tab_off = d.body_off = d.rb_off = d.zimg_off = -1;
       plan->max_nc_n = std::max(plan->max_nc_n, d.n);
-      for (int v = 0; v < d.nv; ++v) {
-        items_nc.push_back(make_int2((int)fi, v));
-        cost_nc.push_back((1ll << d.n) * ((long long)f.nops.size() + 4));
-      }
+      nc_frags.push_back((int)fi);
     }
     d.dist_off = plan->n_dist;
     plan->n_dist += (long long)d.nv * outs;
@@ -611,6 +610,26 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
     it.swap(out);
   };
   sort_items(items_c, cost_c);
+  // Non-Clifford items: with enough variants to fill the GPU, one item per
+  // preparation combination (the gates run once, every basis combination of
+  // the outputs is applied to a copy of the state); otherwise one per variant
+  // (latency: no serial basis tails).
+  {
+    long long nc_total = 0;
+    for (int fi : nc_frags) nc_total += plan->fdev[fi].nv;
+    const int chunk = nc_total > 2ll * std::max(c->sm_count, 148) ? 1 << 30 : 1;
+    plan->nc_basis_chunk = chunk;
+    for (int fi : nc_frags) {
+      const FragDev& d = plan->fdev[fi];
+      const int n_prep = 1 << (2 * d.qin), n_basis = d.nv / n_prep;
+      const long long nops = plan->frags[fi].nops.size();
+      for (int b0 = 0; b0 < n_basis; b0 += std::min(chunk, n_basis))
+        for (int pc = 0; pc < n_prep; ++pc) {
+          items_nc.push_back(make_int2(fi, pc + n_prep * b0));
+          cost_nc.push_back((1ll << d.n) * (nops + 4 + 8ll * std::min(chunk, n_basis - b0)));
+        }
+    }
+  }
   sort_items(items_nc, cost_nc);
 
   int f0 = 0;
@@ -806,7 +825,7 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
   bool ok = st.commit(c, plan->A);
   if (!ok) { delete plan; return fail(c, CCS_ERR_OOM, "plan upload failed"); }
   dp.frags = dfr; dp.cops = dco; dp.nops = dno; dp.moments = dmo; dp.wires = dwi; dp.zoffs = dzo;
-  dp.items_cliff = dic; dp.items_nc = din;
+  dp.items_cliff = dic; dp.items_nc = din; dp.nc_basis_chunk = plan->nc_basis_chunk;
   dp.n_items_cliff = (int)items_c.size(); dp.n_items_nc = (int)items_nc.size();
   dp.items_body = dib; dp.n_items_body = (int)items_b.size(); dp.max_body_cols = max_body_cols;
   dp.cliff_frags = dcf; dp.n_cliff_frags = (int)cliff_frags.size();

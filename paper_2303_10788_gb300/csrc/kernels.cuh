@@ -71,7 +71,8 @@ struct DevPlan {
   const int* wires;
   const int* zoffs;
   const int2* items_cliff;    // (frag, variant), costliest first
-  const int2* items_nc;
+  const int2* items_nc;       // (frag, first variant) of every statevector item
+  int nc_basis_chunk;         // basis combinations an item covers (variants v0, v0 + 4^qin, ...)
   int n_items_cliff, n_items_nc;
   const int2* items_body;     // (frag, 64-row word) of every Clifford fragment's body
   int n_items_body, max_body_cols;

@@ -1,11 +1,13 @@
-// Non-Clifford fragments (K4): one complex64 statevector of 2^n amplitudes per
-// variant in shared memory (the paper hands these fragments to an exact
-// statevector simulator, Sec. V-B).  Gates arrive fused into 2x2 / 4x4
-// unitaries.  Each op reads one buffer and writes the other (ping-pong), one
-// output amplitude per thread and pass: out_i = sum_c M[r(i)][c] psi[j_c(i)],
-// so an op costs one short dependency chain and one barrier.  Outputs: the
-// exact marginal on A_f and the Z-string values, both reduced in a fixed
-// order (deterministic).
+// Non-Clifford fragments (K4): complex64 statevectors of 2^n amplitudes in
+// shared memory (the paper hands these fragments to an exact statevector
+// simulator, Sec. V-B).  A variant is (preparations, the fragment's gates U,
+// output basis changes), so an item (one preparation combination and a
+// range of basis combinations) runs U once and then, for each basis
+// combination, applies the output basis changes to a copy of the state.  Gates arrive fused into 2x2 / 4x4 unitaries; each
+// gate reads one buffer and writes the other (ping-pong), one output
+// amplitude per thread and pass, one barrier per gate.  Outputs per
+// variant: the exact marginal on A_f and the Z-string values, both reduced
+// in a fixed order (deterministic).
 #include "kernels.cuh"
 
 namespace ccs {
@@ -64,8 +66,8 @@ constexpr int kZChunk = 256;    // Z-string masks built per pass
 
 __global__ void __launch_bounds__(512) statevector_kernel(DevPlan P, DevRes R, int max_n) {
   extern __shared__ float2 sv_smem[];
-  float2* buf[2] = {sv_smem, sv_smem + (1u << max_n)};
-  NCOp* ops_s = reinterpret_cast<NCOp*>(sv_smem + (2u << max_n));
+  float2* buf[3] = {sv_smem, sv_smem + (1u << max_n), sv_smem + (2u << max_n)};
+  NCOp* ops_s = reinterpret_cast<NCOp*>(sv_smem + (3u << max_n));
   __shared__ int s_item;
   __shared__ unsigned s_abit[kMaxMeas];     // bit of each A wire in the amplitude index
   __shared__ unsigned s_zm[kZChunk];        // Z masks of a chunk of Z-strings
@@ -79,14 +81,16 @@ __global__ void __launch_bounds__(512) statevector_kernel(DevPlan P, DevRes R, i
     if (item >= P.n_items_nc) break;
     const int2 it = P.items_nc[item];
     const FragDev& F = P.frags[it.x];
-    const int v = it.y, n = F.n, qin = F.qin, qout = F.qout, nA = F.nA, nz = F.nz;
+    const int n = F.n, qin = F.qin, qout = F.qout, nA = F.nA, nz = F.nz;
+    const int n_prep = 1 << (2 * qin), n_basis = F.nv / n_prep;
+    const int pc = it.y % n_prep, b0 = it.y / n_prep, b1 = min(n_basis, b0 + P.nc_basis_chunk);
     const unsigned N = 1u << n;
     const int op0 = P.moments[F.mom_off], op1 = P.moments[F.mom_off + F.n_moments];
     int cur = 0;
     for (unsigned i = tid; i < N; i += blockDim.x) buf[0][i] = make_float2(i == 0 ? 1.f : 0.f, 0.f);
     __syncthreads();
     for (int o = 0; o < qin; ++o) {
-      apply_1q(buf[cur], buf[cur ^ 1], N, P.wires[F.qin_off + o], P.prep_mats + 8 * digit_in(v, o));
+      apply_1q(buf[cur], buf[cur ^ 1], N, P.wires[F.qin_off + o], P.prep_mats + 8 * digit_in(pc, o));
       cur ^= 1;
       __syncthreads();
     }
@@ -104,71 +108,82 @@ __global__ void __launch_bounds__(512) statevector_kernel(DevPlan P, DevRes R, i
         __syncthreads();
       }
     }
-    for (int o = 0; o < qout; ++o) {
-      apply_1q(buf[cur], buf[cur ^ 1], N, P.wires[F.qout_off + o], P.basis_mats + 8 * digit_out(v, qin, o));
-      cur ^= 1;
-      __syncthreads();
-    }
-    // probabilities into the other buffer
-    const float2* psi = buf[cur];
-    float* pr = reinterpret_cast<float*>(buf[cur ^ 1]);
-    for (unsigned i = tid; i < N; i += blockDim.x) pr[i] = psi[i].x * psi[i].x + psi[i].y * psi[i].y;
+    // U |prep> stays in buf[cur]; each basis combination works in the other two
+    const float2* psiU = buf[cur];
+    float2* w0 = buf[cur ^ 1];
+    float2* w1 = buf[3 - cur - (cur ^ 1)];
     for (int j = tid; j < nA; j += blockDim.x) s_abit[j] = 1u << P.wires[F.A_off + j];
     for (int o = tid; o < qout; o += blockDim.x) s_qm[o] = 1u << P.wires[F.qout_off + o];
     __syncthreads();
-    // marginal on A: one warp per output, lanes over its completions, then a
-    // fixed shuffle tree
     unsigned amask = 0;
     for (int j = 0; j < nA; ++j) amask |= s_abit[j];
     const unsigned rest = (N - 1) & ~amask;
     const unsigned ncomp = 1u << (n - nA);
-    float* d = R.dist + F.dist_off + ((long long)v << nA);
-    for (unsigned y = warp; y < (1u << nA); y += nwarps) {
-      unsigned base = 0;
-      for (int j = 0; j < nA; ++j)
-        if ((y >> j) & 1u) base |= s_abit[j];
-      float acc = 0.f;
-      for (unsigned c = lane; c < ncomp; c += 32) {
-        unsigned idx = base, cc = c;          // deposit c's bits into the positions of `rest`
-        for (unsigned rm = rest; rm && cc; rm &= rm - 1, cc >>= 1)
-          if (cc & 1u) idx |= rm & (0u - rm);
-        acc += pr[idx];
+    for (int bc = b0; bc < b1; ++bc) {
+      const int v = pc + n_prep * bc;
+      const float2* psi = psiU;
+      float2* wa = w0;
+      float2* wb = w1;
+      for (int o = 0; o < qout; ++o) {
+        apply_1q(psi, wa, N, P.wires[F.qout_off + o], P.basis_mats + 8 * digit_out(v, qin, o));
+        __syncthreads();
+        psi = wa;
+        float2* t = wa; wa = wb; wb = t;
       }
-      for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) d[y] = acc;
-    }
-    // Z-string values <Z_S> = sum_x (-1)^{|x & S|} p(x): the Walsh-Hadamard
-    // transform of the probabilities, in place
-    if (nz > 0) {
+      // probabilities into a free buffer (not psiU, not psi)
+      float* pr = reinterpret_cast<float*>(psi == w0 ? w1 : w0);
+      for (unsigned i = tid; i < N; i += blockDim.x) pr[i] = psi[i].x * psi[i].x + psi[i].y * psi[i].y;
       __syncthreads();
-      for (int h = 0; h < n; ++h) {
-        for (unsigned t = tid; t < (N >> 1); t += blockDim.x) {
-          const unsigned i0 = insert_zero(t, h), i1 = i0 | (1u << h);
-          const float x0 = pr[i0], x1 = pr[i1];
-          pr[i0] = x0 + x1;
-          pr[i1] = x0 - x1;
+      // marginal on A: one warp per output, lanes over its completions, then a
+      // fixed shuffle tree
+      float* d = R.dist + F.dist_off + ((long long)v << nA);
+      for (unsigned y = warp; y < (1u << nA); y += nwarps) {
+        unsigned base = 0;
+        for (int j = 0; j < nA; ++j)
+          if ((y >> j) & 1u) base |= s_abit[j];
+        float acc = 0.f;
+        for (unsigned c = lane; c < ncomp; c += 32) {
+          unsigned idx = base, cc = c;          // deposit c's bits into the positions of `rest`
+          for (unsigned rm = rest; rm && cc; rm &= rm - 1, cc >>= 1)
+            if (cc & 1u) idx |= rm & (0u - rm);
+          acc += pr[idx];
         }
-        __syncthreads();
+        for (int o = 16; o; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) d[y] = acc;
       }
-      for (int z0 = 0; z0 < nz; z0 += kZChunk) {
-        const int zc = min(kZChunk, nz - z0);
-        for (int k = tid; k < zc; k += blockDim.x) {
-          unsigned zm = 0;
-          for (int q = P.zoffs[F.zw_off + z0 + k]; q < P.zoffs[F.zw_off + z0 + k + 1]; ++q) zm ^= 1u << P.wires[q];
-          s_zm[k] = zm;
-        }
+      // Z-string values <Z_S> = sum_x (-1)^{|x & S|} p(x): the Walsh-Hadamard
+      // transform of the probabilities, in place
+      if (nz > 0) {
         __syncthreads();
-        for (int ev = tid; ev < (zc << qout); ev += blockDim.x) {
-          const int k = ev >> qout, u = ev & ((1 << qout) - 1);
-          unsigned zm = s_zm[k];
-          for (int o = 0; o < qout; ++o)
-            if ((u >> o) & 1) zm ^= s_qm[o];
-          R.zval[F.zval_off + ((long long)v * nz + z0 + k) * (1 << qout) + u] = pr[zm];
+        for (int h = 0; h < n; ++h) {
+          for (unsigned t = tid; t < (N >> 1); t += blockDim.x) {
+            const unsigned i0 = insert_zero(t, h), i1 = i0 | (1u << h);
+            const float x0 = pr[i0], x1 = pr[i1];
+            pr[i0] = x0 + x1;
+            pr[i1] = x0 - x1;
+          }
+          __syncthreads();
         }
-        __syncthreads();
+        for (int z0 = 0; z0 < nz; z0 += kZChunk) {
+          const int zc = min(kZChunk, nz - z0);
+          for (int k = tid; k < zc; k += blockDim.x) {
+            unsigned zm = 0;
+            for (int q = P.zoffs[F.zw_off + z0 + k]; q < P.zoffs[F.zw_off + z0 + k + 1]; ++q) zm ^= 1u << P.wires[q];
+            s_zm[k] = zm;
+          }
+          __syncthreads();
+          for (int ev = tid; ev < (zc << qout); ev += blockDim.x) {
+            const int k = ev >> qout, u = ev & ((1 << qout) - 1);
+            unsigned zm = s_zm[k];
+            for (int o = 0; o < qout; ++o)
+              if ((u >> o) & 1) zm ^= s_qm[o];
+            R.zval[F.zval_off + ((long long)v * nz + z0 + k) * (1 << qout) + u] = pr[zm];
+          }
+          __syncthreads();
+        }
       }
+      __syncthreads();
     }
-    __syncthreads();
   }
 }
 
@@ -176,7 +191,7 @@ cudaError_t launch_statevector(const DevPlan& p, const DevRes& r, int max_n, int
                                cudaStream_t s) {
   if (p.n_items_nc == 0) return cudaSuccess;
 
-  const size_t smem = ((size_t)16 << max_n) + (size_t)kOpStage * sizeof(NCOp);
+  const size_t smem = ((size_t)24 << max_n) + (size_t)kOpStage * sizeof(NCOp);
   cudaError_t err = cudaFuncSetAttribute(statevector_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
   if (err != cudaSuccess) return err;
