@@ -200,6 +200,7 @@ struct ccs_plan_s {
   Allocs A;
   long long n_spaces = 0, n_counts = 0, n_dist = 0, n_zval = 0, n_tab = 0, n_T = 0, n_TZ = 0, n_body = 0;
   long long n_zimg = 0;             // uint64 words of Z images
+  long long n_pbasis = 0;           // uint32 words of projected shared-row bases
   long long n_marg = 0, n_zexp = 0;
   std::vector<long long> t_prefix, tz_prefix, out_prefix, z_prefix, r_prefix, blk_prefix;
   std::vector<int2> direct_items;   // (problem, hub-output slice) contracted leaf by leaf
@@ -550,6 +551,13 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
       plan->n_body += (long long)(2 * d.n + 3) * d.W;
       d.rb_off = (long long)kRowBasisWords * (long long)cliff_frags.size();
       cliff_frags.push_back((int)fi);
+      d.pb_off = -1;
+      if (d.qout <= kMaxPbQout) {
+        int combos = 1;
+        for (int o = 0; o < d.qout; ++o) combos *= 3;
+        d.pb_off = plan->n_pbasis;
+        plan->n_pbasis += 25ll * combos;
+      }
       {   // Z images: every string, X, Y, Z of every quantum output, Z of every marginal wire
         const int ni = d.nz + 3 * d.qout + d.m;
         d.zimg_off = plan->n_zimg;
@@ -575,7 +583,7 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
         cost_c.push_back((long long)d.W * (d.n_moments + 4) * std::max(1, d.n / 16) + d.nz * 4 + d.nA * d.n);
       }
     } else {
-      d.space_off = d.counts_off = d.tab_off = d.body_off = d.rb_off = d.zimg_off = -1;
+      d.space_off = d.counts_off = d.tab_off = d.body_off = d.rb_off = d.zimg_off = d.pb_off = -1;
       plan->max_nc_n = std::max(plan->max_nc_n, d.n);
       nc_frags.push_back((int)fi);
     }
@@ -1071,6 +1079,7 @@ int ccs_eval_variants(ccs_ctx c, ccs_plan p, const ccs_eval_opts* opts, ccs_res*
     d.body = r->A.get<unsigned long long>(std::max<long long>(p->n_body, 2));
     d.rowbasis = r->A.get<unsigned long long>(std::max<long long>((long long)kRowBasisWords * p->dp.n_cliff_frags, 1));
     d.zimg = r->A.get<unsigned long long>(std::max<long long>(p->n_zimg, 1));
+    d.pbasis = r->A.get<uint32_t>(std::max<long long>(p->n_pbasis, 1));
 
     d.status = r->A.get<unsigned>(4);
     r->scratch = r->A.get<float>(std::max<long long>(p->r_total + p->part_total, 1));
@@ -1091,7 +1100,7 @@ int ccs_eval_variants(ccs_ctx c, ccs_plan p, const ccs_eval_opts* opts, ccs_res*
       r->rt_scratch = r->A.get<uint16_t>(p->rt_total);
     }
     if (!d.spaces || !d.dist || !d.zval || !d.T || !d.TQ || !d.TZ || !d.marg || !d.zexp || !d.work || !d.status ||
-        !d.body || !d.rowbasis || !d.zimg || !d.fragcnt ||
+        !d.body || !d.rowbasis || !d.zimg || !d.fragcnt || !d.pbasis ||
         !r->scratch || (p->rt_total && (!d.TQh || !r->rt_scratch))) {
       delete r;
       return fail(c, CCS_ERR_OOM, "result allocation failed");

@@ -439,6 +439,44 @@ __device__ __forceinline__ unsigned pack_out_digits(int v, int qin, int qout) {
   return p;
 }
 
+// Fold the lanes' rows (bits < nA) into a warp's echelon basis: lane p holds
+// the vector with pivot p in `mine`, `have` the pivot set (warp-uniform).
+__device__ __forceinline__ void absorb32(uint32_t row, uint32_t& have, uint32_t& mine, int nA, int lane) {
+  const unsigned FULLW = 0xffffffffu;
+  for (uint32_t h = have; h; h &= h - 1) {
+    const int p = __ffs(h) - 1;
+    const uint32_t bp = __shfl_sync(FULLW, mine, p);
+    if ((row >> p) & 1u) row ^= bp;
+  }
+  for (int p = 0; p < nA; ++p) {
+    if ((have >> p) & 1u) continue;
+    const unsigned msk = __ballot_sync(FULLW, (row >> p) & 1u);
+    if (!msk) continue;
+    const int leader = __ffs(msk) - 1;
+    const uint32_t prow = __shfl_sync(FULLW, row, leader);
+    if (lane == leader) row = 0;
+    else if ((row >> p) & 1u) row ^= prow;
+    if (lane == p) mine = prow;
+    have |= 1u << p;
+  }
+}
+
+// Projection of an extended vector (X bits on A, then Z bits on the quantum
+// outputs) through output basis digits pout (0 X, 1 Y, 2 Z): the X bit of
+// output o becomes its observable's anticommutation bit, z for X, x ^ z for
+// Y, x for Z.
+__device__ __forceinline__ uint32_t project_ext(unsigned long long e, int nA, int m, int qout, unsigned pout) {
+  uint32_t keepX = (1u << m) - 1u, fromZ = 0u;
+  for (int o = 0; o < qout; ++o) {
+    const unsigned d = (pout >> (2 * o)) & 3u;
+    if (d != 0) keepX |= 1u << (m + o);
+    if (d != 2) fromZ |= 1u << (m + o);
+  }
+  const uint32_t x = (uint32_t)(e & ((1ull << nA) - 1ull));
+  const uint32_t z = (uint32_t)((e >> nA) << m);
+  return (x & keepX) ^ (z & fromZ);
+}
+
 // Fold `row` into the warp's echelon basis eb[] (pivot slots) / have.
 __device__ __forceinline__ void absorb64(unsigned long long row, unsigned long long* eb, unsigned long long& have,
                                          int ne, int lane) {
@@ -583,7 +621,27 @@ __global__ void __launch_bounds__(256) body_basis_kernel(DevPlan P, DevRes R) {
   if (warp == 0) {
     unsigned long long* out = R.rowbasis + F.rb_off;
     for (int p = lane; p < 64; p += 32) out[p] = ((have >> p) & 1ull) ? s_eb[0][p] : 0ull;
-    if (lane == 0) out[64] = have;
+    if (lane == 0) {
+      out[64] = have;
+      s_eh[0] = have;
+    }
+  }
+  if (F.pb_off < 0) return;
+  // the shared rows projected through each output basis combination
+  __syncthreads();
+  const unsigned long long sh = s_eh[0];
+  int combos = 1;
+  for (int o = 0; o < F.qout; ++o) combos *= 3;
+  for (int pc = warp; pc < combos; pc += nwarps) {
+    unsigned pout = 0;
+    for (int o = 0, t = pc; o < F.qout; ++o, t /= 3) pout |= (unsigned)(t % 3) << (2 * o);
+    uint32_t h32 = 0, mine = 0;
+    absorb32(((sh >> lane) & 1ull) ? project_ext(s_eb[0][lane], nA, F.m, F.qout, pout) : 0u, h32, mine, nA, lane);
+    absorb32(((sh >> (lane + 32)) & 1ull) ? project_ext(s_eb[0][lane + 32], nA, F.m, F.qout, pout) : 0u, h32,
+             mine, nA, lane);
+    uint32_t* pb = R.pbasis + F.pb_off + 25ll * pc;
+    if (lane < 24) pb[lane] = ((h32 >> lane) & 1u) ? mine : 0u;
+    if (lane == 0) pb[24] = h32;
   }
 }
 
@@ -652,28 +710,19 @@ __global__ void __launch_bounds__(256) screen_kernel(DevPlan P, DevRes R, EvalPa
       return (x & keepX) ^ (z & fromZ);
     };
     uint32_t have = 0, mine = 0;
-    auto absorb = [&](uint32_t row) {
-      for (uint32_t h = have; h; h &= h - 1) {
-        const int p = __ffs(h) - 1;
-        const uint32_t bp = __shfl_sync(FULLW, mine, p);
-        if ((row >> p) & 1u) row ^= bp;
-      }
-      for (int p = 0; p < nA; ++p) {
-        if ((have >> p) & 1u) continue;
-        const unsigned msk = __ballot_sync(FULLW, (row >> p) & 1u);
-        if (!msk) continue;
-        const int leader = __ffs(msk) - 1;
-        const uint32_t prow = __shfl_sync(FULLW, row, leader);
-        if (lane == leader) row = 0;
-        else if ((row >> p) & 1u) row ^= prow;
-        if (lane == p) mine = prow;
-        have |= 1u << p;
-      }
-    };
+    auto absorb = [&](uint32_t row) { absorb32(row, have, mine, nA, lane); };
     const unsigned long long* rb = R.rowbasis + F.rb_off;
-    const unsigned long long sh = rb[64];
-    absorb(((sh >> lane) & 1ull) ? project(rb[lane]) : 0u);
-    absorb(((sh >> (lane + 32)) & 1ull) ? project(rb[lane + 32]) : 0u);
+    if (F.pb_off >= 0) {   // the shared rows' basis for this output basis combination
+      int pc = v;
+      for (int i = 0; i < F.qin; ++i) pc >>= 2;
+      const uint32_t* pb = R.pbasis + F.pb_off + 25ll * pc;
+      have = pb[24];
+      mine = lane < 24 ? pb[lane] : 0u;
+    } else {
+      const unsigned long long sh = rb[64];
+      absorb(((sh >> lane) & 1ull) ? project(rb[lane]) : 0u);
+      absorb(((sh >> (lane + 32)) & 1ull) ? project(rb[lane + 32]) : 0u);
+    }
     {   // new stabilizer rows of the quantum inputs (bits only): the image of
         // C Z C^+ is D, S or their product, from the fragment's input rows
       uint32_t row = 0;

@@ -32,6 +32,8 @@ struct FragDev {
   long long body_off;      // uint64 index of the shared body tableau ((2n+3)*W words), Clifford only
   long long rb_off;        // uint64 index of the fragment's kRowBasisWords (shared-row basis + offset table)
   long long zimg_off;      // uint64 index of the Z images (nz + 3 qout + m records of 2 Wh + 1 words)
+  long long pb_off;        // uint32 index of the projected shared-row bases, 25 words per output basis
+                           // combination (3^qout of them), -1 when qout > kMaxPbQout
 };
 
 // Canonical affine outcome space of a Clifford variant.
@@ -104,6 +106,7 @@ struct DevRes {
   unsigned long long* rowbasis;   // shared-row bases, 65 words per Clifford fragment
   unsigned long long* zimg;   // Z images: backward images of the Z-strings and measured Paulis
   unsigned* fragcnt;          // per Clifford fragment: measurement records done (zeroed per evaluation)
+  uint32_t* pbasis;           // projected shared-row bases (pivot slots 0..23 + pivot mask)
   float* T;
   float* TQ;               // contraction operands: Q for hubs, T' for the other fragments
   uint16_t* TQh;           // bf16 copy of the hubs' Q (tensor-core path), may be null
@@ -120,6 +123,9 @@ struct DevRes {
 // (kMaxCuts destabilizer words, then kMaxCuts stabilizer words).
 constexpr int kRowBasisWords = 65 + 128 + 2 * kMaxCuts;
 constexpr int kRbInputRows = 193;
+// Fragments with at most this many quantum outputs get their shared-row
+// basis projected once per output basis combination (3^qout <= 81).
+constexpr int kMaxPbQout = 4;
 
 // Largest intermediate (floats) of a star contracted leaf by leaf in shared
 // memory; larger stars take the R / GEMM / reduce chain.
