@@ -105,32 +105,6 @@ void gate_matrix_1q(int op, cd m[4]) {
   }
 }
 
-// 4x4 (index = bit_a + 2 bit_b) matrix of a gate on roles (ra, rb).
-void gate_matrix_2(int op, int ra, int rb, cd m[16]) {
-  for (int i = 0; i < 16; ++i) m[i] = 0;
-  if (op == CCS_CX || op == CCS_CZ) {
-    for (int j = 0; j < 4; ++j) {
-      int bits[2] = {j & 1, (j >> 1) & 1};
-      if (op == CCS_CX) {
-        int out[2] = {bits[0], bits[1]};
-        out[rb] ^= bits[ra];
-        m[(out[0] | out[1] << 1) * 4 + j] = 1;
-      } else {
-        m[j * 4 + j] = (bits[0] & bits[1]) ? -1.0 : 1.0;
-      }
-    }
-    return;
-  }
-  cd g[4];
-  gate_matrix_1q(op, g);
-  for (int i = 0; i < 4; ++i)
-    for (int j = 0; j < 4; ++j) {
-      int ia = (ra == 0) ? (i & 1) : (i >> 1), ja = (ra == 0) ? (j & 1) : (j >> 1);
-      int ib = (ra == 0) ? (i >> 1) : (i & 1), jb = (ra == 0) ? (j >> 1) : (j & 1);
-      m[i * 4 + j] = (ib == jb) ? g[ia * 2 + ja] : cd(0);
-    }
-}
-
 // A fused op: statevector fragments keep the gate word (for the unitary);
 // Clifford fragments apply each gate to the op's 16-pattern planes as it
 // arrives, so no word is stored.
@@ -200,7 +174,7 @@ std::vector<std::vector<const Fused*>> fuse_and_layer(const Frag& f, std::vector
     for (int side = 0; side < 2; ++side)
       if (g1[side]) const_cast<Fused*>(g1[side])->word.clear();
     nf.add(op, 0, 1, planes);
-    ops.push_back(nf);
+    ops.push_back(std::move(nf));
     last[a] = last[b] = (int)ops.size() - 1;
   }
   std::vector<int> layer_of_q(n, -1);
@@ -272,7 +246,7 @@ int fragment_problem(Problem& p, int pi, std::vector<Frag>& out, std::string& er
       Frag f;
       f.problem = pi;
       f.index = (int)out.size() - first;
-      out.push_back(f);
+      out.push_back(std::move(f));
     }
     Frag& f = out[it->second];
     int q = (int)(std::upper_bound(base.begin(), base.end(), s) - base.begin()) - 1;
@@ -389,17 +363,30 @@ void compile_nc(Frag& f) {
         }
         for (int i = 0; i < 4; ++i) { o.m[2 * i] = (float)U[i].real(); o.m[2 * i + 1] = (float)U[i].imag(); }
       } else {
-        cd U[16], G[16], R[16];
+        // U <- G U gate by gate, as row operations on the 4x4 (index = bit_a + 2 bit_b)
+        cd U[16];
         for (int i = 0; i < 16; ++i) U[i] = (i % 5 == 0) ? 1.0 : 0.0;
         for (auto& g : F->word) {
-          gate_matrix_2(g[0], g[1], g[2] < 0 ? 1 - g[1] : g[2], G);
-          for (int i = 0; i < 4; ++i)
-            for (int j = 0; j < 4; ++j) {
-              cd s = 0;
-              for (int k = 0; k < 4; ++k) s += G[i * 4 + k] * U[k * 4 + j];
-              R[i * 4 + j] = s;
+          const int op = g[0], ra = g[1], rb = g[2] < 0 ? 1 - g[1] : g[2];
+          if (op == CCS_CX) {          // rows with control bit set: swap the target bit
+            for (int i = 0; i < 4; ++i)
+              if (((i >> ra) & 1) && !((i >> rb) & 1))
+                for (int j = 0; j < 4; ++j) std::swap(U[i * 4 + j], U[(i | (1 << rb)) * 4 + j]);
+          } else if (op == CCS_CZ) {   // row with both bits set: negate
+            for (int j = 0; j < 4; ++j) U[3 * 4 + j] = -U[3 * 4 + j];
+          } else {                     // one-qubit gate on role ra: mix row pairs
+            cd G[4];
+            gate_matrix_1q(op, G);
+            for (int i0 = 0; i0 < 4; ++i0) {
+              if ((i0 >> ra) & 1) continue;
+              const int i1 = i0 | (1 << ra);
+              for (int j = 0; j < 4; ++j) {
+                const cd u0 = U[i0 * 4 + j], u1 = U[i1 * 4 + j];
+                U[i0 * 4 + j] = G[0] * u0 + G[1] * u1;
+                U[i1 * 4 + j] = G[2] * u0 + G[3] * u1;
+              }
             }
-          for (int i = 0; i < 16; ++i) U[i] = R[i];
+          }
         }
         for (int i = 0; i < 16; ++i) { o.m[2 * i] = (float)U[i].real(); o.m[2 * i + 1] = (float)U[i].imag(); }
       }
