@@ -198,11 +198,11 @@ struct ccs_plan_s {
   std::vector<ProblemDev> pdev;
   DevPlan dp{};
   Allocs A;
-  long long n_spaces = 0, n_counts = 0, n_dist = 0, n_zval = 0, n_tab = 0, n_T = 0, n_TZ = 0, n_body = 0;
+  long long n_spaces = 0, n_counts = 0, n_dist = 0, n_zval = 0, n_tab = 0, n_T = 0, n_body = 0;
   long long n_zimg = 0;             // uint64 words of Z images
   long long n_pbasis = 0;           // uint32 words of projected shared-row bases
   long long n_marg = 0, n_zexp = 0;
-  std::vector<long long> t_prefix, tz_prefix, out_prefix, z_prefix, r_prefix, blk_prefix;
+  std::vector<long long> t_prefix, out_prefix, z_prefix, r_prefix, blk_prefix;
   std::vector<int2> direct_items;   // (problem, hub-output slice) contracted leaf by leaf
   int2* d_direct_items = nullptr;
   long long direct_stage_floats = 0;
@@ -214,7 +214,6 @@ struct ccs_plan_s {
   long long* d_s_prefix = nullptr;
   int max_tile_smem = 0;
   long long* d_t_prefix = nullptr;
-  long long* d_tz_prefix = nullptr;
   long long* d_out_prefix = nullptr;
   long long* d_z_prefix = nullptr;
   int cliff_smem_words = 0, max_nc_n = 1;
@@ -593,8 +592,6 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
     plan->n_zval += (long long)d.nv * d.nz * (1ll << d.qout);
     d.T_off = (plan->n_T + 63) & ~63ll;     // 256-byte aligned (TMA needs 16)
     plan->n_T = d.T_off + (1ll << d.m) * (1ll << (2 * d.n_slots));
-    d.TZ_off = plan->n_TZ;
-    plan->n_TZ += (long long)d.nz * (1ll << (2 * d.n_slots));
     plan->fdev.push_back(d);
   }
   {   // distributions: statevector fragments first (all a sampled evaluation needs), then Clifford
@@ -642,14 +639,12 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
 
   int f0 = 0;
   plan->t_prefix.push_back(0);
-  plan->tz_prefix.push_back(0);
   plan->out_prefix.push_back(0);
   plan->z_prefix.push_back(0);
   plan->r_prefix.push_back(0);
   plan->blk_prefix.push_back(0);
   for (auto& f : plan->fdev) {
     plan->t_prefix.push_back(plan->t_prefix.back() + (1ll << f.m) * (1ll << (2 * f.n_slots)));
-    plan->tz_prefix.push_back(plan->tz_prefix.back() + (long long)f.nz * (1ll << (2 * f.n_slots)));
   }
   // roles in star problems: the hub's contraction operand is Q, the others' T'
   {
@@ -687,17 +682,16 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
   // statevector fragments (side branch); T^S of every fragment; then the
   // contraction operands Q (hubs) and T' (the others)
   std::vector<int> fidx_c, fidx_nc, fidx_h, fidx_hn, fidx_o;
-  std::vector<long long> tp_c{0}, tzp_c{0}, tp_nc{0}, tzp_nc{0}, tp_h{0}, tp_hn{0}, tp_o{0};
-  std::vector<long long> zero_h{0}, zero_hn{0}, zero_o{0};
+  std::vector<long long> tp_c{0}, tp_nc{0}, tp_h{0}, tp_hn{0}, tp_o{0};
   for (int fi = 0; fi < (int)plan->fdev.size(); ++fi) {
     const FragDev& f = plan->fdev[fi];
-    const long long t = (1ll << f.m) * (1ll << (2 * f.n_slots)), tz = (long long)f.nz * (1ll << (2 * f.n_slots));
+    const long long t = (1ll << f.m) * (1ll << (2 * f.n_slots));
     const long long tf = f.role == 1 ? 0 : t;    // hubs: T only on request
-    if (f.clifford) { fidx_c.push_back(fi); tp_c.push_back(tp_c.back() + tf); tzp_c.push_back(tzp_c.back() + tz); }
-    else { fidx_nc.push_back(fi); tp_nc.push_back(tp_nc.back() + tf); tzp_nc.push_back(tzp_nc.back() + tz); }
-    if (f.role == 1) { fidx_h.push_back(fi); tp_h.push_back(tp_h.back() + t); zero_h.push_back(0); }
-    if (f.role == 1 && !f.clifford) { fidx_hn.push_back(fi); tp_hn.push_back(tp_hn.back() + t); zero_hn.push_back(0); }
-    if (f.role == 2) { fidx_o.push_back(fi); tp_o.push_back(tp_o.back() + t); zero_o.push_back(0); }
+    if (f.clifford) { fidx_c.push_back(fi); tp_c.push_back(tp_c.back() + tf); }
+    else { fidx_nc.push_back(fi); tp_nc.push_back(tp_nc.back() + tf); }
+    if (f.role == 1) { fidx_h.push_back(fi); tp_h.push_back(tp_h.back() + t); }
+    if (f.role == 1 && !f.clifford) { fidx_hn.push_back(fi); tp_hn.push_back(tp_hn.back() + t); }
+    if (f.role == 2) { fidx_o.push_back(fi); tp_o.push_back(tp_o.back() + t); }
   }
   for (auto& P : plan->problems) {
     ProblemDev d{};
@@ -796,21 +790,21 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
   for (int b = 0; b < 3; ++b) { basis[b] = basis_op(b); basis_matrix(b, &basism[8 * b]); }
 
   int *d_fidx_c, *d_fidx_nc, *d_fidx_h, *d_fidx_hn, *d_fidx_o;
-  long long *d_tp_c, *d_tzp_c, *d_tp_nc, *d_tzp_nc, *d_tp_h, *d_tp_hn, *d_tp_o, *d_zh, *d_zhn, *d_zo;
+  long long *d_tp_c, *d_tp_nc, *d_tp_h, *d_tp_hn, *d_tp_o;
   if (!c->host_only) {
     Staging st;
-    st.add(fidx_c, &d_fidx_c); st.add(fidx_nc, &d_fidx_nc); st.add(tp_c, &d_tp_c); st.add(tzp_c, &d_tzp_c);
-    st.add(tp_nc, &d_tp_nc); st.add(tzp_nc, &d_tzp_nc); st.add(fidx_h, &d_fidx_h); st.add(fidx_o, &d_fidx_o);
-    st.add(tp_h, &d_tp_h); st.add(tp_o, &d_tp_o); st.add(zero_h, &d_zh); st.add(zero_o, &d_zo);
-    st.add(fidx_hn, &d_fidx_hn); st.add(tp_hn, &d_tp_hn); st.add(zero_hn, &d_zhn);
+    st.add(fidx_c, &d_fidx_c); st.add(fidx_nc, &d_fidx_nc); st.add(tp_c, &d_tp_c);
+    st.add(tp_nc, &d_tp_nc); st.add(fidx_h, &d_fidx_h); st.add(fidx_o, &d_fidx_o);
+    st.add(tp_h, &d_tp_h); st.add(tp_o, &d_tp_o);
+    st.add(fidx_hn, &d_fidx_hn); st.add(tp_hn, &d_tp_hn);
     st.add(items_hub, &plan->d_items_hub); st.add(items_plain, &plan->d_items_plain);
     bool okf = st.commit(c, plan->A);
     if (!okf) { delete plan; return fail(c, CCS_ERR_OOM, "plan upload failed"); }
-    plan->fold_cliff = FoldSet{d_fidx_c, d_tp_c, d_tzp_c, (int)fidx_c.size(), tp_c.back(), tzp_c.back()};
-    plan->fold_nc = FoldSet{d_fidx_nc, d_tp_nc, d_tzp_nc, (int)fidx_nc.size(), tp_nc.back(), tzp_nc.back()};
-    plan->fold_hubs = FoldSet{d_fidx_h, d_tp_h, d_zh, (int)fidx_h.size(), tp_h.back(), 0};
-    plan->fold_hubs_nc = FoldSet{d_fidx_hn, d_tp_hn, d_zhn, (int)fidx_hn.size(), tp_hn.back(), 0};
-    plan->fold_others = FoldSet{d_fidx_o, d_tp_o, d_zo, (int)fidx_o.size(), tp_o.back(), 0};
+    plan->fold_cliff = FoldSet{d_fidx_c, d_tp_c, (int)fidx_c.size(), tp_c.back()};
+    plan->fold_nc = FoldSet{d_fidx_nc, d_tp_nc, (int)fidx_nc.size(), tp_nc.back()};
+    plan->fold_hubs = FoldSet{d_fidx_h, d_tp_h, (int)fidx_h.size(), tp_h.back()};
+    plan->fold_hubs_nc = FoldSet{d_fidx_hn, d_tp_hn, (int)fidx_hn.size(), tp_hn.back()};
+    plan->fold_others = FoldSet{d_fidx_o, d_tp_o, (int)fidx_o.size(), tp_o.back()};
   }
   if (c->host_only) {
     plan->dp.n_items_cliff = (int)items_c.size();
@@ -827,7 +821,7 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
   st.add(zoffs, &dzo); st.add(items_c, &dic); st.add(items_nc, &din); st.add(items_b, &dib);
   st.add(cliff_frags, &dcf); st.add(items_z, &diz); st.add(zblocks, &dzb); st.add(plan->pdev, &dpr); st.add(prep, &dpo); st.add(basis, &dbo);
   st.add(prepm, &dpm); st.add(basism, &dbm); st.add(plan->t_prefix, &plan->d_t_prefix);
-  st.add(plan->tz_prefix, &plan->d_tz_prefix); st.add(plan->out_prefix, &plan->d_out_prefix);
+  st.add(plan->out_prefix, &plan->d_out_prefix);
   st.add(plan->z_prefix, &plan->d_z_prefix); st.add(plan->r_prefix, &plan->d_r_prefix);
   st.add(plan->blk_prefix, &plan->d_blk_prefix); st.add(plan->direct_items, &plan->d_direct_items);
   bool ok = st.commit(c, plan->A);
@@ -1071,7 +1065,6 @@ int ccs_eval_variants(ccs_ctx c, ccs_plan p, const ccs_eval_opts* opts, ccs_res*
     d.zval = r->A.get<float>(std::max<long long>(p->n_zval, 1));
     d.T = r->A.get<float>(std::max<long long>(p->n_T, 1));
     d.TQ = r->A.get<float>(std::max<long long>(p->n_T, 1));
-    d.TZ = r->A.get<float>(std::max<long long>(p->n_TZ, 1));
     d.marg = r->A.get<double>(std::max<long long>(p->n_marg, 1));
     d.zexp = r->A.get<double>(std::max<long long>(p->n_zexp, 1));
     d.work = r->A.get<unsigned>(4 + (long long)p->dp.n_cliff_frags);   // + per-fragment record counters
@@ -1099,7 +1092,7 @@ int ccs_eval_variants(ccs_ctx c, ccs_plan p, const ccs_eval_opts* opts, ccs_res*
       d.TQh = r->A.get<uint16_t>(p->n_T);
       r->rt_scratch = r->A.get<uint16_t>(p->rt_total);
     }
-    if (!d.spaces || !d.dist || !d.zval || !d.T || !d.TQ || !d.TZ || !d.marg || !d.zexp || !d.work || !d.status ||
+    if (!d.spaces || !d.dist || !d.zval || !d.T || !d.TQ || !d.marg || !d.zexp || !d.work || !d.status ||
         !d.body || !d.rowbasis || !d.zimg || !d.fragcnt || !d.pbasis ||
         !r->scratch || (p->rt_total && (!d.TQh || !r->rt_scratch))) {
       delete r;
@@ -1429,15 +1422,15 @@ int ccs_get_tensor(ccs_ctx c, ccs_res r, int problem, int fragment, float* out) 
   if (d->role == 1) {   // a hub's T is not formed on the hot path: fold it now
     const int g = (int)(d - r->plan->fdev.data());
     std::vector<int> fi{g};
-    std::vector<long long> tp{0, cnt}, tz{0, 0};
+    std::vector<long long> tp{0, cnt};
     Allocs tmp;
     tmp.ctx = c;
-    int* dfi; long long *dtp, *dtz;
-    if (!upload(c, tmp, fi, &dfi) || !upload(c, tmp, tp, &dtp) || !upload(c, tmp, tz, &dtz)) {
+    int* dfi; long long* dtp;
+    if (!upload(c, tmp, fi, &dfi) || !upload(c, tmp, tp, &dtp)) {
       tmp.release();
       return fail(c, CCS_ERR_OOM, "tensor fold buffers");
     }
-    cudaError_t e2 = launch_fold(r->plan->dp, r->dr, r->ep, FoldSet{dfi, dtp, dtz, 1, cnt, 0}, c->stream);
+    cudaError_t e2 = launch_fold(r->plan->dp, r->dr, r->ep, FoldSet{dfi, dtp, 1, cnt}, c->stream);
     if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(c->stream);
     tmp.release();
     if (e2 != cudaSuccess) return cuda_fail(c, e2, "tensor fold");

@@ -28,7 +28,6 @@ struct FragDev {
   long long tab_off;       // uint64 index of variant 0 ((2n+3)*W each), -1 if not kept
   long long T_off;         // float index of T_f (2^m x 4^n_slots); also indexes TQ
   int role;                // 0 plain, 1 hub of a star (TQ = Q), 2 other fragment of a star (TQ = T')
-  long long TZ_off;        // float index of T_f^S (nz x 4^n_slots)
   long long body_off;      // uint64 index of the shared body tableau ((2n+3)*W words), Clifford only
   long long rb_off;        // uint64 index of the fragment's kRowBasisWords (shared-row basis + offset table)
   long long zimg_off;      // uint64 index of the Z images (nz + 3 qout + m records of 2 Wh + 1 words)
@@ -110,7 +109,6 @@ struct DevRes {
   float* T;
   float* TQ;               // contraction operands: Q for hubs, T' for the other fragments
   uint16_t* TQh;           // bf16 copy of the hubs' Q (tensor-core path), may be null
-  float* TZ;
   double* marg;
   double* zexp;
   unsigned int* work;         // persistent-kernel work counters
@@ -176,13 +174,12 @@ cudaError_t launch_sample_hub(const DevPlan& p, const DevRes& r, const EvalParam
 cudaError_t launch_statevector(const DevPlan& p, const DevRes& r, int max_n, int threads,
                                int grid, cudaStream_t s);
 // A subset of fragments to fold: fidx[i] is the FragDev index of segment i;
-// t_prefix / tz_prefix (nf + 1 entries) count T_f and T_f^S entries.
+// t_prefix (nf + 1 entries) counts T_f entries.
 struct FoldSet {
   const int* fidx;
   const long long* t_prefix;
-  const long long* tz_prefix;
   int nf;
-  long long total, total_z;
+  long long total;
 };
 cudaError_t launch_fold(const DevPlan& p, const DevRes& r, const EvalParams& e, const FoldSet& f,
                         cudaStream_t s);

@@ -203,35 +203,6 @@ __global__ void prime_kernel(DevPlan P, DevRes R, const int* fidx, const long lo
   }
 }
 
-__global__ void fold_z_kernel(DevPlan P, DevRes R, const int* fidx, const long long* prefix, int nf,
-                              long long total) {
-  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
-       g += (long long)gridDim.x * blockDim.x) {
-    const int fs = find_seg(prefix, nf, g);
-    const FragDev& F = P.frags[fidx[fs]];
-    const long long loc = g - prefix[fs];
-    const int S2 = 2 * F.n_slots;
-    const int zi = (int)(loc >> S2), Pi = (int)(loc & ((1ll << S2) - 1));
-    PauliSplit ps;
-    split_P(F, Pi, ps);
-    int vout = 0, mul = 1, u = 0;
-    for (int j = 0; j < F.qout; ++j) {
-      const int beta = ps.pout[j] == 1 ? 0 : ps.pout[j] == 2 ? 1 : 2;
-      vout += beta * mul;
-      mul *= 3;
-      if (ps.pout[j] != 0) u |= 1 << j;
-    }
-    int vstride = 1;
-    for (int i = 0; i < F.qin; ++i) vstride *= 4;
-    double acc = 0.0;
-    for_each_prep(F, ps, [&](int vin, double coef) {
-      const long long v = vin + (long long)vstride * vout;
-      acc += coef * (double)R.zval[F.zval_off + (v * F.nz + zi) * (1 << F.qout) + u];
-    });
-    R.TZ[F.TZ_off + loc] = (float)acc;
-  }
-}
-
 cudaError_t launch_operands(const DevPlan& p, const DevRes& r, const EvalParams& e, const FoldSet& hubs,
                             const FoldSet& others, cudaStream_t s) {
   if (hubs.total > 0) {
@@ -447,7 +418,7 @@ struct ProblemShared {
   int m[kMaxProblemFrags], ns[kMaxProblemFrags];
   int slot_cut[kMaxProblemFrags][kMaxCuts];
   int marg_pos[kMaxProblemFrags][kMaxMarginal];
-  long long T_off[kMaxProblemFrags], TZ_off[kMaxProblemFrags];
+  long long T_off[kMaxProblemFrags];
 };
 
 __device__ void load_problem(const DevPlan& P, const ProblemDev& Pb, ProblemShared& S) {
@@ -458,7 +429,6 @@ __device__ void load_problem(const DevPlan& P, const ProblemDev& Pb, ProblemShar
     S.m[t] = L.m;
     S.ns[t] = L.n_slots;
     S.T_off[t] = L.T_off;
-    S.TZ_off[t] = L.TZ_off;
     for (int i = 0; i < L.n_slots; ++i) S.slot_cut[t][i] = L.slot_cut[i];
     for (int j = 0; j < L.m; ++j) S.marg_pos[t][j] = L.marg_pos[j];
   }
@@ -471,21 +441,62 @@ __device__ __forceinline__ int frag_digits(const ProblemShared& S, int l, long l
   return pl;
 }
 
+// T_f^S(zi, P) folded from the variants' Z-string values the way T_f is
+// folded from their distributions: the preparation tuples of P's input
+// Paulis (weights mu) at the output bases of P's output Paulis, each taking
+// the value of Z_S times the observables of the outputs whose Pauli is not I.
+__device__ float fold_z_value(const DevRes& R, const FragDev& F, int zi, int Pi) {
+  PauliSplit ps;
+  split_P(F, Pi, ps);
+  int vout = 0, mul = 1, u = 0;
+  for (int j = 0; j < F.qout; ++j) {
+    const int beta = ps.pout[j] == 1 ? 0 : ps.pout[j] == 2 ? 1 : 2;
+    vout += beta * mul;
+    mul *= 3;
+    if (ps.pout[j] != 0) u |= 1 << j;
+  }
+  int vstride = 1;
+  for (int i = 0; i < F.qin; ++i) vstride *= 4;
+  double acc = 0.0;
+  for_each_prep(F, ps, [&](int vin, double coef) {
+    const long long v = vin + (long long)vstride * vout;
+    acc += coef * (double)R.zval[F.zval_off + (v * F.nz + zi) * (1 << F.qout) + u];
+  });
+  return (float)acc;
+}
+
 // <Z_S> = 2^-k sum_P prod_f T_f^S(P|f): one block per (problem, string),
-// FP32 products, FP64 sums, fixed-order tree reduction.
+// FP32 products, FP64 sums, fixed-order tree reduction; T_f^S is folded from
+// the variants' Z values here (no separate fold pass).
 __device__ void z_string_block(const DevPlan& P, const DevRes& R, const long long* prefix, int np, long long g,
-                               ProblemShared& S, double* red, double* zexp_out) {
+                               ProblemShared& S, double* red, float* s_tz, int tz_cap, double* zexp_out) {
   const int pi = find_seg(prefix, np, g);
   const ProblemDev& Pb = P.problems[pi];
   const int zi = (int)(g - prefix[pi]);
   load_problem(P, Pb, S);
   __syncthreads();
+  // every fragment's T_f^S(zi, .) folded once into shared memory when it fits
+  int tz_tot = 0;
+  for (int l = 0; l < S.nf; ++l) tz_tot += 1 << (2 * S.ns[l]);
+  const bool staged = tz_tot <= tz_cap;
+  if (staged) {
+    for (int i = threadIdx.x; i < tz_tot; i += blockDim.x) {
+      int l = 0, o = 0;
+      while (i >= o + (1 << (2 * S.ns[l]))) { o += 1 << (2 * S.ns[l]); ++l; }
+      s_tz[i] = fold_z_value(R, P.frags[Pb.frag0 + l], zi, i - o);
+    }
+    __syncthreads();
+  }
   const long long K = 1ll << (2 * S.k);
   double part = 0.0;
   for (long long Pp = threadIdx.x; Pp < K; Pp += blockDim.x) {
     float t = 1.f;
-    for (int l = 0; l < S.nf; ++l)
-      t *= R.TZ[S.TZ_off[l] + ((long long)zi << (2 * S.ns[l])) + frag_digits(S, l, Pp)];
+    int o = 0;
+    for (int l = 0; l < S.nf; ++l) {
+      const int pl = frag_digits(S, l, Pp);
+      t *= staged ? s_tz[o + pl] : fold_z_value(R, P.frags[Pb.frag0 + l], zi, pl);
+      o += 1 << (2 * S.ns[l]);
+    }
     part += (double)t;
   }
   red[threadIdx.x] = part;
@@ -522,7 +533,7 @@ __global__ void __launch_bounds__(512) contract_kernel(DevPlan P, DevRes R, int 
   __shared__ float s_T[kLeafStage];
   for (long long b = blockIdx.x; b < n_direct + z_total; b += gridDim.x) {
     if (b >= n_direct) {
-      z_string_block(P, R, z_prefix, np, b - n_direct, S, red, zexp_out);
+      z_string_block(P, R, z_prefix, np, b - n_direct, S, red, s_T, kLeafStage, zexp_out);
       __syncthreads();
       continue;
     }
@@ -668,18 +679,10 @@ __global__ void __launch_bounds__(512) contract_kernel(DevPlan P, DevRes R, int 
 
 cudaError_t launch_fold(const DevPlan& p, const DevRes& r, const EvalParams& e, const FoldSet& f,
                         cudaStream_t s) {
-  if (f.total > 0) {
-    const long long blocks = (f.total + 255) / 256;
-    fold_kernel<<<(unsigned)(blocks < 65535 * 8 ? blocks : 65535 * 8), 256, 0, s>>>(p, r, e, f.fidx, f.t_prefix,
-                                                                              f.nf, f.total); note_launch();
-    cudaError_t err = cudaGetLastError();
-    if (err != cudaSuccess) return err;
-  }
-  if (f.total_z > 0) {
-    const long long blocks = (f.total_z + 255) / 256;
-    fold_z_kernel<<<(unsigned)(blocks < 65535 * 8 ? blocks : 65535 * 8), 256, 0, s>>>(p, r, f.fidx, f.tz_prefix,
-                                                                                f.nf, f.total_z); note_launch();
-  }
+  if (f.total == 0) return cudaSuccess;
+  const long long blocks = (f.total + 255) / 256;
+  fold_kernel<<<(unsigned)(blocks < 65535 * 8 ? blocks : 65535 * 8), 256, 0, s>>>(p, r, e, f.fidx, f.t_prefix, f.nf,
+                                                                            f.total); note_launch();
   return cudaGetLastError();
 }
 
