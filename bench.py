@@ -306,15 +306,18 @@ def stage_rooflines(stage, w, ws, prob_infos, pk, pk_kind, precision):
 
     clifford    alu: body evolution, once per Clifford fragment: 140 lane ops
                 per fused op and 64-row word (4x4 GF(2) map + sign polynomial
-                on 64-bit words); per variant, either the rank screen
+                on 64-bit words); Z-image records, once per fragment: the
+                ordered row product over n columns x W words, 25 lane ops per
+                word, for nz + 3 qout + m records; per variant the screen
                 (elimination of n_meas + n_qout + n_qin vectors over n_meas
-                bits, 4 lane ops per vector-bit) or, for problems with
-                Z-strings, the tableau kernel: copy of the (2n+3)W body words
-                plus 8 lane ops per word per Z-string evaluation
-    sample      alu: 25 lane ops per shot (a quarter of one Philox4x32-10 call:
-                10 rounds x 6 ops / 4, + mask, 3 table lookups, 2 xors, atomic)
-                and, for a star's hub, 60 lane ops per output (packed counter
-                loads, 16-point Walsh-Hadamard transform, operand stores)
+                bits, 4 lane ops per vector-bit) and its Z-string values (per
+                string and output subset, ~2 image factors x Wh words x 6 ops)
+    sample      alu: per shot a 1/(4 s) share of one Philox4x32-10 call (60
+                lane ops; s = 4, 2, 1 shots per output word at |A| <= 8, 16,
+                above), 3 lane ops per table lookup (L = 1, 2, 3 lookups) and
+                4 for the field, index and atomic; for a star's hub 35 lane ops
+                per output (packed counter loads, the 16-point Walsh-Hadamard
+                transform on paired 16-bit lanes, operand stores)
     statevector alu: a fused 4x4 complex op costs 32 FP32 flops per amplitude
     fold, operands, recombine
                 hbm: fold/operands: variant data read once and fragment
@@ -334,17 +337,18 @@ def stage_rooflines(stage, w, ws, prob_infos, pk, pk_kind, precision):
                     if not i["clifford"]:
                         continue
                     W = 2 * ((i["n_wires"] + 63) // 64)
+                    nz = len(x.zstrings)
                     if st == "clifford":
                         ops += i["n_ops"] * W * 140
-                        if x.zstrings:
-                            ops += i["n_variants"] * ((2 * i["n_wires"] + 3) * W +
-                                                      8 * W * len(x.zstrings) * (1 << i["n_qout"]))
-                        else:
-                            ops += i["n_variants"] * (i["n_meas"] + i["n_qout"] + i["n_qin"]) * i["n_meas"] * 4
+                        ops += (nz + 3 * i["n_qout"] + i["n_marg"]) * i["n_wires"] * W * 25
+                        ops += i["n_variants"] * (i["n_meas"] + i["n_qout"] + i["n_qin"]) * i["n_meas"] * 4
+                        ops += i["n_variants"] * nz * (1 << i["n_qout"]) * 2 * (W // 2) * 6
                     else:
-                        ops += i["n_variants"] * x.shots * 25
+                        per_word = 4 if i["n_meas"] <= 8 else 2 if i["n_meas"] <= 16 else 1
+                        lookups = 1 if i["n_meas"] <= 8 else 2 if i["n_meas"] <= 16 else 3
+                        ops += i["n_variants"] * x.shots * (60 / (4 * per_word) + 3 * lookups + 4)
                         if i["n_slots"] == len(x.cuts):   # hub of the star (one slot per cut)
-                            ops += i["n_variants"] * (1 << i["n_marg"]) * 60
+                            ops += i["n_variants"] * (1 << i["n_marg"]) * 35
             out[st] = {"bound": "alu", "achieved": ops / t / 1e12, "peak": lanes / 1e12, "unit": "T lane-op/s",
                        "peak_source": f"derived: {N_SM} SMs x 128 lanes x {clk/1e6:.0f} MHz"}
         elif st == "statevector":
