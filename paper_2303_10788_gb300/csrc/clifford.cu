@@ -1236,12 +1236,25 @@ __device__ __forceinline__ void hub_pair_out(int (&a)[16], int (&c)[16], int* wh
         make_float2((float)wht[sm] * inv, (float)wht[16 + sm] * inv);
   }
 }
-// Byte-counter variant of hub_pair_out: p[b] holds the counts of outputs o
-// and o+1 for basis outcome b as two 16-bit lanes; the 16-point transform
-// runs on both lanes at once (|sums| <= 16 * 255 fit in 16 bits).
-__device__ __forceinline__ void hub_pair_out_packed(unsigned (&p)[16], unsigned* wht, const int* s_czD,
-                                                    const int* s_czS, int nz, float* QT, int M, int o,
-                                                    float inv) {
+// Register select p[i] for a CTA-uniform index (a binary tree of selects).
+__device__ __forceinline__ unsigned pick16(const unsigned (&p)[16], int i) {
+  unsigned a[8], b[4], c[2];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = (i & 1) ? p[2 * k + 1] : p[2 * k];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) b[k] = (i & 2) ? a[2 * k + 1] : a[2 * k];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) c[k] = (i & 4) ? b[2 * k + 1] : b[2 * k];
+  return (i & 8) ? c[1] : c[0];
+}
+
+// Packed variant of hub_pair_out: p[b] holds the counts of outputs o and o+1
+// for basis outcome b as two 16-bit lanes; the 16-point transform runs on
+// both lanes at once (an output's bins sum to at most the shots, so every
+// transform value fits a signed 16-bit lane below 32768 shots), and the
+// variant's sign masks pick from registers (no shared-memory scratch).
+__device__ __forceinline__ void hub_pair_out_packed(unsigned (&p)[16], const int* s_czD, const int* s_czS, int nz,
+                                                    float* QT, int M, int o, float inv) {
 #pragma unroll
   for (int h = 1; h < 16; h <<= 1)
 #pragma unroll
@@ -1251,10 +1264,8 @@ __device__ __forceinline__ void hub_pair_out_packed(unsigned (&p)[16], unsigned*
         p[b] = __vadd2(x, y);
         p[b | h] = __vsub2(x, y);
       }
-#pragma unroll
-  for (int b = 0; b < 16; ++b) wht[b] = p[b];
   for (int cz = 0; cz < (1 << nz); ++cz) {
-    const unsigned w = wht[s_czS[cz]];
+    const unsigned w = pick16(p, s_czS[cz]);
     const int lo = (int)(short)(w & 0xffffu), hi = (int)(short)(w >> 16);
     *reinterpret_cast<float2*>(QT + (long long)s_czD[cz] * M + o) = make_float2((float)lo * inv, (float)hi * inv);
   }
@@ -1348,8 +1359,9 @@ __global__ void __launch_bounds__(512) sample_hub_kernel(DevPlan P, DevRes R, Ev
     // Pairs of outputs (o, o+1) share the packed counter words.  Per pair,
     // a 16-point Walsh-Hadamard transform over the output bits gives the
     // signed sum for every sign mask at once; each thread parks it in its
-    // own slot after the histogram (17 words packed, 33 unpacked: odd
-    // strides, no bank conflicts) and picks the variant's masks.
+    // own 33-word slot after the histogram (odd stride: no bank conflicts)
+    // and picks the variant's masks; below 32768 shots the transform runs
+    // on packed lanes and picks from registers, with no slot.
     if ((int)threadIdx.x < (1 << nz)) {
       int D = Dbase, smask = fixed_mask;
       for (int i = 0; i < nz; ++i)
@@ -1358,7 +1370,7 @@ __global__ void __launch_bounds__(512) sample_hub_kernel(DevPlan P, DevRes R, Ev
       s_czS[threadIdx.x] = smask;
     }
     __syncthreads();
-    int* wht = reinterpret_cast<int*>(hist2 + hist_words) + threadIdx.x * (E.shots <= 32767u ? 17 : 33);
+    int* wht = reinterpret_cast<int*>(hist2 + hist_words) + threadIdx.x * (E.shots <= 32767u ? 0 : 33);
     if (E.shots <= 32767u) {
       // an output's bins sum to at most the shots, so every transform value
       // fits a signed 16-bit lane: the counter word (outputs o, o+1) is
@@ -1368,7 +1380,7 @@ __global__ void __launch_bounds__(512) sample_hub_kernel(DevPlan P, DevRes R, Ev
         unsigned pk[16];
 #pragma unroll
         for (int b = 0; b < 16; ++b) pk[b] = b < nb ? hist2[((uint32_t)o | ((uint32_t)b << m)) >> 1] : 0u;
-        hub_pair_out_packed(pk, reinterpret_cast<unsigned*>(wht), s_czD, s_czS, nz, QT, M, o, inv);
+        hub_pair_out_packed(pk, s_czD, s_czS, nz, QT, M, o, inv);
       }
     } else
     for (int o2 = threadIdx.x; o2 < (M >> 1); o2 += blockDim.x) {
@@ -1497,7 +1509,7 @@ __global__ void __launch_bounds__(256) sample_hub8_kernel(DevPlan P, DevRes R, E
   const uint32_t cmask = rank >= 32 ? 0xffffffffu : ((1u << rank) - 1u);
   const float inv = (float)E.inv_shots;
   float* QT = R.TQ + F.T_off;
-  const int wstride = E.shots <= 32767u ? 17 : 33;   // packed transforms need 16 words, unpacked 32
+  const int wstride = E.shots <= 32767u ? 0 : 33;    // only the unpacked transform parks values
   int* wht = reinterpret_cast<int*>(h32 + hist_words) + tid * wstride;
   uint32_t* gcount = R.counts + F.counts_off + ((long long)v << nA);
   bool narrow = (unsigned long long)E.shots <= (64ull << rank);
@@ -1522,7 +1534,6 @@ __global__ void __launch_bounds__(256) sample_hub8_kernel(DevPlan P, DevRes R, E
     if (narrow) {
       if (keep_counts)
         for (uint32_t y = tid; y < (1u << nA); y += nt) gcount[y] = (h32[y >> 2] >> ((y & 3u) << 3)) & 0xffu;
-      unsigned* pw = reinterpret_cast<unsigned*>(wht);
       for (int q = tid; q < (M >> 2); q += nt) {       // outputs o..o+3 share a counter word
         const int o = 4 * q;
         uint32_t w[16];
@@ -1533,7 +1544,7 @@ __global__ void __launch_bounds__(256) sample_hub8_kernel(DevPlan P, DevRes R, E
           unsigned pk[16];    // outputs o + 2 half and o + 2 half + 1 as 16-bit lanes
 #pragma unroll
           for (int b = 0; b < 16; ++b) pk[b] = __byte_perm(w[b], 0u, half ? 0x4342 : 0x4140);
-          hub_pair_out_packed(pk, pw, s_czD, s_czS, nz, QT, M, o + 2 * half, inv);
+          hub_pair_out_packed(pk, s_czD, s_czS, nz, QT, M, o + 2 * half, inv);
         }
       }
     }
@@ -1562,11 +1573,11 @@ __global__ void __launch_bounds__(256) sample_hub8_kernel(DevPlan P, DevRes R, E
         }
       for (int o2 = tid; o2 < (Mh >> 1); o2 += nt) {    // pairs of outputs within the half
         const int ol = 2 * o2;
-        if (wstride == 17) {                   // an output's bins sum to at most the shots
+        if (wstride == 0) {                    // an output's bins sum to at most the shots
           unsigned pk[16];
 #pragma unroll
           for (int b = 0; b < 16; ++b) pk[b] = b < nb ? h32[((uint32_t)ol | ((uint32_t)b << mh)) >> 1] : 0u;
-          hub_pair_out_packed(pk, reinterpret_cast<unsigned*>(wht), s_czD, s_czS, nz, QT, M, h * Mh + ol, inv);
+          hub_pair_out_packed(pk, s_czD, s_czS, nz, QT, M, h * Mh + ol, inv);
           continue;
         }
         int a[16], c[16];
@@ -1587,7 +1598,7 @@ cudaError_t launch_sample_hub(const DevPlan& p, const DevRes& r, const EvalParam
   if (n_items == 0 || e.shots == 0) return cudaSuccess;
   if (bytes_ok && e.shots <= 0xffffu && max_nA >= 2 && max_nA <= 16) {   // byte counters, 256 threads
     const int hist_words = (1 << max_nA) / 4;
-    const size_t smem = (size_t)4 * hist_words + (size_t)256 * (e.shots <= 32767u ? 17 : 33) * 4;
+    const size_t smem = (size_t)4 * hist_words + (size_t)256 * (e.shots <= 32767u ? 0 : 33) * 4;
     cudaError_t err = cudaFuncSetAttribute(sample_hub8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     sample_hub8_kernel<<<n_items, 256, smem, s>>>(p, r, e, items, keep_counts, hist_words); note_launch();
@@ -1597,7 +1608,7 @@ cudaError_t launch_sample_hub(const DevPlan& p, const DevRes& r, const EvalParam
   const int hist_words = wide ? (1 << max_nA) : ((1 << max_nA) > 1 ? (1 << (max_nA - 1)) : 1);
   // packed counters, then 33 ints per thread for the transform of the 16-bit path
   threads = threads >= 512 ? 512 : threads >= 256 ? 256 : 128;
-  const size_t smem = (size_t)4 * hist_words + (wide ? 0 : (size_t)threads * (e.shots <= 32767u ? 17 : 33) * 4);
+  const size_t smem = (size_t)4 * hist_words + (wide ? 0 : (size_t)threads * (e.shots <= 32767u ? 0 : 33) * 4);
   cudaError_t err = cudaFuncSetAttribute(sample_hub_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   sample_hub_kernel<<<n_items, threads, smem, s>>>(p, r, e, items, keep_counts, wide, hist_words); note_launch();
