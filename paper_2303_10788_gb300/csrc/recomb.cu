@@ -226,11 +226,12 @@ cudaError_t launch_operands(const DevPlan& p, const DevRes& r, const EvalParams&
 // For a star (hub h + leaves), p(o) = 2^-k sum_P T_h[o_h, P] R[P, o_l] with
 // R[P, o_l] = prod_leaves T_l[o_l|l, P|l] (leaf outputs concatenated in
 // fragment order; cut-free fragments contribute their P-independent factor).
-// R is built once (it is the GEMM's B operand), then a tiled GEMM with split-K
-// writes FP32 partial tiles, and the partials are summed in FP64 in a fixed
-// order, scaled by 2^-k and scattered to marginal order.  BF16 mode rounds
-// both operands to bf16 (as a bf16 tensor-core GEMM would) with FP32
-// accumulation.
+// Stars that contract_kernel does not take leaf by leaf (the tensor-core path
+// and stars too wide for a slice) go through the GEMM chain: R is built once
+// (it is the GEMM's B operand), then a tiled GEMM with split-K writes FP32
+// partial tiles, and the partials are summed in FP64 in a fixed order, scaled
+// by 2^-k and scattered to marginal order.  BF16 mode rounds both operands to
+// bf16 (as a bf16 tensor-core GEMM would) with FP32 accumulation.
 
 __global__ void build_r_kernel(DevPlan P, DevRes R, int precision, const long long* prefix, int np,
                                long long total, float* scratch, uint16_t* rt_scratch) {
@@ -374,7 +375,7 @@ __global__ void reduce_scatter_kernel(DevPlan P, const long long* prefix, int np
        g += (long long)gridDim.x * blockDim.x) {
     const int pi = find_seg(prefix, np, g);
     const ProblemDev& Pb = P.problems[pi];
-    if (Pb.direct) continue;                  // written by the one-pass contraction
+    if (Pb.direct) continue;                  // written by the leaf-by-leaf contraction
     const long long loc = g - prefix[pi];
     const long long m = loc / Pb.N, n = loc - m * Pb.N;
     double acc = 0.0;
@@ -391,22 +392,6 @@ __global__ void reduce_scatter_kernel(DevPlan P, const long long* prefix, int np
     }
     marg_out[Pb.marg_off + o] = ldexp(acc, -Pb.k);
   }
-}
-
-// Marginal index of output (m, n) of a star: hub bits, then the leaves' bits
-// in fragment order.
-__device__ __forceinline__ long long scatter_index(const DevPlan& P, const ProblemDev& Pb, long long m, long long n) {
-  long long o = 0;
-  const FragDev& Hb = P.frags[Pb.frag0 + Pb.hub];
-  for (int j = 0; j < Hb.m; ++j) o |= ((m >> j) & 1) << Hb.marg_pos[j];
-  int off = 0;
-  for (int l = 0; l < Pb.n_frags; ++l) {
-    if (l == Pb.hub) continue;
-    const FragDev& L = P.frags[Pb.frag0 + l];
-    for (int j = 0; j < L.m; ++j) o |= ((n >> (off + j)) & 1) << L.marg_pos[j];
-    off += L.m;
-  }
-  return o;
 }
 
 // Fragment descriptors of one problem, read once into shared memory so that
