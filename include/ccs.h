@@ -185,10 +185,17 @@ typedef struct {
 /* Evaluate every variant of every fragment of the plan on the GPU: tableau
  * evolution, GF(2) reduction to the affine outcome space, Philox sampling
  * (Clifford) or complex64 statevectors (non-Clifford), then the fold of the
- * variant data into one tensor per fragment.  Shot s of variant v of
- * fragment f of problem c uses Philox counter (s, v, f, c).  If *res is NULL
- * a result is created, else its buffers are reused (same plan only).  The
- * call is asynchronous on the context stream; getters synchronise. */
+ * variant data into one tensor per fragment.  By default each Clifford
+ * fragment's gates are evolved once (the body) and every variant's outcome
+ * space and Z-string values follow from the body without a tableau per
+ * variant; with keep_tableaus each variant's final tableau is formed too
+ * (same results bit for bit).  Philox call (g, v, f, c) (counter words:
+ * call index, variant, fragment, problem) yields four 32-bit words of the
+ * variant's stream; shot t takes field t mod s of word t div s, s = 4 / 2 / 1
+ * shots per word when the space's rank is <= 8 / <= 16 / above, and uses the
+ * field's low rank bits.  If *res is NULL a result is created, else its
+ * buffers are reused (same plan only).  The call is asynchronous on the
+ * context stream; getters synchronise. */
 int ccs_eval_variants(ccs_ctx ctx, ccs_plan plan, const ccs_eval_opts* opts, ccs_res* res);
 void ccs_res_free(ccs_res res);
 /* Launch shape in use for a result (after autotuning, if any): threads per
