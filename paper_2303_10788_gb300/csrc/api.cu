@@ -606,12 +606,24 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
     delete plan;
     return fail(c, CCS_ERR_UNSUPPORTED, "Clifford fragment does not fit in shared memory");
   }
+  // Items costliest first, ties in insertion order.  A fragment's items are
+  // consecutive and cost the same, so the runs of equal cost are sorted
+  // stably instead of the items (the same order, far fewer comparisons).
   auto sort_items = [](std::vector<int2>& it, std::vector<long long>& cost) {
-    std::vector<size_t> idx(it.size());
-    for (size_t i = 0; i < idx.size(); ++i) idx[i] = i;
-    std::stable_sort(idx.begin(), idx.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
-    std::vector<int2> out(it.size());
-    for (size_t i = 0; i < idx.size(); ++i) out[i] = it[idx[i]];
+    std::vector<std::pair<size_t, size_t>> runs;
+    for (size_t i = 0; i < it.size();) {
+      size_t j = i + 1;
+      while (j < it.size() && cost[j] == cost[i]) ++j;
+      runs.push_back({i, j});
+      i = j;
+    }
+    std::stable_sort(runs.begin(), runs.end(),
+                     [&](const std::pair<size_t, size_t>& a, const std::pair<size_t, size_t>& b) {
+                       return cost[a.first] > cost[b.first];
+                     });
+    std::vector<int2> out;
+    out.reserve(it.size());
+    for (auto& r : runs) out.insert(out.end(), it.begin() + r.first, it.begin() + r.second);
     it.swap(out);
   };
   sort_items(items_c, cost_c);

@@ -56,25 +56,24 @@ void chp_planes(int op, int ra, int rb, uint32_t x[2], uint32_t z[2], uint32_t& 
 // Identity planes: pattern v has x_a = bit 0, z_a = bit 1, x_b = bit 2, z_b = bit 3 of v.
 constexpr uint32_t kPX0 = 0xaaaau, kPX1 = 0xf0f0u, kPZ0 = 0xccccu, kPZ1 = 0xff00u;
 
-// (M, anf) of the Clifford update given by its 16-pattern planes.
+// (M, anf) of the Clifford update given by its 16-pattern planes: column j
+// of M is the image of the unit pattern 1 << j (bit i of plane i at that
+// pattern), and the sign polynomial's algebraic normal form is the Moebius
+// transform of the 16-entry flip truth table (a[s] = XOR of f[t], t a subset
+// of s), done on the 16-bit word one variable at a time.
 CliffordOp clifford_from_planes(const uint32_t x[2], const uint32_t z[2], uint32_t flip) {
-  int u[16], f[16];
-  for (int v = 0; v < 16; ++v) {
-    u[v] = (int)(((x[0] >> v) & 1u) | (((z[0] >> v) & 1u) << 1) | (((x[1] >> v) & 1u) << 2) |
-                 (((z[1] >> v) & 1u) << 3));
-    f[v] = (int)((flip >> v) & 1u);
-  }
   CliffordOp op{0, 0, 0, 0};
-  for (int j = 0; j < 4; ++j)
-    for (int i = 0; i < 4; ++i)
-      if ((u[1 << j] >> i) & 1) op.M |= (uint16_t)(1u << (4 * i + j));
-  int a[16];
-  for (int s = 0; s < 16; ++s) a[s] = f[s];
+  const uint32_t planes[4] = {x[0], z[0], x[1], z[1]};
+  uint32_t M = 0;
   for (int i = 0; i < 4; ++i)
-    for (int s = 0; s < 16; ++s)
-      if (s & (1 << i)) a[s] ^= a[s ^ (1 << i)];
-  for (int s = 0; s < 16; ++s)
-    if (a[s]) op.anf |= (uint16_t)(1u << s);
+    for (int j = 0; j < 4; ++j) M |= ((planes[i] >> (1u << j)) & 1u) << (4 * i + j);
+  op.M = (uint16_t)M;
+  uint32_t a = flip & 0xffffu;
+  a ^= (a << 1) & 0xaaaau;
+  a ^= (a << 2) & 0xccccu;
+  a ^= (a << 4) & 0xf0f0u;
+  a ^= (a << 8) & 0xff00u;
+  op.anf = (uint16_t)a;
   return op;
 }
 
