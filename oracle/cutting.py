@@ -37,7 +37,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from workloads import H, S, SDG, X, Y, Z, CX, CZ, T, TDG, NQ
+from workloads import H, S, SDG, X, Y, Z, CX, CZ, T, TDG, ZPOW, NQ, gate_param
 
 PREP_GATES = {0: [], 1: [X], 2: [H], 3: [H, S]}          # |0>,|1>,|+>,|+i>
 BASIS_GATES = {0: [H], 1: [SDG, H], 2: []}               # X, Y, Z
@@ -52,7 +52,7 @@ BETA = [2, 0, 1, 2]                                       # basis of P: I->Z, X,
 @dataclass
 class Fragment:
     wires: list                  # (qubit, segment)
-    gates: list                  # (op, a, b) on local wires
+    gates: list                  # (op, a, b) or (ZPOW, a, -1, exponent) on local wires
     qin: list                    # (cut id, local wire), cut order
     qout: list                   # (cut id, local wire), cut order
     marg: list                   # (marginal position, local wire), marginal order
@@ -90,6 +90,17 @@ class Fragment:
         return g
 
 
+def is_clifford_gate(g):
+    """T and T^dagger are not Clifford; Z^a is Clifford exactly when 2a is an
+    integer (then Z^a = S^{2a}, Sec. II-C); every other opcode is."""
+    if g[0] in (T, TDG):
+        return False
+    if g[0] == ZPOW:
+        k = 2.0 * gate_param(g)
+        return k == np.floor(k)
+    return True
+
+
 def canonical_cuts(cuts):
     cs = sorted({(int(q), int(g)) for q, g in cuts}, key=lambda c: (c[1], c[0]))
     return cs
@@ -114,7 +125,8 @@ def fragment_circuit(circuit, cuts, marginal):
             s = parent[s]
         return s
 
-    for gi, (op, a, b) in enumerate(gates):
+    for gi, g in enumerate(gates):
+        op, a, b = g[:3]
         if NQ[op] == 2:
             ra, rb = find((a, seg(a, gi))), find((b, seg(b, gi)))
             if ra != rb:
@@ -130,15 +142,16 @@ def fragment_circuit(circuit, cuts, marginal):
         for li, s in enumerate(wires):
             where[s] = (fi, li)
         frags.append(Fragment(wires, [], [], [], []))
-    for gi, (op, a, b) in enumerate(gates):
+    for gi, g in enumerate(gates):
+        op, a, b = g[:3]
         fa, la = where[(a, seg(a, gi))]
         if NQ[op] == 2:
             fb, lb = where[(b, seg(b, gi))]
             assert fa == fb
             frags[fa].gates.append((op, la, lb))
         else:
-            frags[fa].gates.append((op, la, -1))
-            if op in (T, TDG):
+            frags[fa].gates.append((op, la, -1) + tuple(g[3:]))
+            if not is_clifford_gate(g):
                 frags[fa].clifford = False
     for ci, (q, g) in enumerate(cuts):
         k = pos[q].index(g) + 1

@@ -20,7 +20,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from workloads import H, S, SDG, X, Y, Z, CX, CZ, T, TDG
+from workloads import H, S, SDG, X, Y, Z, CX, CZ, T, TDG, ZPOW, gate_param
 
 
 class Tableau:
@@ -79,8 +79,16 @@ class Tableau:
         self.z[:, a] = za ^ xb
         self.z[:, b] = zb ^ xa
 
-    def apply(self, op, a, b=-1):
-        if op == H:
+    def apply(self, op, a, b=-1, param=0.0):
+        if op == ZPOW:
+            # Z^a = (Z^{1/2})^{2a} = S^{2a}: Clifford exactly when 2a is an
+            # integer (e^{i pi a} in {1, i, -1, -i}), Sec. II-C
+            k = 2.0 * param
+            if k != np.floor(k):
+                raise ValueError("Z^a with 2a not an integer is not a Clifford gate")
+            for _ in range(int(k) % 4):
+                self.s(a)
+        elif op == H:
             self.h(a)
         elif op == S:
             self.s(a)
@@ -102,8 +110,8 @@ class Tableau:
             raise ValueError(f"unknown gate {op}")
 
     def run(self, gates):
-        for op, a, b in gates:
-            self.apply(op, a, b)
+        for g in gates:
+            self.apply(g[0], g[1], g[2], gate_param(g))
         return self
 
 

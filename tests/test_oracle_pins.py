@@ -9,8 +9,8 @@ import os
 import numpy as np
 import pytest
 
-from workloads import (H, S, SDG, X, Y, Z, CX, CZ, T, Circuit, small_star, config1,
-                       random_clifford_circuit, t_to_s, brickwork_star, Region)
+from workloads import (H, S, SDG, X, Y, Z, CX, CZ, T, TDG, ZPOW, Circuit, small_star, config1,
+                       random_clifford_circuit, t_to_s, brickwork_star, Region, hwea, sk_qaoa)
 from workloads.circuits import C1_WORDS
 from oracle import tableau as tb
 from oracle import statevector as sv
@@ -137,6 +137,77 @@ def test_outcome_space_matches_statevector(seed):
         assert not (off >> piv[i]) & 1
     for zs in [A[:1], A[:2], A]:
         assert abs(tb.z_expectation(t, zs) - sv.z_expectation(sv.run(n, c.gates), n, zs)) < 1e-12
+
+
+def test_zpow_special_exponents():
+    """Z^a = diag(1, e^{i pi a}) is the identity at a = 0 and 2, and the
+    named gates of Sec. II-C at a = 1/2 (S), 1 (Z), -1/2 = 3/2 (S^dagger),
+    1/4 (T) and -1/4 (T^dagger)."""
+    for a in (0.0, 2.0, -4.0):
+        assert np.allclose(sv.zpow_matrix(a), np.eye(2), atol=1e-15)
+    for a, op in ((0.5, S), (1.0, Z), (-0.5, SDG), (1.5, SDG), (0.25, T), (-0.25, TDG), (2.25, T)):
+        assert np.allclose(sv.zpow_matrix(a), sv.MATS[op], atol=1e-15), a
+
+
+def _insert_zpow(c, exps, seed):
+    rng = np.random.default_rng(seed)
+    for a in exps:
+        c.gates.insert(int(rng.integers(len(c.gates) + 1)), (ZPOW, int(rng.integers(c.n_qubits)), -1, float(a)))
+    return c
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_clifford_zpow_tableau_matches_statevector(seed):
+    """Z^a with 2a an integer is S^{2a}: the tableau's outcome space and
+    Z-string values equal the dense statevector's (brute force), for
+    exponents on both sides of zero and beyond one period."""
+    n = 6
+    c = _insert_zpow(random_clifford_circuit(n, 60, seed + 300), (0.5, 1.0, 1.5, 2.0, -0.5, 3.5, 7.0, -2.5), seed)
+    A = [0, 2, 3, 5]
+    t = tb.Tableau(n).run(c.gates)
+    off, B, rho = tb.outcome_space(t, A)
+    psi = sv.run(n, c.gates)
+    assert np.allclose(sv.marginal(psi, n, A), tb.exact_distribution(off, B, len(A)), atol=1e-12)
+    for zs in ([0], [1, 4], [0, 2, 3, 5]):
+        assert abs(tb.z_expectation(t, zs) - sv.z_expectation(psi, n, zs)) < 1e-12
+    with pytest.raises(ValueError):
+        tb.Tableau(2).run([(ZPOW, 0, -1, 0.3)])
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_cut_identity_with_zpow(seed):
+    """Non-Clifford Z^a (2a not an integer) inside the cut-out regions: the
+    exact recombination equals the uncut statevector."""
+    rng = np.random.default_rng(seed)
+    w = small_star(n=9, depth=7, region_full=(0, 1, 2), boundary=3, window=(2, 5), n_t=3, seed=20 + seed)
+    c = Circuit(w.circuit.n_qubits)
+    for g in w.circuit.gates:       # every T becomes Z^a at the same place
+        c.gates.append((ZPOW, g[1], -1, float(rng.uniform(-3, 3))) if g[0] == T else g)
+    r = evaluate(c, w.cuts, w.marginal, w.zstrings, mode="exact")
+    assert sum(not f.clifford for f in r.fragments) == 1
+    bf, bz = brute_force(c, w.marginal, w.zstrings)
+    assert np.abs(r.marginal - bf).max() < 1e-12
+    assert np.abs(r.zexp - bz).max() < 1e-12
+
+
+def test_paper_workload_generators():
+    """HWEA and SK-QAOA (Sec. VI-B): with the injected gates removed the
+    circuits are Clifford (the tableau accepts them) and the statevector of
+    the Clifford ansatz has the affine-space distribution."""
+    for w in (hwea(8, rounds=5, n_t=2), sk_qaoa(7, n_t=1), hwea(6, rounds=3, n_t=2, zpow=True),
+              sk_qaoa(6, n_t=2, zpow=True)):
+        c = w.circuit
+        assert sum(g[0] in (T, TDG, ZPOW) for g in c.gates) == c.n_t > 0
+        cl = Circuit(c.n_qubits, [g for g in c.gates if g[0] not in (T, TDG, ZPOW)])
+        t = tb.Tableau(cl.n_qubits).run(cl.gates)
+        A = list(range(cl.n_qubits))
+        off, B, rho = tb.outcome_space(t, A)
+        p = sv.marginal(sv.run(cl.n_qubits, cl.gates), cl.n_qubits, A)
+        assert np.allclose(p, tb.exact_distribution(off, B, len(A)), atol=1e-12)
+    # SK-QAOA is all-to-all: every pair interacts
+    c = sk_qaoa(9).circuit
+    pairs = {tuple(sorted(g[1:3])) for g in c.gates if g[0] == CX}
+    assert len(pairs) == 9 * 8 // 2
 
 
 def test_philox_known_answers():

@@ -7,10 +7,10 @@ the CUDA path can both consume it without sharing any computation.
 """
 
 from .circuits import (  # noqa: F401
-    H, S, SDG, X, Y, Z, CX, CZ, T, TDG, GATE_NAMES, NQ,
-    Circuit, Region, Workload,
+    H, S, SDG, X, Y, Z, CX, CZ, T, TDG, ZPOW, GATE_NAMES, NQ, gate_param,
+    Circuit, Region, Workload, SEED_BASE,
     random_c1_word, random_c2_word, brickwork_star,
     config1, config2, config3, config4, config5_circuit, small_star,
     random_clifford_circuit, random_distributions, zstrings_for,
-    t_to_s,
+    t_to_s, hwea, sk_qaoa,
 )

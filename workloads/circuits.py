@@ -1,9 +1,11 @@
 """Seeded near-Clifford circuit generators shaped like the paper's workloads.
 
 Circuits follow the paper's near-Clifford setting (Sec. III-A, Sec. IV): a
-Clifford body with a few T = Z^{1/4} gates (Sec. II-C).  Gates are stored as
-``(op, q0, q1)`` tuples (``q1 = -1`` for one-qubit gates) using the opcodes
-below, which match ``ccs_gate.op`` in ``include/ccs.h``.
+Clifford body with a few T = Z^{1/4} gates (Sec. II-C), or other Z^a
+rotations (Sec. VIII).  Gates are stored as ``(op, q0, q1)`` tuples
+(``q1 = -1`` for one-qubit gates) using the opcodes below, which match
+``ccs_gate.op`` in ``include/ccs.h``; a Z^a gate carries its exponent as a
+fourth entry, ``(ZPOW, q, -1, a)``.
 
 The partition is fixed first (a "star"): each non-Clifford region is a set of
 full qubits plus a time window of one boundary qubit, i.e. two wire cuts per
@@ -25,9 +27,14 @@ from dataclasses import dataclass, field
 import numpy as np
 
 # Opcodes (ccs_gate.op).
-H, S, SDG, X, Y, Z, CX, CZ, T, TDG = range(10)
-GATE_NAMES = ["H", "S", "SDG", "X", "Y", "Z", "CX", "CZ", "T", "TDG"]
-NQ = [1, 1, 1, 1, 1, 1, 2, 2, 1, 1]
+H, S, SDG, X, Y, Z, CX, CZ, T, TDG, ZPOW = range(11)
+GATE_NAMES = ["H", "S", "SDG", "X", "Y", "Z", "CX", "CZ", "T", "TDG", "ZPOW"]
+NQ = [1, 1, 1, 1, 1, 1, 2, 2, 1, 1, 1]
+
+
+def gate_param(g):
+    """The exponent of a Z^a gate tuple (0.0 for every other gate)."""
+    return float(g[3]) if len(g) > 3 else 0.0
 
 SEED_BASE = 230310788
 
@@ -44,20 +51,28 @@ _C2_CLASS_SIZES = np.array([576, 5184, 5184, 576], dtype=np.float64)
 @dataclass
 class Circuit:
     n_qubits: int
-    gates: list = field(default_factory=list)   # (op, q0, q1)
+    gates: list = field(default_factory=list)   # (op, q0, q1) or (ZPOW, q, -1, a)
 
     def add(self, op, q0, q1=-1):
         self.gates.append((int(op), int(q0), int(q1)))
 
+    def add_zpow(self, q, a):
+        self.gates.append((ZPOW, int(q), -1, float(a)))
+
     @property
     def n_t(self):
-        return sum(1 for g in self.gates if g[0] in (T, TDG))
+        """Number of T, T^dagger and Z^a gates."""
+        return sum(1 for g in self.gates if g[0] in (T, TDG, ZPOW))
 
     def as_array(self):
-        """(n_gates, 3) int32 array of (op, q0, q1)."""
+        """(n_gates, 3) int32 array of (op, q0, q1); exponents dropped."""
         if not self.gates:
             return np.zeros((0, 3), dtype=np.int32)
-        return np.asarray(self.gates, dtype=np.int32)
+        return np.asarray([g[:3] for g in self.gates], dtype=np.int32)
+
+    def params(self):
+        """(n_gates,) float64 array of Z^a exponents (0 for other gates)."""
+        return np.asarray([gate_param(g) for g in self.gates], dtype=np.float64)
 
 
 @dataclass
@@ -271,6 +286,78 @@ def config5_circuit(rng, n_lo=50, n_hi=401, t_lo=4, t_hi=41, max_regions=4):
     return c, cuts, regs
 
 
+# Clifford-angle rotations as gate words (circuit order), up to global phase:
+# R_z(k pi/2) = S^k, R_y(k pi/2), R_x(k pi/2) = H R_z(k pi/2) H.
+RZ_WORDS = [[], [S], [Z], [SDG]]
+RY_WORDS = [[], [Z, H], [Y], [H, Z]]
+RX_WORDS = [[], [H, S, H], [X], [H, SDG, H]]
+
+
+def _inject(rng, c, n_t, zpow):
+    """Insert n_t non-Clifford gates at uniformly random (position, qubit):
+    T or T^dagger, or Z^a with a uniform in (0, 2) off the multiples of 1/2."""
+    for _ in range(n_t):
+        pos = int(rng.integers(len(c.gates) + 1))
+        q = int(rng.integers(c.n_qubits))
+        if zpow:
+            a = float(rng.uniform(0.02, 0.48)) + 0.5 * int(rng.integers(4))
+            c.gates.insert(pos, (ZPOW, q, -1, a))
+        else:
+            c.gates.insert(pos, (T if rng.random() < 0.5 else TDG, q, -1))
+
+
+def hwea(n, rounds=5, n_t=1, seed=SEED_BASE + 6, marginal=10, n_z=0, shots=4096, zpow=False):
+    """Near-Clifford hardware-efficient ansatz (Sec. VI-B): per round a layer
+    of one-qubit rotations R_y R_z, a linear chain of CX entanglers and a
+    second rotation layer, every angle a multiple of pi/2 (a Clifford ansatz,
+    Sec. IV-B), with n_t non-Clifford gates injected at random places.  No
+    cut set: the cut search chooses one."""
+    rng = np.random.default_rng(seed)
+    c = Circuit(n)
+
+    def rotations():
+        for q in range(n):
+            for op in RY_WORDS[int(rng.integers(4))] + RZ_WORDS[int(rng.integers(4))]:
+                c.add(op, q)
+
+    for _ in range(rounds):
+        rotations()
+        for q in range(n - 1):
+            c.add(CX, q, q + 1)
+        rotations()
+    _inject(rng, c, n_t, zpow)
+    marg = sorted(int(q) for q in rng.choice(n, size=min(marginal, n), replace=False))
+    return Workload(f"hwea{n}x{rounds}", c, None, marg, zstrings_for(n, n_z, rng), shots, seed)
+
+
+def sk_qaoa(n, rounds=1, n_t=1, seed=SEED_BASE + 7, marginal=10, n_z=0, shots=4096, zpow=False):
+    """Near-Clifford MaxCut QAOA on the Sherrington-Kirkpatrick model
+    (Sec. VI-B): |+>^n, then per round exp(-i gamma J_ab Z_a Z_b) on every
+    pair (all-to-all, J_ab = +-1, as CX R_z CX) and the mixer R_x(beta) on
+    every qubit, gamma and beta multiples of pi/4 so that every rotation is
+    Clifford; n_t non-Clifford gates injected at random places."""
+    rng = np.random.default_rng(seed)
+    c = Circuit(n)
+    for q in range(n):
+        c.add(H, q)
+    for _ in range(rounds):
+        g = int(rng.integers(1, 4))             # gamma = g pi/4
+        b = int(rng.integers(1, 4))             # beta = b pi/4
+        for a in range(n):
+            for q in range(a + 1, n):
+                k = (g * (1 if rng.random() < 0.5 else -1)) % 4
+                c.add(CX, a, q)
+                for op in RZ_WORDS[k]:
+                    c.add(op, q)
+                c.add(CX, a, q)
+        for q in range(n):
+            for op in RX_WORDS[b]:
+                c.add(op, q)
+    _inject(rng, c, n_t, zpow)
+    marg = sorted(int(q) for q in rng.choice(n, size=min(marginal, n), replace=False))
+    return Workload(f"skqaoa{n}x{rounds}", c, None, marg, zstrings_for(n, n_z, rng), shots, seed)
+
+
 def random_clifford_circuit(n, n_gates, seed, t_count=0):
     """Unstructured random circuit over the full gate set (oracle pins)."""
     rng = np.random.default_rng(seed)
@@ -291,8 +378,8 @@ def random_clifford_circuit(n, n_gates, seed, t_count=0):
 def t_to_s(circuit):
     """Replace every T by S and TDG by SDG (the circuit becomes Clifford)."""
     c = Circuit(circuit.n_qubits)
-    for op, a, b in circuit.gates:
-        c.gates.append(({T: S, TDG: SDG}.get(op, op), a, b))
+    for g in circuit.gates:
+        c.gates.append(({T: S, TDG: SDG}.get(g[0], g[0]),) + tuple(g[1:]))
     return c
 
 
