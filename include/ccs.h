@@ -60,14 +60,20 @@ extern "C" {
 #define CCS_ERR_DEVICE_CHECK (-9)
 
 /* Gate opcodes (Sec. II-A, II-C): Paulis, S = Z^{1/2}, H, CX, CZ; T = Z^{1/4}
- * and its inverse are the non-Clifford gates. */
+ * and its inverse are the non-Clifford gates.  CCS_ZPOW is Z^a =
+ * diag(1, e^{i pi a}) with a = param (Sec. VIII: the cutter isolates any Z^a):
+ * when 2a is an integer it is the Clifford S^{2a} (identity, S, Z or S^dagger)
+ * and is simulated as such; otherwise it is non-Clifford and its wire segment
+ * goes to a statevector fragment like a T gate. */
 enum {
   CCS_H = 0, CCS_S = 1, CCS_SDG = 2, CCS_X = 3, CCS_Y = 4, CCS_Z = 5,
-  CCS_CX = 6, CCS_CZ = 7, CCS_T = 8, CCS_TDG = 9
+  CCS_CX = 6, CCS_CZ = 7, CCS_T = 8, CCS_TDG = 9, CCS_ZPOW = 10
 };
 
 /* One gate.  q[1] is the target of CX (q[0] the control) and is ignored for
- * one-qubit gates.  nq, flags and param are reserved (set to 0). */
+ * one-qubit gates.  param is the exponent a of CCS_ZPOW (finite, else
+ * CCS_ERR_INVALID_ARG) and ignored for the other opcodes; nq and flags are
+ * reserved (set to 0). */
 typedef struct {
   uint8_t op;
   uint8_t nq;

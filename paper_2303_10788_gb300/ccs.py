@@ -242,16 +242,20 @@ def ccs_create(device=0, torch_allocator=True):
 
 
 def _pack_problem(prob):
-    """prob: object with .circuit (n_qubits, gates=[(op,q0,q1)]), .cuts (or None),
-    .marginal, .zstrings."""
+    """prob: object with .circuit (n_qubits, gates=[(op,q0,q1)] or
+    (10, q, -1, a) for Z^a), .cuts (or None), .marginal, .zstrings."""
     circ = prob.circuit
     ng = len(circ.gates)
     arr = np.zeros(max(1, ng), dtype=_GATE_DTYPE)
     if ng:
-        g = np.asarray(circ.gates, dtype=np.int64).reshape(ng, 3)
+        g = np.asarray([t[:3] for t in circ.gates], dtype=np.int64).reshape(ng, 3)
         arr["op"][:ng] = g[:, 0]
         arr["q"][:ng, 0] = g[:, 1]
         arr["q"][:ng, 1] = np.maximum(g[:, 2], 0)
+        zp = [(i, t[3]) for i, t in enumerate(circ.gates) if len(t) > 3]
+        if zp:
+            idx, val = zip(*zp)
+            arr["param"][list(idx)] = val
     gates = (ccs_gate * max(1, ng)).from_buffer(arr)
     cuts = getattr(prob, "cuts", None)
     ccuts = (ccs_cut * max(1, len(cuts) if cuts else 1))()

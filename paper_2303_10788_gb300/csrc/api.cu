@@ -317,16 +317,15 @@ int ccs_featurize(ccs_ctx c, const ccs_problem* q, const ccs_cut* cuts, int n_cu
   if (!c || !q || (n_cuts > 0 && !cuts) || !x || !rowptr || !glob) return fail(c, CCS_ERR_INVALID_ARG, "bad arguments");
   Problem P;
   P.n_qubits = q->n_qubits;
-  for (uint32_t g = 0; g < q->n_gates; ++g) {
-    const ccs_gate& G = q->gates[g];
-    P.gates.push_back({(int)G.op, (int)G.q[0], (G.op == CCS_CX || G.op == CCS_CZ) ? (int)G.q[1] : -1});
-  }
+  std::string err;
+  if (q->n_gates && !q->gates) return fail(c, CCS_ERR_INVALID_ARG, "null gate list");
+  int rc = load_gates(q->gates, q->n_gates, P.gates, P.gparam, err);
+  if (rc != CCS_OK) return fail(c, rc, err);
   P.marginal.assign(q->marginal, q->marginal + q->n_marginal);
   std::vector<ccs_cut> cs(cuts, cuts + std::max(0, n_cuts));
   std::vector<float> X, v, vt, g;
   std::vector<int> rp, cl;
-  std::string err;
-  int rc = featurize(P, cs, X, rp, cl, v, vt, g, err);
+  rc = featurize(P, cs, X, rp, cl, v, vt, g, err);
   if (rc != CCS_OK) return fail(c, rc, err);
   if ((int)cl.size() > cap_nnz) return fail(c, CCS_ERR_INVALID_ARG, "edge buffer too small");
   std::copy(X.begin(), X.end(), x);
@@ -438,11 +437,8 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
     Problem& P = pr[pi];
     P.n_qubits = q.n_qubits;
     if (q.n_qubits == 0 || (q.n_gates && !q.gates)) { prc[pi] = CCS_ERR_INVALID_ARG; perr[pi] = "empty circuit"; return; }
-    P.gates.reserve(q.n_gates);
-    for (uint32_t g = 0; g < q.n_gates; ++g) {
-      const ccs_gate& G = q.gates[g];
-      P.gates.push_back({(int)G.op, (int)G.q[0], (G.op == CCS_CX || G.op == CCS_CZ) ? (int)G.q[1] : -1});
-    }
+    prc[pi] = load_gates(q.gates, q.n_gates, P.gates, P.gparam, perr[pi]);
+    if (prc[pi] != CCS_OK) return;
     P.marginal.assign(q.marginal, q.marginal + q.n_marginal);
     for (uint32_t z = 0; z < q.n_zstrings; ++z)
       P.zstrings.emplace_back(q.zstring_qubits + q.zstring_offsets[z], q.zstring_qubits + q.zstring_offsets[z + 1]);
@@ -865,18 +861,16 @@ int ccs_cut_candidates(ccs_ctx c, const ccs_problem* q, const ccs_cut_opts* opts
   if (opts) o = *opts;
   Problem P;
   P.n_qubits = q->n_qubits;
-  for (uint32_t g = 0; g < q->n_gates; ++g) {
-    const ccs_gate& G = q->gates[g];
-    if (G.op > CCS_TDG) return fail(c, CCS_ERR_UNSUPPORTED_GATE, "unknown gate opcode");
-    P.gates.push_back({(int)G.op, (int)G.q[0], (G.op == CCS_CX || G.op == CCS_CZ) ? (int)G.q[1] : -1});
-  }
+  std::string err;
+  if (q->n_gates && !q->gates) return fail(c, CCS_ERR_INVALID_ARG, "null gate list");
+  int rc = load_gates(q->gates, q->n_gates, P.gates, P.gparam, err);
+  if (rc != CCS_OK) return fail(c, rc, err);
   P.marginal.assign(q->marginal, q->marginal + q->n_marginal);
   CutSearchOpts so;
   so.max_cuts = std::min(o.max_cuts, kMaxCuts);
   so.max_nc_width = std::min(o.max_nc_width > 0 ? o.max_nc_width : 10, kMaxNCWidth);
   std::vector<CutCandidate> cands;
-  std::string err;
-  int rc = greedy_cuts(P, so, cands, err);
+  rc = greedy_cuts(P, so, cands, err);
   if (rc != CCS_OK) return fail(c, rc, err);
   int n = 0, used = 0;
   offsets[0] = 0;

@@ -246,7 +246,7 @@ int greedy_cuts(const Problem& p, const CutSearchOpts& o, std::vector<CutCandida
       C.pos_of[g][1] = (int)C.ops_on[G[2]].size();
       C.ops_on[G[2]].push_back(g);
     }
-    if (G[0] == CCS_T || G[0] == CCS_TDG) C.nonclifford.push_back(g);
+    if (is_nonclifford_op(G[0])) C.nonclifford.push_back(g);
   }
   cands.clear();
   if (C.nonclifford.empty()) {

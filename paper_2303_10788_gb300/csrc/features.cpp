@@ -30,7 +30,7 @@ int featurize(const Problem& p0, const std::vector<ccs_cut>& cuts, std::vector<f
   std::vector<int> tcount(n, 0), gcount(n, 0), nc_gates(n, 0), ncut(n, 0), marg(n, 0), in_hub(n, 0);
   for (auto& g : p.gates) {
     gcount[g[1]]++;
-    if (g[0] == CCS_T || g[0] == CCS_TDG) tcount[g[1]]++;
+    if (is_nonclifford_op(g[0])) tcount[g[1]]++;
     if (g[0] == CCS_CX || g[0] == CCS_CZ) {
       gcount[g[2]]++;
       adj[g[1]][g[2]]++;

@@ -12,7 +12,7 @@ namespace ccs {
 namespace {
 
 bool is_two_qubit(int op) { return op == CCS_CX || op == CCS_CZ; }
-bool is_clifford_op(int op) { return op >= CCS_H && op <= CCS_CZ; }
+bool is_clifford_op(int op) { return (op >= CCS_H && op <= CCS_CZ) || op == kOpI; }
 
 struct UF {
   std::vector<int> p;
@@ -86,7 +86,7 @@ CliffordOp clifford_from_word(const std::vector<std::array<int, 3>>& word) {
 
 using cd = std::complex<double>;
 
-void gate_matrix_1q(int op, cd m[4]) {
+void gate_matrix_1q(int op, double param, cd m[4]) {
   const double r = 1.0 / std::sqrt(2.0);
   const cd I(0, 1);
   cd id[4] = {1, 0, 0, 1};
@@ -100,21 +100,28 @@ void gate_matrix_1q(int op, cd m[4]) {
     case CCS_Z: m[3] = -1; break;
     case CCS_T: m[3] = std::polar(1.0, M_PI / 4); break;
     case CCS_TDG: m[3] = std::polar(1.0, -M_PI / 4); break;
-    default: break;
+    case CCS_ZPOW: m[3] = std::polar(1.0, M_PI * param); break;   // Z^a = diag(1, e^{i pi a})
+    default: break;                                                // kOpI: identity
   }
 }
+
+// One gate of a fused op's word: opcode, roles (rb < 0: one-qubit), exponent.
+struct WordGate {
+  int op, ra, rb;
+  double param;
+};
 
 // A fused op: statevector fragments keep the gate word (for the unitary);
 // Clifford fragments apply each gate to the op's 16-pattern planes as it
 // arrives, so no word is stored.
 struct Fused {
   int a, b;                                   // b < 0: one-qubit op
-  std::vector<std::array<int, 3>> word;       // (op, role_a, role_b), statevector fragments only
+  std::vector<WordGate> word;                 // statevector fragments only
   uint32_t px[2] = {kPX0, kPX1}, pz[2] = {kPZ0, kPZ1}, pf = 0;
   bool dead = false;
-  void add(int op, int ra, int rb, bool planes) {
+  void add(int op, int ra, int rb, bool planes, double param) {
     if (planes) chp_planes(op, ra, rb < 0 ? 1 - ra : rb, px, pz, pf);
-    else word.push_back({op, ra, rb});
+    else word.push_back({op, ra, rb, param});
   }
 };
 
@@ -122,15 +129,17 @@ struct Fused {
 std::vector<std::vector<const Fused*>> fuse_and_layer(const Frag& f, std::vector<Fused>& ops, bool planes) {
   const int n = f.n();
   std::vector<int> last(n, -1);
-  for (auto& g : f.gates) {
-    int op = g[0], a = g[1], b = g[2];
+  for (size_t gi = 0; gi < f.gates.size(); ++gi) {
+    const auto& g = f.gates[gi];
+    const int op = g[0], a = g[1], b = g[2];
+    const double prm = f.gparam.empty() ? 0.0 : f.gparam[gi];
     if (!is_two_qubit(op)) {
       if (last[a] >= 0) {
         Fused& F = ops[last[a]];
-        F.add(op, F.a == a ? 0 : 1, -1, planes);
+        F.add(op, F.a == a ? 0 : 1, -1, planes, prm);
       } else {
         ops.push_back(Fused{a, -1});
-        ops.back().add(op, 0, -1, planes);
+        ops.back().add(op, 0, -1, planes, prm);
         last[a] = (int)ops.size() - 1;
       }
       continue;
@@ -139,7 +148,7 @@ std::vector<std::vector<const Fused*>> fuse_and_layer(const Frag& f, std::vector
     if (la >= 0 && la == lb) {
       Fused& F = ops[la];
       int ra = F.a == a ? 0 : 1;
-      F.add(op, ra, 1 - ra, planes);
+      F.add(op, ra, 1 - ra, planes, 0.0);
       continue;
     }
     Fused nf{a, b};
@@ -148,7 +157,7 @@ std::vector<std::vector<const Fused*>> fuse_and_layer(const Frag& f, std::vector
       int lq = side == 0 ? la : lb;
       if (lq >= 0 && ops[lq].b < 0) {     // absorb a trailing one-qubit op
         if (!planes)
-          for (auto& w : ops[lq].word) nf.word.push_back({w[0], side, -1});
+          for (auto& w : ops[lq].word) nf.word.push_back({w.op, side, -1, w.param});
         g1[side] = &ops[lq];
         ops[lq].dead = true;
       }
@@ -172,7 +181,7 @@ std::vector<std::vector<const Fused*>> fuse_and_layer(const Frag& f, std::vector
     }
     for (int side = 0; side < 2; ++side)
       if (g1[side]) const_cast<Fused*>(g1[side])->word.clear();
-    nf.add(op, 0, 1, planes);
+    nf.add(op, 0, 1, planes, 0.0);
     ops.push_back(std::move(nf));
     last[a] = last[b] = (int)ops.size() - 1;
   }
@@ -193,12 +202,41 @@ std::vector<std::vector<const Fused*>> fuse_and_layer(const Frag& f, std::vector
 
 }  // namespace
 
+int load_gates(const ccs_gate* G, uint32_t ng, std::vector<std::array<int, 3>>& gates,
+               std::vector<double>& gparam, std::string& err) {
+  static const int kSPow[4] = {kOpI, CCS_S, CCS_Z, CCS_SDG};   // S^0 .. S^3
+  gates.resize(ng);
+  gparam.assign(ng, 0.0);
+  for (uint32_t i = 0; i < ng; ++i) {
+    const ccs_gate& g = G[i];
+    if (g.op > CCS_ZPOW) { err = "unknown gate opcode"; return CCS_ERR_UNSUPPORTED_GATE; }
+    int op = g.op;
+    if (op == CCS_ZPOW) {
+      const double k = 2.0 * g.param;
+      if (!std::isfinite(k)) { err = "Z^a exponent not finite"; return CCS_ERR_INVALID_ARG; }
+      if (k == std::floor(k)) {
+        double m = std::fmod(k, 4.0);       // exact for every integral double
+        if (m < 0) m += 4.0;
+        op = kSPow[(int)m];
+      } else {
+        double a = std::fmod(g.param, 2.0);  // e^{i pi a} has period 2 in a
+        if (a < 0) a += 2.0;
+        gparam[i] = a;
+      }
+    }
+    const bool two = op == CCS_CX || op == CCS_CZ;
+    gates[i] = {op, (int)g.q[0], two ? (int)g.q[1] : -1};
+  }
+  return CCS_OK;
+}
+
 int fragment_problem(Problem& p, int pi, std::vector<Frag>& out, std::string& err) {
   const int n = (int)p.n_qubits;
   const int ng = (int)p.gates.size();
+  if (!p.gparam.empty() && (int)p.gparam.size() != ng) { err = "gate exponent list size"; return CCS_ERR_INVALID_ARG; }
   for (int gi = 0; gi < ng; ++gi) {
     auto& g = p.gates[gi];
-    if (g[0] < 0 || g[0] > CCS_TDG) { err = "unknown gate opcode"; return CCS_ERR_UNSUPPORTED_GATE; }
+    if (g[0] < 0 || (g[0] > CCS_ZPOW && g[0] != kOpI)) { err = "unknown gate opcode"; return CCS_ERR_UNSUPPORTED_GATE; }
     if (g[1] < 0 || g[1] >= n) { err = "gate qubit out of range"; return CCS_ERR_INVALID_ARG; }
     if (is_two_qubit(g[0]) && (g[2] < 0 || g[2] >= n || g[2] == g[1])) {
       err = "bad two-qubit gate operands"; return CCS_ERR_INVALID_ARG;
@@ -259,8 +297,10 @@ int fragment_problem(Problem& p, int pi, std::vector<Frag>& out, std::string& er
     if (is_two_qubit(g[0])) {
       auto wb = where[base[g[2]] + seg(g[2], gi)];
       f.gates.push_back({g[0], wa.second, wb.second});
+      f.gparam.push_back(0.0);
     } else {
       f.gates.push_back({g[0], wa.second, -1});
+      f.gparam.push_back(p.gparam.empty() ? 0.0 : p.gparam[gi]);
       if (!is_clifford_op(g[0])) f.clifford = false;
     }
   }
@@ -355,7 +395,7 @@ void compile_nc(Frag& f) {
         cd U[4] = {1, 0, 0, 1};
         for (auto& g : F->word) {
           cd G[4], R[4];
-          gate_matrix_1q(g[0], G);
+          gate_matrix_1q(g.op, g.param, G);
           for (int i = 0; i < 2; ++i)
             for (int j = 0; j < 2; ++j) R[i * 2 + j] = G[i * 2] * U[j] + G[i * 2 + 1] * U[2 + j];
           for (int i = 0; i < 4; ++i) U[i] = R[i];
@@ -366,7 +406,7 @@ void compile_nc(Frag& f) {
         cd U[16];
         for (int i = 0; i < 16; ++i) U[i] = (i % 5 == 0) ? 1.0 : 0.0;
         for (auto& g : F->word) {
-          const int op = g[0], ra = g[1], rb = g[2] < 0 ? 1 - g[1] : g[2];
+          const int op = g.op, ra = g.ra, rb = g.rb < 0 ? 1 - g.ra : g.rb;
           if (op == CCS_CX) {          // rows with control bit set: swap the target bit
             for (int i = 0; i < 4; ++i)
               if (((i >> ra) & 1) && !((i >> rb) & 1))
@@ -375,7 +415,7 @@ void compile_nc(Frag& f) {
             for (int j = 0; j < 4; ++j) U[3 * 4 + j] = -U[3 * 4 + j];
           } else {                     // one-qubit gate on role ra: mix row pairs
             cd G[4];
-            gate_matrix_1q(op, G);
+            gate_matrix_1q(op, g.param, G);
             for (int i0 = 0; i0 < 4; ++i0) {
               if ((i0 >> ra) & 1) continue;
               const int i1 = i0 | (1 << ra);
@@ -411,7 +451,7 @@ static void one_qubit_matrix(const std::vector<int>& w, float out[8]) {
   cd U[4] = {1, 0, 0, 1};
   for (int g : w) {
     cd G[4], R[4];
-    gate_matrix_1q(g, G);
+    gate_matrix_1q(g, 0.0, G);
     for (int i = 0; i < 2; ++i)
       for (int j = 0; j < 2; ++j) R[i * 2 + j] = G[i * 2] * U[j] + G[i * 2 + 1] * U[2 + j];
     for (int i = 0; i < 4; ++i) U[i] = R[i];

@@ -19,6 +19,19 @@ constexpr int kMaxTableauQubits = 640;  // (2n+3) x 2*ceil(n/64) words fit 227 K
 constexpr int kMaxCuts = 12;
 constexpr int kMaxMarginal = 24;
 
+// Internal opcode of a Z^a gate with 2a = 0 mod 4 (the identity): kept as a
+// gate so that cut positions, which are gate indices, stay valid.
+constexpr int kOpI = 64;
+
+inline bool is_nonclifford_op(int op) { return op == CCS_T || op == CCS_TDG || op == CCS_ZPOW; }
+
+// The ABI gate list as (op, q0, q1) triples (q1 = -1 for one-qubit gates) and
+// per-gate exponents: Z^a with 2a an integer becomes the Clifford S^{2a}
+// (kOpI, S, Z or SDG, Sec. II-C); any other Z^a stays CCS_ZPOW with its
+// exponent reduced mod 2 in `gparam` (0 for every other gate).
+int load_gates(const ccs_gate* g, uint32_t n_gates, std::vector<std::array<int, 3>>& gates,
+               std::vector<double>& gparam, std::string& err);
+
 // A fused one- or two-qubit Clifford conjugation acting on the bit-sliced
 // columns (x_a, z_a, x_b, z_b) = (v0, v1, v2, v3):
 //   u_i = XOR_j M[i][j] v_j            (M bit 4*i + j)
@@ -41,6 +54,7 @@ struct Frag {
   bool clifford = true;
   std::vector<std::pair<uint32_t, uint32_t>> wires;  // (qubit, segment)
   std::vector<std::array<int, 3>> gates;             // (op, a, b), local wires
+  std::vector<double> gparam;                        // per gate: Z^a exponent, else 0
   std::vector<int> qin_cut, qin_wire, qout_cut, qout_wire;
   std::vector<int> marg_pos, marg_wire;
   std::vector<int> slots;       // incident cut ids, ascending
@@ -66,6 +80,7 @@ struct Frag {
 struct Problem {
   uint32_t n_qubits = 0;
   std::vector<std::array<int, 3>> gates;
+  std::vector<double> gparam;    // per gate: Z^a exponent, else 0 (may be empty: all 0)
   std::vector<ccs_cut> cuts;     // canonical order
   std::vector<uint32_t> marginal;
   std::vector<std::vector<uint32_t>> zstrings;

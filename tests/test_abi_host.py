@@ -107,6 +107,11 @@ def test_error_codes(hctx):
     _expect(hctx, [_P(c, [], [0, 0])], "INVALID_ARG")               # repeated marginal qubit
     bad = Circuit(2); bad.gates.append((42, 0, -1))
     _expect(hctx, [_P(bad, [], [0])], "UNSUPPORTED_GATE")
+    bad = Circuit(2); bad.gates.append((11, 0, -1))                 # first opcode past CCS_ZPOW
+    _expect(hctx, [_P(bad, [], [0])], "UNSUPPORTED_GATE")
+    for a in (float("nan"), float("inf"), 1e308):                   # Z^a needs a finite 2a
+        bad = Circuit(2); bad.add_zpow(0, a)
+        _expect(hctx, [_P(bad, [], [0])], "INVALID_ARG")
     loop = Circuit(2)                                               # both ends of the cut in one fragment
     loop.add(CX, 0, 1); loop.add(H, 0); loop.add(CX, 0, 1)
     _expect(hctx, [_P(loop, [(0, 1)], [0])], "UNSUPPORTED")

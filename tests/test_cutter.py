@@ -9,7 +9,8 @@ import numpy as np
 import pytest
 
 from paper_2303_10788_gb300 import ccs
-from workloads import config1, config2, config3, config4, small_star, random_clifford_circuit
+from workloads import (config1, config2, config3, config4, small_star, random_clifford_circuit, hwea,
+                       sk_qaoa, ZPOW)
 from oracle.pipeline import evaluate, brute_force
 
 
@@ -61,3 +62,56 @@ def test_search_matches_planted_partition(hctx):
 def test_clifford_circuit_needs_no_cuts(hctx):
     c = random_clifford_circuit(30, 200, 3)
     assert ccs.ccs_cut_candidates(hctx, _P(c, [0, 1]))[0][0] == []
+
+
+def _with_zpow(c, exps, seed):
+    rng = np.random.default_rng(seed)
+    for a in exps:
+        c.gates.insert(int(rng.integers(len(c.gates) + 1)), (ZPOW, int(rng.integers(c.n_qubits)), -1, float(a)))
+    return c
+
+
+def test_zpow_cuts_are_exact(hctx):
+    """Z^a gates: the search isolates those with 2a not an integer and treats
+    the others (S^{2a}) as Clifford; the searched cuts reproduce brute force."""
+    for seed in range(3):
+        c = _with_zpow(random_clifford_circuit(7, 50, seed + 60), (0.3, -1.5, 0.5, 2.0, 1.17), seed)
+        marg = [1, 4, 6]
+        cands = ccs.ccs_cut_candidates(hctx, _P(c, marg), max_nc_width=5)
+        bf, _ = brute_force(c, marg)
+        r = evaluate(c, cands[0][0], marg, mode="exact")
+        assert np.abs(r.marginal - bf).max() < 1e-12
+    c = _with_zpow(random_clifford_circuit(12, 120, 7), (0.5, 1.0, 1.5, 0.0, -0.5, 4.0, 1e6 + 0.5), 7)
+    assert ccs.ccs_cut_candidates(hctx, _P(c, [0, 1]))[0][0] == []
+    plan = ccs.ccs_build_fragments(hctx, [_P(c, [0, 1])])
+    assert ccs.ccs_plan_counts(hctx, plan, 0) == (1, 0)
+    assert ccs.ccs_fragment_info_get(hctx, plan, 0, 0)["clifford"]
+
+
+@pytest.mark.parametrize("w", [hwea(10, rounds=5, n_t=1, n_z=4), hwea(8, rounds=3, n_t=2, n_z=4, zpow=True),
+                               sk_qaoa(8, n_t=1, n_z=4), sk_qaoa(7, n_t=2, n_z=4, zpow=True)],
+                         ids=["hwea10", "hwea8_zpow", "skqaoa8", "skqaoa7_zpow"])
+def test_paper_workloads_searched_cuts_exact(hctx, w):
+    """The paper's benchmark shapes (Sec. VI-B) through the cut search: the
+    chosen cuts reproduce the uncut statevector exactly (oracle)."""
+    cands = ccs.ccs_cut_candidates(hctx, _P(w.circuit, w.marginal, w.zstrings), max_nc_width=4)
+    assert cands[0][0], "a non-Clifford gate needs cuts at this width limit"
+    bf, bz = brute_force(w.circuit, w.marginal, w.zstrings)
+    r = evaluate(w.circuit, cands[0][0], w.marginal, w.zstrings, mode="exact")
+    assert max(f.n for f in r.fragments if not f.clifford) <= 4
+    assert np.abs(r.marginal - bf).max() < 1e-12
+    assert np.abs(r.zexp - bz).max() < 1e-12
+
+
+def test_hwea_300_qubits_plan(hctx):
+    """HWEA at the paper's largest width (300 qubits, 5 rounds, one T): the
+    search cuts the T's wire segment out, with two cuts (the qubit's two outer
+    segments stay in a 301-wire Clifford body) or one when the T follows the
+    qubit's last entangler."""
+    for seed in range(5):
+        w = hwea(300, rounds=5, n_t=1, seed=230310794 + seed)
+        plan = ccs.ccs_build_fragments(hctx, [_P(w.circuit, w.marginal)])
+        nf, nc = ccs.ccs_plan_counts(hctx, plan, 0)
+        infos = [ccs.ccs_fragment_info_get(hctx, plan, 0, f) for f in range(nf)]
+        assert nc in (1, 2)
+        assert sorted((i["clifford"], i["n_wires"]) for i in infos) == [(0, 1), (1, 299 + nc)]
