@@ -35,6 +35,10 @@ namespace {
 
 struct Window {
   int q, a, b;
+  // positions [sa, sb) already closed: every two-qubit gate there has its
+  // partner position inside the region (empty when sa == sb).  Windows only
+  // grow, so a closed position stays closed.
+  int sa = 0, sb = 0;
 };
 using Region = std::vector<Window>;   // sorted by qubit, one window per qubit
 
@@ -42,8 +46,10 @@ struct Ctx {
   const Problem* P;
   int n;
   std::vector<std::vector<int>> ops_on;      // gate indices per qubit
+  std::vector<std::vector<int>> tq_before;   // per qubit: two-qubit gates among ops_on[q][0, pos)
   std::vector<std::array<int, 2>> pos_of;    // position of gate g in ops_on[q0], ops_on[q1]
   std::vector<int> nonclifford;
+  std::vector<char> in_marginal;
 };
 
 bool two_qubit(int op) { return op == CCS_CX || op == CCS_CZ; }
@@ -68,22 +74,33 @@ void close_region(const Ctx& C, Region& r) {
     }
     for (size_t i = 0; i < r.size(); ++i) {
       const Window w = r[i];
-      for (int pos = w.a; pos < w.b; ++pos) {
-        const int g = C.ops_on[w.q][pos];
-        const auto& G = C.P->gates[g];
-        if (!two_qubit(G[0])) continue;
-        const int p = G[1] == w.q ? G[2] : G[1];
-        const int pp = C.pos_of[g][G[1] == w.q ? 1 : 0];
-        Window* o = find_w(r, p);
-        if (!o) {
-          r.push_back({p, pp, pp + 1});
-          changed = true;
-        } else if (pp < o->a || pp >= o->b) {
-          o->a = std::min(o->a, pp);
-          o->b = std::max(o->b, pp + 1);
-          changed = true;
+      const int q = w.q;
+      auto scan = [&](int lo, int hi) {
+        for (int pos = lo; pos < hi; ++pos) {
+          const int g = C.ops_on[q][pos];
+          const auto& G = C.P->gates[g];
+          if (!two_qubit(G[0])) continue;
+          const int p = G[1] == q ? G[2] : G[1];
+          const int pp = C.pos_of[g][G[1] == q ? 1 : 0];
+          Window* o = find_w(r, p);
+          if (!o) {
+            r.push_back({p, pp, pp + 1});
+            changed = true;
+          } else if (pp < o->a || pp >= o->b) {
+            o->a = std::min(o->a, pp);
+            o->b = std::max(o->b, pp + 1);
+            changed = true;
+          }
         }
+      };
+      if (w.sa == w.sb) {
+        scan(w.a, w.b);
+      } else {
+        scan(w.a, w.sa);
+        scan(w.sb, w.b);
       }
+      r[i].sa = w.a;
+      r[i].sb = w.b;
     }
   }
   std::sort(r.begin(), r.end(), [](const Window& x, const Window& y) { return x.q < y.q; });
@@ -100,8 +117,22 @@ Region merge(const Region& x, const Region& y) {
   Region r = x;
   for (auto& w : y) {
     Window* o = find_w(r, w.q);
-    if (!o) r.push_back(w);
-    else { o->a = std::min(o->a, w.a); o->b = std::max(o->b, w.b); }
+    if (!o) {
+      r.push_back(w);
+      continue;
+    }
+    o->a = std::min(o->a, w.a);
+    o->b = std::max(o->b, w.b);
+    // closed positions: the union when the two closed ranges meet, else the longer one
+    if (w.sa == w.sb) continue;
+    if (o->sa == o->sb || (std::max(o->sa, w.sa) <= std::min(o->sb, w.sb))) {
+      const bool oe = o->sa == o->sb;
+      o->sa = oe ? w.sa : std::min(o->sa, w.sa);
+      o->sb = oe ? w.sb : std::max(o->sb, w.sb);
+    } else if (w.sb - w.sa > o->sb - o->sa) {
+      o->sa = w.sa;
+      o->sb = w.sb;
+    }
   }
   return r;
 }
@@ -168,27 +199,30 @@ std::vector<ccs_cut> cuts_of(const Ctx& C, const std::vector<Region>& rs) {
 
 // Estimated work of a state straight from its windows (the Clifford rest is
 // taken as one fragment).
+// (The regions are closed: a two-qubit gate inside one window is inside its
+// partner's window too, so the region's distinct gates are the window
+// lengths less half the two-qubit positions.)
 double estimate(const Ctx& C, const std::vector<Region>& rs, int max_width, bool* ok) {
   *ok = true;
   const int n = C.n;
   long long nc_gates_total = 0;
   double cost = 0.0;
   int k = 0, body_qin = 0, body_qout = 0, body_wires = n, body_marg = 0, nc_marg = 0;
-  std::set<int> marg(C.P->marginal.begin(), C.P->marginal.end());
   for (auto& r : rs) {
     int width = (int)r.size(), qin = 0, qout = 0;
-    long long gates = 0;
-    std::set<int> inside;
-    for (auto& w : r)
-      for (int p = w.a; p < w.b; ++p) inside.insert(C.ops_on[w.q][p]);
-    gates = (long long)inside.size();
+    long long len_sum = 0, tq_sum = 0;
+    for (auto& w : r) {
+      len_sum += w.b - w.a;
+      tq_sum += C.tq_before[w.q][w.b] - C.tq_before[w.q][w.a];
+    }
+    const long long gates = len_sum - tq_sum / 2;
     for (auto& w : r) {
       const int len = (int)C.ops_on[w.q].size();
       const bool pre = w.a > 0, post = w.b < len;
       qin += pre;
       qout += post;
       body_wires += (pre && post) ? 1 : (!pre && !post) ? -1 : 0;
-      if (!post && marg.count(w.q)) ++nc_marg;
+      if (!post && C.in_marginal[w.q]) ++nc_marg;
     }
     if (width > max_width) *ok = false;
     k += qin + qout;
@@ -197,7 +231,7 @@ double estimate(const Ctx& C, const std::vector<Region>& rs, int max_width, bool
     nc_gates_total += gates;
     cost += std::pow(4.0, qin) * std::pow(3.0, qout) * (double)gates * std::ldexp(1.0, width) / 64.0;
   }
-  body_marg = (int)marg.size() - nc_marg;
+  body_marg = (int)C.P->marginal.size() - nc_marg;
   const long long body_gates = (long long)C.P->gates.size() - nc_gates_total;
   const double W = 2.0 * std::ceil(std::max(1, body_wires) / 64.0);
   cost += std::pow(4.0, body_qin) * std::pow(3.0, body_qout) * ((double)body_gates / 6.0 * W + 1024.0);
@@ -208,20 +242,93 @@ double estimate(const Ctx& C, const std::vector<Region>& rs, int max_width, bool
 
 }  // namespace
 
-double plan_cost(const Problem& p, const std::vector<ccs_cut>& cuts, bool* ok) {
-  Problem q = p;
-  q.cuts = cuts;
-  std::vector<Frag> frags;
-  std::string err;
-  if (fragment_problem(q, 0, frags, err) != CCS_OK || q.hub < 0) {
+// The fragments a cut set gives, counted without building them: the same
+// segments, union-find and checks as fragment_problem, keeping per fragment
+// only its wire, gate, input/output and marginal counts.  Fragments are
+// numbered by their first segment, as fragment_problem orders them, so the
+// cost sums in the same order.
+double plan_cost(const Problem& p, const std::vector<ccs_cut>& cuts_in, bool* ok) {
+  auto invalid = [&]() {
     if (ok) *ok = false;
-    return INFINITY;
+    return (double)INFINITY;
+  };
+  const int n = (int)p.n_qubits;
+  const int ng = (int)p.gates.size();
+  std::vector<ccs_cut> cuts = cuts_in;
+  for (auto& c : cuts)
+    if ((int)c.qubit >= n || (int)c.gate_index > ng) return invalid();
+  std::sort(cuts.begin(), cuts.end(), [](const ccs_cut& x, const ccs_cut& y) {
+    return x.gate_index != y.gate_index ? x.gate_index < y.gate_index : x.qubit < y.qubit;
+  });
+  for (size_t i = 1; i < cuts.size(); ++i)
+    if (cuts[i].qubit == cuts[i - 1].qubit && cuts[i].gate_index == cuts[i - 1].gate_index) return invalid();
+  if ((int)cuts.size() > kMaxCuts || p.marginal.size() > (size_t)kMaxMarginal) return invalid();
+  for (size_t i = 0; i < p.marginal.size(); ++i) {
+    if ((int)p.marginal[i] >= n) return invalid();
+    for (size_t j = 0; j < i; ++j)
+      if (p.marginal[i] == p.marginal[j]) return invalid();
   }
+  // cut positions per qubit, ascending (cuts are sorted by gate index)
+  std::vector<int> cnt(n + 1, 0), start(n + 1, 0), pos(cuts.size());
+  for (auto& c : cuts) cnt[c.qubit]++;
+  for (int q = 0; q < n; ++q) start[q + 1] = start[q] + cnt[q];
+  {
+    std::vector<int> fill(start.begin(), start.end() - 1);
+    for (auto& c : cuts) pos[fill[c.qubit]++] = (int)c.gate_index;
+  }
+  std::vector<int> base(n + 1, 0);
+  for (int q = 0; q < n; ++q) base[q + 1] = base[q] + cnt[q] + 1;
+  auto seg = [&](int q, int g) {
+    return base[q] + (int)(std::upper_bound(pos.begin() + start[q], pos.begin() + start[q] + cnt[q], g) -
+                           (pos.begin() + start[q]));
+  };
+  UF uf(base[n]);
+  for (int gi = 0; gi < ng; ++gi) {
+    const auto& g = p.gates[gi];
+    if (two_qubit(g[0])) uf.join(seg(g[1], gi), seg(g[2], gi));
+  }
+  std::vector<int> fid(base[n], -1), of_seg(base[n]);
+  int nf = 0;
+  for (int s = 0; s < base[n]; ++s) {
+    const int r = uf.find(s);
+    if (fid[r] < 0) fid[r] = nf++;
+    of_seg[s] = fid[r];
+  }
+  std::vector<int> wires(nf, 0), gates(nf, 0), qin(nf, 0), qout(nf, 0), marg(nf, 0);
+  std::vector<char> cliff(nf, 1);
+  for (int s = 0; s < base[n]; ++s) wires[of_seg[s]]++;
+  for (int gi = 0; gi < ng; ++gi) {
+    const auto& g = p.gates[gi];
+    const int f = of_seg[seg(g[1], gi)];
+    gates[f]++;
+    if (!two_qubit(g[0]) && is_nonclifford_op(g[0])) cliff[f] = 0;
+  }
+  for (auto& c : cuts) {
+    const int q = (int)c.qubit;
+    const int k = (int)(std::find(pos.begin() + start[q], pos.begin() + start[q] + cnt[q], (int)c.gate_index) -
+                        (pos.begin() + start[q])) + 1;
+    const int fu = of_seg[base[q] + k - 1], fd = of_seg[base[q] + k];
+    if (fu == fd) return invalid();
+    qout[fu]++;
+    qin[fd]++;
+  }
+  for (auto q : p.marginal) marg[of_seg[base[q] + cnt[q]]]++;
+  bool star = cuts.empty();
+  for (int f = 0; f < nf; ++f) {
+    if (!cliff[f] && wires[f] > kMaxNCWidth) return invalid();
+    if (cliff[f] && wires[f] > kMaxTableauQubits) return invalid();
+    if (marg[f] + qout[f] > kMaxMeas) return invalid();
+    if (qin[f] + qout[f] == (int)cuts.size()) star = true;
+  }
+  if (!star) return invalid();
   double cost = 0.0;
-  for (auto& f : frags) {
-    const double nv = (double)f.n_variants();
-    if (f.clifford) cost += nv * ((double)f.gates.size() / 6.0 * 2.0 * std::ceil(f.n() / 64.0) + 1024.0);
-    else cost += nv * (double)f.gates.size() * std::ldexp(1.0, f.n()) / 64.0;
+  for (int f = 0; f < nf; ++f) {
+    int v = 1;
+    for (int i = 0; i < qin[f]; ++i) v *= 4;
+    for (int i = 0; i < qout[f]; ++i) v *= 3;
+    const double nv = (double)v;
+    if (cliff[f]) cost += nv * ((double)gates[f] / 6.0 * 2.0 * std::ceil(wires[f] / 64.0) + 1024.0);
+    else cost += nv * (double)gates[f] * std::ldexp(1.0, wires[f]) / 64.0;
   }
   cost += std::pow(4.0, (double)cuts.size()) * std::ldexp(1.0, (int)p.marginal.size()) / 16.0;
   if (ok) *ok = true;
@@ -248,6 +355,15 @@ int greedy_cuts(const Problem& p, const CutSearchOpts& o, std::vector<CutCandida
     }
     if (is_nonclifford_op(G[0])) C.nonclifford.push_back(g);
   }
+  C.tq_before.assign(C.n, {});
+  for (int q = 0; q < C.n; ++q) {
+    auto& t = C.tq_before[q];
+    t.assign(C.ops_on[q].size() + 1, 0);
+    for (size_t i = 0; i < C.ops_on[q].size(); ++i) t[i + 1] = t[i] + (two_qubit(p.gates[C.ops_on[q][i]][0]) ? 1 : 0);
+  }
+  C.in_marginal.assign(C.n, 0);
+  for (auto q : p.marginal)
+    if ((int)q < C.n) C.in_marginal[q] = 1;
   cands.clear();
   if (C.nonclifford.empty()) {
     cands.push_back({{}, 0.0, {}});

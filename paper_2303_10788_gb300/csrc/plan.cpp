@@ -14,19 +14,6 @@ namespace {
 bool is_two_qubit(int op) { return op == CCS_CX || op == CCS_CZ; }
 bool is_clifford_op(int op) { return (op >= CCS_H && op <= CCS_CZ) || op == kOpI; }
 
-struct UF {
-  std::vector<int> p;
-  explicit UF(int n) : p(n) { std::iota(p.begin(), p.end(), 0); }
-  int find(int x) {
-    while (p[x] != x) { p[x] = p[p[x]]; x = p[x]; }
-    return x;
-  }
-  void join(int a, int b) {
-    a = find(a); b = find(b);
-    if (a != b) p[std::max(a, b)] = std::min(a, b);
-  }
-};
-
 // CHP update (Sec. III of Aaronson-Gottesman) of the local Pauli patterns
 // (x_a, z_a, x_b, z_b) and their signs, 16 patterns at once: bit v of each
 // plane is the x_a, z_a, x_b, z_b or sign bit of pattern v.

@@ -2,9 +2,11 @@
 // compiled gate streams the device kernels consume.
 #pragma once
 
+#include <algorithm>
 #include <array>
 #include <complex>
 #include <cstdint>
+#include <numeric>
 #include <string>
 #include <vector>
 
@@ -86,6 +88,20 @@ struct Problem {
   std::vector<std::vector<uint32_t>> zstrings;
   std::vector<int> frag_ids;     // into Plan::frags
   int hub = -1;                  // local fragment index of the star's hub, -1 if not a star
+};
+
+// Union-find over wire segments; the root of a set is its smallest member.
+struct UF {
+  std::vector<int> p;
+  explicit UF(int n) : p(n) { std::iota(p.begin(), p.end(), 0); }
+  int find(int x) {
+    while (p[x] != x) { p[x] = p[p[x]]; x = p[x]; }
+    return x;
+  }
+  void join(int a, int b) {
+    a = find(a); b = find(b);
+    if (a != b) p[std::max(a, b)] = std::min(a, b);
+  }
 };
 
 // Fragment a problem at its cuts (the cuts must already be canonical).
