@@ -24,19 +24,24 @@ constexpr int kZOffStage = 257, kZWireStage = 1024;
 
 namespace {
 
-__device__ __forceinline__ uint64_t bm(unsigned v, int bit) { return 0ull - (uint64_t)((v >> bit) & 1u); }
+// 0 or ~0u: bit `bit` of v spread over a word (a constant shift pair once
+// `bit` is unrolled).
+__device__ __forceinline__ uint32_t bm32(unsigned v, int bit) {
+  return (uint32_t)((int32_t)(v << (31 - bit)) >> 31);
+}
 
 // Apply one fused Clifford op to this thread's G words wk[0..G) (entries
-// >= W are skipped): the op's 31 bit masks are expanded once for all G.
+// >= W are skipped): the op's 31 bit masks are expanded once for all G, as
+// 32-bit words, and each 64-row word is updated as two 32-bit halves.
 // The words are spread so that one load instruction of a warp touches each
 // shared-memory bank pair at most twice (see word_map below).
 template <int G>
 __device__ __forceinline__ void apply_op_g(CliffordOp op, uint64_t* tab, int W, int zb, const int (&wk)[G],
                                            uint64_t (&rd)[G]) {
   const unsigned M = op.M, A = op.anf;
-  uint64_t m[16], a[16];
+  uint32_t m[16], a[16];
 #pragma unroll
-  for (int i = 0; i < 16; ++i) { m[i] = bm(M, i); a[i] = bm(A, i); }
+  for (int i = 0; i < 16; ++i) { m[i] = bm32(M, i); a[i] = bm32(A, i); }
   uint64_t* pxa = tab + (size_t)op.qa * W;
   uint64_t* pza = tab + (size_t)(zb + op.qa) * W;
   uint64_t* pxb = tab + (size_t)op.qb * W;
@@ -45,15 +50,27 @@ __device__ __forceinline__ void apply_op_g(CliffordOp op, uint64_t* tab, int W, 
   for (int k = 0; k < G; ++k) {
     const int w = wk[k];
     if (G > 1 && w >= W) continue;
-    const uint64_t v0 = pxa[w], v1 = pza[w], v2 = pxb[w], v3 = pzb[w];
-    const uint64_t v01 = v0 & v1, v23 = v2 & v3;
-    rd[k] ^= (v0 & a[1]) ^ (v1 & a[2]) ^ (v01 & a[3]) ^ (v2 & a[4]) ^ ((v0 & v2) & a[5]) ^ ((v1 & v2) & a[6]) ^
-             ((v01 & v2) & a[7]) ^ (v3 & a[8]) ^ ((v0 & v3) & a[9]) ^ ((v1 & v3) & a[10]) ^ ((v01 & v3) & a[11]) ^
-             (v23 & a[12]) ^ ((v0 & v23) & a[13]) ^ ((v1 & v23) & a[14]) ^ ((v01 & v23) & a[15]);
-    pxa[w] = (v0 & m[0]) ^ (v1 & m[1]) ^ (v2 & m[2]) ^ (v3 & m[3]);
-    pza[w] = (v0 & m[4]) ^ (v1 & m[5]) ^ (v2 & m[6]) ^ (v3 & m[7]);
-    pxb[w] = (v0 & m[8]) ^ (v1 & m[9]) ^ (v2 & m[10]) ^ (v3 & m[11]);
-    pzb[w] = (v0 & m[12]) ^ (v1 & m[13]) ^ (v2 & m[14]) ^ (v3 & m[15]);
+    const uint64_t V0 = pxa[w], V1 = pza[w], V2 = pxb[w], V3 = pzb[w];
+    uint32_t r[2], u0[2], u1[2], u2[2], u3[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const uint32_t v0 = (uint32_t)(V0 >> (32 * h)), v1 = (uint32_t)(V1 >> (32 * h));
+      const uint32_t v2 = (uint32_t)(V2 >> (32 * h)), v3 = (uint32_t)(V3 >> (32 * h));
+      const uint32_t v01 = v0 & v1, v23 = v2 & v3;
+      r[h] = (v0 & a[1]) ^ (v1 & a[2]) ^ (v01 & a[3]) ^ (v2 & a[4]) ^ ((v0 & v2) & a[5]) ^ ((v1 & v2) & a[6]) ^
+             ((v01 & v2) & a[7]) ^ (v3 & a[8]) ^ ((v0 & v3) & a[9]) ^ ((v1 & v3) & a[10]) ^
+             ((v01 & v3) & a[11]) ^ (v23 & a[12]) ^ ((v0 & v23) & a[13]) ^ ((v1 & v23) & a[14]) ^
+             ((v01 & v23) & a[15]);
+      u0[h] = (v0 & m[0]) ^ (v1 & m[1]) ^ (v2 & m[2]) ^ (v3 & m[3]);
+      u1[h] = (v0 & m[4]) ^ (v1 & m[5]) ^ (v2 & m[6]) ^ (v3 & m[7]);
+      u2[h] = (v0 & m[8]) ^ (v1 & m[9]) ^ (v2 & m[10]) ^ (v3 & m[11]);
+      u3[h] = (v0 & m[12]) ^ (v1 & m[13]) ^ (v2 & m[14]) ^ (v3 & m[15]);
+    }
+    rd[k] ^= ((uint64_t)r[1] << 32) | r[0];
+    pxa[w] = ((uint64_t)u0[1] << 32) | u0[0];
+    pza[w] = ((uint64_t)u1[1] << 32) | u1[0];
+    pxb[w] = ((uint64_t)u2[1] << 32) | u2[0];
+    pzb[w] = ((uint64_t)u3[1] << 32) | u3[0];
   }
 }
 
@@ -244,10 +261,24 @@ __global__ void __launch_bounds__(256) body_kernel(DevPlan P, DevRes R, int smem
   const int* mom = staged ? mom_s : P.moments + F.mom_off;
   const int wk[1] = {0};
   uint64_t rd[1] = {0ull};
-  for (int mm = 0; mm < F.n_moments; ++mm) {
-    const int b0 = mom[mm], b1 = mom[mm + 1];
-    for (int o = b0 + tid; o < b1; o += nt) apply_op_g<1>(ops[o], tab, 1, zb, wk, rd);
-    __syncthreads();
+  if (F.n_moments > 0) {
+    // each thread's first op of the next moment is fetched while this
+    // moment's op is applied (the op stream does not depend on the tableau)
+    int b0 = mom[0], b1 = mom[1];
+    CliffordOp nxt{};
+    if (b0 + tid < b1) nxt = ops[b0 + tid];
+    for (int mm = 0; mm < F.n_moments; ++mm) {
+      const int c0 = b0, c1 = b1;
+      const CliffordOp cur = nxt;
+      if (mm + 1 < F.n_moments) {
+        b0 = c1;
+        b1 = mom[mm + 2];
+        if (b0 + tid < b1) nxt = ops[b0 + tid];
+      }
+      if (c0 + tid < c1) apply_op_g<1>(cur, tab, 1, zb, wk, rd);
+      for (int o = c0 + tid + nt; o < c1; o += nt) apply_op_g<1>(ops[o], tab, 1, zb, wk, rd);
+      __syncthreads();
+    }
   }
   atomicXor(reinterpret_cast<unsigned long long*>(&tab[rcol]), (unsigned long long)rd[0]);
   __syncthreads();
