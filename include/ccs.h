@@ -147,9 +147,11 @@ typedef struct {
  * fragment's variant list, compile its gates into moments of fused one- and
  * two-qubit Clifford updates (Clifford fragments) or 2x2 / 4x4 unitaries
  * (non-Clifford fragments), and upload the plan to the device.
- * Errors: INVALID_ARG (bad qubit index, cut position, marginal),
+ * Errors: INVALID_ARG (bad qubit index, cut position, marginal, Z^a
+ * exponent; an empty circuit; more than 2^24 qubits or 2^30 gates),
  * UNSUPPORTED_GATE, TOO_MANY_CUTS, NC_TOO_WIDE, UNSUPPORTED (a cut whose two
- * ends lie in the same fragment), OOM, CUDA. */
+ * ends lie in the same fragment), OOM (device, or a failed host
+ * allocation), CUDA. */
 int ccs_build_fragments(ccs_ctx ctx, const ccs_problem* problems, int n_problems,
                         const ccs_cut_opts* opts, ccs_plan* out);
 void ccs_plan_free(ccs_plan plan);

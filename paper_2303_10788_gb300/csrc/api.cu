@@ -1,5 +1,7 @@
 #include <thread>
 #include <atomic>
+#include <exception>
+#include <mutex>
 // C ABI of the circuit-cutting hot path (declared in include/ccs.h).
 #include <cuda_runtime.h>
 
@@ -11,6 +13,7 @@
 #include <tuple>
 #include <vector>
 
+#include "abi_guard.hpp"
 #include "kernels.cuh"
 #include "plan.hpp"
 
@@ -136,13 +139,25 @@ void parallel_for(int n, F&& f) {
     for (int i = 0; i < n; ++i) f(i);
     return;
   }
+  // an exception in a worker is carried to the calling thread (the first
+  // one wins; the other items still run)
   std::atomic<int> next{0};
+  std::exception_ptr first;
+  std::mutex mu;
   std::vector<std::thread> th;
   for (int t = 0; t < T; ++t)
     th.emplace_back([&] {
-      for (int i = next.fetch_add(1); i < n; i = next.fetch_add(1)) f(i);
+      for (int i = next.fetch_add(1); i < n; i = next.fetch_add(1)) {
+        try {
+          f(i);
+        } catch (...) {
+          std::lock_guard<std::mutex> lk(mu);
+          if (!first) first = std::current_exception();
+        }
+      }
     });
   for (auto& x : th) x.join();
+  if (first) std::rethrow_exception(first);
 }
 
 // Host arrays gathered into one pinned buffer and sent with one copy.
@@ -307,34 +322,39 @@ static int learned_pick(ccs_ctx c, const Problem& P, const std::vector<CutCandid
 extern "C" {
 
 int ccs_set_cut_model(ccs_ctx c, ccs_mpnn net) {
-  if (!c) return CCS_ERR_INVALID_ARG;
-  c->cut_model = net;
-  return CCS_OK;
+  return abi_guard([&](int code, const char* m) { return fail(c, code, m); }, [&]() -> int {
+    if (!c) return CCS_ERR_INVALID_ARG;
+    c->cut_model = net;
+    return CCS_OK;
+  });
 }
 
 int ccs_featurize(ccs_ctx c, const ccs_problem* q, const ccs_cut* cuts, int n_cuts, float* x, int32_t* rowptr,
                   int32_t* col, float* val, float* val_t, int cap_nnz, float* glob) {
-  if (!c || !q || (n_cuts > 0 && !cuts) || !x || !rowptr || !glob) return fail(c, CCS_ERR_INVALID_ARG, "bad arguments");
-  Problem P;
-  P.n_qubits = q->n_qubits;
-  std::string err;
-  if (q->n_gates && !q->gates) return fail(c, CCS_ERR_INVALID_ARG, "null gate list");
-  int rc = load_gates(q->gates, q->n_gates, P.gates, P.gparam, err);
-  if (rc != CCS_OK) return fail(c, rc, err);
-  P.marginal.assign(q->marginal, q->marginal + q->n_marginal);
-  std::vector<ccs_cut> cs(cuts, cuts + std::max(0, n_cuts));
-  std::vector<float> X, v, vt, g;
-  std::vector<int> rp, cl;
-  rc = featurize(P, cs, X, rp, cl, v, vt, g, err);
-  if (rc != CCS_OK) return fail(c, rc, err);
-  if ((int)cl.size() > cap_nnz) return fail(c, CCS_ERR_INVALID_ARG, "edge buffer too small");
-  std::copy(X.begin(), X.end(), x);
-  std::copy(rp.begin(), rp.end(), rowptr);
-  std::copy(cl.begin(), cl.end(), col);
-  if (val) std::copy(v.begin(), v.end(), val);
-  if (val_t) std::copy(vt.begin(), vt.end(), val_t);
-  std::copy(g.begin(), g.end(), glob);
-  return (int)cl.size();
+  return abi_guard([&](int code, const char* m) { return fail(c, code, m); }, [&]() -> int {
+    if (!c || !q || (n_cuts > 0 && !cuts) || !x || !rowptr || !glob) return fail(c, CCS_ERR_INVALID_ARG, "bad arguments");
+    Problem P;
+    P.n_qubits = q->n_qubits;
+    std::string err;
+    int rc = check_circuit(*q, err);
+    if (rc != CCS_OK) return fail(c, rc, err);
+    rc = load_gates(q->gates, q->n_gates, P.gates, P.gparam, err);
+    if (rc != CCS_OK) return fail(c, rc, err);
+    P.marginal.assign(q->marginal, q->marginal + q->n_marginal);
+    std::vector<ccs_cut> cs(cuts, cuts + std::max(0, n_cuts));
+    std::vector<float> X, v, vt, g;
+    std::vector<int> rp, cl;
+    rc = featurize(P, cs, X, rp, cl, v, vt, g, err);
+    if (rc != CCS_OK) return fail(c, rc, err);
+    if ((int)cl.size() > cap_nnz) return fail(c, CCS_ERR_INVALID_ARG, "edge buffer too small");
+    std::copy(X.begin(), X.end(), x);
+    std::copy(rp.begin(), rp.end(), rowptr);
+    std::copy(cl.begin(), cl.end(), col);
+    if (val) std::copy(v.begin(), v.end(), val);
+    if (val_t) std::copy(vt.begin(), vt.end(), val_t);
+    std::copy(g.begin(), g.end(), glob);
+    return (int)cl.size();
+  });
 }
 
 long long ccs_launch_count(void) { return launch_count(); }
@@ -342,38 +362,40 @@ long long ccs_launch_count(void) { return launch_count(); }
 const char* ccs_version(void) { return "ccs 0.1 (sm_103a)"; }
 
 int ccs_create(ccs_ctx* out, int device, void* cuda_stream, const ccs_allocator* alloc) {
-  if (!out) return CCS_ERR_INVALID_ARG;
-  *out = nullptr;
-  if (device < 0) {   // host-only context: fragments and plans can be built and inspected
+  return abi_guard([](int code, const char*) { return code; }, [&]() -> int {
+    if (!out) return CCS_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (device < 0) {   // host-only context: fragments and plans can be built and inspected
+      ccs_ctx c = new ccs_ctx_s();
+      c->device = -1;
+      c->host_only = true;
+      c->smem_optin = 227 * 1024;
+      *out = c;
+      return CCS_OK;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return CCS_ERR_CUDA;
     ccs_ctx c = new ccs_ctx_s();
-    c->device = -1;
-    c->host_only = true;
-    c->smem_optin = 227 * 1024;
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    if (alloc && alloc->alloc && alloc->free) {
+      c->alloc = *alloc;
+      c->own_alloc = false;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) { delete c; return CCS_ERR_CUDA; }
+    cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming) != cudaSuccess) {
+      delete c;
+      return CCS_ERR_CUDA;
+    }
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    c->smem_optin = (size_t)optin;
     *out = c;
     return CCS_OK;
-  }
-  int ndev = 0;
-  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return CCS_ERR_CUDA;
-  ccs_ctx c = new ccs_ctx_s();
-  c->device = device;
-  c->stream = (cudaStream_t)cuda_stream;
-  if (alloc && alloc->alloc && alloc->free) {
-    c->alloc = *alloc;
-    c->own_alloc = false;
-  }
-  if (cudaSetDevice(device) != cudaSuccess) { delete c; return CCS_ERR_CUDA; }
-  cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
-  if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming) != cudaSuccess) {
-    delete c;
-    return CCS_ERR_CUDA;
-  }
-  int optin = 0;
-  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
-  c->smem_optin = (size_t)optin;
-  *out = c;
-  return CCS_OK;
+  });
 }
 
 void ccs_destroy(ccs_ctx c) {
@@ -388,499 +410,509 @@ void ccs_destroy(ccs_ctx c) {
 }
 
 int ccs_set_profiling(ccs_ctx c, int on) {
-  if (!c) return CCS_ERR_INVALID_ARG;
-  if (c->host_only) return fail(c, CCS_ERR_UNSUPPORTED, "host-only context");
-  c->profiling = on != 0;
-  c->stage_mask = 0;
-  return CCS_OK;
+  return abi_guard([&](int code, const char* m) { return fail(c, code, m); }, [&]() -> int {
+    if (!c) return CCS_ERR_INVALID_ARG;
+    if (c->host_only) return fail(c, CCS_ERR_UNSUPPORTED, "host-only context");
+    c->profiling = on != 0;
+    c->stage_mask = 0;
+    return CCS_OK;
+  });
 }
 
 int ccs_get_stage_times(ccs_ctx c, double* ms, int cap) {
-  if (!c || !ms || cap < ST_N) return fail(c, CCS_ERR_INVALID_ARG, "bad arguments");
-  if (c->host_only || !c->profiling) return fail(c, CCS_ERR_UNSUPPORTED, "profiling is off");
-  cudaError_t e = cudaStreamSynchronize(c->stream);
-  if (e != cudaSuccess) return cuda_fail(c, e, "synchronize");
-  for (int st = 0; st < ST_N; ++st) {
-    ms[st] = -1.0;
-    if (c->stage_mask & (1 << st)) {
-      float t = 0.f;
-      if (cudaEventElapsedTime(&t, c->ev[2 * st], c->ev[2 * st + 1]) == cudaSuccess) ms[st] = t;
+  return abi_guard([&](int code, const char* m) { return fail(c, code, m); }, [&]() -> int {
+    if (!c || !ms || cap < ST_N) return fail(c, CCS_ERR_INVALID_ARG, "bad arguments");
+    if (c->host_only || !c->profiling) return fail(c, CCS_ERR_UNSUPPORTED, "profiling is off");
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "synchronize");
+    for (int st = 0; st < ST_N; ++st) {
+      ms[st] = -1.0;
+      if (c->stage_mask & (1 << st)) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, c->ev[2 * st], c->ev[2 * st + 1]) == cudaSuccess) ms[st] = t;
+      }
     }
-  }
-  return ST_N;
+    return ST_N;
+  });
 }
 
 const char* ccs_last_error(ccs_ctx c) { return c ? c->err.c_str() : "null context"; }
 
 int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, const ccs_cut_opts* opts,
                         ccs_plan* out) {
-  if (!c || !out || (n_problems > 0 && !probs) || n_problems < 0) return fail(c, CCS_ERR_INVALID_ARG, "bad arguments");
-  *out = nullptr;
-  if (!c->host_only) cudaSetDevice(c->device);
-  ccs_cut_opts o{kMaxCuts, 10, 0};
-  if (opts) o = *opts;
-  auto plan = new ccs_plan_s();
-  plan->ctx = c;
-  plan->A.ctx = c;
-  std::string err;
-  // Per problem, on host threads: parse, cut search (if asked), fragment
-  // and compile.  Results are joined in problem order, so the plan does not
-  // depend on the thread count.
-  const int np = n_problems;
-  std::vector<Problem> pr(np);
-  std::vector<std::vector<Frag>> pf(np);
-  std::vector<std::vector<CutCandidate>> pc(np);
-  std::vector<int> prc(np, CCS_OK);
-  std::vector<std::string> perr(np);
-  parallel_for(np, [&](int pi) {
-    const ccs_problem& q = probs[pi];
-    Problem& P = pr[pi];
-    P.n_qubits = q.n_qubits;
-    if (q.n_qubits == 0 || (q.n_gates && !q.gates)) { prc[pi] = CCS_ERR_INVALID_ARG; perr[pi] = "empty circuit"; return; }
-    prc[pi] = load_gates(q.gates, q.n_gates, P.gates, P.gparam, perr[pi]);
-    if (prc[pi] != CCS_OK) return;
-    P.marginal.assign(q.marginal, q.marginal + q.n_marginal);
-    for (uint32_t z = 0; z < q.n_zstrings; ++z)
-      P.zstrings.emplace_back(q.zstring_qubits + q.zstring_offsets[z], q.zstring_qubits + q.zstring_offsets[z + 1]);
-    if (q.n_cuts >= 0) {
-      if (q.n_cuts > 0 && !q.cuts) { prc[pi] = CCS_ERR_INVALID_ARG; perr[pi] = "null cut list"; return; }
-      P.cuts.assign(q.cuts, q.cuts + q.n_cuts);
-      if ((int)P.cuts.size() > o.max_cuts) { prc[pi] = CCS_ERR_TOO_MANY_CUTS; perr[pi] = "too many cuts"; return; }
-    } else {
-      CutSearchOpts so;
-      so.max_cuts = std::min(o.max_cuts, kMaxCuts);
-      so.max_nc_width = std::min(o.max_nc_width > 0 ? o.max_nc_width : 10, kMaxNCWidth);
-      prc[pi] = greedy_cuts(P, so, pc[pi], perr[pi]);
+  return abi_guard([&](int code, const char* m) { return fail(c, code, m); }, [&]() -> int {
+    if (!c || !out || (n_problems > 0 && !probs) || n_problems < 0) return fail(c, CCS_ERR_INVALID_ARG, "bad arguments");
+    *out = nullptr;
+    if (!c->host_only) cudaSetDevice(c->device);
+    ccs_cut_opts o{kMaxCuts, 10, 0};
+    if (opts) o = *opts;
+    auto plan = new ccs_plan_s();
+    plan->ctx = c;
+    plan->A.ctx = c;
+    std::string err;
+    // Per problem, on host threads: parse, cut search (if asked), fragment
+    // and compile.  Results are joined in problem order, so the plan does not
+    // depend on the thread count.
+    const int np = n_problems;
+    std::vector<Problem> pr(np);
+    std::vector<std::vector<Frag>> pf(np);
+    std::vector<std::vector<CutCandidate>> pc(np);
+    std::vector<int> prc(np, CCS_OK);
+    std::vector<std::string> perr(np);
+    parallel_for(np, [&](int pi) {
+      const ccs_problem& q = probs[pi];
+      Problem& P = pr[pi];
+      P.n_qubits = q.n_qubits;
+      prc[pi] = check_circuit(q, perr[pi]);
       if (prc[pi] != CCS_OK) return;
-      P.cuts = pc[pi].front().cuts;
-    }
-  });
-  for (int pi = 0; pi < np; ++pi)
-    if (prc[pi] != CCS_OK) { delete plan; return fail(c, prc[pi], perr[pi]); }
-  // the learned choice runs the scorer on the GPU: one problem at a time
-  if (o.use_learned && c->cut_model && !c->host_only)
+      prc[pi] = load_gates(q.gates, q.n_gates, P.gates, P.gparam, perr[pi]);
+      if (prc[pi] != CCS_OK) return;
+      P.marginal.assign(q.marginal, q.marginal + q.n_marginal);
+      for (uint32_t z = 0; z < q.n_zstrings; ++z)
+        P.zstrings.emplace_back(q.zstring_qubits + q.zstring_offsets[z], q.zstring_qubits + q.zstring_offsets[z + 1]);
+      if (q.n_cuts >= 0) {
+        if (q.n_cuts > 0 && !q.cuts) { prc[pi] = CCS_ERR_INVALID_ARG; perr[pi] = "null cut list"; return; }
+        P.cuts.assign(q.cuts, q.cuts + q.n_cuts);
+        if ((int)P.cuts.size() > o.max_cuts) { prc[pi] = CCS_ERR_TOO_MANY_CUTS; perr[pi] = "too many cuts"; return; }
+      } else {
+        CutSearchOpts so;
+        so.max_cuts = std::min(o.max_cuts, kMaxCuts);
+        so.max_nc_width = std::min(o.max_nc_width > 0 ? o.max_nc_width : 10, kMaxNCWidth);
+        prc[pi] = greedy_cuts(P, so, pc[pi], perr[pi]);
+        if (prc[pi] != CCS_OK) return;
+        P.cuts = pc[pi].front().cuts;
+      }
+    });
     for (int pi = 0; pi < np; ++pi)
-      if (pc[pi].size() > 1) {
-        int pick = 0;
-        int rc = learned_pick(c, pr[pi], pc[pi], &pick);
-        if (rc != CCS_OK) { delete plan; return rc; }
-        pr[pi].cuts = pc[pi][pick].cuts;
-      }
-  parallel_for(np, [&](int pi) {
-    prc[pi] = fragment_problem(pr[pi], pi, pf[pi], perr[pi]);
-    if (prc[pi] != CCS_OK) return;
-    for (auto& f : pf[pi]) {
-      if (f.clifford) compile_clifford(f);
-      else compile_nc(f);
-    }
-  });
-  for (int pi = 0; pi < np; ++pi)
-    if (prc[pi] != CCS_OK) { delete plan; return fail(c, prc[pi], "problem " + std::to_string(pi) + ": " + perr[pi]); }
-  for (int pi = 0; pi < np; ++pi) {
-    const int base = (int)plan->frags.size();      // fragment ids become plan-global
-    for (auto& id : pr[pi].frag_ids) id += base;
-    for (auto& f : pf[pi]) plan->frags.push_back(std::move(f));
-    plan->problems.push_back(std::move(pr[pi]));
-  }
-
-  // --- flatten ---------------------------------------------------------------
-  std::vector<CliffordOp> cops;
-  std::vector<NCOp> nops;
-  std::vector<int> moments, wires, zoffs;
-  std::vector<int2> items_c, items_nc, items_b, items_z, zblocks;
-  std::vector<int> nc_frags;
-  std::vector<int> cliff_frags;
-  int img_words_max = 0, body_words_max = 0;
-  int max_body_stage = 0, max_moment_ops = 1;
-  int max_body_cols = 0;
-  std::vector<long long> cost_c, cost_nc;
-  for (size_t fi = 0; fi < plan->frags.size(); ++fi) {
-    Frag& f = plan->frags[fi];
-    FragDev d{};
-    d.n = f.n();
-    d.Wh = (d.n + 63) / 64;
-    d.W = 2 * d.Wh;
-    d.nA = f.n_meas();
-    d.m = (int)f.marg_wire.size();
-    d.qin = (int)f.qin_wire.size();
-    d.qout = (int)f.qout_wire.size();
-    d.nv = f.n_variants();
-    d.clifford = f.clifford ? 1 : 0;
-    d.problem = f.problem;
-    d.findex = f.index;
-    d.ops_off = f.clifford ? (int)cops.size() : (int)nops.size();
-    d.mom_off = (int)moments.size();
-    d.n_moments = f.n_moments();
-    for (int x : f.moment_start) moments.push_back(x);
-    if (f.clifford) cops.insert(cops.end(), f.cops.begin(), f.cops.end());
-    else nops.insert(nops.end(), f.nops.begin(), f.nops.end());
-    d.A_off = (int)wires.size();
-    for (int w : f.marg_wire) wires.push_back(w);
-    for (int w : f.qout_wire) wires.push_back(w);
-    d.qin_off = (int)wires.size();
-    for (int w : f.qin_wire) wires.push_back(w);
-    d.qout_off = (int)wires.size();
-    for (int w : f.qout_wire) wires.push_back(w);
-    d.nz = (int)f.zwires.size();
-    d.zw_off = (int)zoffs.size();
-    for (auto& zw : f.zwires) {
-      zoffs.push_back((int)wires.size());
-      for (int w : zw) wires.push_back(w);
-    }
-    zoffs.push_back((int)wires.size());
-    d.n_slots = (int)f.slots.size();
-    for (int j = 0; j < d.n_slots; ++j) {
-      d.slot_code[j] = (f.slot_kind[j] << 8) | f.slot_idx[j];
-      d.slot_cut[j] = f.slots[j];
-    }
-    for (int j = 0; j < d.m; ++j) d.marg_pos[j] = f.marg_pos[j];
-    const long long outs = 1ll << d.nA;
-    if (f.clifford) {
-      d.space_off = plan->n_spaces;
-      plan->n_spaces += d.nv;
-      d.counts_off = plan->n_counts;
-      plan->n_counts += (long long)d.nv * outs;
-      d.tab_off = plan->n_tab;
-      plan->n_tab += (long long)d.nv * (2 * d.n + 3) * d.W;
-      d.body_off = plan->n_body;      // even: (2n+3)*W is even, so 16-byte aligned
-      plan->n_body += (long long)(2 * d.n + 3) * d.W;
-      d.rb_off = (long long)kRowBasisWords * (long long)cliff_frags.size();
-      cliff_frags.push_back((int)fi);
-      d.pb_off = -1;
-      if (d.qout <= kMaxPbQout) {
-        int combos = 1;
-        for (int o = 0; o < d.qout; ++o) combos *= 3;
-        d.pb_off = plan->n_pbasis;
-        plan->n_pbasis += 25ll * combos;
-      }
-      {   // Z images: every string, X, Y, Z of every quantum output, Z of every marginal wire
-        const int ni = d.nz + 3 * d.qout + d.m;
-        d.zimg_off = plan->n_zimg;
-        plan->n_zimg += (long long)ni * (2 * d.Wh + 1);
-        img_words_max = std::max(img_words_max, ni * (2 * d.Wh + 1));
-        body_words_max = std::max(body_words_max, (2 * d.n + 3) * d.W);
-        for (int k = 0; k < ni; ++k) items_z.push_back(make_int2((int)fi, k));
-        if (d.nz > 0)
-          for (int v = 0; v < d.nv; v += zblock_variants(d.nz)) zblocks.push_back(make_int2((int)fi, v));
-      }
-      max_body_stage = std::max(max_body_stage, 2 * d.n + 3 + (int)f.cops.size() + (d.n_moments + 2) / 2 + 1);
-      for (int mm = 0; mm < f.n_moments(); ++mm)
-        max_moment_ops = std::max(max_moment_ops, f.moment_start[mm + 1] - f.moment_start[mm]);
-      for (int w = 0; w < d.W; ++w) items_b.push_back(make_int2((int)fi, w));
-      max_body_cols = std::max(max_body_cols, 2 * d.n + 3);
-      const int words = (2 * d.n + 3) * d.W + (d.n + 1) / 2 + 2;
-      const int staged = words + (int)f.cops.size() + (d.n_moments + 2) / 2 + 2;   // + op stream
-      plan->cliff_smem_words =
-          std::max(plan->cliff_smem_words, (size_t)staged * 8 <= c->smem_optin ? staged : words);
-      plan->body_smem_words = std::max(plan->body_smem_words, words);
-      for (int v = 0; v < d.nv; ++v) {
-        items_c.push_back(make_int2((int)fi, v));
-        cost_c.push_back((long long)d.W * (d.n_moments + 4) * std::max(1, d.n / 16) + d.nz * 4 + d.nA * d.n);
-      }
-    } else {
-      d.space_off = d.counts_off = d.tab_off = d.body_off = d.rb_off = d.zimg_off = d.pb_off = -1;
-      plan->max_nc_n = std::max(plan->max_nc_n, d.n);
-      nc_frags.push_back((int)fi);
-    }
-    d.dist_off = plan->n_dist;
-    plan->n_dist += (long long)d.nv * outs;
-    d.zval_off = plan->n_zval;
-    plan->n_zval += (long long)d.nv * d.nz * (1ll << d.qout);
-    d.T_off = (plan->n_T + 63) & ~63ll;     // 256-byte aligned (TMA needs 16)
-    plan->n_T = d.T_off + (1ll << d.m) * (1ll << (2 * d.n_slots));
-    plan->fdev.push_back(d);
-  }
-  {   // distributions: statevector fragments first (all a sampled evaluation needs), then Clifford
-    long long off = 0;
-    for (auto& f : plan->fdev)
-      if (!f.clifford) { f.dist_off = off; off += (long long)f.nv << f.nA; }
-    plan->n_dist_nc = off;
-    for (auto& f : plan->fdev)
-      if (f.clifford) { f.dist_off = off; off += (long long)f.nv << f.nA; }
-  }
-  if ((size_t)plan->cliff_smem_words * 8 > c->smem_optin && !items_c.empty()) {
-    delete plan;
-    return fail(c, CCS_ERR_UNSUPPORTED, "Clifford fragment does not fit in shared memory");
-  }
-  // Items costliest first, ties in insertion order.  A fragment's items are
-  // consecutive and cost the same, so the runs of equal cost are sorted
-  // stably instead of the items (the same order, far fewer comparisons).
-  auto sort_items = [](std::vector<int2>& it, std::vector<long long>& cost) {
-    std::vector<std::pair<size_t, size_t>> runs;
-    for (size_t i = 0; i < it.size();) {
-      size_t j = i + 1;
-      while (j < it.size() && cost[j] == cost[i]) ++j;
-      runs.push_back({i, j});
-      i = j;
-    }
-    std::stable_sort(runs.begin(), runs.end(),
-                     [&](const std::pair<size_t, size_t>& a, const std::pair<size_t, size_t>& b) {
-                       return cost[a.first] > cost[b.first];
-                     });
-    std::vector<int2> out;
-    out.reserve(it.size());
-    for (auto& r : runs) out.insert(out.end(), it.begin() + r.first, it.begin() + r.second);
-    it.swap(out);
-  };
-  sort_items(items_c, cost_c);
-  // Non-Clifford items: with enough variants to fill the GPU, one item per
-  // preparation combination (the gates run once, every basis combination of
-  // the outputs is applied to a copy of the state); otherwise one per variant
-  // (latency: no serial basis tails).
-  {
-    long long nc_total = 0;
-    for (int fi : nc_frags) nc_total += plan->fdev[fi].nv;
-    const int chunk = nc_total > 2ll * std::max(c->sm_count, 148) ? 1 << 30 : 1;
-    plan->nc_basis_chunk = chunk;
-    for (int fi : nc_frags) {
-      const FragDev& d = plan->fdev[fi];
-      const int n_prep = 1 << (2 * d.qin), n_basis = d.nv / n_prep;
-      const long long nops = plan->frags[fi].nops.size();
-      for (int b0 = 0; b0 < n_basis; b0 += std::min(chunk, n_basis))
-        for (int pc = 0; pc < n_prep; ++pc) {
-          items_nc.push_back(make_int2(fi, pc + n_prep * b0));
-          cost_nc.push_back((1ll << d.n) * (nops + 4 + 8ll * std::min(chunk, n_basis - b0)));
+      if (prc[pi] != CCS_OK) { delete plan; return fail(c, prc[pi], perr[pi]); }
+    // the learned choice runs the scorer on the GPU: one problem at a time
+    if (o.use_learned && c->cut_model && !c->host_only)
+      for (int pi = 0; pi < np; ++pi)
+        if (pc[pi].size() > 1) {
+          int pick = 0;
+          int rc = learned_pick(c, pr[pi], pc[pi], &pick);
+          if (rc != CCS_OK) { delete plan; return rc; }
+          pr[pi].cuts = pc[pi][pick].cuts;
         }
+    parallel_for(np, [&](int pi) {
+      prc[pi] = fragment_problem(pr[pi], pi, pf[pi], perr[pi]);
+      if (prc[pi] != CCS_OK) return;
+      for (auto& f : pf[pi]) {
+        if (f.clifford) compile_clifford(f);
+        else compile_nc(f);
+      }
+    });
+    for (int pi = 0; pi < np; ++pi)
+      if (prc[pi] != CCS_OK) { delete plan; return fail(c, prc[pi], "problem " + std::to_string(pi) + ": " + perr[pi]); }
+    for (int pi = 0; pi < np; ++pi) {
+      const int base = (int)plan->frags.size();      // fragment ids become plan-global
+      for (auto& id : pr[pi].frag_ids) id += base;
+      for (auto& f : pf[pi]) plan->frags.push_back(std::move(f));
+      plan->problems.push_back(std::move(pr[pi]));
     }
-  }
-  sort_items(items_nc, cost_nc);
 
-  int f0 = 0;
-  plan->t_prefix.push_back(0);
-  plan->out_prefix.push_back(0);
-  plan->z_prefix.push_back(0);
-  plan->r_prefix.push_back(0);
-  plan->blk_prefix.push_back(0);
-  for (auto& f : plan->fdev) {
-    plan->t_prefix.push_back(plan->t_prefix.back() + (1ll << f.m) * (1ll << (2 * f.n_slots)));
-  }
-  // roles in star problems: the hub's contraction operand is Q, the others' T'
-  {
-    int f0r = 0;
+    // --- flatten ---------------------------------------------------------------
+    std::vector<CliffordOp> cops;
+    std::vector<NCOp> nops;
+    std::vector<int> moments, wires, zoffs;
+    std::vector<int2> items_c, items_nc, items_b, items_z, zblocks;
+    std::vector<int> nc_frags;
+    std::vector<int> cliff_frags;
+    int img_words_max = 0, body_words_max = 0;
+    int max_body_stage = 0, max_moment_ops = 1;
+    int max_body_cols = 0;
+    std::vector<long long> cost_c, cost_nc;
+    for (size_t fi = 0; fi < plan->frags.size(); ++fi) {
+      Frag& f = plan->frags[fi];
+      FragDev d{};
+      d.n = f.n();
+      d.Wh = (d.n + 63) / 64;
+      d.W = 2 * d.Wh;
+      d.nA = f.n_meas();
+      d.m = (int)f.marg_wire.size();
+      d.qin = (int)f.qin_wire.size();
+      d.qout = (int)f.qout_wire.size();
+      d.nv = f.n_variants();
+      d.clifford = f.clifford ? 1 : 0;
+      d.problem = f.problem;
+      d.findex = f.index;
+      d.ops_off = f.clifford ? (int)cops.size() : (int)nops.size();
+      d.mom_off = (int)moments.size();
+      d.n_moments = f.n_moments();
+      for (int x : f.moment_start) moments.push_back(x);
+      if (f.clifford) cops.insert(cops.end(), f.cops.begin(), f.cops.end());
+      else nops.insert(nops.end(), f.nops.begin(), f.nops.end());
+      d.A_off = (int)wires.size();
+      for (int w : f.marg_wire) wires.push_back(w);
+      for (int w : f.qout_wire) wires.push_back(w);
+      d.qin_off = (int)wires.size();
+      for (int w : f.qin_wire) wires.push_back(w);
+      d.qout_off = (int)wires.size();
+      for (int w : f.qout_wire) wires.push_back(w);
+      d.nz = (int)f.zwires.size();
+      d.zw_off = (int)zoffs.size();
+      for (auto& zw : f.zwires) {
+        zoffs.push_back((int)wires.size());
+        for (int w : zw) wires.push_back(w);
+      }
+      zoffs.push_back((int)wires.size());
+      d.n_slots = (int)f.slots.size();
+      for (int j = 0; j < d.n_slots; ++j) {
+        d.slot_code[j] = (f.slot_kind[j] << 8) | f.slot_idx[j];
+        d.slot_cut[j] = f.slots[j];
+      }
+      for (int j = 0; j < d.m; ++j) d.marg_pos[j] = f.marg_pos[j];
+      const long long outs = 1ll << d.nA;
+      if (f.clifford) {
+        d.space_off = plan->n_spaces;
+        plan->n_spaces += d.nv;
+        d.counts_off = plan->n_counts;
+        plan->n_counts += (long long)d.nv * outs;
+        d.tab_off = plan->n_tab;
+        plan->n_tab += (long long)d.nv * (2 * d.n + 3) * d.W;
+        d.body_off = plan->n_body;      // even: (2n+3)*W is even, so 16-byte aligned
+        plan->n_body += (long long)(2 * d.n + 3) * d.W;
+        d.rb_off = (long long)kRowBasisWords * (long long)cliff_frags.size();
+        cliff_frags.push_back((int)fi);
+        d.pb_off = -1;
+        if (d.qout <= kMaxPbQout) {
+          int combos = 1;
+          for (int o = 0; o < d.qout; ++o) combos *= 3;
+          d.pb_off = plan->n_pbasis;
+          plan->n_pbasis += 25ll * combos;
+        }
+        {   // Z images: every string, X, Y, Z of every quantum output, Z of every marginal wire
+          const int ni = d.nz + 3 * d.qout + d.m;
+          d.zimg_off = plan->n_zimg;
+          plan->n_zimg += (long long)ni * (2 * d.Wh + 1);
+          img_words_max = std::max(img_words_max, ni * (2 * d.Wh + 1));
+          body_words_max = std::max(body_words_max, (2 * d.n + 3) * d.W);
+          for (int k = 0; k < ni; ++k) items_z.push_back(make_int2((int)fi, k));
+          if (d.nz > 0)
+            for (int v = 0; v < d.nv; v += zblock_variants(d.nz)) zblocks.push_back(make_int2((int)fi, v));
+        }
+        max_body_stage = std::max(max_body_stage, 2 * d.n + 3 + (int)f.cops.size() + (d.n_moments + 2) / 2 + 1);
+        for (int mm = 0; mm < f.n_moments(); ++mm)
+          max_moment_ops = std::max(max_moment_ops, f.moment_start[mm + 1] - f.moment_start[mm]);
+        for (int w = 0; w < d.W; ++w) items_b.push_back(make_int2((int)fi, w));
+        max_body_cols = std::max(max_body_cols, 2 * d.n + 3);
+        const int words = (2 * d.n + 3) * d.W + (d.n + 1) / 2 + 2;
+        const int staged = words + (int)f.cops.size() + (d.n_moments + 2) / 2 + 2;   // + op stream
+        plan->cliff_smem_words =
+            std::max(plan->cliff_smem_words, (size_t)staged * 8 <= c->smem_optin ? staged : words);
+        plan->body_smem_words = std::max(plan->body_smem_words, words);
+        for (int v = 0; v < d.nv; ++v) {
+          items_c.push_back(make_int2((int)fi, v));
+          cost_c.push_back((long long)d.W * (d.n_moments + 4) * std::max(1, d.n / 16) + d.nz * 4 + d.nA * d.n);
+        }
+      } else {
+        d.space_off = d.counts_off = d.tab_off = d.body_off = d.rb_off = d.zimg_off = d.pb_off = -1;
+        plan->max_nc_n = std::max(plan->max_nc_n, d.n);
+        nc_frags.push_back((int)fi);
+      }
+      d.dist_off = plan->n_dist;
+      plan->n_dist += (long long)d.nv * outs;
+      d.zval_off = plan->n_zval;
+      plan->n_zval += (long long)d.nv * d.nz * (1ll << d.qout);
+      d.T_off = (plan->n_T + 63) & ~63ll;     // 256-byte aligned (TMA needs 16)
+      plan->n_T = d.T_off + (1ll << d.m) * (1ll << (2 * d.n_slots));
+      plan->fdev.push_back(d);
+    }
+    {   // distributions: statevector fragments first (all a sampled evaluation needs), then Clifford
+      long long off = 0;
+      for (auto& f : plan->fdev)
+        if (!f.clifford) { f.dist_off = off; off += (long long)f.nv << f.nA; }
+      plan->n_dist_nc = off;
+      for (auto& f : plan->fdev)
+        if (f.clifford) { f.dist_off = off; off += (long long)f.nv << f.nA; }
+    }
+    if ((size_t)plan->cliff_smem_words * 8 > c->smem_optin && !items_c.empty()) {
+      delete plan;
+      return fail(c, CCS_ERR_UNSUPPORTED, "Clifford fragment does not fit in shared memory");
+    }
+    // Items costliest first, ties in insertion order.  A fragment's items are
+    // consecutive and cost the same, so the runs of equal cost are sorted
+    // stably instead of the items (the same order, far fewer comparisons).
+    auto sort_items = [](std::vector<int2>& it, std::vector<long long>& cost) {
+      std::vector<std::pair<size_t, size_t>> runs;
+      for (size_t i = 0; i < it.size();) {
+        size_t j = i + 1;
+        while (j < it.size() && cost[j] == cost[i]) ++j;
+        runs.push_back({i, j});
+        i = j;
+      }
+      std::stable_sort(runs.begin(), runs.end(),
+                       [&](const std::pair<size_t, size_t>& a, const std::pair<size_t, size_t>& b) {
+                         return cost[a.first] > cost[b.first];
+                       });
+      std::vector<int2> out;
+      out.reserve(it.size());
+      for (auto& r : runs) out.insert(out.end(), it.begin() + r.first, it.begin() + r.second);
+      it.swap(out);
+    };
+    sort_items(items_c, cost_c);
+    // Non-Clifford items: with enough variants to fill the GPU, one item per
+    // preparation combination (the gates run once, every basis combination of
+    // the outputs is applied to a copy of the state); otherwise one per variant
+    // (latency: no serial basis tails).
+    {
+      long long nc_total = 0;
+      for (int fi : nc_frags) nc_total += plan->fdev[fi].nv;
+      const int chunk = nc_total > 2ll * std::max(c->sm_count, 148) ? 1 << 30 : 1;
+      plan->nc_basis_chunk = chunk;
+      for (int fi : nc_frags) {
+        const FragDev& d = plan->fdev[fi];
+        const int n_prep = 1 << (2 * d.qin), n_basis = d.nv / n_prep;
+        const long long nops = plan->frags[fi].nops.size();
+        for (int b0 = 0; b0 < n_basis; b0 += std::min(chunk, n_basis))
+          for (int pc = 0; pc < n_prep; ++pc) {
+            items_nc.push_back(make_int2(fi, pc + n_prep * b0));
+            cost_nc.push_back((1ll << d.n) * (nops + 4 + 8ll * std::min(chunk, n_basis - b0)));
+          }
+      }
+    }
+    sort_items(items_nc, cost_nc);
+
+    int f0 = 0;
+    plan->t_prefix.push_back(0);
+    plan->out_prefix.push_back(0);
+    plan->z_prefix.push_back(0);
+    plan->r_prefix.push_back(0);
+    plan->blk_prefix.push_back(0);
+    for (auto& f : plan->fdev) {
+      plan->t_prefix.push_back(plan->t_prefix.back() + (1ll << f.m) * (1ll << (2 * f.n_slots)));
+    }
+    // roles in star problems: the hub's contraction operand is Q, the others' T'
+    {
+      int f0r = 0;
+      for (auto& P : plan->problems) {
+        const int nfr = (int)P.frag_ids.size();
+        if (P.hub >= 0)
+          for (int l = 0; l < nfr; ++l) plan->fdev[f0r + l].role = (l == P.hub) ? 1 : 2;
+        f0r += nfr;
+      }
+    }
+    // shot counts: non-hub Clifford fragments first (they are zeroed before
+    // sampling), hub fragments after (written whole by the fused sampler)
+    {
+      long long off = 0;
+      for (auto& f : plan->fdev)
+        if (f.clifford && f.role != 1) { f.counts_off = off; off += (long long)f.nv << f.nA; }
+      plan->n_counts_plain = off;
+      for (auto& f : plan->fdev)
+        if (f.clifford && f.role == 1) { f.counts_off = off; off += (long long)f.nv << f.nA; }
+    }
+    std::vector<int2> items_hub, items_plain;
+    for (auto& it : items_c) {
+      const FragDev& f = plan->fdev[it.x];
+      if (f.role == 1) {
+        items_hub.push_back(it);
+        plan->max_hub_nA = std::max(plan->max_hub_nA, f.nA);
+        if (f.m < 2 || f.qout > 4 || f.nA > 16) plan->hub_bytes_ok = false;
+      }
+      else items_plain.push_back(it);
+    }
+    plan->n_items_hub = (int)items_hub.size();
+    plan->n_items_plain = (int)items_plain.size();
+    // fold sets: T of non-hub Clifford fragments (main stream) and non-hub
+    // statevector fragments (side branch); T^S of every fragment; then the
+    // contraction operands Q (hubs) and T' (the others)
+    std::vector<int> fidx_c, fidx_nc, fidx_h, fidx_hn, fidx_o;
+    std::vector<long long> tp_c{0}, tp_nc{0}, tp_h{0}, tp_hn{0}, tp_o{0};
+    for (int fi = 0; fi < (int)plan->fdev.size(); ++fi) {
+      const FragDev& f = plan->fdev[fi];
+      const long long t = (1ll << f.m) * (1ll << (2 * f.n_slots));
+      const long long tf = f.role == 1 ? 0 : t;    // hubs: T only on request
+      if (f.clifford) { fidx_c.push_back(fi); tp_c.push_back(tp_c.back() + tf); }
+      else { fidx_nc.push_back(fi); tp_nc.push_back(tp_nc.back() + tf); }
+      if (f.role == 1) { fidx_h.push_back(fi); tp_h.push_back(tp_h.back() + t); }
+      if (f.role == 1 && !f.clifford) { fidx_hn.push_back(fi); tp_hn.push_back(tp_hn.back() + t); }
+      if (f.role == 2) { fidx_o.push_back(fi); tp_o.push_back(tp_o.back() + t); }
+    }
     for (auto& P : plan->problems) {
-      const int nfr = (int)P.frag_ids.size();
-      if (P.hub >= 0)
-        for (int l = 0; l < nfr; ++l) plan->fdev[f0r + l].role = (l == P.hub) ? 1 : 2;
-      f0r += nfr;
+      ProblemDev d{};
+      d.k = (int)P.cuts.size();
+      d.n_frags = (int)P.frag_ids.size();
+      d.frag0 = f0;
+      d.hub = P.hub;
+      d.n_marg = (int)P.marginal.size();
+      d.nz = (int)P.zstrings.size();
+      d.marg_off = plan->n_marg;
+      d.zexp_off = plan->n_zexp;
+      plan->n_marg += 1ll << d.n_marg;
+      plan->n_zexp += d.nz;
+      plan->out_prefix.push_back(plan->n_marg);
+      plan->z_prefix.push_back(plan->n_zexp);
+      if (P.hub < 0) plan->all_star = false;
+      if (P.hub >= 0) {
+        const int m_hub = plan->fdev[f0 + P.hub].m;
+        d.M = 1 << m_hub;
+        d.N = 1 << (d.n_marg - m_hub);
+        d.K = 1ll << (2 * d.k);
+        auto up4 = [](int x) { return (x + 3) & ~3; };
+        d.TN = std::min(up4(d.N), 64);                          // tile: TM x TN, 4x4 per thread,
+        d.TM = std::min(up4(d.M), 4096 / d.TN);                 // at most 256 threads
+        d.mtiles = (d.M + d.TM - 1) / d.TM;
+        d.ntiles = (d.N + d.TN - 1) / d.TN;
+        d.hub_T_off = plan->fdev[f0 + P.hub].T_off;
+        d.tc = (gemm_tc_supported(d.M, d.N, d.K) && d.K >= 4096 && d.M >= 128) ? 1 : 0;
+        // leaf by leaf in shared memory, the hub outputs in slices of TM (the
+        // contraction never mixes hub outputs), when every intermediate of a
+        // slice fits: per hub output the intermediates hold rest_l x N_1..N_l
+        // floats (the first leaf reads the hub operand from global memory)
+        long long per_m = d.n_frags > 1 ? 1 : d.K, A = 1, rest = d.K;   // the first leaf reads Q^T in place
+        int slots = 0;
+        for (int l = 0; l < d.n_frags; ++l) {
+          if (l == P.hub) continue;
+          const FragDev& L = plan->fdev[f0 + l];
+          rest >>= 2 * L.n_slots;
+          A <<= L.m;
+          slots += L.n_slots;
+          per_m = std::max(per_m, rest * A);
+        }
+        auto slice = [&](long long pm) {
+          long long t = 1;
+          while (2 * t <= d.M && 2 * t * pm <= kDirectSmemFloats && 2 * t + d.N <= kDirectSmemFloats) t *= 2;
+          return t;
+        };
+        long long tm = slice(per_m);
+        // staging the operand slice first (coalesced, then every read in shared
+        // memory) when that does not shrink the slice
+        const long long per_m_staged = std::max(per_m, d.K);
+        d.direct_staged = per_m_staged <= kDirectSmemFloats && slice(per_m_staged) == tm;
+        if (d.direct_staged) per_m = per_m_staged;
+        d.direct = (!d.tc && slots == d.k && per_m <= kDirectSmemFloats && tm + d.N <= kDirectSmemFloats) ? 1 : 0;
+        if (d.direct) {
+          d.splits = 1;
+          d.TM = (int)tm;                      // hub outputs per block
+          d.mtiles = (int)(d.M / tm);
+          d.r_off = plan->r_total;
+          d.part_off = plan->part_total;
+          d.blk_off = plan->gemm_blocks;
+          for (int t = 0; t < d.mtiles; ++t) plan->direct_items.push_back(make_int2((int)plan->pdev.size(), t));
+          plan->direct_stage_floats =
+              std::max(plan->direct_stage_floats, std::max(tm * per_m, tm + (long long)d.N));
+        }
+        if (!d.direct) {
+          const long long base = (long long)d.mtiles * d.ntiles;
+          const int target = 2 * std::max(c->sm_count, 148);
+          const long long max_splits = std::max(1ll, d.K / 32);
+          d.splits = (int)std::max(1ll, std::min(max_splits, (target + base - 1) / base));
+          plan->chain = 1;
+          d.r_off = plan->r_total;
+          plan->r_total += d.K * d.N;
+          d.part_off = plan->part_total;
+          plan->part_total += (long long)d.splits * d.M * d.N;
+          d.blk_off = plan->gemm_blocks;
+          plan->gemm_blocks += base * d.splits;
+          plan->max_tile_smem = std::max(plan->max_tile_smem, 16 * (d.TM + d.TN) * 4);
+        }
+        if (d.tc) {
+          d.rt_off = (plan->rt_total + 63) & ~63ll;
+          plan->rt_total = d.rt_off + d.K * d.N;
+        }
+      }
+      plan->r_prefix.push_back(plan->r_total);
+      plan->blk_prefix.push_back(plan->gemm_blocks);
+      f0 += d.n_frags;
+      plan->pdev.push_back(d);
     }
-  }
-  // shot counts: non-hub Clifford fragments first (they are zeroed before
-  // sampling), hub fragments after (written whole by the fused sampler)
-  {
-    long long off = 0;
-    for (auto& f : plan->fdev)
-      if (f.clifford && f.role != 1) { f.counts_off = off; off += (long long)f.nv << f.nA; }
-    plan->n_counts_plain = off;
-    for (auto& f : plan->fdev)
-      if (f.clifford && f.role == 1) { f.counts_off = off; off += (long long)f.nv << f.nA; }
-  }
-  std::vector<int2> items_hub, items_plain;
-  for (auto& it : items_c) {
-    const FragDev& f = plan->fdev[it.x];
-    if (f.role == 1) {
-      items_hub.push_back(it);
-      plan->max_hub_nA = std::max(plan->max_hub_nA, f.nA);
-      if (f.m < 2 || f.qout > 4 || f.nA > 16) plan->hub_bytes_ok = false;
-    }
-    else items_plain.push_back(it);
-  }
-  plan->n_items_hub = (int)items_hub.size();
-  plan->n_items_plain = (int)items_plain.size();
-  // fold sets: T of non-hub Clifford fragments (main stream) and non-hub
-  // statevector fragments (side branch); T^S of every fragment; then the
-  // contraction operands Q (hubs) and T' (the others)
-  std::vector<int> fidx_c, fidx_nc, fidx_h, fidx_hn, fidx_o;
-  std::vector<long long> tp_c{0}, tp_nc{0}, tp_h{0}, tp_hn{0}, tp_o{0};
-  for (int fi = 0; fi < (int)plan->fdev.size(); ++fi) {
-    const FragDev& f = plan->fdev[fi];
-    const long long t = (1ll << f.m) * (1ll << (2 * f.n_slots));
-    const long long tf = f.role == 1 ? 0 : t;    // hubs: T only on request
-    if (f.clifford) { fidx_c.push_back(fi); tp_c.push_back(tp_c.back() + tf); }
-    else { fidx_nc.push_back(fi); tp_nc.push_back(tp_nc.back() + tf); }
-    if (f.role == 1) { fidx_h.push_back(fi); tp_h.push_back(tp_h.back() + t); }
-    if (f.role == 1 && !f.clifford) { fidx_hn.push_back(fi); tp_hn.push_back(tp_hn.back() + t); }
-    if (f.role == 2) { fidx_o.push_back(fi); tp_o.push_back(tp_o.back() + t); }
-  }
-  for (auto& P : plan->problems) {
-    ProblemDev d{};
-    d.k = (int)P.cuts.size();
-    d.n_frags = (int)P.frag_ids.size();
-    d.frag0 = f0;
-    d.hub = P.hub;
-    d.n_marg = (int)P.marginal.size();
-    d.nz = (int)P.zstrings.size();
-    d.marg_off = plan->n_marg;
-    d.zexp_off = plan->n_zexp;
-    plan->n_marg += 1ll << d.n_marg;
-    plan->n_zexp += d.nz;
-    plan->out_prefix.push_back(plan->n_marg);
-    plan->z_prefix.push_back(plan->n_zexp);
-    if (P.hub < 0) plan->all_star = false;
-    if (P.hub >= 0) {
-      const int m_hub = plan->fdev[f0 + P.hub].m;
-      d.M = 1 << m_hub;
-      d.N = 1 << (d.n_marg - m_hub);
-      d.K = 1ll << (2 * d.k);
-      auto up4 = [](int x) { return (x + 3) & ~3; };
-      d.TN = std::min(up4(d.N), 64);                          // tile: TM x TN, 4x4 per thread,
-      d.TM = std::min(up4(d.M), 4096 / d.TN);                 // at most 256 threads
-      d.mtiles = (d.M + d.TM - 1) / d.TM;
-      d.ntiles = (d.N + d.TN - 1) / d.TN;
-      d.hub_T_off = plan->fdev[f0 + P.hub].T_off;
-      d.tc = (gemm_tc_supported(d.M, d.N, d.K) && d.K >= 4096 && d.M >= 128) ? 1 : 0;
-      // leaf by leaf in shared memory, the hub outputs in slices of TM (the
-      // contraction never mixes hub outputs), when every intermediate of a
-      // slice fits: per hub output the intermediates hold rest_l x N_1..N_l
-      // floats (the first leaf reads the hub operand from global memory)
-      long long per_m = d.n_frags > 1 ? 1 : d.K, A = 1, rest = d.K;   // the first leaf reads Q^T in place
-      int slots = 0;
-      for (int l = 0; l < d.n_frags; ++l) {
-        if (l == P.hub) continue;
-        const FragDev& L = plan->fdev[f0 + l];
-        rest >>= 2 * L.n_slots;
-        A <<= L.m;
-        slots += L.n_slots;
-        per_m = std::max(per_m, rest * A);
-      }
-      auto slice = [&](long long pm) {
-        long long t = 1;
-        while (2 * t <= d.M && 2 * t * pm <= kDirectSmemFloats && 2 * t + d.N <= kDirectSmemFloats) t *= 2;
-        return t;
-      };
-      long long tm = slice(per_m);
-      // staging the operand slice first (coalesced, then every read in shared
-      // memory) when that does not shrink the slice
-      const long long per_m_staged = std::max(per_m, d.K);
-      d.direct_staged = per_m_staged <= kDirectSmemFloats && slice(per_m_staged) == tm;
-      if (d.direct_staged) per_m = per_m_staged;
-      d.direct = (!d.tc && slots == d.k && per_m <= kDirectSmemFloats && tm + d.N <= kDirectSmemFloats) ? 1 : 0;
-      if (d.direct) {
-        d.splits = 1;
-        d.TM = (int)tm;                      // hub outputs per block
-        d.mtiles = (int)(d.M / tm);
-        d.r_off = plan->r_total;
-        d.part_off = plan->part_total;
-        d.blk_off = plan->gemm_blocks;
-        for (int t = 0; t < d.mtiles; ++t) plan->direct_items.push_back(make_int2((int)plan->pdev.size(), t));
-        plan->direct_stage_floats =
-            std::max(plan->direct_stage_floats, std::max(tm * per_m, tm + (long long)d.N));
-      }
-      if (!d.direct) {
-        const long long base = (long long)d.mtiles * d.ntiles;
-        const int target = 2 * std::max(c->sm_count, 148);
-        const long long max_splits = std::max(1ll, d.K / 32);
-        d.splits = (int)std::max(1ll, std::min(max_splits, (target + base - 1) / base));
-        plan->chain = 1;
-        d.r_off = plan->r_total;
-        plan->r_total += d.K * d.N;
-        d.part_off = plan->part_total;
-        plan->part_total += (long long)d.splits * d.M * d.N;
-        d.blk_off = plan->gemm_blocks;
-        plan->gemm_blocks += base * d.splits;
-        plan->max_tile_smem = std::max(plan->max_tile_smem, 16 * (d.TM + d.TN) * 4);
-      }
-      if (d.tc) {
-        d.rt_off = (plan->rt_total + 63) & ~63ll;
-        plan->rt_total = d.rt_off + d.K * d.N;
-      }
-    }
-    plan->r_prefix.push_back(plan->r_total);
-    plan->blk_prefix.push_back(plan->gemm_blocks);
-    f0 += d.n_frags;
-    plan->pdev.push_back(d);
-  }
 
-  // the scratch holds every problem's R operand first, then the split-K partials
-  for (auto& d : plan->pdev) d.part_off += plan->r_total;
-  std::vector<CliffordOp> prep(4), basis(3);
-  std::vector<float> prepm(32), basism(24);
-  for (int s = 0; s < 4; ++s) { prep[s] = prep_op(s); prep_matrix(s, &prepm[8 * s]); }
-  for (int b = 0; b < 3; ++b) { basis[b] = basis_op(b); basis_matrix(b, &basism[8 * b]); }
+    // the scratch holds every problem's R operand first, then the split-K partials
+    for (auto& d : plan->pdev) d.part_off += plan->r_total;
+    std::vector<CliffordOp> prep(4), basis(3);
+    std::vector<float> prepm(32), basism(24);
+    for (int s = 0; s < 4; ++s) { prep[s] = prep_op(s); prep_matrix(s, &prepm[8 * s]); }
+    for (int b = 0; b < 3; ++b) { basis[b] = basis_op(b); basis_matrix(b, &basism[8 * b]); }
 
-  int *d_fidx_c, *d_fidx_nc, *d_fidx_h, *d_fidx_hn, *d_fidx_o;
-  long long *d_tp_c, *d_tp_nc, *d_tp_h, *d_tp_hn, *d_tp_o;
-  if (!c->host_only) {
+    int *d_fidx_c, *d_fidx_nc, *d_fidx_h, *d_fidx_hn, *d_fidx_o;
+    long long *d_tp_c, *d_tp_nc, *d_tp_h, *d_tp_hn, *d_tp_o;
+    if (!c->host_only) {
+      Staging st;
+      st.add(fidx_c, &d_fidx_c); st.add(fidx_nc, &d_fidx_nc); st.add(tp_c, &d_tp_c);
+      st.add(tp_nc, &d_tp_nc); st.add(fidx_h, &d_fidx_h); st.add(fidx_o, &d_fidx_o);
+      st.add(tp_h, &d_tp_h); st.add(tp_o, &d_tp_o);
+      st.add(fidx_hn, &d_fidx_hn); st.add(tp_hn, &d_tp_hn);
+      st.add(items_hub, &plan->d_items_hub); st.add(items_plain, &plan->d_items_plain);
+      bool okf = st.commit(c, plan->A);
+      if (!okf) { delete plan; return fail(c, CCS_ERR_OOM, "plan upload failed"); }
+      plan->fold_cliff = FoldSet{d_fidx_c, d_tp_c, (int)fidx_c.size(), tp_c.back()};
+      plan->fold_nc = FoldSet{d_fidx_nc, d_tp_nc, (int)fidx_nc.size(), tp_nc.back()};
+      plan->fold_hubs = FoldSet{d_fidx_h, d_tp_h, (int)fidx_h.size(), tp_h.back()};
+      plan->fold_hubs_nc = FoldSet{d_fidx_hn, d_tp_hn, (int)fidx_hn.size(), tp_hn.back()};
+      plan->fold_others = FoldSet{d_fidx_o, d_tp_o, (int)fidx_o.size(), tp_o.back()};
+    }
+    if (c->host_only) {
+      plan->dp.n_items_cliff = (int)items_c.size();
+      plan->dp.n_items_nc = (int)items_nc.size();
+      *out = plan;
+      return CCS_OK;
+    }
+    DevPlan& dp = plan->dp;
+    FragDev* dfr; CliffordOp* dco; NCOp* dno; int* dmo; int* dwi; int* dzo; int2* dic; int2* din; int2* dib; int* dcf;
+    int2* diz = nullptr; int2* dzb = nullptr;
+    ProblemDev* dpr; CliffordOp* dpo; CliffordOp* dbo; float* dpm; float* dbm;
     Staging st;
-    st.add(fidx_c, &d_fidx_c); st.add(fidx_nc, &d_fidx_nc); st.add(tp_c, &d_tp_c);
-    st.add(tp_nc, &d_tp_nc); st.add(fidx_h, &d_fidx_h); st.add(fidx_o, &d_fidx_o);
-    st.add(tp_h, &d_tp_h); st.add(tp_o, &d_tp_o);
-    st.add(fidx_hn, &d_fidx_hn); st.add(tp_hn, &d_tp_hn);
-    st.add(items_hub, &plan->d_items_hub); st.add(items_plain, &plan->d_items_plain);
-    bool okf = st.commit(c, plan->A);
-    if (!okf) { delete plan; return fail(c, CCS_ERR_OOM, "plan upload failed"); }
-    plan->fold_cliff = FoldSet{d_fidx_c, d_tp_c, (int)fidx_c.size(), tp_c.back()};
-    plan->fold_nc = FoldSet{d_fidx_nc, d_tp_nc, (int)fidx_nc.size(), tp_nc.back()};
-    plan->fold_hubs = FoldSet{d_fidx_h, d_tp_h, (int)fidx_h.size(), tp_h.back()};
-    plan->fold_hubs_nc = FoldSet{d_fidx_hn, d_tp_hn, (int)fidx_hn.size(), tp_hn.back()};
-    plan->fold_others = FoldSet{d_fidx_o, d_tp_o, (int)fidx_o.size(), tp_o.back()};
-  }
-  if (c->host_only) {
-    plan->dp.n_items_cliff = (int)items_c.size();
-    plan->dp.n_items_nc = (int)items_nc.size();
+    st.add(plan->fdev, &dfr); st.add(cops, &dco); st.add(nops, &dno); st.add(moments, &dmo); st.add(wires, &dwi);
+    st.add(zoffs, &dzo); st.add(items_c, &dic); st.add(items_nc, &din); st.add(items_b, &dib);
+    st.add(cliff_frags, &dcf); st.add(items_z, &diz); st.add(zblocks, &dzb); st.add(plan->pdev, &dpr); st.add(prep, &dpo); st.add(basis, &dbo);
+    st.add(prepm, &dpm); st.add(basism, &dbm); st.add(plan->t_prefix, &plan->d_t_prefix);
+    st.add(plan->out_prefix, &plan->d_out_prefix);
+    st.add(plan->z_prefix, &plan->d_z_prefix); st.add(plan->r_prefix, &plan->d_r_prefix);
+    st.add(plan->blk_prefix, &plan->d_blk_prefix); st.add(plan->direct_items, &plan->d_direct_items);
+    bool ok = st.commit(c, plan->A);
+    if (!ok) { delete plan; return fail(c, CCS_ERR_OOM, "plan upload failed"); }
+    dp.frags = dfr; dp.cops = dco; dp.nops = dno; dp.moments = dmo; dp.wires = dwi; dp.zoffs = dzo;
+    dp.items_cliff = dic; dp.items_nc = din; dp.nc_basis_chunk = plan->nc_basis_chunk;
+    dp.n_items_cliff = (int)items_c.size(); dp.n_items_nc = (int)items_nc.size();
+    dp.items_body = dib; dp.n_items_body = (int)items_b.size(); dp.max_body_cols = max_body_cols;
+    dp.cliff_frags = dcf; dp.n_cliff_frags = (int)cliff_frags.size();
+    dp.items_zimg = diz; dp.n_items_zimg = (int)items_z.size();
+    dp.zblocks = dzb; dp.n_zblocks = (int)zblocks.size();
+    dp.body_words_max = body_words_max; dp.img_words_max = img_words_max;
+    dp.max_body_stage_words = max_body_stage;
+    dp.max_moment_ops = max_moment_ops;
+    dp.problems = dpr; dp.n_problems = (int)plan->pdev.size();
+    dp.prep_ops = dpo; dp.basis_ops = dbo; dp.prep_mats = dpm; dp.basis_mats = dbm;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) { delete plan; return cuda_fail(c, e, "plan upload"); }
     *out = plan;
     return CCS_OK;
-  }
-  DevPlan& dp = plan->dp;
-  FragDev* dfr; CliffordOp* dco; NCOp* dno; int* dmo; int* dwi; int* dzo; int2* dic; int2* din; int2* dib; int* dcf;
-  int2* diz = nullptr; int2* dzb = nullptr;
-  ProblemDev* dpr; CliffordOp* dpo; CliffordOp* dbo; float* dpm; float* dbm;
-  Staging st;
-  st.add(plan->fdev, &dfr); st.add(cops, &dco); st.add(nops, &dno); st.add(moments, &dmo); st.add(wires, &dwi);
-  st.add(zoffs, &dzo); st.add(items_c, &dic); st.add(items_nc, &din); st.add(items_b, &dib);
-  st.add(cliff_frags, &dcf); st.add(items_z, &diz); st.add(zblocks, &dzb); st.add(plan->pdev, &dpr); st.add(prep, &dpo); st.add(basis, &dbo);
-  st.add(prepm, &dpm); st.add(basism, &dbm); st.add(plan->t_prefix, &plan->d_t_prefix);
-  st.add(plan->out_prefix, &plan->d_out_prefix);
-  st.add(plan->z_prefix, &plan->d_z_prefix); st.add(plan->r_prefix, &plan->d_r_prefix);
-  st.add(plan->blk_prefix, &plan->d_blk_prefix); st.add(plan->direct_items, &plan->d_direct_items);
-  bool ok = st.commit(c, plan->A);
-  if (!ok) { delete plan; return fail(c, CCS_ERR_OOM, "plan upload failed"); }
-  dp.frags = dfr; dp.cops = dco; dp.nops = dno; dp.moments = dmo; dp.wires = dwi; dp.zoffs = dzo;
-  dp.items_cliff = dic; dp.items_nc = din; dp.nc_basis_chunk = plan->nc_basis_chunk;
-  dp.n_items_cliff = (int)items_c.size(); dp.n_items_nc = (int)items_nc.size();
-  dp.items_body = dib; dp.n_items_body = (int)items_b.size(); dp.max_body_cols = max_body_cols;
-  dp.cliff_frags = dcf; dp.n_cliff_frags = (int)cliff_frags.size();
-  dp.items_zimg = diz; dp.n_items_zimg = (int)items_z.size();
-  dp.zblocks = dzb; dp.n_zblocks = (int)zblocks.size();
-  dp.body_words_max = body_words_max; dp.img_words_max = img_words_max;
-  dp.max_body_stage_words = max_body_stage;
-  dp.max_moment_ops = max_moment_ops;
-  dp.problems = dpr; dp.n_problems = (int)plan->pdev.size();
-  dp.prep_ops = dpo; dp.basis_ops = dbo; dp.prep_mats = dpm; dp.basis_mats = dbm;
-  cudaError_t e = cudaStreamSynchronize(c->stream);
-  if (e != cudaSuccess) { delete plan; return cuda_fail(c, e, "plan upload"); }
-  *out = plan;
-  return CCS_OK;
+  });
 }
 
 void ccs_plan_free(ccs_plan p) { delete p; }
 
 int ccs_cut_candidates(ccs_ctx c, const ccs_problem* q, const ccs_cut_opts* opts, ccs_cut* cuts_out,
                        int cap_cuts, int* offsets, double* costs, int cap_cands) {
-  if (!c || !q || !cuts_out || !offsets || cap_cands < 1) return fail(c, CCS_ERR_INVALID_ARG, "bad arguments");
-  ccs_cut_opts o{kMaxCuts, 10, 0};
-  if (opts) o = *opts;
-  Problem P;
-  P.n_qubits = q->n_qubits;
-  std::string err;
-  if (q->n_gates && !q->gates) return fail(c, CCS_ERR_INVALID_ARG, "null gate list");
-  int rc = load_gates(q->gates, q->n_gates, P.gates, P.gparam, err);
-  if (rc != CCS_OK) return fail(c, rc, err);
-  P.marginal.assign(q->marginal, q->marginal + q->n_marginal);
-  CutSearchOpts so;
-  so.max_cuts = std::min(o.max_cuts, kMaxCuts);
-  so.max_nc_width = std::min(o.max_nc_width > 0 ? o.max_nc_width : 10, kMaxNCWidth);
-  std::vector<CutCandidate> cands;
-  rc = greedy_cuts(P, so, cands, err);
-  if (rc != CCS_OK) return fail(c, rc, err);
-  int n = 0, used = 0;
-  offsets[0] = 0;
-  for (auto& cd : cands) {
-    if (n >= cap_cands || used + (int)cd.cuts.size() > cap_cuts) break;
-    for (auto& x : cd.cuts) cuts_out[used++] = x;
-    if (costs) costs[n] = cd.cost;
-    offsets[++n] = used;
-  }
-  return n;
+  return abi_guard([&](int code, const char* m) { return fail(c, code, m); }, [&]() -> int {
+    if (!c || !q || !cuts_out || !offsets || cap_cands < 1) return fail(c, CCS_ERR_INVALID_ARG, "bad arguments");
+    ccs_cut_opts o{kMaxCuts, 10, 0};
+    if (opts) o = *opts;
+    Problem P;
+    P.n_qubits = q->n_qubits;
+    std::string err;
+    int rc = check_circuit(*q, err);
+    if (rc != CCS_OK) return fail(c, rc, err);
+    rc = load_gates(q->gates, q->n_gates, P.gates, P.gparam, err);
+    if (rc != CCS_OK) return fail(c, rc, err);
+    P.marginal.assign(q->marginal, q->marginal + q->n_marginal);
+    CutSearchOpts so;
+    so.max_cuts = std::min(o.max_cuts, kMaxCuts);
+    so.max_nc_width = std::min(o.max_nc_width > 0 ? o.max_nc_width : 10, kMaxNCWidth);
+    std::vector<CutCandidate> cands;
+    rc = greedy_cuts(P, so, cands, err);
+    if (rc != CCS_OK) return fail(c, rc, err);
+    int n = 0, used = 0;
+    offsets[0] = 0;
+    for (auto& cd : cands) {
+      if (n >= cap_cands || used + (int)cd.cuts.size() > cap_cuts) break;
+      for (auto& x : cd.cuts) cuts_out[used++] = x;
+      if (costs) costs[n] = cd.cost;
+      offsets[++n] = used;
+    }
+    return n;
+  });
 }
 
 // Evaluation as two branches: Clifford variants (tableaus -> spaces/Z-values
@@ -1041,155 +1073,159 @@ static int autotune(ccs_ctx c, ccs_plan p, ccs_res r) {
 
 int ccs_get_tuning(ccs_ctx c, ccs_res r, int* cliff_threads, int* words_per_op, int* shots_per_cta,
                    int* hub_threads) {
-  if (!c || !r) return fail(c, CCS_ERR_INVALID_ARG, "bad arguments");
-  if (hub_threads) *hub_threads = (r->hub_bytes && r->plan->hub_bytes_ok) ? 256 : r->hub_threads;
-  if (cliff_threads) *cliff_threads = r->cliff_threads;
-  if (words_per_op) *words_per_op = r->ep.shared_body ? 1 : r->cliff_words;
-  if (shots_per_cta) *shots_per_cta = r->sample_spc;
-  return CCS_OK;
+  return abi_guard([&](int code, const char* m) { return fail(c, code, m); }, [&]() -> int {
+    if (!c || !r) return fail(c, CCS_ERR_INVALID_ARG, "bad arguments");
+    if (hub_threads) *hub_threads = (r->hub_bytes && r->plan->hub_bytes_ok) ? 256 : r->hub_threads;
+    if (cliff_threads) *cliff_threads = r->cliff_threads;
+    if (words_per_op) *words_per_op = r->ep.shared_body ? 1 : r->cliff_words;
+    if (shots_per_cta) *shots_per_cta = r->sample_spc;
+    return CCS_OK;
+  });
 }
 
 int ccs_eval_variants(ccs_ctx c, ccs_plan p, const ccs_eval_opts* opts, ccs_res* res) {
-  if (!c || !p || !opts || !res) return fail(c, CCS_ERR_INVALID_ARG, "bad arguments");
-  if (opts->mode != CCS_EXACT && opts->mode != CCS_SAMPLED) return fail(c, CCS_ERR_INVALID_ARG, "bad mode");
-  if (opts->mode == CCS_SAMPLED && opts->shots == 0) return fail(c, CCS_ERR_INVALID_ARG, "zero shots");
-  if (opts->mode == CCS_SAMPLED && opts->shots > 0xffffu && p->max_hub_nA > 15)
-    return fail(c, CCS_ERR_UNSUPPORTED, "more than 65535 shots with a 16-bit hub outcome space");
-  if (opts->mode == CCS_SAMPLED && p->max_hub_nA > 16)   // the hub histogram lives in shared memory
-    return fail(c, CCS_ERR_UNSUPPORTED, "hub measured set wider than 16 bits in sampled mode");
-  if (c->host_only) return fail(c, CCS_ERR_UNSUPPORTED, "host-only context cannot evaluate");
-  cudaSetDevice(c->device);
-  ccs_res r = *res;
-  if (r && r->plan != p) return fail(c, CCS_ERR_INVALID_ARG, "result belongs to another plan");
-  if (!r) {
-    r = new ccs_res_s();
-    r->plan = p;
-    r->A.ctx = c;
-    DevRes& d = r->dr;
-    d.spaces = r->A.get<SpaceRec>(std::max<long long>(p->n_spaces, 1));
-    d.dist = r->A.get<float>(std::max<long long>(p->n_dist_nc, 1));   // exact mode widens it
-    d.zval = r->A.get<float>(std::max<long long>(p->n_zval, 1));
-    d.T = r->A.get<float>(std::max<long long>(p->n_T, 1));
-    d.TQ = r->A.get<float>(std::max<long long>(p->n_T, 1));
-    d.marg = r->A.get<double>(std::max<long long>(p->n_marg, 1));
-    d.zexp = r->A.get<double>(std::max<long long>(p->n_zexp, 1));
-    d.work = r->A.get<unsigned>(4 + (long long)p->dp.n_cliff_frags);   // + per-fragment record counters
-    d.fragcnt = d.work ? d.work + 4 : nullptr;
-    d.body = r->A.get<unsigned long long>(std::max<long long>(p->n_body, 2));
-    d.rowbasis = r->A.get<unsigned long long>(std::max<long long>((long long)kRowBasisWords * p->dp.n_cliff_frags, 1));
-    d.zimg = r->A.get<unsigned long long>(std::max<long long>(p->n_zimg, 1));
-    d.pbasis = r->A.get<uint32_t>(std::max<long long>(p->n_pbasis, 1));
+  return abi_guard([&](int code, const char* m) { return fail(c, code, m); }, [&]() -> int {
+    if (!c || !p || !opts || !res) return fail(c, CCS_ERR_INVALID_ARG, "bad arguments");
+    if (opts->mode != CCS_EXACT && opts->mode != CCS_SAMPLED) return fail(c, CCS_ERR_INVALID_ARG, "bad mode");
+    if (opts->mode == CCS_SAMPLED && opts->shots == 0) return fail(c, CCS_ERR_INVALID_ARG, "zero shots");
+    if (opts->mode == CCS_SAMPLED && opts->shots > 0xffffu && p->max_hub_nA > 15)
+      return fail(c, CCS_ERR_UNSUPPORTED, "more than 65535 shots with a 16-bit hub outcome space");
+    if (opts->mode == CCS_SAMPLED && p->max_hub_nA > 16)   // the hub histogram lives in shared memory
+      return fail(c, CCS_ERR_UNSUPPORTED, "hub measured set wider than 16 bits in sampled mode");
+    if (c->host_only) return fail(c, CCS_ERR_UNSUPPORTED, "host-only context cannot evaluate");
+    cudaSetDevice(c->device);
+    ccs_res r = *res;
+    if (r && r->plan != p) return fail(c, CCS_ERR_INVALID_ARG, "result belongs to another plan");
+    if (!r) {
+      r = new ccs_res_s();
+      r->plan = p;
+      r->A.ctx = c;
+      DevRes& d = r->dr;
+      d.spaces = r->A.get<SpaceRec>(std::max<long long>(p->n_spaces, 1));
+      d.dist = r->A.get<float>(std::max<long long>(p->n_dist_nc, 1));   // exact mode widens it
+      d.zval = r->A.get<float>(std::max<long long>(p->n_zval, 1));
+      d.T = r->A.get<float>(std::max<long long>(p->n_T, 1));
+      d.TQ = r->A.get<float>(std::max<long long>(p->n_T, 1));
+      d.marg = r->A.get<double>(std::max<long long>(p->n_marg, 1));
+      d.zexp = r->A.get<double>(std::max<long long>(p->n_zexp, 1));
+      d.work = r->A.get<unsigned>(4 + (long long)p->dp.n_cliff_frags);   // + per-fragment record counters
+      d.fragcnt = d.work ? d.work + 4 : nullptr;
+      d.body = r->A.get<unsigned long long>(std::max<long long>(p->n_body, 2));
+      d.rowbasis = r->A.get<unsigned long long>(std::max<long long>((long long)kRowBasisWords * p->dp.n_cliff_frags, 1));
+      d.zimg = r->A.get<unsigned long long>(std::max<long long>(p->n_zimg, 1));
+      d.pbasis = r->A.get<uint32_t>(std::max<long long>(p->n_pbasis, 1));
 
-    d.status = r->A.get<unsigned>(4);
-    r->scratch = r->A.get<float>(std::max<long long>(p->r_total + p->part_total, 1));
-    {   // default launch shape before any tuning: wide tableaus take 8 words per op, 512 threads
-      int max_n = 0;
-      for (auto& f : p->fdev)
-        if (f.clifford) max_n = std::max(max_n, f.n);
-      const int W = 2 * ((max_n + 63) / 64);
-      r->cliff_words = W >= 16 ? 8 : W >= 8 ? 4 : 1;
-      r->cliff_threads = max_n > 256 ? 512 : 256;
-      // small hub CTAs when a variant has few shots and few outputs (more CTAs per SM);
-      // byte counters when the histogram would otherwise fill an SM's shared memory
-      r->hub_threads = (p->max_hub_nA <= 12 && opts->shots <= 4096) ? 128 : 512;
-      r->hub_bytes = p->hub_bytes_ok && p->max_hub_nA >= 13;
+      d.status = r->A.get<unsigned>(4);
+      r->scratch = r->A.get<float>(std::max<long long>(p->r_total + p->part_total, 1));
+      {   // default launch shape before any tuning: wide tableaus take 8 words per op, 512 threads
+        int max_n = 0;
+        for (auto& f : p->fdev)
+          if (f.clifford) max_n = std::max(max_n, f.n);
+        const int W = 2 * ((max_n + 63) / 64);
+        r->cliff_words = W >= 16 ? 8 : W >= 8 ? 4 : 1;
+        r->cliff_threads = max_n > 256 ? 512 : 256;
+        // small hub CTAs when a variant has few shots and few outputs (more CTAs per SM);
+        // byte counters when the histogram would otherwise fill an SM's shared memory
+        r->hub_threads = (p->max_hub_nA <= 12 && opts->shots <= 4096) ? 128 : 512;
+        r->hub_bytes = p->hub_bytes_ok && p->max_hub_nA >= 13;
+      }
+      if (p->rt_total) {
+        d.TQh = r->A.get<uint16_t>(p->n_T);
+        r->rt_scratch = r->A.get<uint16_t>(p->rt_total);
+      }
+      if (!d.spaces || !d.dist || !d.zval || !d.T || !d.TQ || !d.marg || !d.zexp || !d.work || !d.status ||
+          !d.body || !d.rowbasis || !d.zimg || !d.fragcnt || !d.pbasis ||
+          !r->scratch || (p->rt_total && (!d.TQh || !r->rt_scratch))) {
+        delete r;
+        return fail(c, CCS_ERR_OOM, "result allocation failed");
+      }
+      cudaMemsetAsync(d.status, 0, 4 * sizeof(unsigned), c->stream);
+      *res = r;
     }
-    if (p->rt_total) {
-      d.TQh = r->A.get<uint16_t>(p->n_T);
-      r->rt_scratch = r->A.get<uint16_t>(p->rt_total);
+    // buffers a mode needs are added on first use; a replaced buffer drops the captured graph
+    auto drop_graph = [&]() {
+      if (r->graph) { cudaGraphExecDestroy(r->graph); r->graph = nullptr; }
+    };
+    const bool want_full_counts = opts->keep_tableaus && p->n_counts > p->n_counts_plain;
+    if (opts->mode == CCS_SAMPLED && p->n_counts && (!r->have_counts || (want_full_counts && !r->counts_full))) {
+      r->dr.counts = r->A.get<uint32_t>(want_full_counts ? p->n_counts : std::max<long long>(p->n_counts_plain, 1));
+      if (!r->dr.counts) return fail(c, CCS_ERR_OOM, "counts allocation failed");
+      r->have_counts = true;
+      r->counts_full = want_full_counts;
+      drop_graph();
     }
-    if (!d.spaces || !d.dist || !d.zval || !d.T || !d.TQ || !d.marg || !d.zexp || !d.work || !d.status ||
-        !d.body || !d.rowbasis || !d.zimg || !d.fragcnt || !d.pbasis ||
-        !r->scratch || (p->rt_total && (!d.TQh || !r->rt_scratch))) {
-      delete r;
-      return fail(c, CCS_ERR_OOM, "result allocation failed");
+    if (opts->mode == CCS_EXACT && !r->dist_full && p->n_dist > p->n_dist_nc) {
+      r->dr.dist = r->A.get<float>(p->n_dist);
+      if (!r->dr.dist) return fail(c, CCS_ERR_OOM, "distribution allocation failed");
+      r->dist_full = true;
+      drop_graph();
     }
-    cudaMemsetAsync(d.status, 0, 4 * sizeof(unsigned), c->stream);
-    *res = r;
-  }
-  // buffers a mode needs are added on first use; a replaced buffer drops the captured graph
-  auto drop_graph = [&]() {
-    if (r->graph) { cudaGraphExecDestroy(r->graph); r->graph = nullptr; }
-  };
-  const bool want_full_counts = opts->keep_tableaus && p->n_counts > p->n_counts_plain;
-  if (opts->mode == CCS_SAMPLED && p->n_counts && (!r->have_counts || (want_full_counts && !r->counts_full))) {
-    r->dr.counts = r->A.get<uint32_t>(want_full_counts ? p->n_counts : std::max<long long>(p->n_counts_plain, 1));
-    if (!r->dr.counts) return fail(c, CCS_ERR_OOM, "counts allocation failed");
-    r->have_counts = true;
-    r->counts_full = want_full_counts;
-    drop_graph();
-  }
-  if (opts->mode == CCS_EXACT && !r->dist_full && p->n_dist > p->n_dist_nc) {
-    r->dr.dist = r->A.get<float>(p->n_dist);
-    if (!r->dr.dist) return fail(c, CCS_ERR_OOM, "distribution allocation failed");
-    r->dist_full = true;
-    drop_graph();
-  }
-  if (opts->keep_tableaus && !r->have_tabs && p->n_tab) {
-    r->dr.tabs = r->A.get<unsigned long long>(p->n_tab);
-    if (!r->dr.tabs) return fail(c, CCS_ERR_OOM, "tableau allocation failed");
-    r->have_tabs = true;
-  }
-  EvalParams e{};
-  e.mode = opts->mode;
-  e.shots = opts->mode == CCS_SAMPLED ? opts->shots : 0;
-  e.seed_lo = opts->seed_lo;
-  e.seed_hi = opts->seed_hi;
-  e.keep_tableaus = opts->keep_tableaus && r->have_tabs;
-  e.shared_body = opts->per_variant_body ? 0 : 1;
-  e.screen = e.shared_body && p->dp.n_cliff_frags > 0 && !e.keep_tableaus;
-  if (opts->hub_sampler < 0 || opts->hub_sampler > 2) return fail(c, CCS_ERR_INVALID_ARG, "bad hub sampler");
-  e.hub_sampler = opts->hub_sampler;
-  if (opts->hub_sampler == 1) r->hub_bytes = false;
-  if (opts->hub_sampler == 2) r->hub_bytes = p->hub_bytes_ok;
-  e.inv_shots = e.shots ? 1.0 / (double)e.shots : 0.0;
-  r->ep = e;
-  if (opts->autotune && !r->graph && opts->hub_sampler == 0) {
-    const bool prof = c->profiling;
-    c->profiling = false;
-    int rc = autotune(c, p, r);
-    c->profiling = prof;
-    if (rc != CCS_OK) return rc;
-  }
-  if (!opts->use_graph || c->profiling) {
-    c->stage_mask = 0;
-    return enqueue_eval(c, p, r);
-  }
-  const bool same = r->graph && r->graph_key.mode == e.mode && r->graph_key.shots == e.shots &&
-                    r->graph_key.seed_lo == e.seed_lo && r->graph_key.seed_hi == e.seed_hi &&
-                    r->graph_key.keep_tableaus == e.keep_tableaus && r->graph_key.shared_body == e.shared_body &&
-                    r->graph_key.hub_sampler == e.hub_sampler;
-  if (!same) {
-    if (r->graph) { cudaGraphExecDestroy(r->graph); r->graph = nullptr; }
-    cudaStream_t s = c->stream;
-    bool tmp_stream = false;
-    if (s == nullptr) {   // the legacy stream cannot be captured
-      if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return fail(c, CCS_ERR_CUDA, "stream");
-      tmp_stream = true;
+    if (opts->keep_tableaus && !r->have_tabs && p->n_tab) {
+      r->dr.tabs = r->A.get<unsigned long long>(p->n_tab);
+      if (!r->dr.tabs) return fail(c, CCS_ERR_OOM, "tableau allocation failed");
+      r->have_tabs = true;
     }
-    cudaStream_t saved = c->stream;
-    c->stream = s;
-    cudaGraph_t g;
-    cudaError_t err = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
-    if (err != cudaSuccess) { c->stream = saved; return cuda_fail(c, err, "begin capture"); }
-    const long long before = launch_count();
-    int rc = enqueue_eval(c, p, r);
-    r->graph_launches = launch_count() - before;
-    note_launches(-r->graph_launches);      // captured, not launched
-    err = cudaStreamEndCapture(s, &g);
-    c->stream = saved;
-    if (tmp_stream) cudaStreamDestroy(s);
-    if (rc != CCS_OK) return rc;
-    if (err != cudaSuccess) return cuda_fail(c, err, "end capture");
-    err = cudaGraphInstantiate(&r->graph, g, 0);
-    cudaGraphDestroy(g);
-    if (err != cudaSuccess) return cuda_fail(c, err, "graph instantiate");
-    r->graph_key = e;
-  }
-  cudaError_t err = cudaGraphLaunch(r->graph, c->stream);
-  if (err != cudaSuccess) return cuda_fail(c, err, "graph launch");
-  note_launches(r->graph_launches);
-  return CCS_OK;
+    EvalParams e{};
+    e.mode = opts->mode;
+    e.shots = opts->mode == CCS_SAMPLED ? opts->shots : 0;
+    e.seed_lo = opts->seed_lo;
+    e.seed_hi = opts->seed_hi;
+    e.keep_tableaus = opts->keep_tableaus && r->have_tabs;
+    e.shared_body = opts->per_variant_body ? 0 : 1;
+    e.screen = e.shared_body && p->dp.n_cliff_frags > 0 && !e.keep_tableaus;
+    if (opts->hub_sampler < 0 || opts->hub_sampler > 2) return fail(c, CCS_ERR_INVALID_ARG, "bad hub sampler");
+    e.hub_sampler = opts->hub_sampler;
+    if (opts->hub_sampler == 1) r->hub_bytes = false;
+    if (opts->hub_sampler == 2) r->hub_bytes = p->hub_bytes_ok;
+    e.inv_shots = e.shots ? 1.0 / (double)e.shots : 0.0;
+    r->ep = e;
+    if (opts->autotune && !r->graph && opts->hub_sampler == 0) {
+      const bool prof = c->profiling;
+      c->profiling = false;
+      int rc = autotune(c, p, r);
+      c->profiling = prof;
+      if (rc != CCS_OK) return rc;
+    }
+    if (!opts->use_graph || c->profiling) {
+      c->stage_mask = 0;
+      return enqueue_eval(c, p, r);
+    }
+    const bool same = r->graph && r->graph_key.mode == e.mode && r->graph_key.shots == e.shots &&
+                      r->graph_key.seed_lo == e.seed_lo && r->graph_key.seed_hi == e.seed_hi &&
+                      r->graph_key.keep_tableaus == e.keep_tableaus && r->graph_key.shared_body == e.shared_body &&
+                      r->graph_key.hub_sampler == e.hub_sampler;
+    if (!same) {
+      if (r->graph) { cudaGraphExecDestroy(r->graph); r->graph = nullptr; }
+      cudaStream_t s = c->stream;
+      bool tmp_stream = false;
+      if (s == nullptr) {   // the legacy stream cannot be captured
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return fail(c, CCS_ERR_CUDA, "stream");
+        tmp_stream = true;
+      }
+      cudaStream_t saved = c->stream;
+      c->stream = s;
+      cudaGraph_t g;
+      cudaError_t err = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+      if (err != cudaSuccess) { c->stream = saved; return cuda_fail(c, err, "begin capture"); }
+      const long long before = launch_count();
+      int rc = enqueue_eval(c, p, r);
+      r->graph_launches = launch_count() - before;
+      note_launches(-r->graph_launches);      // captured, not launched
+      err = cudaStreamEndCapture(s, &g);
+      c->stream = saved;
+      if (tmp_stream) cudaStreamDestroy(s);
+      if (rc != CCS_OK) return rc;
+      if (err != cudaSuccess) return cuda_fail(c, err, "end capture");
+      err = cudaGraphInstantiate(&r->graph, g, 0);
+      cudaGraphDestroy(g);
+      if (err != cudaSuccess) return cuda_fail(c, err, "graph instantiate");
+      r->graph_key = e;
+    }
+    cudaError_t err = cudaGraphLaunch(r->graph, c->stream);
+    if (err != cudaSuccess) return cuda_fail(c, err, "graph launch");
+    note_launches(r->graph_launches);
+    return CCS_OK;
+  });
 }
 
 void ccs_res_free(ccs_res r) { delete r; }
@@ -1205,64 +1241,66 @@ static int check_status(ccs_ctx c, ccs_res r) {
 
 int ccs_recombine(ccs_ctx c, ccs_plan p, ccs_res r, const ccs_recomb_opts* opts, double* marginal_out,
                   double* zexp_out) {
-  if (!c || !p || !r || r->plan != p) return fail(c, CCS_ERR_INVALID_ARG, "bad arguments");
-  if (c->host_only) return fail(c, CCS_ERR_UNSUPPORTED, "host-only context cannot recombine");
-  if (!p->all_star) return fail(c, CCS_ERR_UNSUPPORTED, "fragments do not form a star");
-  const int prec = opts ? opts->precision : CCS_FP32;
-  const bool on_dev = opts && opts->outputs_on_device;
-  if (prec != CCS_FP32 && prec != CCS_BF16) return fail(c, CCS_ERR_INVALID_ARG, "bad precision");
-  cudaSetDevice(c->device);
-  const bool tc = !(opts && opts->no_tensor_cores);
-  RecombSizes rz{p->r_total, p->part_total, p->gemm_blocks, p->n_marg, p->n_zexp,
-                 p->d_direct_items, (int)p->direct_items.size(), (int)p->direct_stage_floats, p->chain,
-                 p->d_r_prefix, p->d_blk_prefix, p->d_out_prefix, p->d_z_prefix, p->max_tile_smem,
-                 tc ? p->pdev.data() : nullptr, (int)p->pdev.size(), r->rt_scratch};
-  cudaError_t e;
-  if (opts && opts->use_graph && !c->profiling) {
-    const int key = prec * 2 + (tc ? 1 : 0);
-    if (!r->rgraph || r->rgraph_key != key) {
-      if (r->rgraph) { cudaGraphExecDestroy(r->rgraph); r->rgraph = nullptr; }
-      cudaStream_t s = c->stream;
-      bool tmp_stream = false;
-      if (s == nullptr) {   // the legacy stream cannot be captured
-        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return fail(c, CCS_ERR_CUDA, "stream");
-        tmp_stream = true;
-      }
-      cudaGraph_t g;
-      if ((e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+  return abi_guard([&](int code, const char* m) { return fail(c, code, m); }, [&]() -> int {
+    if (!c || !p || !r || r->plan != p) return fail(c, CCS_ERR_INVALID_ARG, "bad arguments");
+    if (c->host_only) return fail(c, CCS_ERR_UNSUPPORTED, "host-only context cannot recombine");
+    if (!p->all_star) return fail(c, CCS_ERR_UNSUPPORTED, "fragments do not form a star");
+    const int prec = opts ? opts->precision : CCS_FP32;
+    const bool on_dev = opts && opts->outputs_on_device;
+    if (prec != CCS_FP32 && prec != CCS_BF16) return fail(c, CCS_ERR_INVALID_ARG, "bad precision");
+    cudaSetDevice(c->device);
+    const bool tc = !(opts && opts->no_tensor_cores);
+    RecombSizes rz{p->r_total, p->part_total, p->gemm_blocks, p->n_marg, p->n_zexp,
+                   p->d_direct_items, (int)p->direct_items.size(), (int)p->direct_stage_floats, p->chain,
+                   p->d_r_prefix, p->d_blk_prefix, p->d_out_prefix, p->d_z_prefix, p->max_tile_smem,
+                   tc ? p->pdev.data() : nullptr, (int)p->pdev.size(), r->rt_scratch};
+    cudaError_t e;
+    if (opts && opts->use_graph && !c->profiling) {
+      const int key = prec * 2 + (tc ? 1 : 0);
+      if (!r->rgraph || r->rgraph_key != key) {
+        if (r->rgraph) { cudaGraphExecDestroy(r->rgraph); r->rgraph = nullptr; }
+        cudaStream_t s = c->stream;
+        bool tmp_stream = false;
+        if (s == nullptr) {   // the legacy stream cannot be captured
+          if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return fail(c, CCS_ERR_CUDA, "stream");
+          tmp_stream = true;
+        }
+        cudaGraph_t g;
+        if ((e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+          if (tmp_stream) cudaStreamDestroy(s);
+          return cuda_fail(c, e, "begin capture");
+        }
+        const long long before = launch_count();
+        cudaError_t le = launch_recombine(p->dp, r->dr, prec, rz, r->scratch, r->dr.marg, r->dr.zexp, s);
+        r->rgraph_launches = launch_count() - before;
+        note_launches(-r->rgraph_launches);      // captured, not launched
+        e = cudaStreamEndCapture(s, &g);
         if (tmp_stream) cudaStreamDestroy(s);
-        return cuda_fail(c, e, "begin capture");
+        if (le != cudaSuccess) return cuda_fail(c, le, "recombine kernel");
+        if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
+        e = cudaGraphInstantiate(&r->rgraph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
+        r->rgraph_key = key;
       }
-      const long long before = launch_count();
-      cudaError_t le = launch_recombine(p->dp, r->dr, prec, rz, r->scratch, r->dr.marg, r->dr.zexp, s);
-      r->rgraph_launches = launch_count() - before;
-      note_launches(-r->rgraph_launches);      // captured, not launched
-      e = cudaStreamEndCapture(s, &g);
-      if (tmp_stream) cudaStreamDestroy(s);
-      if (le != cudaSuccess) return cuda_fail(c, le, "recombine kernel");
-      if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
-      e = cudaGraphInstantiate(&r->rgraph, g, 0);
-      cudaGraphDestroy(g);
-      if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
-      r->rgraph_key = key;
+      if ((e = cudaGraphLaunch(r->rgraph, c->stream)) != cudaSuccess) return cuda_fail(c, e, "graph launch");
+      note_launches(r->rgraph_launches);
+    } else {
+      stage_begin(c, ST_RECOMB);
+      e = launch_recombine(p->dp, r->dr, prec, rz, r->scratch, r->dr.marg, r->dr.zexp, c->stream);
+      if (e != cudaSuccess) return cuda_fail(c, e, "recombine kernel");
+      stage_end(c, ST_RECOMB);
     }
-    if ((e = cudaGraphLaunch(r->rgraph, c->stream)) != cudaSuccess) return cuda_fail(c, e, "graph launch");
-    note_launches(r->rgraph_launches);
-  } else {
-    stage_begin(c, ST_RECOMB);
-    e = launch_recombine(p->dp, r->dr, prec, rz, r->scratch, r->dr.marg, r->dr.zexp, c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e, "recombine kernel");
-    stage_end(c, ST_RECOMB);
-  }
-  const cudaMemcpyKind kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-  if (marginal_out && p->n_marg)
-    if ((e = cudaMemcpyAsync(marginal_out, r->dr.marg, p->n_marg * sizeof(double), kind, c->stream)) != cudaSuccess)
-      return cuda_fail(c, e, "copy marginal");
-  if (zexp_out && p->n_zexp)
-    if ((e = cudaMemcpyAsync(zexp_out, r->dr.zexp, p->n_zexp * sizeof(double), kind, c->stream)) != cudaSuccess)
-      return cuda_fail(c, e, "copy zexp");
-  if (on_dev) return CCS_OK;
-  return check_status(c, r);
+    const cudaMemcpyKind kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (marginal_out && p->n_marg)
+      if ((e = cudaMemcpyAsync(marginal_out, r->dr.marg, p->n_marg * sizeof(double), kind, c->stream)) != cudaSuccess)
+        return cuda_fail(c, e, "copy marginal");
+    if (zexp_out && p->n_zexp)
+      if ((e = cudaMemcpyAsync(zexp_out, r->dr.zexp, p->n_zexp * sizeof(double), kind, c->stream)) != cudaSuccess)
+        return cuda_fail(c, e, "copy zexp");
+    if (on_dev) return CCS_OK;
+    return check_status(c, r);
+  });
 }
 
 // --- inspection -------------------------------------------------------------
@@ -1275,44 +1313,52 @@ static const Frag* find_frag(ccs_plan p, int problem, int fragment, int* global)
 }
 
 int ccs_plan_counts(ccs_ctx c, ccs_plan p, int problem, int* nf, int* nc) {
-  if (!p || problem < 0 || problem >= (int)p->problems.size()) return fail(c, CCS_ERR_INVALID_ARG, "bad problem");
-  if (nf) *nf = (int)p->problems[problem].frag_ids.size();
-  if (nc) *nc = (int)p->problems[problem].cuts.size();
-  return CCS_OK;
+  return abi_guard([&](int code, const char* m) { return fail(c, code, m); }, [&]() -> int {
+    if (!p || problem < 0 || problem >= (int)p->problems.size()) return fail(c, CCS_ERR_INVALID_ARG, "bad problem");
+    if (nf) *nf = (int)p->problems[problem].frag_ids.size();
+    if (nc) *nc = (int)p->problems[problem].cuts.size();
+    return CCS_OK;
+  });
 }
 
 int ccs_fragment_info_get(ccs_ctx c, ccs_plan p, int problem, int fragment, ccs_fragment_info* out) {
-  int g;
-  const Frag* f = p ? find_frag(p, problem, fragment, &g) : nullptr;
-  if (!f || !out) return fail(c, CCS_ERR_INVALID_ARG, "bad fragment");
-  out->n_wires = f->n();
-  out->clifford = f->clifford;
-  out->n_variants = f->n_variants();
-  out->n_qin = (int)f->qin_wire.size();
-  out->n_qout = (int)f->qout_wire.size();
-  out->n_marg = (int)f->marg_wire.size();
-  out->n_meas = f->n_meas();
-  out->n_slots = (int)f->slots.size();
-  out->n_ops = f->clifford ? (int)f->cops.size() : (int)f->nops.size();
-  out->n_moments = f->n_moments();
-  out->n_zstrings = (int)f->zwires.size();
-  return CCS_OK;
+  return abi_guard([&](int code, const char* m) { return fail(c, code, m); }, [&]() -> int {
+    int g;
+    const Frag* f = p ? find_frag(p, problem, fragment, &g) : nullptr;
+    if (!f || !out) return fail(c, CCS_ERR_INVALID_ARG, "bad fragment");
+    out->n_wires = f->n();
+    out->clifford = f->clifford;
+    out->n_variants = f->n_variants();
+    out->n_qin = (int)f->qin_wire.size();
+    out->n_qout = (int)f->qout_wire.size();
+    out->n_marg = (int)f->marg_wire.size();
+    out->n_meas = f->n_meas();
+    out->n_slots = (int)f->slots.size();
+    out->n_ops = f->clifford ? (int)f->cops.size() : (int)f->nops.size();
+    out->n_moments = f->n_moments();
+    out->n_zstrings = (int)f->zwires.size();
+    return CCS_OK;
+  });
 }
 
 int ccs_plan_cuts(ccs_ctx c, ccs_plan p, int problem, ccs_cut* out, int cap) {
-  if (!p || problem < 0 || problem >= (int)p->problems.size()) return fail(c, CCS_ERR_INVALID_ARG, "bad problem");
-  const auto& cuts = p->problems[problem].cuts;
-  if (cap < (int)cuts.size()) return fail(c, CCS_ERR_INVALID_ARG, "buffer too small");
-  for (size_t i = 0; i < cuts.size(); ++i) out[i] = cuts[i];
-  return (int)cuts.size();
+  return abi_guard([&](int code, const char* m) { return fail(c, code, m); }, [&]() -> int {
+    if (!p || problem < 0 || problem >= (int)p->problems.size()) return fail(c, CCS_ERR_INVALID_ARG, "bad problem");
+    const auto& cuts = p->problems[problem].cuts;
+    if (cap < (int)cuts.size()) return fail(c, CCS_ERR_INVALID_ARG, "buffer too small");
+    for (size_t i = 0; i < cuts.size(); ++i) out[i] = cuts[i];
+    return (int)cuts.size();
+  });
 }
 
 int ccs_fragment_wires(ccs_ctx c, ccs_plan p, int problem, int fragment, uint32_t* out) {
-  int g;
-  const Frag* f = p ? find_frag(p, problem, fragment, &g) : nullptr;
-  if (!f || !out) return fail(c, CCS_ERR_INVALID_ARG, "bad fragment");
-  for (int i = 0; i < f->n(); ++i) { out[2 * i] = f->wires[i].first; out[2 * i + 1] = f->wires[i].second; }
-  return CCS_OK;
+  return abi_guard([&](int code, const char* m) { return fail(c, code, m); }, [&]() -> int {
+    int g;
+    const Frag* f = p ? find_frag(p, problem, fragment, &g) : nullptr;
+    if (!f || !out) return fail(c, CCS_ERR_INVALID_ARG, "bad fragment");
+    for (int i = 0; i < f->n(); ++i) { out[2 * i] = f->wires[i].first; out[2 * i + 1] = f->wires[i].second; }
+    return CCS_OK;
+  });
 }
 
 static int locate(ccs_ctx c, ccs_res r, int problem, int fragment, int variant, const FragDev** fd) {
@@ -1327,122 +1373,136 @@ static int locate(ccs_ctx c, ccs_res r, int problem, int fragment, int variant, 
 }
 
 int ccs_get_tableau(ccs_ctx c, ccs_res r, int problem, int fragment, int variant, uint8_t* out) {
-  const FragDev* d;
-  int rc = locate(c, r, problem, fragment, variant, &d);
-  if (rc) return rc;
-  if (!d->clifford || !r->ep.keep_tableaus || variant < 0) return fail(c, CCS_ERR_INVALID_ARG, "no tableau kept");
-  const int n = d->n, W = d->W, Wh = d->Wh, ncol = 2 * n + 3;
-  std::vector<unsigned long long> h((size_t)ncol * W);
-  cudaError_t e = cudaMemcpy(h.data(), r->dr.tabs + d->tab_off + (long long)variant * ncol * W,
-                             h.size() * 8, cudaMemcpyDeviceToHost);
-  if (e != cudaSuccess) return cuda_fail(c, e, "copy tableau");
-  auto bit = [&](int col, int row) -> uint8_t {
-    const int word = row < n ? row / 64 : Wh + (row - n) / 64;
-    const int b = row < n ? row % 64 : (row - n) % 64;
-    return (uint8_t)((h[(size_t)col * W + word] >> b) & 1ull);
-  };
-  for (int row = 0; row < 2 * n; ++row) {
-    uint8_t* o = out + (size_t)row * (2 * n + 1);
-    for (int j = 0; j < n; ++j) { o[j] = bit(j, row); o[n + j] = bit(n + 1 + j, row); }
-    o[2 * n] = bit(2 * (n + 1), row);
-  }
-  return CCS_OK;
+  return abi_guard([&](int code, const char* m) { return fail(c, code, m); }, [&]() -> int {
+    const FragDev* d;
+    int rc = locate(c, r, problem, fragment, variant, &d);
+    if (rc) return rc;
+    if (!d->clifford || !r->ep.keep_tableaus || variant < 0) return fail(c, CCS_ERR_INVALID_ARG, "no tableau kept");
+    const int n = d->n, W = d->W, Wh = d->Wh, ncol = 2 * n + 3;
+    std::vector<unsigned long long> h((size_t)ncol * W);
+    cudaError_t e = cudaMemcpy(h.data(), r->dr.tabs + d->tab_off + (long long)variant * ncol * W,
+                               h.size() * 8, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "copy tableau");
+    auto bit = [&](int col, int row) -> uint8_t {
+      const int word = row < n ? row / 64 : Wh + (row - n) / 64;
+      const int b = row < n ? row % 64 : (row - n) % 64;
+      return (uint8_t)((h[(size_t)col * W + word] >> b) & 1ull);
+    };
+    for (int row = 0; row < 2 * n; ++row) {
+      uint8_t* o = out + (size_t)row * (2 * n + 1);
+      for (int j = 0; j < n; ++j) { o[j] = bit(j, row); o[n + j] = bit(n + 1 + j, row); }
+      o[2 * n] = bit(2 * (n + 1), row);
+    }
+    return CCS_OK;
+  });
 }
 
 int ccs_get_outcome_space(ccs_ctx c, ccs_res r, int problem, int fragment, int variant, uint64_t* off,
                           uint64_t* basis, int* rank) {
-  const FragDev* d;
-  int rc = locate(c, r, problem, fragment, variant, &d);
-  if (rc) return rc;
-  if (!d->clifford || variant < 0) return fail(c, CCS_ERR_INVALID_ARG, "not a Clifford variant");
-  SpaceRec s;
-  cudaError_t e = cudaMemcpy(&s, r->dr.spaces + d->space_off + variant, sizeof(s), cudaMemcpyDeviceToHost);
-  if (e != cudaSuccess) return cuda_fail(c, e, "copy space");
-  if (off) *off = s.off;
-  if (rank) *rank = s.rank;
-  if (basis)
-    for (int i = 0; i < s.rank; ++i) basis[i] = s.basis[i];
-  return CCS_OK;
+  return abi_guard([&](int code, const char* m) { return fail(c, code, m); }, [&]() -> int {
+    const FragDev* d;
+    int rc = locate(c, r, problem, fragment, variant, &d);
+    if (rc) return rc;
+    if (!d->clifford || variant < 0) return fail(c, CCS_ERR_INVALID_ARG, "not a Clifford variant");
+    SpaceRec s;
+    cudaError_t e = cudaMemcpy(&s, r->dr.spaces + d->space_off + variant, sizeof(s), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "copy space");
+    if (off) *off = s.off;
+    if (rank) *rank = s.rank;
+    if (basis)
+      for (int i = 0; i < s.rank; ++i) basis[i] = s.basis[i];
+    return CCS_OK;
+  });
 }
 
 int ccs_get_counts(ccs_ctx c, ccs_res r, int problem, int fragment, int variant, uint32_t* out) {
-  const FragDev* d;
-  int rc = locate(c, r, problem, fragment, variant, &d);
-  if (rc) return rc;
-  if (!d->clifford || r->ep.mode != CCS_SAMPLED || variant < 0) return fail(c, CCS_ERR_INVALID_ARG, "no counts");
-  if (d->role == 1 && !r->ep.keep_tableaus) return fail(c, CCS_ERR_INVALID_ARG, "hub counts are kept only with keep_tableaus");
-  cudaError_t e = cudaMemcpy(out, r->dr.counts + d->counts_off + ((long long)variant << d->nA),
-                             sizeof(uint32_t) << d->nA, cudaMemcpyDeviceToHost);
-  return e == cudaSuccess ? CCS_OK : cuda_fail(c, e, "copy counts");
+  return abi_guard([&](int code, const char* m) { return fail(c, code, m); }, [&]() -> int {
+    const FragDev* d;
+    int rc = locate(c, r, problem, fragment, variant, &d);
+    if (rc) return rc;
+    if (!d->clifford || r->ep.mode != CCS_SAMPLED || variant < 0) return fail(c, CCS_ERR_INVALID_ARG, "no counts");
+    if (d->role == 1 && !r->ep.keep_tableaus) return fail(c, CCS_ERR_INVALID_ARG, "hub counts are kept only with keep_tableaus");
+    cudaError_t e = cudaMemcpy(out, r->dr.counts + d->counts_off + ((long long)variant << d->nA),
+                               sizeof(uint32_t) << d->nA, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? CCS_OK : cuda_fail(c, e, "copy counts");
+  });
 }
 
 int ccs_get_dist(ccs_ctx c, ccs_res r, int problem, int fragment, int variant, float* out) {
-  const FragDev* d;
-  int rc = locate(c, r, problem, fragment, variant, &d);
-  if (rc) return rc;
-  if ((d->clifford && r->ep.mode != CCS_EXACT) || variant < 0) return fail(c, CCS_ERR_INVALID_ARG, "no distribution");
-  cudaError_t e = cudaMemcpy(out, r->dr.dist + d->dist_off + ((long long)variant << d->nA),
-                             sizeof(float) << d->nA, cudaMemcpyDeviceToHost);
-  return e == cudaSuccess ? CCS_OK : cuda_fail(c, e, "copy dist");
+  return abi_guard([&](int code, const char* m) { return fail(c, code, m); }, [&]() -> int {
+    const FragDev* d;
+    int rc = locate(c, r, problem, fragment, variant, &d);
+    if (rc) return rc;
+    if ((d->clifford && r->ep.mode != CCS_EXACT) || variant < 0) return fail(c, CCS_ERR_INVALID_ARG, "no distribution");
+    cudaError_t e = cudaMemcpy(out, r->dr.dist + d->dist_off + ((long long)variant << d->nA),
+                               sizeof(float) << d->nA, cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? CCS_OK : cuda_fail(c, e, "copy dist");
+  });
 }
 
 int ccs_get_zvals(ccs_ctx c, ccs_res r, int problem, int fragment, int variant, float* out) {
-  const FragDev* d;
-  int rc = locate(c, r, problem, fragment, variant, &d);
-  if (rc) return rc;
-  if (variant < 0) return fail(c, CCS_ERR_INVALID_ARG, "no variant");
-  const long long cnt = (long long)d->nz << d->qout;
-  if (cnt == 0) return CCS_OK;
-  cudaError_t e = cudaMemcpy(out, r->dr.zval + d->zval_off + (long long)variant * cnt, cnt * sizeof(float),
-                             cudaMemcpyDeviceToHost);
-  return e == cudaSuccess ? CCS_OK : cuda_fail(c, e, "copy Z values");
+  return abi_guard([&](int code, const char* m) { return fail(c, code, m); }, [&]() -> int {
+    const FragDev* d;
+    int rc = locate(c, r, problem, fragment, variant, &d);
+    if (rc) return rc;
+    if (variant < 0) return fail(c, CCS_ERR_INVALID_ARG, "no variant");
+    const long long cnt = (long long)d->nz << d->qout;
+    if (cnt == 0) return CCS_OK;
+    cudaError_t e = cudaMemcpy(out, r->dr.zval + d->zval_off + (long long)variant * cnt, cnt * sizeof(float),
+                               cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? CCS_OK : cuda_fail(c, e, "copy Z values");
+  });
 }
 
 int ccs_get_operand(ccs_ctx c, ccs_res r, int problem, int fragment, float* out) {
-  const FragDev* d;
-  int rc = locate(c, r, problem, fragment, -1, &d);
-  if (rc) return rc;
-  if (d->role == 0) return fail(c, CCS_ERR_INVALID_ARG, "not part of a star contraction");
-  const long long cnt = (1ll << d->m) << (2 * d->n_slots);
-  if (d->role != 1) {
-    cudaError_t e = cudaMemcpy(out, r->dr.TQ + d->T_off, cnt * sizeof(float), cudaMemcpyDeviceToHost);
-    return e == cudaSuccess ? CCS_OK : cuda_fail(c, e, "copy operand");
-  }
-  // the hub's Q is stored transposed on the device ([d][o]); return [o][d]
-  std::vector<float> t(cnt);
-  cudaError_t e = cudaMemcpy(t.data(), r->dr.TQ + d->T_off, cnt * sizeof(float), cudaMemcpyDeviceToHost);
-  if (e != cudaSuccess) return cuda_fail(c, e, "copy operand");
-  const long long M = 1ll << d->m, K = 1ll << (2 * d->n_slots);
-  for (long long k = 0; k < K; ++k)
-    for (long long o = 0; o < M; ++o) out[o * K + k] = t[k * M + o];
-  return CCS_OK;
+  return abi_guard([&](int code, const char* m) { return fail(c, code, m); }, [&]() -> int {
+    const FragDev* d;
+    int rc = locate(c, r, problem, fragment, -1, &d);
+    if (rc) return rc;
+    if (d->role == 0) return fail(c, CCS_ERR_INVALID_ARG, "not part of a star contraction");
+    const long long cnt = (1ll << d->m) << (2 * d->n_slots);
+    if (d->role != 1) {
+      cudaError_t e = cudaMemcpy(out, r->dr.TQ + d->T_off, cnt * sizeof(float), cudaMemcpyDeviceToHost);
+      return e == cudaSuccess ? CCS_OK : cuda_fail(c, e, "copy operand");
+    }
+    // the hub's Q is stored transposed on the device ([d][o]); return [o][d]
+    std::vector<float> t(cnt);
+    cudaError_t e = cudaMemcpy(t.data(), r->dr.TQ + d->T_off, cnt * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "copy operand");
+    const long long M = 1ll << d->m, K = 1ll << (2 * d->n_slots);
+    for (long long k = 0; k < K; ++k)
+      for (long long o = 0; o < M; ++o) out[o * K + k] = t[k * M + o];
+    return CCS_OK;
+  });
 }
 
 int ccs_get_tensor(ccs_ctx c, ccs_res r, int problem, int fragment, float* out) {
-  const FragDev* d;
-  int rc = locate(c, r, problem, fragment, -1, &d);
-  if (rc) return rc;
-  const long long cnt = (1ll << d->m) << (2 * d->n_slots);
-  if (d->role == 1 && d->clifford && r->ep.mode == CCS_SAMPLED && !r->ep.keep_tableaus)
-    return fail(c, CCS_ERR_INVALID_ARG, "a sampled hub's tensor needs its counts (keep_tableaus)");
-  if (d->role == 1) {   // a hub's T is not formed on the hot path: fold it now
-    const int g = (int)(d - r->plan->fdev.data());
-    std::vector<int> fi{g};
-    std::vector<long long> tp{0, cnt};
-    Allocs tmp;
-    tmp.ctx = c;
-    int* dfi; long long* dtp;
-    if (!upload(c, tmp, fi, &dfi) || !upload(c, tmp, tp, &dtp)) {
+  return abi_guard([&](int code, const char* m) { return fail(c, code, m); }, [&]() -> int {
+    const FragDev* d;
+    int rc = locate(c, r, problem, fragment, -1, &d);
+    if (rc) return rc;
+    const long long cnt = (1ll << d->m) << (2 * d->n_slots);
+    if (d->role == 1 && d->clifford && r->ep.mode == CCS_SAMPLED && !r->ep.keep_tableaus)
+      return fail(c, CCS_ERR_INVALID_ARG, "a sampled hub's tensor needs its counts (keep_tableaus)");
+    if (d->role == 1) {   // a hub's T is not formed on the hot path: fold it now
+      const int g = (int)(d - r->plan->fdev.data());
+      std::vector<int> fi{g};
+      std::vector<long long> tp{0, cnt};
+      Allocs tmp;
+      tmp.ctx = c;
+      int* dfi; long long* dtp;
+      if (!upload(c, tmp, fi, &dfi) || !upload(c, tmp, tp, &dtp)) {
+        tmp.release();
+        return fail(c, CCS_ERR_OOM, "tensor fold buffers");
+      }
+      cudaError_t e2 = launch_fold(r->plan->dp, r->dr, r->ep, FoldSet{dfi, dtp, 1, cnt}, c->stream);
+      if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(c->stream);
       tmp.release();
-      return fail(c, CCS_ERR_OOM, "tensor fold buffers");
+      if (e2 != cudaSuccess) return cuda_fail(c, e2, "tensor fold");
     }
-    cudaError_t e2 = launch_fold(r->plan->dp, r->dr, r->ep, FoldSet{dfi, dtp, 1, cnt}, c->stream);
-    if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(c->stream);
-    tmp.release();
-    if (e2 != cudaSuccess) return cuda_fail(c, e2, "tensor fold");
-  }
-  cudaError_t e = cudaMemcpy(out, r->dr.T + d->T_off, cnt * sizeof(float), cudaMemcpyDeviceToHost);
-  return e == cudaSuccess ? CCS_OK : cuda_fail(c, e, "copy tensor");
+    cudaError_t e = cudaMemcpy(out, r->dr.T + d->T_off, cnt * sizeof(float), cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? CCS_OK : cuda_fail(c, e, "copy tensor");
+  });
 }
 
 }  // extern "C"
@@ -1462,31 +1522,33 @@ float* g_noalloc_addr[kMaxDevices] = {};
 
 extern "C" int ccs_recombine_noalloc(ccs_ctx c, ccs_plan p, ccs_res r, int precision, double* marginal_out,
                                      double* zexp_out) {
-  if (!c || !p || !r || r->plan != p) return fail(c, CCS_ERR_INVALID_ARG, "bad arguments");
-  if (c->host_only) return fail(c, CCS_ERR_UNSUPPORTED, "host-only context cannot recombine");
-  if (!p->all_star) return fail(c, CCS_ERR_UNSUPPORTED, "fragments do not form a star");
-  if (precision != CCS_FP32 && precision != CCS_BF16) return fail(c, CCS_ERR_INVALID_ARG, "bad precision");
-  if ((p->n_marg && !marginal_out) || (p->n_zexp && !zexp_out))
-    return fail(c, CCS_ERR_INVALID_ARG, "null output buffer");
-  const long long need = p->r_total + p->part_total;
-  if (need > kNoAllocScratchFloats)
-    return fail(c, CCS_ERR_UNSUPPORTED,
-                "recombination needs " + std::to_string(need * 4) + " bytes of scratch; the fixed scratch of "
-                "ccs_recombine_noalloc holds " + std::to_string(kNoAllocScratchFloats * 4) + " bytes");
-  if (c->device < 0 || c->device >= kMaxDevices) return fail(c, CCS_ERR_UNSUPPORTED, "device index too large");
-  cudaError_t e = cudaSetDevice(c->device);
-  if (e != cudaSuccess) return cuda_fail(c, e, "set device");
-  if (!g_noalloc_addr[c->device]) {   // first call on this device: resolve the array's address
-    float* ptr = nullptr;
-    e = cudaGetSymbolAddress((void**)&ptr, g_noalloc_scratch);
-    if (e != cudaSuccess) return cuda_fail(c, e, "cudaGetSymbolAddress of the fixed scratch");
-    g_noalloc_addr[c->device] = ptr;
-  }
-  RecombSizes rz{p->r_total, p->part_total, p->gemm_blocks, p->n_marg, p->n_zexp,
-                 p->d_direct_items, (int)p->direct_items.size(), (int)p->direct_stage_floats, p->chain,
-                 p->d_r_prefix, p->d_blk_prefix, p->d_out_prefix, p->d_z_prefix, p->max_tile_smem,
-                 nullptr, 0, nullptr};
-  e = launch_recombine(p->dp, r->dr, precision, rz, g_noalloc_addr[c->device], marginal_out, zexp_out, c->stream);
-  if (e != cudaSuccess) return cuda_fail(c, e, "recombine kernel");
-  return CCS_OK;
+  return abi_guard([&](int code, const char* m) { return fail(c, code, m); }, [&]() -> int {
+    if (!c || !p || !r || r->plan != p) return fail(c, CCS_ERR_INVALID_ARG, "bad arguments");
+    if (c->host_only) return fail(c, CCS_ERR_UNSUPPORTED, "host-only context cannot recombine");
+    if (!p->all_star) return fail(c, CCS_ERR_UNSUPPORTED, "fragments do not form a star");
+    if (precision != CCS_FP32 && precision != CCS_BF16) return fail(c, CCS_ERR_INVALID_ARG, "bad precision");
+    if ((p->n_marg && !marginal_out) || (p->n_zexp && !zexp_out))
+      return fail(c, CCS_ERR_INVALID_ARG, "null output buffer");
+    const long long need = p->r_total + p->part_total;
+    if (need > kNoAllocScratchFloats)
+      return fail(c, CCS_ERR_UNSUPPORTED,
+                  "recombination needs " + std::to_string(need * 4) + " bytes of scratch; the fixed scratch of "
+                  "ccs_recombine_noalloc holds " + std::to_string(kNoAllocScratchFloats * 4) + " bytes");
+    if (c->device < 0 || c->device >= kMaxDevices) return fail(c, CCS_ERR_UNSUPPORTED, "device index too large");
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "set device");
+    if (!g_noalloc_addr[c->device]) {   // first call on this device: resolve the array's address
+      float* ptr = nullptr;
+      e = cudaGetSymbolAddress((void**)&ptr, g_noalloc_scratch);
+      if (e != cudaSuccess) return cuda_fail(c, e, "cudaGetSymbolAddress of the fixed scratch");
+      g_noalloc_addr[c->device] = ptr;
+    }
+    RecombSizes rz{p->r_total, p->part_total, p->gemm_blocks, p->n_marg, p->n_zexp,
+                   p->d_direct_items, (int)p->direct_items.size(), (int)p->direct_stage_floats, p->chain,
+                   p->d_r_prefix, p->d_blk_prefix, p->d_out_prefix, p->d_z_prefix, p->max_tile_smem,
+                   nullptr, 0, nullptr};
+    e = launch_recombine(p->dp, r->dr, precision, rz, g_noalloc_addr[c->device], marginal_out, zexp_out, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "recombine kernel");
+    return CCS_OK;
+  });
 }

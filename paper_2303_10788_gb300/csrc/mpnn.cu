@@ -19,6 +19,7 @@
 #include <string>
 #include <vector>
 
+#include "abi_guard.hpp"
 #include "kernels.cuh"
 
 namespace ccs {
@@ -315,43 +316,45 @@ extern "C" {
 int ccs_mpnn_num_params(void) { return kParams; }
 
 int ccs_mpnn_create(ccs_ctx c, uint64_t seed, ccs_mpnn* out) {
-  if (!c || !out) return CCS_ERR_INVALID_ARG;
-  *out = nullptr;
-  auto* n = new ccs_mpnn_s();
-  n->ctx = c;
-  bool ok = cudaMalloc(&n->master, kParams * 4) == cudaSuccess && cudaMalloc(&n->w16, kParams * 2) == cudaSuccess &&
-            cudaMalloc(&n->grad, kParams * 4) == cudaSuccess && cudaMalloc(&n->m, kParams * 4) == cudaSuccess &&
-            cudaMalloc(&n->v, kParams * 4) == cudaSuccess;
-  if (!ok) {
-    ccs_mpnn_free(n);
-    return CCS_ERR_OOM;
-  }
-  // He-style uniform init from a 64-bit LCG; biases zero
-  std::vector<float> h(kParams, 0.f);
-  uint64_t st = seed * 6364136223846793005ull + 1442695040888963407ull;
-  auto uni = [&]() {
-    st = st * 6364136223846793005ull + 1442695040888963407ull;
-    return (float)((st >> 11) * (1.0 / 9007199254740992.0)) * 2.f - 1.f;
-  };
-  auto fill = [&](int off, int rows, int cols) {
-    const float a = std::sqrt(6.f / (float)cols);
-    for (int i = 0; i < rows * cols; ++i) h[off + i] = a * uni();
-  };
-  fill(oWin, kH, kIn);
-  for (int l = 0; l < kLayers; ++l) {
-    fill(oLayer + l * kLayerSize, kH, kH);
-    fill(oLayer + l * kLayerSize + kH * kH, kH, kH);
-  }
-  fill(oWr1, kH, kR);
-  fill(oWr2, 1, kH);
-  if (ccs_mpnn_set_params(c, n, h.data()) != CCS_OK) {
-    ccs_mpnn_free(n);
-    return CCS_ERR_CUDA;
-  }
-  cudaMemset(n->m, 0, kParams * 4);
-  cudaMemset(n->v, 0, kParams * 4);
-  *out = n;
-  return CCS_OK;
+  return abi_guard([](int code, const char*) { return code; }, [&]() -> int {
+    if (!c || !out) return CCS_ERR_INVALID_ARG;
+    *out = nullptr;
+    auto* n = new ccs_mpnn_s();
+    n->ctx = c;
+    bool ok = cudaMalloc(&n->master, kParams * 4) == cudaSuccess && cudaMalloc(&n->w16, kParams * 2) == cudaSuccess &&
+              cudaMalloc(&n->grad, kParams * 4) == cudaSuccess && cudaMalloc(&n->m, kParams * 4) == cudaSuccess &&
+              cudaMalloc(&n->v, kParams * 4) == cudaSuccess;
+    if (!ok) {
+      ccs_mpnn_free(n);
+      return CCS_ERR_OOM;
+    }
+    // He-style uniform init from a 64-bit LCG; biases zero
+    std::vector<float> h(kParams, 0.f);
+    uint64_t st = seed * 6364136223846793005ull + 1442695040888963407ull;
+    auto uni = [&]() {
+      st = st * 6364136223846793005ull + 1442695040888963407ull;
+      return (float)((st >> 11) * (1.0 / 9007199254740992.0)) * 2.f - 1.f;
+    };
+    auto fill = [&](int off, int rows, int cols) {
+      const float a = std::sqrt(6.f / (float)cols);
+      for (int i = 0; i < rows * cols; ++i) h[off + i] = a * uni();
+    };
+    fill(oWin, kH, kIn);
+    for (int l = 0; l < kLayers; ++l) {
+      fill(oLayer + l * kLayerSize, kH, kH);
+      fill(oLayer + l * kLayerSize + kH * kH, kH, kH);
+    }
+    fill(oWr1, kH, kR);
+    fill(oWr2, 1, kH);
+    if (ccs_mpnn_set_params(c, n, h.data()) != CCS_OK) {
+      ccs_mpnn_free(n);
+      return CCS_ERR_CUDA;
+    }
+    cudaMemset(n->m, 0, kParams * 4);
+    cudaMemset(n->v, 0, kParams * 4);
+    *out = n;
+    return CCS_OK;
+  });
 }
 
 void ccs_mpnn_free(ccs_mpnn n) {
@@ -365,60 +368,70 @@ void ccs_mpnn_free(ccs_mpnn n) {
 }
 
 int ccs_mpnn_params(ccs_ctx c, ccs_mpnn n, float* out) {
-  if (!c || !n || !out) return CCS_ERR_INVALID_ARG;
-  cudaStreamSynchronize(c_stream(c));
-  return cudaMemcpy(out, n->master, kParams * 4, cudaMemcpyDeviceToHost) == cudaSuccess ? CCS_OK : CCS_ERR_CUDA;
+  return abi_guard([](int code, const char*) { return code; }, [&]() -> int {
+    if (!c || !n || !out) return CCS_ERR_INVALID_ARG;
+    cudaStreamSynchronize(c_stream(c));
+    return cudaMemcpy(out, n->master, kParams * 4, cudaMemcpyDeviceToHost) == cudaSuccess ? CCS_OK : CCS_ERR_CUDA;
+  });
 }
 
 int ccs_mpnn_set_params(ccs_ctx c, ccs_mpnn n, const float* in) {
-  if (!c || !n || !in) return CCS_ERR_INVALID_ARG;
-  if (cudaMemcpy(n->master, in, kParams * 4, cudaMemcpyHostToDevice) != cudaSuccess) return CCS_ERR_CUDA;
-  to_half<<<blocks(kParams), 256>>>(n->master, n->w16, kParams); note_launch();
-  n->step = 0;
-  return cudaDeviceSynchronize() == cudaSuccess ? CCS_OK : CCS_ERR_CUDA;
+  return abi_guard([](int code, const char*) { return code; }, [&]() -> int {
+    if (!c || !n || !in) return CCS_ERR_INVALID_ARG;
+    if (cudaMemcpy(n->master, in, kParams * 4, cudaMemcpyHostToDevice) != cudaSuccess) return CCS_ERR_CUDA;
+    to_half<<<blocks(kParams), 256>>>(n->master, n->w16, kParams); note_launch();
+    n->step = 0;
+    return cudaDeviceSynchronize() == cudaSuccess ? CCS_OK : CCS_ERR_CUDA;
+  });
 }
 
 int ccs_mpnn_forward(ccs_ctx c, ccs_mpnn n, const ccs_graph_batch* b, float* pred) {
-  if (!c || !n || !b || !pred || b->n_graphs <= 0) return CCS_ERR_INVALID_ARG;
-  cudaStream_t s = c_stream(c);
-  Batch d;
-  int rc = upload_batch(b, nullptr, s, d);
-  if (rc != CCS_OK) return rc;
-  forward(n, d, s);
-  if (cudaMemcpyAsync(pred, d.y, d.g * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess) return CCS_ERR_CUDA;
-  return cudaStreamSynchronize(s) == cudaSuccess ? CCS_OK : CCS_ERR_CUDA;
+  return abi_guard([](int code, const char*) { return code; }, [&]() -> int {
+    if (!c || !n || !b || !pred || b->n_graphs <= 0) return CCS_ERR_INVALID_ARG;
+    cudaStream_t s = c_stream(c);
+    Batch d;
+    int rc = upload_batch(b, nullptr, s, d);
+    if (rc != CCS_OK) return rc;
+    forward(n, d, s);
+    if (cudaMemcpyAsync(pred, d.y, d.g * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess) return CCS_ERR_CUDA;
+    return cudaStreamSynchronize(s) == cudaSuccess ? CCS_OK : CCS_ERR_CUDA;
+  });
 }
 
 int ccs_mpnn_gradient(ccs_ctx c, ccs_mpnn n, const ccs_graph_batch* b, const float* target, float* loss,
                       float* grad) {
-  if (!c || !n || !b || !target || b->n_graphs <= 0) return CCS_ERR_INVALID_ARG;
-  cudaStream_t s = c_stream(c);
-  Batch d;
-  int rc = upload_batch(b, target, s, d);
-  if (rc != CCS_OK) return rc;
-  forward(n, d, s);
-  backward(n, d, s);
-  if (loss && cudaMemcpyAsync(loss, d.loss, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess) return CCS_ERR_CUDA;
-  if (grad && cudaMemcpyAsync(grad, n->grad, kParams * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess)
-    return CCS_ERR_CUDA;
-  return cudaStreamSynchronize(s) == cudaSuccess ? CCS_OK : CCS_ERR_CUDA;
+  return abi_guard([](int code, const char*) { return code; }, [&]() -> int {
+    if (!c || !n || !b || !target || b->n_graphs <= 0) return CCS_ERR_INVALID_ARG;
+    cudaStream_t s = c_stream(c);
+    Batch d;
+    int rc = upload_batch(b, target, s, d);
+    if (rc != CCS_OK) return rc;
+    forward(n, d, s);
+    backward(n, d, s);
+    if (loss && cudaMemcpyAsync(loss, d.loss, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess) return CCS_ERR_CUDA;
+    if (grad && cudaMemcpyAsync(grad, n->grad, kParams * 4, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      return CCS_ERR_CUDA;
+    return cudaStreamSynchronize(s) == cudaSuccess ? CCS_OK : CCS_ERR_CUDA;
+  });
 }
 
 int ccs_mpnn_train_step(ccs_ctx c, ccs_mpnn n, const ccs_graph_batch* b, const float* target, float lr,
                         float* loss) {
-  if (!c || !n || !b || !target || b->n_graphs <= 0) return CCS_ERR_INVALID_ARG;
-  cudaStream_t s = c_stream(c);
-  Batch d;
-  int rc = upload_batch(b, target, s, d);
-  if (rc != CCS_OK) return rc;
-  forward(n, d, s);
-  backward(n, d, s);
-  n->step += 1;
-  const float b1 = 0.9f, b2 = 0.999f;
-  const float c1 = 1.f - std::pow(b1, (float)n->step), c2 = 1.f - std::pow(b2, (float)n->step);
-  adam<<<blocks(kParams), 256, 0, s>>>(n->master, n->w16, n->grad, n->m, n->v, kParams, lr, b1, b2, c1, c2, 1e-8f); note_launch();
-  if (loss && cudaMemcpyAsync(loss, d.loss, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess) return CCS_ERR_CUDA;
-  return cudaStreamSynchronize(s) == cudaSuccess ? CCS_OK : CCS_ERR_CUDA;
+  return abi_guard([](int code, const char*) { return code; }, [&]() -> int {
+    if (!c || !n || !b || !target || b->n_graphs <= 0) return CCS_ERR_INVALID_ARG;
+    cudaStream_t s = c_stream(c);
+    Batch d;
+    int rc = upload_batch(b, target, s, d);
+    if (rc != CCS_OK) return rc;
+    forward(n, d, s);
+    backward(n, d, s);
+    n->step += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - std::pow(b1, (float)n->step), c2 = 1.f - std::pow(b2, (float)n->step);
+    adam<<<blocks(kParams), 256, 0, s>>>(n->master, n->w16, n->grad, n->m, n->v, kParams, lr, b1, b2, c1, c2, 1e-8f); note_launch();
+    if (loss && cudaMemcpyAsync(loss, d.loss, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess) return CCS_ERR_CUDA;
+    return cudaStreamSynchronize(s) == cudaSuccess ? CCS_OK : CCS_ERR_CUDA;
+  });
 }
 
 }  // extern "C"

@@ -189,6 +189,13 @@ std::vector<std::vector<const Fused*>> fuse_and_layer(const Frag& f, std::vector
 
 }  // namespace
 
+int check_circuit(const ccs_problem& q, std::string& err) {
+  if (q.n_qubits == 0 || (q.n_gates && !q.gates)) { err = "empty circuit"; return CCS_ERR_INVALID_ARG; }
+  if (q.n_qubits > kMaxCircuitQubits) { err = "too many qubits"; return CCS_ERR_INVALID_ARG; }
+  if (q.n_gates > kMaxCircuitGates) { err = "too many gates"; return CCS_ERR_INVALID_ARG; }
+  return CCS_OK;
+}
+
 int load_gates(const ccs_gate* G, uint32_t ng, std::vector<std::array<int, 3>>& gates,
                std::vector<double>& gparam, std::string& err) {
   static const int kSPow[4] = {kOpI, CCS_S, CCS_Z, CCS_SDG};   // S^0 .. S^3

@@ -20,6 +20,9 @@ constexpr int kMaxNCWidth = 12;     // complex64 statevector of 2^12 amplitudes 
 constexpr int kMaxTableauQubits = 640;  // (2n+3) x 2*ceil(n/64) words fit 227 KB of smem
 constexpr int kMaxCuts = 12;
 constexpr int kMaxMarginal = 24;
+// Circuit size accepted at the ABI (host arrays are linear in both).
+constexpr uint32_t kMaxCircuitQubits = 1u << 24;
+constexpr uint32_t kMaxCircuitGates = 1u << 30;
 
 // Internal opcode of a Z^a gate with 2a = 0 mod 4 (the identity): kept as a
 // gate so that cut positions, which are gate indices, stay valid.
@@ -33,6 +36,10 @@ inline bool is_nonclifford_op(int op) { return op == CCS_T || op == CCS_TDG || o
 // exponent reduced mod 2 in `gparam` (0 for every other gate).
 int load_gates(const ccs_gate* g, uint32_t n_gates, std::vector<std::array<int, 3>>& gates,
                std::vector<double>& gparam, std::string& err);
+
+// CCS_OK, or INVALID_ARG for an empty circuit, a null gate list or a size
+// beyond kMaxCircuitQubits / kMaxCircuitGates.
+int check_circuit(const ccs_problem& q, std::string& err);
 
 // A fused one- or two-qubit Clifford conjugation acting on the bit-sliced
 // columns (x_a, z_a, x_b, z_b) = (v0, v1, v2, v3):

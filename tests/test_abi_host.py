@@ -112,6 +112,12 @@ def test_error_codes(hctx):
     for a in (float("nan"), float("inf"), 1e308):                   # Z^a needs a finite 2a
         bad = Circuit(2); bad.add_zpow(0, a)
         _expect(hctx, [_P(bad, [], [0])], "INVALID_ARG")
+    _expect(hctx, [_P(Circuit(0), [], [])], "INVALID_ARG")          # no qubits
+    huge = Circuit((1 << 24) + 1); huge.add(H, 0)                   # beyond the qubit bound
+    _expect(hctx, [_P(huge, [], [0])], "INVALID_ARG")
+    with pytest.raises(ccs.CCSError) as e:                          # the cut search checks it too
+        ccs.ccs_cut_candidates(hctx, _P(huge, None, [0]))
+    assert "INVALID_ARG" in str(e.value)
     loop = Circuit(2)                                               # both ends of the cut in one fragment
     loop.add(CX, 0, 1); loop.add(H, 0); loop.add(CX, 0, 1)
     _expect(hctx, [_P(loop, [(0, 1)], [0])], "UNSUPPORTED")
