@@ -286,9 +286,6 @@ __global__ void __launch_bounds__(256) body_kernel(DevPlan P, DevRes R, int smem
   for (int c = tid; c < ncol; c += nt) dst[(size_t)c * W + w] = tab[c];
 }
 
-namespace {
-}  // namespace
-
 // --- Z images -------------------------------------------------------------
 // Pauli expectations of a variant without its tableau.  With the body's rows
 // D_j = U X_j U^+ and S_j = U Z_j U^+ (signs included), every Pauli Q on the

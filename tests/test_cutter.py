@@ -115,3 +115,28 @@ def test_hwea_300_qubits_plan(hctx):
         infos = [ccs.ccs_fragment_info_get(hctx, plan, 0, f) for f in range(nf)]
         assert nc in (1, 2)
         assert sorted((i["clifford"], i["n_wires"]) for i in infos) == [(0, 1), (1, 299 + nc)]
+
+
+@pytest.mark.parametrize("w", [hwea(60, rounds=5, n_t=2, n_z=0), sk_qaoa(14, n_t=2, zpow=True),
+                               small_star(n=12, depth=9, region_full=(0, 1, 2, 3), boundary=4, window=(2, 6),
+                                          n_t=3, seed=3)],
+                         ids=["hwea60", "skqaoa14_zpow", "star12"])
+def test_candidate_costs_from_oracle_fragments(hctx, w):
+    """Each candidate's cost is the work model summed over the fragments its
+    cuts give: recomputed here from the oracle's fragmenting (variants 4^qin
+    3^qout; Clifford: gates / 6 x 2 ceil(n / 64) + 1024 per variant;
+    statevector: gates x 2^n / 64 per variant; recombination 4^k 2^|o| / 16)."""
+    from oracle.cutting import fragment_circuit
+    cands = ccs.ccs_cut_candidates(hctx, _P(w.circuit, w.marginal), max_nc_width=6)
+    assert cands
+    for cuts, cost in cands[:12]:
+        frags, cc = fragment_circuit(w.circuit, cuts, w.marginal)
+        want = 0.0
+        for f in frags:
+            nv = float(f.n_variants)
+            if f.clifford:
+                want += nv * (len(f.gates) / 6.0 * 2.0 * np.ceil(f.n / 64.0) + 1024.0)
+            else:
+                want += nv * len(f.gates) * 2.0 ** f.n / 64.0
+        want += 4.0 ** len(cc) * 2.0 ** len(w.marginal) / 16.0
+        assert abs(cost - want) <= 1e-12 * want, (cuts, cost, want)
