@@ -140,3 +140,19 @@ def test_candidate_costs_from_oracle_fragments(hctx, w):
                 want += nv * len(f.gates) * 2.0 ** f.n / 64.0
         want += 4.0 ** len(cc) * 2.0 ** len(w.marginal) / 16.0
         assert abs(cost - want) <= 1e-12 * want, (cuts, cost, want)
+
+
+def test_learned_cut_data_path_on_host(hctx):
+    """The scorer's data path before any GPU work: the circuit population,
+    greedy candidates from a spawn pool (identical to direct calls, in
+    circuit order) and the judge filter (within the factor of the greedy
+    choice, at most max_cuts cuts)."""
+    from paper_2303_10788_gb300 import learned_cuts as lc
+    ws = lc.population(4, seed=77)
+    pooled = lc.candidates(ws, cap=6, procs=2)
+    direct = [ccs.ccs_cut_candidates(hctx, w, cap=6) for w in ws]
+    assert pooled == direct
+    for cs in pooled:
+        js = lc.judged(cs, judge=16.0, max_cuts=8)
+        assert js and js[0] == cs[0]
+        assert all(e <= 16.0 * cs[0][1] and len(c) <= 8 for c, e in js)
