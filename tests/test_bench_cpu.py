@@ -40,3 +40,15 @@ def test_reference_arm_other_ranks_are_silent():
     lines = _run(["--impl", "reference", "--workload", "config1", "--steps", "1", "--warmup", "0"],
                  {"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
     assert lines == []
+
+
+def test_cpu_baseline_single_and_threaded():
+    """The GPU arm's cpu_baseline: the oracle single-threaded and over all
+    host cores (spawned processes)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from workloads import config1
+    b = bench.oracle_baseline([config1()], threaded_budget_s=1.0)
+    assert b["kind"] == "oracle" and b["cores"] == 1 and b["value"] > 0
+    t = b["threaded"]
+    assert t["cores"] == (os.cpu_count() or 1) and t["value"] > 0 and t["unit"] == b["unit"]
