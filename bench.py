@@ -346,7 +346,7 @@ def run_ours(args, rank, world, local_rank):
             "e2e": {"value": units_per_step * world / e2e_s, "unit": UNIT, "circuits_per_s": world * len(ws) / e2e_s,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "clocks": clocks}
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:   # the oracle baseline at N = 1 only
         line["cpu_baseline"] = oracle_baseline(ws)
     if rank == 0:
         print(json.dumps(line), flush=True)
