@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -446,7 +447,9 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
     if (!c->host_only) cudaSetDevice(c->device);
     ccs_cut_opts o{kMaxCuts, 10, 0};
     if (opts) o = *opts;
-    auto plan = new ccs_plan_s();
+    // the plan is freed on every early return and on an exception
+    std::unique_ptr<ccs_plan_s> owned(new ccs_plan_s());
+    ccs_plan plan = owned.get();
     plan->ctx = c;
     plan->A.ctx = c;
     std::string err;
@@ -484,14 +487,14 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
       }
     });
     for (int pi = 0; pi < np; ++pi)
-      if (prc[pi] != CCS_OK) { delete plan; return fail(c, prc[pi], perr[pi]); }
+      if (prc[pi] != CCS_OK) { return fail(c, prc[pi], perr[pi]); }
     // the learned choice runs the scorer on the GPU: one problem at a time
     if (o.use_learned && c->cut_model && !c->host_only)
       for (int pi = 0; pi < np; ++pi)
         if (pc[pi].size() > 1) {
           int pick = 0;
           int rc = learned_pick(c, pr[pi], pc[pi], &pick);
-          if (rc != CCS_OK) { delete plan; return rc; }
+          if (rc != CCS_OK) { return rc; }
           pr[pi].cuts = pc[pi][pick].cuts;
         }
     parallel_for(np, [&](int pi) {
@@ -503,7 +506,7 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
       }
     });
     for (int pi = 0; pi < np; ++pi)
-      if (prc[pi] != CCS_OK) { delete plan; return fail(c, prc[pi], "problem " + std::to_string(pi) + ": " + perr[pi]); }
+      if (prc[pi] != CCS_OK) { return fail(c, prc[pi], "problem " + std::to_string(pi) + ": " + perr[pi]); }
     for (int pi = 0; pi < np; ++pi) {
       const int base = (int)plan->frags.size();      // fragment ids become plan-global
       for (auto& id : pr[pi].frag_ids) id += base;
@@ -627,7 +630,6 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
         if (f.clifford) { f.dist_off = off; off += (long long)f.nv << f.nA; }
     }
     if ((size_t)plan->cliff_smem_words * 8 > c->smem_optin && !items_c.empty()) {
-      delete plan;
       return fail(c, CCS_ERR_UNSUPPORTED, "Clifford fragment does not fit in shared memory");
     }
     // Items costliest first, ties in insertion order.  A fragment's items are
@@ -835,7 +837,7 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
       st.add(fidx_hn, &d_fidx_hn); st.add(tp_hn, &d_tp_hn);
       st.add(items_hub, &plan->d_items_hub); st.add(items_plain, &plan->d_items_plain);
       bool okf = st.commit(c, plan->A);
-      if (!okf) { delete plan; return fail(c, CCS_ERR_OOM, "plan upload failed"); }
+      if (!okf) { return fail(c, CCS_ERR_OOM, "plan upload failed"); }
       plan->fold_cliff = FoldSet{d_fidx_c, d_tp_c, (int)fidx_c.size(), tp_c.back()};
       plan->fold_nc = FoldSet{d_fidx_nc, d_tp_nc, (int)fidx_nc.size(), tp_nc.back()};
       plan->fold_hubs = FoldSet{d_fidx_h, d_tp_h, (int)fidx_h.size(), tp_h.back()};
@@ -845,7 +847,7 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
     if (c->host_only) {
       plan->dp.n_items_cliff = (int)items_c.size();
       plan->dp.n_items_nc = (int)items_nc.size();
-      *out = plan;
+      *out = owned.release();
       return CCS_OK;
     }
     DevPlan& dp = plan->dp;
@@ -861,7 +863,7 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
     st.add(plan->z_prefix, &plan->d_z_prefix); st.add(plan->r_prefix, &plan->d_r_prefix);
     st.add(plan->blk_prefix, &plan->d_blk_prefix); st.add(plan->direct_items, &plan->d_direct_items);
     bool ok = st.commit(c, plan->A);
-    if (!ok) { delete plan; return fail(c, CCS_ERR_OOM, "plan upload failed"); }
+    if (!ok) { return fail(c, CCS_ERR_OOM, "plan upload failed"); }
     dp.frags = dfr; dp.cops = dco; dp.nops = dno; dp.moments = dmo; dp.wires = dwi; dp.zoffs = dzo;
     dp.items_cliff = dic; dp.items_nc = din; dp.nc_basis_chunk = plan->nc_basis_chunk;
     dp.n_items_cliff = (int)items_c.size(); dp.n_items_nc = (int)items_nc.size();
@@ -875,8 +877,8 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
     dp.problems = dpr; dp.n_problems = (int)plan->pdev.size();
     dp.prep_ops = dpo; dp.basis_ops = dbo; dp.prep_mats = dpm; dp.basis_mats = dbm;
     cudaError_t e = cudaStreamSynchronize(c->stream);
-    if (e != cudaSuccess) { delete plan; return cuda_fail(c, e, "plan upload"); }
-    *out = plan;
+    if (e != cudaSuccess) { return cuda_fail(c, e, "plan upload"); }
+    *out = owned.release();
     return CCS_OK;
   });
 }
@@ -1097,7 +1099,8 @@ int ccs_eval_variants(ccs_ctx c, ccs_plan p, const ccs_eval_opts* opts, ccs_res*
     ccs_res r = *res;
     if (r && r->plan != p) return fail(c, CCS_ERR_INVALID_ARG, "result belongs to another plan");
     if (!r) {
-      r = new ccs_res_s();
+      std::unique_ptr<ccs_res_s> owned_r(new ccs_res_s());   // freed on a failed allocation or an exception
+      r = owned_r.get();
       r->plan = p;
       r->A.ctx = c;
       DevRes& d = r->dr;
@@ -1136,11 +1139,10 @@ int ccs_eval_variants(ccs_ctx c, ccs_plan p, const ccs_eval_opts* opts, ccs_res*
       if (!d.spaces || !d.dist || !d.zval || !d.T || !d.TQ || !d.marg || !d.zexp || !d.work || !d.status ||
           !d.body || !d.rowbasis || !d.zimg || !d.fragcnt || !d.pbasis ||
           !r->scratch || (p->rt_total && (!d.TQh || !r->rt_scratch))) {
-        delete r;
         return fail(c, CCS_ERR_OOM, "result allocation failed");
       }
       cudaMemsetAsync(d.status, 0, 4 * sizeof(unsigned), c->stream);
-      *res = r;
+      *res = owned_r.release();
     }
     // buffers a mode needs are added on first use; a replaced buffer drops the captured graph
     auto drop_graph = [&]() {
