@@ -98,6 +98,59 @@ struct WordGate {
   double param;
 };
 
+// rows (u0, u1) <- G (u0, u1) for a one-qubit gate G, n entries per row: the
+// Paulis, S, S^dagger and the identity as exact permutations / sign and
+// i-multiples, the phase gates on u1 only, H as r(u0 + u1), r(u0 - u1);
+// other gates as the full 2x2 product.
+void mix_rows(int op, double param, cd* u0, cd* u1, int n) {
+  switch (op) {
+    case kOpI: return;
+    case CCS_X:
+      for (int j = 0; j < n; ++j) std::swap(u0[j], u1[j]);
+      return;
+    case CCS_Y:
+      for (int j = 0; j < n; ++j) {
+        const cd a = u0[j], b = u1[j];
+        u0[j] = cd(b.imag(), -b.real());     // -i b
+        u1[j] = cd(-a.imag(), a.real());     //  i a
+      }
+      return;
+    case CCS_Z:
+      for (int j = 0; j < n; ++j) u1[j] = -u1[j];
+      return;
+    case CCS_S:
+      for (int j = 0; j < n; ++j) u1[j] = cd(-u1[j].imag(), u1[j].real());
+      return;
+    case CCS_SDG:
+      for (int j = 0; j < n; ++j) u1[j] = cd(u1[j].imag(), -u1[j].real());
+      return;
+    case CCS_T: case CCS_TDG: case CCS_ZPOW: {
+      cd G[4];
+      gate_matrix_1q(op, param, G);
+      for (int j = 0; j < n; ++j) u1[j] = G[3] * u1[j];
+      return;
+    }
+    case CCS_H: {
+      const double r = 1.0 / std::sqrt(2.0);
+      for (int j = 0; j < n; ++j) {
+        const cd a = u0[j], b = u1[j];
+        u0[j] = r * a + r * b;
+        u1[j] = r * a - r * b;
+      }
+      return;
+    }
+    default: {
+      cd G[4];
+      gate_matrix_1q(op, param, G);
+      for (int j = 0; j < n; ++j) {
+        const cd a = u0[j], b = u1[j];
+        u0[j] = G[0] * a + G[1] * b;
+        u1[j] = G[2] * a + G[3] * b;
+      }
+    }
+  }
+}
+
 // A fused op: statevector fragments keep the gate word (for the unitary);
 // Clifford fragments apply each gate to the op's 16-pattern planes as it
 // arrives, so no word is stored.
@@ -386,14 +439,8 @@ void compile_nc(Frag& f) {
       o.a = F->a;
       o.b = F->b;
       if (F->b < 0) {
-        cd U[4] = {1, 0, 0, 1};
-        for (auto& g : F->word) {
-          cd G[4], R[4];
-          gate_matrix_1q(g.op, g.param, G);
-          for (int i = 0; i < 2; ++i)
-            for (int j = 0; j < 2; ++j) R[i * 2 + j] = G[i * 2] * U[j] + G[i * 2 + 1] * U[2 + j];
-          for (int i = 0; i < 4; ++i) U[i] = R[i];
-        }
+        cd U[4] = {1, 0, 0, 1};    // U <- G U: rows 0 and 1 of the 2x2
+        for (auto& g : F->word) mix_rows(g.op, g.param, U, U + 2, 2);
         for (int i = 0; i < 4; ++i) { o.m[2 * i] = (float)U[i].real(); o.m[2 * i + 1] = (float)U[i].imag(); }
       } else {
         // U <- G U gate by gate, as row operations on the 4x4 (index = bit_a + 2 bit_b)
@@ -408,16 +455,9 @@ void compile_nc(Frag& f) {
           } else if (op == CCS_CZ) {   // row with both bits set: negate
             for (int j = 0; j < 4; ++j) U[3 * 4 + j] = -U[3 * 4 + j];
           } else {                     // one-qubit gate on role ra: mix row pairs
-            cd G[4];
-            gate_matrix_1q(op, g.param, G);
             for (int i0 = 0; i0 < 4; ++i0) {
               if ((i0 >> ra) & 1) continue;
-              const int i1 = i0 | (1 << ra);
-              for (int j = 0; j < 4; ++j) {
-                const cd u0 = U[i0 * 4 + j], u1 = U[i1 * 4 + j];
-                U[i0 * 4 + j] = G[0] * u0 + G[1] * u1;
-                U[i1 * 4 + j] = G[2] * u0 + G[3] * u1;
-              }
+              mix_rows(op, g.param, U + i0 * 4, U + (i0 | (1 << ra)) * 4, 4);
             }
           }
         }
