@@ -203,21 +203,20 @@ std::vector<std::vector<const Fused*>> fuse_and_layer(const Frag& f, std::vector
       }
     }
     if (planes && (g1[0] || g1[1])) {   // nf = (g1[0] on role 0) x (g1[1] on role 1), then the gate
-      uint32_t x[2] = {0, 0}, z[2] = {0, 0}, fl = 0;
-      for (int v = 0; v < 16; ++v)
-        for (int side = 0; side < 2; ++side) {
-          const int w = (v >> (2 * side)) & 3;            // this role's (x, z) as a one-qubit pattern
-          unsigned xo = w & 1, zo = (w >> 1) & 1, fo = 0;
-          if (g1[side]) {
-            xo = (g1[side]->px[0] >> w) & 1u;
-            zo = (g1[side]->pz[0] >> w) & 1u;
-            fo = (g1[side]->pf >> w) & 1u;
-          }
-          x[side] |= xo << v;
-          z[side] |= zo << v;
-          fl ^= fo << v;
-        }
-      nf.px[0] = x[0]; nf.px[1] = x[1]; nf.pz[0] = z[0]; nf.pz[1] = z[1]; nf.pf = fl;
+      // A one-qubit op's planes hold its images of the patterns w = 0..3 in
+      // bits 0..3.  Role 0 reads w from bits 0-1 of the two-qubit pattern v
+      // (the 4-bit image repeated in every nibble), role 1 from bits 2-3
+      // (bit k of the image filling nibble k).
+      auto rep = [](uint32_t t) { t &= 0xfu; return t * 0x1111u; };
+      auto spread = [](uint32_t t) {
+        return ((t & 1u) ? 0x000fu : 0u) | ((t & 2u) ? 0x00f0u : 0u) | ((t & 4u) ? 0x0f00u : 0u) |
+               ((t & 8u) ? 0xf000u : 0u);
+      };
+      nf.px[0] = g1[0] ? rep(g1[0]->px[0]) : kPX0;
+      nf.pz[0] = g1[0] ? rep(g1[0]->pz[0]) : kPZ0;
+      nf.px[1] = g1[1] ? spread(g1[1]->px[0]) : kPX1;
+      nf.pz[1] = g1[1] ? spread(g1[1]->pz[0]) : kPZ1;
+      nf.pf = (g1[0] ? rep(g1[0]->pf) : 0u) ^ (g1[1] ? spread(g1[1]->pf) : 0u);
     }
     for (int side = 0; side < 2; ++side)
       if (g1[side]) const_cast<Fused*>(g1[side])->word.clear();
