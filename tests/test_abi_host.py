@@ -158,3 +158,22 @@ def test_batched_plan_equals_single_plans():
         for f in range(nf):
             assert ccs.ccs_fragment_info_get(hctx, plan, pi, f) == ccs.ccs_fragment_info_get(hctx, one, 0, f)
             assert ccs.ccs_fragment_wires(hctx, plan, pi, f) == ccs.ccs_fragment_wires(hctx, one, 0, f)
+
+
+def test_clifford_zpow_plans_like_its_gate(hctx):
+    """Z^a with 2a an integer is planned as S^{2a}: Z^{1/2}, Z^1, Z^{-1/2}
+    give the same fragments and compiled op stream sizes as S, Z, S^dagger,
+    and Z^2 (the identity) stays a Clifford no-op."""
+    from workloads import ZPOW, S, SDG, Z
+    base = random_clifford_circuit(6, 60, seed=21)
+    for a, op in ((0.5, S), (1.0, Z), (-0.5, SDG), (2.0, None)):
+        cz, cg = Circuit(6, list(base.gates)), Circuit(6, list(base.gates))
+        cz.gates.insert(30, (ZPOW, 2, -1, a))
+        cg.gates.insert(30, (op, 2, -1) if op is not None else (S, 2, -1))
+        if op is None:
+            cg.gates.insert(31, (SDG, 2, -1))                       # S S^dagger: also the identity
+        iz = ccs.ccs_fragment_info_get(hctx, ccs.ccs_build_fragments(hctx, [_P(cz, [], [0, 2])]), 0, 0)
+        ig = ccs.ccs_fragment_info_get(hctx, ccs.ccs_build_fragments(hctx, [_P(cg, [], [0, 2])]), 0, 0)
+        assert iz["clifford"] and ig["clifford"]
+        if op is not None:
+            assert (iz["n_ops"], iz["n_moments"]) == (ig["n_ops"], ig["n_moments"])
