@@ -4,7 +4,6 @@
 
 #include <algorithm>
 #include <cmath>
-#include <map>
 #include <numeric>
 
 namespace ccs {
@@ -309,40 +308,54 @@ int fragment_problem(Problem& p, int pi, std::vector<Frag>& out, std::string& er
   for (auto& c : p.cuts) pos[c.qubit].push_back((int)c.gate_index);
   std::vector<int> base(n + 1, 0);
   for (int q = 0; q < n; ++q) base[q + 1] = base[q] + (int)pos[q].size() + 1;
-  auto seg = [&](int q, int g) {
-    return (int)(std::upper_bound(pos[q].begin(), pos[q].end(), g) - pos[q].begin());
+  // segment of each gate's operands, in one pass over the gates: a cut
+  // (q, g) starts q's next segment at gate g
+  std::vector<int> seg_a(ng), seg_b(ng, -1), next_cut(n, 0);
+  auto seg_at = [&](int q, int gi) {
+    int& k = next_cut[q];
+    while (k < (int)pos[q].size() && pos[q][k] <= gi) ++k;
+    return base[q] + k;
   };
-  UF uf(base[n]);
   for (int gi = 0; gi < ng; ++gi) {
-    auto& g = p.gates[gi];
-    if (is_two_qubit(g[0])) uf.join(base[g[1]] + seg(g[1], gi), base[g[2]] + seg(g[2], gi));
+    const auto& g = p.gates[gi];
+    seg_a[gi] = seg_at(g[1], gi);
+    if (is_two_qubit(g[0])) seg_b[gi] = seg_at(g[2], gi);
   }
+  UF uf(base[n]);
+  for (int gi = 0; gi < ng; ++gi)
+    if (seg_b[gi] >= 0) uf.join(seg_a[gi], seg_b[gi]);
   // fragments ordered by first wire; wires by (qubit, segment) = segment id
-  std::map<int, int> root_to_frag;
+  std::vector<int> root_to_frag(base[n], -1);
   std::vector<std::pair<int, int>> where(base[n]);
   const int first = (int)out.size();
-  for (int s = 0; s < base[n]; ++s) {
-    int r = uf.find(s);
-    auto it = root_to_frag.find(r);
-    if (it == root_to_frag.end()) {
-      it = root_to_frag.emplace(r, (int)out.size()).first;
-      Frag f;
-      f.problem = pi;
-      f.index = (int)out.size() - first;
-      out.push_back(std::move(f));
+  for (int q = 0, s = 0; q < n; ++q)
+    for (; s < base[q + 1]; ++s) {
+      const int r = uf.find(s);
+      if (root_to_frag[r] < 0) {
+        root_to_frag[r] = (int)out.size();
+        Frag f;
+        f.problem = pi;
+        f.index = (int)out.size() - first;
+        out.push_back(std::move(f));
+      }
+      Frag& f = out[root_to_frag[r]];
+      where[s] = {root_to_frag[r], f.n()};
+      f.wires.push_back({(uint32_t)q, (uint32_t)(s - base[q])});
     }
-    Frag& f = out[it->second];
-    int q = (int)(std::upper_bound(base.begin(), base.end(), s) - base.begin()) - 1;
-    where[s] = {it->second, f.n()};
-    f.wires.push_back({(uint32_t)q, (uint32_t)(s - base[q])});
+  {
+    std::vector<int> count(out.size() - first, 0);
+    for (int gi = 0; gi < ng; ++gi) count[where[seg_a[gi]].first - first]++;
+    for (size_t fi = 0; fi < count.size(); ++fi) {
+      out[first + fi].gates.reserve(count[fi]);
+      out[first + fi].gparam.reserve(count[fi]);
+    }
   }
   for (int gi = 0; gi < ng; ++gi) {
-    auto& g = p.gates[gi];
-    auto wa = where[base[g[1]] + seg(g[1], gi)];
+    const auto& g = p.gates[gi];
+    const auto wa = where[seg_a[gi]];
     Frag& f = out[wa.first];
-    if (is_two_qubit(g[0])) {
-      auto wb = where[base[g[2]] + seg(g[2], gi)];
-      f.gates.push_back({g[0], wa.second, wb.second});
+    if (seg_b[gi] >= 0) {
+      f.gates.push_back({g[0], wa.second, where[seg_b[gi]].second});
       f.gparam.push_back(0.0);
     } else {
       f.gates.push_back({g[0], wa.second, -1});
