@@ -128,6 +128,14 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def host_cores():
+    """Cores this process may run on (its affinity mask), else the CPU count."""
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
 def _oracle_chunk(args):
     """Worker of the threaded baseline (a spawned process): the oracle on a
     list of body variants."""
@@ -143,7 +151,7 @@ def oracle_threaded(w, n_variants, body, per_variant_s, budget_s=10.0):
     separate processes (spawned, so no CUDA state is inherited): each process
     evaluates its own body variants; only the parallel part is timed."""
     import multiprocessing as mp
-    procs = os.cpu_count() or 1
+    procs = host_cores()
     k = max(1, int(budget_s / 2 / max(per_variant_s, 1e-3)))
     chunks = [[(p * k + i) * 97 % n_variants for i in range(k)] for p in range(procs)]
     with mp.get_context("spawn").Pool(procs) as pool:
@@ -211,7 +219,7 @@ def run_reference(args, rank, world):
     body = max(range(len(frags)), key=lambda i: frags[i].n if frags[i].clifford else -1)
     nv = frags[body].n_variants
     nsamp = 8
-    procs = os.cpu_count() or 1
+    procs = host_cores()
     chunks = [[(p * nsamp + i) * 97 % nv for i in range(nsamp)] for p in range(procs)]
     pool = None
     try:

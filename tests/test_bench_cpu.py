@@ -51,4 +51,4 @@ def test_cpu_baseline_single_and_threaded():
     b = bench.oracle_baseline([config1()], threaded_budget_s=1.0)
     assert b["kind"] == "oracle" and b["cores"] == 1 and b["value"] > 0
     t = b["threaded"]
-    assert t["cores"] == (os.cpu_count() or 1) and t["value"] > 0 and t["unit"] == b["unit"]
+    assert t["cores"] == bench.host_cores() and t["value"] > 0 and t["unit"] == b["unit"]
