@@ -128,12 +128,14 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def host_cores():
-    """Cores this process may run on (its affinity mask), else the CPU count."""
+def host_cores(cap=32):
+    """Cores this process may run on (its affinity mask, else the CPU count),
+    at most `cap` (bounds the oracle runs' length on very wide hosts)."""
     try:
-        return max(1, len(os.sched_getaffinity(0)))
+        n = len(os.sched_getaffinity(0))
     except (AttributeError, OSError):
-        return os.cpu_count() or 1
+        n = os.cpu_count() or 1
+    return max(1, min(cap, n))
 
 
 def _oracle_chunk(args):
