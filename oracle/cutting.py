@@ -176,27 +176,40 @@ def fold(frag, dists):
 
     y = o | b << m with m marginal bits and b the quantum-output bits.
     """
-    m = len(frag.marg)
-    qi, qo = len(frag.qin), len(frag.qout)
-    role = {}
-    for j, (c, _) in enumerate(frag.qin):
-        role[c] = ("in", j)
-    for j, (c, _) in enumerate(frag.qout):
-        role[c] = ("out", j)
-    nslot = len(frag.slots)
-    T_ = np.zeros((1 << m, 4 ** nslot))
     dists = np.asarray(dists, np.float64)
+    return fold_columns(frag, range(4 ** len(frag.slots)), lambda v: dists[v])
+
+
+def pauli_digits(frag, P):
+    """Split a fragment Pauli index into (P_in per quantum input, P_out per
+    quantum output), both in cut order."""
+    pin = [0] * len(frag.qin)
+    pout = [0] * len(frag.qout)
+    role = {c: ("in", j) for j, (c, _) in enumerate(frag.qin)}
+    role.update({c: ("out", j) for j, (c, _) in enumerate(frag.qout)})
+    for j, c in enumerate(frag.slots):
+        pj = (P >> (2 * j)) & 3
+        kind, idx = role[c]
+        if kind == "in":
+            pin[idx] = pj
+        else:
+            pout[idx] = pj
+    return pin, pout
+
+
+def fold_columns(frag, Ps, dist_of):
+    """Columns T_f[:, P] for the Pauli indices ``Ps`` (in that order), each by
+    the definition above: the variants measured in basis beta(P_out),
+    weighted by prod mu(P_in, s) and, per outcome b of the quantum outputs,
+    prod lambda(P_out, b).  ``dist_of(v)`` returns variant v's distribution;
+    only the variants a column needs are asked for."""
+    m = len(frag.marg)
+    qo = len(frag.qout)
+    Ps = list(Ps)
+    T_ = np.zeros((1 << m, len(Ps)))
     o_idx = np.arange(1 << m)
-    for P in range(4 ** nslot):
-        pin = [0] * qi
-        pout = [0] * qo
-        for j, c in enumerate(frag.slots):
-            pj = (P >> (2 * j)) & 3
-            kind, idx = role[c]
-            if kind == "in":
-                pin[idx] = pj
-            else:
-                pout[idx] = pj
+    for col, P in enumerate(Ps):
+        pin, pout = pauli_digits(frag, P)
         beta = [BETA[p] for p in pout]
         acc = np.zeros(1 << m)
         for v in range(frag.n_variants):
@@ -208,13 +221,14 @@ def fold(frag, dists):
                 coef *= MU[pi_, si]
             if coef == 0.0:
                 continue
+            dv = dist_of(v)
             for b in range(1 << qo):
                 lam = 1.0
                 for j, pj in enumerate(pout):
                     if pj != 0 and (b >> j) & 1:
                         lam = -lam
-                acc += coef * lam * dists[v][o_idx | (b << m)]
-        T_[:, P] = acc
+                acc += coef * lam * dv[o_idx | (b << m)]
+        T_[:, col] = acc
     return T_
 
 
