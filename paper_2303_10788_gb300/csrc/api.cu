@@ -800,11 +800,20 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
           const int target = 2 * std::max(c->sm_count, 148);
           const long long max_splits = std::max(1ll, d.K / 32);
           d.splits = (int)std::max(1ll, std::min(max_splits, (target + base - 1) / base));
+          // a wide hub operand with few leaf outputs streams through the
+          // CUDA-core GEMM (4 hub outputs x N per thread, two CTAs per SM)
+          d.stream = (d.N <= 16 && d.M >= 128 && d.M % 4 == 0 && d.K >= 1024 && d.hub_T_off % 4 == 0) ? 1 : 0;
+          if (d.stream) {
+            d.sthreads = std::min(256, d.M / 4);
+            d.smblocks = (d.M / 4 + d.sthreads - 1) / d.sthreads;
+            const long long max_ss = std::max(1ll, d.K / 64);
+            d.ssplits = (int)std::max(1ll, std::min(max_ss, (long long)(target + d.smblocks - 1) / d.smblocks));
+          }
           plan->chain = 1;
           d.r_off = plan->r_total;
           plan->r_total += d.K * d.N;
-          d.part_off = plan->part_total;
-          plan->part_total += (long long)d.splits * d.M * d.N;
+          d.part_off = (plan->part_total + 3) & ~3ll;      // float4 stores of the streaming GEMM
+          plan->part_total = d.part_off + (long long)std::max(d.splits, d.stream ? d.ssplits : 0) * d.M * d.N;
           d.blk_off = plan->gemm_blocks;
           plan->gemm_blocks += base * d.splits;
           plan->max_tile_smem = std::max(plan->max_tile_smem, 16 * (d.TM + d.TN) * 4);
@@ -821,6 +830,7 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
     }
 
     // the scratch holds every problem's R operand first, then the split-K partials
+    plan->r_total = (plan->r_total + 3) & ~3ll;
     for (auto& d : plan->pdev) d.part_off += plan->r_total;
     std::vector<CliffordOp> prep(4), basis(3);
     std::vector<float> prepm(32), basism(24);
@@ -1255,7 +1265,7 @@ int ccs_recombine(ccs_ctx c, ccs_plan p, ccs_res r, const ccs_recomb_opts* opts,
     RecombSizes rz{p->r_total, p->part_total, p->gemm_blocks, p->n_marg, p->n_zexp,
                    p->d_direct_items, (int)p->direct_items.size(), (int)p->direct_stage_floats, p->chain,
                    p->d_r_prefix, p->d_blk_prefix, p->d_out_prefix, p->d_z_prefix, p->max_tile_smem,
-                   tc ? p->pdev.data() : nullptr, (int)p->pdev.size(), r->rt_scratch};
+                   p->pdev.data(), (int)p->pdev.size(), r->rt_scratch, tc ? 1 : 0};
     cudaError_t e;
     if (opts && opts->use_graph && !c->profiling) {
       const int key = prec * 2 + (tc ? 1 : 0);
@@ -1519,6 +1529,9 @@ namespace {
 constexpr long long kNoAllocScratchFloats = 2ll << 20;   // 8 MiB of float
 static __device__ __align__(256) float g_noalloc_scratch[kNoAllocScratchFloats];
 constexpr int kMaxDevices = 64;
+// device address of the array per device, looked up under the lock on the
+// first call that needs it (a later cudaDeviceReset invalidates it)
+std::mutex g_noalloc_mu;
 float* g_noalloc_addr[kMaxDevices] = {};
 }  // namespace
 
@@ -1539,17 +1552,22 @@ extern "C" int ccs_recombine_noalloc(ccs_ctx c, ccs_plan p, ccs_res r, int preci
     if (c->device < 0 || c->device >= kMaxDevices) return fail(c, CCS_ERR_UNSUPPORTED, "device index too large");
     cudaError_t e = cudaSetDevice(c->device);
     if (e != cudaSuccess) return cuda_fail(c, e, "set device");
-    if (!g_noalloc_addr[c->device]) {   // first call on this device: resolve the array's address
-      float* ptr = nullptr;
-      e = cudaGetSymbolAddress((void**)&ptr, g_noalloc_scratch);
-      if (e != cudaSuccess) return cuda_fail(c, e, "cudaGetSymbolAddress of the fixed scratch");
-      g_noalloc_addr[c->device] = ptr;
+    float* scratch = nullptr;
+    {
+      std::lock_guard<std::mutex> lock(g_noalloc_mu);
+      if (!g_noalloc_addr[c->device]) {   // first call on this device: resolve the array's address
+        float* ptr = nullptr;
+        e = cudaGetSymbolAddress((void**)&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaGetSymbolAddress of the fixed scratch");
+        g_noalloc_addr[c->device] = ptr;
+      }
+      scratch = g_noalloc_addr[c->device];
     }
     RecombSizes rz{p->r_total, p->part_total, p->gemm_blocks, p->n_marg, p->n_zexp,
                    p->d_direct_items, (int)p->direct_items.size(), (int)p->direct_stage_floats, p->chain,
                    p->d_r_prefix, p->d_blk_prefix, p->d_out_prefix, p->d_z_prefix, p->max_tile_smem,
-                   nullptr, 0, nullptr};
-    e = launch_recombine(p->dp, r->dr, precision, rz, g_noalloc_addr[c->device], marginal_out, zexp_out, c->stream);
+                   p->pdev.data(), (int)p->pdev.size(), nullptr, 0};
+    e = launch_recombine(p->dp, r->dr, precision, rz, scratch, marginal_out, zexp_out, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "recombine kernel");
     return CCS_OK;
   });

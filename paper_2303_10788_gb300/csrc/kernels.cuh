@@ -61,6 +61,9 @@ struct ProblemDev {
   int tc;                  // 1: eligible for the tensor-core GEMM in BF16 mode
   int direct;              // 1: contracted leaf by leaf in shared memory, TM hub outputs per CTA
   int direct_staged;       // 1: the slice's hub operand (K x TM) is staged first; 0: the first leaf streams it
+  // streaming CUDA-core GEMM of a wide hub (FP32, or BF16 off the tensor cores):
+  // sthreads threads x 4 hub outputs per CTA, smblocks CTAs across M, ssplits across K
+  int stream, sthreads, smblocks, ssplits;
 };
 
 // Device views of a plan + result.
@@ -202,10 +205,10 @@ struct RecombSizes {
   const long long* out_prefix;   // per problem, M*N outputs
   const long long* z_prefix;     // per problem, Z-strings
   int max_tile_smem;             // bytes of dynamic shared memory per GEMM block
-  // tensor-core path (BF16 only; null host list disables it)
-  const ProblemDev* host_problems;
+  const ProblemDev* host_problems;   // host copy of the problems (per-problem GEMM launches)
   int n_problems;
-  uint16_t* rt_scratch;          // bf16 R'^T of eligible problems
+  uint16_t* rt_scratch;          // bf16 R'^T of problems eligible for the tensor-core GEMM
+  int tensor_cores;              // 1: BF16 contractions of eligible problems on tcgen05
 };
 cudaError_t launch_recombine(const DevPlan& p, const DevRes& r, int precision, const RecombSizes& z,
                              float* scratch, double* marg_out, double* zexp_out, cudaStream_t s);

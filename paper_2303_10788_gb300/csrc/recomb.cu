@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(256) gemm_splitk_kernel(DevPlan P, DevRes R, i
   for (long long b = blockIdx.x; b < total_blocks; b += gridDim.x) {
     const int pi = find_seg(blk_prefix, np, b);
     const ProblemDev& Pb = P.problems[pi];
-    if (skip_tc && Pb.tc) continue;          // done by the tensor-core GEMM
+    if ((skip_tc && Pb.tc) || Pb.stream) continue;   // done by the tensor-core or the streaming GEMM
     const FragDev& Hb = P.frags[Pb.frag0 + Pb.hub];
     long long loc = b - blk_prefix[pi];
     const int nt = (int)(loc % Pb.ntiles); loc /= Pb.ntiles;
@@ -334,6 +334,106 @@ __global__ void __launch_bounds__(256) gemm_splitk_kernel(DevPlan P, DevRes R, i
   }
 }
 
+// Streaming CUDA-core GEMM of a wide hub operand: the partial
+//   C[m][n] = sum_{k in one K range} Q^T[k][m] R[k][n]
+// of one split.  Thread t of CTA (mb, split) owns the hub outputs
+// m = 4 (mb blockDim + t) .. +3 and every column n: one 16-byte streaming
+// load of Q^T per row (a CTA reads blockDim x 16 contiguous bytes of each
+// row, each byte once), the R rows of the range staged in shared memory and
+// read as broadcasts, eight rows of loads in flight.  FP32 FMA per split;
+// the splits are summed in FP64 by reduce_scatter_kernel.  BF16 mode rounds
+// the hub values to bf16 (R is rounded when it is built).
+constexpr int kStreamChunk = 256;   // R rows staged per pass
+
+template <int NN>
+__device__ __forceinline__ void stream_fma(float (&acc)[4][NN], float4 a, const float* rrow, int bf16) {
+  if (bf16) { a.x = to_bf16f(a.x); a.y = to_bf16f(a.y); a.z = to_bf16f(a.z); a.w = to_bf16f(a.w); }
+  float rv[NN];
+  if constexpr (NN >= 4) {
+#pragma unroll
+    for (int j = 0; j < NN; j += 4) {
+      const float4 r4 = *reinterpret_cast<const float4*>(rrow + j);
+      rv[j] = r4.x; rv[j + 1] = r4.y; rv[j + 2] = r4.z; rv[j + 3] = r4.w;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < NN; ++j) rv[j] = rrow[j];
+  }
+#pragma unroll
+  for (int j = 0; j < NN; ++j) {
+    acc[0][j] = fmaf(a.x, rv[j], acc[0][j]);
+    acc[1][j] = fmaf(a.y, rv[j], acc[1][j]);
+    acc[2][j] = fmaf(a.z, rv[j], acc[2][j]);
+    acc[3][j] = fmaf(a.w, rv[j], acc[3][j]);
+  }
+}
+
+template <int NN>
+__global__ void __launch_bounds__(256, 2) gemm_stream_kernel(const float* __restrict__ At, const float* __restrict__ Rm,
+                                                             int M, long long K, long long kchunk, int mblocks,
+                                                             float* __restrict__ part, int bf16) {
+  __shared__ __align__(16) float Rs[kStreamChunk * NN];
+  const int mb = blockIdx.x % mblocks, split = blockIdx.x / mblocks;
+  const long long k0 = (long long)split * kchunk, k1 = min(K, k0 + kchunk);
+  const int m = 4 * (mb * (int)blockDim.x + (int)threadIdx.x);
+  const bool act = m < M;
+  float acc[4][NN];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < NN; ++j) acc[i][j] = 0.f;
+  for (long long kc = k0; kc < k1; kc += kStreamChunk) {
+    const int rows = (int)min((long long)kStreamChunk, k1 - kc);
+    __syncthreads();                       // the previous chunk's rows are consumed
+    for (int i = threadIdx.x; i < rows * NN; i += blockDim.x) Rs[i] = Rm[kc * NN + i];
+    __syncthreads();
+    if (!act) continue;
+    const float* ap = At + kc * M + m;
+    int r = 0;
+    for (; r + 8 <= rows; r += 8) {
+      float4 a[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) a[u] = __ldcs(reinterpret_cast<const float4*>(ap + (long long)(r + u) * M));
+#pragma unroll
+      for (int u = 0; u < 8; ++u) stream_fma<NN>(acc, a[u], Rs + (r + u) * NN, bf16);
+    }
+    for (; r < rows; ++r)
+      stream_fma<NN>(acc, __ldcs(reinterpret_cast<const float4*>(ap + (long long)r * M)), Rs + r * NN, bf16);
+  }
+  if (!act) return;
+  float* dst = part + ((long long)split * M + m) * NN;    // 4 x NN contiguous floats
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < NN; ++j) dst[i * NN + j] = acc[i][j];
+}
+
+template <int NN>
+static cudaError_t launch_stream_nn(const float* At, const float* Rm, const ProblemDev& Pb, float* part, int bf16,
+                                    cudaStream_t s) {
+  long long kchunk = (Pb.K + Pb.ssplits - 1) / Pb.ssplits;
+  kchunk = (kchunk + 7) & ~7ll;
+  const long long splits = (Pb.K + kchunk - 1) / kchunk;    // every split but the last is full
+  gemm_stream_kernel<NN><<<(unsigned)(Pb.smblocks * splits), Pb.sthreads, 0, s>>>(At, Rm, Pb.M, Pb.K, kchunk,
+                                                                                  Pb.smblocks, part, bf16);
+  note_launch();
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_stream(const DevRes& r, const ProblemDev& Pb, float* scratch, int bf16, cudaStream_t s) {
+  const float* At = r.TQ + Pb.hub_T_off;
+  const float* Rm = scratch + Pb.r_off;
+  float* part = scratch + Pb.part_off;
+  switch (Pb.N) {
+    case 1: return launch_stream_nn<1>(At, Rm, Pb, part, bf16, s);
+    case 2: return launch_stream_nn<2>(At, Rm, Pb, part, bf16, s);
+    case 4: return launch_stream_nn<4>(At, Rm, Pb, part, bf16, s);
+    case 8: return launch_stream_nn<8>(At, Rm, Pb, part, bf16, s);
+    case 16: return launch_stream_nn<16>(At, Rm, Pb, part, bf16, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 // BF16 K-major copy of a hub operand for the tensor-core GEMM:
 // Qh[o][D] = bf16(Q^T[D][o]), through 64 x 64 shared-memory tiles: each
 // warp reads 256 contiguous bytes of a Q^T row (o fastest) and writes 128
@@ -370,7 +470,7 @@ __global__ void __launch_bounds__(256) hub_bf16_kernel(const float* __restrict__
 }
 
 __global__ void reduce_scatter_kernel(DevPlan P, const long long* prefix, int np, long long total,
-                                      const float* scratch, double* marg_out) {
+                                      const float* scratch, double* marg_out, int use_tc) {
   for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
        g += (long long)gridDim.x * blockDim.x) {
     const int pi = find_seg(prefix, np, g);
@@ -378,8 +478,9 @@ __global__ void reduce_scatter_kernel(DevPlan P, const long long* prefix, int np
     if (Pb.direct) continue;                  // written by the leaf-by-leaf contraction
     const long long loc = g - prefix[pi];
     const long long m = loc / Pb.N, n = loc - m * Pb.N;
+    const int splits = (Pb.stream && !(use_tc && Pb.tc)) ? Pb.ssplits : Pb.splits;
     double acc = 0.0;
-    for (int s = 0; s < Pb.splits; ++s) acc += (double)scratch[Pb.part_off + ((long long)s * Pb.M + m) * Pb.N + n];
+    for (int s = 0; s < splits; ++s) acc += (double)scratch[Pb.part_off + ((long long)s * Pb.M + m) * Pb.N + n];
     long long o = 0;
     const FragDev& Hb = P.frags[Pb.frag0 + Pb.hub];
     for (int j = 0; j < Hb.m; ++j) o |= ((m >> j) & 1) << Hb.marg_pos[j];
@@ -679,7 +780,7 @@ cudaError_t launch_recombine(const DevPlan& p, const DevRes& r, int precision, c
   };
   cudaError_t err = cudaSuccess;
   if (z.out_total > 0 && z.chain) {
-    const bool use_tc = precision == CCS_BF16 && z.host_problems && z.rt_scratch && r.TQh;
+    const bool use_tc = precision == CCS_BF16 && z.tensor_cores && z.rt_scratch && r.TQh;
     if (z.r_total > 0) {
       build_r_kernel<<<grid(z.r_total, 256), 256, 0, s>>>(p, r, precision, z.r_prefix, p.n_problems, z.r_total,
                                                           scratch, use_tc ? z.rt_scratch : nullptr); note_launch();
@@ -694,6 +795,11 @@ cudaError_t launch_recombine(const DevPlan& p, const DevRes& r, int precision, c
                            z.max_tile_smem, s>>>(p, r, precision, z.blk_prefix, p.n_problems, z.gemm_blocks, scratch,
                                                  use_tc ? 1 : 0); note_launch();
       if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    }
+    for (int i = 0; i < z.n_problems; ++i) {     // wide hubs off the tensor cores: streaming GEMM
+      const ProblemDev& Pb = z.host_problems[i];
+      if (!Pb.stream || Pb.direct || (use_tc && Pb.tc)) continue;
+      if ((err = launch_stream(r, Pb, scratch, precision == CCS_BF16 ? 1 : 0, s)) != cudaSuccess) return err;
     }
     if (use_tc) {
       for (int i = 0; i < z.n_problems; ++i) {
@@ -712,7 +818,7 @@ cudaError_t launch_recombine(const DevPlan& p, const DevRes& r, int precision, c
     }
     {
       reduce_scatter_kernel<<<grid(z.out_total, 256), 256, 0, s>>>(p, z.out_prefix, p.n_problems, z.out_total,
-                                                                  scratch, marg_out); note_launch();
+                                                                  scratch, marg_out, use_tc ? 1 : 0); note_launch();
       if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
   }
