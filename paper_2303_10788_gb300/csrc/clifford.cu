@@ -1147,9 +1147,10 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
       k0 += 0x9E3779B9u;
       k1 += 0xBB67AE85u;
     }
-    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
-    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    // each 32 x 32 -> 64-bit product is one wide multiply (high and low words)
+    const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
+    const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
+    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k1, (uint32_t)p0);
   }
   return c;
 }
@@ -1168,13 +1169,20 @@ __device__ __forceinline__ void for_shots(uint32_t t0, uint32_t t1, uint4 ctr, u
     ctr.x = g;
     const uint4 o = philox4x32_10(ctr, k0, k1);
     const uint32_t w4[4] = {o.x, o.y, o.z, o.w};
+    if ((unsigned long long)(4 * S) * (g + 1) <= t1) {    // every shot of the call is in range
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
+      for (int j = 0; j < 4; ++j)
 #pragma unroll
-      for (int h = 0; h < S; ++h) {
-        const uint32_t t = (4 * g + j) * S + h;
-        if (t < t1) fn((S == 1 ? w4[j] : w4[j] >> (h * WB)) & cmask);
-      }
+        for (int h = 0; h < S; ++h) fn((S == 1 ? w4[j] : w4[j] >> (h * WB)) & cmask);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int h = 0; h < S; ++h) {
+          const uint32_t t = (4 * g + j) * S + h;
+          if (t < t1) fn((S == 1 ? w4[j] : w4[j] >> (h * WB)) & cmask);
+        }
+    }
   }
 }
 
@@ -1474,21 +1482,91 @@ __global__ void __launch_bounds__(512) sample_hub_kernel(DevPlan P, DevRes R, Ev
   }
 }
 
-// --- the hub sampler with byte counters (two CTAs per SM) -----------------
+// Readout of a byte-counter histogram into the variant's operand rows,
+// specialised on ZM, the quantum outputs measured in the Z basis.  Row cz
+// of the variant needs S(o, cz) = sum_b (-1)^(b . smask_cz) count(o, b) with
+// smask_cz = the X/Y-basis outputs (whose outcome always flips the sign)
+// plus the Z outputs selected by cz.  So the bins are first summed over the
+// X/Y bits with their fixed signs (F over the Z bits), then a Walsh-Hadamard
+// transform over the Z bits gives every row at once: 16 - 2^nz + nz 2^nz
+// adds instead of a full 16-point transform.  Four outputs o..o+3 share a
+// counter word; each half is processed as two 16-bit lanes of one 32-bit
+// integer (signed lane sums stay below 2^15 in magnitude, so plain integer
+// adds keep the lanes separable).  Returns the thread's sum of all counter
+// bytes read (the caller compares the block's total with the shots: a byte
+// that wrapped makes it smaller).
+__host__ __device__ constexpr int popc4(int x) { return (x & 1) + ((x >> 1) & 1) + ((x >> 2) & 1) + ((x >> 3) & 1); }
+__host__ __device__ constexpr int pext4(int b, int zm) {
+  int r = 0, k = 0;
+  for (int j = 0; j < 4; ++j)
+    if ((zm >> j) & 1) r |= ((b >> j) & 1) << k++;
+  return r;
+}
+
+template <int ZM>
+__device__ __forceinline__ unsigned hub8_readout(const uint32_t* __restrict__ h32, int m, int M, int nb,
+                                                 const int* s_czD, float* __restrict__ QT, float inv) {
+  constexpr int NR = 1 << popc4(ZM);
+  unsigned tot = 0;
+  for (int q = threadIdx.x; q < (M >> 2); q += blockDim.x) {
+    const int o = 4 * q;
+    uint32_t w[16];
+#pragma unroll
+    for (int b = 0; b < 16; ++b) w[b] = b < nb ? h32[((uint32_t)o | ((uint32_t)b << m)) >> 2] : 0u;
+#pragma unroll
+    for (int b = 0; b < 16; ++b) tot = __dp4a(w[b], 0x01010101u, tot);
+    float out[NR][4];
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      int F[NR];
+#pragma unroll
+      for (int i = 0; i < NR; ++i) F[i] = 0;
+#pragma unroll
+      for (int b = 0; b < 16; ++b) {     // outputs o + 2 half, o + 2 half + 1 as 16-bit lanes
+        const int x = (int)__byte_perm(w[b], 0u, half ? 0x4342 : 0x4140);
+        if (popc4(b & ~ZM & 15) & 1) F[pext4(b, ZM)] -= x;
+        else F[pext4(b, ZM)] += x;
+      }
+#pragma unroll
+      for (int h = 1; h < NR; h <<= 1)
+#pragma unroll
+        for (int i = 0; i < NR; ++i)
+          if (!(i & h)) {
+            const int a = F[i], c = F[i | h];
+            F[i] = a + c;
+            F[i | h] = a - c;
+          }
+#pragma unroll
+      for (int i = 0; i < NR; ++i) {
+        const int lo = (int)(short)(F[i] & 0xffff), hi = (F[i] - lo) >> 16;
+        out[i][2 * half] = (float)lo * inv;
+        out[i][2 * half + 1] = (float)hi * inv;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < NR; ++i)
+      *reinterpret_cast<float4*>(QT + (long long)s_czD[i] * M + o) = make_float4(out[i][0], out[i][1], out[i][2], out[i][3]);
+  }
+  return tot;
+}
+
+// --- the hub sampler with byte counters (three CTAs per SM) ---------------
 // Same result as sample_hub_kernel, for hubs with |A| <= 16, at least two
 // marginal bits and at most four quantum outputs, below 65536 shots.  The
-// histogram holds 8-bit counters (2^16 of them in 64 KB) so two CTAs fit on
-// an SM.  Counts stay exact: a variant whose expected count per outcome is
-// above 64 (shots > 64 * 2^rank), or whose counting overflowed a byte
-// (the atomic's old value tells), is counted again with 16-bit counters in
-// two passes, each over the outputs o of one half (top marginal bit).
+// histogram holds 8-bit counters (2^16 of them in 64 KB) so three CTAs fit
+// on an SM (a readout sum of 16 bytes stays below 2^15 whatever the shots).  Counts stay exact: a variant whose expected count per outcome
+// is above 64 (shots > 64 * 2^rank), or whose counting wrapped a byte (the
+// bytes then sum to less than the shots: a wrap loses 256 from the byte and
+// carries at most 1 into the next), is counted again with 16-bit counters
+// in two passes, each over the outputs o of one half (top marginal bit),
+// and its operand rows are rewritten.
 __global__ void __launch_bounds__(256) sample_hub8_kernel(DevPlan P, DevRes R, EvalParams E, const int2* items,
                                                           int keep_counts, int hist_words) {
   extern __shared__ __align__(16) uint32_t h32[];
   __shared__ uint32_t tbl[3][256];
   __shared__ FragDev sF;
   __shared__ int s_czD[16], s_czS[16];
-  __shared__ int s_over;
+  __shared__ unsigned s_tot;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int2 it = items[blockIdx.x];
   {
@@ -1496,7 +1574,7 @@ __global__ void __launch_bounds__(256) sample_hub8_kernel(DevPlan P, DevRes R, E
     int* dst = reinterpret_cast<int*>(&sF);
     for (int i = tid; i < (int)(sizeof(FragDev) / 4); i += nt) dst[i] = src[i];
   }
-  if (tid == 0) s_over = 0;
+  if (tid == 0) s_tot = 0u;
   __syncthreads();
   const FragDev& F = sF;
   const int v = it.y, nA = F.nA, m = F.m, M = 1 << m, nb = 1 << F.qout;
@@ -1505,7 +1583,7 @@ __global__ void __launch_bounds__(256) sample_hub8_kernel(DevPlan P, DevRes R, E
   const uint32_t off = sp.off;
   build_tables(tbl, sp, rank);
   // the variant's operand columns: one D and sign mask per Z-basis choice
-  int nz = 0;
+  int nz = 0, zm = 0;
   {
     int beta[kMaxCuts], zpos[kMaxCuts], zout[kMaxCuts];
     int t = v;
@@ -1521,6 +1599,7 @@ __global__ void __launch_bounds__(256) sample_hub8_kernel(DevPlan P, DevRes R, E
       } else if (beta[idx] == 2) {
         zpos[nz] = j;
         zout[nz++] = idx;
+        zm |= 1 << idx;
       } else {
         Dbase |= (beta[idx] == 0 ? 1 : 2) << (2 * j);
         fixed_mask |= 1 << idx;
@@ -1552,30 +1631,28 @@ __global__ void __launch_bounds__(256) sample_hub8_kernel(DevPlan P, DevRes R, E
     by_rank(rank, [&](auto lk) {
       constexpr int L = decltype(lk)::value;
       for_shots<L>(0u, E.shots, ctr, E.seed_lo, E.seed_hi, cmask, [&](uint32_t c) {
-        const uint32_t y = space_point<L>(tbl, off, c), sh = (y & 3u) << 3;
-        const uint32_t old = atomicAdd(&h32[y >> 2], 1u << sh);
-        if (((old >> sh) & 0xffu) == 0xffu) s_over = 1;     // a byte wrapped: recount wider
+        const uint32_t y = space_point<L>(tbl, off, c);
+        atomicAdd(&h32[y >> 2], 1u << ((y & 3u) << 3));
       });
     });
     __syncthreads();
-    narrow = s_over == 0;
-    if (narrow) {
-      if (keep_counts)
-        for (uint32_t y = tid; y < (1u << nA); y += nt) gcount[y] = (h32[y >> 2] >> ((y & 3u) << 3)) & 0xffu;
-      for (int q = tid; q < (M >> 2); q += nt) {       // outputs o..o+3 share a counter word
-        const int o = 4 * q;
-        uint32_t w[16];
-#pragma unroll
-        for (int b = 0; b < 16; ++b) w[b] = b < nb ? h32[((uint32_t)o | ((uint32_t)b << m)) >> 2] : 0u;
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-          unsigned pk[16];    // outputs o + 2 half and o + 2 half + 1 as 16-bit lanes
-#pragma unroll
-          for (int b = 0; b < 16; ++b) pk[b] = __byte_perm(w[b], 0u, half ? 0x4342 : 0x4140);
-          hub_pair_out_packed(pk, s_czD, s_czS, nz, QT, M, o + 2 * half, inv);
-        }
-      }
+    if (keep_counts)
+      for (uint32_t y = tid; y < (1u << nA); y += nt) gcount[y] = (h32[y >> 2] >> ((y & 3u) << 3)) & 0xffu;
+    unsigned tot = 0;
+    switch (zm) {
+#define CCS_HUB8_CASE(z) \
+  case z: tot = hub8_readout<z>(h32, m, M, nb, s_czD, QT, inv); break;
+      CCS_HUB8_CASE(0) CCS_HUB8_CASE(1) CCS_HUB8_CASE(2) CCS_HUB8_CASE(3)
+      CCS_HUB8_CASE(4) CCS_HUB8_CASE(5) CCS_HUB8_CASE(6) CCS_HUB8_CASE(7)
+      CCS_HUB8_CASE(8) CCS_HUB8_CASE(9) CCS_HUB8_CASE(10) CCS_HUB8_CASE(11)
+      CCS_HUB8_CASE(12) CCS_HUB8_CASE(13) CCS_HUB8_CASE(14) CCS_HUB8_CASE(15)
+#undef CCS_HUB8_CASE
+      default: break;
     }
+    tot = __reduce_add_sync(0xffffffffu, tot);
+    if ((tid & 31) == 0) atomicAdd(&s_tot, tot);
+    __syncthreads();
+    narrow = s_tot == E.shots;      // no byte wrapped
   }
   if (!narrow) {   // 16-bit counters, outputs of one half (top marginal bit) per pass
     const int mh = m - 1, Mh = M >> 1;

@@ -1,7 +1,11 @@
 """ccs_recombine_noalloc: recombination for callers that cannot allocate device
 memory when they need the result (its scratch is a fixed array inside the
 library).  Checked through the C ABI against ccs_recombine on two calls in a
-row, and for its size limit.  Collected last on purpose."""
+row, in FP32 and BF16, on plans that contract leaf by leaf (no scratch) and
+on a plan whose contraction runs through the fixed scratch (the leaves'
+Kronecker operand and the split-K partials); a large plan, then a small one,
+then the large one again; and for its size limit.  Collected last on
+purpose."""
 import numpy as np
 import pytest
 
@@ -18,20 +22,52 @@ def ctx():
     return ccs.ccs_create(0)
 
 
-@pytest.mark.parametrize("make", [config1, config2])
-def test_noalloc_matches_recombine_twice(ctx, make):
-    import torch
-    w = make()
+def scratch_star():
+    """A 24-qubit star with four 2-wire leaves (8 cuts, 4^8 cut terms) and a
+    7-bit hub marginal: its contraction is a GEMM over the cut index whose
+    Kronecker operand (4^8 x 16 floats) and partials fit the fixed scratch."""
+    regs = [Region([q], q + 1, 2, 6, [q, q + 1], 1) for q in (0, 6, 12, 18)]
+    c, cuts = brickwork_star(24, 9, regs, seed=5)
+    marg = [0, 6, 12, 18, 3, 4, 9, 10, 15, 16, 21]
+    return Workload("scratch_star", c, cuts, marg, [[3, 9], [0, 4, 21]], 1024, 5)
+
+
+def _evaluated(ctx, w):
     plan = ccs.ccs_build_fragments(ctx, [w])
     res = ccs.ccs_eval_variants(ctx, plan, mode=ccs.CCS_SAMPLED, shots=w.shots, seed_lo=3, seed_hi=4)
-    ref_m, ref_z = ccs.ccs_recombine(ctx, plan, res)
+    return plan, res
+
+
+def _noalloc_twice(ctx, plan, res, w, precision):
+    import torch
+    ref_m, ref_z = ccs.ccs_recombine(ctx, plan, res, precision=precision, tensor_cores=False)
     for _ in range(2):
         m = torch.full((1 << len(w.marginal),), -1.0, dtype=torch.float64, device="cuda")
-        z = torch.full((len(w.zstrings),), -7.0, dtype=torch.float64, device="cuda")
-        ccs.ccs_recombine_noalloc(ctx, plan, res, m, z)
+        z = torch.full((max(1, len(w.zstrings)),), -7.0, dtype=torch.float64, device="cuda")
+        ccs.ccs_recombine_noalloc(ctx, plan, res, m, z, precision=precision)
         torch.cuda.synchronize()
         assert np.abs(m.cpu().numpy() - ref_m).max() < TOL
-        assert np.abs(z.cpu().numpy() - ref_z).max() < TOL
+        if len(w.zstrings):
+            assert np.abs(z.cpu().numpy()[:len(w.zstrings)] - ref_z).max() < TOL
+
+
+@pytest.mark.parametrize("precision", [ccs.CCS_FP32, ccs.CCS_BF16])
+@pytest.mark.parametrize("make", [config1, config2])
+def test_noalloc_matches_recombine_twice(ctx, make, precision):
+    w = make()
+    plan, res = _evaluated(ctx, w)
+    _noalloc_twice(ctx, plan, res, w, precision)
+
+
+@pytest.mark.parametrize("precision", [ccs.CCS_FP32, ccs.CCS_BF16])
+def test_noalloc_through_its_scratch_large_small_large(ctx, precision):
+    w_big, w_small = scratch_star(), config1()
+    nf, nc = ccs.ccs_plan_counts(ctx, ccs.ccs_build_fragments(ctx, [w_big]), 0)
+    assert nc == 8
+    big, small = _evaluated(ctx, w_big), _evaluated(ctx, w_small)
+    _noalloc_twice(ctx, *big, w_big, precision)
+    _noalloc_twice(ctx, *small, w_small, precision)
+    _noalloc_twice(ctx, *big, w_big, precision)
 
 
 def test_noalloc_rejects_plans_beyond_its_scratch(ctx):
