@@ -1,27 +1,45 @@
 #!/usr/bin/env python
-"""Benchmark of the Clifford circuit-cutting hot path on one GB300.
+"""Benchmark of the Clifford circuit-cutting hot path on GB300s.
 
-Workload (default): 100 qubits, depth-20 random Clifford brickwork, 10 T gates
-in two non-Clifford regions of 9 wires, 4 wire cuts -> 3 fragments (86-wire
-Clifford body with 144 variants, two 9-wire statevector fragments with 12),
-10^4 Philox shots per Clifford variant, 12-qubit marginal + 64 Z-strings.
-One step = one pass of the whole path: tableau evolution, outcome spaces,
-sampling, statevectors, fold, recombination.
+Workload (default, the largest single-GPU configuration): 500 qubits, depth-30
+random Clifford brickwork, 16 T gates in four 2-wire non-Clifford regions, 8
+wire cuts -> a 500-wire Clifford body (1000 x 1001-bit tableau, 20736
+variants) and four statevector leaves; 2^14 Philox shots per Clifford
+variant; 16-qubit marginal from the contraction over the 4^8 cut terms.
+One step = one pass of the whole path: body evolution, outcome spaces,
+sampling folded into the contraction operand, statevectors, fold,
+contraction.
 
 value   Clifford variant-shots/s, plan resident on the device, one CUDA-graph
-        replay + device-side recombination per step, L2 flushed between steps.
+        replay of the evaluation + one of the recombination per step, L2
+        flushed between steps (outside the step events); the FP32
+        contraction (the precision gated at 1e-5 against the FP64 oracle).
 e2e     the same metric through the public C ABI from host buffers: plan build
         (host compile + upload), evaluation, recombination into host memory.
+plain   the plain GPU form in the same run: per-variant simulation of every
+        variant's whole circuit, stream launches, FP32, no tuning.
+bf16    the same steps with the contraction in BF16 on the tensor cores.
+stitched
+        the same circuits in the Clifford-specific stitching mode (exact: no
+        shots, each hub operand row in closed form, vanishing rows skipped).
+
+With --gpus N (torchrun, or N spawned ranks when started plainly) every rank
+runs its own batch of the workload (other Philox seeds; other circuits for
+many-circuit workloads): independent problems, no data-path collective,
+weak scaling; the step time is the max over ranks.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
 import tempfile
+import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -30,6 +48,7 @@ sys.path.insert(0, ROOT)
 METRIC = "Clifford variant-shots/s and circuits/s end-to-end; % of HBM/tensor roofline"
 UNIT = "variant-shots/s"
 SEED = (0x9E3779B9, 0x7F4A7C15)
+N_SM = 152
 
 
 def peaks():
@@ -39,8 +58,8 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def workloads_for(name):
-    """The batch of circuits one step processes."""
+def workloads_for(name, rank=0):
+    """The batch of circuits one step of one rank processes."""
     import workloads as W
     if name == "config1":
         return [W.config1()]
@@ -49,15 +68,16 @@ def workloads_for(name):
     if name == "config3":
         return [W.config3()]
     if name == "config4":
-        return W.config4(256)
+        return W.config4(256, seed_offset=rank)
     # the paper's own benchmark shapes (Sec. VI-B, 5000 shots per sampled
     # distribution as in Sec. VI-A); cut sets are searched by the library
     if name == "hwea300":
-        return [W.hwea(300, rounds=5, n_t=1, n_z=8, shots=5000)]
+        return [W.hwea(300, rounds=5, n_t=1, n_z=8, shots=5000, seed=W.SEED_BASE + 6 + 1000 * rank)]
     if name == "hwea300x64":
-        return [W.hwea(300, rounds=5, n_t=1, n_z=8, shots=5000, seed=W.SEED_BASE + 600 + i) for i in range(64)]
+        return [W.hwea(300, rounds=5, n_t=1, n_z=8, shots=5000, seed=W.SEED_BASE + 600 + i + 1000 * rank)
+                for i in range(64)]
     if name == "skqaoa26":
-        return [W.sk_qaoa(26, rounds=1, n_t=1, n_z=8, shots=5000)]
+        return [W.sk_qaoa(26, rounds=1, n_t=1, n_z=8, shots=5000, seed=W.SEED_BASE + 7 + 1000 * rank)]
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -86,10 +106,58 @@ def describe(ws):
             f"variant, {len(w.marginal)}-qubit marginal each, one plan and one launch sequence per step")
 
 
+# --- clocks during the timed region ------------------------------------------
+
 class Clocks:
-    """nvidia-smi sampling during the timed region."""
+    """SM clock and throttle reasons sampled during the timed region: NVML
+    (read-only queries, every 2 ms on a thread) when the driver's library
+    loads, else nvidia-smi."""
+
+    _BITS = {"hw_slowdown": 0x8, "hw_thermal_slowdown": 0x40, "sw_thermal_slowdown": 0x20, "sw_power_cap": 0x4}
 
     def __init__(self, index):
+        self.sm, self.mx, self.reasons, self.p = [], 0.0, set(), None
+        self.stop_ev = threading.Event()
+        self.nv = self._nvml(index)
+        if self.nv is not None:
+            self.t = threading.Thread(target=self._poll, daemon=True)
+            self.t.start()
+        else:
+            self._smi(index)
+
+    def _nvml(self, index):
+        import ctypes as C
+        try:
+            nv = C.CDLL("libnvidia-ml.so.1")
+            if nv.nvmlInit_v2() != 0:
+                return None
+            h = C.c_void_p()
+            if nv.nvmlDeviceGetHandleByIndex_v2(C.c_uint(index), C.byref(h)) != 0:
+                return None
+            mx = C.c_uint()
+            if nv.nvmlDeviceGetMaxClockInfo(h, 1, C.byref(mx)) == 0:       # NVML_CLOCK_SM
+                self.mx = float(mx.value)
+            self.h = h
+            self.reason_fn = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                getattr(nv, "nvmlDeviceGetCurrentClocksThrottleReasons")
+            return nv
+        except Exception:
+            return None
+
+    def _poll(self):
+        import ctypes as C
+        mhz, rs = C.c_uint(), C.c_ulonglong()
+        while True:
+            if self.nv.nvmlDeviceGetClockInfo(self.h, 1, C.byref(mhz)) == 0:
+                self.sm.append(float(mhz.value))
+            if self.reason_fn(self.h, C.byref(rs)) == 0:
+                for n, b in self._BITS.items():
+                    if rs.value & b:
+                        self.reasons.add(n)
+            if self.stop_ev.wait(0.002):
+                return
+
+    def _smi(self, index):
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -102,31 +170,38 @@ class Clocks:
             self.p = None
 
     def stop(self):
-        if self.p is None:
-            return None
-        self.p.terminate()
-        try:
-            self.p.wait(5)
-        except Exception:
-            self.p.kill()
-        self.f.flush()
-        rows = [l.split(",") for l in open(self.f.name).read().splitlines() if l.strip()]
-        os.unlink(self.f.name)
-        sm, mx, reasons = [], 0.0, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in rows:
+        if self.nv is not None:
+            self.stop_ev.set()
+            self.t.join(2)
+            src = "nvml"
+        elif self.p is not None:
+            self.p.terminate()
             try:
-                sm.append(float(r[1])); mx = max(mx, float(r[2]))
-                for n, v in zip(names, r[5:9]):
-                    if v.strip() == "Active":
-                        reasons.add(n)
+                self.p.wait(5)
             except Exception:
-                pass
-        if not sm:
+                self.p.kill()
+            self.f.flush()
+            names = list(self._BITS)
+            for l in open(self.f.name).read().splitlines():
+                r = l.split(",")
+                try:
+                    self.sm.append(float(r[1])); self.mx = max(self.mx, float(r[2]))
+                    for n, v in zip(names, r[5:9]):
+                        if v.strip() == "Active":
+                            self.reasons.add(n)
+                except Exception:
+                    pass
+            os.unlink(self.f.name)
+            src = "nvidia-smi"
+        else:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        if not self.sm:
+            return None
+        return {"sm_mhz": statistics.median(self.sm), "sm_max_mhz": self.mx, "reasons": sorted(self.reasons),
+                "samples": len(self.sm), "source": src}
 
+
+# --- the CPU oracle ------------------------------------------------------------
 
 def host_cores(cap=32):
     """Cores this process may run on (its affinity mask, else the CPU count),
@@ -196,7 +271,8 @@ def oracle_baseline(ws, budget_s=20.0, threaded=True, threaded_budget_s=10.0):
             vs.append(v)
         out = {"value": len(vs) * w.shots / t_tot, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{len(vs)} body variants x {w.shots} shots of the first circuit ({t_tot:.1f} s "
-                         f"single-threaded; a whole circuit has {ncl} Clifford variants)"}
+                         f"single-threaded; a whole circuit has {ncl} Clifford variants; Clifford body "
+                         f"variants only: no statevector variants, fold or recombination)"}
         per_variant = t_tot / len(vs)
     if threaded and frags[body].clifford:
         try:
@@ -209,7 +285,8 @@ def oracle_baseline(ws, budget_s=20.0, threaded=True, threaded_budget_s=10.0):
 def run_reference(args, rank, world):
     """Reference arm: the CPU oracle, timed on all host cores (rank 0 only):
     one spawned process per core, each evaluating its own sample of body
-    variants every step; one process in this one when no pool can start."""
+    variants every step (sized so a step takes a few seconds); one process
+    in this one when no pool can start."""
     if rank != 0:
         return
     import multiprocessing as mp
@@ -220,7 +297,11 @@ def run_reference(args, rank, world):
     frags, _ = fragment_circuit(w.circuit, w.cuts, w.marginal)
     body = max(range(len(frags)), key=lambda i: frags[i].n if frags[i].clifford else -1)
     nv = frags[body].n_variants
-    nsamp = 8
+    t0 = time.perf_counter()      # one variant, to size the per-step sample
+    evaluate_workload(w, mode="sampled", seed_lo=SEED[0], seed_hi=SEED[1], variants_only={body: [0]},
+                      keep_tableaus=False)
+    per_v = time.perf_counter() - t0
+    nsamp = max(1, min(8, int(2.5 / max(per_v, 1e-3))))
     procs = host_cores()
     chunks = [[(p * nsamp + i) * 97 % nv for i in range(nsamp)] for p in range(procs)]
     pool = None
@@ -256,16 +337,140 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8/f64",
             "data": "synthetic",
-            "config": {"workload": describe(ws), "parallelism": f"CPU oracle, {procs} host processes"},
+            "config": {"workload": describe(ws), "parallelism": f"CPU oracle, {procs} host processes",
+                       "scope": "Clifford body variants only (tableau, outcome space, shots); "
+                                "no statevector variants, fold or recombination"},
             "cpu_baseline": {"kind": "oracle", "cores": procs, "value": val, "unit": UNIT,
-                             "sample": f"per step: {procs} processes x {nsamp} body variants x {w.shots} shots"},
+                             "sample": f"per step: {procs} processes x {nsamp} body variants x {w.shots} shots "
+                                       f"(Clifford body variants only)"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
+# --- rooflines -----------------------------------------------------------------
+
+def _ncu_traffic(kernel, workload):
+    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu
+    summary (profiles/dram_traffic.md), or None when none is recorded or the
+    kernel's source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    for m in re.finditer(r"^\|\s*(\w+)\s*\|\s*(\w+)\s*\|\s*([0-9.]+)\s*\|\s*([0-9.]+)\s*\|\s*(\S+)\s*\|\s*([0-9a-f]{16})\s*\|",
+                         text, re.M):
+        k, wl, rd, wr, src, sha = m.groups()
+        if k == kernel and wl == workload:
+            try:
+                now = hashlib.sha256(open(os.path.join(ROOT, src), "rb").read()).hexdigest()[:16]
+            except OSError:
+                return None
+            return (float(rd) + float(wr)) * 1e6 if now == sha else None
+    return None
+
+
+STAGE_KERNEL = {"sample": "sample_hub8_kernel", "recombine": "gemm_stream_kernel", "clifford": "body_basis_kernel"}
+
+
+def stage_kernel(st, precision):
+    """The kernel whose DRAM counters stand for a stage (its longest launch)."""
+    if st == "recombine" and precision == "bf16":
+        return "gemm_bf16_tc_kernel"
+    return STAGE_KERNEL.get(st)
+
+
+def stage_rooflines(stage, ws, prob_infos, pk, pk_kind, precision, workload):
+    """Roofline of every stage: algorithmic work per launch / live duration.
+
+    Peaks: lane ops = SMs x 128 lanes x max SM clock (one 32-bit op per lane
+    per clock, the issue limit); FP32 = SMs x 128 FMA x 2 x clock; shared
+    memory = SMs x 128 B x clock; HBM = the measured copy bandwidth.
+
+    clifford    smem: the body evolved once per Clifford fragment, each fused
+                two-qubit op reading and writing its 4 columns of 2n bits
+                (2n bytes per op); per variant the screen's elimination of
+                (n_meas + n_qout + n_qin) vectors of n_meas bits (4 bytes each,
+                read and written per pivot)
+    sample      alu: per shot a 1/(4 s) share of one Philox4x32-10 call (10
+                rounds of 2 wide multiplies and 2 three-way XORs = 40 lane
+                ops; s = 4, 2, 1 shots per output word at |A| <= 8, 16, above),
+                1 op for its field, 3 per table lookup (L = 1, 2, 3) and 3 for
+                the counter increment; per hub variant and output o, 2^qout
+                counter reads and one store per operand row of the variant
+                (2^(Z-basis outputs)), averaged over the variants
+    statevector alu: a fused 4x4 complex op costs 32 FP32 flops per amplitude
+    recombine   hbm: the hub operand read once (4 B per element, 2 B in BF16),
+                the Kronecker operand R (K x N x 4 B) and the split-K partials
+                written and read once
+    fold, operands
+                hbm: variant data read once and fragment tensors written once
+    """
+    clk = pk.get("sm_max_mhz", 2070.0) * 1e6
+    lanes = N_SM * 128 * clk
+    out = {}
+    for st, ms in stage.items():
+        t = ms * 1e-3
+        if t <= 0:
+            continue
+        if st == "clifford":
+            by = 0
+            for x, infos in zip(ws, prob_infos):
+                for i in infos:
+                    if i["clifford"]:
+                        by += i["n_ops"] * 2 * i["n_wires"]
+                        by += i["n_variants"] * (i["n_meas"] + i["n_qout"] + i["n_qin"]) * i["n_meas"] * 8
+            out[st] = {"bound": "smem", "achieved": by / t / 1e9, "peak": N_SM * 128 * clk / 1e9, "unit": "GB/s",
+                       "peak_source": f"derived: {N_SM} SMs x 128 B x {clk/1e6:.0f} MHz"}
+        elif st == "sample":
+            ops = 0.0
+            for x, infos in zip(ws, prob_infos):
+                for i in infos:
+                    if not i["clifford"]:
+                        continue
+                    per_word = 4 if i["n_meas"] <= 8 else 2 if i["n_meas"] <= 16 else 1
+                    lookups = 1 if i["n_meas"] <= 8 else 2 if i["n_meas"] <= 16 else 3
+                    ops += i["n_variants"] * x.shots * (40 / (4 * per_word) + 1 + 3 * lookups + 3)
+                    if i["n_slots"] == len(x.cuts):   # hub of the star: the operand rows
+                        rows = (4 ** i["n_qin"]) * (4 ** i["n_qout"]) / max(1, i["n_variants"])
+                        ops += i["n_variants"] * (1 << i["n_marg"]) * ((1 << i["n_qout"]) + rows)
+            out[st] = {"bound": "alu", "achieved": ops / t / 1e12, "peak": lanes / 1e12, "unit": "T lane-op/s",
+                       "peak_source": f"derived: {N_SM} SMs x 128 lanes x {clk/1e6:.0f} MHz"}
+        elif st == "statevector":
+            fl = sum(i["n_variants"] * i["n_ops"] * 32 * (1 << i["n_wires"])
+                     for infos in prob_infos for i in infos if not i["clifford"])
+            out[st] = {"bound": "alu", "achieved": fl / t / 1e12, "peak": N_SM * 256 * clk / 1e12,
+                       "unit": "TFLOP/s", "peak_source": f"derived: {N_SM} SMs x 128 FP32 FMA x 2 x {clk/1e6:.0f} MHz"}
+        else:
+            by = 0
+            for x, infos in zip(ws, prob_infos):
+                k = len(x.cuts)
+                if st == "recombine":
+                    M = 1 << max([i["n_marg"] for i in infos if i["n_slots"] == k] or [0])
+                    N = (1 << len(x.marginal)) // M
+                    by += (4 ** k) * M * (2 if precision == "bf16" else 4) + (4 ** k) * N * 4
+                else:
+                    for i in infos:
+                        hub = i["n_slots"] == k
+                        if st == "fold" and not (hub and i["clifford"]):
+                            by += i["n_variants"] * 4 * (1 << i["n_meas"]) + 4 * (1 << i["n_marg"]) * 4 ** i["n_slots"]
+                        if st == "operands" and not hub:
+                            by += 8 * (1 << i["n_marg"]) * 4 ** i["n_slots"]
+            out[st] = {"bound": "hbm", "achieved": by / t / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                       "peak_source": pk_kind}
+        out[st]["frac"] = out[st]["achieved"] / out[st]["peak"]
+        kern = stage_kernel(st, precision)
+        out[st]["traffic"] = _ncu_traffic(kern, workload) if kern else None
+        out[st]["ms"] = ms
+    return out
+
+
+# --- our arm -------------------------------------------------------------------
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_2303_10788_gb300 import ccs
+    from paper_2303_10788_gb300.sharding import max_over_ranks
     torch.cuda.set_device(local_rank)
     dist = None
     if world > 1:
@@ -277,7 +482,7 @@ def run_ours(args, rank, world, local_rank):
             dist.barrier()
         torch.cuda.synchronize()
 
-    ws_in = workloads_for(args.workload)          # cuts None: searched inside ccs_build_fragments
+    ws_in = workloads_for(args.workload, rank)      # cuts None: searched inside ccs_build_fragments
     seed = (SEED[0] + rank, SEED[1])
     ctx = ccs.ccs_create(local_rank)
     plan = ccs.ccs_build_fragments(ctx, ws_in)
@@ -296,33 +501,37 @@ def run_ours(args, rank, world, local_rank):
     prec = ccs.CCS_BF16 if args.precision == "bf16" else ccs.CCS_FP32
     pvb = bool(args.per_variant_body or args.plain)
     graph = not args.plain
-    res = ccs.ccs_eval_variants(ctx, plan, mode=ccs.CCS_SAMPLED, shots=w.shots, seed_lo=seed[0],
-                                seed_hi=seed[1], use_graph=graph, autotune=args.autotune and not args.plain, per_variant_body=pvb)
+    tune = not args.no_autotune and not args.plain
+    ev = dict(mode=ccs.CCS_SAMPLED, shots=w.shots, seed_lo=seed[0], seed_hi=seed[1], per_variant_body=pvb)
+    res = ccs.ccs_eval_variants(ctx, plan, use_graph=graph, autotune=tune, **ev)
     tuning = ccs.ccs_get_tuning(ctx, res)
 
-    def step():
-        ccs.ccs_eval_variants(ctx, plan, mode=ccs.CCS_SAMPLED, shots=w.shots, seed_lo=seed[0],
-                              seed_hi=seed[1], use_graph=graph, res=res, per_variant_body=pvb)
-        ccs.ccs_recombine(ctx, plan, res, precision=prec, marginal_out=marg, zexp_out=zexp, use_graph=graph)
+    def step(p=prec):
+        ccs.ccs_eval_variants(ctx, plan, use_graph=graph, res=res, **ev)
+        ccs.ccs_recombine(ctx, plan, res, precision=p, marginal_out=marg, zexp_out=zexp, use_graph=graph)
+
+    def timed(fn, steps):
+        """CUDA-event time of `steps` calls of fn, L2 flushed before each."""
+        stream = torch.cuda.current_stream()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(steps):
+            flush.zero_()
+            evs[i][0].record(stream)
+            fn()
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs) / 1e3
 
     for _ in range(max(3, args.warmup)):
         step()
-    stream = torch.cuda.current_stream()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     barrier()
     clk = Clocks(local_rank)
     launches0 = ccs.ccs_launch_count()
-    for i in range(args.steps):
-        flush.zero_()
-        evs[i][0].record(stream)
-        step()
-        evs[i][1].record(stream)
+    t_local = timed(step, args.steps)
     barrier()
     launches = ccs.ccs_launch_count() - launches0
     clocks = clk.stop()
-    step_ms = [a.elapsed_time(b) for a, b in evs]
-    from paper_2303_10788_gb300.sharding import max_over_ranks
-    t_tot = max_over_ranks(sum(step_ms) / 1e3, dist, device="cuda")
+    t_tot = max_over_ranks(t_local, dist, device="cuda")
     value = units_per_step * args.steps * world / t_tot
 
     # --- per-stage kernel times (profiled pass, same work, no graph) ----------
@@ -330,8 +539,7 @@ def run_ours(args, rank, world, local_rank):
     acc = {}
     for _ in range(args.steps):
         flush.zero_()
-        ccs.ccs_eval_variants(ctx, plan, mode=ccs.CCS_SAMPLED, shots=w.shots, seed_lo=seed[0],
-                              seed_hi=seed[1], res=res, per_variant_body=pvb)
+        ccs.ccs_eval_variants(ctx, plan, res=res, **ev)
         ccs.ccs_recombine(ctx, plan, res, precision=prec, marginal_out=marg, zexp_out=zexp)
         for k, v in ccs.ccs_get_stage_times(ctx).items():
             acc.setdefault(k, []).append(v)
@@ -348,19 +556,18 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         p2 = ccs.ccs_build_fragments(ctx, packed)
-        r2 = ccs.ccs_eval_variants(ctx, p2, mode=ccs.CCS_SAMPLED, shots=w.shots, seed_lo=seed[0],
-                                   seed_hi=seed[1], per_variant_body=pvb)
+        r2 = ccs.ccs_eval_variants(ctx, p2, **ev)
         m_host, z_host = ccs.ccs_recombine(ctx, p2, r2, precision=prec)
         e2e_times.append(time.perf_counter() - t0)
         del r2, p2
-    e2e_s = statistics.mean(e2e_times)
+    e2e_s = max_over_ranks(statistics.mean(e2e_times), dist, device="cuda")
     h2d = sum(24 * len(x.circuit.gates) + 8 * len(x.cuts or []) + 4 * len(x.marginal) +
               4 * sum(len(z) + 1 for z in x.zstrings) for x in ws)
     d2h = 8 * sum((1 << len(x.marginal)) + len(x.zstrings) for x in ws)
 
     pk, pk_kind = peaks()
-    roofs = stage_rooflines(stage, w, ws, prob_infos, pk, pk_kind, args.precision)
-    roof = dict(roofs[dom], stage=dom)
+    roofs = stage_rooflines(stage, ws, prob_infos, pk, pk_kind, args.precision, args.workload)
+    roof = dict(roofs[dom], stage=dom, kernel=stage_kernel(dom, args.precision))
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64/" + args.precision, "data": "synthetic",
@@ -368,19 +575,62 @@ def run_ours(args, rank, world, local_rank):
                                                    if any(x.cuts is None for x in ws_in) else ""),
                        "variant_shots_per_step": units_per_step,
                        "l2": "flushed between steps (512 MB write, outside the step events)",
-                       "parallelism": f"{world} independent replicas (no collective)",
+                       "parallelism": (f"{world} ranks, each its own batch (other Philox seeds"
+                                       f"{', other circuits' if len(ws) > 1 else ''}); no collective"),
                        "launch": ("plain: per-variant simulation, stream launches" if args.plain else
                                   "two CUDA-graph replays per step (evaluation, recombination)"),
                        "recombination": args.precision + (" (tcgen05 where eligible)" if args.precision == "bf16" else
-                                                          " (CUDA-core FMA)"),
+                                                          " (CUDA-core FMA, FP64 across splits)"),
                        "tuning": {"threads": tuning[0], "words_per_op": tuning[1], "shots_per_cta": tuning[2],
-                                  "hub_threads": tuning[3],
-                                  "autotuned": bool(args.autotune)}},
+                                  "hub_threads": tuning[3], "autotuned": tune}},
             "circuits_per_s": world * len(ws) * args.steps / t_tot,
             "stage_ms": stage, "roofline": roof, "stage_roofline": roofs,
             "e2e": {"value": units_per_step * world / e2e_s, "unit": UNIT, "circuits_per_s": world * len(ws) / e2e_s,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "clocks": clocks}
+
+    # --- the same run's other forms: BF16 tensor-core contraction, plain GPU form
+    if not args.plain and not args.no_extras:
+        k2 = max(3, min(args.steps, 10))
+        if prec == ccs.CCS_FP32:
+            for _ in range(2):
+                step(ccs.CCS_BF16)
+            t16 = max_over_ranks(timed(lambda: step(ccs.CCS_BF16), k2), dist, device="cuda")
+            line["bf16"] = {"value": units_per_step * k2 * world / t16, "ms_per_step": 1e3 * t16 / k2,
+                            "circuits_per_s": world * len(ws) * k2 / t16,
+                            "recombination": "bf16 operands, tcgen05 where eligible, FP32 accumulation"}
+        # Clifford-specific stitching (no shots: the hub operand in closed form,
+        # vanishing rows skipped); the same circuits, exact results
+        ev_s = dict(mode=ccs.CCS_STITCH, per_variant_body=False)
+        res_s = ccs.ccs_eval_variants(ctx, plan, use_graph=True, **ev_s)
+
+        def stitch_step():
+            ccs.ccs_eval_variants(ctx, plan, use_graph=True, res=res_s, **ev_s)
+            ccs.ccs_recombine(ctx, plan, res_s, precision=ccs.CCS_FP32, marginal_out=marg, zexp_out=zexp,
+                              use_graph=True)
+
+        for _ in range(2):
+            stitch_step()
+        ts = max_over_ranks(timed(stitch_step, k2), dist, device="cuda")
+        line["stitched"] = {"ms_per_step": 1e3 * ts / k2, "circuits_per_s": world * len(ws) * k2 / ts,
+                            "variants_per_s": n_cliff_var * k2 * world / ts,
+                            "mode": "Clifford-specific stitching (exact; no shots; zero Pauli rows skipped)"}
+        del res_s
+        ev_p = dict(ev, per_variant_body=True)
+        res_p = ccs.ccs_eval_variants(ctx, plan, **ev_p)
+
+        def plain_step():
+            ccs.ccs_eval_variants(ctx, plan, res=res_p, **ev_p)
+            ccs.ccs_recombine(ctx, plan, res_p, precision=ccs.CCS_FP32, marginal_out=marg, zexp_out=zexp)
+
+        kp = max(2, min(args.steps, 5))
+        plain_step()
+        tp = max_over_ranks(timed(plain_step, kp), dist, device="cuda")
+        line["plain"] = {"value": units_per_step * kp * world / tp, "ms_per_step": 1e3 * tp / kp,
+                         "circuits_per_s": world * len(ws) * kp / tp,
+                         "form": "per-variant simulation of each variant's whole circuit, stream launches, "
+                                 "FP32 contraction, default launch shapes"}
+        del res_p
     if rank == 0 and world == 1 and not args.no_cpu_baseline:   # the oracle baseline at N = 1 only
         line["cpu_baseline"] = oracle_baseline(ws)
     if rank == 0:
@@ -389,109 +639,38 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
-N_SM = 152
-
-
-def stage_rooflines(stage, w, ws, prob_infos, pk, pk_kind, precision):
-    """Roofline of every stage: algorithmic work per launch / live duration.
-
-    Lane-op peak = SMs x 128 lanes x clock (one 32-bit integer/logic op per
-    lane per clock); FP32 peak = SMs x 128 FMA x 2 x clock; HBM peak = the
-    measured copy bandwidth.
-
-    clifford    alu: body evolution, once per Clifford fragment: 140 lane ops
-                per fused op and 64-row word (4x4 GF(2) map + sign polynomial
-                on 64-bit words); Z-image records, once per fragment: the
-                ordered row product over n columns x W words, 25 lane ops per
-                word, for nz + 3 qout + m records; per variant the screen
-                (elimination of n_meas + n_qout + n_qin vectors over n_meas
-                bits, 4 lane ops per vector-bit) and its Z-string values (per
-                string and output subset, ~2 image factors x Wh words x 6 ops)
-    sample      alu: per shot a 1/(4 s) share of one Philox4x32-10 call (60
-                lane ops; s = 4, 2, 1 shots per output word at |A| <= 8, 16,
-                above), 3 lane ops per table lookup (L = 1, 2, 3 lookups) and
-                4 for the field, index and atomic; for a star's hub 35 lane ops
-                per output (packed counter loads, the 16-point Walsh-Hadamard
-                transform on paired 16-bit lanes, operand stores)
-    statevector alu: a fused 4x4 complex op costs 32 FP32 flops per amplitude
-    fold, operands, recombine
-                hbm: fold/operands: variant data read once and fragment
-                tensors written once; recombine: the hub operand read once by
-                the GEMM (plus its BF16 transpose: 4 B read + 2 B written per
-                element) and the leaves' operand
-    """
-    clk = pk.get("sm_max_mhz", 2070.0) * 1e6
-    lanes = N_SM * 128 * clk
-    out = {}
-    for st, ms in stage.items():
-        t = ms * 1e-3
-        if st in ("clifford", "sample"):
-            ops = 0
-            for x, infos in zip(ws, prob_infos):
-                for i in infos:
-                    if not i["clifford"]:
-                        continue
-                    W = 2 * ((i["n_wires"] + 63) // 64)
-                    nz = len(x.zstrings)
-                    if st == "clifford":
-                        ops += i["n_ops"] * W * 140
-                        ops += (nz + 3 * i["n_qout"] + i["n_marg"]) * i["n_wires"] * W * 25
-                        ops += i["n_variants"] * (i["n_meas"] + i["n_qout"] + i["n_qin"]) * i["n_meas"] * 4
-                        ops += i["n_variants"] * nz * (1 << i["n_qout"]) * 2 * (W // 2) * 6
-                    else:
-                        per_word = 4 if i["n_meas"] <= 8 else 2 if i["n_meas"] <= 16 else 1
-                        lookups = 1 if i["n_meas"] <= 8 else 2 if i["n_meas"] <= 16 else 3
-                        ops += i["n_variants"] * x.shots * (60 / (4 * per_word) + 3 * lookups + 4)
-                        if i["n_slots"] == len(x.cuts):   # hub of the star (one slot per cut)
-                            ops += i["n_variants"] * (1 << i["n_marg"]) * 35
-            out[st] = {"bound": "alu", "achieved": ops / t / 1e12, "peak": lanes / 1e12, "unit": "T lane-op/s",
-                       "peak_source": f"derived: {N_SM} SMs x 128 lanes x {clk/1e6:.0f} MHz"}
-        elif st == "statevector":
-            fl = sum(i["n_variants"] * i["n_ops"] * 32 * (1 << i["n_wires"])
-                     for infos in prob_infos for i in infos if not i["clifford"])
-            out[st] = {"bound": "alu", "achieved": fl / t / 1e12, "peak": N_SM * 256 * clk / 1e12,
-                       "unit": "TFLOP/s", "peak_source": f"derived: {N_SM} SMs x 128 FP32 FMA x 2 x {clk/1e6:.0f} MHz"}
-        else:
-            by = 0
-            for x, infos in zip(ws, prob_infos):
-                k = len(x.cuts)
-                if st == "recombine":
-                    M = 1 << max([i["n_marg"] for i in infos if i["n_slots"] == k] or [0])
-                    N = (1 << len(x.marginal)) // M
-                    by += (4 ** k) * M * (8 if precision == "bf16" else 4) + (4 ** k) * N * 4
-                else:
-                    for i in infos:
-                        hub = i["n_slots"] == k
-                        if st == "fold" and not (hub and i["clifford"]):
-                            by += i["n_variants"] * 4 * (1 << i["n_meas"]) + 4 * (1 << i["n_marg"]) * 4 ** i["n_slots"]
-                        if st == "operands" and not hub:
-                            by += 8 * (1 << i["n_marg"]) * 4 ** i["n_slots"]
-            out[st] = {"bound": "hbm", "achieved": by / t / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                       "peak_source": pk_kind}
-        out[st]["frac"] = out[st]["achieved"] / out[st]["peak"]
-        out[st]["traffic"] = None
-        out[st]["ms"] = ms
-    return out
+def _spawned(local_rank, world, port, argv):
+    os.environ.update(RANK=str(local_rank), LOCAL_RANK=str(local_rank), WORLD_SIZE=str(world),
+                      MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    sys.argv = [sys.argv[0]] + argv
+    main()
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="config2")
+    ap.add_argument("--workload", default="config3")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the BF16 and plain-form figures")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"],
                     help="operands of the 4^k contraction (bf16 uses the tcgen05 GEMM where it applies)")
-    ap.add_argument("--autotune", action="store_true", help="tune launch shapes on the plan before timing")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--per-variant-body", action="store_true",
                     help="simulate every variant's whole circuit (no shared fragment body)")
     ap.add_argument("--plain", action="store_true",
                     help="the plain GPU form: per-variant simulation, no CUDA graph, FP32, no autotuning")
     args = ap.parse_args()
+    if "WORLD_SIZE" not in os.environ and args.gpus > 1:
+        # started without a launcher: one spawned rank per GPU
+        import torch.multiprocessing as mp
+        port = 29400 + os.getpid() % 1000
+        mp.start_processes(_spawned, args=(args.gpus, port, sys.argv[1:]), nprocs=args.gpus, start_method="spawn")
+        return
     rank = int(os.environ.get("RANK", 0))
-    world = int(os.environ.get("WORLD_SIZE", args.gpus if args.gpus == 1 else 1))
+    world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
     if args.impl == "reference":
         run_reference(args, rank, world)

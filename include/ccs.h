@@ -170,9 +170,23 @@ int ccs_cut_candidates(ccs_ctx ctx, const ccs_problem* problem, const ccs_cut_op
 /* --- variant evaluation (Sec. V-B) ---------------------------------------- */
 #define CCS_EXACT 0
 #define CCS_SAMPLED 1
+/* Clifford-specific stitching (Sec. IX): every Pauli expectation of a
+ * stabilizer state is -1, 0 or +1 and follows from the state without
+ * shots, and the Pauli terms that vanish contribute nothing downstream.
+ * In this mode every Clifford variant is exact (as CCS_EXACT); a star
+ * hub's contraction operand (one row per preparation tuple and output
+ * Pauli string) is formed in closed form from each variant's outcome space
+ * -- a row is either identically zero, when its sign mask is not
+ * orthogonal to the space's purely quantum-output directions, or +-2^-r
+ * times a sign affine in the outputs on the space's projection -- without
+ * shots or per-variant distributions, and the contraction skips the rows
+ * that vanish.  Results equal CCS_EXACT's up to FP32 rounding order. */
+#define CCS_STITCH 2
 typedef struct {
   int32_t mode;            /* CCS_EXACT: closed-form 2^-rank per Clifford variant;
-                              CCS_SAMPLED: `shots` Philox shots per Clifford variant */
+                              CCS_SAMPLED: `shots` Philox shots per Clifford variant;
+                              CCS_STITCH: CCS_EXACT with the hub operand in closed form
+                              and its vanishing rows skipped */
   uint32_t shots;
   uint32_t seed_lo, seed_hi;   /* Philox4x32-10 key */
   int32_t keep_tableaus;   /* 1: keep every final tableau (ccs_get_tableau) and the
@@ -222,7 +236,12 @@ typedef struct {
                                  tcgen05 GEMM applies (0: use it, the default) */
   int32_t use_graph;          /* 1: capture the contraction launches in a CUDA graph
                                  kept on the result (per precision and tensor-core
-                                 choice) and replay it */
+                                 choice) and replay it (full cut-index range only) */
+  uint64_t k_lo, k_hi;        /* sum only the cut-index terms P in [k_lo, k_hi) of every
+                                 problem (clamped to its 4^k; k_hi = 0: to the end).
+                                 Partial results over disjoint ranges add up to the
+                                 full one: the split a multi-GPU contraction reduces
+                                 with one FP64 sum.  Partial ranges run on CUDA cores. */
 } ccs_recomb_opts;
 
 /* p(o) = 2^-k sum_{P in {I,X,Y,Z}^k} prod_f T_f(o_f, P|f) for every problem,
@@ -352,7 +371,9 @@ int ccs_get_outcome_space(ccs_ctx ctx, ccs_res res, int problem, int fragment, i
 /* Shot counts of a sampled Clifford variant, 2^|A_f| uint32. */
 int ccs_get_counts(ccs_ctx ctx, ccs_res res, int problem, int fragment, int variant, uint32_t* out);
 /* Probabilities of a variant over 2^|A_f| outcomes (float32): exact ones for
- * non-Clifford variants and exact-mode Clifford variants. */
+ * non-Clifford variants, exact-mode Clifford variants and, in CCS_STITCH
+ * mode, Clifford variants of fragments that are not a star's hub (a
+ * stitched hub forms no per-variant distribution: INVALID_ARG). */
 int ccs_get_dist(ccs_ctx ctx, ccs_res res, int problem, int fragment, int variant, float* out);
 /* Z-string values of a variant (float32, nz x 2^n_qout, row-major): entry
  * [s][u] is <Z_S prod_{o in u} M_o> of the fragment's final state, S the

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libccs.so")
 CCS_OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "UNSUPPORTED_GATE", -3: "TOO_MANY_CUTS", -4: "NC_TOO_WIDE",
           -5: "OOM", -6: "CUDA", -7: "TIMEOUT", -8: "UNSUPPORTED", -9: "DEVICE_CHECK"}
-CCS_EXACT, CCS_SAMPLED = 0, 1
+CCS_EXACT, CCS_SAMPLED, CCS_STITCH = 0, 1, 2
 CCS_FP32, CCS_BF16 = 0, 1
 
 # Every symbol include/ccs.h declares (checked by the ABI test).
@@ -69,7 +69,7 @@ class ccs_eval_opts(C.Structure):
 
 class ccs_recomb_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("outputs_on_device", C.c_int32), ("no_tensor_cores", C.c_int32),
-                ("use_graph", C.c_int32)]
+                ("use_graph", C.c_int32), ("k_lo", C.c_uint64), ("k_hi", C.c_uint64)]
 
 
 class ccs_fragment_info(C.Structure):
@@ -316,13 +316,16 @@ def ccs_eval_variants(ctx, plan, mode=CCS_SAMPLED, shots=1024, seed_lo=0x1234, s
 
 
 def ccs_recombine(ctx, plan, res, precision=CCS_FP32, marginal_out=None, zexp_out=None, tensor_cores=True,
-                  use_graph=False):
+                  use_graph=False, k_range=None):
     """Host mode (default): returns (marginal, zexp) float64 numpy arrays with
     all problems back to back.  Device mode: pass torch float64 CUDA tensors
-    as ``marginal_out`` / ``zexp_out``; the call does not synchronise."""
+    as ``marginal_out`` / ``zexp_out``; the call does not synchronise.
+    ``k_range`` = (lo, hi): sum only the cut-index terms in [lo, hi)
+    (hi = 0: to the end) -- a partial result of a split contraction."""
+    lo, hi = k_range if k_range is not None else (0, 0)
     on_dev = marginal_out is not None and hasattr(marginal_out, "data_ptr")
     if on_dev:
-        opts = ccs_recomb_opts(precision, 1, 0 if tensor_cores else 1, int(use_graph))
+        opts = ccs_recomb_opts(precision, 1, 0 if tensor_cores else 1, int(use_graph), lo, hi)
         ctx.check(lib().ccs_recombine(ctx.h, plan.h, res.h, C.byref(opts),
                                       C.c_void_p(marginal_out.data_ptr()),
                                       C.c_void_p(zexp_out.data_ptr() if zexp_out is not None else None)),
@@ -332,7 +335,7 @@ def ccs_recombine(ctx, plan, res, precision=CCS_FP32, marginal_out=None, zexp_ou
     nz = sum(len(getattr(p, "zstrings", []) or []) for p in plan.problems)
     marg = np.zeros(max(nm, 1))
     zexp = np.zeros(max(nz, 1))
-    opts = ccs_recomb_opts(precision, 0, 0 if tensor_cores else 1, int(use_graph))
+    opts = ccs_recomb_opts(precision, 0, 0 if tensor_cores else 1, int(use_graph), lo, hi)
     ctx.check(lib().ccs_recombine(ctx.h, plan.h, res.h, C.byref(opts),
                                   marg.ctypes.data_as(C.c_void_p), zexp.ctypes.data_as(C.c_void_p)),
               "ccs_recombine")

@@ -242,6 +242,10 @@ struct ccs_plan_s {
   bool hub_bytes_ok = true;         // every hub fits the byte-counter sampler
   long long n_counts_plain = 0;     // counts of non-hub Clifford fragments come first
   long long n_dist_nc = 0;          // distributions of statevector fragments come first
+  long long n_dist_stitch = 0;      // ... then non-hub Clifford fragments (all a stitched evaluation needs)
+  long long n_qrows = 0;            // operand-row flags of the Clifford hubs
+  bool stitch_ok = true;            // every Clifford hub has at most 4 quantum outputs
+  bool tableau_fits = true;         // every Clifford fragment's whole tableau fits in shared memory
   bool all_star = true;
   ~ccs_plan_s() { A.release(); }
 };
@@ -253,7 +257,8 @@ struct ccs_res_s {
   bool have_tabs = false;
   bool have_counts = false;
   bool counts_full = false;   // counts include the hubs' (kept for inspection)
-  bool dist_full = false;     // distributions include the Clifford fragments' (exact mode)
+  long long dist_len = 0;     // floats of the distribution buffer (statevector fragments first,
+                              // then non-hub Clifford, then hub Clifford fragments)
   Allocs A;
   cudaGraphExec_t graph = nullptr;
   long long graph_launches = 0;   // kernel nodes of the captured graph
@@ -626,12 +631,10 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
       for (auto& f : plan->fdev)
         if (!f.clifford) { f.dist_off = off; off += (long long)f.nv << f.nA; }
       plan->n_dist_nc = off;
-      for (auto& f : plan->fdev)
-        if (f.clifford) { f.dist_off = off; off += (long long)f.nv << f.nA; }
     }
-    if ((size_t)plan->cliff_smem_words * 8 > c->smem_optin && !items_c.empty()) {
-      return fail(c, CCS_ERR_UNSUPPORTED, "Clifford fragment does not fit in shared memory");
-    }
+    // a per-variant tableau (kept tableaus, per-variant bodies) must fit in
+    // shared memory; the shared-body path has no such limit (checked at evaluation)
+    plan->tableau_fits = (size_t)plan->cliff_smem_words * 8 <= c->smem_optin || items_c.empty();
     // Items costliest first, ties in insertion order.  A fragment's items are
     // consecutive and cost the same, so the runs of equal cost are sorted
     // stably instead of the items (the same order, far fewer comparisons).
@@ -692,6 +695,24 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
         if (P.hub >= 0)
           for (int l = 0; l < nfr; ++l) plan->fdev[f0r + l].role = (l == P.hub) ? 1 : 2;
         f0r += nfr;
+      }
+    }
+    // distributions of Clifford fragments: non-hub ones first (exact
+    // distributions a stitched evaluation still forms), hubs after
+    {
+      long long off = plan->n_dist_nc;
+      for (auto& f : plan->fdev)
+        if (f.clifford && f.role != 1) { f.dist_off = off; off += (long long)f.nv << f.nA; }
+      plan->n_dist_stitch = off;
+      for (auto& f : plan->fdev)
+        if (f.clifford && f.role == 1) { f.dist_off = off; off += (long long)f.nv << f.nA; }
+      for (auto& f : plan->fdev) {
+        f.qrow_off = -1;
+        if (f.clifford && f.role == 1) {
+          f.qrow_off = plan->n_qrows;
+          plan->n_qrows += 1ll << (2 * f.n_slots);
+          if (f.qout > 4) plan->stitch_ok = false;
+        }
       }
     }
     // shot counts: non-hub Clifford fragments first (they are zeroed before
@@ -757,6 +778,7 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
         d.mtiles = (d.M + d.TM - 1) / d.TM;
         d.ntiles = (d.N + d.TN - 1) / d.TN;
         d.hub_T_off = plan->fdev[f0 + P.hub].T_off;
+        d.hub_qrow_off = plan->fdev[f0 + P.hub].qrow_off;
         d.tc = (gemm_tc_supported(d.M, d.N, d.K) && d.K >= 4096 && d.M >= 128) ? 1 : 0;
         // leaf by leaf in shared memory, the hub outputs in slices of TM (the
         // contraction never mixes hub outputs), when every intermediate of a
@@ -944,6 +966,10 @@ static int enqueue_eval(ccs_ctx c, ccs_plan p, ccs_res r) {
   if (e.mode == CCS_EXACT && p->n_dist)
     if ((err = cudaMemsetAsync(r->dr.dist, 0, p->n_dist * sizeof(float), s)) != cudaSuccess)
       return cuda_fail(c, err, "memset dist");
+  if (e.mode == CCS_STITCH && p->n_dist_stitch > p->n_dist_nc)    // the non-hub Clifford distributions
+    if ((err = cudaMemsetAsync(r->dr.dist + p->n_dist_nc, 0, (p->n_dist_stitch - p->n_dist_nc) * sizeof(float),
+                               s)) != cudaSuccess)
+      return cuda_fail(c, err, "memset dist");
   const DevPlan& dp = p->dp;
   const bool fork = dp.n_items_nc > 0 && !c->profiling;
   cudaStream_t s2 = fork ? c->side : s;
@@ -989,6 +1015,12 @@ static int enqueue_eval(ccs_ctx c, ccs_plan p, ccs_res r) {
         return cuda_fail(c, err, "sample kernel");
       stage_end(c, ST_SAMPLE);
     }
+    if (e.mode == CCS_STITCH) {   // Clifford hubs: the operand in closed form from the outcome spaces
+      stage_begin(c, ST_SAMPLE);
+      if ((err = launch_hub_exact(dp, r->dr, p->d_items_hub, p->n_items_hub, s)) != cudaSuccess)
+        return cuda_fail(c, err, "hub exact kernel");
+      stage_end(c, ST_SAMPLE);
+    }
     stage_begin(c, ST_FOLD);
     if ((err = launch_fold(dp, r->dr, e, p->fold_cliff, s)) != cudaSuccess) return cuda_fail(c, err, "fold kernel");
     stage_end(c, ST_FOLD);
@@ -998,8 +1030,9 @@ static int enqueue_eval(ccs_ctx c, ccs_plan p, ccs_res r) {
     if ((err = cudaStreamWaitEvent(s, c->join_ev, 0)) != cudaSuccess) return cuda_fail(c, err, "join wait");
   }
   stage_begin(c, ST_OPERANDS);
-  // hubs: Clifford hubs in sampled mode already have Q from the fused sampler
-  const FoldSet& hubs = e.mode == CCS_SAMPLED ? p->fold_hubs_nc : p->fold_hubs;
+  // hubs: Clifford hubs in sampled and stitched modes already have Q (the
+  // fused sampler, the closed form)
+  const FoldSet& hubs = e.mode == CCS_EXACT ? p->fold_hubs : p->fold_hubs_nc;
   if ((err = launch_operands(dp, r->dr, e, hubs, p->fold_others, s)) != cudaSuccess)
     return cuda_fail(c, err, "operand kernels");
   stage_end(c, ST_OPERANDS);
@@ -1098,7 +1131,13 @@ int ccs_get_tuning(ccs_ctx c, ccs_res r, int* cliff_threads, int* words_per_op, 
 int ccs_eval_variants(ccs_ctx c, ccs_plan p, const ccs_eval_opts* opts, ccs_res* res) {
   return abi_guard([&](int code, const char* m) { return fail(c, code, m); }, [&]() -> int {
     if (!c || !p || !opts || !res) return fail(c, CCS_ERR_INVALID_ARG, "bad arguments");
-    if (opts->mode != CCS_EXACT && opts->mode != CCS_SAMPLED) return fail(c, CCS_ERR_INVALID_ARG, "bad mode");
+    if (opts->mode != CCS_EXACT && opts->mode != CCS_SAMPLED && opts->mode != CCS_STITCH)
+      return fail(c, CCS_ERR_INVALID_ARG, "bad mode");
+    if ((opts->keep_tableaus || opts->per_variant_body) && !p->tableau_fits)
+      return fail(c, CCS_ERR_UNSUPPORTED, "a Clifford fragment's tableau does not fit in shared memory "
+                                          "(kept tableaus and per-variant bodies need it; at most 640 wires)");
+    if (opts->mode == CCS_STITCH && !p->stitch_ok)
+      return fail(c, CCS_ERR_UNSUPPORTED, "stitched mode: a Clifford hub with more than 4 quantum outputs");
     if (opts->mode == CCS_SAMPLED && opts->shots == 0) return fail(c, CCS_ERR_INVALID_ARG, "zero shots");
     if (opts->mode == CCS_SAMPLED && opts->shots > 0xffffu && p->max_hub_nA > 15)
       return fail(c, CCS_ERR_UNSUPPORTED, "more than 65535 shots with a 16-bit hub outcome space");
@@ -1115,7 +1154,9 @@ int ccs_eval_variants(ccs_ctx c, ccs_plan p, const ccs_eval_opts* opts, ccs_res*
       r->A.ctx = c;
       DevRes& d = r->dr;
       d.spaces = r->A.get<SpaceRec>(std::max<long long>(p->n_spaces, 1));
-      d.dist = r->A.get<float>(std::max<long long>(p->n_dist_nc, 1));   // exact mode widens it
+      d.dist = r->A.get<float>(std::max<long long>(p->n_dist_nc, 1));   // exact / stitched modes widen it
+      r->dist_len = p->n_dist_nc;
+      d.qnz = r->A.get<uint8_t>(std::max<long long>(p->n_qrows, 1));
       d.zval = r->A.get<float>(std::max<long long>(p->n_zval, 1));
       d.T = r->A.get<float>(std::max<long long>(p->n_T, 1));
       d.TQ = r->A.get<float>(std::max<long long>(p->n_T, 1));
@@ -1146,7 +1187,7 @@ int ccs_eval_variants(ccs_ctx c, ccs_plan p, const ccs_eval_opts* opts, ccs_res*
         d.TQh = r->A.get<uint16_t>(p->n_T);
         r->rt_scratch = r->A.get<uint16_t>(p->rt_total);
       }
-      if (!d.spaces || !d.dist || !d.zval || !d.T || !d.TQ || !d.marg || !d.zexp || !d.work || !d.status ||
+      if (!d.spaces || !d.dist || !d.qnz || !d.zval || !d.T || !d.TQ || !d.marg || !d.zexp || !d.work || !d.status ||
           !d.body || !d.rowbasis || !d.zimg || !d.fragcnt || !d.pbasis ||
           !r->scratch || (p->rt_total && (!d.TQh || !r->rt_scratch))) {
         return fail(c, CCS_ERR_OOM, "result allocation failed");
@@ -1166,11 +1207,16 @@ int ccs_eval_variants(ccs_ctx c, ccs_plan p, const ccs_eval_opts* opts, ccs_res*
       r->counts_full = want_full_counts;
       drop_graph();
     }
-    if (opts->mode == CCS_EXACT && !r->dist_full && p->n_dist > p->n_dist_nc) {
-      r->dr.dist = r->A.get<float>(p->n_dist);
-      if (!r->dr.dist) return fail(c, CCS_ERR_OOM, "distribution allocation failed");
-      r->dist_full = true;
-      drop_graph();
+    {
+      const long long need = opts->mode == CCS_EXACT ? p->n_dist : opts->mode == CCS_STITCH ? p->n_dist_stitch
+                                                                                          : p->n_dist_nc;
+      if (need > r->dist_len) {
+        float* nd = r->A.get<float>(need);   // every evaluation rewrites what it reads
+        if (!nd) return fail(c, CCS_ERR_OOM, "distribution allocation failed");
+        r->dr.dist = nd;
+        r->dist_len = need;
+        drop_graph();
+      }
     }
     if (opts->keep_tableaus && !r->have_tabs && p->n_tab) {
       r->dr.tabs = r->A.get<unsigned long long>(p->n_tab);
@@ -1261,14 +1307,20 @@ int ccs_recombine(ccs_ctx c, ccs_plan p, ccs_res r, const ccs_recomb_opts* opts,
     const bool on_dev = opts && opts->outputs_on_device;
     if (prec != CCS_FP32 && prec != CCS_BF16) return fail(c, CCS_ERR_INVALID_ARG, "bad precision");
     cudaSetDevice(c->device);
-    const bool tc = !(opts && opts->no_tensor_cores);
+    const bool stitched = r->ep.mode == CCS_STITCH;
+    const bool tc = !(opts && opts->no_tensor_cores) && !stitched;   // stitched rows skip zeros on CUDA cores
     RecombSizes rz{p->r_total, p->part_total, p->gemm_blocks, p->n_marg, p->n_zexp,
                    p->d_direct_items, (int)p->direct_items.size(), (int)p->direct_stage_floats, p->chain,
                    p->d_r_prefix, p->d_blk_prefix, p->d_out_prefix, p->d_z_prefix, p->max_tile_smem,
-                   p->pdev.data(), (int)p->pdev.size(), r->rt_scratch, tc ? 1 : 0};
+                   p->pdev.data(), (int)p->pdev.size(), r->rt_scratch, tc ? 1 : 0, stitched ? 1 : 0, KRange{0, -1}};
+    if (opts && (opts->k_lo || opts->k_hi)) {
+      if (opts->k_hi && opts->k_hi <= opts->k_lo) return fail(c, CCS_ERR_INVALID_ARG, "empty cut-index range");
+      if (opts->k_lo > (1ull << 62) || opts->k_hi > (1ull << 62)) return fail(c, CCS_ERR_INVALID_ARG, "bad range");
+      rz.krange = KRange{(long long)opts->k_lo, opts->k_hi ? (long long)opts->k_hi : -1};
+    }
     cudaError_t e;
-    if (opts && opts->use_graph && !c->profiling) {
-      const int key = prec * 2 + (tc ? 1 : 0);
+    if (opts && opts->use_graph && !c->profiling && rz.krange.full()) {
+      const int key = prec * 2 + (tc ? 1 : 0) + (stitched ? 4 : 0);
       if (!r->rgraph || r->rgraph_key != key) {
         if (r->rgraph) { cudaGraphExecDestroy(r->rgraph); r->rgraph = nullptr; }
         cudaStream_t s = c->stream;
@@ -1445,7 +1497,8 @@ int ccs_get_dist(ccs_ctx c, ccs_res r, int problem, int fragment, int variant, f
     const FragDev* d;
     int rc = locate(c, r, problem, fragment, variant, &d);
     if (rc) return rc;
-    if ((d->clifford && r->ep.mode != CCS_EXACT) || variant < 0) return fail(c, CCS_ERR_INVALID_ARG, "no distribution");
+    const bool have = !d->clifford || r->ep.mode == CCS_EXACT || (r->ep.mode == CCS_STITCH && d->role != 1);
+    if (!have || variant < 0) return fail(c, CCS_ERR_INVALID_ARG, "no distribution");
     cudaError_t e = cudaMemcpy(out, r->dr.dist + d->dist_off + ((long long)variant << d->nA),
                                sizeof(float) << d->nA, cudaMemcpyDeviceToHost);
     return e == cudaSuccess ? CCS_OK : cuda_fail(c, e, "copy dist");
@@ -1482,8 +1535,13 @@ int ccs_get_operand(ccs_ctx c, ccs_res r, int problem, int fragment, float* out)
     cudaError_t e = cudaMemcpy(t.data(), r->dr.TQ + d->T_off, cnt * sizeof(float), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(c, e, "copy operand");
     const long long M = 1ll << d->m, K = 1ll << (2 * d->n_slots);
+    std::vector<uint8_t> live(K, 1);
+    if (r->ep.mode == CCS_STITCH && d->clifford) {   // rows flagged zero may never have been written
+      e = cudaMemcpy(live.data(), r->dr.qnz + d->qrow_off, K, cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) return cuda_fail(c, e, "copy row flags");
+    }
     for (long long k = 0; k < K; ++k)
-      for (long long o = 0; o < M; ++o) out[o * K + k] = t[k * M + o];
+      for (long long o = 0; o < M; ++o) out[o * K + k] = live[k] ? t[k * M + o] : 0.f;
     return CCS_OK;
   });
 }
@@ -1496,6 +1554,8 @@ int ccs_get_tensor(ccs_ctx c, ccs_res r, int problem, int fragment, float* out) 
     const long long cnt = (1ll << d->m) << (2 * d->n_slots);
     if (d->role == 1 && d->clifford && r->ep.mode == CCS_SAMPLED && !r->ep.keep_tableaus)
       return fail(c, CCS_ERR_INVALID_ARG, "a sampled hub's tensor needs its counts (keep_tableaus)");
+    if (d->role == 1 && d->clifford && r->ep.mode == CCS_STITCH)
+      return fail(c, CCS_ERR_INVALID_ARG, "a stitched hub forms no per-variant distribution (see ccs_get_operand)");
     if (d->role == 1) {   // a hub's T is not formed on the hot path: fold it now
       const int g = (int)(d - r->plan->fdev.data());
       std::vector<int> fi{g};
@@ -1566,7 +1626,8 @@ extern "C" int ccs_recombine_noalloc(ccs_ctx c, ccs_plan p, ccs_res r, int preci
     RecombSizes rz{p->r_total, p->part_total, p->gemm_blocks, p->n_marg, p->n_zexp,
                    p->d_direct_items, (int)p->direct_items.size(), (int)p->direct_stage_floats, p->chain,
                    p->d_r_prefix, p->d_blk_prefix, p->d_out_prefix, p->d_z_prefix, p->max_tile_smem,
-                   p->pdev.data(), (int)p->pdev.size(), nullptr, 0};
+                   p->pdev.data(), (int)p->pdev.size(), nullptr, 0, r->ep.mode == CCS_STITCH ? 1 : 0,
+                   KRange{0, -1}};
     e = launch_recombine(p->dp, r->dr, precision, rz, scratch, marginal_out, zexp_out, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "recombine kernel");
     return CCS_OK;

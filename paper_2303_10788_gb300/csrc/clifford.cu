@@ -19,7 +19,7 @@
 
 namespace ccs {
 
-constexpr int kMaxWh = (kMaxTableauQubits + 63) / 64;
+constexpr int kMaxWh = (kMaxBodyQubits + 63) / 64;
 constexpr int kZOffStage = 257, kZWireStage = 1024;
 
 namespace {
@@ -813,7 +813,7 @@ __global__ void __launch_bounds__(256) screen_kernel(DevPlan P, DevRes R, EvalPa
       sp.flags = 0u;
     }
     __syncwarp();
-    if (E.mode == CCS_EXACT) {
+    if (E.mode == CCS_EXACT || (E.mode == CCS_STITCH && F.role != 1)) {
       const float pr = ldexpf(1.0f, -rank);
       float* d = R.dist + F.dist_off + ((long long)v << nA);
       if (rank == nA) {
@@ -1103,7 +1103,7 @@ __global__ void __launch_bounds__(512) clifford_kernel(DevPlan P, DevRes R, Eval
       for (int i = 0; i < kMaxMeas; ++i) sp.basis[i] = i < s_rank ? s_basis[i] : 0u;
       sp.flags = 0;
     }
-    if (E.mode == CCS_EXACT) {
+    if (E.mode == CCS_EXACT || (E.mode == CCS_STITCH && F.role != 1)) {
       const int rk = s_rank;
       const float pr = ldexpf(1.0f, -rk);
       float* d = R.dist + F.dist_off + ((long long)v << nA);
@@ -1482,6 +1482,45 @@ __global__ void __launch_bounds__(512) sample_hub_kernel(DevPlan P, DevRes R, Ev
   }
 }
 
+// The operand rows a hub variant v owns: its preparation digits at the input
+// slots, and at the output slots the Pauli its basis reads (X, Y), or I or Z
+// for a Z-basis output; one row per choice of I/Z (2^nz rows, bit i of the
+// row index = the i-th Z-basis output).  s_czD[row] = the row's Pauli index
+// D, s_czS[row] = its sign mask over the quantum-output bits (X/Y-basis
+// outputs always flip the sign, a Z-basis output where it reads Z).  zm =
+// the Z-basis outputs.  Called by every thread; threads < 2^nz write.
+__device__ __forceinline__ void hub_variant_rows(const FragDev& F, int v, int* s_czD, int* s_czS, int& nz, int& zm) {
+  int beta[kMaxCuts], zpos[kMaxCuts], zout[kMaxCuts];
+  int t = v;
+  for (int i = 0; i < F.qin; ++i) t /= 4;
+  for (int j = 0; j < F.qout; ++j) { beta[j] = t % 3; t /= 3; }
+  int Dbase = 0, fixed_mask = 0;
+  nz = 0;
+  zm = 0;
+  for (int j = 0; j < F.n_slots; ++j) {
+    const int code = F.slot_code[j], idx = code & 255;
+    if ((code >> 8) == 0) {
+      int u = v;
+      for (int i = 0; i < idx; ++i) u /= 4;
+      Dbase |= (u % 4) << (2 * j);
+    } else if (beta[idx] == 2) {
+      zpos[nz] = j;
+      zout[nz++] = idx;
+      zm |= 1 << idx;
+    } else {
+      Dbase |= (beta[idx] == 0 ? 1 : 2) << (2 * j);
+      fixed_mask |= 1 << idx;
+    }
+  }
+  if ((int)threadIdx.x < (1 << nz)) {
+    int D = Dbase, smask = fixed_mask;
+    for (int i = 0; i < nz; ++i)
+      if ((threadIdx.x >> i) & 1) { D |= 3 << (2 * zpos[i]); smask |= 1 << zout[i]; }
+    s_czD[threadIdx.x] = D;
+    s_czS[threadIdx.x] = smask;
+  }
+}
+
 // Readout of a byte-counter histogram into the variant's operand rows,
 // specialised on ZM, the quantum outputs measured in the Z basis.  Row cz
 // of the variant needs S(o, cz) = sum_b (-1)^(b . smask_cz) count(o, b) with
@@ -1582,37 +1621,9 @@ __global__ void __launch_bounds__(256) sample_hub8_kernel(DevPlan P, DevRes R, E
   const int rank = sp.rank;
   const uint32_t off = sp.off;
   build_tables(tbl, sp, rank);
-  // the variant's operand columns: one D and sign mask per Z-basis choice
-  int nz = 0, zm = 0;
-  {
-    int beta[kMaxCuts], zpos[kMaxCuts], zout[kMaxCuts];
-    int t = v;
-    for (int i = 0; i < F.qin; ++i) t /= 4;
-    for (int j = 0; j < F.qout; ++j) { beta[j] = t % 3; t /= 3; }
-    int Dbase = 0, fixed_mask = 0;
-    for (int j = 0; j < F.n_slots; ++j) {
-      const int code = F.slot_code[j], idx = code & 255;
-      if ((code >> 8) == 0) {
-        int u = v;
-        for (int i = 0; i < idx; ++i) u /= 4;
-        Dbase |= (u % 4) << (2 * j);
-      } else if (beta[idx] == 2) {
-        zpos[nz] = j;
-        zout[nz++] = idx;
-        zm |= 1 << idx;
-      } else {
-        Dbase |= (beta[idx] == 0 ? 1 : 2) << (2 * j);
-        fixed_mask |= 1 << idx;
-      }
-    }
-    if (tid < (1 << nz)) {
-      int D = Dbase, smask = fixed_mask;
-      for (int i = 0; i < nz; ++i)
-        if ((tid >> i) & 1) { D |= 3 << (2 * zpos[i]); smask |= 1 << zout[i]; }
-      s_czD[tid] = D;
-      s_czS[tid] = smask;
-    }
-  }
+  // the variant's operand rows: one D and sign mask per Z-basis choice
+  int nz, zm;
+  hub_variant_rows(F, v, s_czD, s_czS, nz, zm);
   const uint32_t cmask = rank >= 32 ? 0xffffffffu : ((1u << rank) - 1u);
   const float inv = (float)E.inv_shots;
   float* QT = R.TQ + F.T_off;
@@ -1696,6 +1707,88 @@ __global__ void __launch_bounds__(256) sample_hub8_kernel(DevPlan P, DevRes R, E
       }
     }
   }
+}
+
+// --- stitched mode: a Clifford hub's operand in closed form (Sec. IX) -------
+// A variant's outcomes y = (o, b) (o the marginal bits, b the quantum-output
+// bits) are uniform, probability 2^-r, on off + span(B), B in reduced
+// echelon form with pivot = lowest bit.  The vectors with pivot in b have no
+// o part: they span K = {b : (0, b) in span B}, 2^kb elements.  The others
+// project to an echelon basis of the o-projection.  For an output o in
+// off_o + that projection the b with (o, b) in the space form a coset
+// b0(o) + K, with b0(o) = off_b + the b parts of the vectors o's pivot bits
+// select; for other o there is none.  So row cz of the operand,
+//   Q(o, cz) = sum_b (-1)^(b . s_cz) p(o, b),
+// vanishes for every o unless s_cz is orthogonal to K, and is then
+// 2^(kb - r) (-1)^(b0(o) . s_cz) on the projection and 0 elsewhere: exact
+// in FP32, no shots, no per-variant distribution.  One CTA per hub variant
+// writes its rows' flags (1 unless identically zero) and its nonzero rows;
+// its zero rows only when the problem's contraction reads every row (the
+// streaming GEMM skips flagged rows).
+__global__ void __launch_bounds__(256) hub_exact_kernel(DevPlan P, DevRes R, const int2* items) {
+  __shared__ FragDev sF;
+  __shared__ int s_czD[16], s_czS[16], s_live[16];
+  __shared__ uint32_t s_vo[kMaxMeas], s_vb[kMaxMeas], s_kg[kMaxMeas];
+  __shared__ int s_piv[kMaxMeas], s_cnt[2];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int2 it = items[blockIdx.x];
+  {
+    const int* src = reinterpret_cast<const int*>(P.frags + it.x);
+    int* dst = reinterpret_cast<int*>(&sF);
+    for (int i = tid; i < (int)(sizeof(FragDev) / 4); i += nt) dst[i] = src[i];
+  }
+  __syncthreads();
+  const FragDev& F = sF;
+  const int v = it.y, m = F.m, M = 1 << m;
+  int nz, zm;
+  hub_variant_rows(F, v, s_czD, s_czS, nz, zm);
+  const SpaceRec& sp = R.spaces[F.space_off + v];
+  const int rank = sp.rank;
+  if (tid == 0) {
+    int ro = 0, kb = 0;
+    for (int j = 0; j < rank; ++j) {
+      const uint32_t vec = sp.basis[j];
+      const int p = __ffs((int)vec) - 1;
+      if (p < m) { s_vo[ro] = vec & (uint32_t)(M - 1); s_vb[ro] = vec >> m; s_piv[ro] = p; ++ro; }
+      else s_kg[kb++] = vec >> m;
+    }
+    s_cnt[0] = ro;
+    s_cnt[1] = kb;
+  }
+  __syncthreads();
+  const int ro = s_cnt[0], kb = s_cnt[1], nrows = 1 << nz;
+  if (tid < nrows) {
+    bool live = true;
+    for (int j = 0; j < kb; ++j) live = live && !(__popc(s_kg[j] & (uint32_t)s_czS[tid]) & 1);
+    s_live[tid] = live ? 1 : 0;
+    R.qnz[F.qrow_off + s_czD[tid]] = live ? 1 : 0;
+  }
+  __syncthreads();
+  const bool write_zero = P.problems[F.problem].stream == 0;
+  int any = write_zero ? 1 : 0;
+  for (int i = 0; i < nrows; ++i) any |= s_live[i];
+  if (!any) return;
+  const float c = ldexpf(1.0f, kb - rank);
+  const uint32_t off_o = sp.off & (uint32_t)(M - 1), off_b = sp.off >> m;
+  float* QT = R.TQ + F.T_off;
+  for (int o = tid; o < M; o += nt) {
+    const uint32_t y = (uint32_t)o ^ off_o;
+    uint32_t x = 0u, bb = off_b;
+    for (int t = 0; t < ro; ++t)
+      if ((y >> s_piv[t]) & 1u) { x ^= s_vo[t]; bb ^= s_vb[t]; }
+    const bool member = x == y;
+    for (int cz = 0; cz < nrows; ++cz) {
+      if (!s_live[cz] && !write_zero) continue;
+      const float val = (s_live[cz] && member) ? ((__popc(bb & (uint32_t)s_czS[cz]) & 1) ? -c : c) : 0.f;
+      QT[(long long)s_czD[cz] * M + o] = val;
+    }
+  }
+}
+
+cudaError_t launch_hub_exact(const DevPlan& p, const DevRes& r, const int2* items, int n_items, cudaStream_t s) {
+  if (n_items == 0) return cudaSuccess;
+  hub_exact_kernel<<<n_items, 256, 0, s>>>(p, r, items); note_launch();
+  return cudaGetLastError();
 }
 
 cudaError_t launch_sample_hub(const DevPlan& p, const DevRes& r, const EvalParams& e, const int2* items, int n_items,

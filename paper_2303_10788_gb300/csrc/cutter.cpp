@@ -316,7 +316,7 @@ double plan_cost(const Problem& p, const std::vector<ccs_cut>& cuts_in, bool* ok
   bool star = cuts.empty();
   for (int f = 0; f < nf; ++f) {
     if (!cliff[f] && wires[f] > kMaxNCWidth) return invalid();
-    if (cliff[f] && wires[f] > kMaxTableauQubits) return invalid();
+    if (cliff[f] && wires[f] > kMaxBodyQubits) return invalid();
     if (marg[f] + qout[f] > kMaxMeas) return invalid();
     if (qin[f] + qout[f] == (int)cuts.size()) star = true;
   }

@@ -33,6 +33,7 @@ struct FragDev {
   long long zimg_off;      // uint64 index of the Z images (nz + 3 qout + m records of 2 Wh + 1 words)
   long long pb_off;        // uint32 index of the projected shared-row bases, 25 words per output basis
                            // combination (3^qout of them), -1 when qout > kMaxPbQout
+  long long qrow_off;      // byte index of a Clifford hub's operand-row flags (4^n_slots), -1 otherwise
 };
 
 // Canonical affine outcome space of a Clifford variant.
@@ -58,6 +59,7 @@ struct ProblemDev {
   long long blk_off;       // first GEMM block of this problem
   long long rt_off;        // bf16 index of R'^T (N x K) in the bf16 scratch (tensor-core path)
   long long hub_T_off;     // T_off of the hub
+  long long hub_qrow_off;  // qrow_off of the hub (-1: not a Clifford hub)
   int tc;                  // 1: eligible for the tensor-core GEMM in BF16 mode
   int direct;              // 1: contracted leaf by leaf in shared memory, TM hub outputs per CTA
   int direct_staged;       // 1: the slice's hub operand (K x TM) is staged first; 0: the first leaf streams it
@@ -114,6 +116,7 @@ struct DevRes {
   uint16_t* TQh;           // bf16 copy of the hubs' Q (tensor-core path), may be null
   double* marg;
   double* zexp;
+  uint8_t* qnz;            // stitched results: per Clifford hub operand row, 1 unless identically zero
   unsigned int* work;         // persistent-kernel work counters
   unsigned int* status;       // device-side error word
 };
@@ -136,7 +139,7 @@ constexpr long long kDirectSmemFloats = 12288;
 __host__ __device__ inline int zblock_variants(int nz) { return nz >= 256 ? 1 : 256 / nz; }
 
 struct EvalParams {
-  int mode;                   // CCS_EXACT / CCS_SAMPLED
+  int mode;                   // CCS_EXACT / CCS_SAMPLED / CCS_STITCH
   uint32_t shots, seed_lo, seed_hi;
   int keep_tableaus;
   int shared_body;            // 1: variants start from their fragment's body tableau
@@ -174,6 +177,9 @@ cudaError_t launch_sample(const DevPlan& p, const DevRes& r, const EvalParams& e
 // (the byte-counter kernel applies)
 cudaError_t launch_sample_hub(const DevPlan& p, const DevRes& r, const EvalParams& e, const int2* items,
                               int n_items, int max_nA, int threads, int keep_counts, bool bytes_ok, cudaStream_t s);
+// Stitched mode: the contraction operand of Clifford hubs in closed form from
+// each variant's outcome space (one CTA per hub variant), with the row flags.
+cudaError_t launch_hub_exact(const DevPlan& p, const DevRes& r, const int2* items, int n_items, cudaStream_t s);
 cudaError_t launch_statevector(const DevPlan& p, const DevRes& r, int max_n, int threads,
                                int grid, cudaStream_t s);
 // A subset of fragments to fold: fidx[i] is the FragDev index of segment i;
@@ -194,6 +200,15 @@ cudaError_t launch_operands(const DevPlan& p, const DevRes& r, const EvalParams&
 // and scatter into marg_out (2^n_marg doubles per problem at marg_off), and
 // the Z-string contraction into zexp_out.  `scratch` holds R and the split-K
 // partials (r_total + part_total floats).
+// A range [lo, hi) of the cut index P summed by a partial contraction
+// (hi < 0: to the end); every problem clamps it to its own 4^k.
+struct KRange {
+  long long lo, hi;
+  __host__ __device__ long long lo_of(long long K) const { return lo < K ? lo : K; }
+  __host__ __device__ long long hi_of(long long K) const { return hi < 0 || hi > K ? K : hi; }
+  __host__ __device__ bool full() const { return lo == 0 && hi < 0; }
+};
+
 struct RecombSizes {
   long long r_total, part_total, gemm_blocks, out_total, z_total;
   const int2* direct_items;      // (problem, hub-output slice) contracted leaf by leaf, one CTA each
@@ -209,6 +224,9 @@ struct RecombSizes {
   int n_problems;
   uint16_t* rt_scratch;          // bf16 R'^T of problems eligible for the tensor-core GEMM
   int tensor_cores;              // 1: BF16 contractions of eligible problems on tcgen05
+  int stitched;                  // 1: Clifford hubs' operand rows flagged in DevRes::qnz (zero rows
+                                 //    of streamed problems are neither written nor read)
+  KRange krange;                 // the cut-index terms summed ({0, -1}: all)
 };
 cudaError_t launch_recombine(const DevPlan& p, const DevRes& r, int precision, const RecombSizes& z,
                              float* scratch, double* marg_out, double* zexp_out, cudaStream_t s);

@@ -405,7 +405,7 @@ int fragment_problem(Problem& p, int pi, std::vector<Frag>& out, std::string& er
   for (int fi = first; fi < (int)out.size(); ++fi) {
     Frag& f = out[fi];
     if (!f.clifford && f.n() > kMaxNCWidth) { err = "non-Clifford fragment too wide"; return CCS_ERR_NC_TOO_WIDE; }
-    if (f.clifford && f.n() > kMaxTableauQubits) { err = "Clifford fragment too wide"; return CCS_ERR_UNSUPPORTED; }
+    if (f.clifford && f.n() > kMaxBodyQubits) { err = "Clifford fragment too wide"; return CCS_ERR_UNSUPPORTED; }
     if (f.n_meas() > kMaxMeas) { err = "fragment measures too many wires"; return CCS_ERR_UNSUPPORTED; }
     p.frag_ids.push_back(fi);
   }

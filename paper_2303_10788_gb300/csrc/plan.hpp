@@ -17,7 +17,11 @@ namespace ccs {
 // Limits of the device kernels.
 constexpr int kMaxMeas = 24;        // |A_f|: dense 2^|A_f| outcome tables
 constexpr int kMaxNCWidth = 12;     // complex64 statevector of 2^12 amplitudes in smem
-constexpr int kMaxTableauQubits = 640;  // (2n+3) x 2*ceil(n/64) words fit 227 KB of smem
+constexpr int kMaxTableauQubits = 640;  // per-variant tableaus: (2n+3) x 2*ceil(n/64) words fit 227 KB of smem
+// Clifford fragments on the shared-body path (the default: one body per
+// fragment, kept in global memory, one 64-row word per column in a CTA's
+// shared memory; no per-variant tableau): a warp covers its 2*ceil(n/64) words.
+constexpr int kMaxBodyQubits = 1024;
 constexpr int kMaxCuts = 12;
 constexpr int kMaxMarginal = 24;
 // Circuit size accepted at the ABI (host arrays are linear in both).

@@ -234,7 +234,7 @@ cudaError_t launch_operands(const DevPlan& p, const DevRes& r, const EvalParams&
 // bf16 (as a bf16 tensor-core GEMM would) with FP32 accumulation.
 
 __global__ void build_r_kernel(DevPlan P, DevRes R, int precision, const long long* prefix, int np,
-                               long long total, float* scratch, uint16_t* rt_scratch) {
+                               long long total, float* scratch, uint16_t* rt_scratch, int stitched) {
   for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
        g += (long long)gridDim.x * blockDim.x) {
     const int pi = find_seg(prefix, np, g);
@@ -242,6 +242,8 @@ __global__ void build_r_kernel(DevPlan P, DevRes R, int precision, const long lo
     const long long loc = g - prefix[pi];
     const long long Pp = loc / Pb.N;
     const long long ol = loc - Pp * Pb.N;
+    // a streamed stitched hub reads no R row of a zero operand row
+    if (stitched && Pb.stream && Pb.hub_qrow_off >= 0 && !R.qnz[Pb.hub_qrow_off + Pp]) continue;
     float v = 1.f;
     int off = 0;
     for (int l = 0; l < Pb.n_frags; ++l) {
@@ -267,7 +269,8 @@ constexpr int kTK = 16;
 // each k step is two float4 reads and 16 FMAs.
 __global__ void __launch_bounds__(256) gemm_splitk_kernel(DevPlan P, DevRes R, int precision,
                                                           const long long* blk_prefix, int np,
-                                                          long long total_blocks, float* scratch, int skip_tc) {
+                                                          long long total_blocks, float* scratch, int skip_tc,
+                                                          KRange kr) {
   extern __shared__ __align__(16) float sm[];
   for (long long b = blockIdx.x; b < total_blocks; b += gridDim.x) {
     const int pi = find_seg(blk_prefix, np, b);
@@ -281,7 +284,8 @@ __global__ void __launch_bounds__(256) gemm_splitk_kernel(DevPlan P, DevRes R, i
     const int TM = Pb.TM, TN = Pb.TN, M = Pb.M, N = Pb.N;
     const long long K = Pb.K;
     const long long kchunk = (K + Pb.splits - 1) / Pb.splits;
-    const long long k0 = split * kchunk, k1 = k0 + kchunk < K ? k0 + kchunk : K;
+    const long long s0 = split * kchunk;     // this split's terms within the requested range
+    const long long k0 = max(s0, kr.lo_of(K)), k1 = min(min(s0 + kchunk, K), kr.hi_of(K));
     float* As = sm;                  // kTK x TM
     float* Bs = sm + kTK * TM;       // kTK x TN
     const float* At = R.TQ + Hb.T_off;       // the hub's Q stored transposed: K x M, row-major
@@ -371,10 +375,13 @@ __device__ __forceinline__ void stream_fma(float (&acc)[4][NN], float4 a, const 
 template <int NN>
 __global__ void __launch_bounds__(256, 2) gemm_stream_kernel(const float* __restrict__ At, const float* __restrict__ Rm,
                                                              int M, long long K, long long kchunk, int mblocks,
-                                                             float* __restrict__ part, int bf16) {
+                                                             float* __restrict__ part, int bf16,
+                                                             const uint8_t* __restrict__ live, KRange kr) {
   __shared__ __align__(16) float Rs[kStreamChunk * NN];
+  __shared__ __align__(8) uint8_t Ls[kStreamChunk];     // row flags of the chunk (stitched operands)
   const int mb = blockIdx.x % mblocks, split = blockIdx.x / mblocks;
-  const long long k0 = (long long)split * kchunk, k1 = min(K, k0 + kchunk);
+  const long long s0 = (long long)split * kchunk;     // this split's rows within the requested range
+  const long long k0 = max(s0, kr.lo_of(K)), k1 = min(min(K, s0 + kchunk), kr.hi_of(K));
   const int m = 4 * (mb * (int)blockDim.x + (int)threadIdx.x);
   const bool act = m < M;
   float acc[4][NN];
@@ -385,12 +392,25 @@ __global__ void __launch_bounds__(256, 2) gemm_stream_kernel(const float* __rest
   for (long long kc = k0; kc < k1; kc += kStreamChunk) {
     const int rows = (int)min((long long)kStreamChunk, k1 - kc);
     __syncthreads();                       // the previous chunk's rows are consumed
-    for (int i = threadIdx.x; i < rows * NN; i += blockDim.x) Rs[i] = Rm[kc * NN + i];
+    if (live)
+      for (int i = threadIdx.x; i < kStreamChunk; i += blockDim.x) Ls[i] = i < rows ? live[kc + i] : 0;
+    for (int i = threadIdx.x; i < rows * NN; i += blockDim.x)
+      if (!live || live[kc + i / NN]) Rs[i] = Rm[kc * NN + i];
     __syncthreads();
     if (!act) continue;
     const float* ap = At + kc * M + m;
     int r = 0;
     for (; r + 8 <= rows; r += 8) {
+      if (live) {        // rows flagged zero are skipped (they may never have been written)
+        const unsigned long long l8 = *reinterpret_cast<const unsigned long long*>(Ls + r);
+        if (!l8) continue;
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if ((l8 >> (8 * u)) & 0xffull)
+            stream_fma<NN>(acc, __ldcs(reinterpret_cast<const float4*>(ap + (long long)(r + u) * M)),
+                           Rs + (r + u) * NN, bf16);
+        continue;
+      }
       float4 a[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) a[u] = __ldcs(reinterpret_cast<const float4*>(ap + (long long)(r + u) * M));
@@ -398,7 +418,8 @@ __global__ void __launch_bounds__(256, 2) gemm_stream_kernel(const float* __rest
       for (int u = 0; u < 8; ++u) stream_fma<NN>(acc, a[u], Rs + (r + u) * NN, bf16);
     }
     for (; r < rows; ++r)
-      stream_fma<NN>(acc, __ldcs(reinterpret_cast<const float4*>(ap + (long long)r * M)), Rs + r * NN, bf16);
+      if (!live || Ls[r])
+        stream_fma<NN>(acc, __ldcs(reinterpret_cast<const float4*>(ap + (long long)r * M)), Rs + r * NN, bf16);
   }
   if (!act) return;
   float* dst = part + ((long long)split * M + m) * NN;    // 4 x NN contiguous floats
@@ -410,26 +431,28 @@ __global__ void __launch_bounds__(256, 2) gemm_stream_kernel(const float* __rest
 
 template <int NN>
 static cudaError_t launch_stream_nn(const float* At, const float* Rm, const ProblemDev& Pb, float* part, int bf16,
-                                    cudaStream_t s) {
+                                    const uint8_t* live, KRange kr, cudaStream_t s) {
   long long kchunk = (Pb.K + Pb.ssplits - 1) / Pb.ssplits;
   kchunk = (kchunk + 7) & ~7ll;
   const long long splits = (Pb.K + kchunk - 1) / kchunk;    // every split but the last is full
   gemm_stream_kernel<NN><<<(unsigned)(Pb.smblocks * splits), Pb.sthreads, 0, s>>>(At, Rm, Pb.M, Pb.K, kchunk,
-                                                                                  Pb.smblocks, part, bf16);
+                                                                                  Pb.smblocks, part, bf16, live, kr);
   note_launch();
   return cudaGetLastError();
 }
 
-static cudaError_t launch_stream(const DevRes& r, const ProblemDev& Pb, float* scratch, int bf16, cudaStream_t s) {
+static cudaError_t launch_stream(const DevRes& r, const ProblemDev& Pb, float* scratch, int bf16, int stitched,
+                                 KRange kr, cudaStream_t s) {
   const float* At = r.TQ + Pb.hub_T_off;
   const float* Rm = scratch + Pb.r_off;
   float* part = scratch + Pb.part_off;
+  const uint8_t* live = (stitched && Pb.hub_qrow_off >= 0) ? r.qnz + Pb.hub_qrow_off : nullptr;
   switch (Pb.N) {
-    case 1: return launch_stream_nn<1>(At, Rm, Pb, part, bf16, s);
-    case 2: return launch_stream_nn<2>(At, Rm, Pb, part, bf16, s);
-    case 4: return launch_stream_nn<4>(At, Rm, Pb, part, bf16, s);
-    case 8: return launch_stream_nn<8>(At, Rm, Pb, part, bf16, s);
-    case 16: return launch_stream_nn<16>(At, Rm, Pb, part, bf16, s);
+    case 1: return launch_stream_nn<1>(At, Rm, Pb, part, bf16, live, kr, s);
+    case 2: return launch_stream_nn<2>(At, Rm, Pb, part, bf16, live, kr, s);
+    case 4: return launch_stream_nn<4>(At, Rm, Pb, part, bf16, live, kr, s);
+    case 8: return launch_stream_nn<8>(At, Rm, Pb, part, bf16, live, kr, s);
+    case 16: return launch_stream_nn<16>(At, Rm, Pb, part, bf16, live, kr, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -555,7 +578,7 @@ __device__ float fold_z_value(const DevRes& R, const FragDev& F, int zi, int Pi)
 // FP32 products, FP64 sums, fixed-order tree reduction; T_f^S is folded from
 // the variants' Z values here (no separate fold pass).
 __device__ void z_string_block(const DevPlan& P, const DevRes& R, const long long* prefix, int np, long long g,
-                               ProblemShared& S, double* red, float* s_tz, int tz_cap, double* zexp_out) {
+                               ProblemShared& S, double* red, float* s_tz, int tz_cap, double* zexp_out, KRange kr) {
   const int pi = find_seg(prefix, np, g);
   const ProblemDev& Pb = P.problems[pi];
   const int zi = (int)(g - prefix[pi]);
@@ -575,7 +598,7 @@ __device__ void z_string_block(const DevPlan& P, const DevRes& R, const long lon
   }
   const long long K = 1ll << (2 * S.k);
   double part = 0.0;
-  for (long long Pp = threadIdx.x; Pp < K; Pp += blockDim.x) {
+  for (long long Pp = kr.lo_of(K) + threadIdx.x; Pp < kr.hi_of(K); Pp += blockDim.x) {
     float t = 1.f;
     int o = 0;
     for (int l = 0; l < S.nf; ++l) {
@@ -612,14 +635,14 @@ __device__ void z_string_block(const DevPlan& P, const DevRes& R, const long lon
 __global__ void __launch_bounds__(512) contract_kernel(DevPlan P, DevRes R, int precision,
                                                       const int2* direct_items, int n_direct, int stage_floats,
                                                       const long long* z_prefix, int np, long long z_total,
-                                                      double* marg_out, double* zexp_out) {
+                                                      double* marg_out, double* zexp_out, KRange krg) {
   extern __shared__ __align__(16) float s_buf[];   // two buffers of stage_floats
   __shared__ double red[512];
   __shared__ ProblemShared S;
   __shared__ float s_T[kLeafStage];
   for (long long b = blockIdx.x; b < n_direct + z_total; b += gridDim.x) {
     if (b >= n_direct) {
-      z_string_block(P, R, z_prefix, np, b - n_direct, S, red, s_T, kLeafStage, zexp_out);
+      z_string_block(P, R, z_prefix, np, b - n_direct, S, red, s_T, kLeafStage, zexp_out, krg);
       __syncthreads();
       continue;
     }
@@ -628,6 +651,7 @@ __global__ void __launch_bounds__(512) contract_kernel(DevPlan P, DevRes R, int 
     const int M = Pb.TM, lm = __ffs(M) - 1;      // this block's hub outputs; extents are powers of two
     const int m0 = di.y * M, Mfull = Pb.M;
     const int K = (int)Pb.K;
+    const long long klo = krg.lo_of(K), khi = krg.hi_of(K);   // cut-index terms summed
     const float* At = R.TQ + Pb.hub_T_off + m0;  // the hub's Q stored transposed: K x Mfull, row-major
     load_problem(P, Pb, S);
     __syncthreads();
@@ -655,7 +679,10 @@ __global__ void __launch_bounds__(512) contract_kernel(DevPlan P, DevRes R, int 
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           const int t = t0 + u * blockDim.x;
-          if (t < K * M) v[u] = At[(long long)expand(t >> lm, 0) * Mfull + (t & (M - 1))];
+          if (t < K * M) {
+            const long long kk = expand(t >> lm, 0);
+            v[u] = (kk >= klo && kk < khi) ? At[kk * Mfull + (t & (M - 1))] : 0.f;
+          }
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
@@ -694,7 +721,8 @@ __global__ void __launch_bounds__(512) contract_kernel(DevPlan P, DevRes R, int 
               const int g = g0 + u;
               int kg = 0;
               for (int i = 0; i < S.ns[l]; ++i) kg |= ((g >> (2 * i)) & 3) << (2 * S.slot_cut[l][i]);
-              a[u] = g < G ? At[(long long)(kr | kg) * Mfull + outer] : 0.f;
+              const long long kk = (long long)(kr | kg);
+              a[u] = (g < G && kk >= klo && kk < khi) ? At[kk * Mfull + outer] : 0.f;
             }
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
@@ -780,10 +808,11 @@ cudaError_t launch_recombine(const DevPlan& p, const DevRes& r, int precision, c
   };
   cudaError_t err = cudaSuccess;
   if (z.out_total > 0 && z.chain) {
-    const bool use_tc = precision == CCS_BF16 && z.tensor_cores && z.rt_scratch && r.TQh;
+    const bool use_tc = precision == CCS_BF16 && z.tensor_cores && z.rt_scratch && r.TQh && z.krange.full();
     if (z.r_total > 0) {
       build_r_kernel<<<grid(z.r_total, 256), 256, 0, s>>>(p, r, precision, z.r_prefix, p.n_problems, z.r_total,
-                                                          scratch, use_tc ? z.rt_scratch : nullptr); note_launch();
+                                                          scratch, use_tc ? z.rt_scratch : nullptr, z.stitched);
+      note_launch();
       if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
     if (z.gemm_blocks > 0) {
@@ -793,13 +822,15 @@ cudaError_t launch_recombine(const DevPlan& p, const DevRes& r, int precision, c
       }
       gemm_splitk_kernel<<<(unsigned)(z.gemm_blocks < 65535ll * 16 ? z.gemm_blocks : 65535ll * 16), 256,
                            z.max_tile_smem, s>>>(p, r, precision, z.blk_prefix, p.n_problems, z.gemm_blocks, scratch,
-                                                 use_tc ? 1 : 0); note_launch();
+                                                 use_tc ? 1 : 0, z.krange); note_launch();
       if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
     for (int i = 0; i < z.n_problems; ++i) {     // wide hubs off the tensor cores: streaming GEMM
       const ProblemDev& Pb = z.host_problems[i];
       if (!Pb.stream || Pb.direct || (use_tc && Pb.tc)) continue;
-      if ((err = launch_stream(r, Pb, scratch, precision == CCS_BF16 ? 1 : 0, s)) != cudaSuccess) return err;
+      if ((err = launch_stream(r, Pb, scratch, precision == CCS_BF16 ? 1 : 0, z.stitched, z.krange, s)) !=
+          cudaSuccess)
+        return err;
     }
     if (use_tc) {
       for (int i = 0; i < z.n_problems; ++i) {
@@ -831,7 +862,7 @@ cudaError_t launch_recombine(const DevPlan& p, const DevRes& r, int precision, c
     }
     contract_kernel<<<(unsigned)(blocks < 65535ll * 16 ? blocks : 65535ll * 16), 512, smem, s>>>(
         p, r, precision, z.direct_items, z.n_direct, z.direct_stage_floats, z.z_prefix, p.n_problems, z.z_total,
-        marg_out, zexp_out);
+        marg_out, zexp_out, z.krange);
     note_launch();
     err = cudaGetLastError();
   }

@@ -8,6 +8,12 @@ with these values; nothing here reads the library.
 
     python tests/golden/make_golden.py config3 [--procs 8]
     python tests/golden/make_golden.py config4 [--procs 8] [--circuits 0,1,...]
+    python tests/golden/make_golden.py exact [--procs 8]
+
+``exact`` (after the two above) writes the exact-mode marginals (strong
+simulation, Sec. V-C: each Clifford variant's distribution is 2^-rank on its
+outcome space) of the same circuits from the stored oracle outcome spaces,
+so no tableau is simulated again.
 
 config3 (500-qubit body, 20736 variants, 2^14 shots, 4^8 cut terms) takes
 about 5 CPU-hours; it is spread over ``--procs`` spawned processes.  Each
@@ -169,13 +175,83 @@ def make_config4(procs, circuits):
     print("wrote", out)
 
 
+# --- exact mode from the stored outcome spaces -----------------------------------
+
+def _exact_dist(row, nbits):
+    from oracle import tableau as tb
+    rank, off = int(row[0]), int(row[1])
+    return tb.exact_distribution(off, [int(b) for b in row[2:2 + rank]], nbits)
+
+
+def _c3_exact_block(b_idx):
+    from oracle.cutting import BETA, fold_columns, pauli_digits
+    w, frags, _, body = _c3_setup()
+    f = frags[body]
+    nin = 4 ** len(f.qin)
+    beta = f.variant_digits(b_idx * nin)[1]
+    sp = np.load(os.path.join(HERE, "config3_sampled.npz"))["spaces"]
+    dists = {v: _exact_dist(sp[v], len(f.A)) for v in range(b_idx * nin, (b_idx + 1) * nin)}
+    Ps = [P for P in range(4 ** len(f.slots))
+          if [BETA[p] for p in pauli_digits(f, P)[1]] == beta]
+    return Ps, fold_columns(f, Ps, lambda v: dists[v])
+
+
+def _c4_exact_one(ci):
+    from workloads import config4
+    from oracle import statevector as sv
+    from oracle.cutting import fragment_circuit, fold, recombine
+    w = config4(256)[ci]
+    frags, cuts = fragment_circuit(w.circuit, w.cuts, w.marginal)
+    rows = np.load(os.path.join(HERE, "config4_sampled.npz"))[f"spaces_{ci}"]
+    by = {(int(r[0]), int(r[1])): r[2:] for r in rows}
+    tensors = []
+    for fi, fr in enumerate(frags):
+        if fr.clifford:
+            dists = [_exact_dist(by[(fi, v)], len(fr.A)) for v in range(fr.n_variants)]
+        else:
+            dists = [sv.marginal(sv.run(fr.n, fr.variant_gates(v)), fr.n, fr.A) for v in range(fr.n_variants)]
+        tensors.append(fold(fr, dists))
+    return ci, recombine(frags, tensors, len(cuts), len(w.marginal))
+
+
+def make_exact(procs):
+    from oracle import statevector as sv
+    from oracle.cutting import fold, recombine
+    t0 = time.time()
+    w, frags, cuts, body = _c3_setup()
+    f = frags[body]
+    tensors = [None if fi == body else
+               fold(fr, [sv.marginal(sv.run(fr.n, fr.variant_gates(v)), fr.n, fr.A) for v in range(fr.n_variants)])
+               for fi, fr in enumerate(frags)]
+    Tb = np.zeros((1 << len(f.marg), 4 ** len(f.slots)))
+    g4 = np.load(os.path.join(HERE, "config4_sampled.npz"))
+    circuits = [int(c) for c in g4["circuits"]]
+    m4 = {}
+    with mp.get_context("spawn").Pool(procs) as pool:
+        r4 = pool.map_async(_c4_exact_one, circuits)
+        for Ps, cols in pool.imap_unordered(_c3_exact_block, range(3 ** len(f.qout))):
+            Tb[:, Ps] = cols
+        print(f"config3 blocks: {time.time() - t0:.0f} s", flush=True)
+        for ci, m in r4.get():
+            m4[ci] = m
+    tensors[body] = Tb
+    m3 = recombine(frags, tensors, len(cuts), len(w.marginal))
+    print(f"config3 recombined: {time.time() - t0:.0f} s; sum {m3.sum():.9f}", flush=True)
+    out = os.path.join(HERE, "exact_marginals.npz")
+    np.savez_compressed(out, config3=m3, config4_circuits=np.array(circuits, np.int64),
+                        config4=np.stack([m4[c] for c in circuits]))
+    print("wrote", out)
+
+
 if __name__ == "__main__":
     ap = argparse.ArgumentParser()
-    ap.add_argument("which", choices=["config3", "config4"])
+    ap.add_argument("which", choices=["config3", "config4", "exact"])
     ap.add_argument("--procs", type=int, default=os.cpu_count() or 1)
     ap.add_argument("--circuits", default="0,1,2,3,4,5,6,7")
     a = ap.parse_args()
     if a.which == "config3":
         make_config3(a.procs, out=os.path.join(HERE, "config3_sampled.npz"))
-    else:
+    elif a.which == "config4":
         make_config4(a.procs, [int(c) for c in a.circuits.split(",")])
+    else:
+        make_exact(a.procs)

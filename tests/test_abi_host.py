@@ -130,8 +130,8 @@ def test_error_codes(hctx):
     for _ in range(14):
         many.add(CX, 0, 1)
     _expect(hctx, [_P(many, [(0, i) for i in range(1, 14)], [0])], "TOO_MANY_CUTS")
-    chain = Circuit(641)                                            # Clifford tableau wider than 640 wires
-    for q in range(640):
+    chain = Circuit(1025)                                           # Clifford fragment wider than 1024 wires
+    for q in range(1024):
         chain.add(CX, q, q + 1)
     _expect(hctx, [_P(chain, [], [0])], "UNSUPPORTED")
     _expect(hctx, [_P(chain, [], list(range(25)))], "INVALID_ARG")  # marginal wider than 24 qubits
