@@ -370,7 +370,7 @@ def _ncu_traffic(kernel, workload):
     return None
 
 
-STAGE_KERNEL = {"sample": "sample_hub8_kernel", "recombine": "gemm_stream_kernel", "clifford": "body_basis_kernel"}
+STAGE_KERNEL = {"sample": "sample_hub8_kernel", "recombine": "gemm_stream_bulk_kernel", "clifford": "body_basis_kernel"}
 
 
 def stage_kernel(st, precision):
@@ -582,7 +582,8 @@ def run_ours(args, rank, world, local_rank):
                        "recombination": args.precision + (" (tcgen05 where eligible)" if args.precision == "bf16" else
                                                           " (CUDA-core FMA, FP64 across splits)"),
                        "tuning": {"threads": tuning[0], "words_per_op": tuning[1], "shots_per_cta": tuning[2],
-                                  "hub_threads": tuning[3], "autotuned": tune}},
+                                  "hub_threads": abs(tuning[3]),
+                                  "hub_counters": "8-bit" if tuning[3] < 0 else "16-bit", "autotuned": tune}},
             "circuits_per_s": world * len(ws) * args.steps / t_tot,
             "stage_ms": stage, "roofline": roof, "stage_roofline": roofs,
             "e2e": {"value": units_per_step * world / e2e_s, "unit": UNIT, "circuits_per_s": world * len(ws) / e2e_s,

@@ -200,8 +200,9 @@ typedef struct {
                               every variant from it (same tableaus bit for bit) */
   int32_t hub_sampler;     /* star hubs' sampler: 0 automatic (or autotuned), 1 16-bit
                               counters, 2 byte counters with an exact 16-bit recount where
-                              a byte could overflow (used only if every hub has >= 2
-                              marginal bits, <= 4 quantum outputs, |A| <= 16); same counts */
+                              a byte could overflow, 256 threads per CTA, 3 the same with 512
+                              (2 and 3 used only if every hub has >= 2 marginal bits, <= 4
+                              quantum outputs, |A| <= 16); same counts */
 } ccs_eval_opts;
 
 /* Evaluate every variant of every fragment of the plan on the GPU: tableau
@@ -222,7 +223,8 @@ int ccs_eval_variants(ccs_ctx ctx, ccs_plan plan, const ccs_eval_opts* opts, ccs
 void ccs_res_free(ccs_res res);
 /* Launch shape in use for a result (after autotuning, if any): threads per
  * tableau CTA, 64-row words of one fused op per thread, shots per sampling
- * CTA, threads per fused hub-sampler CTA.  Any output may be NULL. */
+ * CTA, threads per fused hub-sampler CTA (negative: the byte-counter
+ * sampler with that many threads).  Any output may be NULL. */
 int ccs_get_tuning(ccs_ctx ctx, ccs_res res, int* cliff_threads, int* words_per_op, int* shots_per_cta,
                    int* hub_threads);
 

@@ -270,8 +270,8 @@ struct ccs_res_s {
   int cliff_threads = 256;
   int cliff_words = 1;        // words per op per thread in the tableau kernel
   int sample_spc = 4096;
-  int hub_threads = 512;      // threads of the fused hub sampler CTA (16-bit counters)
-  bool hub_bytes = false;     // use the byte-counter hub sampler (256 threads, two CTAs per SM)
+  int hub_threads = 512;      // threads of the fused hub sampler CTA (either counter width)
+  bool hub_bytes = false;     // use the byte-counter hub sampler (64 KB of counters at |A| = 16)
   float* scratch = nullptr;   // recombination: R operand + split-K partials
   uint16_t* rt_scratch = nullptr;   // bf16 R'^T of tensor-core-eligible problems
   ~ccs_res_s() {
@@ -1055,7 +1055,8 @@ static int autotune(ccs_ctx c, ccs_plan p, ccs_res r) {
   auto it = c->tuned.find(key);
   if (it != c->tuned.end()) {
     std::tie(r->cliff_threads, r->cliff_words, r->sample_spc, r->hub_threads) = it->second;
-    r->hub_bytes = r->hub_threads == 256;
+    r->hub_bytes = r->hub_threads < 0;       // cached as minus the threads of the byte-counter kernel
+    r->hub_threads = std::abs(r->hub_threads);
     return CCS_OK;
   }
   cudaEvent_t e0, e1;
@@ -1077,7 +1078,7 @@ static int autotune(ccs_ctx c, ccs_plan p, ccs_res r) {
   const int threads_c[] = {128, 256, 512};
   const int words_c[] = {1, 2, 4, 8};
   const int spc_c[] = {1024, 2048, 4096, 8192};
-  const int hub_c[] = {128, 512, 256};      // 256: the byte-counter kernel
+  const int hub_c[] = {128, 512, 256, 512};  // 16-bit counters, then byte counters
   const int max_w = 2 * ((max_n + 63) / 64);
   const bool sampled = r->ep.mode == CCS_SAMPLED;
   int rc = CCS_OK;
@@ -1101,18 +1102,19 @@ static int autotune(ccs_ctx c, ccs_plan p, ccs_res r) {
   }
   r->sample_spc = bs;
   bool bb = r->hub_bytes;
-  for (int hi = 0; sampled && p->n_items_hub && hi < 3 && rc == CCS_OK; ++hi) {
-    if (hi == 2 && !p->hub_bytes_ok) continue;
-    r->hub_bytes = hi == 2;
+  for (int hi = 0; sampled && p->n_items_hub && hi < 4 && rc == CCS_OK; ++hi) {
+    const bool bytes = hi >= 2;
+    if (bytes && !p->hub_bytes_ok) continue;
+    r->hub_bytes = bytes;
     r->hub_threads = hub_c[hi];
-    if ((rc = time_it(&ms)) == CCS_OK && ms < best) { best = ms; bh = hub_c[hi]; bb = hi == 2; }
+    if ((rc = time_it(&ms)) == CCS_OK && ms < best) { best = ms; bh = hub_c[hi]; bb = bytes; }
   }
   r->hub_threads = bh;
   r->hub_bytes = bb;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc != CCS_OK) return rc;
-  c->tuned[key] = std::make_tuple(bt, bw, bs, bh);
+  c->tuned[key] = std::make_tuple(bt, bw, bs, bb ? -bh : bh);
   return CCS_OK;
 }
 
@@ -1120,7 +1122,7 @@ int ccs_get_tuning(ccs_ctx c, ccs_res r, int* cliff_threads, int* words_per_op, 
                    int* hub_threads) {
   return abi_guard([&](int code, const char* m) { return fail(c, code, m); }, [&]() -> int {
     if (!c || !r) return fail(c, CCS_ERR_INVALID_ARG, "bad arguments");
-    if (hub_threads) *hub_threads = (r->hub_bytes && r->plan->hub_bytes_ok) ? 256 : r->hub_threads;
+    if (hub_threads) *hub_threads = (r->hub_bytes && r->plan->hub_bytes_ok) ? -r->hub_threads : r->hub_threads;
     if (cliff_threads) *cliff_threads = r->cliff_threads;
     if (words_per_op) *words_per_op = r->ep.shared_body ? 1 : r->cliff_words;
     if (shots_per_cta) *shots_per_cta = r->sample_spc;
@@ -1180,8 +1182,8 @@ int ccs_eval_variants(ccs_ctx c, ccs_plan p, const ccs_eval_opts* opts, ccs_res*
         r->cliff_threads = max_n > 256 ? 512 : 256;
         // small hub CTAs when a variant has few shots and few outputs (more CTAs per SM);
         // byte counters when the histogram would otherwise fill an SM's shared memory
-        r->hub_threads = (p->max_hub_nA <= 12 && opts->shots <= 4096) ? 128 : 512;
         r->hub_bytes = p->hub_bytes_ok && p->max_hub_nA >= 13;
+        r->hub_threads = r->hub_bytes ? 256 : (p->max_hub_nA <= 12 && opts->shots <= 4096) ? 128 : 512;
       }
       if (p->rt_total) {
         d.TQh = r->A.get<uint16_t>(p->n_T);
@@ -1231,10 +1233,16 @@ int ccs_eval_variants(ccs_ctx c, ccs_plan p, const ccs_eval_opts* opts, ccs_res*
     e.keep_tableaus = opts->keep_tableaus && r->have_tabs;
     e.shared_body = opts->per_variant_body ? 0 : 1;
     e.screen = e.shared_body && p->dp.n_cliff_frags > 0 && !e.keep_tableaus;
-    if (opts->hub_sampler < 0 || opts->hub_sampler > 2) return fail(c, CCS_ERR_INVALID_ARG, "bad hub sampler");
+    if (opts->hub_sampler < 0 || opts->hub_sampler > 3) return fail(c, CCS_ERR_INVALID_ARG, "bad hub sampler");
     e.hub_sampler = opts->hub_sampler;
-    if (opts->hub_sampler == 1) r->hub_bytes = false;
-    if (opts->hub_sampler == 2) r->hub_bytes = p->hub_bytes_ok;
+    if (opts->hub_sampler == 1) {
+      r->hub_bytes = false;
+      if (r->hub_threads != 128) r->hub_threads = 512;
+    }
+    if (opts->hub_sampler >= 2) {
+      r->hub_bytes = p->hub_bytes_ok;
+      r->hub_threads = opts->hub_sampler == 3 ? 512 : 256;
+    }
     e.inv_shots = e.shots ? 1.0 / (double)e.shots : 0.0;
     r->ep = e;
     if (opts->autotune && !r->graph && opts->hub_sampler == 0) {

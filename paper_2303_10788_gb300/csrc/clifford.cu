@@ -1599,8 +1599,8 @@ __device__ __forceinline__ unsigned hub8_readout(const uint32_t* __restrict__ h3
 // carries at most 1 into the next), is counted again with 16-bit counters
 // in two passes, each over the outputs o of one half (top marginal bit),
 // and its operand rows are rewritten.
-__global__ void __launch_bounds__(256) sample_hub8_kernel(DevPlan P, DevRes R, EvalParams E, const int2* items,
-                                                          int keep_counts, int hist_words) {
+__global__ void __launch_bounds__(512, 2) sample_hub8_kernel(DevPlan P, DevRes R, EvalParams E, const int2* items,
+                                                             int keep_counts, int hist_words) {
   extern __shared__ __align__(16) uint32_t h32[];
   __shared__ uint32_t tbl[3][256];
   __shared__ FragDev sF;
@@ -1794,12 +1794,13 @@ cudaError_t launch_hub_exact(const DevPlan& p, const DevRes& r, const int2* item
 cudaError_t launch_sample_hub(const DevPlan& p, const DevRes& r, const EvalParams& e, const int2* items, int n_items,
                               int max_nA, int threads, int keep_counts, bool bytes_ok, cudaStream_t s) {
   if (n_items == 0 || e.shots == 0) return cudaSuccess;
-  if (bytes_ok && e.shots <= 0xffffu && max_nA >= 2 && max_nA <= 16) {   // byte counters, 256 threads
+  if (bytes_ok && e.shots <= 0xffffu && max_nA >= 2 && max_nA <= 16) {   // byte counters, 256 or 512 threads
+    const int t8 = threads >= 512 ? 512 : 256;
     const int hist_words = (1 << max_nA) / 4;
-    const size_t smem = (size_t)4 * hist_words + (size_t)256 * (e.shots <= 32767u ? 0 : 33) * 4;
+    const size_t smem = (size_t)4 * hist_words + (size_t)t8 * (e.shots <= 32767u ? 0 : 33) * 4;
     cudaError_t err = cudaFuncSetAttribute(sample_hub8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    sample_hub8_kernel<<<n_items, 256, smem, s>>>(p, r, e, items, keep_counts, hist_words); note_launch();
+    sample_hub8_kernel<<<n_items, t8, smem, s>>>(p, r, e, items, keep_counts, hist_words); note_launch();
     return cudaGetLastError();
   }
   const int wide = e.shots > 0xffffu ? 1 : 0;     // 32-bit counters when 16 bits could overflow

@@ -429,14 +429,148 @@ __global__ void __launch_bounds__(256, 2) gemm_stream_kernel(const float* __rest
     for (int j = 0; j < NN; ++j) dst[i * NN + j] = acc[i][j];
 }
 
+// The same split-K product for dense operands with the loads moved off the
+// threads: one producer lane streams the CTA's slice of each Q^T row
+// (blockDim' x 16 bytes, contiguous) and the R rows of a stage into a
+// shared-memory ring with cp.async.bulk (the TMA engine), completing on the
+// stage's mbarrier; the consumer warps wait for a stage, take their float4
+// of each row from shared memory (conflict-free) and release the stage.
+// Every wait is bounded by a clock budget: on expiry the kernel sets status
+// bit 8, stops issuing, waits (bounded) for its copies in flight and writes
+// zero partials.
+constexpr int kBulkRows = 8, kBulkStages = 3;
+constexpr unsigned long long kBulkWaitBudget = 2000000000ull;   // ~1 s of SM clocks
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool bulk_wait(uint64_t* bar, uint32_t phase) {
+  const unsigned long long t0 = clock64();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > kBulkWaitBudget) return false;
+  }
+}
+
+template <int NN>
+__global__ void __launch_bounds__(288, 2) gemm_stream_bulk_kernel(const float* __restrict__ At,
+                                                                 const float* __restrict__ Rm, int M, long long K,
+                                                                 long long kchunk, int mblocks, float* __restrict__ part,
+                                                                 int bf16, KRange kr, unsigned* status) {
+  extern __shared__ __align__(128) uint8_t bulk_smem[];
+  const int nc = (int)blockDim.x - 32;                  // consumer threads, 4 hub outputs each
+  const int row_bytes = nc * 16;
+  float* A_s = reinterpret_cast<float*>(bulk_smem);                                   // [stage][row][4 nc]
+  float* R_s = reinterpret_cast<float*>(bulk_smem + kBulkStages * kBulkRows * row_bytes);   // [stage][row][NN]
+  uint64_t* full = reinterpret_cast<uint64_t*>(bulk_smem + kBulkStages * kBulkRows * (row_bytes + NN * 4));
+  uint64_t* empty = full + kBulkStages;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + kBulkStages);
+  const int mb = blockIdx.x % mblocks, split = blockIdx.x / mblocks;
+  const long long s0 = (long long)split * kchunk;
+  const long long k0 = max(s0, kr.lo_of(K)), k1 = min(min(K, s0 + kchunk), kr.hi_of(K));
+  const long long nrows = k1 > k0 ? k1 - k0 : 0;
+  const int nstage = (int)((nrows + kBulkRows - 1) / kBulkRows);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, cw = nc >> 5;
+  const int m0 = mb * nc * 4;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kBulkStages; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[i])), "r"(1) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[i])), "r"(cw) : "memory");
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (warp == cw) {                                     // producer warp
+    if (lane == 0) {
+      int issued = 0;
+      for (int i = 0; i < nstage; ++i) {
+        const int st = i % kBulkStages;
+        if (i >= kBulkStages && !bulk_wait(&empty[st], ((i / kBulkStages) - 1) & 1)) {
+          atomicOr(status, 8u);
+          *abort_flag = 1;
+        }
+        if (*abort_flag) break;
+        const long long r0 = k0 + (long long)i * kBulkRows;
+        const int rows = (int)min((long long)kBulkRows, k1 - r0);
+        const uint32_t bytes = (uint32_t)(rows * row_bytes + rows * NN * 4);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&full[st])), "r"(bytes)
+                     : "memory");
+        for (int r = 0; r < rows; ++r)
+          asm volatile(
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                  smem_u32(A_s + ((size_t)st * kBulkRows + r) * nc * 4)),
+              "l"(At + (r0 + r) * M + m0), "r"(row_bytes), "r"(smem_u32(&full[st]))
+              : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                smem_u32(R_s + (size_t)st * kBulkRows * NN)),
+            "l"(Rm + r0 * NN), "r"((uint32_t)(rows * NN * 4)), "r"(smem_u32(&full[st]))
+            : "memory");
+        issued = i + 1;
+      }
+      if (*abort_flag)      // let copies already issued land before the shared memory is released
+        for (int i = max(0, issued - kBulkStages); i < issued; ++i) bulk_wait(&full[i % kBulkStages], (i / kBulkStages) & 1);
+    }
+    return;
+  }
+  float acc[4][NN];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < NN; ++j) acc[i][j] = 0.f;
+  for (int i = 0; i < nstage; ++i) {
+    const int st = i % kBulkStages;
+    bool ok = !*abort_flag && bulk_wait(&full[st], (i / kBulkStages) & 1);
+    ok = __all_sync(0xffffffffu, ok) != 0;
+    if (!ok) {
+      if (lane == 0) { atomicOr(status, 8u); *abort_flag = 1; }
+      break;
+    }
+    const long long r0 = k0 + (long long)i * kBulkRows;
+    const int rows = (int)min((long long)kBulkRows, k1 - r0);
+    const float* as = A_s + (size_t)st * kBulkRows * nc * 4 + threadIdx.x * 4;
+    const float* rs = R_s + (size_t)st * kBulkRows * NN;
+    for (int r = 0; r < rows; ++r)
+      stream_fma<NN>(acc, *reinterpret_cast<const float4*>(as + (size_t)r * nc * 4), rs + r * NN, bf16);
+    __syncwarp();
+    if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[st])) : "memory");
+  }
+  const int m = m0 + 4 * (int)threadIdx.x;
+  if (m >= M) return;
+  const bool good = !*abort_flag;
+  float* dst = part + ((long long)split * M + m) * NN;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < NN; ++j) dst[i * NN + j] = good ? acc[i][j] : 0.f;
+}
+
 template <int NN>
 static cudaError_t launch_stream_nn(const float* At, const float* Rm, const ProblemDev& Pb, float* part, int bf16,
-                                    const uint8_t* live, KRange kr, cudaStream_t s) {
+                                    const uint8_t* live, KRange kr, unsigned* status, cudaStream_t s) {
   long long kchunk = (Pb.K + Pb.ssplits - 1) / Pb.ssplits;
   kchunk = (kchunk + 7) & ~7ll;
   const long long splits = (Pb.K + kchunk - 1) / kchunk;    // every split but the last is full
-  gemm_stream_kernel<NN><<<(unsigned)(Pb.smblocks * splits), Pb.sthreads, 0, s>>>(At, Rm, Pb.M, Pb.K, kchunk,
-                                                                                  Pb.smblocks, part, bf16, live, kr);
+  const bool bulk = NN >= 4 && live == nullptr && Pb.sthreads % 32 == 0 && status != nullptr &&
+                    (reinterpret_cast<uintptr_t>(At) & 15) == 0 && (reinterpret_cast<uintptr_t>(Rm) & 15) == 0 &&
+                    (Pb.M * 4) % 16 == 0;
+  if (bulk) {   // dense operand: rows streamed by the TMA engine into a shared-memory ring
+    const size_t smem = (size_t)kBulkStages * kBulkRows * (Pb.sthreads * 16 + NN * 4) + 2 * kBulkStages * 8 + 16;
+    cudaError_t err =
+        cudaFuncSetAttribute(gemm_stream_bulk_kernel<NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    gemm_stream_bulk_kernel<NN><<<(unsigned)(Pb.smblocks * splits), Pb.sthreads + 32, smem, s>>>(
+        At, Rm, Pb.M, Pb.K, kchunk, Pb.smblocks, part, bf16, kr, status);
+  } else {
+    gemm_stream_kernel<NN><<<(unsigned)(Pb.smblocks * splits), Pb.sthreads, 0, s>>>(At, Rm, Pb.M, Pb.K, kchunk,
+                                                                                    Pb.smblocks, part, bf16, live, kr);
+  }
   note_launch();
   return cudaGetLastError();
 }
@@ -448,11 +582,11 @@ static cudaError_t launch_stream(const DevRes& r, const ProblemDev& Pb, float* s
   float* part = scratch + Pb.part_off;
   const uint8_t* live = (stitched && Pb.hub_qrow_off >= 0) ? r.qnz + Pb.hub_qrow_off : nullptr;
   switch (Pb.N) {
-    case 1: return launch_stream_nn<1>(At, Rm, Pb, part, bf16, live, kr, s);
-    case 2: return launch_stream_nn<2>(At, Rm, Pb, part, bf16, live, kr, s);
-    case 4: return launch_stream_nn<4>(At, Rm, Pb, part, bf16, live, kr, s);
-    case 8: return launch_stream_nn<8>(At, Rm, Pb, part, bf16, live, kr, s);
-    case 16: return launch_stream_nn<16>(At, Rm, Pb, part, bf16, live, kr, s);
+    case 1: return launch_stream_nn<1>(At, Rm, Pb, part, bf16, live, kr, r.status, s);
+    case 2: return launch_stream_nn<2>(At, Rm, Pb, part, bf16, live, kr, r.status, s);
+    case 4: return launch_stream_nn<4>(At, Rm, Pb, part, bf16, live, kr, r.status, s);
+    case 8: return launch_stream_nn<8>(At, Rm, Pb, part, bf16, live, kr, r.status, s);
+    case 16: return launch_stream_nn<16>(At, Rm, Pb, part, bf16, live, kr, r.status, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -502,8 +636,19 @@ __global__ void reduce_scatter_kernel(DevPlan P, const long long* prefix, int np
     const long long loc = g - prefix[pi];
     const long long m = loc / Pb.N, n = loc - m * Pb.N;
     const int splits = (Pb.stream && !(use_tc && Pb.tc)) ? Pb.ssplits : Pb.splits;
-    double acc = 0.0;
-    for (int s = 0; s < splits; ++s) acc += (double)scratch[Pb.part_off + ((long long)s * Pb.M + m) * Pb.N + n];
+    // four independent FP64 sums (more loads in flight), combined in a fixed order
+    const float* pp = scratch + Pb.part_off + m * Pb.N + n;
+    const long long st = (long long)Pb.M * Pb.N;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int s = 0;
+    for (; s + 4 <= splits; s += 4) {
+      a0 += (double)pp[(long long)s * st];
+      a1 += (double)pp[(long long)(s + 1) * st];
+      a2 += (double)pp[(long long)(s + 2) * st];
+      a3 += (double)pp[(long long)(s + 3) * st];
+    }
+    for (; s < splits; ++s) a0 += (double)pp[(long long)s * st];
+    const double acc = (a0 + a1) + (a2 + a3);
     long long o = 0;
     const FragDev& Hb = P.frags[Pb.frag0 + Pb.hub];
     for (int j = 0; j < Hb.m; ++j) o |= ((m >> j) & 1) << Hb.marg_pos[j];

@@ -55,8 +55,8 @@ def _candidates_worker(args):
     for w in ws:
         try:
             res.append(ccs.ccs_cut_candidates(ctx, w, cap=cap))
-        except Exception:
-            res.append([])
+        except ccs.CCSError:
+            res.append([])          # no cut set within the limits (counted by the callers)
     return res
 
 
@@ -101,17 +101,34 @@ def device_time(ctx, w, cuts, mode, reps=1):
     return ev[0].elapsed_time(ev[1]) / 1e3 / reps
 
 
-def make_dataset(ctx, ws, cands, judge, max_cuts, log=print):
+def _reason(e):
+    """Short label of a refused candidate (the library's error code name)."""
+    msg = str(e)
+    for code in ("UNSUPPORTED", "NC_TOO_WIDE", "TOO_MANY_CUTS", "INVALID_ARG", "OOM"):
+        if code in msg:
+            return code + (": not a star" if "star" in msg else ": hub wider than 16 bits" if "16 bits" in msg
+                           else "")
+    return type(e).__name__
+
+
+def make_dataset(ctx, ws, cands, judge, max_cuts, log=print, dropped=None):
+    """Timed samples (features, log device time) of every judged candidate.
+    Candidates the library refuses are counted in ``dropped`` by reason."""
     from paper_2303_10788_gb300 import ccs
     graphs, target, groups = [], [], []
+    dropped = {} if dropped is None else dropped
     t0 = time.time()
     for i, (w, cs) in enumerate(zip(ws, cands)):
         g0 = len(graphs)
+        if not cs:
+            dropped["no candidate"] = dropped.get("no candidate", 0) + 1
         for cuts, _ in judged(cs, judge, max_cuts):
             try:
                 t = device_time(ctx, w, cuts, ccs.CCS_SAMPLED)
-            except Exception:
-                continue            # unsupported topology or hub wider than 16 bits
+            except ccs.CCSError as e:
+                r = _reason(e)
+                dropped[r] = dropped.get(r, 0) + 1
+                continue
             graphs.append(ccs.ccs_featurize(ctx, w, cuts))
             target.append(math.log(t))
         if len(graphs) > g0:
@@ -147,14 +164,39 @@ def predict(ctx, net, graphs, chunk=512):
     return np.concatenate(out) if out else np.zeros(0, np.float32)
 
 
-def evaluate(ctx, net, ws, cands, judge, max_cuts, check_exact=True, log=print):
-    """Greedy vs learned on held-out circuits: device time of each choice,
-    the best measured candidate, and exact-mode agreement of the results."""
+def e2e_time(ctx, w, learned, reps=3):
+    """Median wall seconds of one circuit end to end through the C ABI: plan
+    build (cut search, and with ``learned`` the scorer on the GPU picking
+    among the candidates), sampled evaluation, recombination into host
+    memory; after one untimed run."""
     from paper_2303_10788_gb300 import ccs
-    rows = []
+    pk = ccs.pack_problems([Workload(w.name, w.circuit, None, w.marginal, w.zstrings, w.shots, w.seed)])
+    ts = []
+    for i in range(reps + 1):
+        t0 = time.perf_counter()
+        plan = ccs.ccs_build_fragments(ctx, pk, use_learned=1 if learned else 0)
+        res = ccs.ccs_eval_variants(ctx, plan, mode=ccs.CCS_SAMPLED, shots=w.shots)
+        ccs.ccs_recombine(ctx, plan, res)
+        if i:
+            ts.append(time.perf_counter() - t0)
+        del res, plan
+    return float(np.median(ts))
+
+
+def evaluate(ctx, net, ws, cands, judge, max_cuts, check_exact=True, log=print, e2e_reps=3):
+    """Greedy vs learned on held-out circuits: device time of each choice
+    (evaluation + recombination, two repeats), the best measured candidate,
+    exact-mode agreement of the results, and end-to-end circuits/s of the
+    library's greedy and learned paths (cut search and the scorer's own cost
+    included, median of ``e2e_reps`` repeats).  Candidates the library
+    refuses are counted by reason."""
+    from paper_2303_10788_gb300 import ccs
+    rows, dropped = [], {}
+    ccs.ccs_set_cut_model(ctx, net)
     for w, cs in zip(ws, cands):
         js = judged(cs, judge, max_cuts)
         if not js:
+            dropped["no candidate"] = dropped.get("no candidate", 0) + 1
             continue
         feats = [ccs.ccs_featurize(ctx, w, c) for c, _ in js]
         pred = predict(ctx, net, feats)
@@ -163,7 +205,9 @@ def evaluate(ctx, net, ws, cands, judge, max_cuts, check_exact=True, log=print):
         for c, _ in js:
             try:
                 times.append(device_time(ctx, w, c, ccs.CCS_SAMPLED, reps=2))
-            except Exception:
+            except ccs.CCSError as e:
+                r = _reason(e)
+                dropped[r] = dropped.get(r, 0) + 1
                 times.append(float("inf"))
         if not np.isfinite(times[0]) or not np.isfinite(times[pick]):
             continue
@@ -175,17 +219,35 @@ def evaluate(ctx, net, ws, cands, judge, max_cuts, check_exact=True, log=print):
                 r = ccs.ccs_eval_variants(ctx, p, mode=ccs.CCS_EXACT)
                 out.append(ccs.ccs_recombine(ctx, p, r)[0])
             agree = float(np.abs(out[0] - out[1]).max())
-        rows.append({"greedy": times[0], "learned": times[pick], "best": float(min(times)),
-                     "changed": pick != 0, "n_cands": len(js), "max_abs_diff": agree})
+        row = {"greedy": times[0], "learned": times[pick], "best": float(min(times)),
+               "changed": pick != 0, "n_cands": len(js), "max_abs_diff": agree}
+        if e2e_reps:
+            try:
+                row["e2e_greedy"] = e2e_time(ctx, w, False, e2e_reps)
+                row["e2e_learned"] = e2e_time(ctx, w, True, e2e_reps)
+            except ccs.CCSError as e:       # the library's own pick refused (counted, left out)
+                row.pop("e2e_greedy", None)
+                r = "end to end: " + _reason(e)
+                dropped[r] = dropped.get(r, 0) + 1
+        rows.append(row)
+    ccs.ccs_set_cut_model(ctx, None)
     g = sum(r["greedy"] for r in rows)
     l = sum(r["learned"] for r in rows)
     b = sum(r["best"] for r in rows)
+    both = [r for r in rows if "e2e_learned" in r]
+    eg = sum(r["e2e_greedy"] for r in both)
+    el = sum(r["e2e_learned"] for r in both)
     diffs = [r["max_abs_diff"] for r in rows if r["max_abs_diff"] is not None]
     return {"circuits": len(rows), "greedy_circuits_per_s": len(rows) / g if g else 0.0,
             "learned_circuits_per_s": len(rows) / l if l else 0.0,
             "best_candidate_circuits_per_s": len(rows) / b if b else 0.0,
             "speedup_learned_over_greedy": g / l if l else 0.0,
+            "e2e_circuits": len(both),
+            "e2e_greedy_circuits_per_s": len(both) / eg if eg else 0.0,
+            "e2e_learned_circuits_per_s": len(both) / el if el else 0.0,
+            "e2e_speedup_learned_over_greedy": eg / el if el else 0.0,
             "picks_changed": sum(r["changed"] for r in rows),
+            "dropped_candidates": dropped,
             "max_abs_diff_exact": max(diffs) if diffs else 0.0,
             "rows": rows}
 
@@ -212,13 +274,14 @@ def main(argv=None):
     print(f"candidates: {time.time() - t0:.0f} s", flush=True)
     from paper_2303_10788_gb300 import ccs
     ctx = ccs.ccs_create(0)
-    graphs, target, _ = make_dataset(ctx, ws_tr, c_tr, a.judge, a.max_cuts)
-    print(f"dataset: {len(graphs)} samples, {time.time() - t0:.0f} s", flush=True)
+    dropped = {}
+    graphs, target, _ = make_dataset(ctx, ws_tr, c_tr, a.judge, a.max_cuts, dropped=dropped)
+    print(f"dataset: {len(graphs)} samples, {time.time() - t0:.0f} s; dropped {dropped}", flush=True)
     net = ccs.ccs_mpnn_create(ctx, seed=a.seed)
     mu, sd = train(ctx, net, graphs, target, a.epochs, a.batch, a.lr, a.seed)
     rep = evaluate(ctx, net, ws_te, c_te, a.judge, a.max_cuts)
-    rep.update({"train_circuits": a.train, "train_samples": len(graphs), "target_mean": mu, "target_std": sd,
-                "seconds": time.time() - t0})
+    rep.update({"train_circuits": a.train, "train_samples": len(graphs), "train_dropped_candidates": dropped,
+                "target_mean": mu, "target_std": sd, "seconds": time.time() - t0})
     print(json.dumps({k: v for k, v in rep.items() if k != "rows"}), flush=True)
     if a.weights:
         np.savez(a.weights, params=ccs.ccs_mpnn_params(ctx, net), target_mean=mu, target_std=sd)

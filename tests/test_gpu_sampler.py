@@ -29,10 +29,19 @@ def test_byte_sampler_equals_16bit(ctx, make):
     kw = dict(mode=ccs.CCS_SAMPLED, shots=ws[0].shots, seed_lo=SEED[0], seed_hi=SEED[1], keep_tableaus=True)
     r16 = ccs.ccs_eval_variants(ctx, plan, hub_sampler=1, **kw)
     r8 = ccs.ccs_eval_variants(ctx, plan, hub_sampler=2, **kw)
-    assert ccs.ccs_get_tuning(ctx, r8)[3] == 256 and ccs.ccs_get_tuning(ctx, r16)[3] != 256
+    r8w = ccs.ccs_eval_variants(ctx, plan, hub_sampler=3, **kw)      # byte counters, 512-thread CTAs
+    assert ccs.ccs_get_tuning(ctx, r8)[3] == -256 and ccs.ccs_get_tuning(ctx, r8w)[3] == -512
+    assert ccs.ccs_get_tuning(ctx, r16)[3] > 0
     m16, z16 = ccs.ccs_recombine(ctx, plan, r16)
     m8, z8 = ccs.ccs_recombine(ctx, plan, r8)
+    m8w, z8w = ccs.ccs_recombine(ctx, plan, r8w)
     assert np.array_equal(m16, m8) and np.array_equal(z16, z8)
+    assert np.array_equal(m8w, m8) and np.array_equal(z8w, z8)
+    for f in range(ccs.ccs_plan_counts(ctx, plan, 0)[0]):
+        info = ccs.ccs_fragment_info_get(ctx, plan, 0, f)
+        if info["clifford"] and info["n_slots"] == ccs.ccs_plan_counts(ctx, plan, 0)[1]:
+            for v in range(0, info["n_variants"], max(1, info["n_variants"] // 7)):
+                assert np.array_equal(ccs.ccs_get_counts(ctx, r8w, 0, f, v), ccs.ccs_get_counts(ctx, r8, 0, f, v))
     rng = np.random.default_rng(0)
     checked = 0
     for pi in range(len(ws)):
