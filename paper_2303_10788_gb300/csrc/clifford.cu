@@ -1487,10 +1487,14 @@ __global__ void __launch_bounds__(512) sample_hub_kernel(DevPlan P, DevRes R, Ev
 // for a Z-basis output; one row per choice of I/Z (2^nz rows, bit i of the
 // row index = the i-th Z-basis output).  s_czD[row] = the row's Pauli index
 // D, s_czS[row] = its sign mask over the quantum-output bits (X/Y-basis
-// outputs always flip the sign, a Z-basis output where it reads Z).  zm =
-// the Z-basis outputs.  Called by every thread; threads < 2^nz write.
-__device__ __forceinline__ void hub_variant_rows(const FragDev& F, int v, int* s_czD, int* s_czS, int& nz, int& zm) {
+// outputs always flip the sign, a Z-basis output where it reads Z).
+// s_nzm[0] = nz, s_nzm[1] = the Z-basis outputs as a bit mask.  Warp 0
+// computes them (its lanes < 2^nz write the rows); the caller synchronises
+// the block before reading them.
+__device__ __forceinline__ void hub_variant_rows(const FragDev& F, int v, int* s_czD, int* s_czS, int* s_nzm) {
+  if (threadIdx.x >= 32) return;
   int beta[kMaxCuts], zpos[kMaxCuts], zout[kMaxCuts];
+  int nz, zm;
   int t = v;
   for (int i = 0; i < F.qin; ++i) t /= 4;
   for (int j = 0; j < F.qout; ++j) { beta[j] = t % 3; t /= 3; }
@@ -1518,6 +1522,10 @@ __device__ __forceinline__ void hub_variant_rows(const FragDev& F, int v, int* s
       if ((threadIdx.x >> i) & 1) { D |= 3 << (2 * zpos[i]); smask |= 1 << zout[i]; }
     s_czD[threadIdx.x] = D;
     s_czS[threadIdx.x] = smask;
+  }
+  if (threadIdx.x == 0) {
+    s_nzm[0] = nz;
+    s_nzm[1] = zm;
   }
 }
 
@@ -1604,7 +1612,7 @@ __global__ void __launch_bounds__(512, 2) sample_hub8_kernel(DevPlan P, DevRes R
   extern __shared__ __align__(16) uint32_t h32[];
   __shared__ uint32_t tbl[3][256];
   __shared__ FragDev sF;
-  __shared__ int s_czD[16], s_czS[16];
+  __shared__ int s_czD[16], s_czS[16], s_nzm[2];
   __shared__ unsigned s_tot;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int2 it = items[blockIdx.x];
@@ -1622,8 +1630,7 @@ __global__ void __launch_bounds__(512, 2) sample_hub8_kernel(DevPlan P, DevRes R
   const uint32_t off = sp.off;
   build_tables(tbl, sp, rank);
   // the variant's operand rows: one D and sign mask per Z-basis choice
-  int nz, zm;
-  hub_variant_rows(F, v, s_czD, s_czS, nz, zm);
+  hub_variant_rows(F, v, s_czD, s_czS, s_nzm);
   const uint32_t cmask = rank >= 32 ? 0xffffffffu : ((1u << rank) - 1u);
   const float inv = (float)E.inv_shots;
   float* QT = R.TQ + F.T_off;
@@ -1650,7 +1657,7 @@ __global__ void __launch_bounds__(512, 2) sample_hub8_kernel(DevPlan P, DevRes R
     if (keep_counts)
       for (uint32_t y = tid; y < (1u << nA); y += nt) gcount[y] = (h32[y >> 2] >> ((y & 3u) << 3)) & 0xffu;
     unsigned tot = 0;
-    switch (zm) {
+    switch (s_nzm[1]) {
 #define CCS_HUB8_CASE(z) \
   case z: tot = hub8_readout<z>(h32, m, M, nb, s_czD, QT, inv); break;
       CCS_HUB8_CASE(0) CCS_HUB8_CASE(1) CCS_HUB8_CASE(2) CCS_HUB8_CASE(3)
@@ -1666,6 +1673,8 @@ __global__ void __launch_bounds__(512, 2) sample_hub8_kernel(DevPlan P, DevRes R
     narrow = s_tot == E.shots;      // no byte wrapped
   }
   if (!narrow) {   // 16-bit counters, outputs of one half (top marginal bit) per pass
+    __syncthreads();
+    const int nz = s_nzm[0];
     const int mh = m - 1, Mh = M >> 1;
     for (int h = 0; h < 2; ++h) {
       __syncthreads();
@@ -1727,7 +1736,7 @@ __global__ void __launch_bounds__(512, 2) sample_hub8_kernel(DevPlan P, DevRes R
 // streaming GEMM skips flagged rows).
 __global__ void __launch_bounds__(256) hub_exact_kernel(DevPlan P, DevRes R, const int2* items) {
   __shared__ FragDev sF;
-  __shared__ int s_czD[16], s_czS[16], s_live[16];
+  __shared__ int s_czD[16], s_czS[16], s_live[16], s_nzm[2];
   __shared__ uint32_t s_vo[kMaxMeas], s_vb[kMaxMeas], s_kg[kMaxMeas];
   __shared__ int s_piv[kMaxMeas], s_cnt[2];
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -1740,11 +1749,10 @@ __global__ void __launch_bounds__(256) hub_exact_kernel(DevPlan P, DevRes R, con
   __syncthreads();
   const FragDev& F = sF;
   const int v = it.y, m = F.m, M = 1 << m;
-  int nz, zm;
-  hub_variant_rows(F, v, s_czD, s_czS, nz, zm);
+  hub_variant_rows(F, v, s_czD, s_czS, s_nzm);
   const SpaceRec& sp = R.spaces[F.space_off + v];
   const int rank = sp.rank;
-  if (tid == 0) {
+  if (tid == 32) {
     int ro = 0, kb = 0;
     for (int j = 0; j < rank; ++j) {
       const uint32_t vec = sp.basis[j];
@@ -1756,7 +1764,7 @@ __global__ void __launch_bounds__(256) hub_exact_kernel(DevPlan P, DevRes R, con
     s_cnt[1] = kb;
   }
   __syncthreads();
-  const int ro = s_cnt[0], kb = s_cnt[1], nrows = 1 << nz;
+  const int ro = s_cnt[0], kb = s_cnt[1], nrows = 1 << s_nzm[0];
   if (tid < nrows) {
     bool live = true;
     for (int j = 0; j < kb; ++j) live = live && !(__popc(s_kg[j] & (uint32_t)s_czS[tid]) & 1);
