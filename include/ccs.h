@@ -37,6 +37,10 @@
  * Errors: every int-returning call returns CCS_OK (0) or a negative
  * CCS_ERR_* code and leaves a message in ccs_last_error(ctx).  No exception
  * crosses the ABI.  A context must be used by one host thread at a time.
+ * A plan may be evaluated and recombined by any context on the same device
+ * (for example one thread building plans with its own context while another
+ * evaluates them); the context that built a plan must outlive it, and a plan
+ * or result is used by one thread at a time.
  */
 #ifndef CCS_ABI_H_
 #define CCS_ABI_H_

@@ -300,21 +300,24 @@ static int learned_pick(ccs_ctx c, const Problem& P, const std::vector<CutCandid
   *pick = 0;
   if (idx.size() < 2) return CCS_OK;
   const int nc = (int)idx.size();
+  // the interaction graph once, the candidates' node features on host threads
+  const GraphBase g = graph_base(P);
+  std::vector<std::vector<float>> xs(nc), gs(nc);
+  std::vector<int> rcs(nc, CCS_OK);
+  std::vector<std::string> errs(nc);
+  parallel_for(nc, [&](int i) { rcs[i] = featurize_nodes(P, g, cands[idx[i]].cuts, xs[i], gs[i], errs[i]); });
+  for (int i = 0; i < nc; ++i)
+    if (rcs[i] != CCS_OK) return fail(c, rcs[i], errs[i]);
   std::vector<float> X, val, valt, glob;
   std::vector<int> rowptr{0}, col, goff{0};
-  std::string err;
-  for (int i : idx) {
-    std::vector<float> x1, v1, vt1, g1;
-    std::vector<int> rp1, c1;
-    int rc = featurize(P, cands[i].cuts, x1, rp1, c1, v1, vt1, g1, err);
-    if (rc != CCS_OK) return fail(c, rc, err);
+  for (int i = 0; i < nc; ++i) {
     const int base = goff.back(), e0 = rowptr.back();
-    X.insert(X.end(), x1.begin(), x1.end());
-    for (size_t r = 1; r < rp1.size(); ++r) rowptr.push_back(e0 + rp1[r]);
-    for (int cc : c1) col.push_back(base + cc);
-    val.insert(val.end(), v1.begin(), v1.end());
-    valt.insert(valt.end(), vt1.begin(), vt1.end());
-    glob.insert(glob.end(), g1.begin(), g1.end());
+    X.insert(X.end(), xs[i].begin(), xs[i].end());
+    for (size_t r = 1; r < g.rowptr.size(); ++r) rowptr.push_back(e0 + g.rowptr[r]);
+    for (int cc : g.col) col.push_back(base + cc);
+    val.insert(val.end(), g.val.begin(), g.val.end());
+    valt.insert(valt.end(), g.val_t.begin(), g.val_t.end());
+    glob.insert(glob.end(), gs[i].begin(), gs[i].end());
     goff.push_back(base + (int)P.n_qubits);
   }
   ccs_graph_batch b{goff.back(), nc, X.data(), rowptr.data(), col.data(), val.data(), valt.data(), goff.data(),
@@ -1245,6 +1248,12 @@ int ccs_eval_variants(ccs_ctx c, ccs_plan p, const ccs_eval_opts* opts, ccs_res*
     }
     e.inv_shots = e.shots ? 1.0 / (double)e.shots : 0.0;
     r->ep = e;
+    {   // sampled hubs keep exact 16-bit count sums (|sum| <= shots)
+      const int i16 = (e.mode == CCS_SAMPLED && e.shots <= 32767u) ? 1 : 0;
+      if (i16 != r->dr.hub_i16) drop_graph();
+      r->dr.hub_i16 = i16;
+      r->dr.hub_scale = (float)e.inv_shots;
+    }
     if (opts->autotune && !r->graph && opts->hub_sampler == 0) {
       const bool prof = c->profiling;
       c->profiling = false;
@@ -1328,7 +1337,7 @@ int ccs_recombine(ccs_ctx c, ccs_plan p, ccs_res r, const ccs_recomb_opts* opts,
     }
     cudaError_t e;
     if (opts && opts->use_graph && !c->profiling && rz.krange.full()) {
-      const int key = prec * 2 + (tc ? 1 : 0) + (stitched ? 4 : 0);
+      const int key = prec * 2 + (tc ? 1 : 0) + (stitched ? 4 : 0) + (r->dr.hub_i16 ? 8 : 0);
       if (!r->rgraph || r->rgraph_key != key) {
         if (r->rgraph) { cudaGraphExecDestroy(r->rgraph); r->rgraph = nullptr; }
         cudaStream_t s = c->stream;
@@ -1540,7 +1549,14 @@ int ccs_get_operand(ccs_ctx c, ccs_res r, int problem, int fragment, float* out)
     }
     // the hub's Q is stored transposed on the device ([d][o]); return [o][d]
     std::vector<float> t(cnt);
-    cudaError_t e = cudaMemcpy(t.data(), r->dr.TQ + d->T_off, cnt * sizeof(float), cudaMemcpyDeviceToHost);
+    cudaError_t e;
+    if (r->dr.hub_i16 && d->clifford) {   // exact int16 count sums times 1/shots
+      std::vector<int16_t> h(cnt);
+      e = cudaMemcpy(h.data(), r->dr.TQ + d->T_off, cnt * sizeof(int16_t), cudaMemcpyDeviceToHost);
+      for (long long i = 0; i < cnt; ++i) t[i] = (float)h[i] * r->dr.hub_scale;
+    } else {
+      e = cudaMemcpy(t.data(), r->dr.TQ + d->T_off, cnt * sizeof(float), cudaMemcpyDeviceToHost);
+    }
     if (e != cudaSuccess) return cuda_fail(c, e, "copy operand");
     const long long M = 1ll << d->m, K = 1ll << (2 * d->n_slots);
     std::vector<uint8_t> live(K, 1);

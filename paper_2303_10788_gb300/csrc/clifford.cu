@@ -1245,11 +1245,28 @@ __global__ void __launch_bounds__(256) sample_kernel(DevPlan P, DevRes R, EvalPa
 }
 
 namespace {
+// Stores of the hub operand: signed count sums (row index idx = D M + o),
+// as 16-bit integers when QH is set (exact: |sum| <= shots <= 32767; the
+// readers scale by 1/shots), else scaled to FP32 in QT.
+__device__ __forceinline__ void put1(float* QT, int16_t* QH, long long idx, int a, float inv) {
+  if (QH) QH[idx] = (int16_t)a;
+  else QT[idx] = (float)a * inv;
+}
+__device__ __forceinline__ void put2(float* QT, int16_t* QH, long long idx, int a, int b, float inv) {
+  if (QH) *reinterpret_cast<short2*>(QH + idx) = make_short2((short)a, (short)b);
+  else *reinterpret_cast<float2*>(QT + idx) = make_float2((float)a * inv, (float)b * inv);
+}
+__device__ __forceinline__ void put4(float* QT, int16_t* QH, long long idx, const int (&v)[4], float inv) {
+  if (QH) *reinterpret_cast<short4*>(QH + idx) = make_short4((short)v[0], (short)v[1], (short)v[2], (short)v[3]);
+  else *reinterpret_cast<float4*>(QT + idx) = make_float4((float)v[0] * inv, (float)v[1] * inv, (float)v[2] * inv,
+                                                          (float)v[3] * inv);
+}
 // signed sums of the counts c[b] (b = output bits) for every sign mask by a
 // 16-point Walsh-Hadamard transform, for the outputs o and o+1 (a, c), then
 // the variant's operand rows Q^T[D][o..o+1]
 __device__ __forceinline__ void hub_pair_out(int (&a)[16], int (&c)[16], int* wht, const int* s_czD,
-                                             const int* s_czS, int nz, float* QT, int M, int o, float inv) {
+                                             const int* s_czS, int nz, float* QT, int16_t* QH, int M, int o,
+                                             float inv) {
 #pragma unroll
   for (int h = 1; h < 16; h <<= 1)
 #pragma unroll
@@ -1268,8 +1285,7 @@ __device__ __forceinline__ void hub_pair_out(int (&a)[16], int (&c)[16], int* wh
   }
   for (int cz = 0; cz < (1 << nz); ++cz) {
     const int sm = s_czS[cz];
-    *reinterpret_cast<float2*>(QT + (long long)s_czD[cz] * M + o) =
-        make_float2((float)wht[sm] * inv, (float)wht[16 + sm] * inv);
+    put2(QT, QH, (long long)s_czD[cz] * M + o, wht[sm], wht[16 + sm], inv);
   }
 }
 // Register select p[i] for a CTA-uniform index (a binary tree of selects).
@@ -1290,7 +1306,7 @@ __device__ __forceinline__ unsigned pick16(const unsigned (&p)[16], int i) {
 // transform value fits a signed 16-bit lane below 32768 shots), and the
 // variant's sign masks pick from registers (no shared-memory scratch).
 __device__ __forceinline__ void hub_pair_out_packed(unsigned (&p)[16], const int* s_czD, const int* s_czS, int nz,
-                                                    float* QT, int M, int o, float inv) {
+                                                    float* QT, int16_t* QH, int M, int o, float inv) {
 #pragma unroll
   for (int h = 1; h < 16; h <<= 1)
 #pragma unroll
@@ -1303,7 +1319,7 @@ __device__ __forceinline__ void hub_pair_out_packed(unsigned (&p)[16], const int
   for (int cz = 0; cz < (1 << nz); ++cz) {
     const unsigned w = pick16(p, s_czS[cz]);
     const int lo = (int)(short)(w & 0xffffu), hi = (int)(short)(w >> 16);
-    *reinterpret_cast<float2*>(QT + (long long)s_czD[cz] * M + o) = make_float2((float)lo * inv, (float)hi * inv);
+    put2(QT, QH, (long long)s_czD[cz] * M + o, lo, hi, inv);
   }
 }
 
@@ -1391,6 +1407,7 @@ __global__ void __launch_bounds__(512) sample_hub_kernel(DevPlan P, DevRes R, Ev
   const int m = F.m, M = 1 << m, nb = 1 << F.qout;
   const float inv = (float)E.inv_shots;
   float* QT = R.TQ + F.T_off;
+  int16_t* QH = R.hub_i16 ? reinterpret_cast<int16_t*>(R.TQ + F.T_off) : nullptr;
   if (!wide && m >= 1 && F.qout <= 4 && E.shots <= (1u << 26)) {
     // Pairs of outputs (o, o+1) share the packed counter words.  Per pair,
     // a 16-point Walsh-Hadamard transform over the output bits gives the
@@ -1416,7 +1433,7 @@ __global__ void __launch_bounds__(512) sample_hub_kernel(DevPlan P, DevRes R, Ev
         unsigned pk[16];
 #pragma unroll
         for (int b = 0; b < 16; ++b) pk[b] = b < nb ? hist2[((uint32_t)o | ((uint32_t)b << m)) >> 1] : 0u;
-        hub_pair_out_packed(pk, s_czD, s_czS, nz, QT, M, o, inv);
+        hub_pair_out_packed(pk, s_czD, s_czS, nz, QT, QH, M, o, inv);
       }
     } else
     for (int o2 = threadIdx.x; o2 < (M >> 1); o2 += blockDim.x) {
@@ -1446,8 +1463,7 @@ __global__ void __launch_bounds__(512) sample_hub_kernel(DevPlan P, DevRes R, Ev
       }
       for (int cz = 0; cz < (1 << nz); ++cz) {
         const int sm = s_czS[cz];
-        *reinterpret_cast<float2*>(QT + (long long)s_czD[cz] * M + o) =
-            make_float2((float)wht[sm] * inv, (float)wht[16 + sm] * inv);
+        put2(QT, QH, (long long)s_czD[cz] * M + o, wht[sm], wht[16 + sm], inv);
       }
     }
   } else if (F.qout <= 4 && E.shots <= (1u << 26)) {     // |acc| <= 16 shots fits an int
@@ -1462,7 +1478,7 @@ __global__ void __launch_bounds__(512) sample_hub_kernel(DevPlan P, DevRes R, Ev
         int acc = 0;
 #pragma unroll
         for (int b = 0; b < 16; ++b) acc += (__popc(b & smask) & 1) ? -c[b] : c[b];
-        QT[(long long)D * M + o] = (float)acc * inv;
+        put1(QT, QH, (long long)D * M + o, acc, inv);
       }
     }
   } else {
@@ -1476,7 +1492,8 @@ __global__ void __launch_bounds__(512) sample_hub_kernel(DevPlan P, DevRes R, Ev
           const long long cnt = count((uint32_t)o | ((uint32_t)b << m));
           acc += (__popc(b & smask) & 1) ? -cnt : cnt;
         }
-        QT[(long long)D * M + o] = (float)((double)acc * E.inv_shots);
+        if (QH) QH[(long long)D * M + o] = (int16_t)acc;
+        else QT[(long long)D * M + o] = (float)((double)acc * E.inv_shots);
       }
     }
   }
@@ -1552,7 +1569,8 @@ __host__ __device__ constexpr int pext4(int b, int zm) {
 
 template <int ZM>
 __device__ __forceinline__ unsigned hub8_readout(const uint32_t* __restrict__ h32, int m, int M, int nb,
-                                                 const int* s_czD, float* __restrict__ QT, float inv) {
+                                                 const int* s_czD, float* __restrict__ QT, int16_t* __restrict__ QH,
+                                                 float inv) {
   constexpr int NR = 1 << popc4(ZM);
   unsigned tot = 0;
   for (int q = threadIdx.x; q < (M >> 2); q += blockDim.x) {
@@ -1562,7 +1580,7 @@ __device__ __forceinline__ unsigned hub8_readout(const uint32_t* __restrict__ h3
     for (int b = 0; b < 16; ++b) w[b] = b < nb ? h32[((uint32_t)o | ((uint32_t)b << m)) >> 2] : 0u;
 #pragma unroll
     for (int b = 0; b < 16; ++b) tot = __dp4a(w[b], 0x01010101u, tot);
-    float out[NR][4];
+    int out[NR][4];
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
       int F[NR];
@@ -1586,13 +1604,12 @@ __device__ __forceinline__ unsigned hub8_readout(const uint32_t* __restrict__ h3
 #pragma unroll
       for (int i = 0; i < NR; ++i) {
         const int lo = (int)(short)(F[i] & 0xffff), hi = (F[i] - lo) >> 16;
-        out[i][2 * half] = (float)lo * inv;
-        out[i][2 * half + 1] = (float)hi * inv;
+        out[i][2 * half] = lo;
+        out[i][2 * half + 1] = hi;
       }
     }
 #pragma unroll
-    for (int i = 0; i < NR; ++i)
-      *reinterpret_cast<float4*>(QT + (long long)s_czD[i] * M + o) = make_float4(out[i][0], out[i][1], out[i][2], out[i][3]);
+    for (int i = 0; i < NR; ++i) put4(QT, QH, (long long)s_czD[i] * M + o, out[i], inv);
   }
   return tot;
 }
@@ -1634,6 +1651,7 @@ __global__ void __launch_bounds__(512, 2) sample_hub8_kernel(DevPlan P, DevRes R
   const uint32_t cmask = rank >= 32 ? 0xffffffffu : ((1u << rank) - 1u);
   const float inv = (float)E.inv_shots;
   float* QT = R.TQ + F.T_off;
+  int16_t* QH = R.hub_i16 ? reinterpret_cast<int16_t*>(R.TQ + F.T_off) : nullptr;
   const int wstride = E.shots <= 32767u ? 0 : 33;    // only the unpacked transform parks values
   int* wht = reinterpret_cast<int*>(h32 + hist_words) + tid * wstride;
   uint32_t* gcount = R.counts + F.counts_off + ((long long)v << nA);
@@ -1659,7 +1677,7 @@ __global__ void __launch_bounds__(512, 2) sample_hub8_kernel(DevPlan P, DevRes R
     unsigned tot = 0;
     switch (s_nzm[1]) {
 #define CCS_HUB8_CASE(z) \
-  case z: tot = hub8_readout<z>(h32, m, M, nb, s_czD, QT, inv); break;
+  case z: tot = hub8_readout<z>(h32, m, M, nb, s_czD, QT, QH, inv); break;
       CCS_HUB8_CASE(0) CCS_HUB8_CASE(1) CCS_HUB8_CASE(2) CCS_HUB8_CASE(3)
       CCS_HUB8_CASE(4) CCS_HUB8_CASE(5) CCS_HUB8_CASE(6) CCS_HUB8_CASE(7)
       CCS_HUB8_CASE(8) CCS_HUB8_CASE(9) CCS_HUB8_CASE(10) CCS_HUB8_CASE(11)
@@ -1702,7 +1720,7 @@ __global__ void __launch_bounds__(512, 2) sample_hub8_kernel(DevPlan P, DevRes R
           unsigned pk[16];
 #pragma unroll
           for (int b = 0; b < 16; ++b) pk[b] = b < nb ? h32[((uint32_t)ol | ((uint32_t)b << mh)) >> 1] : 0u;
-          hub_pair_out_packed(pk, s_czD, s_czS, nz, QT, M, h * Mh + ol, inv);
+          hub_pair_out_packed(pk, s_czD, s_czS, nz, QT, QH, M, h * Mh + ol, inv);
           continue;
         }
         int a[16], c[16];
@@ -1712,7 +1730,7 @@ __global__ void __launch_bounds__(512, 2) sample_hub8_kernel(DevPlan P, DevRes R
           a[b] = (int)(w & 0xffffu);
           c[b] = (int)(w >> 16);
         }
-        hub_pair_out(a, c, wht, s_czD, s_czS, nz, QT, M, h * Mh + ol, inv);
+        hub_pair_out(a, c, wht, s_czD, s_czS, nz, QT, QH, M, h * Mh + ol, inv);
       }
     }
   }

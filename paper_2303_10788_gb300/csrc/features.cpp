@@ -10,15 +10,57 @@
 // fragment / 12, log2(n) / 9, log2(gates) / 17, fragments / 8.
 #include <algorithm>
 #include <cmath>
-#include <map>
 
 #include "plan.hpp"
 
 namespace ccs {
 
-int featurize(const Problem& p0, const std::vector<ccs_cut>& cuts, std::vector<float>& x, std::vector<int>& rowptr,
-              std::vector<int>& col, std::vector<float>& val, std::vector<float>& val_t, std::vector<float>& glob,
-              std::string& err) {
+// Candidate-independent part: the interaction graph (CSR of A = D^-1 Adj and
+// of the transposed values) and the per-qubit gate counts.
+GraphBase graph_base(const Problem& p) {
+  GraphBase g;
+  const int n = (int)p.n_qubits;
+  g.tcount.assign(n, 0);
+  g.gcount.assign(n, 0);
+  std::vector<std::pair<int, int>> e;
+  for (auto& gt : p.gates) {
+    g.gcount[gt[1]]++;
+    if (is_nonclifford_op(gt[0])) g.tcount[gt[1]]++;
+    if (gt[0] == CCS_CX || gt[0] == CCS_CZ) {
+      g.gcount[gt[2]]++;
+      e.push_back({gt[1], gt[2]});
+      e.push_back({gt[2], gt[1]});
+    }
+  }
+  std::sort(e.begin(), e.end());
+  g.rowptr.assign(n + 1, 0);
+  std::vector<int> w;                      // edge weights (gate counts), CSR order
+  for (size_t i = 0; i < e.size();) {
+    size_t j = i + 1;
+    while (j < e.size() && e[j] == e[i]) ++j;
+    g.col.push_back(e[i].second);
+    w.push_back((int)(j - i));
+    g.rowptr[e[i].first + 1]++;
+    i = j;
+  }
+  for (int q = 0; q < n; ++q) g.rowptr[q + 1] += g.rowptr[q];
+  std::vector<double> deg(n, 0.0);
+  for (int q = 0; q < n; ++q)
+    for (int t = g.rowptr[q]; t < g.rowptr[q + 1]; ++t) deg[q] += w[t];
+  g.val.resize(w.size());
+  g.val_t.resize(w.size());
+  for (int q = 0; q < n; ++q)
+    for (int t = g.rowptr[q]; t < g.rowptr[q + 1]; ++t) {
+      g.val[t] = (float)(w[t] / deg[q]);
+      g.val_t[t] = (float)(w[t] / deg[g.col[t]]);
+    }
+  return g;
+}
+
+// Candidate-dependent part: fragment the circuit under the cut set, then the
+// node features (8 per qubit) and the global features.
+int featurize_nodes(const Problem& p0, const GraphBase& g, const std::vector<ccs_cut>& cuts, std::vector<float>& x,
+                    std::vector<float>& glob, std::string& err) {
   Problem p = p0;
   p.cuts = cuts;
   p.zstrings.clear();
@@ -26,17 +68,7 @@ int featurize(const Problem& p0, const std::vector<ccs_cut>& cuts, std::vector<f
   int rc = fragment_problem(p, 0, frags, err);
   if (rc != CCS_OK) return rc;
   const int n = (int)p.n_qubits;
-  std::vector<std::map<int, int>> adj(n);
-  std::vector<int> tcount(n, 0), gcount(n, 0), nc_gates(n, 0), ncut(n, 0), marg(n, 0), in_hub(n, 0);
-  for (auto& g : p.gates) {
-    gcount[g[1]]++;
-    if (is_nonclifford_op(g[0])) tcount[g[1]]++;
-    if (g[0] == CCS_CX || g[0] == CCS_CZ) {
-      gcount[g[2]]++;
-      adj[g[1]][g[2]]++;
-      adj[g[2]][g[1]]++;
-    }
-  }
+  std::vector<int> nc_gates(n, 0), ncut(n, 0), marg(n, 0), in_hub(n, 0);
   for (auto& c : p.cuts) ncut[c.qubit]++;
   for (auto q : p.marginal) marg[q] = 1;
   double hub_v = 1.0, other_v = 0.0;
@@ -50,45 +82,29 @@ int featurize(const Problem& p0, const std::vector<ccs_cut>& cuts, std::vector<f
     // per-wire gate counts of non-Clifford fragments
     if (!f.clifford) {
       std::vector<int> per(f.n(), 0);
-      for (auto& g : f.gates) {
-        per[g[1]]++;
-        if (g[2] >= 0) per[g[2]]++;
+      for (auto& gt : f.gates) {
+        per[gt[1]]++;
+        if (gt[2] >= 0) per[gt[2]]++;
       }
       for (int li = 0; li < f.n(); ++li) nc_gates[f.wires[li].first] += per[li];
     }
     if (hub)
-      for (auto& w : f.wires) {
-        const int q = (int)w.first;
-        int last = 0;
-        for (auto& c : p.cuts)
-          if ((int)c.qubit == q) ++last;
-        if ((int)w.second == last) in_hub[q] = 1;
+      for (auto& wr : f.wires) {
+        const int q = (int)wr.first;
+        if ((int)wr.second == ncut[q]) in_hub[q] = 1;     // the qubit's last segment
       }
   }
   x.assign((size_t)n * 8, 0.f);
-  rowptr.assign(n + 1, 0);
-  col.clear();
-  val.clear();
-  val_t.clear();
-  std::vector<double> deg(n, 0.0);
-  for (int q = 0; q < n; ++q)
-    for (auto& e : adj[q]) deg[q] += e.second;
   for (int q = 0; q < n; ++q) {
     float* r = &x[(size_t)q * 8];
     r[0] = 1.f;
-    r[1] = tcount[q] / 4.f;
-    r[2] = adj[q].size() / 4.f;
-    r[3] = gcount[q] / 100.f;
-    r[4] = gcount[q] ? (float)nc_gates[q] / (float)gcount[q] : 0.f;
+    r[1] = g.tcount[q] / 4.f;
+    r[2] = (g.rowptr[q + 1] - g.rowptr[q]) / 4.f;
+    r[3] = g.gcount[q] / 100.f;
+    r[4] = g.gcount[q] ? (float)nc_gates[q] / (float)g.gcount[q] : 0.f;
     r[5] = (float)ncut[q];
     r[6] = (float)marg[q];
     r[7] = (float)in_hub[q];
-    for (auto& e : adj[q]) {
-      col.push_back(e.first);
-      val.push_back((float)(e.second / deg[q]));
-      val_t.push_back((float)(e.second / deg[e.first]));
-    }
-    rowptr[q + 1] = (int)col.size();
   }
   const double k = (double)p.cuts.size();
   glob = {(float)(k / 8.0),
@@ -99,6 +115,19 @@ int featurize(const Problem& p0, const std::vector<ccs_cut>& cuts, std::vector<f
           (float)(std::log2((double)n) / 9.0),
           (float)(std::log2(1.0 + (double)p.gates.size()) / 17.0),
           (float)(frags.size() / 8.0)};
+  return CCS_OK;
+}
+
+int featurize(const Problem& p0, const std::vector<ccs_cut>& cuts, std::vector<float>& x, std::vector<int>& rowptr,
+              std::vector<int>& col, std::vector<float>& val, std::vector<float>& val_t, std::vector<float>& glob,
+              std::string& err) {
+  GraphBase g = graph_base(p0);
+  int rc = featurize_nodes(p0, g, cuts, x, glob, err);
+  if (rc != CCS_OK) return rc;
+  rowptr = std::move(g.rowptr);
+  col = std::move(g.col);
+  val = std::move(g.val);
+  val_t = std::move(g.val_t);
   return CCS_OK;
 }
 

@@ -117,6 +117,9 @@ struct DevRes {
   double* marg;
   double* zexp;
   uint8_t* qnz;            // stitched results: per Clifford hub operand row, 1 unless identically zero
+  int hub_i16;             // sampled results (<= 32767 shots): the Clifford hubs' operands hold their
+                           // signed count sums as int16 (value = sum x hub_scale), half the bytes
+  float hub_scale;         // 1 / shots
   unsigned int* work;         // persistent-kernel work counters
   unsigned int* status;       // device-side error word
 };
@@ -147,6 +150,22 @@ struct EvalParams {
   int hub_sampler;            // host only: the caller's hub sampler choice (0 automatic)
   double inv_shots;
 };
+
+// Read view of a hub's contraction operand (Q^T, row-major K x M) from
+// float index `off` of TQ on: FP32, or int16 count sums times the scale.
+struct HubView {
+  const float* f;
+  const int16_t* h;
+  float scale;
+  __device__ __forceinline__ float at(long long i) const { return h ? (float)h[i] * scale : f[i]; }
+};
+__device__ __forceinline__ HubView hub_view(const DevRes& R, const FragDev& H, long long off) {
+  HubView v;
+  v.f = R.TQ + off;
+  v.h = (R.hub_i16 && H.clifford) ? reinterpret_cast<const int16_t*>(R.TQ + H.T_off) + (off - H.T_off) : nullptr;
+  v.scale = R.hub_scale;
+  return v;
+}
 
 // Kernels the library has launched in this process; a replayed CUDA graph
 // adds its kernel nodes once per replay.

@@ -144,4 +144,15 @@ int greedy_cuts(const Problem& p, const CutSearchOpts& o, std::vector<CutCandida
                 std::string& err);
 double plan_cost(const Problem& p, const std::vector<ccs_cut>& cuts, bool* ok);
 
+// The learned scorer's input graph: the candidate-independent interaction
+// graph (CSR of A = D^-1 Adj and of A^T's values, per-qubit gate counts)
+// once per circuit, the node and global features per candidate cut set.
+struct GraphBase {
+  std::vector<int> rowptr, col, tcount, gcount;
+  std::vector<float> val, val_t;
+};
+GraphBase graph_base(const Problem& p);
+int featurize_nodes(const Problem& p, const GraphBase& g, const std::vector<ccs_cut>& cuts, std::vector<float>& x,
+                    std::vector<float>& glob, std::string& err);
+
 }  // namespace ccs

@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(256) gemm_splitk_kernel(DevPlan P, DevRes R, i
     const long long k0 = max(s0, kr.lo_of(K)), k1 = min(min(s0 + kchunk, K), kr.hi_of(K));
     float* As = sm;                  // kTK x TM
     float* Bs = sm + kTK * TM;       // kTK x TN
-    const float* At = R.TQ + Hb.T_off;       // the hub's Q stored transposed: K x M, row-major
+    const HubView At = hub_view(R, Hb, Hb.T_off);   // the hub's Q stored transposed: K x M, row-major
     const float* Bm = scratch + Pb.r_off;    // K x N, row-major
     const int tn4 = TN >> 2;
     const bool act = (int)threadIdx.x < (TM >> 2) * tn4;
@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(256) gemm_splitk_kernel(DevPlan P, DevRes R, i
       for (int t = threadIdx.x; t < TM * kTK; t += blockDim.x) {
         const int m = t % TM, k = t / TM;
         const long long gm = (long long)mt * TM + m, gk = kk + k;
-        float v = (gm < M && gk < k1) ? At[gk * M + gm] : 0.f;
+        float v = (gm < M && gk < k1) ? At.at(gk * M + gm) : 0.f;
         if (precision == CCS_BF16) v = to_bf16f(v);
         As[k * TM + m] = v;
       }
@@ -349,6 +349,21 @@ __global__ void __launch_bounds__(256) gemm_splitk_kernel(DevPlan P, DevRes R, i
 // the hub values to bf16 (R is rounded when it is built).
 constexpr int kStreamChunk = 256;   // R rows staged per pass
 
+// Four consecutive hub operand entries as floats: FP32 as stored, or the
+// int16 count sums themselves (the streaming GEMMs apply 1/shots once to
+// each accumulator at the end: exact when the shots are a power of two).
+__device__ __forceinline__ float4 hub4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ float4 hub4(const int16_t* p) {
+  const short4 v = *reinterpret_cast<const short4*>(p);
+  return make_float4((float)v.x, (float)v.y, (float)v.z, (float)v.w);
+}
+__device__ __forceinline__ float4 hub4_stream(const float* p) { return __ldcs(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ float4 hub4_stream(const int16_t* p) {
+  const int2 w = __ldcs(reinterpret_cast<const int2*>(p));
+  return make_float4((float)(short)(w.x & 0xffff), (float)(short)((unsigned)w.x >> 16), (float)(short)(w.y & 0xffff),
+                     (float)(short)((unsigned)w.y >> 16));
+}
+
 template <int NN>
 __device__ __forceinline__ void stream_fma(float (&acc)[4][NN], float4 a, const float* rrow, int bf16) {
   if (bf16) { a.x = to_bf16f(a.x); a.y = to_bf16f(a.y); a.z = to_bf16f(a.z); a.w = to_bf16f(a.w); }
@@ -372,11 +387,11 @@ __device__ __forceinline__ void stream_fma(float (&acc)[4][NN], float4 a, const 
   }
 }
 
-template <int NN>
-__global__ void __launch_bounds__(256, 2) gemm_stream_kernel(const float* __restrict__ At, const float* __restrict__ Rm,
-                                                             int M, long long K, long long kchunk, int mblocks,
-                                                             float* __restrict__ part, int bf16,
-                                                             const uint8_t* __restrict__ live, KRange kr) {
+template <int NN, class T>
+__global__ void __launch_bounds__(256, 2) gemm_stream_kernel(const T* __restrict__ At, float sc,
+                                                             const float* __restrict__ Rm, int M, long long K,
+                                                             long long kchunk, int mblocks, float* __restrict__ part,
+                                                             int bf16, const uint8_t* __restrict__ live, KRange kr) {
   __shared__ __align__(16) float Rs[kStreamChunk * NN];
   __shared__ __align__(8) uint8_t Ls[kStreamChunk];     // row flags of the chunk (stitched operands)
   const int mb = blockIdx.x % mblocks, split = blockIdx.x / mblocks;
@@ -398,7 +413,7 @@ __global__ void __launch_bounds__(256, 2) gemm_stream_kernel(const float* __rest
       if (!live || live[kc + i / NN]) Rs[i] = Rm[kc * NN + i];
     __syncthreads();
     if (!act) continue;
-    const float* ap = At + kc * M + m;
+    const T* ap = At + kc * M + m;
     int r = 0;
     for (; r + 8 <= rows; r += 8) {
       if (live) {        // rows flagged zero are skipped (they may never have been written)
@@ -407,26 +422,25 @@ __global__ void __launch_bounds__(256, 2) gemm_stream_kernel(const float* __rest
 #pragma unroll
         for (int u = 0; u < 8; ++u)
           if ((l8 >> (8 * u)) & 0xffull)
-            stream_fma<NN>(acc, __ldcs(reinterpret_cast<const float4*>(ap + (long long)(r + u) * M)),
-                           Rs + (r + u) * NN, bf16);
+            stream_fma<NN>(acc, hub4_stream(ap + (long long)(r + u) * M), Rs + (r + u) * NN, bf16);
         continue;
       }
       float4 a[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) a[u] = __ldcs(reinterpret_cast<const float4*>(ap + (long long)(r + u) * M));
+      for (int u = 0; u < 8; ++u) a[u] = hub4_stream(ap + (long long)(r + u) * M);
 #pragma unroll
       for (int u = 0; u < 8; ++u) stream_fma<NN>(acc, a[u], Rs + (r + u) * NN, bf16);
     }
     for (; r < rows; ++r)
       if (!live || Ls[r])
-        stream_fma<NN>(acc, __ldcs(reinterpret_cast<const float4*>(ap + (long long)r * M)), Rs + r * NN, bf16);
+        stream_fma<NN>(acc, hub4_stream(ap + (long long)r * M), Rs + r * NN, bf16);
   }
   if (!act) return;
   float* dst = part + ((long long)split * M + m) * NN;    // 4 x NN contiguous floats
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < NN; ++j) dst[i * NN + j] = acc[i][j];
+    for (int j = 0; j < NN; ++j) dst[i * NN + j] = acc[i][j] * sc;
 }
 
 // The same split-K product for dense operands with the loads moved off the
@@ -457,15 +471,15 @@ __device__ __forceinline__ bool bulk_wait(uint64_t* bar, uint32_t phase) {
   }
 }
 
-template <int NN>
-__global__ void __launch_bounds__(288, 2) gemm_stream_bulk_kernel(const float* __restrict__ At,
+template <int NN, class T>
+__global__ void __launch_bounds__(288, 2) gemm_stream_bulk_kernel(const T* __restrict__ At, float sc,
                                                                  const float* __restrict__ Rm, int M, long long K,
                                                                  long long kchunk, int mblocks, float* __restrict__ part,
                                                                  int bf16, KRange kr, unsigned* status) {
   extern __shared__ __align__(128) uint8_t bulk_smem[];
   const int nc = (int)blockDim.x - 32;                  // consumer threads, 4 hub outputs each
-  const int row_bytes = nc * 16;
-  float* A_s = reinterpret_cast<float*>(bulk_smem);                                   // [stage][row][4 nc]
+  const int row_bytes = nc * 4 * (int)sizeof(T);
+  T* A_s = reinterpret_cast<T*>(bulk_smem);                                           // [stage][row][4 nc]
   float* R_s = reinterpret_cast<float*>(bulk_smem + kBulkStages * kBulkRows * row_bytes);   // [stage][row][NN]
   uint64_t* full = reinterpret_cast<uint64_t*>(bulk_smem + kBulkStages * kBulkRows * (row_bytes + NN * 4));
   uint64_t* empty = full + kBulkStages;
@@ -534,10 +548,9 @@ __global__ void __launch_bounds__(288, 2) gemm_stream_bulk_kernel(const float* _
     }
     const long long r0 = k0 + (long long)i * kBulkRows;
     const int rows = (int)min((long long)kBulkRows, k1 - r0);
-    const float* as = A_s + (size_t)st * kBulkRows * nc * 4 + threadIdx.x * 4;
+    const T* as = A_s + (size_t)st * kBulkRows * nc * 4 + threadIdx.x * 4;
     const float* rs = R_s + (size_t)st * kBulkRows * NN;
-    for (int r = 0; r < rows; ++r)
-      stream_fma<NN>(acc, *reinterpret_cast<const float4*>(as + (size_t)r * nc * 4), rs + r * NN, bf16);
+    for (int r = 0; r < rows; ++r) stream_fma<NN>(acc, hub4(as + (size_t)r * nc * 4), rs + r * NN, bf16);
     __syncwarp();
     if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[st])) : "memory");
   }
@@ -548,55 +561,73 @@ __global__ void __launch_bounds__(288, 2) gemm_stream_bulk_kernel(const float* _
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < NN; ++j) dst[i * NN + j] = good ? acc[i][j] : 0.f;
+    for (int j = 0; j < NN; ++j) dst[i * NN + j] = good ? acc[i][j] * sc : 0.f;
 }
 
-template <int NN>
-static cudaError_t launch_stream_nn(const float* At, const float* Rm, const ProblemDev& Pb, float* part, int bf16,
-                                    const uint8_t* live, KRange kr, unsigned* status, cudaStream_t s) {
+template <int NN, class T>
+static cudaError_t launch_stream_nn(const T* At, float sc, const float* Rm, const ProblemDev& Pb, float* part,
+                                    int bf16, const uint8_t* live, KRange kr, unsigned* status, cudaStream_t s) {
   long long kchunk = (Pb.K + Pb.ssplits - 1) / Pb.ssplits;
   kchunk = (kchunk + 7) & ~7ll;
   const long long splits = (Pb.K + kchunk - 1) / kchunk;    // every split but the last is full
   const bool bulk = NN >= 4 && live == nullptr && Pb.sthreads % 32 == 0 && status != nullptr &&
                     (reinterpret_cast<uintptr_t>(At) & 15) == 0 && (reinterpret_cast<uintptr_t>(Rm) & 15) == 0 &&
-                    (Pb.M * 4) % 16 == 0;
+                    (Pb.M * sizeof(T)) % 16 == 0;
   if (bulk) {   // dense operand: rows streamed by the TMA engine into a shared-memory ring
-    const size_t smem = (size_t)kBulkStages * kBulkRows * (Pb.sthreads * 16 + NN * 4) + 2 * kBulkStages * 8 + 16;
+    const size_t smem =
+        (size_t)kBulkStages * kBulkRows * (Pb.sthreads * 4 * sizeof(T) + NN * 4) + 2 * kBulkStages * 8 + 16;
     cudaError_t err =
-        cudaFuncSetAttribute(gemm_stream_bulk_kernel<NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(gemm_stream_bulk_kernel<NN, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    gemm_stream_bulk_kernel<NN><<<(unsigned)(Pb.smblocks * splits), Pb.sthreads + 32, smem, s>>>(
-        At, Rm, Pb.M, Pb.K, kchunk, Pb.smblocks, part, bf16, kr, status);
+    gemm_stream_bulk_kernel<NN, T><<<(unsigned)(Pb.smblocks * splits), Pb.sthreads + 32, smem, s>>>(
+        At, sc, Rm, Pb.M, Pb.K, kchunk, Pb.smblocks, part, bf16, kr, status);
   } else {
-    gemm_stream_kernel<NN><<<(unsigned)(Pb.smblocks * splits), Pb.sthreads, 0, s>>>(At, Rm, Pb.M, Pb.K, kchunk,
-                                                                                    Pb.smblocks, part, bf16, live, kr);
+    gemm_stream_kernel<NN, T><<<(unsigned)(Pb.smblocks * splits), Pb.sthreads, 0, s>>>(
+        At, sc, Rm, Pb.M, Pb.K, kchunk, Pb.smblocks, part, bf16, live, kr);
   }
   note_launch();
   return cudaGetLastError();
 }
 
-static cudaError_t launch_stream(const DevRes& r, const ProblemDev& Pb, float* scratch, int bf16, int stitched,
-                                 KRange kr, cudaStream_t s) {
-  const float* At = r.TQ + Pb.hub_T_off;
+// The hub operand of a problem as the host sees it (a Clifford hub's sampled
+// operand holds int16 count sums).
+static HubView hub_host_view(const DevRes& r, const ProblemDev& Pb) {
+  HubView v;
+  v.f = r.TQ + Pb.hub_T_off;
+  v.h = (r.hub_i16 && Pb.hub_qrow_off >= 0) ? reinterpret_cast<const int16_t*>(r.TQ + Pb.hub_T_off) : nullptr;
+  v.scale = r.hub_scale;
+  return v;
+}
+
+template <class T>
+static cudaError_t launch_stream_t(const T* At, float sc, const DevRes& r, const ProblemDev& Pb, float* scratch,
+                                   int bf16, int stitched, KRange kr, cudaStream_t s) {
   const float* Rm = scratch + Pb.r_off;
   float* part = scratch + Pb.part_off;
   const uint8_t* live = (stitched && Pb.hub_qrow_off >= 0) ? r.qnz + Pb.hub_qrow_off : nullptr;
   switch (Pb.N) {
-    case 1: return launch_stream_nn<1>(At, Rm, Pb, part, bf16, live, kr, r.status, s);
-    case 2: return launch_stream_nn<2>(At, Rm, Pb, part, bf16, live, kr, r.status, s);
-    case 4: return launch_stream_nn<4>(At, Rm, Pb, part, bf16, live, kr, r.status, s);
-    case 8: return launch_stream_nn<8>(At, Rm, Pb, part, bf16, live, kr, r.status, s);
-    case 16: return launch_stream_nn<16>(At, Rm, Pb, part, bf16, live, kr, r.status, s);
+    case 1: return launch_stream_nn<1>(At, sc, Rm, Pb, part, bf16, live, kr, r.status, s);
+    case 2: return launch_stream_nn<2>(At, sc, Rm, Pb, part, bf16, live, kr, r.status, s);
+    case 4: return launch_stream_nn<4>(At, sc, Rm, Pb, part, bf16, live, kr, r.status, s);
+    case 8: return launch_stream_nn<8>(At, sc, Rm, Pb, part, bf16, live, kr, r.status, s);
+    case 16: return launch_stream_nn<16>(At, sc, Rm, Pb, part, bf16, live, kr, r.status, s);
     default: return cudaErrorInvalidValue;
   }
+}
+
+static cudaError_t launch_stream(const DevRes& r, const ProblemDev& Pb, float* scratch, int bf16, int stitched,
+                                 KRange kr, cudaStream_t s) {
+  const HubView v = hub_host_view(r, Pb);
+  if (v.h) return launch_stream_t(v.h, v.scale, r, Pb, scratch, bf16, stitched, kr, s);
+  return launch_stream_t(v.f, 1.0f, r, Pb, scratch, bf16, stitched, kr, s);
 }
 
 // BF16 K-major copy of a hub operand for the tensor-core GEMM:
 // Qh[o][D] = bf16(Q^T[D][o]), through 64 x 64 shared-memory tiles: each
 // warp reads 256 contiguous bytes of a Q^T row (o fastest) and writes 128
 // contiguous bytes of a Qh row as bf16 pairs (D fastest).
-__global__ void __launch_bounds__(256) hub_bf16_kernel(const float* __restrict__ QT, __nv_bfloat16* __restrict__ Qh,
-                                                       int M, long long K) {
+__global__ void __launch_bounds__(256) hub_bf16_kernel(HubView QT, __nv_bfloat16* __restrict__ Qh, int M,
+                                                       long long K) {
   __shared__ float tile[64][65];
   const long long tiles_d = (K + 63) / 64, tiles_o = (M + 63) / 64;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;   // 8 warps
@@ -608,7 +639,7 @@ __global__ void __launch_bounds__(256) hub_bf16_kernel(const float* __restrict__
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int o = o0 + lane + 32 * h;
-        tile[r][lane + 32 * h] = (d < K && o < M) ? QT[d * M + o] : 0.f;
+        tile[r][lane + 32 * h] = (d < K && o < M) ? QT.at(d * M + o) : 0.f;
       }
     }
     __syncthreads();
@@ -797,7 +828,8 @@ __global__ void __launch_bounds__(512) contract_kernel(DevPlan P, DevRes R, int 
     const int m0 = di.y * M, Mfull = Pb.M;
     const int K = (int)Pb.K;
     const long long klo = krg.lo_of(K), khi = krg.hi_of(K);   // cut-index terms summed
-    const float* At = R.TQ + Pb.hub_T_off + m0;  // the hub's Q stored transposed: K x Mfull, row-major
+    // the hub's Q stored transposed: K x Mfull, row-major (this slice's columns from m0)
+    const HubView At = hub_view(R, P.frags[Pb.frag0 + Pb.hub], Pb.hub_T_off + m0);
     load_problem(P, Pb, S);
     __syncthreads();
     float* X = s_buf;
@@ -826,7 +858,7 @@ __global__ void __launch_bounds__(512) contract_kernel(DevPlan P, DevRes R, int 
           const int t = t0 + u * blockDim.x;
           if (t < K * M) {
             const long long kk = expand(t >> lm, 0);
-            v[u] = (kk >= klo && kk < khi) ? At[kk * Mfull + (t & (M - 1))] : 0.f;
+            v[u] = (kk >= klo && kk < khi) ? At.at(kk * Mfull + (t & (M - 1))) : 0.f;
           }
         }
 #pragma unroll
@@ -867,7 +899,7 @@ __global__ void __launch_bounds__(512) contract_kernel(DevPlan P, DevRes R, int 
               int kg = 0;
               for (int i = 0; i < S.ns[l]; ++i) kg |= ((g >> (2 * i)) & 3) << (2 * S.slot_cut[l][i]);
               const long long kk = (long long)(kr | kg);
-              a[u] = (g < G && kk >= klo && kk < khi) ? At[kk * Mfull + outer] : 0.f;
+              a[u] = (g < G && kk >= klo && kk < khi) ? At.at(kk * Mfull + outer) : 0.f;
             }
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
@@ -984,7 +1016,7 @@ cudaError_t launch_recombine(const DevPlan& p, const DevRes& r, int precision, c
         {
           const long long tiles = ((Pb.K + 63) / 64) * ((Pb.M + 63) / 64);
           hub_bf16_kernel<<<(unsigned)(tiles < 152 * 32 ? tiles : 152 * 32), 256, 0, s>>>(
-              r.TQ + Pb.hub_T_off, reinterpret_cast<__nv_bfloat16*>(r.TQh) + Pb.hub_T_off, Pb.M, Pb.K); note_launch();
+              hub_host_view(r, Pb), reinterpret_cast<__nv_bfloat16*>(r.TQh) + Pb.hub_T_off, Pb.M, Pb.K); note_launch();
           if ((err = cudaGetLastError()) != cudaSuccess) return err;
         }
         err = launch_gemm_tc(r.TQh + Pb.hub_T_off, z.rt_scratch + Pb.rt_off, Pb.M, Pb.N, Pb.K, Pb.splits,

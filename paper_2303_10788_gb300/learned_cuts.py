@@ -264,23 +264,29 @@ def main(argv=None):
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--seed", type=int, default=SEED)
     ap.add_argument("--weights", default=None, help="write the trained parameters (npz)")
+    ap.add_argument("--load", default=None, help="evaluate these trained parameters (npz) instead of training")
     ap.add_argument("--report", default=None, help="write the evaluation report (json)")
     a = ap.parse_args(argv)
     t0 = time.time()
-    ws_tr = population(a.train, a.seed)
+    ws_tr = population(a.train, a.seed) if not a.load else []
     ws_te = population(a.test, a.seed + 1_000_003)
-    c_tr = candidates(ws_tr, a.cands)
+    c_tr = candidates(ws_tr, a.cands) if ws_tr else []
     c_te = candidates(ws_te, a.cands)
     print(f"candidates: {time.time() - t0:.0f} s", flush=True)
     from paper_2303_10788_gb300 import ccs
     ctx = ccs.ccs_create(0)
     dropped = {}
-    graphs, target, _ = make_dataset(ctx, ws_tr, c_tr, a.judge, a.max_cuts, dropped=dropped)
-    print(f"dataset: {len(graphs)} samples, {time.time() - t0:.0f} s; dropped {dropped}", flush=True)
-    net = ccs.ccs_mpnn_create(ctx, seed=a.seed)
-    mu, sd = train(ctx, net, graphs, target, a.epochs, a.batch, a.lr, a.seed)
+    if a.load:
+        net = ccs.load_cut_scorer(ctx, a.load)
+        graphs, mu, sd = [], float("nan"), float("nan")
+    else:
+        graphs, target, _ = make_dataset(ctx, ws_tr, c_tr, a.judge, a.max_cuts, dropped=dropped)
+        print(f"dataset: {len(graphs)} samples, {time.time() - t0:.0f} s; dropped {dropped}", flush=True)
+        net = ccs.ccs_mpnn_create(ctx, seed=a.seed)
+        mu, sd = train(ctx, net, graphs, target, a.epochs, a.batch, a.lr, a.seed)
     rep = evaluate(ctx, net, ws_te, c_te, a.judge, a.max_cuts)
-    rep.update({"train_circuits": a.train, "train_samples": len(graphs), "train_dropped_candidates": dropped,
+    rep.update({"train_circuits": 0 if a.load else a.train, "loaded": a.load, "train_samples": len(graphs),
+                "train_dropped_candidates": dropped,
                 "target_mean": mu, "target_std": sd, "seconds": time.time() - t0})
     print(json.dumps({k: v for k, v in rep.items() if k != "rows"}), flush=True)
     if a.weights:
