@@ -372,7 +372,7 @@ def _ncu_traffic(kernel, workload):
     return None
 
 
-STAGE_KERNEL = {"sample": "sample_hub8_kernel", "recombine": "gemm_stream_bulk_kernel", "clifford": "body_basis_kernel"}
+STAGE_KERNEL = {"sample": "sample_hub8_kernel", "recombine": "gemm_fact_bulk_kernel", "clifford": "body_basis_kernel"}
 
 
 def stage_kernel(st, precision):

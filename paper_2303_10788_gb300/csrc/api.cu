@@ -833,6 +833,30 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
             d.smblocks = (d.M / 4 + d.sthreads - 1) / d.sthreads;
             const long long max_ss = std::max(1ll, d.K / 64);
             d.ssplits = (int)std::max(1ll, std::min(max_ss, (long long)(target + d.smblocks - 1) / d.smblocks));
+            // the first leaf (lowest leaf-output bits) with 1-4 cuts and 1-2 marginal bits
+            // is contracted while streaming
+            int l1 = 0;
+            while (l1 < d.n_frags && l1 == P.hub) ++l1;
+            if (l1 < d.n_frags) {
+              const FragDev& L = plan->fdev[f0 + l1];
+              const int N1 = 1 << L.m, G1 = 1 << (2 * L.n_slots);
+              if (L.n_slots >= 1 && L.n_slots <= 2 && N1 <= 2 && d.N % N1 == 0 && d.N / N1 >= 1) {
+                d.fact = 1;
+                d.fl1 = l1;
+                d.fl1_T_off = L.T_off;
+                d.G1 = G1;
+                d.N1 = N1;
+                d.NR = d.N / N1;
+                d.ndig1 = L.n_slots;
+                for (int i = 0; i < L.n_slots; ++i) d.dig1[i] = L.slot_cut[i];
+                d.ndigr = 0;
+                for (int cc = 0; cc < d.k; ++cc) {
+                  bool mine = false;
+                  for (int i = 0; i < L.n_slots; ++i) mine = mine || L.slot_cut[i] == cc;
+                  if (!mine) d.digr[d.ndigr++] = cc;
+                }
+              }
+            }
           }
           plan->chain = 1;
           d.r_off = plan->r_total;

@@ -66,6 +66,13 @@ struct ProblemDev {
   // streaming CUDA-core GEMM of a wide hub (FP32, or BF16 off the tensor cores):
   // sthreads threads x 4 hub outputs per CTA, smblocks CTAs across M, ssplits across K
   int stream, sthreads, smblocks, ssplits;
+  // the first leaf contracted while streaming (FP32, full range, dense rows):
+  // its G1 = 4^s1 cut-digit rows per group against its table (N1 outputs),
+  // then the other leaves' product table Rrest[group][NR] (NR = N / N1)
+  int fact, fl1, G1, N1, NR;
+  long long fl1_T_off;     // T_off of that leaf (its table T'[x1][g1])
+  int ndig1, ndigr;
+  int dig1[kMaxCuts], digr[kMaxCuts];   // cut positions of the leaf's digits / of the other digits
 };
 
 // Device views of a plan + result.

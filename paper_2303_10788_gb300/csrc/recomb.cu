@@ -233,8 +233,14 @@ cudaError_t launch_operands(const DevPlan& p, const DevRes& r, const EvalParams&
 // by 2^-k and scattered to marginal order.  BF16 mode rounds both operands to
 // bf16 (as a bf16 tensor-core GEMM would) with FP32 accumulation.
 
+// Whether a problem's FP32 contraction takes the first-leaf streaming path
+// (dense rows, full cut-index range; its Rrest table then replaces R).
+static __host__ __device__ bool fact_path(const ProblemDev& Pb, int precision, int stitched, bool full_range) {
+  return Pb.stream && Pb.fact && !Pb.direct && precision == CCS_FP32 && !stitched && full_range;
+}
+
 __global__ void build_r_kernel(DevPlan P, DevRes R, int precision, const long long* prefix, int np,
-                               long long total, float* scratch, uint16_t* rt_scratch, int stitched) {
+                               long long total, float* scratch, uint16_t* rt_scratch, int stitched, int full_range) {
   for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
        g += (long long)gridDim.x * blockDim.x) {
     const int pi = find_seg(prefix, np, g);
@@ -242,8 +248,10 @@ __global__ void build_r_kernel(DevPlan P, DevRes R, int precision, const long lo
     const long long loc = g - prefix[pi];
     const long long Pp = loc / Pb.N;
     const long long ol = loc - Pp * Pb.N;
-    // a streamed stitched hub reads no R row of a zero operand row
+    // a streamed stitched hub reads no R row of a zero operand row; a problem
+    // on the first-leaf path builds its own smaller table instead of R
     if (stitched && Pb.stream && Pb.hub_qrow_off >= 0 && !R.qnz[Pb.hub_qrow_off + Pp]) continue;
+    if (fact_path(Pb, precision, stitched, full_range != 0) && !(rt_scratch && Pb.tc)) continue;
     float v = 1.f;
     int off = 0;
     for (int l = 0; l < Pb.n_frags; ++l) {
@@ -564,12 +572,200 @@ __global__ void __launch_bounds__(288, 2) gemm_stream_bulk_kernel(const T* __res
     for (int j = 0; j < NN; ++j) dst[i * NN + j] = good ? acc[i][j] * sc : 0.f;
 }
 
+// --- the first leaf contracted while streaming --------------------------
+// For a star whose first leaf l1 (the lowest leaf-output bits) owns s1 <= 2
+// cuts and N1 <= 2 marginal outputs, the Kronecker operand factorises as
+//   R[P][x1 + N1 xr] = T'_l1[x1][g1(P)] Rrest[rest(P)][xr],
+// g1 the leaf's cut digits of P and rest the others.  So the G1 = 4^s1 rows
+// of one rest value (a group) contract first against the leaf's table,
+//   Y[m][x1] = sum_g1 Q^T[P(g1, rest)][m] T'_l1[x1][g1],
+// and only then meet the other leaves: acc[m][x1 + N1 xr] += Y[m][x1]
+// Rrest[rest][xr] -- 4 (N1 G1 + N) FMA per group and 4 hub outputs instead
+// of 4 G1 N: 12 instead of 64 per operand row at config 3.  Rows are fetched
+// one group per pipeline stage by the TMA engine (bulk copies of each row's
+// CTA slice), as in gemm_stream_bulk_kernel; FP32, dense rows, full range.
+struct FactDigits {
+  int ndig1, ndigr;
+  int dig1[kMaxCuts], digr[kMaxCuts];
+};
+
+__device__ __forceinline__ long long scatter_digits(long long v, int nd, const int* pos) {
+  long long p = 0;
+  for (int j = 0; j < nd; ++j) p |= ((v >> (2 * j)) & 3ll) << (2 * pos[j]);
+  return p;
+}
+
+// Rrest[group][xr] = prod over the leaves after l1 of T'_l[x_l][g_l(P)], P the
+// group's rest digits (the first leaf's digits zero), x_l the leaves' bits of xr.
+__global__ void build_rrest_kernel(DevPlan P, DevRes R, ProblemDev Pb, FactDigits dg, float* __restrict__ rr,
+                                   long long total) {
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
+       g += (long long)gridDim.x * blockDim.x) {
+    const long long grp = g / Pb.NR;
+    const int xr = (int)(g - grp * Pb.NR);
+    const long long Pp = scatter_digits(grp, dg.ndigr, dg.digr);
+    float v = 1.f;
+    int off = 0;
+    for (int l = 0; l < Pb.n_frags; ++l) {
+      if (l == Pb.hub || l == Pb.fl1) continue;
+      const FragDev& L = P.frags[Pb.frag0 + l];
+      const int x = (xr >> off) & ((1 << L.m) - 1);
+      off += L.m;
+      int pl = 0;
+      for (int i = 0; i < L.n_slots; ++i) pl |= (int)((Pp >> (2 * L.slot_cut[i])) & 3) << (2 * i);
+      v *= R.TQ[L.T_off + ((long long)x << (2 * L.n_slots)) + pl];
+    }
+    rr[g] = v;
+  }
+}
+
+template <int N1, int NR, class T>
+__global__ void __launch_bounds__(288, 2) gemm_fact_bulk_kernel(const T* __restrict__ At, float sc,
+                                                                const float* __restrict__ T1, int G1,
+                                                                const float* __restrict__ Rr, int M, long long ngroups,
+                                                                long long gchunk, int mblocks, int stages,
+                                                                float* __restrict__ part, FactDigits dg,
+                                                                unsigned* status) {
+  constexpr int N = N1 * NR;
+  extern __shared__ __align__(128) uint8_t fact_smem[];
+  const int nc = (int)blockDim.x - 32;                  // consumer threads, 4 hub outputs each
+  const int row_bytes = nc * 4 * (int)sizeof(T);
+  const int stage_bytes = G1 * row_bytes;
+  T* A_s = reinterpret_cast<T*>(fact_smem);
+  float* T1s = reinterpret_cast<float*>(fact_smem + (size_t)stages * stage_bytes);   // [x1][g1]
+  uint64_t* full = reinterpret_cast<uint64_t*>(T1s + ((N1 * G1 + 1) & ~1));
+  uint64_t* empty = full + stages;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + stages);
+  const int mb = blockIdx.x % mblocks, split = blockIdx.x / mblocks;
+  const long long gr0 = (long long)split * gchunk, gr1 = min(ngroups, gr0 + gchunk);
+  const int nstage = gr1 > gr0 ? (int)(gr1 - gr0) : 0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, cw = nc >> 5;
+  const int m0 = mb * nc * 4;
+  for (int i = threadIdx.x; i < N1 * G1; i += blockDim.x) T1s[i] = T1[i];
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < stages; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[i])), "r"(1) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[i])), "r"(cw) : "memory");
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (warp == cw) {                                     // producer warp
+    if (lane == 0) {
+      int issued = 0;
+      for (int i = 0; i < nstage; ++i) {
+        const int st = i % stages;
+        if (i >= stages && !bulk_wait(&empty[st], ((i / stages) - 1) & 1)) {
+          atomicOr(status, 8u);
+          *abort_flag = 1;
+        }
+        if (*abort_flag) break;
+        const long long prest = scatter_digits(gr0 + i, dg.ndigr, dg.digr);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&full[st])),
+                     "r"((uint32_t)stage_bytes)
+                     : "memory");
+        for (int g = 0; g < G1; ++g) {
+          const long long row = prest | scatter_digits(g, dg.ndig1, dg.dig1);
+          asm volatile(
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                  smem_u32(A_s + ((size_t)st * G1 + g) * nc * 4)),
+              "l"(At + row * M + m0), "r"(row_bytes), "r"(smem_u32(&full[st]))
+              : "memory");
+        }
+        issued = i + 1;
+      }
+      if (*abort_flag)      // let copies already issued land before the shared memory is released
+        for (int i = max(0, issued - stages); i < issued; ++i) bulk_wait(&full[i % stages], (i / stages) & 1);
+    }
+    return;
+  }
+  float acc[4][N];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < N; ++j) acc[i][j] = 0.f;
+  for (int i = 0; i < nstage; ++i) {
+    const int st = i % stages;
+    bool ok = !*abort_flag && bulk_wait(&full[st], (i / stages) & 1);
+    ok = __all_sync(0xffffffffu, ok) != 0;
+    if (!ok) {
+      if (lane == 0) { atomicOr(status, 8u); *abort_flag = 1; }
+      break;
+    }
+    float y[4][N1];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int x = 0; x < N1; ++x) y[a][x] = 0.f;
+    const T* as = A_s + (size_t)st * G1 * nc * 4 + threadIdx.x * 4;
+    for (int g = 0; g < G1; ++g) {
+      const float4 v = hub4(as + (size_t)g * nc * 4);
+#pragma unroll
+      for (int x = 0; x < N1; ++x) {
+        const float t = T1s[x * G1 + g];
+        y[0][x] = fmaf(v.x, t, y[0][x]);
+        y[1][x] = fmaf(v.y, t, y[1][x]);
+        y[2][x] = fmaf(v.z, t, y[2][x]);
+        y[3][x] = fmaf(v.w, t, y[3][x]);
+      }
+    }
+    __syncwarp();
+    if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[st])) : "memory");
+    const float* rr = Rr + (gr0 + i) * NR;
+    float rv[NR];
+#pragma unroll
+    for (int xr = 0; xr < NR; ++xr) rv[xr] = __ldg(rr + xr);
+#pragma unroll
+    for (int xr = 0; xr < NR; ++xr)
+#pragma unroll
+      for (int x = 0; x < N1; ++x)
+#pragma unroll
+        for (int a = 0; a < 4; ++a) acc[a][x + N1 * xr] = fmaf(y[a][x], rv[xr], acc[a][x + N1 * xr]);
+  }
+  const int m = m0 + 4 * (int)threadIdx.x;
+  if (m >= M) return;
+  const bool good = !*abort_flag;
+  float* dst = part + ((long long)split * M + m) * N;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < N; ++j) dst[i * N + j] = good ? acc[i][j] * sc : 0.f;
+}
+
+template <int N1, int NR, class T>
+static cudaError_t launch_fact_t(const T* At, float sc, const DevPlan& p, const DevRes& r, const ProblemDev& Pb,
+                                 float* scratch, cudaStream_t s) {
+  FactDigits dg{};
+  dg.ndig1 = Pb.ndig1;
+  dg.ndigr = Pb.ndigr;
+  for (int i = 0; i < kMaxCuts; ++i) { dg.dig1[i] = Pb.dig1[i]; dg.digr[i] = Pb.digr[i]; }
+  const long long ngroups = Pb.K / Pb.G1;
+  float* rr = scratch + Pb.r_off;                 // the group table takes R's place
+  build_rrest_kernel<<<(unsigned)std::min<long long>((ngroups * Pb.NR + 255) / 256, 65535), 256, 0, s>>>(
+      p, r, Pb, dg, rr, ngroups * Pb.NR);
+  note_launch();
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  const long long gchunk = (ngroups + Pb.ssplits - 1) / Pb.ssplits;
+  const long long splits = Pb.ssplits;            // every split writes its partial (zero when empty)
+  const int stage_bytes = Pb.G1 * Pb.sthreads * 4 * (int)sizeof(T);
+  const int stages = std::max(2, std::min(4, (112 << 10) / stage_bytes));
+  const size_t smem = (size_t)stages * stage_bytes + (size_t)((N1 * Pb.G1 + 1) & ~1) * 4 + 2 * stages * 8 + 16;
+  err = cudaFuncSetAttribute(gemm_fact_bulk_kernel<N1, NR, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  gemm_fact_bulk_kernel<N1, NR, T><<<(unsigned)(Pb.smblocks * splits), Pb.sthreads + 32, smem, s>>>(
+      At, sc, r.TQ + Pb.fl1_T_off, Pb.G1, rr, Pb.M, ngroups, gchunk, Pb.smblocks, stages, scratch + Pb.part_off, dg,
+      r.status);
+  note_launch();
+  return cudaGetLastError();
+}
+
 template <int NN, class T>
 static cudaError_t launch_stream_nn(const T* At, float sc, const float* Rm, const ProblemDev& Pb, float* part,
                                     int bf16, const uint8_t* live, KRange kr, unsigned* status, cudaStream_t s) {
-  long long kchunk = (Pb.K + Pb.ssplits - 1) / Pb.ssplits;
-  kchunk = (kchunk + 7) & ~7ll;
-  const long long splits = (Pb.K + kchunk - 1) / kchunk;    // every split but the last is full
+  const long long kchunk = (Pb.K + Pb.ssplits - 1) / Pb.ssplits;
+  const long long splits = Pb.ssplits;         // every split writes its partial (zero when its range is empty)
   const bool bulk = NN >= 4 && live == nullptr && Pb.sthreads % 32 == 0 && status != nullptr &&
                     (reinterpret_cast<uintptr_t>(At) & 15) == 0 && (reinterpret_cast<uintptr_t>(Rm) & 15) == 0 &&
                     (Pb.M * sizeof(T)) % 16 == 0;
@@ -613,6 +809,30 @@ static cudaError_t launch_stream_t(const T* At, float sc, const DevRes& r, const
     case 16: return launch_stream_nn<16>(At, sc, Rm, Pb, part, bf16, live, kr, r.status, s);
     default: return cudaErrorInvalidValue;
   }
+}
+
+template <class T>
+static cudaError_t launch_fact_any(const T* At, float sc, const DevPlan& p, const DevRes& r, const ProblemDev& Pb,
+                                   float* scratch, cudaStream_t s) {
+  switch (Pb.N1 * 32 + Pb.NR) {
+    case 32 + 1: return launch_fact_t<1, 1>(At, sc, p, r, Pb, scratch, s);
+    case 32 + 2: return launch_fact_t<1, 2>(At, sc, p, r, Pb, scratch, s);
+    case 32 + 4: return launch_fact_t<1, 4>(At, sc, p, r, Pb, scratch, s);
+    case 32 + 8: return launch_fact_t<1, 8>(At, sc, p, r, Pb, scratch, s);
+    case 32 + 16: return launch_fact_t<1, 16>(At, sc, p, r, Pb, scratch, s);
+    case 64 + 1: return launch_fact_t<2, 1>(At, sc, p, r, Pb, scratch, s);
+    case 64 + 2: return launch_fact_t<2, 2>(At, sc, p, r, Pb, scratch, s);
+    case 64 + 4: return launch_fact_t<2, 4>(At, sc, p, r, Pb, scratch, s);
+    case 64 + 8: return launch_fact_t<2, 8>(At, sc, p, r, Pb, scratch, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+static cudaError_t launch_fact(const DevPlan& p, const DevRes& r, const ProblemDev& Pb, float* scratch,
+                               cudaStream_t s) {
+  const HubView v = hub_host_view(r, Pb);
+  if (v.h) return launch_fact_any(v.h, v.scale, p, r, Pb, scratch, s);
+  return launch_fact_any(v.f, 1.0f, p, r, Pb, scratch, s);
 }
 
 static cudaError_t launch_stream(const DevRes& r, const ProblemDev& Pb, float* scratch, int bf16, int stitched,
@@ -988,7 +1208,8 @@ cudaError_t launch_recombine(const DevPlan& p, const DevRes& r, int precision, c
     const bool use_tc = precision == CCS_BF16 && z.tensor_cores && z.rt_scratch && r.TQh && z.krange.full();
     if (z.r_total > 0) {
       build_r_kernel<<<grid(z.r_total, 256), 256, 0, s>>>(p, r, precision, z.r_prefix, p.n_problems, z.r_total,
-                                                          scratch, use_tc ? z.rt_scratch : nullptr, z.stitched);
+                                                          scratch, use_tc ? z.rt_scratch : nullptr, z.stitched,
+                                                          z.krange.full() ? 1 : 0);
       note_launch();
       if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
@@ -1005,6 +1226,10 @@ cudaError_t launch_recombine(const DevPlan& p, const DevRes& r, int precision, c
     for (int i = 0; i < z.n_problems; ++i) {     // wide hubs off the tensor cores: streaming GEMM
       const ProblemDev& Pb = z.host_problems[i];
       if (!Pb.stream || Pb.direct || (use_tc && Pb.tc)) continue;
+      if (fact_path(Pb, precision, z.stitched, z.krange.full())) {
+        if ((err = launch_fact(p, r, Pb, scratch, s)) != cudaSuccess) return err;
+        continue;
+      }
       if ((err = launch_stream(r, Pb, scratch, precision == CCS_BF16 ? 1 : 0, z.stitched, z.krange, s)) !=
           cudaSuccess)
         return err;
