@@ -584,6 +584,8 @@ __global__ void __launch_bounds__(288, 2) gemm_stream_bulk_kernel(const T* __res
 // of 4 G1 N: 12 instead of 64 per operand row at config 3.  Rows are fetched
 // one group per pipeline stage by the TMA engine (bulk copies of each row's
 // CTA slice), as in gemm_stream_bulk_kernel; FP32, dense rows, full range.
+constexpr int kFactRrStage = 4096;   // floats of Rrest rows a CTA stages in shared memory
+
 struct FactDigits {
   int ndig1, ndigr;
   int dig1[kMaxCuts], digr[kMaxCuts];
@@ -636,12 +638,20 @@ __global__ void __launch_bounds__(288, 2) gemm_fact_bulk_kernel(const T* __restr
   uint64_t* full = reinterpret_cast<uint64_t*>(T1s + ((N1 * G1 + 1) & ~1));
   uint64_t* empty = full + stages;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + stages);
+  long long* pg = reinterpret_cast<long long*>(empty + stages + 1);   // [G1]: the leaf digits' row offsets
+  int* digr = reinterpret_cast<int*>(pg + G1);                         // the other digits' cut positions
+  float* Rrs = reinterpret_cast<float*>(digr + kMaxCuts);              // this CTA's Rrest rows, when staged
   const int mb = blockIdx.x % mblocks, split = blockIdx.x / mblocks;
   const long long gr0 = (long long)split * gchunk, gr1 = min(ngroups, gr0 + gchunk);
   const int nstage = gr1 > gr0 ? (int)(gr1 - gr0) : 0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, cw = nc >> 5;
   const int m0 = mb * nc * 4;
   for (int i = threadIdx.x; i < N1 * G1; i += blockDim.x) T1s[i] = T1[i];
+  for (int g = threadIdx.x; g < G1; g += blockDim.x) pg[g] = scatter_digits(g, dg.ndig1, dg.dig1);
+  const bool rr_staged = gchunk * NR <= kFactRrStage;
+  if (rr_staged)
+    for (long long i = threadIdx.x; i < (long long)nstage * NR; i += blockDim.x) Rrs[i] = Rr[gr0 * NR + i];
+  if (threadIdx.x < dg.ndigr) digr[threadIdx.x] = dg.digr[threadIdx.x];
   if (threadIdx.x == 0) {
     for (int i = 0; i < stages; ++i) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[i])), "r"(1) : "memory");
@@ -651,33 +661,35 @@ __global__ void __launch_bounds__(288, 2) gemm_fact_bulk_kernel(const T* __restr
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  if (warp == cw) {                                     // producer warp
-    if (lane == 0) {
-      int issued = 0;
-      for (int i = 0; i < nstage; ++i) {
-        const int st = i % stages;
-        if (i >= stages && !bulk_wait(&empty[st], ((i / stages) - 1) & 1)) {
-          atomicOr(status, 8u);
-          *abort_flag = 1;
-        }
-        if (*abort_flag) break;
-        const long long prest = scatter_digits(gr0 + i, dg.ndigr, dg.digr);
+  if (warp == cw) {                                     // producer warp: lanes < G1 copy one row each
+    int issued = 0;
+    for (int i = 0; i < nstage; ++i) {
+      const int st = i % stages;
+      bool ok = true;
+      if (lane == 0 && i >= stages && !bulk_wait(&empty[st], ((i / stages) - 1) & 1)) {
+        atomicOr(status, 8u);
+        *abort_flag = 1;
+      }
+      ok = __shfl_sync(0xffffffffu, (int)!*abort_flag, 0) != 0;
+      if (!ok) break;
+      if (lane == 0)
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&full[st])),
                      "r"((uint32_t)stage_bytes)
                      : "memory");
-        for (int g = 0; g < G1; ++g) {
-          const long long row = prest | scatter_digits(g, dg.ndig1, dg.dig1);
-          asm volatile(
-              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                  smem_u32(A_s + ((size_t)st * G1 + g) * nc * 4)),
-              "l"(At + row * M + m0), "r"(row_bytes), "r"(smem_u32(&full[st]))
-              : "memory");
-        }
-        issued = i + 1;
-      }
-      if (*abort_flag)      // let copies already issued land before the shared memory is released
-        for (int i = max(0, issued - stages); i < issued; ++i) bulk_wait(&full[i % stages], (i / stages) & 1);
+      __syncwarp();
+      long long prest = 0;
+      const long long grp = gr0 + i;
+      for (int j = 0; j < dg.ndigr; ++j) prest |= ((grp >> (2 * j)) & 3ll) << (2 * digr[j]);
+      for (int g = lane; g < G1; g += 32)
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                smem_u32(A_s + ((size_t)st * G1 + g) * nc * 4)),
+            "l"(At + (prest | pg[g]) * M + m0), "r"(row_bytes), "r"(smem_u32(&full[st]))
+            : "memory");
+      issued = i + 1;
     }
+    if (lane == 0 && *abort_flag)      // let copies already issued land before the shared memory is released
+      for (int i = max(0, issued - stages); i < issued; ++i) bulk_wait(&full[i % stages], (i / stages) & 1);
     return;
   }
   float acc[4][N];
@@ -712,10 +724,14 @@ __global__ void __launch_bounds__(288, 2) gemm_fact_bulk_kernel(const T* __restr
     }
     __syncwarp();
     if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[st])) : "memory");
-    const float* rr = Rr + (gr0 + i) * NR;
     float rv[NR];
+    if (rr_staged) {
 #pragma unroll
-    for (int xr = 0; xr < NR; ++xr) rv[xr] = __ldg(rr + xr);
+      for (int xr = 0; xr < NR; ++xr) rv[xr] = Rrs[(long long)i * NR + xr];
+    } else {
+#pragma unroll
+      for (int xr = 0; xr < NR; ++xr) rv[xr] = __ldg(Rr + (gr0 + i) * NR + xr);
+    }
 #pragma unroll
     for (int xr = 0; xr < NR; ++xr)
 #pragma unroll
@@ -751,7 +767,9 @@ static cudaError_t launch_fact_t(const T* At, float sc, const DevPlan& p, const 
   const long long splits = Pb.ssplits;            // every split writes its partial (zero when empty)
   const int stage_bytes = Pb.G1 * Pb.sthreads * 4 * (int)sizeof(T);
   const int stages = std::max(2, std::min(4, (112 << 10) / stage_bytes));
-  const size_t smem = (size_t)stages * stage_bytes + (size_t)((N1 * Pb.G1 + 1) & ~1) * 4 + 2 * stages * 8 + 16;
+  const size_t rr_floats = gchunk * Pb.NR <= kFactRrStage ? (size_t)gchunk * Pb.NR : 0;
+  const size_t smem = (size_t)stages * stage_bytes + (size_t)((N1 * Pb.G1 + 1) & ~1) * 4 + 2 * stages * 8 + 8 +
+                      (size_t)Pb.G1 * 8 + kMaxCuts * 4 + rr_floats * 4 + 16;
   err = cudaFuncSetAttribute(gemm_fact_bulk_kernel<N1, NR, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   gemm_fact_bulk_kernel<N1, NR, T><<<(unsigned)(Pb.smblocks * splits), Pb.sthreads + 32, smem, s>>>(
