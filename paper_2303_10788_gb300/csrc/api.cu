@@ -526,7 +526,7 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
     std::vector<CliffordOp> cops;
     std::vector<NCOp> nops;
     std::vector<int> moments, wires, zoffs;
-    std::vector<int2> items_c, items_nc, items_b, items_z, zblocks;
+    std::vector<int2> items_c, items_nc, items_b, items_z, items_p, zblocks;
     std::vector<int> nc_frags;
     std::vector<int> cliff_frags;
     int img_words_max = 0, body_words_max = 0;
@@ -591,6 +591,7 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
           for (int o = 0; o < d.qout; ++o) combos *= 3;
           d.pb_off = plan->n_pbasis;
           plan->n_pbasis += 25ll * combos;
+          for (int pc = 0; pc < combos; ++pc) items_p.push_back(make_int2((int)fi, pc));
         }
         {   // Z images: every string, X, Y, Z of every quantum output, Z of every marginal wire
           const int ni = d.nz + 3 * d.qout + d.m;
@@ -840,7 +841,9 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
             if (l1 < d.n_frags) {
               const FragDev& L = plan->fdev[f0 + l1];
               const int N1 = 1 << L.m, G1 = 1 << (2 * L.n_slots);
-              if (L.n_slots >= 1 && L.n_slots <= 2 && N1 <= 2 && d.N % N1 == 0 && d.N / N1 >= 1) {
+              // (large operands only: a small star's two extra launches cost more than its FMAs)
+              if (L.n_slots >= 1 && L.n_slots <= 2 && N1 <= 2 && d.N % N1 == 0 && d.N / N1 >= 1 &&
+                  d.K * (long long)d.M >= (1ll << 24)) {
                 d.fact = 1;
                 d.fl1 = l1;
                 d.fl1_T_off = L.T_off;
@@ -911,12 +914,12 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
     }
     DevPlan& dp = plan->dp;
     FragDev* dfr; CliffordOp* dco; NCOp* dno; int* dmo; int* dwi; int* dzo; int2* dic; int2* din; int2* dib; int* dcf;
-    int2* diz = nullptr; int2* dzb = nullptr;
+    int2* diz = nullptr; int2* dzb = nullptr; int2* dip = nullptr;
     ProblemDev* dpr; CliffordOp* dpo; CliffordOp* dbo; float* dpm; float* dbm;
     Staging st;
     st.add(plan->fdev, &dfr); st.add(cops, &dco); st.add(nops, &dno); st.add(moments, &dmo); st.add(wires, &dwi);
     st.add(zoffs, &dzo); st.add(items_c, &dic); st.add(items_nc, &din); st.add(items_b, &dib);
-    st.add(cliff_frags, &dcf); st.add(items_z, &diz); st.add(zblocks, &dzb); st.add(plan->pdev, &dpr); st.add(prep, &dpo); st.add(basis, &dbo);
+    st.add(cliff_frags, &dcf); st.add(items_z, &diz); st.add(items_p, &dip); st.add(zblocks, &dzb); st.add(plan->pdev, &dpr); st.add(prep, &dpo); st.add(basis, &dbo);
     st.add(prepm, &dpm); st.add(basism, &dbm); st.add(plan->t_prefix, &plan->d_t_prefix);
     st.add(plan->out_prefix, &plan->d_out_prefix);
     st.add(plan->z_prefix, &plan->d_z_prefix); st.add(plan->r_prefix, &plan->d_r_prefix);
@@ -929,6 +932,7 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
     dp.items_body = dib; dp.n_items_body = (int)items_b.size(); dp.max_body_cols = max_body_cols;
     dp.cliff_frags = dcf; dp.n_cliff_frags = (int)cliff_frags.size();
     dp.items_zimg = diz; dp.n_items_zimg = (int)items_z.size();
+    dp.items_proj = dip; dp.n_items_proj = (int)items_p.size();
     dp.zblocks = dzb; dp.n_zblocks = (int)zblocks.size();
     dp.body_words_max = body_words_max; dp.img_words_max = img_words_max;
     dp.max_body_stage_words = max_body_stage;

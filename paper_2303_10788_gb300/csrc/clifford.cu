@@ -654,23 +654,29 @@ __global__ void __launch_bounds__(256) body_basis_kernel(DevPlan P, DevRes R) {
       s_eh[0] = have;
     }
   }
-  if (F.pb_off < 0) return;
-  // the shared rows projected through each output basis combination
-  __syncthreads();
-  const unsigned long long sh = s_eh[0];
-  int combos = 1;
-  for (int o = 0; o < F.qout; ++o) combos *= 3;
-  for (int pc = warp; pc < combos; pc += nwarps) {
-    unsigned pout = 0;
-    for (int o = 0, t = pc; o < F.qout; ++o, t /= 3) pout |= (unsigned)(t % 3) << (2 * o);
-    uint32_t h32 = 0, mine = 0;
-    absorb32(((sh >> lane) & 1ull) ? project_ext(s_eb[0][lane], nA, F.m, F.qout, pout) : 0u, h32, mine, nA, lane);
-    absorb32(((sh >> (lane + 32)) & 1ull) ? project_ext(s_eb[0][lane + 32], nA, F.m, F.qout, pout) : 0u, h32,
-             mine, nA, lane);
-    uint32_t* pb = R.pbasis + F.pb_off + 25ll * pc;
-    if (lane < 24) pb[lane] = ((h32 >> lane) & 1u) ? mine : 0u;
-    if (lane == 0) pb[24] = h32;
-  }
+}
+
+// The shared rows' basis projected through one output basis combination of
+// one fragment (one warp per (fragment, combination); the screen reads the
+// result instead of projecting per variant).
+__global__ void __launch_bounds__(256) proj_kernel(DevPlan P, DevRes R) {
+  const int lane = threadIdx.x & 31;
+  const int item = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (item >= P.n_items_proj) return;
+  const int2 it = P.items_proj[item];
+  const FragDev& F = P.frags[it.x];
+  const int pc = it.y, nA = F.nA;
+  const unsigned long long* rb = R.rowbasis + F.rb_off;
+  const unsigned long long sh = rb[64];
+  unsigned pout = 0;
+  for (int o = 0, t = pc; o < F.qout; ++o, t /= 3) pout |= (unsigned)(t % 3) << (2 * o);
+  uint32_t h32 = 0, mine = 0;
+  absorb32(((sh >> lane) & 1ull) ? project_ext(rb[lane], nA, F.m, F.qout, pout) : 0u, h32, mine, nA, lane);
+  absorb32(((sh >> (lane + 32)) & 1ull) ? project_ext(rb[lane + 32], nA, F.m, F.qout, pout) : 0u, h32, mine, nA,
+           lane);
+  uint32_t* pb = R.pbasis + F.pb_off + 25ll * pc;
+  if (lane < 24) pb[lane] = ((h32 >> lane) & 1u) ? mine : 0u;
+  if (lane == 0) pb[24] = h32;
 }
 
 // --- screen -----------------------------------------------------------------
@@ -1195,6 +1201,16 @@ __device__ __forceinline__ uint32_t space_point(const uint32_t (*tbl)[256], uint
   return y;
 }
 
+// A full-rank space in canonical form (pivots = lowest bits, reduced, offset
+// with every pivot bit clear) has the identity basis and a zero offset, so a
+// shot's outcome is its coefficient bits; checked, not assumed.
+__device__ __forceinline__ bool space_is_identity(const SpaceRec& sp, int rank, int nA) {
+  if (rank != nA || sp.off != 0u) return false;
+  for (int j = 0; j < rank; ++j)
+    if (sp.basis[j] != (1u << j)) return false;
+  return true;
+}
+
 // Calls fn with the lookups a rank needs as a compile-time constant.
 template <class Fn>
 __device__ __forceinline__ void by_rank(int rank, Fn fn) {
@@ -1352,6 +1368,7 @@ __global__ void __launch_bounds__(512) sample_hub_kernel(DevPlan P, DevRes R, Ev
   const int rank = sp.rank;
   const uint32_t off = sp.off;
   build_tables(tbl, sp, rank);
+  const bool ident = space_is_identity(sp, rank, nA);   // every thread: the same answer
   const int nwords = wide ? (1 << nA) : ((1 << nA) > 1 ? (1 << (nA - 1)) : 1);
   {   // zero the histogram, 16 bytes per store
     uint4* h4 = reinterpret_cast<uint4*>(hist2);
@@ -1365,7 +1382,7 @@ __global__ void __launch_bounds__(512) sample_hub_kernel(DevPlan P, DevRes R, Ev
     by_rank(rank, [&](auto lk) {
       constexpr int L = decltype(lk)::value;
       for_shots<L>(0u, E.shots, ctr, E.seed_lo, E.seed_hi, cmask, [&](uint32_t c) {
-        const uint32_t y = space_point<L>(tbl, off, c);
+        const uint32_t y = ident ? c : space_point<L>(tbl, off, c);   // full rank: the coefficient bits
         if (wide) atomicAdd(&hist2[y], 1u);
         else atomicAdd(&hist2[y >> 1], 1u << ((y & 1u) << 4));
       });
@@ -1631,6 +1648,7 @@ __global__ void __launch_bounds__(512, 2) sample_hub8_kernel(DevPlan P, DevRes R
   __shared__ FragDev sF;
   __shared__ int s_czD[16], s_czS[16], s_nzm[2];
   __shared__ unsigned s_tot;
+  __shared__ int s_ident;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int2 it = items[blockIdx.x];
   {
@@ -1646,6 +1664,7 @@ __global__ void __launch_bounds__(512, 2) sample_hub8_kernel(DevPlan P, DevRes R
   const int rank = sp.rank;
   const uint32_t off = sp.off;
   build_tables(tbl, sp, rank);
+  if (tid == 32) s_ident = space_is_identity(sp, rank, nA) ? 1 : 0;
   // the variant's operand rows: one D and sign mask per Z-basis choice
   hub_variant_rows(F, v, s_czD, s_czS, s_nzm);
   const uint32_t cmask = rank >= 32 ? 0xffffffffu : ((1u << rank) - 1u);
@@ -1666,10 +1685,14 @@ __global__ void __launch_bounds__(512, 2) sample_hub8_kernel(DevPlan P, DevRes R
     const uint4 ctr = make_uint4(0u, (uint32_t)v, (uint32_t)F.findex, (uint32_t)F.problem);
     by_rank(rank, [&](auto lk) {
       constexpr int L = decltype(lk)::value;
-      for_shots<L>(0u, E.shots, ctr, E.seed_lo, E.seed_hi, cmask, [&](uint32_t c) {
-        const uint32_t y = space_point<L>(tbl, off, c);
-        atomicAdd(&h32[y >> 2], 1u << ((y & 3u) << 3));
-      });
+      if (s_ident)      // full rank: the outcome is the coefficient bits (no table lookup)
+        for_shots<L>(0u, E.shots, ctr, E.seed_lo, E.seed_hi, cmask,
+                     [&](uint32_t c) { atomicAdd(&h32[c >> 2], 1u << ((c & 3u) << 3)); });
+      else
+        for_shots<L>(0u, E.shots, ctr, E.seed_lo, E.seed_hi, cmask, [&](uint32_t c) {
+          const uint32_t y = space_point<L>(tbl, off, c);
+          atomicAdd(&h32[y >> 2], 1u << ((y & 3u) << 3));
+        });
     });
     __syncthreads();
     if (keep_counts)
@@ -1876,6 +1899,8 @@ cudaError_t launch_body(const DevPlan& p, const DevRes& r, int smem_optin, bool 
   if (err != cudaSuccess || p.n_cliff_frags == 0) return err;
   // fragments with no measurement record get no table: nothing reads it
   body_basis_kernel<<<p.n_cliff_frags + p.n_items_zimg, 256, 0, s>>>(p, r); note_launch();
+  if ((err = cudaGetLastError()) != cudaSuccess || p.n_items_proj == 0) return err;
+  proj_kernel<<<(p.n_items_proj + 7) / 8, 256, 0, s>>>(p, r); note_launch();
   return cudaGetLastError();
 }
 

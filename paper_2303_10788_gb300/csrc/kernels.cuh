@@ -95,6 +95,8 @@ struct DevPlan {
   int n_cliff_frags;
   const int2* items_zimg;     // (frag, record) of every Z-image record
   int n_items_zimg;
+  const int2* items_proj;     // (frag, output basis combination) of every projected shared-row basis
+  int n_items_proj;
   const int2* zblocks;        // (frag, first variant) of each block of Z-string values
   int n_zblocks;
   int body_words_max;         // widest Clifford body tableau, uint64 words

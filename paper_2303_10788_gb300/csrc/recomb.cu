@@ -1046,7 +1046,7 @@ __device__ void z_string_block(const DevPlan& P, const DevRes& R, const long lon
 // the 2^m K 2^(m_1+..+m_L) of the Kronecker GEMM.  Sums are compensated
 // (Neumaier) FP32; operands are rounded to bf16 first in BF16 mode.
 // Blocks after the problems compute the Z-string expectations.
-__global__ void __launch_bounds__(512) contract_kernel(DevPlan P, DevRes R, int precision,
+__global__ void __launch_bounds__(512, 2) contract_kernel(DevPlan P, DevRes R, int precision,
                                                       const int2* direct_items, int n_direct, int stage_floats,
                                                       const long long* z_prefix, int np, long long z_total,
                                                       double* marg_out, double* zexp_out, KRange krg) {
