@@ -770,7 +770,11 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
       plan->n_zexp += d.nz;
       plan->out_prefix.push_back(plan->n_marg);
       plan->z_prefix.push_back(plan->n_zexp);
-      if (P.hub < 0) plan->all_star = false;
+      if (P.hub < 0) {          // not a star: the general contraction over all fragment tensors
+        plan->all_star = false;
+        d.general = 1;
+        d.K = 1ll << (2 * d.k);
+      }
       if (P.hub >= 0) {
         const int m_hub = plan->fdev[f0 + P.hub].m;
         d.M = 1 << m_hub;
@@ -1347,7 +1351,6 @@ int ccs_recombine(ccs_ctx c, ccs_plan p, ccs_res r, const ccs_recomb_opts* opts,
   return abi_guard([&](int code, const char* m) { return fail(c, code, m); }, [&]() -> int {
     if (!c || !p || !r || r->plan != p) return fail(c, CCS_ERR_INVALID_ARG, "bad arguments");
     if (c->host_only) return fail(c, CCS_ERR_UNSUPPORTED, "host-only context cannot recombine");
-    if (!p->all_star) return fail(c, CCS_ERR_UNSUPPORTED, "fragments do not form a star");
     const int prec = opts ? opts->precision : CCS_FP32;
     const bool on_dev = opts && opts->outputs_on_device;
     if (prec != CCS_FP32 && prec != CCS_BF16) return fail(c, CCS_ERR_INVALID_ARG, "bad precision");
@@ -1357,7 +1360,8 @@ int ccs_recombine(ccs_ctx c, ccs_plan p, ccs_res r, const ccs_recomb_opts* opts,
     RecombSizes rz{p->r_total, p->part_total, p->gemm_blocks, p->n_marg, p->n_zexp,
                    p->d_direct_items, (int)p->direct_items.size(), (int)p->direct_stage_floats, p->chain,
                    p->d_r_prefix, p->d_blk_prefix, p->d_out_prefix, p->d_z_prefix, p->max_tile_smem,
-                   p->pdev.data(), (int)p->pdev.size(), r->rt_scratch, tc ? 1 : 0, stitched ? 1 : 0, KRange{0, -1}};
+                   p->pdev.data(), (int)p->pdev.size(), r->rt_scratch, tc ? 1 : 0, stitched ? 1 : 0, KRange{0, -1},
+                   p->all_star ? 0 : 1};
     if (opts && (opts->k_lo || opts->k_hi)) {
       if (opts->k_hi && opts->k_hi <= opts->k_lo) return fail(c, CCS_ERR_INVALID_ARG, "empty cut-index range");
       if (opts->k_lo > (1ull << 62) || opts->k_hi > (1ull << 62)) return fail(c, CCS_ERR_INVALID_ARG, "bad range");
@@ -1652,7 +1656,6 @@ extern "C" int ccs_recombine_noalloc(ccs_ctx c, ccs_plan p, ccs_res r, int preci
   return abi_guard([&](int code, const char* m) { return fail(c, code, m); }, [&]() -> int {
     if (!c || !p || !r || r->plan != p) return fail(c, CCS_ERR_INVALID_ARG, "bad arguments");
     if (c->host_only) return fail(c, CCS_ERR_UNSUPPORTED, "host-only context cannot recombine");
-    if (!p->all_star) return fail(c, CCS_ERR_UNSUPPORTED, "fragments do not form a star");
     if (precision != CCS_FP32 && precision != CCS_BF16) return fail(c, CCS_ERR_INVALID_ARG, "bad precision");
     if ((p->n_marg && !marginal_out) || (p->n_zexp && !zexp_out))
       return fail(c, CCS_ERR_INVALID_ARG, "null output buffer");
@@ -1679,7 +1682,7 @@ extern "C" int ccs_recombine_noalloc(ccs_ctx c, ccs_plan p, ccs_res r, int preci
                    p->d_direct_items, (int)p->direct_items.size(), (int)p->direct_stage_floats, p->chain,
                    p->d_r_prefix, p->d_blk_prefix, p->d_out_prefix, p->d_z_prefix, p->max_tile_smem,
                    p->pdev.data(), (int)p->pdev.size(), nullptr, 0, r->ep.mode == CCS_STITCH ? 1 : 0,
-                   KRange{0, -1}};
+                   KRange{0, -1}, p->all_star ? 0 : 1};
     e = launch_recombine(p->dp, r->dr, precision, rz, scratch, marginal_out, zexp_out, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "recombine kernel");
     return CCS_OK;

@@ -62,6 +62,8 @@ struct ProblemDev {
   long long hub_qrow_off;  // qrow_off of the hub (-1: not a Clifford hub)
   int tc;                  // 1: eligible for the tensor-core GEMM in BF16 mode
   int direct;              // 1: contracted leaf by leaf in shared memory, TM hub outputs per CTA
+  int general;             // 1: no fragment on every cut (not a star): every output summed over the
+                           //    cut index from all fragment tensors (general_contract_kernel)
   int direct_staged;       // 1: the slice's hub operand (K x TM) is staged first; 0: the first leaf streams it
   // streaming CUDA-core GEMM of a wide hub (FP32, or BF16 off the tensor cores):
   // sthreads threads x 4 hub outputs per CTA, smblocks CTAs across M, ssplits across K
@@ -255,6 +257,7 @@ struct RecombSizes {
   int stitched;                  // 1: Clifford hubs' operand rows flagged in DevRes::qnz (zero rows
                                  //    of streamed problems are neither written nor read)
   KRange krange;                 // the cut-index terms summed ({0, -1}: all)
+  int has_general;               // 1: some problem is not a star
 };
 cudaError_t launch_recombine(const DevPlan& p, const DevRes& r, int precision, const RecombSizes& z,
                              float* scratch, double* marg_out, double* zexp_out, cudaStream_t s);

@@ -411,6 +411,10 @@ int fragment_problem(Problem& p, int pi, std::vector<Frag>& out, std::string& er
   }
   // star: one fragment on every cut
   const int nf = (int)out.size() - first;
+  if (nf > kMaxProblemFragments) {
+    err = "more than " + std::to_string(kMaxProblemFragments) + " fragments in one problem";
+    return CCS_ERR_UNSUPPORTED;
+  }
   p.hub = -1;
   if (p.cuts.empty()) {
     p.hub = 0;

@@ -23,6 +23,7 @@ constexpr int kMaxTableauQubits = 640;  // per-variant tableaus: (2n+3) x 2*ceil
 // shared memory; no per-variant tableau): a warp covers its 2*ceil(n/64) words.
 constexpr int kMaxBodyQubits = 1024;
 constexpr int kMaxCuts = 12;
+constexpr int kMaxProblemFragments = kMaxCuts + 1;   // fragments of one problem (the contraction stages them)
 constexpr int kMaxMarginal = 24;
 // Circuit size accepted at the ABI (host arrays are linear in both).
 constexpr uint32_t kMaxCircuitQubits = 1u << 24;

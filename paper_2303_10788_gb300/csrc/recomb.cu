@@ -901,7 +901,7 @@ __global__ void reduce_scatter_kernel(DevPlan P, const long long* prefix, int np
        g += (long long)gridDim.x * blockDim.x) {
     const int pi = find_seg(prefix, np, g);
     const ProblemDev& Pb = P.problems[pi];
-    if (Pb.direct) continue;                  // written by the leaf-by-leaf contraction
+    if (Pb.direct || Pb.general) continue;    // written by the leaf-by-leaf or the general contraction
     const long long loc = g - prefix[pi];
     const long long m = loc / Pb.N, n = loc - m * Pb.N;
     const int splits = (Pb.stream && !(use_tc && Pb.tc)) ? Pb.ssplits : Pb.splits;
@@ -934,7 +934,7 @@ __global__ void reduce_scatter_kernel(DevPlan P, const long long* prefix, int np
 
 // Fragment descriptors of one problem, read once into shared memory so that
 // the per-element loops below do no dependent global loads.
-constexpr int kMaxProblemFrags = kMaxCuts + 1;
+constexpr int kMaxProblemFrags = kMaxProblemFragments;   // checked when the plan is built
 constexpr int kLeafStage = 2048;   // floats of a leaf table staged in shared memory
 struct ProblemShared {
   int nf, hub, k;
@@ -1046,6 +1046,235 @@ __device__ void z_string_block(const DevPlan& P, const DevRes& R, const long lon
 // the 2^m K 2^(m_1+..+m_L) of the Kronecker GEMM.  Sums are compensated
 // (Neumaier) FP32; operands are rounded to bf16 first in BF16 mode.
 // Blocks after the problems compute the Z-string expectations.
+// One operand entry as a float: FP32 as stored, or an int16 count sum times 1/shots.
+__device__ __forceinline__ float hub_elem(const float* A, float, long long i) { return A[i]; }
+__device__ __forceinline__ float hub_elem(const int16_t* A, float sc, long long i) { return (float)A[i] * sc; }
+// Four consecutive operand entries (16-byte FP32 or 8-byte int16 load; the
+// caller guarantees the alignment).
+__device__ __forceinline__ void hub_vec4(const float* A, float, long long i, float (&v)[4]) {
+  const float4 q = __ldg(reinterpret_cast<const float4*>(A + i));
+  v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void hub_vec4(const int16_t* A, float sc, long long i, float (&v)[4]) {
+  const int2 q = __ldg(reinterpret_cast<const int2*>(A + i));
+  v[0] = (float)(int)(short)(q.x & 0xffff) * sc;
+  v[1] = (float)(q.x >> 16) * sc;
+  v[2] = (float)(int)(short)(q.y & 0xffff) * sc;
+  v[3] = (float)(q.y >> 16) * sc;
+}
+__device__ __forceinline__ void hub_vec2(const float* A, float, long long i, float (&v)[2]) {
+  const float2 q = __ldg(reinterpret_cast<const float2*>(A + i));
+  v[0] = q.x; v[1] = q.y;
+}
+__device__ __forceinline__ void hub_vec2(const int16_t* A, float sc, long long i, float (&v)[2]) {
+  const int q = __ldg(reinterpret_cast<const int*>(A + i));
+  v[0] = (float)(int)(short)(q & 0xffff) * sc;
+  v[1] = (float)(q >> 16) * sc;
+}
+__device__ __forceinline__ void neumaier(float& sum, float& comp, float p) {
+  const float t = sum + p;                     // keep the low part the sum loses
+  comp += fabsf(sum) >= fabsf(p) ? (sum - t) + p : (p - t) + sum;
+  sum = t;
+}
+
+// The first leaf of a slice, read from the hub operand in global memory:
+//   Y[r][x][m] = sum_g Q^T[kr(r) | kg(g)][m0 + m] T'[x][g]
+// (r: the other leaves' digits, g: this leaf's, x: its outputs), each thread
+// VW consecutive hub outputs (one vector load per row) and two outputs x
+// (every operand load used twice), four rows in flight.
+constexpr int kFirstVec = 4;    // hub outputs per thread of the first-leaf pass (one vector load)
+constexpr int kFirstX = 1;      // leaf outputs per thread (1 or 2)
+template <int VW, int NX, class T, class Expand>
+__device__ __forceinline__ void first_leaf_global(const T* __restrict__ At, float sc, int bf16, long long Mfull,
+                                                  int lm, int lG, int ml, int lrest, long long klo, long long khi,
+                                                  const float* tv, bool tv_rounded, const int* kg_tab,
+                                                  const ProblemShared& S, int l, Expand expand, float* Y) {
+  const int G = 1 << lG, lV = VW == 4 ? 2 : VW == 2 ? 1 : 0, lmv = lm - lV;
+  const int nx = (NX == 2 && ml > 0) ? 2 : 1, lxc = nx == 2 ? ml - 1 : ml;
+  const int lout = lm + ml;
+  const int n_items = 1 << (lrest + lxc + lmv);
+  for (int e = threadIdx.x; e < n_items; e += blockDim.x) {
+    const int mv = e & ((1 << lmv) - 1);
+    const int x0 = ((e >> lmv) & ((1 << lxc) - 1)) * nx;
+    const int r = e >> (lmv + lxc);
+    const int kr = expand(r << lG, l);
+    float s0[VW], c0[VW], s1[NX == 2 ? VW : 1], c1[NX == 2 ? VW : 1];
+#pragma unroll
+    for (int v = 0; v < VW; ++v) { s0[v] = c0[v] = 0.f; if (NX == 2) s1[v] = c1[v] = 0.f; }
+    const T* base = At + mv * VW;
+    for (int g0 = 0; g0 < G; g0 += 4) {        // G = 4^slots: a multiple of 4
+      float a[4][VW];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int g = g0 + u;
+        int kg;
+        if (kg_tab) kg = kg_tab[g];
+        else {
+          kg = 0;
+          for (int i = 0; i < S.ns[l]; ++i) kg |= ((g >> (2 * i)) & 3) << (2 * S.slot_cut[l][i]);
+        }
+        const long long kk = (long long)(kr | kg);
+        if (kk >= klo && kk < khi) {
+          if constexpr (VW == 4) hub_vec4(base, sc, kk * Mfull, a[u]);
+          else if constexpr (VW == 2) hub_vec2(base, sc, kk * Mfull, a[u]);
+          else a[u][0] = hub_elem(base, sc, kk * Mfull);
+        } else {
+#pragma unroll
+          for (int v = 0; v < VW; ++v) a[u][v] = 0.f;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int g = g0 + u;
+        float t0 = tv[x0 * G + g], t1 = nx == 2 ? tv[(x0 + 1) * G + g] : 0.f;
+        if (bf16 && !tv_rounded) { t0 = to_bf16f(t0); t1 = to_bf16f(t1); }
+#pragma unroll
+        for (int v = 0; v < VW; ++v) {
+          const float av = bf16 ? to_bf16f(a[u][v]) : a[u][v];
+          neumaier(s0[v], c0[v], av * t0);
+          if (NX == 2 && nx == 2) neumaier(s1[v], c1[v], av * t1);
+        }
+      }
+    }
+    float* y = Y + ((long long)r << lout) + mv * VW;
+#pragma unroll
+    for (int v = 0; v < VW; ++v) {
+      y[((long long)x0 << lm) + v] = s0[v] + c0[v];
+      if (NX == 2 && nx == 2) y[((long long)(x0 + 1) << lm) + v] = s1[v] + c1[v];
+    }
+  }
+}
+
+// One slice of TM hub outputs of one star, contracted leaf by leaf (the
+// body of contract_kernel), for the hub operand's stored element type.
+template <class T>
+__device__ __forceinline__ void contract_item(const DevPlan& P, const DevRes& R, int precision, const ProblemDev& Pb,
+                                              const T* __restrict__ At, float sc, int m0, int M, int lm, int Mfull,
+                                              int K, long long klo, long long khi, ProblemShared& S, float* s_buf,
+                                              int stage_floats, float* s_T, double* marg_out) {
+  load_problem(P, Pb, S);
+  __syncthreads();
+  float* X = s_buf;
+  float* Y = s_buf + stage_floats;
+  // compact cut index (groups in leaf order, the first leaf's lowest) ->
+  // cut index, for the digits of leaves from `from` on
+  auto expand = [&](int kc, int from) -> int {
+    int k = 0, rem = kc;
+    for (int l = from; l < S.nf; ++l) {
+      if (l == S.hub) continue;
+      for (int i = 0; i < S.ns[l]; ++i) {
+        k |= (rem & 3) << (2 * S.slot_cut[l][i]);
+        rem >>= 2;
+      }
+    }
+    return k;
+  };
+  int first = 0;
+  while (first < S.nf && first == S.hub) ++first;
+  const bool staged0 = first >= S.nf;         // no leaf: the operand is the result
+  if (staged0) {
+    for (int t0 = threadIdx.x; t0 < K * M; t0 += 8 * blockDim.x) {   // 8 loads in flight per thread
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int t = t0 + u * blockDim.x;
+        if (t < K * M) {
+          const long long kk = expand(t >> lm, 0);
+          v[u] = (kk >= klo && kk < khi) ? hub_elem(At, sc, kk * Mfull + (t & (M - 1))) : 0.f;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int t = t0 + u * blockDim.x;
+        if (t < K * M) X[t] = precision == CCS_BF16 ? to_bf16f(v[u]) : v[u];
+      }
+    }
+  }
+  int lA = lm, lrest = 2 * S.k;                // log2 of the outer and rest extents
+  for (int l = first; l < S.nf; ++l) {
+    if (l == S.hub) continue;
+    const int lG = 2 * S.ns[l], G = 1 << lG, Nl = 1 << S.m[l];
+    lrest -= lG;
+    const bool tstaged = Nl * G <= kLeafStage;
+    __syncthreads();                           // X complete; previous s_T consumed
+    if (tstaged)
+      for (int i = threadIdx.x; i < Nl * G; i += blockDim.x) {
+        float v = R.TQ[S.T_off[l] + i];
+        if (precision == CCS_BF16) v = to_bf16f(v);
+        s_T[i] = v;
+      }
+    // the first leaf's digits in the cut index, tabulated behind its table when they fit
+    int* kg_tab = nullptr;
+    if (l == first && !staged0 && tstaged && Nl * G + G <= kLeafStage) {
+      kg_tab = reinterpret_cast<int*>(s_T + Nl * G);
+      for (int g = threadIdx.x; g < G; g += blockDim.x) {
+        int kg = 0;
+        for (int i = 0; i < S.ns[l]; ++i) kg |= ((g >> (2 * i)) & 3) << (2 * S.slot_cut[l][i]);
+        kg_tab[g] = kg;
+      }
+    }
+    __syncthreads();
+    const int lout = lA + S.m[l], A = 1 << lA;
+    if (l == first && !staged0) {
+      const float* tv = tstaged ? s_T : R.TQ + S.T_off[l];
+      if ((1 << lm) >= kFirstVec)              // aligned vectors: T_off and m0 are multiples of TM
+        first_leaf_global<kFirstVec, kFirstX>(At, sc, precision == CCS_BF16, Mfull, lm, lG, S.m[l], lrest, klo, khi, tv, tstaged,
+                             kg_tab, S, l, expand, Y);
+      else
+        first_leaf_global<1, kFirstX>(At, sc, precision == CCS_BF16, Mfull, lm, lG, S.m[l], lrest, klo, khi, tv, tstaged,
+                             kg_tab, S, l, expand, Y);
+      float* tmp = X; X = Y; Y = tmp;
+      lA = lout;
+      continue;
+    }
+    for (int e = threadIdx.x; e < (1 << (lrest + lout)); e += blockDim.x) {
+      const int r = e >> lout, rm = e & ((1 << lout) - 1);
+      const int x = rm >> lA, outer = rm & (A - 1);
+      float sum = 0.f, comp = 0.f;
+      const float* xs = X + ((r << lG) << lA) + outer;
+      const float* ts = tstaged ? s_T + x * G : nullptr;
+      for (int g = 0; g < G; ++g) {
+        float tv;
+        if (tstaged) tv = ts[g];
+        else {
+          tv = R.TQ[S.T_off[l] + (long long)x * G + g];
+          if (precision == CCS_BF16) tv = to_bf16f(tv);
+        }
+        neumaier(sum, comp, xs[g << lA] * tv);
+      }
+      Y[e] = sum + comp;
+    }
+    float* tmp = X; X = Y; Y = tmp;
+    lA = lout;
+  }
+  // X[m + M n] = C[m][n]; marginal index = hub bits of m | leaf bits of n,
+  // both tabulated in the free buffer (TM + N entries, within its size)
+  const int hub = S.hub, N = 1 << (lA - lm);
+  unsigned* orow = reinterpret_cast<unsigned*>(Y);
+  unsigned* ocol = orow + M;
+  for (int m = threadIdx.x; m < M; m += blockDim.x) {
+    unsigned o = 0;
+    for (int j = 0; j < S.m[hub]; ++j) o |= ((unsigned)((m0 + m) >> j) & 1u) << S.marg_pos[hub][j];
+    orow[m] = o;
+  }
+  for (int n = threadIdx.x; n < N; n += blockDim.x) {
+    unsigned o = 0;
+    int off = 0;
+    for (int l = 0; l < S.nf; ++l) {
+      if (l == hub) continue;
+      for (int j = 0; j < S.m[l]; ++j) o |= ((unsigned)(n >> (off + j)) & 1u) << S.marg_pos[l][j];
+      off += S.m[l];
+    }
+    ocol[n] = o;
+  }
+  __syncthreads();
+  const double scale = ldexp(1.0, -S.k);       // exact: a power of two
+  double* out = marg_out + Pb.marg_off;
+  for (int t = threadIdx.x; t < (1 << lA); t += blockDim.x)
+    out[orow[t & (M - 1)] | ocol[t >> lm]] = (double)X[t] * scale;
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(512, 2) contract_kernel(DevPlan P, DevRes R, int precision,
                                                       const int2* direct_items, int n_direct, int stage_floats,
                                                       const long long* z_prefix, int np, long long z_total,
@@ -1066,143 +1295,15 @@ __global__ void __launch_bounds__(512, 2) contract_kernel(DevPlan P, DevRes R, i
     const int m0 = di.y * M, Mfull = Pb.M;
     const int K = (int)Pb.K;
     const long long klo = krg.lo_of(K), khi = krg.hi_of(K);   // cut-index terms summed
-    // the hub's Q stored transposed: K x Mfull, row-major (this slice's columns from m0)
-    const HubView At = hub_view(R, P.frags[Pb.frag0 + Pb.hub], Pb.hub_T_off + m0);
-    load_problem(P, Pb, S);
-    __syncthreads();
-    float* X = s_buf;
-    float* Y = s_buf + stage_floats;
-    // compact cut index (groups in leaf order, the first leaf's lowest) ->
-    // cut index, for the digits of leaves from `from` on
-    auto expand = [&](int kc, int from) -> int {
-      int k = 0, rem = kc;
-      for (int l = from; l < S.nf; ++l) {
-        if (l == S.hub) continue;
-        for (int i = 0; i < S.ns[l]; ++i) {
-          k |= (rem & 3) << (2 * S.slot_cut[l][i]);
-          rem >>= 2;
-        }
-      }
-      return k;
-    };
-    int first = 0;
-    while (first < S.nf && first == S.hub) ++first;
-    const bool staged0 = Pb.direct_staged || first >= S.nf;   // no leaf: the operand is the result
-    if (staged0) {
-      for (int t0 = threadIdx.x; t0 < K * M; t0 += 8 * blockDim.x) {   // 8 loads in flight per thread
-        float v[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int t = t0 + u * blockDim.x;
-          if (t < K * M) {
-            const long long kk = expand(t >> lm, 0);
-            v[u] = (kk >= klo && kk < khi) ? At.at(kk * Mfull + (t & (M - 1))) : 0.f;
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int t = t0 + u * blockDim.x;
-          if (t < K * M) X[t] = precision == CCS_BF16 ? to_bf16f(v[u]) : v[u];
-        }
-      }
-    }
-    int lA = lm, lrest = 2 * S.k;                // log2 of the outer and rest extents
-    for (int l = first; l < S.nf; ++l) {
-      if (l == S.hub) continue;
-      const int lG = 2 * S.ns[l], G = 1 << lG, Nl = 1 << S.m[l];
-      lrest -= lG;
-      const bool tstaged = Nl * G <= kLeafStage;
-      __syncthreads();                           // X complete; previous s_T consumed
-      if (tstaged)
-        for (int i = threadIdx.x; i < Nl * G; i += blockDim.x) {
-          float v = R.TQ[S.T_off[l] + i];
-          if (precision == CCS_BF16) v = to_bf16f(v);
-          s_T[i] = v;
-        }
-      __syncthreads();
-      const int lout = lA + S.m[l], A = 1 << lA;
-      for (int e = threadIdx.x; e < (1 << (lrest + lout)); e += blockDim.x) {
-        const int r = e >> lout, rm = e & ((1 << lout) - 1);
-        const int x = rm >> lA, outer = rm & (A - 1);
-        float sum = 0.f, comp = 0.f;
-        if (l == first && !staged0) {
-          // the first leaf reads the hub operand in global memory: rows of
-          // the cut index, the block's TM hub outputs contiguous in each
-          const int kr = expand(r << lG, l);     // the other leaves' digits of this row group
-          for (int g0 = 0; g0 < G; g0 += 8) {    // 8 loads in flight
-            float a[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-              const int g = g0 + u;
-              int kg = 0;
-              for (int i = 0; i < S.ns[l]; ++i) kg |= ((g >> (2 * i)) & 3) << (2 * S.slot_cut[l][i]);
-              const long long kk = (long long)(kr | kg);
-              a[u] = (g < G && kk >= klo && kk < khi) ? At.at(kk * Mfull + outer) : 0.f;
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-              const int g = g0 + u;
-              if (g >= G) break;
-              const float av = precision == CCS_BF16 ? to_bf16f(a[u]) : a[u];
-              float tv;
-              if (tstaged) tv = s_T[x * G + g];
-              else {
-                tv = R.TQ[S.T_off[l] + (long long)x * G + g];
-                if (precision == CCS_BF16) tv = to_bf16f(tv);
-              }
-              const float p = av * tv;
-              const float t2 = sum + p;           // Neumaier: keep the lost low part
-              comp += fabsf(sum) >= fabsf(p) ? (sum - t2) + p : (p - t2) + sum;
-              sum = t2;
-            }
-          }
-        } else {
-          const float* xs = X + ((r << lG) << lA) + outer;
-          const float* ts = tstaged ? s_T + x * G : nullptr;
-          for (int g = 0; g < G; ++g) {
-            float tv;
-            if (tstaged) tv = ts[g];
-            else {
-              tv = R.TQ[S.T_off[l] + (long long)x * G + g];
-              if (precision == CCS_BF16) tv = to_bf16f(tv);
-            }
-            const float p = xs[g << lA] * tv;
-            const float t2 = sum + p;
-            comp += fabsf(sum) >= fabsf(p) ? (sum - t2) + p : (p - t2) + sum;
-            sum = t2;
-          }
-        }
-        Y[e] = sum + comp;
-      }
-      float* tmp = X; X = Y; Y = tmp;
-      lA = lout;
-    }
-    // X[m + M n] = C[m][n]; marginal index = hub bits of m | leaf bits of n,
-    // both tabulated in the free buffer (TM + N entries, within its size)
-    const int hub = S.hub, N = 1 << (lA - lm);
-    unsigned* orow = reinterpret_cast<unsigned*>(Y);
-    unsigned* ocol = orow + M;
-    for (int m = threadIdx.x; m < M; m += blockDim.x) {
-      unsigned o = 0;
-      for (int j = 0; j < S.m[hub]; ++j) o |= ((unsigned)((m0 + m) >> j) & 1u) << S.marg_pos[hub][j];
-      orow[m] = o;
-    }
-    for (int n = threadIdx.x; n < N; n += blockDim.x) {
-      unsigned o = 0;
-      int off = 0;
-      for (int l = 0; l < S.nf; ++l) {
-        if (l == hub) continue;
-        for (int j = 0; j < S.m[l]; ++j) o |= ((unsigned)(n >> (off + j)) & 1u) << S.marg_pos[l][j];
-        off += S.m[l];
-      }
-      ocol[n] = o;
-    }
-    __syncthreads();
-    const double scale = ldexp(1.0, -S.k);       // exact: a power of two
-    double* out = marg_out + Pb.marg_off;
-    for (int t = threadIdx.x; t < (1 << lA); t += blockDim.x)
-      out[orow[t & (M - 1)] | ocol[t >> lm]] = (double)X[t] * scale;
-    __syncthreads();
+    // the hub's Q stored transposed: K x Mfull, row-major (this slice's columns from m0),
+    // FP32 or int16 count sums: one branch per slice, none per element
+    const HubView hv = hub_view(R, P.frags[Pb.frag0 + Pb.hub], Pb.hub_T_off + m0);
+    if (hv.h)
+      contract_item(P, R, precision, Pb, hv.h, hv.scale, m0, M, lm, Mfull, K, klo, khi, S, s_buf, stage_floats, s_T,
+                    marg_out);
+    else
+      contract_item(P, R, precision, Pb, hv.f, 1.0f, m0, M, lm, Mfull, K, klo, khi, S, s_buf, stage_floats, s_T,
+                    marg_out);
   }
 }
 
@@ -1213,6 +1314,51 @@ cudaError_t launch_fold(const DevPlan& p, const DevRes& r, const EvalParams& e, 
   fold_kernel<<<(unsigned)(blocks < 65535 * 8 ? blocks : 65535 * 8), 256, 0, s>>>(p, r, e, f.fidx, f.t_prefix, f.nf,
                                                                             f.total); note_launch();
   return cudaGetLastError();
+}
+
+// --- any topology ----------------------------------------------------------
+// A problem with no fragment on every cut (a chain or a tree of fragments,
+// Sec. V-C's general tensor network) is summed directly: for each output o,
+//   p(o) = 2^-k sum_P prod_f T_f(o_f, P|f),
+// one CTA per output, the cut index strided over its threads (FP32 products,
+// compensated FP32 sums per thread, FP64 across threads in a fixed order).
+// 4^k x 2^|o| x fragments reads: the general form, not a fast path.
+__global__ void __launch_bounds__(256) general_contract_kernel(DevPlan P, DevRes R, int precision,
+                                                               const long long* out_prefix, int np, long long total,
+                                                               double* marg_out, KRange kr) {
+  __shared__ double red[256];
+  __shared__ ProblemShared S;
+  for (long long b = blockIdx.x; b < total; b += gridDim.x) {
+    const int pi = find_seg(out_prefix, np, b);
+    const ProblemDev& Pb = P.problems[pi];
+    if (!Pb.general) continue;                 // stars are contracted by the other kernels
+    const long long o = b - out_prefix[pi];
+    load_problem(P, Pb, S);
+    __syncthreads();
+    const long long K = Pb.K, lo = kr.lo_of(K), hi = kr.hi_of(K);
+    float sum = 0.f, comp = 0.f;
+    for (long long Pp = lo + threadIdx.x; Pp < hi; Pp += blockDim.x) {
+      float t = 1.f;
+      for (int l = 0; l < S.nf; ++l) {
+        int of = 0;
+        for (int j = 0; j < S.m[l]; ++j) of |= (int)((o >> S.marg_pos[l][j]) & 1) << j;
+        float v = R.T[S.T_off[l] + ((long long)of << (2 * S.ns[l])) + frag_digits(S, l, Pp)];
+        if (precision == CCS_BF16) v = to_bf16f(v);
+        t *= v;
+      }
+      const float t2 = sum + t;                // Neumaier: keep the lost low part
+      comp += fabsf(sum) >= fabsf(t) ? (sum - t2) + t : (t - t2) + sum;
+      sum = t2;
+    }
+    red[threadIdx.x] = (double)sum + (double)comp;
+    __syncthreads();
+    for (int s2 = blockDim.x / 2; s2; s2 >>= 1) {
+      if ((int)threadIdx.x < s2) red[threadIdx.x] += red[threadIdx.x + s2];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) marg_out[Pb.marg_off + o] = ldexp(red[0], -S.k);
+    __syncthreads();
+  }
 }
 
 cudaError_t launch_recombine(const DevPlan& p, const DevRes& r, int precision, const RecombSizes& z,
@@ -1272,6 +1418,12 @@ cudaError_t launch_recombine(const DevPlan& p, const DevRes& r, int precision, c
                                                                   scratch, marg_out, use_tc ? 1 : 0); note_launch();
       if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
+  }
+  if (z.has_general && z.out_total > 0) {
+    general_contract_kernel<<<(unsigned)(z.out_total < 65535ll * 16 ? z.out_total : 65535ll * 16), 256, 0, s>>>(
+        p, r, precision, z.out_prefix, p.n_problems, z.out_total, marg_out, z.krange);
+    note_launch();
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
   const long long blocks = z.n_direct + z.z_total;
   if (blocks > 0) {

@@ -3,14 +3,14 @@ memory when they need the result (its scratch is a fixed array inside the
 library).  Checked through the C ABI against ccs_recombine on two calls in a
 row, in FP32 and BF16, on plans that contract leaf by leaf (no scratch) and
 on a plan whose contraction runs through the fixed scratch (the leaves'
-Kronecker operand and the split-K partials); a large plan, then a small one,
+Kronecker operand and the split-K partials); on a chain of fragments; a large plan, then a small one,
 then the large one again; and for its size limit.  Collected last on
 purpose."""
 import numpy as np
 import pytest
 
 from paper_2303_10788_gb300 import ccs
-from workloads import Region, Workload, brickwork_star, config1, config2
+from workloads import Region, Workload, brickwork_star, config1, config2, tree_circuit
 
 pytestmark = pytest.mark.gpu
 
@@ -68,6 +68,17 @@ def test_noalloc_through_its_scratch_large_small_large(ctx, precision):
     _noalloc_twice(ctx, *big, w_big, precision)
     _noalloc_twice(ctx, *small, w_small, precision)
     _noalloc_twice(ctx, *big, w_big, precision)
+
+
+@pytest.mark.parametrize("precision", [ccs.CCS_FP32, ccs.CCS_BF16])
+def test_noalloc_non_star_plan(ctx, precision):
+    # a chain of four fragments: no fragment carries every cut
+    c, cuts = tree_circuit([0, 1, 2], 16, 2, seed=1)
+    w = Workload("chain4", c, cuts, [0, 2, 4, 9, 11], [[0, 1, 11], [1, 10]], 512, 3)
+    plan, res = _evaluated(ctx, w)
+    nf, nc = ccs.ccs_plan_counts(ctx, plan, 0)
+    assert max(ccs.ccs_fragment_info_get(ctx, plan, 0, f)["n_slots"] for f in range(nf)) < nc
+    _noalloc_twice(ctx, plan, res, w, precision)
 
 
 def test_noalloc_rejects_plans_beyond_its_scratch(ctx):

@@ -11,6 +11,6 @@ from .circuits import (  # noqa: F401
     Circuit, Region, Workload, SEED_BASE,
     random_c1_word, random_c2_word, brickwork_star,
     config1, config2, config3, config4, config5_circuit, small_star,
-    random_clifford_circuit, random_distributions, zstrings_for,
+    random_clifford_circuit, tree_circuit, random_distributions, zstrings_for,
     t_to_s, hwea, sk_qaoa,
 )

@@ -375,6 +375,44 @@ def random_clifford_circuit(n, n_gates, seed, t_count=0):
     return c
 
 
+def tree_circuit(parents, gates_per_block, n_t, seed, width=3):
+    """Blocks of ``width`` wires joined in a tree: block b (b >= 1) hangs below
+    block ``parents[b-1]``.  Each child block's first wire takes one CX from
+    its parent block's second wire and is cut right after it, so the
+    fragments follow the tree (a chain, or branches of any shape).  Returns
+    (circuit, cuts); T/TDG gates are placed after the cuts."""
+    rng = np.random.default_rng(seed)
+    nb = len(parents) + 1
+    c = Circuit(nb * width)
+    ops1 = [H, S, SDG, X, Y, Z]
+    child_first = {b * width for b in range(1, nb)}
+
+    def fill(count, before_cuts):
+        for _ in range(count):
+            b = int(rng.integers(nb))
+            qs = [b * width + i for i in range(width)]
+            if rng.random() < 0.45:
+                # before the cuts a child's first wire stays out of its block
+                pool = qs[1:] if (before_cuts and qs[0] in child_first) else qs
+                a, t = (int(v) for v in rng.choice(pool, size=2, replace=False))
+                c.add([CX, CZ][int(rng.integers(2))], a, t)
+            else:
+                c.add(ops1[int(rng.integers(len(ops1)))], int(rng.choice(qs)))
+
+    for q in range(c.n_qubits):
+        c.add(H, q)
+    fill(gates_per_block * nb // 2, True)
+    for b, p in enumerate(parents, start=1):
+        c.add(CX, p * width + 1, b * width)
+    cuts = [(b * width, len(c.gates)) for b in range(1, nb)]
+    start = len(c.gates)
+    fill(gates_per_block * nb // 2, False)
+    for _ in range(n_t):
+        pos = int(rng.integers(start, len(c.gates) + 1))
+        c.gates.insert(pos, (T if rng.random() < 0.5 else TDG, int(rng.integers(c.n_qubits)), -1))
+    return c, cuts
+
+
 def t_to_s(circuit):
     """Replace every T by S and TDG by SDG (the circuit becomes Clifford)."""
     c = Circuit(circuit.n_qubits)
