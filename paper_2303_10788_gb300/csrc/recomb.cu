@@ -991,7 +991,7 @@ __device__ float fold_z_value(const DevRes& R, const FragDev& F, int zi, int Pi)
 // <Z_S> = 2^-k sum_P prod_f T_f^S(P|f): one block per (problem, string),
 // FP32 products, FP64 sums, fixed-order tree reduction; T_f^S is folded from
 // the variants' Z values here (no separate fold pass).
-__device__ void z_string_block(const DevPlan& P, const DevRes& R, const long long* prefix, int np, long long g,
+__device__ __noinline__ void z_string_block(const DevPlan& P, const DevRes& R, const long long* prefix, int np, long long g,
                                ProblemShared& S, double* red, float* s_tz, int tz_cap, double* zexp_out, KRange kr) {
   const int pi = find_seg(prefix, np, g);
   const ProblemDev& Pb = P.problems[pi];
@@ -1049,28 +1049,25 @@ __device__ void z_string_block(const DevPlan& P, const DevRes& R, const long lon
 // One operand entry as a float: FP32 as stored, or an int16 count sum times 1/shots.
 __device__ __forceinline__ float hub_elem(const float* A, float, long long i) { return A[i]; }
 __device__ __forceinline__ float hub_elem(const int16_t* A, float sc, long long i) { return (float)A[i] * sc; }
-// Four consecutive operand entries (16-byte FP32 or 8-byte int16 load; the
-// caller guarantees the alignment).
-__device__ __forceinline__ void hub_vec4(const float* A, float, long long i, float (&v)[4]) {
-  const float4 q = __ldg(reinterpret_cast<const float4*>(A + i));
-  v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+// VW consecutive operand entries as one load (16/8/4-byte FP32, 8/4/2-byte
+// int16), kept packed until used; the caller guarantees the alignment.
+template <class T, int VW> struct RawVec;
+template <> struct RawVec<float, 4> { using type = float4; };
+template <> struct RawVec<float, 2> { using type = float2; };
+template <> struct RawVec<float, 1> { using type = float; };
+template <> struct RawVec<int16_t, 4> { using type = int2; };
+template <> struct RawVec<int16_t, 2> { using type = int; };
+template <> struct RawVec<int16_t, 1> { using type = short; };
+__device__ __forceinline__ float raw_at(const float4& q, int v, float) {
+  return v == 0 ? q.x : v == 1 ? q.y : v == 2 ? q.z : q.w;
 }
-__device__ __forceinline__ void hub_vec4(const int16_t* A, float sc, long long i, float (&v)[4]) {
-  const int2 q = __ldg(reinterpret_cast<const int2*>(A + i));
-  v[0] = (float)(int)(short)(q.x & 0xffff) * sc;
-  v[1] = (float)(q.x >> 16) * sc;
-  v[2] = (float)(int)(short)(q.y & 0xffff) * sc;
-  v[3] = (float)(q.y >> 16) * sc;
+__device__ __forceinline__ float raw_at(const float2& q, int v, float) { return v == 0 ? q.x : q.y; }
+__device__ __forceinline__ float raw_at(float q, int, float) { return q; }
+__device__ __forceinline__ float raw_at(int q, int v, float sc) {
+  return (float)(v ? (q >> 16) : (int)(short)(q & 0xffff)) * sc;
 }
-__device__ __forceinline__ void hub_vec2(const float* A, float, long long i, float (&v)[2]) {
-  const float2 q = __ldg(reinterpret_cast<const float2*>(A + i));
-  v[0] = q.x; v[1] = q.y;
-}
-__device__ __forceinline__ void hub_vec2(const int16_t* A, float sc, long long i, float (&v)[2]) {
-  const int q = __ldg(reinterpret_cast<const int*>(A + i));
-  v[0] = (float)(int)(short)(q & 0xffff) * sc;
-  v[1] = (float)(q >> 16) * sc;
-}
+__device__ __forceinline__ float raw_at(const int2& q, int v, float sc) { return raw_at(v < 2 ? q.x : q.y, v & 1, sc); }
+__device__ __forceinline__ float raw_at(short q, int, float sc) { return (float)q * sc; }
 __device__ __forceinline__ void neumaier(float& sum, float& comp, float p) {
   const float t = sum + p;                     // keep the low part the sum loses
   comp += fabsf(sum) >= fabsf(p) ? (sum - t) + p : (p - t) + sum;
@@ -1082,8 +1079,9 @@ __device__ __forceinline__ void neumaier(float& sum, float& comp, float p) {
 // (r: the other leaves' digits, g: this leaf's, x: its outputs), each thread
 // VW consecutive hub outputs (one vector load per row) and two outputs x
 // (every operand load used twice), four rows in flight.
-constexpr int kFirstVec = 4;    // hub outputs per thread of the first-leaf pass (one vector load)
-constexpr int kFirstX = 1;      // leaf outputs per thread (1 or 2)
+template <class T> constexpr int first_vec() { return sizeof(T) == 2 ? 4 : 2; }   // hub outputs per thread
+constexpr int kFirstX = 2;      // leaf outputs per thread (1 or 2)
+constexpr int kFirstRows = 4;   // operand rows in flight per thread (divides 4^slots)
 template <int VW, int NX, class T, class Expand>
 __device__ __forceinline__ void first_leaf_global(const T* __restrict__ At, float sc, int bf16, long long Mfull,
                                                   int lm, int lG, int ml, int lrest, long long klo, long long khi,
@@ -1102,10 +1100,11 @@ __device__ __forceinline__ void first_leaf_global(const T* __restrict__ At, floa
 #pragma unroll
     for (int v = 0; v < VW; ++v) { s0[v] = c0[v] = 0.f; if (NX == 2) s1[v] = c1[v] = 0.f; }
     const T* base = At + mv * VW;
-    for (int g0 = 0; g0 < G; g0 += 4) {        // G = 4^slots: a multiple of 4
-      float a[4][VW];
+    for (int g0 = 0; g0 < G; g0 += kFirstRows) {
+      using Raw = typename RawVec<T, VW>::type;
+      Raw a[kFirstRows];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < kFirstRows; ++u) {
         const int g = g0 + u;
         int kg;
         if (kg_tab) kg = kg_tab[g];
@@ -1114,23 +1113,17 @@ __device__ __forceinline__ void first_leaf_global(const T* __restrict__ At, floa
           for (int i = 0; i < S.ns[l]; ++i) kg |= ((g >> (2 * i)) & 3) << (2 * S.slot_cut[l][i]);
         }
         const long long kk = (long long)(kr | kg);
-        if (kk >= klo && kk < khi) {
-          if constexpr (VW == 4) hub_vec4(base, sc, kk * Mfull, a[u]);
-          else if constexpr (VW == 2) hub_vec2(base, sc, kk * Mfull, a[u]);
-          else a[u][0] = hub_elem(base, sc, kk * Mfull);
-        } else {
-#pragma unroll
-          for (int v = 0; v < VW; ++v) a[u][v] = 0.f;
-        }
+        a[u] = (kk >= klo && kk < khi) ? __ldg(reinterpret_cast<const Raw*>(base + kk * Mfull)) : Raw{};
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < kFirstRows; ++u) {
         const int g = g0 + u;
         float t0 = tv[x0 * G + g], t1 = nx == 2 ? tv[(x0 + 1) * G + g] : 0.f;
         if (bf16 && !tv_rounded) { t0 = to_bf16f(t0); t1 = to_bf16f(t1); }
 #pragma unroll
         for (int v = 0; v < VW; ++v) {
-          const float av = bf16 ? to_bf16f(a[u][v]) : a[u][v];
+          float av = raw_at(a[u], v, sc);
+          if (bf16) av = to_bf16f(av);
           neumaier(s0[v], c0[v], av * t0);
           if (NX == 2 && nx == 2) neumaier(s1[v], c1[v], av * t1);
         }
@@ -1217,8 +1210,8 @@ __device__ __forceinline__ void contract_item(const DevPlan& P, const DevRes& R,
     const int lout = lA + S.m[l], A = 1 << lA;
     if (l == first && !staged0) {
       const float* tv = tstaged ? s_T : R.TQ + S.T_off[l];
-      if ((1 << lm) >= kFirstVec)              // aligned vectors: T_off and m0 are multiples of TM
-        first_leaf_global<kFirstVec, kFirstX>(At, sc, precision == CCS_BF16, Mfull, lm, lG, S.m[l], lrest, klo, khi, tv, tstaged,
+      if ((1 << lm) >= first_vec<T>())         // aligned vectors: T_off and m0 are multiples of TM
+        first_leaf_global<first_vec<T>(), kFirstX>(At, sc, precision == CCS_BF16, Mfull, lm, lG, S.m[l], lrest, klo, khi, tv, tstaged,
                              kg_tab, S, l, expand, Y);
       else
         first_leaf_global<1, kFirstX>(At, sc, precision == CCS_BF16, Mfull, lm, lG, S.m[l], lrest, klo, khi, tv, tstaged,
