@@ -365,6 +365,25 @@ __device__ __forceinline__ float4 hub4(const int16_t* p) {
   const short4 v = *reinterpret_cast<const short4*>(p);
   return make_float4((float)v.x, (float)v.y, (float)v.z, (float)v.w);
 }
+// VW consecutive operand entries as one load (16/8/4-byte FP32, 8/4/2-byte
+// int16), kept packed until used; the caller guarantees the alignment.
+template <class T, int VW> struct RawVec;
+template <> struct RawVec<float, 4> { using type = float4; };
+template <> struct RawVec<float, 2> { using type = float2; };
+template <> struct RawVec<float, 1> { using type = float; };
+template <> struct RawVec<int16_t, 4> { using type = int2; };
+template <> struct RawVec<int16_t, 2> { using type = int; };
+template <> struct RawVec<int16_t, 1> { using type = short; };
+__device__ __forceinline__ float raw_at(const float4& q, int v, float) {
+  return v == 0 ? q.x : v == 1 ? q.y : v == 2 ? q.z : q.w;
+}
+__device__ __forceinline__ float raw_at(const float2& q, int v, float) { return v == 0 ? q.x : q.y; }
+__device__ __forceinline__ float raw_at(float q, int, float) { return q; }
+__device__ __forceinline__ float raw_at(int q, int v, float sc) {
+  return (float)(v ? (q >> 16) : (int)(short)(q & 0xffff)) * sc;
+}
+__device__ __forceinline__ float raw_at(const int2& q, int v, float sc) { return raw_at(v < 2 ? q.x : q.y, v & 1, sc); }
+__device__ __forceinline__ float raw_at(short q, int, float sc) { return (float)q * sc; }
 __device__ __forceinline__ float4 hub4_stream(const float* p) { return __ldcs(reinterpret_cast<const float4*>(p)); }
 __device__ __forceinline__ float4 hub4_stream(const int16_t* p) {
   const int2 w = __ldcs(reinterpret_cast<const int2*>(p));
@@ -711,16 +730,19 @@ __global__ void __launch_bounds__(288, 2) gemm_fact_bulk_kernel(const T* __restr
 #pragma unroll
       for (int x = 0; x < N1; ++x) y[a][x] = 0.f;
     const T* as = A_s + (size_t)st * G1 * nc * 4 + threadIdx.x * 4;
-    for (int g = 0; g < G1; ++g) {
-      const float4 v = hub4(as + (size_t)g * nc * 4);
+    using Raw = typename RawVec<T, 4>::type;
+    for (int g = 0; g < G1; g += 4) {          // G1 = 4^s1: four rows' loads in flight, kept packed
+      Raw v[4];
 #pragma unroll
-      for (int x = 0; x < N1; ++x) {
-        const float t = T1s[x * G1 + g];
-        y[0][x] = fmaf(v.x, t, y[0][x]);
-        y[1][x] = fmaf(v.y, t, y[1][x]);
-        y[2][x] = fmaf(v.z, t, y[2][x]);
-        y[3][x] = fmaf(v.w, t, y[3][x]);
-      }
+      for (int u = 0; u < 4; ++u) v[u] = *reinterpret_cast<const Raw*>(as + (size_t)(g + u) * nc * 4);
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int x = 0; x < N1; ++x) {
+          const float t = T1s[x * G1 + g + u];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) y[a][x] = fmaf(raw_at(v[u], a, 1.f), t, y[a][x]);
+        }
     }
     __syncwarp();
     if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[st])) : "memory");
@@ -1049,25 +1071,6 @@ __device__ __noinline__ void z_string_block(const DevPlan& P, const DevRes& R, c
 // One operand entry as a float: FP32 as stored, or an int16 count sum times 1/shots.
 __device__ __forceinline__ float hub_elem(const float* A, float, long long i) { return A[i]; }
 __device__ __forceinline__ float hub_elem(const int16_t* A, float sc, long long i) { return (float)A[i] * sc; }
-// VW consecutive operand entries as one load (16/8/4-byte FP32, 8/4/2-byte
-// int16), kept packed until used; the caller guarantees the alignment.
-template <class T, int VW> struct RawVec;
-template <> struct RawVec<float, 4> { using type = float4; };
-template <> struct RawVec<float, 2> { using type = float2; };
-template <> struct RawVec<float, 1> { using type = float; };
-template <> struct RawVec<int16_t, 4> { using type = int2; };
-template <> struct RawVec<int16_t, 2> { using type = int; };
-template <> struct RawVec<int16_t, 1> { using type = short; };
-__device__ __forceinline__ float raw_at(const float4& q, int v, float) {
-  return v == 0 ? q.x : v == 1 ? q.y : v == 2 ? q.z : q.w;
-}
-__device__ __forceinline__ float raw_at(const float2& q, int v, float) { return v == 0 ? q.x : q.y; }
-__device__ __forceinline__ float raw_at(float q, int, float) { return q; }
-__device__ __forceinline__ float raw_at(int q, int v, float sc) {
-  return (float)(v ? (q >> 16) : (int)(short)(q & 0xffff)) * sc;
-}
-__device__ __forceinline__ float raw_at(const int2& q, int v, float sc) { return raw_at(v < 2 ? q.x : q.y, v & 1, sc); }
-__device__ __forceinline__ float raw_at(short q, int, float sc) { return (float)q * sc; }
 __device__ __forceinline__ void neumaier(float& sum, float& comp, float p) {
   const float t = sum + p;                     // keep the low part the sum loses
   comp += fabsf(sum) >= fabsf(p) ? (sum - t) + p : (p - t) + sum;
@@ -1100,7 +1103,7 @@ __device__ __forceinline__ void first_leaf_global(const T* __restrict__ At, floa
 #pragma unroll
     for (int v = 0; v < VW; ++v) { s0[v] = c0[v] = 0.f; if (NX == 2) s1[v] = c1[v] = 0.f; }
     const T* base = At + mv * VW;
-    for (int g0 = 0; g0 < G; g0 += kFirstRows) {
+    for (int g0 = 0; g0 < G; g0 += kFirstRows) {      // G = 4^slots >= 4 (a leaf without cuts is staged)
       using Raw = typename RawVec<T, VW>::type;
       Raw a[kFirstRows];
 #pragma unroll
@@ -1164,7 +1167,9 @@ __device__ __forceinline__ void contract_item(const DevPlan& P, const DevRes& R,
   };
   int first = 0;
   while (first < S.nf && first == S.hub) ++first;
-  const bool staged0 = first >= S.nf;         // no leaf: the operand is the result
+  // no leaf: the operand is the result; a first leaf without cuts: the operand
+  // slice staged (it fits: every leaf's intermediate holds K x TM floats then)
+  const bool staged0 = first >= S.nf || S.ns[first] == 0;
   if (staged0) {
     for (int t0 = threadIdx.x; t0 < K * M; t0 += 8 * blockDim.x) {   // 8 loads in flight per thread
       float v[8];
