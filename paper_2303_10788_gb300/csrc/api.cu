@@ -1265,6 +1265,10 @@ int ccs_eval_variants(ccs_ctx c, ccs_plan p, const ccs_eval_opts* opts, ccs_res*
     e.shots = opts->mode == CCS_SAMPLED ? opts->shots : 0;
     e.seed_lo = opts->seed_lo;
     e.seed_hi = opts->seed_hi;
+    for (int rd = 0; rd < 10; ++rd) {
+      e.keys.k[rd][0] = e.seed_lo + (uint32_t)rd * 0x9E3779B9u;
+      e.keys.k[rd][1] = e.seed_hi + (uint32_t)rd * 0xBB67AE85u;
+    }
     e.keep_tableaus = opts->keep_tableaus && r->have_tabs;
     e.shared_body = opts->per_variant_body ? 0 : 1;
     e.screen = e.shared_body && p->dp.n_cliff_frags > 0 && !e.keep_tableaus;

@@ -1146,17 +1146,15 @@ __device__ __forceinline__ void build_tables(uint32_t (*tbl)[256], const SpaceRe
 
 // --- K3: Philox4x32-10 counter-based sampling from the affine space -------
 namespace {
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const PhiloxKeys& K) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    if (r) {
-      k0 += 0x9E3779B9u;
-      k1 += 0xBB67AE85u;
-    }
-    // each 32 x 32 -> 64-bit product is one wide multiply (high and low words)
+    // each 32 x 32 -> 64-bit product is one wide multiply (high and low words);
+    // the round keys are launch constants
     const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
     const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
-    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k1, (uint32_t)p0);
+    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ K.k[r][0], (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ K.k[r][1],
+                   (uint32_t)p0);
   }
   return c;
 }
@@ -1168,12 +1166,12 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 // word j field h being shot (4 g + j) S + h.  fn receives the shot's rank
 // coefficient bits.
 template <int L, class Fn>
-__device__ __forceinline__ void for_shots(uint32_t t0, uint32_t t1, uint4 ctr, uint32_t k0, uint32_t k1,
-                                          uint32_t cmask, Fn fn) {
+__device__ __forceinline__ void for_shots(uint32_t t0, uint32_t t1, uint4 ctr, const PhiloxKeys& K, uint32_t cmask,
+                                          Fn fn) {
   constexpr int S = L == 1 ? 4 : L == 2 ? 2 : 1, WB = 32 / S;
   for (uint32_t g = t0 / (4 * S) + threadIdx.x; (unsigned long long)(4 * S) * g < t1; g += blockDim.x) {
     ctr.x = g;
-    const uint4 o = philox4x32_10(ctr, k0, k1);
+    const uint4 o = philox4x32_10(ctr, K);
     const uint32_t w4[4] = {o.x, o.y, o.z, o.w};
     if ((unsigned long long)(4 * S) * (g + 1) <= t1) {    // every shot of the call is in range
 #pragma unroll
@@ -1247,7 +1245,7 @@ __global__ void __launch_bounds__(256) sample_kernel(DevPlan P, DevRes R, EvalPa
   const uint4 ctr = make_uint4(0u, (uint32_t)v, (uint32_t)F.findex, (uint32_t)F.problem);
   by_rank(rank, [&](auto lk) {
     constexpr int L = decltype(lk)::value;
-    for_shots<L>(t0, s_end, ctr, E.seed_lo, E.seed_hi, cmask, [&](uint32_t c) {
+    for_shots<L>(t0, s_end, ctr, E.keys, cmask, [&](uint32_t c) {
       const uint32_t y = space_point<L>(tbl, off, c);
       if (smem_hist) atomicAdd(&hist[y], 1u);
       else atomicAdd(&gcounts[y], 1u);
@@ -1381,7 +1379,7 @@ __global__ void __launch_bounds__(512) sample_hub_kernel(DevPlan P, DevRes R, Ev
     const uint4 ctr = make_uint4(0u, (uint32_t)v, (uint32_t)F.findex, (uint32_t)F.problem);
     by_rank(rank, [&](auto lk) {
       constexpr int L = decltype(lk)::value;
-      for_shots<L>(0u, E.shots, ctr, E.seed_lo, E.seed_hi, cmask, [&](uint32_t c) {
+      for_shots<L>(0u, E.shots, ctr, E.keys, cmask, [&](uint32_t c) {
         const uint32_t y = ident ? c : space_point<L>(tbl, off, c);   // full rank: the coefficient bits
         if (wide) atomicAdd(&hist2[y], 1u);
         else atomicAdd(&hist2[y >> 1], 1u << ((y & 1u) << 4));
@@ -1641,8 +1639,10 @@ __device__ __forceinline__ unsigned hub8_readout(const uint32_t* __restrict__ h3
 // carries at most 1 into the next), is counted again with 16-bit counters
 // in two passes, each over the outputs o of one half (top marginal bit),
 // and its operand rows are rewritten.
-__global__ void __launch_bounds__(512, 2) sample_hub8_kernel(DevPlan P, DevRes R, EvalParams E, const int2* items,
-                                                             int keep_counts, int hist_words) {
+template <int NT>    // 256 threads (three CTAs per SM) or 512 (two): registers for each
+__global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 3) sample_hub8_kernel(DevPlan P, DevRes R, EvalParams E,
+                                                                          const int2* items, int keep_counts,
+                                                                          int hist_words) {
   extern __shared__ __align__(16) uint32_t h32[];
   __shared__ uint32_t tbl[3][256];
   __shared__ FragDev sF;
@@ -1686,10 +1686,10 @@ __global__ void __launch_bounds__(512, 2) sample_hub8_kernel(DevPlan P, DevRes R
     by_rank(rank, [&](auto lk) {
       constexpr int L = decltype(lk)::value;
       if (s_ident)      // full rank: the outcome is the coefficient bits (no table lookup)
-        for_shots<L>(0u, E.shots, ctr, E.seed_lo, E.seed_hi, cmask,
+        for_shots<L>(0u, E.shots, ctr, E.keys, cmask,
                      [&](uint32_t c) { atomicAdd(&h32[c >> 2], 1u << ((c & 3u) << 3)); });
       else
-        for_shots<L>(0u, E.shots, ctr, E.seed_lo, E.seed_hi, cmask, [&](uint32_t c) {
+        for_shots<L>(0u, E.shots, ctr, E.keys, cmask, [&](uint32_t c) {
           const uint32_t y = space_point<L>(tbl, off, c);
           atomicAdd(&h32[y >> 2], 1u << ((y & 3u) << 3));
         });
@@ -1724,7 +1724,7 @@ __global__ void __launch_bounds__(512, 2) sample_hub8_kernel(DevPlan P, DevRes R
       const uint4 ctr = make_uint4(0u, (uint32_t)v, (uint32_t)F.findex, (uint32_t)F.problem);
       by_rank(rank, [&](auto lk) {
         constexpr int L = decltype(lk)::value;
-        for_shots<L>(0u, E.shots, ctr, E.seed_lo, E.seed_hi, cmask, [&](uint32_t c) {
+        for_shots<L>(0u, E.shots, ctr, E.keys, cmask, [&](uint32_t c) {
           const uint32_t y = space_point<L>(tbl, off, c);
           if ((int)((y >> mh) & 1u) != h) return;
           const uint32_t yh = (y & (uint32_t)(Mh - 1)) | ((y >> m) << mh);
@@ -1847,9 +1847,10 @@ cudaError_t launch_sample_hub(const DevPlan& p, const DevRes& r, const EvalParam
     const int t8 = threads >= 512 ? 512 : 256;
     const int hist_words = (1 << max_nA) / 4;
     const size_t smem = (size_t)4 * hist_words + (size_t)t8 * (e.shots <= 32767u ? 0 : 33) * 4;
-    cudaError_t err = cudaFuncSetAttribute(sample_hub8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = t8 == 512 ? sample_hub8_kernel<512> : sample_hub8_kernel<256>;
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    sample_hub8_kernel<<<n_items, t8, smem, s>>>(p, r, e, items, keep_counts, hist_words); note_launch();
+    kern<<<n_items, t8, smem, s>>>(p, r, e, items, keep_counts, hist_words); note_launch();
     return cudaGetLastError();
   }
   const int wide = e.shots > 0xffffu ? 1 : 0;     // 32-bit counters when 16 bits could overflow

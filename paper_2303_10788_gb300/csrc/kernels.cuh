@@ -152,9 +152,17 @@ constexpr long long kDirectSmemFloats = 12288;
 // Variants per block of Z-string values (about 256 (variant, string) pairs).
 __host__ __device__ inline int zblock_variants(int nz) { return nz >= 256 ? 1 : 256 / nz; }
 
+// Philox4x32-10 round keys of the key (seed_lo, seed_hi): round r uses
+// (seed_lo + r W0, seed_hi + r W1) mod 2^32, W0 = 0x9E3779B9, W1 = 0xBB67AE85
+// (the generator's Weyl sequence), tabulated once on the host.
+struct PhiloxKeys {
+  uint32_t k[10][2];
+};
+
 struct EvalParams {
   int mode;                   // CCS_EXACT / CCS_SAMPLED / CCS_STITCH
   uint32_t shots, seed_lo, seed_hi;
+  PhiloxKeys keys;            // round keys of (seed_lo, seed_hi)
   int keep_tableaus;
   int shared_body;            // 1: variants start from their fragment's body tableau
   int screen;                 // 1: the screen finishes every Clifford variant (no tableau kernel)

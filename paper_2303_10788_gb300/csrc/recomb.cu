@@ -917,40 +917,58 @@ __global__ void __launch_bounds__(256) hub_bf16_kernel(HubView QT, __nv_bfloat16
   }
 }
 
-__global__ void reduce_scatter_kernel(DevPlan P, const long long* prefix, int np, long long total,
-                                      const float* scratch, double* marg_out, int use_tc) {
-  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
-       g += (long long)gridDim.x * blockDim.x) {
-    const int pi = find_seg(prefix, np, g);
-    const ProblemDev& Pb = P.problems[pi];
-    if (Pb.direct || Pb.general) continue;    // written by the leaf-by-leaf or the general contraction
-    const long long loc = g - prefix[pi];
-    const long long m = loc / Pb.N, n = loc - m * Pb.N;
-    const int splits = (Pb.stream && !(use_tc && Pb.tc)) ? Pb.ssplits : Pb.splits;
-    // four independent FP64 sums (more loads in flight), combined in a fixed order
-    const float* pp = scratch + Pb.part_off + m * Pb.N + n;
-    const long long st = (long long)Pb.M * Pb.N;
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-    int s = 0;
-    for (; s + 4 <= splits; s += 4) {
-      a0 += (double)pp[(long long)s * st];
-      a1 += (double)pp[(long long)(s + 1) * st];
-      a2 += (double)pp[(long long)(s + 2) * st];
-      a3 += (double)pp[(long long)(s + 3) * st];
+// The split-K partials summed in FP64 and scattered to marginal order.  A
+// CTA takes 32 consecutive outputs (one per lane, so every load of a warp is
+// one contiguous row segment); its 8 warps sum splits w, w + 8, ... and the
+// warps' sums are added in warp order: a fixed order, many loads in flight.
+__global__ void __launch_bounds__(256) reduce_scatter_kernel(DevPlan P, const long long* prefix, int np,
+                                                             long long total, const float* scratch, double* marg_out,
+                                                             int use_tc) {
+  __shared__ double red[8][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (long long base = blockIdx.x * 32ll; base < total; base += gridDim.x * 32ll) {
+    const long long g = base + lane;
+    double a0 = 0.0, a1 = 0.0;
+    int pi = -1;
+    if (g < total) {
+      pi = find_seg(prefix, np, g);
+      const ProblemDev& Pb = P.problems[pi];
+      if (Pb.direct || Pb.general) pi = -1;   // written by the leaf-by-leaf or the general contraction
+      else {
+        const long long loc = g - prefix[pi];
+        const int splits = (Pb.stream && !(use_tc && Pb.tc)) ? Pb.ssplits : Pb.splits;
+        const float* pp = scratch + Pb.part_off + loc;    // partial [split][m][n]: loc = m N + n
+        const long long st = (long long)Pb.M * Pb.N;
+        int s = w;
+        for (; s + 8 < splits; s += 16) {
+          a0 += (double)pp[(long long)s * st];
+          a1 += (double)pp[(long long)(s + 8) * st];
+        }
+        if (s < splits) a0 += (double)pp[(long long)s * st];
+      }
     }
-    for (; s < splits; ++s) a0 += (double)pp[(long long)s * st];
-    const double acc = (a0 + a1) + (a2 + a3);
-    long long o = 0;
-    const FragDev& Hb = P.frags[Pb.frag0 + Pb.hub];
-    for (int j = 0; j < Hb.m; ++j) o |= ((m >> j) & 1) << Hb.marg_pos[j];
-    int off = 0;
-    for (int l = 0; l < Pb.n_frags; ++l) {
-      if (l == Pb.hub) continue;
-      const FragDev& L = P.frags[Pb.frag0 + l];
-      for (int j = 0; j < L.m; ++j) o |= ((n >> (off + j)) & 1) << L.marg_pos[j];
-      off += L.m;
+    red[w][lane] = a0 + a1;
+    __syncthreads();
+    if (w == 0 && pi >= 0) {
+      const ProblemDev& Pb = P.problems[pi];
+      double acc = red[0][lane];
+#pragma unroll
+      for (int j = 1; j < 8; ++j) acc += red[j][lane];
+      const long long loc = g - prefix[pi];
+      const long long m = loc / Pb.N, n = loc - m * Pb.N;
+      long long o = 0;
+      const FragDev& Hb = P.frags[Pb.frag0 + Pb.hub];
+      for (int j = 0; j < Hb.m; ++j) o |= ((m >> j) & 1) << Hb.marg_pos[j];
+      int off = 0;
+      for (int l = 0; l < Pb.n_frags; ++l) {
+        if (l == Pb.hub) continue;
+        const FragDev& L = P.frags[Pb.frag0 + l];
+        for (int j = 0; j < L.m; ++j) o |= ((n >> (off + j)) & 1) << L.marg_pos[j];
+        off += L.m;
+      }
+      marg_out[Pb.marg_off + o] = ldexp(acc, -Pb.k);
     }
-    marg_out[Pb.marg_off + o] = ldexp(acc, -Pb.k);
+    __syncthreads();
   }
 }
 
@@ -1412,7 +1430,7 @@ cudaError_t launch_recombine(const DevPlan& p, const DevRes& r, int precision, c
       }
     }
     {
-      reduce_scatter_kernel<<<grid(z.out_total, 256), 256, 0, s>>>(p, z.out_prefix, p.n_problems, z.out_total,
+      reduce_scatter_kernel<<<grid(z.out_total, 32), 256, 0, s>>>(p, z.out_prefix, p.n_problems, z.out_total,
                                                                   scratch, marg_out, use_tc ? 1 : 0); note_launch();
       if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
