@@ -1127,18 +1127,19 @@ __global__ void __launch_bounds__(512) clifford_kernel(DevPlan P, DevRes R, Eval
 // Lookup tables of a variant's affine space: tbl[k][byte] = XOR of the basis
 // vectors 8k + b selected by byte's bits, only for the ceil(rank / 8)
 // groups that exist (entry 0 of the others is 0, which is all a shot of
-// rank-limited coefficients can select there).
+// rank-limited coefficients can select there).  The basis is read once into
+// shared memory; every thread of the block must call this (it synchronises).
 __device__ __forceinline__ void build_tables(uint32_t (*tbl)[256], const SpaceRec& sp, int rank) {
+  __shared__ uint32_t s_b[kMaxMeas];
   const int ntab = rank > 16 ? 3 : rank > 8 ? 2 : 1;
+  if ((int)threadIdx.x < kMaxMeas) s_b[threadIdx.x] = (int)threadIdx.x < rank ? sp.basis[threadIdx.x] : 0u;
+  __syncthreads();
   for (int t = threadIdx.x; t < ntab * 256; t += blockDim.x) {
     const int k = t >> 8, byte = t & 255;
     uint32_t acc = 0;
 #pragma unroll
-    for (int b = 0; b < 8; ++b) {
-      const int j = 8 * k + b;
-      const uint32_t bj = j < rank ? sp.basis[j] : 0u;
-      if ((byte >> b) & 1) acc ^= bj;
-    }
+    for (int b = 0; b < 8; ++b)
+      if ((byte >> b) & 1) acc ^= s_b[8 * k + b];
     tbl[k][byte] = acc;
   }
   if ((int)threadIdx.x < 3 - ntab) tbl[ntab + threadIdx.x][0] = 0u;
@@ -1339,181 +1340,6 @@ __device__ __forceinline__ void hub_pair_out_packed(unsigned (&p)[16], const int
 
 }  // namespace
 
-// --- K3 + K5 fused for the hub of a star --------------------------------
-// One CTA per hub variant: all its shots into a shared-memory histogram
-// (16-bit counters packed in pairs, so |A| <= 16 fits 128 KB), then the
-// variant's slice of the hub operand
-//   Q[o, (s, P_out)] = sum_b prod_j lambda(P_out_j, b_j) count(o, b) / shots
-// for every P_out with beta(P_out) = the variant's bases, written to the
-// transposed store Q^T.  Dense counts are written only when kept for
-// inspection.
-__global__ void __launch_bounds__(512) sample_hub_kernel(DevPlan P, DevRes R, EvalParams E, const int2* items,
-                                                         int keep_counts, int wide, int hist_words) {
-  extern __shared__ __align__(16) uint32_t hist2[];
-  __shared__ uint32_t tbl[3][256];
-  __shared__ FragDev sF;
-  __shared__ int s_czD[16], s_czS[16];
-  const int2 it = items[blockIdx.x];
-  {
-    const int* src = reinterpret_cast<const int*>(P.frags + it.x);
-    int* dst = reinterpret_cast<int*>(&sF);
-    for (int i = threadIdx.x; i < (int)(sizeof(FragDev) / 4); i += blockDim.x) dst[i] = src[i];
-  }
-  __syncthreads();
-  const FragDev& F = sF;
-  const int v = it.y, nA = F.nA;
-  const SpaceRec& sp = R.spaces[F.space_off + v];
-  const int rank = sp.rank;
-  const uint32_t off = sp.off;
-  build_tables(tbl, sp, rank);
-  const bool ident = space_is_identity(sp, rank, nA);   // every thread: the same answer
-  const int nwords = wide ? (1 << nA) : ((1 << nA) > 1 ? (1 << (nA - 1)) : 1);
-  {   // zero the histogram, 16 bytes per store
-    uint4* h4 = reinterpret_cast<uint4*>(hist2);
-    for (int i = threadIdx.x; i < nwords / 4; i += blockDim.x) h4[i] = make_uint4(0u, 0u, 0u, 0u);
-    for (int i = 4 * (nwords / 4) + threadIdx.x; i < nwords; i += blockDim.x) hist2[i] = 0u;
-  }
-  __syncthreads();
-  const uint32_t cmask = rank >= 32 ? 0xffffffffu : ((1u << rank) - 1u);
-  {
-    const uint4 ctr = make_uint4(0u, (uint32_t)v, (uint32_t)F.findex, (uint32_t)F.problem);
-    by_rank(rank, [&](auto lk) {
-      constexpr int L = decltype(lk)::value;
-      for_shots<L>(0u, E.shots, ctr, E.keys, cmask, [&](uint32_t c) {
-        const uint32_t y = ident ? c : space_point<L>(tbl, off, c);   // full rank: the coefficient bits
-        if (wide) atomicAdd(&hist2[y], 1u);
-        else atomicAdd(&hist2[y >> 1], 1u << ((y & 1u) << 4));
-      });
-    });
-  }
-  __syncthreads();
-  auto count = [&](uint32_t y) -> uint32_t {
-    return wide ? hist2[y] : (hist2[y >> 1] >> ((y & 1u) << 4)) & 0xffffu;
-  };
-  if (keep_counts) {
-    uint32_t* g = R.counts + F.counts_off + ((long long)v << nA);
-    for (uint32_t y = threadIdx.x; y < (1u << nA); y += blockDim.x) g[y] = count(y);
-  }
-  // the variant's digits: preparations at input slots, bases at output slots
-  int beta[kMaxCuts];
-  {
-    int t = v;
-    for (int i = 0; i < F.qin; ++i) t /= 4;
-    for (int j = 0; j < F.qout; ++j) { beta[j] = t % 3; t /= 3; }
-  }
-  int zpos[kMaxCuts], zout[kMaxCuts], nz = 0;
-  int Dbase = 0, fixed_mask = 0;   // fixed_mask: X/Y-basis outputs, whose outcome always flips the sign
-  for (int j = 0; j < F.n_slots; ++j) {
-    const int code = F.slot_code[j], idx = code & 255;
-    if ((code >> 8) == 0) {
-      int t = v;
-      for (int i = 0; i < idx; ++i) t /= 4;
-      Dbase |= (t % 4) << (2 * j);
-    } else if (beta[idx] == 2) {
-      zpos[nz] = j;                           // Z basis: P_out in {I, Z}
-      zout[nz++] = idx;
-    } else {
-      Dbase |= (beta[idx] == 0 ? 1 : 2) << (2 * j);   // X basis -> X, Y basis -> Y
-      fixed_mask |= 1 << idx;
-    }
-  }
-  // Q is stored transposed, Q^T[D][o] (o fastest), so each D of the variant
-  // is one coalesced row of 2^m floats.
-  const int m = F.m, M = 1 << m, nb = 1 << F.qout;
-  const float inv = (float)E.inv_shots;
-  float* QT = R.TQ + F.T_off;
-  int16_t* QH = R.hub_i16 ? reinterpret_cast<int16_t*>(R.TQ + F.T_off) : nullptr;
-  if (!wide && m >= 1 && F.qout <= 4 && E.shots <= (1u << 26)) {
-    // Pairs of outputs (o, o+1) share the packed counter words.  Per pair,
-    // a 16-point Walsh-Hadamard transform over the output bits gives the
-    // signed sum for every sign mask at once; each thread parks it in its
-    // own 33-word slot after the histogram (odd stride: no bank conflicts)
-    // and picks the variant's masks; below 32768 shots the transform runs
-    // on packed lanes and picks from registers, with no slot.
-    if ((int)threadIdx.x < (1 << nz)) {
-      int D = Dbase, smask = fixed_mask;
-      for (int i = 0; i < nz; ++i)
-        if ((threadIdx.x >> i) & 1) { D |= 3 << (2 * zpos[i]); smask |= 1 << zout[i]; }
-      s_czD[threadIdx.x] = D;
-      s_czS[threadIdx.x] = smask;
-    }
-    __syncthreads();
-    int* wht = reinterpret_cast<int*>(hist2 + hist_words) + threadIdx.x * (E.shots <= 32767u ? 0 : 33);
-    if (E.shots <= 32767u) {
-      // an output's bins sum to at most the shots, so every transform value
-      // fits a signed 16-bit lane: the counter word (outputs o, o+1) is
-      // transformed as is, two outputs per SIMD add
-      for (int o2 = threadIdx.x; o2 < (M >> 1); o2 += blockDim.x) {
-        const int o = 2 * o2;
-        unsigned pk[16];
-#pragma unroll
-        for (int b = 0; b < 16; ++b) pk[b] = b < nb ? hist2[((uint32_t)o | ((uint32_t)b << m)) >> 1] : 0u;
-        hub_pair_out_packed(pk, s_czD, s_czS, nz, QT, QH, M, o, inv);
-      }
-    } else
-    for (int o2 = threadIdx.x; o2 < (M >> 1); o2 += blockDim.x) {
-      const int o = 2 * o2;
-      int a[16], c[16];
-#pragma unroll
-      for (int b = 0; b < 16; ++b) {
-        const uint32_t w = b < nb ? hist2[((uint32_t)o | ((uint32_t)b << m)) >> 1] : 0u;
-        a[b] = (int)(w & 0xffffu);
-        c[b] = (int)(w >> 16);
-      }
-#pragma unroll
-      for (int h = 1; h < 16; h <<= 1)
-#pragma unroll
-        for (int b = 0; b < 16; ++b)
-          if (!(b & h)) {
-            const int x0 = a[b], y0 = a[b | h], x1 = c[b], y1 = c[b | h];
-            a[b] = x0 + y0;
-            a[b | h] = x0 - y0;
-            c[b] = x1 + y1;
-            c[b | h] = x1 - y1;
-          }
-#pragma unroll
-      for (int b = 0; b < 16; ++b) {
-        wht[b] = a[b];
-        wht[16 + b] = c[b];
-      }
-      for (int cz = 0; cz < (1 << nz); ++cz) {
-        const int sm = s_czS[cz];
-        put2(QT, QH, (long long)s_czD[cz] * M + o, wht[sm], wht[16 + sm], inv);
-      }
-    }
-  } else if (F.qout <= 4 && E.shots <= (1u << 26)) {     // |acc| <= 16 shots fits an int
-    for (int o = threadIdx.x; o < M; o += blockDim.x) {
-      int c[16];
-#pragma unroll
-      for (int b = 0; b < 16; ++b) c[b] = b < nb ? (int)count((uint32_t)o | ((uint32_t)b << m)) : 0;
-      for (int cz = 0; cz < (1 << nz); ++cz) {
-        int D = Dbase, smask = fixed_mask;
-        for (int i = 0; i < nz; ++i)
-          if ((cz >> i) & 1) { D |= 3 << (2 * zpos[i]); smask |= 1 << zout[i]; }
-        int acc = 0;
-#pragma unroll
-        for (int b = 0; b < 16; ++b) acc += (__popc(b & smask) & 1) ? -c[b] : c[b];
-        put1(QT, QH, (long long)D * M + o, acc, inv);
-      }
-    }
-  } else {
-    for (int cz = 0; cz < (1 << nz); ++cz) {
-      int D = Dbase, smask = fixed_mask;
-      for (int i = 0; i < nz; ++i)
-        if ((cz >> i) & 1) { D |= 3 << (2 * zpos[i]); smask |= 1 << zout[i]; }
-      for (int o = threadIdx.x; o < M; o += blockDim.x) {
-        long long acc = 0;
-        for (int b = 0; b < nb; ++b) {
-          const long long cnt = count((uint32_t)o | ((uint32_t)b << m));
-          acc += (__popc(b & smask) & 1) ? -cnt : cnt;
-        }
-        if (QH) QH[(long long)D * M + o] = (int16_t)acc;
-        else QT[(long long)D * M + o] = (float)((double)acc * E.inv_shots);
-      }
-    }
-  }
-}
-
 // The operand rows a hub variant v owns: its preparation digits at the input
 // slots, and at the output slots the Pauli its basis reads (X, Y), or I or Z
 // for a Z-basis output; one row per choice of I/Z (2^nz rows, bit i of the
@@ -1558,6 +1384,174 @@ __device__ __forceinline__ void hub_variant_rows(const FragDev& F, int v, int* s
   if (threadIdx.x == 0) {
     s_nzm[0] = nz;
     s_nzm[1] = zm;
+  }
+}
+
+// --- K3 + K5 fused for the hub of a star --------------------------------
+// One CTA per hub variant: all its shots into a shared-memory histogram
+// (16-bit counters packed in pairs, so |A| <= 16 fits 128 KB), then the
+// variant's slice of the hub operand
+//   Q[o, (s, P_out)] = sum_b prod_j lambda(P_out_j, b_j) count(o, b) / shots
+// for every P_out with beta(P_out) = the variant's bases, written to the
+// transposed store Q^T.  Dense counts are written only when kept for
+// inspection.
+__global__ void __launch_bounds__(512) sample_hub_kernel(DevPlan P, DevRes R, EvalParams E, const int2* items,
+                                                         int keep_counts, int wide, int hist_words) {
+  extern __shared__ __align__(16) uint32_t hist2[];
+  __shared__ uint32_t tbl[3][256];
+  __shared__ FragDev sF;
+  __shared__ int s_czD[16], s_czS[16], s_nzm[2], s_ident;
+  const int2 it = items[blockIdx.x];
+  {
+    const int* src = reinterpret_cast<const int*>(P.frags + it.x);
+    int* dst = reinterpret_cast<int*>(&sF);
+    for (int i = threadIdx.x; i < (int)(sizeof(FragDev) / 4); i += blockDim.x) dst[i] = src[i];
+  }
+  __syncthreads();
+  const FragDev& F = sF;
+  const int v = it.y, nA = F.nA;
+  const SpaceRec& sp = R.spaces[F.space_off + v];
+  const int rank = sp.rank;
+  const uint32_t off = sp.off;
+  build_tables(tbl, sp, rank);
+  if (threadIdx.x == 32) s_ident = space_is_identity(sp, rank, nA) ? 1 : 0;
+  if (F.qout <= 4) hub_variant_rows(F, v, s_czD, s_czS, s_nzm);   // warp 0: at most 16 rows
+  const int nwords = wide ? (1 << nA) : ((1 << nA) > 1 ? (1 << (nA - 1)) : 1);
+  {   // zero the histogram, 16 bytes per store
+    uint4* h4 = reinterpret_cast<uint4*>(hist2);
+    for (int i = threadIdx.x; i < nwords / 4; i += blockDim.x) h4[i] = make_uint4(0u, 0u, 0u, 0u);
+    for (int i = 4 * (nwords / 4) + threadIdx.x; i < nwords; i += blockDim.x) hist2[i] = 0u;
+  }
+  __syncthreads();
+  const bool ident = s_ident != 0;
+  const uint32_t cmask = rank >= 32 ? 0xffffffffu : ((1u << rank) - 1u);
+  {
+    const uint4 ctr = make_uint4(0u, (uint32_t)v, (uint32_t)F.findex, (uint32_t)F.problem);
+    by_rank(rank, [&](auto lk) {
+      constexpr int L = decltype(lk)::value;
+      for_shots<L>(0u, E.shots, ctr, E.keys, cmask, [&](uint32_t c) {
+        const uint32_t y = ident ? c : space_point<L>(tbl, off, c);   // full rank: the coefficient bits
+        if (wide) atomicAdd(&hist2[y], 1u);
+        else atomicAdd(&hist2[y >> 1], 1u << ((y & 1u) << 4));
+      });
+    });
+  }
+  __syncthreads();
+  auto count = [&](uint32_t y) -> uint32_t {
+    return wide ? hist2[y] : (hist2[y >> 1] >> ((y & 1u) << 4)) & 0xffffu;
+  };
+  if (keep_counts) {
+    uint32_t* g = R.counts + F.counts_off + ((long long)v << nA);
+    for (uint32_t y = threadIdx.x; y < (1u << nA); y += blockDim.x) g[y] = count(y);
+  }
+  // Q is stored transposed, Q^T[D][o] (o fastest), so each D of the variant
+  // is one coalesced row of 2^m floats.
+  const int m = F.m, M = 1 << m, nb = 1 << F.qout;
+  const float inv = (float)E.inv_shots;
+  float* QT = R.TQ + F.T_off;
+  int16_t* QH = R.hub_i16 ? reinterpret_cast<int16_t*>(R.TQ + F.T_off) : nullptr;
+  if (!wide && m >= 1 && F.qout <= 4 && E.shots <= (1u << 26)) {
+    // Pairs of outputs (o, o+1) share the packed counter words.  Per pair,
+    // a 16-point Walsh-Hadamard transform over the output bits gives the
+    // signed sum for every sign mask at once; each thread parks it in its
+    // own 33-word slot after the histogram (odd stride: no bank conflicts)
+    // and picks the variant's masks; below 32768 shots the transform runs
+    // on packed lanes and picks from registers, with no slot.
+    const int nz = s_nzm[0];
+    int* wht = reinterpret_cast<int*>(hist2 + hist_words) + threadIdx.x * (E.shots <= 32767u ? 0 : 33);
+    if (E.shots <= 32767u) {
+      // an output's bins sum to at most the shots, so every transform value
+      // fits a signed 16-bit lane: the counter word (outputs o, o+1) is
+      // transformed as is, two outputs per SIMD add
+      for (int o2 = threadIdx.x; o2 < (M >> 1); o2 += blockDim.x) {
+        const int o = 2 * o2;
+        unsigned pk[16];
+#pragma unroll
+        for (int b = 0; b < 16; ++b) pk[b] = b < nb ? hist2[((uint32_t)o | ((uint32_t)b << m)) >> 1] : 0u;
+        hub_pair_out_packed(pk, s_czD, s_czS, nz, QT, QH, M, o, inv);
+      }
+    } else
+    for (int o2 = threadIdx.x; o2 < (M >> 1); o2 += blockDim.x) {
+      const int o = 2 * o2;
+      int a[16], c[16];
+#pragma unroll
+      for (int b = 0; b < 16; ++b) {
+        const uint32_t w = b < nb ? hist2[((uint32_t)o | ((uint32_t)b << m)) >> 1] : 0u;
+        a[b] = (int)(w & 0xffffu);
+        c[b] = (int)(w >> 16);
+      }
+#pragma unroll
+      for (int h = 1; h < 16; h <<= 1)
+#pragma unroll
+        for (int b = 0; b < 16; ++b)
+          if (!(b & h)) {
+            const int x0 = a[b], y0 = a[b | h], x1 = c[b], y1 = c[b | h];
+            a[b] = x0 + y0;
+            a[b | h] = x0 - y0;
+            c[b] = x1 + y1;
+            c[b | h] = x1 - y1;
+          }
+#pragma unroll
+      for (int b = 0; b < 16; ++b) {
+        wht[b] = a[b];
+        wht[16 + b] = c[b];
+      }
+      for (int cz = 0; cz < (1 << nz); ++cz) {
+        const int sm = s_czS[cz];
+        put2(QT, QH, (long long)s_czD[cz] * M + o, wht[sm], wht[16 + sm], inv);
+      }
+    }
+  } else if (F.qout <= 4 && E.shots <= (1u << 26)) {     // |acc| <= 16 shots fits an int
+    const int nz = s_nzm[0];
+    for (int o = threadIdx.x; o < M; o += blockDim.x) {
+      int c[16];
+#pragma unroll
+      for (int b = 0; b < 16; ++b) c[b] = b < nb ? (int)count((uint32_t)o | ((uint32_t)b << m)) : 0;
+      for (int cz = 0; cz < (1 << nz); ++cz) {
+        const int D = s_czD[cz], smask = s_czS[cz];
+        int acc = 0;
+#pragma unroll
+        for (int b = 0; b < 16; ++b) acc += (__popc(b & smask) & 1) ? -c[b] : c[b];
+        put1(QT, QH, (long long)D * M + o, acc, inv);
+      }
+    }
+  } else {   // more than four quantum outputs: the variant's digits decoded per thread
+    int beta[kMaxCuts];
+    {
+      int t = v;
+      for (int i = 0; i < F.qin; ++i) t /= 4;
+      for (int j = 0; j < F.qout; ++j) { beta[j] = t % 3; t /= 3; }
+    }
+    int zpos[kMaxCuts], zout[kMaxCuts], nz = 0;
+    int Dbase = 0, fixed_mask = 0;   // fixed_mask: X/Y-basis outputs, whose outcome always flips the sign
+    for (int j = 0; j < F.n_slots; ++j) {
+      const int code = F.slot_code[j], idx = code & 255;
+      if ((code >> 8) == 0) {
+        int t = v;
+        for (int i = 0; i < idx; ++i) t /= 4;
+        Dbase |= (t % 4) << (2 * j);
+      } else if (beta[idx] == 2) {
+        zpos[nz] = j;                           // Z basis: P_out in {I, Z}
+        zout[nz++] = idx;
+      } else {
+        Dbase |= (beta[idx] == 0 ? 1 : 2) << (2 * j);   // X basis -> X, Y basis -> Y
+        fixed_mask |= 1 << idx;
+      }
+    }
+    for (int cz = 0; cz < (1 << nz); ++cz) {
+      int D = Dbase, smask = fixed_mask;
+      for (int i = 0; i < nz; ++i)
+        if ((cz >> i) & 1) { D |= 3 << (2 * zpos[i]); smask |= 1 << zout[i]; }
+      for (int o = threadIdx.x; o < M; o += blockDim.x) {
+        long long acc = 0;
+        for (int b = 0; b < nb; ++b) {
+          const long long cnt = count((uint32_t)o | ((uint32_t)b << m));
+          acc += (__popc(b & smask) & 1) ? -cnt : cnt;
+        }
+        if (QH) QH[(long long)D * M + o] = (int16_t)acc;
+        else QT[(long long)D * M + o] = (float)((double)acc * E.inv_shots);
+      }
+    }
   }
 }
 
