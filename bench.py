@@ -571,6 +571,10 @@ def run_ours(args, rank, world, local_rank):
 
     def build():
         if not hasattr(tls, "ctx"):
+            # each builder on a stream of its own (a non-blocking stream: its
+            # plan uploads never wait for the evaluation on the main stream)
+            tls.stream = torch.cuda.Stream(local_rank)
+            torch.cuda.set_stream(tls.stream)
             tls.ctx = ccs.ccs_create(local_rank)
             ctxs.append(tls.ctx)
         return ccs.ccs_build_fragments(tls.ctx, packed)

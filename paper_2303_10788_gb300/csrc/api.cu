@@ -41,9 +41,12 @@ struct ccs_ctx_s {
   int n_ev = 0;
   float stage_ms[8] = {};
   int stage_mask = 0;   // stages recorded by the last profiled call
-  // pinned staging buffer for plan uploads (one host->device copy per batch)
+  // pinned staging buffer for plan uploads (one host->device copy per batch);
+  // the event marks the end of the last copy out of it
   char* pinned = nullptr;
   size_t pinned_bytes = 0;
+  cudaEvent_t upload_ev = nullptr;
+  bool upload_pending = false;
 };
 
 cudaStream_t ccs::c_stream(ccs_ctx c) { return c->stream; }
@@ -177,7 +180,8 @@ struct Staging {
     char* d = A.get<char>(total);
     if (!d) return false;
     // the previous copy out of the staging buffer must be done before reuse
-    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return false;
+    // (waits for that copy only, not for other work on the stream)
+    if (!upload_wait(c)) return false;
     if (c->pinned_bytes < total) {
       if (c->pinned) cudaFreeHost(c->pinned);
       c->pinned = nullptr;
@@ -189,7 +193,17 @@ struct Staging {
       if (it.bytes) std::memcpy(c->pinned + it.off, it.src, it.bytes);
       *it.out = d + it.off;
     }
-    return cudaMemcpyAsync(d, c->pinned, total, cudaMemcpyHostToDevice, c->stream) == cudaSuccess;
+    if (cudaMemcpyAsync(d, c->pinned, total, cudaMemcpyHostToDevice, c->stream) != cudaSuccess) return false;
+    if (!c->upload_ev && cudaEventCreateWithFlags(&c->upload_ev, cudaEventDisableTiming) != cudaSuccess) return false;
+    if (cudaEventRecord(c->upload_ev, c->stream) != cudaSuccess) return false;
+    c->upload_pending = true;
+    return true;
+  }
+  static bool upload_wait(ccs_ctx c) {
+    if (!c->upload_pending) return true;
+    if (cudaEventSynchronize(c->upload_ev) != cudaSuccess) return false;
+    c->upload_pending = false;
+    return true;
   }
 };
 
@@ -415,6 +429,7 @@ void ccs_destroy(ccs_ctx c) {
   if (c->join_ev) cudaEventDestroy(c->join_ev);
   if (c->side) cudaStreamDestroy(c->side);
   if (c->pinned) cudaFreeHost(c->pinned);
+  if (c->upload_ev) cudaEventDestroy(c->upload_ev);
   delete c;
 }
 
@@ -943,8 +958,9 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
     dp.max_moment_ops = max_moment_ops;
     dp.problems = dpr; dp.n_problems = (int)plan->pdev.size();
     dp.prep_ops = dpo; dp.basis_ops = dbo; dp.prep_mats = dpm; dp.basis_mats = dbm;
-    cudaError_t e = cudaStreamSynchronize(c->stream);
-    if (e != cudaSuccess) { return cuda_fail(c, e, "plan upload"); }
+    // the plan's arrays are on the device before it is handed out (it may be
+    // used from another context's stream); other work on the stream is not waited for
+    if (!Staging::upload_wait(c)) { return fail(c, CCS_ERR_CUDA, "plan upload"); }
     *out = owned.release();
     return CCS_OK;
   });

@@ -940,11 +940,13 @@ __global__ void __launch_bounds__(256) reduce_scatter_kernel(DevPlan P, const lo
         const float* pp = scratch + Pb.part_off + loc;    // partial [split][m][n]: loc = m N + n
         const long long st = (long long)Pb.M * Pb.N;
         int s = w;
-        for (; s + 8 < splits; s += 16) {
-          a0 += (double)pp[(long long)s * st];
-          a1 += (double)pp[(long long)(s + 8) * st];
+        for (; s + 24 < splits; s += 32) {    // four loads in flight
+          const float v0 = pp[(long long)s * st], v1 = pp[(long long)(s + 8) * st];
+          const float v2 = pp[(long long)(s + 16) * st], v3 = pp[(long long)(s + 24) * st];
+          a0 += (double)v0 + (double)v1;
+          a1 += (double)v2 + (double)v3;
         }
-        if (s < splits) a0 += (double)pp[(long long)s * st];
+        for (; s < splits; s += 8) a0 += (double)pp[(long long)s * st];
       }
     }
     red[w][lane] = a0 + a1;
@@ -1386,14 +1388,24 @@ cudaError_t launch_recombine(const DevPlan& p, const DevRes& r, int precision, c
   cudaError_t err = cudaSuccess;
   if (z.out_total > 0 && z.chain) {
     const bool use_tc = precision == CCS_BF16 && z.tensor_cores && z.rt_scratch && r.TQh && z.krange.full();
-    if (z.r_total > 0) {
+    // launch the R builder and the tiled GEMM only when some problem uses them
+    // (a first-leaf problem builds its own table; streamed hubs have their own GEMM)
+    bool need_r = false, need_gemm = false;
+    for (int i = 0; i < z.n_problems; ++i) {
+      const ProblemDev& Pb = z.host_problems[i];
+      if (Pb.direct || Pb.general) continue;
+      const bool tc = use_tc && Pb.tc;
+      need_r = need_r || tc || !fact_path(Pb, precision, z.stitched, z.krange.full());
+      need_gemm = need_gemm || (!tc && !Pb.stream);
+    }
+    if (z.r_total > 0 && need_r) {
       build_r_kernel<<<grid(z.r_total, 256), 256, 0, s>>>(p, r, precision, z.r_prefix, p.n_problems, z.r_total,
                                                           scratch, use_tc ? z.rt_scratch : nullptr, z.stitched,
                                                           z.krange.full() ? 1 : 0);
       note_launch();
       if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
-    if (z.gemm_blocks > 0) {
+    if (z.gemm_blocks > 0 && need_gemm) {
       if (z.max_tile_smem > 48 * 1024) {
         err = cudaFuncSetAttribute(gemm_splitk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, z.max_tile_smem);
         if (err != cudaSuccess) return err;
