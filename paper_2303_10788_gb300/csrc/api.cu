@@ -1,5 +1,8 @@
 #include <thread>
 #include <atomic>
+#include <condition_variable>
+#include <deque>
+#include <functional>
 #include <exception>
 #include <mutex>
 // C ABI of the circuit-cutting hot path (declared in include/ccs.h).
@@ -130,38 +133,104 @@ struct Allocs {
   }
 };
 
-// f(0..n-1) on up to hardware_concurrency host threads (inline for n = 1).
+// Host worker pool: threads created once (up to hardware_concurrency, at most
+// 32) and kept for the life of the process, so a plan build spawns no thread
+// and each worker keeps its scratch buffers warm.  Several callers may post
+// jobs at once; a caller works on its own job too, so a job finishes even
+// when every worker is busy (and a job posted from inside a job cannot wait
+// on itself).  A job lives on its caller's stack: the caller returns only
+// when every item is done and no worker still holds the job (both counted
+// under the pool's mutex, under which workers also pick jobs up).
+class HostPool {
+ public:
+  struct Job {
+    const std::function<void(int)>* f = nullptr;
+    int n = 0;
+    int holders = 0;                 // workers inside work() (guarded by the pool's mutex)
+    std::atomic<int> next{0}, done{0};
+    std::exception_ptr first;
+    std::mutex err_mu;
+    void work() {
+      for (int i = next.fetch_add(1); i < n; i = next.fetch_add(1)) {
+        try {
+          (*f)(i);
+        } catch (...) {
+          std::lock_guard<std::mutex> lk(err_mu);
+          if (!first) first = std::current_exception();
+        }
+        done.fetch_add(1);
+      }
+    }
+  };
+  static HostPool& get() {
+    static HostPool* pool = new HostPool();   // never destroyed: detached workers outlive static destructors
+    return *pool;
+  }
+  int size() const { return (int)workers_.size(); }
+  void run(Job& j) {
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      jobs_.push_back(&j);
+    }
+    work_cv_.notify_all();
+    j.work();
+    std::unique_lock<std::mutex> lk(mu_);
+    done_cv_.wait(lk, [&] { return j.done.load() == j.n && j.holders == 0; });
+    for (auto it = jobs_.begin(); it != jobs_.end(); ++it)
+      if (*it == &j) { jobs_.erase(it); break; }
+  }
+
+ private:
+  HostPool() {
+    const unsigned hw = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    for (unsigned t = 1; t < hw; ++t) workers_.emplace_back([this] { loop(); });
+    for (auto& w : workers_) w.detach();
+  }
+  void loop() {
+    for (;;) {
+      Job* j = nullptr;
+      {
+        std::unique_lock<std::mutex> lk(mu_);
+        work_cv_.wait(lk, [&] {
+          for (Job* x : jobs_)
+            if (x->next.load() < x->n) { j = x; return true; }
+          return false;
+        });
+        ++j->holders;
+      }
+      j->work();
+      {
+        std::lock_guard<std::mutex> lk(mu_);
+        --j->holders;                // the worker's last access to the job
+      }
+      done_cv_.notify_all();
+    }
+  }
+  std::mutex mu_;
+  std::condition_variable work_cv_, done_cv_;
+  std::deque<Job*> jobs_;
+  std::vector<std::thread> workers_;
+};
+
+// f(0..n-1) on the host pool (inline for n = 1); an exception in any item is
+// carried to the calling thread (the first one wins; the other items still run).
 template <class F>
 void parallel_for(int n, F&& f) {
   if (n <= 1) {
     if (n == 1) f(0);
     return;
   }
-  static const unsigned hw = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
-  const int T = std::min<int>(n, (int)hw);
-  if (T <= 1) {
+  HostPool& pool = HostPool::get();
+  if (pool.size() == 0) {
     for (int i = 0; i < n; ++i) f(i);
     return;
   }
-  // an exception in a worker is carried to the calling thread (the first
-  // one wins; the other items still run)
-  std::atomic<int> next{0};
-  std::exception_ptr first;
-  std::mutex mu;
-  std::vector<std::thread> th;
-  for (int t = 0; t < T; ++t)
-    th.emplace_back([&] {
-      for (int i = next.fetch_add(1); i < n; i = next.fetch_add(1)) {
-        try {
-          f(i);
-        } catch (...) {
-          std::lock_guard<std::mutex> lk(mu);
-          if (!first) first = std::current_exception();
-        }
-      }
-    });
-  for (auto& x : th) x.join();
-  if (first) std::rethrow_exception(first);
+  const std::function<void(int)> fn = [&](int i) { f(i); };
+  HostPool::Job j;
+  j.f = &fn;
+  j.n = n;
+  pool.run(j);
+  if (j.first) std::rethrow_exception(j.first);
 }
 
 // Host arrays gathered into one pinned buffer and sent with one copy.
@@ -548,6 +617,24 @@ int ccs_build_fragments(ccs_ctx c, const ccs_problem* probs, int n_problems, con
     int max_body_stage = 0, max_moment_ops = 1;
     int max_body_cols = 0;
     std::vector<long long> cost_c, cost_nc;
+    {   // sizes first: every array below is filled without reallocation
+      size_t n_cops = 0, n_nops = 0, n_mom = 0, n_var = 0, n_wire = 0;
+      for (const Frag& f : plan->frags) {
+        n_cops += f.cops.size();
+        n_nops += f.nops.size();
+        n_mom += f.moment_start.size();
+        n_wire += 2 * f.qout_wire.size() + f.marg_wire.size() + f.qin_wire.size();
+        for (auto& zw : f.zwires) n_wire += zw.size();
+        if (f.clifford) n_var += f.n_variants();
+      }
+      cops.reserve(n_cops);
+      nops.reserve(n_nops);
+      moments.reserve(n_mom);
+      wires.reserve(n_wire);
+      items_c.reserve(n_var);
+      cost_c.reserve(n_var);
+      plan->fdev.reserve(plan->frags.size());
+    }
     for (size_t fi = 0; fi < plan->frags.size(); ++fi) {
       Frag& f = plan->frags[fi];
       FragDev d{};

@@ -164,8 +164,11 @@ struct Fused {
   }
 };
 
-// Fuse consecutive gates per qubit (pair) and assign ASAP moments.
-std::vector<std::vector<const Fused*>> fuse_and_layer(const Frag& f, std::vector<Fused>& ops, bool planes) {
+// Fuse consecutive gates per qubit (pair) and assign ASAP moments: on return
+// order[start[L] .. start[L+1]) are the live ops of moment L (indices into
+// ops, in creation order).
+void fuse_and_layer(const Frag& f, std::vector<Fused>& ops, bool planes, std::vector<int>& order,
+                    std::vector<int>& start) {
   const int n = f.n();
   std::vector<int> last(n, -1);
   for (size_t gi = 0; gi < f.gates.size(); ++gi) {
@@ -223,19 +226,27 @@ std::vector<std::vector<const Fused*>> fuse_and_layer(const Frag& f, std::vector
     ops.push_back(std::move(nf));
     last[a] = last[b] = (int)ops.size() - 1;
   }
-  std::vector<int> layer_of_q(n, -1);
-  std::vector<std::vector<const Fused*>> layers;
-  for (auto& F : ops) {
+  std::vector<int> layer_of_q(n, -1), lay(ops.size(), -1);
+  int nl = 0;
+  for (size_t i = 0; i < ops.size(); ++i) {
+    const Fused& F = ops[i];
     if (F.dead) continue;
     int L = layer_of_q[F.a];
     if (F.b >= 0) L = std::max(L, layer_of_q[F.b]);
     L += 1;
     layer_of_q[F.a] = L;
     if (F.b >= 0) layer_of_q[F.b] = L;
-    if ((int)layers.size() <= L) layers.resize(L + 1);
-    layers[L].push_back(&F);
+    lay[i] = L;
+    nl = std::max(nl, L + 1);
   }
-  return layers;
+  start.assign(nl + 1, 0);                     // counting sort by moment, stable
+  for (int L : lay)
+    if (L >= 0) ++start[L + 1];
+  for (int L = 0; L < nl; ++L) start[L + 1] += start[L];
+  order.resize(start[nl]);
+  std::vector<int> fill(start.begin(), start.end() - 1);
+  for (size_t i = 0; i < ops.size(); ++i)
+    if (lay[i] >= 0) order[fill[lay[i]]++] = (int)i;
 }
 
 }  // namespace
@@ -251,7 +262,7 @@ int load_gates(const ccs_gate* G, uint32_t ng, std::vector<std::array<int, 3>>& 
                std::vector<double>& gparam, std::string& err) {
   static const int kSPow[4] = {kOpI, CCS_S, CCS_Z, CCS_SDG};   // S^0 .. S^3
   gates.resize(ng);
-  gparam.assign(ng, 0.0);
+  gparam.clear();                    // sized only when a non-Clifford exponent appears (empty: all 0)
   for (uint32_t i = 0; i < ng; ++i) {
     const ccs_gate& g = G[i];
     if (g.op > CCS_ZPOW) { err = "unknown gate opcode"; return CCS_ERR_UNSUPPORTED_GATE; }
@@ -266,6 +277,7 @@ int load_gates(const ccs_gate* G, uint32_t ng, std::vector<std::array<int, 3>>& 
       } else {
         double a = std::fmod(g.param, 2.0);  // e^{i pi a} has period 2 in a
         if (a < 0) a += 2.0;
+        if (gparam.empty()) gparam.assign(ng, 0.0);
         gparam[i] = a;
       }
     }
@@ -347,7 +359,7 @@ int fragment_problem(Problem& p, int pi, std::vector<Frag>& out, std::string& er
     for (int gi = 0; gi < ng; ++gi) count[where[seg_a[gi]].first - first]++;
     for (size_t fi = 0; fi < count.size(); ++fi) {
       out[first + fi].gates.reserve(count[fi]);
-      out[first + fi].gparam.reserve(count[fi]);
+      if (!p.gparam.empty()) out[first + fi].gparam.reserve(count[fi]);
     }
   }
   for (int gi = 0; gi < ng; ++gi) {
@@ -356,10 +368,10 @@ int fragment_problem(Problem& p, int pi, std::vector<Frag>& out, std::string& er
     Frag& f = out[wa.first];
     if (seg_b[gi] >= 0) {
       f.gates.push_back({g[0], wa.second, where[seg_b[gi]].second});
-      f.gparam.push_back(0.0);
+      if (!p.gparam.empty()) f.gparam.push_back(0.0);
     } else {
       f.gates.push_back({g[0], wa.second, -1});
-      f.gparam.push_back(p.gparam.empty() ? 0.0 : p.gparam[gi]);
+      if (!p.gparam.empty()) f.gparam.push_back(p.gparam[gi]);
       if (!is_clifford_op(g[0])) f.clifford = false;
     }
   }
@@ -425,18 +437,35 @@ int fragment_problem(Problem& p, int pi, std::vector<Frag>& out, std::string& er
   return CCS_OK;
 }
 
-void compile_clifford(Frag& f) {
+namespace {
+// Scratch of one host thread, kept between fragments and plan builds (the
+// pool's threads persist), so compiling does not fault in fresh pages.
+struct CompileScratch {
   std::vector<Fused> ops;
-  ops.reserve(f.gates.size());
-  auto layers = fuse_and_layer(f, ops, true);
+  std::vector<int> order, start;
+  void reset(size_t gates) {
+    ops.clear();
+    ops.reserve(gates);                        // no reallocation while ops point at each other
+  }
+};
+}  // namespace
+
+void compile_clifford(Frag& f) {
+  thread_local CompileScratch cs;
+  cs.reset(f.gates.size());
+  fuse_and_layer(f, cs.ops, true, cs.order, cs.start);
+  const int nl = (int)cs.start.size() - 1;
   f.cops.clear();
+  f.cops.reserve(cs.order.size());
   f.moment_start.assign(1, 0);
+  f.moment_start.reserve(nl + 1);
   const uint16_t dummy = (uint16_t)f.n();
-  for (auto& L : layers) {
-    for (auto* F : L) {
-      CliffordOp op = clifford_from_planes(F->px, F->pz, F->pf);
-      op.qa = (uint16_t)F->a;
-      op.qb = F->b >= 0 ? (uint16_t)F->b : dummy;
+  for (int L = 0; L < nl; ++L) {
+    for (int k = cs.start[L]; k < cs.start[L + 1]; ++k) {
+      const Fused& F = cs.ops[cs.order[k]];
+      CliffordOp op = clifford_from_planes(F.px, F.pz, F.pf);
+      op.qa = (uint16_t)F.a;
+      op.qb = F.b >= 0 ? (uint16_t)F.b : dummy;
       f.cops.push_back(op);
     }
     f.moment_start.push_back((int)f.cops.size());
@@ -444,13 +473,15 @@ void compile_clifford(Frag& f) {
 }
 
 void compile_nc(Frag& f) {
-  std::vector<Fused> ops;
-  ops.reserve(f.gates.size());
-  auto layers = fuse_and_layer(f, ops, false);
+  thread_local CompileScratch cs;
+  cs.reset(f.gates.size());
+  fuse_and_layer(f, cs.ops, false, cs.order, cs.start);
+  const int nl = (int)cs.start.size() - 1;
   f.nops.clear();
   f.moment_start.assign(1, 0);
-  for (auto& L : layers) {
-    for (auto* F : L) {
+  for (int L = 0; L < nl; ++L) {
+    for (int k = cs.start[L]; k < cs.start[L + 1]; ++k) {
+      const Fused* F = &cs.ops[cs.order[k]];
       NCOp o{};
       o.a = F->a;
       o.b = F->b;

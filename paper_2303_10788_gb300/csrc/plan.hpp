@@ -68,7 +68,7 @@ struct Frag {
   bool clifford = true;
   std::vector<std::pair<uint32_t, uint32_t>> wires;  // (qubit, segment)
   std::vector<std::array<int, 3>> gates;             // (op, a, b), local wires
-  std::vector<double> gparam;                        // per gate: Z^a exponent, else 0
+  std::vector<double> gparam;                        // per gate: Z^a exponent, else 0 (empty: all 0)
   std::vector<int> qin_cut, qin_wire, qout_cut, qout_wire;
   std::vector<int> marg_pos, marg_wire;
   std::vector<int> slots;       // incident cut ids, ascending
