@@ -229,10 +229,52 @@ __device__ void prep_rows_from_body(const CliffordOp* s_prep, const int* s_qin, 
 
 }  // namespace
 
+namespace {
+// Deep, narrow circuits (moments of a few ops: a chain) are bound by the
+// latency of each op, not by tableau traffic, so their ops are applied
+// cooperatively: eight lanes per op, lane (h, j) producing output column j
+// (X_a, Z_a, X_b, Z_b) on 32-bit half h of the word and a quarter of the
+// op's sign-flip terms (terms 4j .. 4j+3 of its algebraic normal form, whose
+// factors in v2, v3 are fixed by j), reduced over the four lanes of the half
+// by shuffles: the arithmetic of apply_op_g, split over lanes.  Every lane of
+// the block must call it.
+__device__ __forceinline__ void apply_moment_coop(const CliffordOp* ops, int c0, int n_ops, uint32_t* t32, int zb,
+                                                  uint64_t& rd) {
+  const int lane = threadIdx.x & 31;
+  for (int t0 = (int)threadIdx.x - lane; t0 < 8 * n_ops; t0 += (int)blockDim.x) {
+    const int t = t0 + lane;
+    const bool act = t < 8 * n_ops;
+    const int h = (t >> 2) & 1, j = t & 3;
+    uint32_t u = 0u, r = 0u, v0 = 0u, v1 = 0u, v2 = 0u, v3 = 0u;
+    int col = 0;
+    if (act) {
+      const CliffordOp op = ops[c0 + (t >> 3)];
+      v0 = t32[2 * op.qa + h];
+      v1 = t32[2 * (zb + op.qa) + h];
+      v2 = t32[2 * op.qb + h];
+      v3 = t32[2 * (zb + op.qb) + h];
+      const unsigned M = op.M >> (4 * j), A = (op.anf & ~1u) >> (4 * j);   // ANF term 0 is not used
+      u = (v0 & bm32(M, 0)) ^ (v1 & bm32(M, 1)) ^ (v2 & bm32(M, 2)) ^ (v3 & bm32(M, 3));
+      const uint32_t hi = ((j & 1) ? v2 : ~0u) & ((j & 2) ? v3 : ~0u);
+      r = hi & (bm32(A, 0) ^ (v0 & bm32(A, 1)) ^ (v1 & bm32(A, 2)) ^ ((v0 & v1) & bm32(A, 3)));
+      col = j == 0 ? op.qa : j == 1 ? zb + op.qa : j == 2 ? op.qb : zb + op.qb;
+    }
+    r ^= __shfl_xor_sync(0xffffffffu, r, 1);
+    r ^= __shfl_xor_sync(0xffffffffu, r, 2);
+    __syncwarp();                            // every lane has read its inputs
+    if (act) {
+      t32[2 * col + h] = u;
+      if (j == 0) rd ^= (uint64_t)r << (32 * h);
+    }
+  }
+}
+}  // namespace
+
 // --- shared body: one CTA per (Clifford fragment, 64-row word) -------------
 // Rows evolve independently under conjugation, so each word of every column
 // is an independent problem: the CTA keeps one word per column in shared
 // memory and applies the whole op stream to it, moment by moment.
+template <bool COOP>   // COOP: eight lanes per op (moments of at most 32 ops)
 __global__ void __launch_bounds__(256) body_kernel(DevPlan P, DevRes R, int smem_words) {
   extern __shared__ __align__(16) unsigned long long smem_u64[];
   uint64_t* tab = reinterpret_cast<uint64_t*>(smem_u64);
@@ -261,7 +303,13 @@ __global__ void __launch_bounds__(256) body_kernel(DevPlan P, DevRes R, int smem
   const int* mom = staged ? mom_s : P.moments + F.mom_off;
   const int wk[1] = {0};
   uint64_t rd[1] = {0ull};
-  if (F.n_moments > 0) {
+  if (COOP) {
+    uint32_t* t32 = reinterpret_cast<uint32_t*>(tab);
+    for (int mm = 0; mm < F.n_moments; ++mm) {
+      apply_moment_coop(ops, mom[mm], mom[mm + 1] - mom[mm], t32, zb, rd[0]);
+      __syncthreads();
+    }
+  } else if (F.n_moments > 0) {
     // each thread's first op of the next moment is fetched while this
     // moment's op is applied (the op stream does not depend on the tableau)
     int b0 = mom[0], b1 = mom[1];
@@ -1883,12 +1931,16 @@ cudaError_t launch_clifford(const DevPlan& p, const DevRes& r, const EvalParams&
 cudaError_t launch_body(const DevPlan& p, const DevRes& r, int smem_optin, bool basis, cudaStream_t s) {
   if (p.n_items_body == 0) return cudaSuccess;
   const int words = std::max(p.max_body_cols, std::min(p.max_body_stage_words, smem_optin / 8));
-  cudaError_t err = cudaFuncSetAttribute(body_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, words * 8);
+  // moments of at most 32 ops (deep, narrow circuits): eight lanes per op,
+  // a warp per 4 ops of the widest moment; otherwise one thread per op of the
+  // widest moment (whole warps, 32..256): fewer idle warps at each barrier
+  const bool coop = p.max_moment_ops <= 32;
+  const int threads = coop ? std::max(32, (8 * p.max_moment_ops + 31) / 32 * 32)
+                           : std::min(256, std::max(32, (p.max_moment_ops + 31) / 32 * 32));
+  auto kern = coop ? body_kernel<true> : body_kernel<false>;
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, words * 8);
   if (err != cudaSuccess) return err;
-  // one thread per op of the widest moment (whole warps, 32..256): fewer
-  // idle warps at each moment's barrier
-  const int threads = std::min(256, std::max(32, (p.max_moment_ops + 31) / 32 * 32));
-  body_kernel<<<p.n_items_body, threads, (size_t)words * 8, s>>>(p, r, words); note_launch();
+  kern<<<p.n_items_body, threads, (size_t)words * 8, s>>>(p, r, words); note_launch();
   err = cudaGetLastError();
   if (!basis) return err;
   if (err != cudaSuccess || p.n_cliff_frags == 0) return err;
