@@ -372,17 +372,28 @@ def _ncu_traffic(kernel, workload):
     return None
 
 
-STAGE_KERNEL = {"sample": "sample_hub8_kernel", "recombine": "gemm_fact_bulk_kernel", "clifford": "body_basis_kernel"}
+def stage_kernel(st, precision, tuning=None, ws=None, prob_infos=None):
+    """The kernel that stands for a stage (its longest launch): the hub
+    sampler the autotuner picked (byte or 16-bit counters); the contraction
+    of wide hub operands (the first-leaf streaming GEMM, or tcgen05 in BF16)
+    or of small stars (leaf by leaf); the body kernel for the Clifford stage."""
+    if st == "sample":
+        return "sample_hub_kernel" if (tuning or {}).get("hub_counters") == "16-bit" else "sample_hub8_kernel"
+    if st == "recombine":
+        wide = False
+        for x, infos in zip(ws or [], prob_infos or []):
+            k = len(x.cuts or [])
+            hubs = [i for i in infos if i["n_slots"] == k]
+            wide = wide or any((4 ** k) << i["n_marg"] >= 1 << 24 for i in hubs)
+        if not wide:
+            return "contract_kernel"
+        return "gemm_bf16_tc_kernel" if precision == "bf16" else "gemm_fact_bulk_kernel"
+    if st == "clifford":
+        return "body_kernel"
+    return None
 
 
-def stage_kernel(st, precision):
-    """The kernel whose DRAM counters stand for a stage (its longest launch)."""
-    if st == "recombine" and precision == "bf16":
-        return "gemm_bf16_tc_kernel"
-    return STAGE_KERNEL.get(st)
-
-
-def stage_rooflines(stage, ws, prob_infos, pk, pk_kind, precision, workload):
+def stage_rooflines(stage, ws, prob_infos, pk, pk_kind, precision, workload, tuning=None):
     """Roofline of every stage: algorithmic work per launch / live duration.
 
     Peaks: lane ops = SMs x 128 lanes x max SM clock (one 32-bit op per lane
@@ -467,7 +478,7 @@ def stage_rooflines(stage, ws, prob_infos, pk, pk_kind, precision, workload):
             out[st] = {"bound": "hbm", "achieved": by / t / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
                        "peak_source": pk_kind}
         out[st]["frac"] = out[st]["achieved"] / out[st]["peak"]
-        kern = stage_kernel(st, precision)
+        kern = stage_kernel(st, precision, tuning, ws, prob_infos)
         out[st]["traffic"] = _ncu_traffic(kern, workload) if kern else None
         out[st]["ms"] = ms
     return out
@@ -601,8 +612,9 @@ def run_ours(args, rank, world, local_rank):
     d2h = 8 * sum((1 << len(x.marginal)) + len(x.zstrings) for x in ws)
 
     pk, pk_kind = peaks()
-    roofs = stage_rooflines(stage, ws, prob_infos, pk, pk_kind, args.precision, args.workload)
-    roof = dict(roofs[dom], stage=dom, kernel=stage_kernel(dom, args.precision))
+    tune_info = {"hub_counters": "8-bit" if tuning[3] < 0 else "16-bit"}
+    roofs = stage_rooflines(stage, ws, prob_infos, pk, pk_kind, args.precision, args.workload, tune_info)
+    roof = dict(roofs[dom], stage=dom, kernel=stage_kernel(dom, args.precision, tune_info, ws, prob_infos))
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64/" + args.precision, "data": "synthetic",
