@@ -154,8 +154,12 @@ typedef struct {
  * Errors: INVALID_ARG (bad qubit index, cut position, marginal, Z^a
  * exponent; an empty circuit; more than 2^24 qubits or 2^30 gates),
  * UNSUPPORTED_GATE, TOO_MANY_CUTS, NC_TOO_WIDE, UNSUPPORTED (a cut whose two
- * ends lie in the same fragment), OOM (device, or a failed host
- * allocation), CUDA. */
+ * ends lie in the same fragment; a Clifford fragment wider than 1024 wires;
+ * a fragment measuring more than 24 wires; more than 13 fragments in one
+ * problem), OOM (device, or a failed host allocation), CUDA.  Plans may be
+ * built on several host threads at once, each with its own context; the
+ * build uses the library's host worker pool and waits only for its own
+ * upload, not for other work on the context's stream. */
 int ccs_build_fragments(ccs_ctx ctx, const ccs_problem* problems, int n_problems,
                         const ccs_cut_opts* opts, ccs_plan* out);
 void ccs_plan_free(ccs_plan plan);
@@ -250,12 +254,15 @@ typedef struct {
                                  with one FP64 sum.  Partial ranges run on CUDA cores. */
 } ccs_recomb_opts;
 
-/* p(o) = 2^-k sum_{P in {I,X,Y,Z}^k} prod_f T_f(o_f, P|f) for every problem,
- * written to marginal_out (problems back to back, 2^n_marginal doubles each)
- * and <Z_S> to zexp_out (n_zstrings doubles each).  Partial sums over the
- * cut index are combined in FP64.  Synchronises the context stream unless
- * outputs_on_device is set.  Errors: UNSUPPORTED for a problem whose
- * fragments do not form a star (one fragment on every cut). */
+/* p(o) = 2^-k sum_{P in {I,X,Y,Z}^k} prod_f T_f(o_f, P|f) for every problem
+ * (Sec. V-C: one tensor per fragment, one index per cut), written to
+ * marginal_out (problems back to back, 2^n_marginal doubles each) and <Z_S>
+ * to zexp_out (n_zstrings doubles each).  Any fragment topology: a star (one
+ * fragment on every cut) is contracted leaf by leaf or as a GEMM over the cut
+ * index; chains and trees are summed over the whole cut index per output.
+ * Partial sums over the cut index are combined in FP64.  Synchronises the
+ * context stream unless outputs_on_device is set.  Errors: INVALID_ARG,
+ * CUDA. */
 int ccs_recombine(ccs_ctx ctx, ccs_plan plan, ccs_res res, const ccs_recomb_opts* opts,
                   double* marginal_out, double* zexp_out);
 
