@@ -372,6 +372,9 @@ def _ncu_traffic(kernel, workload):
     return None
 
 
+E2E_BUILDERS = 4    # host threads building plans ahead of the device in the end-to-end loop
+
+
 def stage_kernel(st, precision, tuning=None, ws=None, prob_infos=None):
     """The kernel that stands for a stage (its longest launch): the hub
     sampler the autotuner picked (byte or 16-bit counters); the contraction
@@ -572,9 +575,10 @@ def run_ours(args, rank, world, local_rank):
     # the host inputs are the C-ABI problem structs, marshalled once (with
     # the cut search inside the timed build where the workload has no cut
     # set).  Every step builds and uploads its plan, evaluates, recombines
-    # and reads the result back to host memory.  Plans are built on two host
-    # threads (each with its own context) up to two steps ahead of the
-    # device, the way a serving loop overlaps host work with the GPU.
+    # and reads the result back to host memory.  Plans are built on
+    # E2E_BUILDERS host threads (each with its own context and stream) up to
+    # that many steps ahead of the device, the way a serving loop overlaps
+    # host work with the GPU.
     import threading
     from concurrent.futures import ThreadPoolExecutor
     packed = ccs.pack_problems(ws_in)
@@ -590,9 +594,16 @@ def run_ours(args, rank, world, local_rank):
             ctxs.append(tls.ctx)
         return ccs.ccs_build_fragments(tls.ctx, packed)
 
-    depth, built = 2, []
+    depth, built = E2E_BUILDERS, []
     with ThreadPoolExecutor(depth) as ex:
-        ex.submit(build).result()                  # the builder contexts, created outside the timed region
+        gate = threading.Barrier(depth)
+
+        def warm():                                # every builder's context, outside the timed region
+            gate.wait()
+            return build()
+
+        for f in [ex.submit(warm) for _ in range(depth)]:
+            f.result()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         futs = [ex.submit(build) for _ in range(min(depth, args.steps))]
@@ -635,7 +646,8 @@ def run_ours(args, rank, world, local_rank):
             "stage_ms": stage, "roofline": roof, "stage_roofline": roofs,
             "e2e": {"value": units_per_step * world / e2e_s, "unit": UNIT, "circuits_per_s": world * len(ws) / e2e_s,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "pipeline": "plans built on 2 host threads up to 2 steps ahead of the device"},
+                    "pipeline": f"plans built on {E2E_BUILDERS} host threads up to {E2E_BUILDERS} steps ahead "
+                                "of the device"},
             "gpu_launches": launches, "clocks": clocks}
 
     # --- the same run's other forms: BF16 tensor-core contraction, plain GPU form
