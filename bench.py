@@ -392,7 +392,7 @@ def stage_kernel(st, precision, tuning=None, ws=None, prob_infos=None):
             return "contract_kernel"
         return "gemm_bf16_tc_kernel" if precision == "bf16" else "gemm_fact_bulk_kernel"
     if st == "clifford":
-        return "body_kernel"
+        return "clifford_kernel" if (tuning or {}).get("variant_path") else "body_kernel"
     return None
 
 
@@ -623,7 +623,7 @@ def run_ours(args, rank, world, local_rank):
     d2h = 8 * sum((1 << len(x.marginal)) + len(x.zstrings) for x in ws)
 
     pk, pk_kind = peaks()
-    tune_info = {"hub_counters": "8-bit" if tuning[3] < 0 else "16-bit"}
+    tune_info = {"hub_counters": "8-bit" if tuning[3] < 0 else "16-bit", "variant_path": bool(tuning[4])}
     roofs = stage_rooflines(stage, ws, prob_infos, pk, pk_kind, args.precision, args.workload, tune_info)
     roof = dict(roofs[dom], stage=dom, kernel=stage_kernel(dom, args.precision, tune_info, ws, prob_infos))
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -641,7 +641,9 @@ def run_ours(args, rank, world, local_rank):
                                                           " (CUDA-core FMA, FP64 across splits)"),
                        "tuning": {"threads": tuning[0], "words_per_op": tuning[1], "shots_per_cta": tuning[2],
                                   "hub_threads": abs(tuning[3]),
-                                  "hub_counters": "8-bit" if tuning[3] < 0 else "16-bit", "autotuned": tune}},
+                                  "hub_counters": "8-bit" if tuning[3] < 0 else "16-bit",
+                                  "path": "per-variant simulation" if tuning[4] else "shared bodies + screen",
+                                  "autotuned": tune}},
             "circuits_per_s": world * len(ws) * args.steps / t_tot,
             "stage_ms": stage, "roofline": roof, "stage_roofline": roofs,
             "e2e": {"value": units_per_step * world / e2e_s, "unit": UNIT, "circuits_per_s": world * len(ws) / e2e_s,

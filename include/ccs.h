@@ -232,9 +232,13 @@ void ccs_res_free(ccs_res res);
 /* Launch shape in use for a result (after autotuning, if any): threads per
  * tableau CTA, 64-row words of one fused op per thread, shots per sampling
  * CTA, threads per fused hub-sampler CTA (negative: the byte-counter
- * sampler with that many threads).  Any output may be NULL. */
+ * sampler with that many threads), and the evaluation path (1: every
+ * Clifford variant simulates its whole circuit, which the autotuner picks
+ * for small plans when it is faster, or which per_variant_body asks for;
+ * 0: shared bodies and the outcome-space screen).  Both paths give the same
+ * outcome spaces, shots and values.  Any output may be NULL. */
 int ccs_get_tuning(ccs_ctx ctx, ccs_res res, int* cliff_threads, int* words_per_op, int* shots_per_cta,
-                   int* hub_threads);
+                   int* hub_threads, int* variant_path);
 
 /* --- recombination (Sec. V-C) --------------------------------------------- */
 #define CCS_FP32 0

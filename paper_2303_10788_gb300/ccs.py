@@ -127,7 +127,7 @@ def lib():
             "ccs_set_profiling": ([P, C.c_int], C.c_int),
             "ccs_recombine_noalloc": ([P, P, P, C.c_int, P, P], C.c_int),
             "ccs_get_tuning": ([P, P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
-                                C.POINTER(C.c_int)], C.c_int),
+                                C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
             "ccs_cut_candidates": ([P, C.POINTER(ccs_problem), C.POINTER(ccs_cut_opts), C.POINTER(ccs_cut),
                                     C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double), C.c_int], C.c_int),
             "ccs_get_stage_times": ([P, C.POINTER(C.c_double), C.c_int], C.c_int),
@@ -455,11 +455,12 @@ def ccs_recombine_noalloc(ctx, plan, res, marginal_out, zexp_out=None, precision
 
 def ccs_get_tuning(ctx, res):
     """(threads per tableau CTA, words per op per thread, shots per sampling CTA,
-    threads per hub-sampler CTA)."""
-    t, wpo, spc, hub = C.c_int(), C.c_int(), C.c_int(), C.c_int()
-    ctx.check(lib().ccs_get_tuning(ctx.h, res.h, C.byref(t), C.byref(wpo), C.byref(spc), C.byref(hub)),
-              "ccs_get_tuning")
-    return t.value, wpo.value, spc.value, hub.value
+    threads per hub-sampler CTA (negative: byte counters), 1 if every variant
+    simulates its whole circuit else 0)."""
+    t, wpo, spc, hub, vp = C.c_int(), C.c_int(), C.c_int(), C.c_int(), C.c_int()
+    ctx.check(lib().ccs_get_tuning(ctx.h, res.h, C.byref(t), C.byref(wpo), C.byref(spc), C.byref(hub),
+                                   C.byref(vp)), "ccs_get_tuning")
+    return t.value, wpo.value, spc.value, hub.value, vp.value
 
 
 def ccs_get_operand(ctx, res, problem, fragment):

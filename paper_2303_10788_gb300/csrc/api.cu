@@ -34,7 +34,7 @@ struct ccs_ctx_s {
   std::string err;
   ccs_mpnn cut_model = nullptr;   // learned cut scorer (not owned)
   // autotuner results: shape bucket -> (Clifford threads per CTA, shots per sampler CTA)
-  std::map<std::tuple<int, int, unsigned, int>, std::tuple<int, int, int, int>> tuned;
+  std::map<std::tuple<int, int, unsigned, int>, std::tuple<int, int, int, int, int>> tuned;
   // second stream for the statevector branch (forked from / joined into `stream`)
   cudaStream_t side = nullptr;
   cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
@@ -355,6 +355,7 @@ struct ccs_res_s {
   int sample_spc = 4096;
   int hub_threads = 512;      // threads of the fused hub sampler CTA (either counter width)
   bool hub_bytes = false;     // use the byte-counter hub sampler (64 KB of counters at |A| = 16)
+  bool variant_path = false;  // autotuned: every variant simulates its whole circuit (small plans)
   float* scratch = nullptr;   // recombination: R operand + split-K partials
   uint16_t* rt_scratch = nullptr;   // bf16 R'^T of tensor-core-eligible problems
   ~ccs_res_s() {
@@ -1182,6 +1183,8 @@ static int enqueue_eval(ccs_ctx c, ccs_plan p, ccs_res r) {
 // evaluations each) and keep the fastest; cached per shape bucket (widest
 // Clifford fragment rounded up to 64 wires, Clifford variant count rounded up
 // to a power of two, shots, mode).
+constexpr int kVariantPathMaxItems = 8192;   // Clifford variants up to which the autotuner also times the per-variant path
+
 static int autotune(ccs_ctx c, ccs_plan p, ccs_res r) {
   int max_n = 0;
   for (auto& f : p->fdev)
@@ -1192,9 +1195,12 @@ static int autotune(ccs_ctx c, ccs_plan p, ccs_res r) {
       std::make_tuple((max_n + 63) / 64, items, r->ep.shots, r->ep.mode * 4 + r->ep.shared_body * 2 + r->ep.screen);
   auto it = c->tuned.find(key);
   if (it != c->tuned.end()) {
-    std::tie(r->cliff_threads, r->cliff_words, r->sample_spc, r->hub_threads) = it->second;
+    int vp = 0;
+    std::tie(r->cliff_threads, r->cliff_words, r->sample_spc, r->hub_threads, vp) = it->second;
     r->hub_bytes = r->hub_threads < 0;       // cached as minus the threads of the byte-counter kernel
     r->hub_threads = std::abs(r->hub_threads);
+    r->variant_path = vp != 0;
+    if (r->variant_path) { r->ep.shared_body = 0; r->ep.screen = 0; }
     return CCS_OK;
   }
   cudaEvent_t e0, e1;
@@ -1249,18 +1255,50 @@ static int autotune(ccs_ctx c, ccs_plan p, ccs_res r) {
   }
   r->hub_threads = bh;
   r->hub_bytes = bb;
+  // Small plans whose tableaus fit in shared memory: the per-variant path
+  // (every variant simulates its whole circuit in one kernel, no shared-body
+  // chain) can be faster than the shared body's chain of short kernels; it
+  // is timed with its own tableau CTA shapes and kept if faster.  Both paths
+  // give the same outcome spaces, shots and values.
+  r->variant_path = false;
+  if (rc == CCS_OK && r->ep.shared_body && r->ep.screen && p->tableau_fits && p->dp.n_items_cliff > 0 &&
+      p->dp.n_items_cliff <= kVariantPathMaxItems) {
+    if ((rc = time_it(&ms)) == CCS_OK) best = ms;      // the tuned shared-body path
+    float best_v = 1e30f;
+    int vt = bt, vw = bw;
+    r->ep.shared_body = 0;
+    r->ep.screen = 0;
+    for (int ti = 0; ti < 3 && rc == CCS_OK; ++ti)
+      for (int wi = 0; wi < 4 && rc == CCS_OK; ++wi) {
+        if (words_c[wi] > max_w) continue;
+        r->cliff_threads = threads_c[ti];
+        r->cliff_words = words_c[wi];
+        if ((rc = time_it(&ms)) == CCS_OK && ms < best_v) { best_v = ms; vt = threads_c[ti]; vw = words_c[wi]; }
+      }
+    if (rc == CCS_OK && best_v < best) {
+      r->variant_path = true;
+      bt = vt;
+      bw = vw;
+    } else {
+      r->ep.shared_body = 1;
+      r->ep.screen = 1;
+    }
+    r->cliff_threads = bt;
+    r->cliff_words = bw;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc != CCS_OK) return rc;
-  c->tuned[key] = std::make_tuple(bt, bw, bs, bb ? -bh : bh);
+  c->tuned[key] = std::make_tuple(bt, bw, bs, bb ? -bh : bh, r->variant_path ? 1 : 0);
   return CCS_OK;
 }
 
 int ccs_get_tuning(ccs_ctx c, ccs_res r, int* cliff_threads, int* words_per_op, int* shots_per_cta,
-                   int* hub_threads) {
+                   int* hub_threads, int* variant_path) {
   return abi_guard([&](int code, const char* m) { return fail(c, code, m); }, [&]() -> int {
     if (!c || !r) return fail(c, CCS_ERR_INVALID_ARG, "bad arguments");
     if (hub_threads) *hub_threads = (r->hub_bytes && r->plan->hub_bytes_ok) ? -r->hub_threads : r->hub_threads;
+    if (variant_path) *variant_path = r->ep.shared_body ? 0 : 1;
     if (cliff_threads) *cliff_threads = r->cliff_threads;
     if (words_per_op) *words_per_op = r->ep.shared_body ? 1 : r->cliff_words;
     if (shots_per_cta) *shots_per_cta = r->sample_spc;
@@ -1373,7 +1411,9 @@ int ccs_eval_variants(ccs_ctx c, ccs_plan p, const ccs_eval_opts* opts, ccs_res*
       e.keys.k[rd][1] = e.seed_hi + (uint32_t)rd * 0xBB67AE85u;
     }
     e.keep_tableaus = opts->keep_tableaus && r->have_tabs;
-    e.shared_body = opts->per_variant_body ? 0 : 1;
+    // the autotuner's path choice holds for later default-path calls on this result
+    const bool variant_path = r->variant_path && !opts->keep_tableaus && p->tableau_fits;
+    e.shared_body = (opts->per_variant_body || variant_path) ? 0 : 1;
     e.screen = e.shared_body && p->dp.n_cliff_frags > 0 && !e.keep_tableaus;
     if (opts->hub_sampler < 0 || opts->hub_sampler > 3) return fail(c, CCS_ERR_INVALID_ARG, "bad hub sampler");
     e.hub_sampler = opts->hub_sampler;
@@ -1399,6 +1439,7 @@ int ccs_eval_variants(ccs_ctx c, ccs_plan p, const ccs_eval_opts* opts, ccs_res*
       int rc = autotune(c, p, r);
       c->profiling = prof;
       if (rc != CCS_OK) return rc;
+      e = r->ep;                             // the autotuner may have chosen the per-variant path
     }
     if (!opts->use_graph || c->profiling) {
       c->stage_mask = 0;
