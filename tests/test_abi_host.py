@@ -135,6 +135,14 @@ def test_error_codes(hctx):
         chain.add(CX, q, q + 1)
     _expect(hctx, [_P(chain, [], [0])], "UNSUPPORTED")
     _expect(hctx, [_P(chain, [], list(range(25)))], "INVALID_ARG")  # marginal wider than 24 qubits
+    idle = Circuit(14)                                              # 14 fragments: more than a problem may have
+    for q in range(14):
+        idle.add(H, q)
+    _expect(hctx, [_P(idle, [], [0])], "UNSUPPORTED")
+    idle13 = Circuit(13)                                            # 13 fragments: accepted
+    for q in range(13):
+        idle13.add(H, q)
+    ccs.ccs_build_fragments(hctx, [_P(idle13, [], [0])])
 
 
 def test_host_only_context_cannot_evaluate(hctx):

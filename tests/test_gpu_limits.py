@@ -88,3 +88,31 @@ def test_empty_marginal_and_gateless_circuit(ctx):
         plan, res, marg, zexp = run(ctx, idle, mode)
         assert np.array_equal(marg, np.array([1.0, 0.0, 0.0, 0.0]))
         assert np.array_equal(zexp, np.array([1.0]))
+
+
+def test_thirteen_fragments(ctx):
+    """The most fragments one problem may have (13: cuts + 1 for 12 cuts, and
+    every gate-disconnected wire is a fragment of its own): seven two-qubit
+    blocks and five single wires, the first block carrying a T and cut on
+    both wires (two fragments), marginal wires in ten different fragments;
+    exact and sampled against the oracle."""
+    from workloads import CX, H, S, T
+    c = Circuit(19)
+    for b in range(7):
+        a, d = 2 * b, 2 * b + 1
+        c.add(H, a); c.add(CX, a, d); c.add(S, d)
+    c.add(T, 0)
+    g = len(c.gates)                          # the second CX of the first block: both wires cut before it
+    c.add(CX, 0, 1); c.add(H, 1)
+    for q in range(14, 19):
+        c.add(H, q)
+    cuts = [(0, g), (1, g)]
+    w = Workload("thirteen", c, cuts, [0, 2, 4, 6, 8, 10, 12, 14, 16, 18], [[1, 3], [0, 18]], 1024, 7)
+    plan = ccs.ccs_build_fragments(ctx, [w])
+    nf, nc = ccs.ccs_plan_counts(ctx, plan, 0)
+    assert nf == 13 and nc == 2, (nf, nc)
+    for mode, m in ((ccs.CCS_EXACT, "exact"), (ccs.CCS_SAMPLED, "sampled")):
+        _, _, marg, zexp = run(ctx, w, mode)
+        orc = evaluate_workload(w, mode=m, seed_lo=SEED[0], seed_hi=SEED[1])
+        assert np.abs(marg - orc.marginal).max() < 1e-5
+        assert np.abs(zexp - orc.zexp).max() < 1e-5
