@@ -1461,9 +1461,10 @@ __global__ void __launch_bounds__(512) sample_hub_kernel(DevPlan P, DevRes R, Ev
   const SpaceRec& sp = R.spaces[F.space_off + v];
   const int rank = sp.rank;
   const uint32_t off = sp.off;
-  build_tables(tbl, sp, rank);
   if (threadIdx.x == 32) s_ident = space_is_identity(sp, rank, nA) ? 1 : 0;
   if (F.qout <= 4) hub_variant_rows(F, v, s_czD, s_czS, s_nzm);   // warp 0: at most 16 rows
+  __syncthreads();
+  if (!s_ident) build_tables(tbl, sp, rank);   // a full-rank space needs no lookup tables
   const int nwords = wide ? (1 << nA) : ((1 << nA) > 1 ? (1 << (nA - 1)) : 1);
   {   // zero the histogram, 16 bytes per store
     uint4* h4 = reinterpret_cast<uint4*>(hist2);
@@ -1637,7 +1638,7 @@ __device__ __forceinline__ unsigned hub8_readout(const uint32_t* __restrict__ h3
     for (int b = 0; b < 16; ++b) w[b] = b < nb ? h32[((uint32_t)o | ((uint32_t)b << m)) >> 2] : 0u;
 #pragma unroll
     for (int b = 0; b < 16; ++b) tot = __dp4a(w[b], 0x01010101u, tot);
-    int out[NR][4];
+    uint32_t W[NR][2];     // per row: outputs (o, o+1) and (o+2, o+3) as int16 pairs
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
       int F[NR];
@@ -1658,15 +1659,22 @@ __device__ __forceinline__ unsigned hub8_readout(const uint32_t* __restrict__ h3
             F[i] = a + c;
             F[i | h] = a - c;
           }
+      // F = lo + 2^16 hi with |lo|, |hi| <= 16 x 255: the int16 pair word is
+      // F plus the borrow its low lane took from the high one
 #pragma unroll
-      for (int i = 0; i < NR; ++i) {
-        const int lo = (int)(short)(F[i] & 0xffff), hi = (F[i] - lo) >> 16;
-        out[i][2 * half] = lo;
-        out[i][2 * half + 1] = hi;
-      }
+      for (int i = 0; i < NR; ++i) W[i][half] = (uint32_t)F[i] + (((uint32_t)F[i] & 0x8000u) << 1);
     }
 #pragma unroll
-    for (int i = 0; i < NR; ++i) put4(QT, QH, (long long)s_czD[i] * M + o, out[i], inv);
+    for (int i = 0; i < NR; ++i) {
+      const long long idx = (long long)s_czD[i] * M + o;
+      if (QH) {
+        *reinterpret_cast<uint2*>(QH + idx) = make_uint2(W[i][0], W[i][1]);
+      } else {
+        const int v[4] = {(int)(short)(W[i][0] & 0xffffu), (int)(short)(W[i][0] >> 16),
+                          (int)(short)(W[i][1] & 0xffffu), (int)(short)(W[i][1] >> 16)};
+        put4(QT, nullptr, idx, v, inv);
+      }
+    }
   }
   return tot;
 }
@@ -1705,10 +1713,12 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 3) sample_hub8_kernel(DevP
   const SpaceRec& sp = R.spaces[F.space_off + v];
   const int rank = sp.rank;
   const uint32_t off = sp.off;
-  build_tables(tbl, sp, rank);
   if (tid == 32) s_ident = space_is_identity(sp, rank, nA) ? 1 : 0;
   // the variant's operand rows: one D and sign mask per Z-basis choice
   hub_variant_rows(F, v, s_czD, s_czS, s_nzm);
+  __syncthreads();
+  const bool ident = s_ident != 0;
+  if (!ident) build_tables(tbl, sp, rank);   // a full-rank space needs no lookup tables
   const uint32_t cmask = rank >= 32 ? 0xffffffffu : ((1u << rank) - 1u);
   const float inv = (float)E.inv_shots;
   float* QT = R.TQ + F.T_off;
@@ -1727,7 +1737,7 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 3) sample_hub8_kernel(DevP
     const uint4 ctr = make_uint4(0u, (uint32_t)v, (uint32_t)F.findex, (uint32_t)F.problem);
     by_rank(rank, [&](auto lk) {
       constexpr int L = decltype(lk)::value;
-      if (s_ident)      // full rank: the outcome is the coefficient bits (no table lookup)
+      if (ident)        // full rank: the outcome is the coefficient bits (no table lookup)
         for_shots<L>(0u, E.shots, ctr, E.keys, cmask,
                      [&](uint32_t c) { atomicAdd(&h32[c >> 2], 1u << ((c & 3u) << 3)); });
       else
@@ -1767,7 +1777,7 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 2 : 3) sample_hub8_kernel(DevP
       by_rank(rank, [&](auto lk) {
         constexpr int L = decltype(lk)::value;
         for_shots<L>(0u, E.shots, ctr, E.keys, cmask, [&](uint32_t c) {
-          const uint32_t y = space_point<L>(tbl, off, c);
+          const uint32_t y = ident ? c : space_point<L>(tbl, off, c);
           if ((int)((y >> mh) & 1u) != h) return;
           const uint32_t yh = (y & (uint32_t)(Mh - 1)) | ((y >> m) << mh);
           atomicAdd(&h32[yh >> 1], 1u << ((yh & 1u) << 4));
