@@ -320,22 +320,24 @@ int fragment_problem(Problem& p, int pi, std::vector<Frag>& out, std::string& er
   for (auto& c : p.cuts) pos[c.qubit].push_back((int)c.gate_index);
   std::vector<int> base(n + 1, 0);
   for (int q = 0; q < n; ++q) base[q + 1] = base[q] + (int)pos[q].size() + 1;
-  // segment of each gate's operands, in one pass over the gates: a cut
-  // (q, g) starts q's next segment at gate g
-  std::vector<int> seg_a(ng), seg_b(ng, -1), next_cut(n, 0);
-  auto seg_at = [&](int q, int gi) {
-    int& k = next_cut[q];
-    while (k < (int)pos[q].size() && pos[q][k] <= gi) ++k;
-    return base[q] + k;
+  // Each qubit's current segment while walking the gates: a cut (q, g) starts
+  // q's next segment at gate g.  The cuts are sorted by gate index, so one
+  // cursor over them moves every qubit's segment forward; each pass over the
+  // gates replays it (no per-gate segment arrays).
+  thread_local std::vector<int> segcur;
+  auto walk = [&](auto&& visit) {
+    segcur.assign(base.begin(), base.end() - 1);
+    size_t nc = 0;
+    for (int gi = 0; gi < ng; ++gi) {
+      while (nc < p.cuts.size() && (int)p.cuts[nc].gate_index <= gi) ++segcur[p.cuts[nc++].qubit];
+      const auto& g = p.gates[gi];
+      visit(gi, g, segcur[g[1]], is_two_qubit(g[0]) ? segcur[g[2]] : -1);
+    }
   };
-  for (int gi = 0; gi < ng; ++gi) {
-    const auto& g = p.gates[gi];
-    seg_a[gi] = seg_at(g[1], gi);
-    if (is_two_qubit(g[0])) seg_b[gi] = seg_at(g[2], gi);
-  }
   UF uf(base[n]);
-  for (int gi = 0; gi < ng; ++gi)
-    if (seg_b[gi] >= 0) uf.join(seg_a[gi], seg_b[gi]);
+  walk([&](int, const std::array<int, 3>&, int sa, int sb) {
+    if (sb >= 0) uf.join(sa, sb);
+  });
   // fragments ordered by first wire; wires by (qubit, segment) = segment id
   std::vector<int> root_to_frag(base[n], -1);
   std::vector<std::pair<int, int>> where(base[n]);
@@ -356,25 +358,24 @@ int fragment_problem(Problem& p, int pi, std::vector<Frag>& out, std::string& er
     }
   {
     std::vector<int> count(out.size() - first, 0);
-    for (int gi = 0; gi < ng; ++gi) count[where[seg_a[gi]].first - first]++;
+    walk([&](int, const std::array<int, 3>&, int sa, int) { count[where[sa].first - first]++; });
     for (size_t fi = 0; fi < count.size(); ++fi) {
       out[first + fi].gates.reserve(count[fi]);
       if (!p.gparam.empty()) out[first + fi].gparam.reserve(count[fi]);
     }
   }
-  for (int gi = 0; gi < ng; ++gi) {
-    const auto& g = p.gates[gi];
-    const auto wa = where[seg_a[gi]];
+  walk([&](int gi, const std::array<int, 3>& g, int sa, int sb) {
+    const auto wa = where[sa];
     Frag& f = out[wa.first];
-    if (seg_b[gi] >= 0) {
-      f.gates.push_back({g[0], wa.second, where[seg_b[gi]].second});
+    if (sb >= 0) {
+      f.gates.push_back({g[0], wa.second, where[sb].second});
       if (!p.gparam.empty()) f.gparam.push_back(0.0);
     } else {
       f.gates.push_back({g[0], wa.second, -1});
       if (!p.gparam.empty()) f.gparam.push_back(p.gparam[gi]);
       if (!is_clifford_op(g[0])) f.clifford = false;
     }
-  }
+  });
   for (int ci = 0; ci < (int)p.cuts.size(); ++ci) {
     int q = p.cuts[ci].qubit;
     int k = (int)(std::find(pos[q].begin(), pos[q].end(), (int)p.cuts[ci].gate_index) - pos[q].begin()) + 1;
