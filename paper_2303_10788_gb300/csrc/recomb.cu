@@ -70,6 +70,12 @@ __device__ __forceinline__ void for_each_prep(const FragDev& F, const PauliSplit
 }
 
 __device__ __forceinline__ float to_bf16f(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+// sum += p with the low part the rounding loses kept in comp (Neumaier)
+__device__ __forceinline__ void neumaier(float& sum, float& comp, float p) {
+  const float t = sum + p;                     // keep the low part the sum loses
+  comp += fabsf(sum) >= fabsf(p) ? (sum - t) + p : (p - t) + sum;
+  sum = t;
+}
 
 }  // namespace
 
@@ -917,10 +923,12 @@ __global__ void __launch_bounds__(256) hub_bf16_kernel(HubView QT, __nv_bfloat16
   }
 }
 
-// The split-K partials summed in FP64 and scattered to marginal order.  A
-// CTA takes 32 consecutive outputs (one per lane, so every load of a warp is
-// one contiguous row segment); its 8 warps sum splits w, w + 8, ... and the
-// warps' sums are added in warp order: a fixed order, many loads in flight.
+// The split-K partials summed and scattered to marginal order.  A CTA takes
+// 32 consecutive outputs (one per lane, so every load of a warp is one
+// contiguous row segment); its 8 warps sum splits w, w + 8, ... with
+// compensated FP32 sums (FP64 arithmetic is scarce on this GPU), and the
+// warps' (sum, compensation) pairs are added in FP64 in warp order: a fixed
+// order, many loads in flight.
 __global__ void __launch_bounds__(256) reduce_scatter_kernel(DevPlan P, const long long* prefix, int np,
                                                              long long total, const float* scratch, double* marg_out,
                                                              int use_tc) {
@@ -928,7 +936,7 @@ __global__ void __launch_bounds__(256) reduce_scatter_kernel(DevPlan P, const lo
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (long long base = blockIdx.x * 32ll; base < total; base += gridDim.x * 32ll) {
     const long long g = base + lane;
-    double a0 = 0.0, a1 = 0.0;
+    float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
     int pi = -1;
     if (g < total) {
       pi = find_seg(prefix, np, g);
@@ -943,13 +951,15 @@ __global__ void __launch_bounds__(256) reduce_scatter_kernel(DevPlan P, const lo
         for (; s + 24 < splits; s += 32) {    // four loads in flight
           const float v0 = pp[(long long)s * st], v1 = pp[(long long)(s + 8) * st];
           const float v2 = pp[(long long)(s + 16) * st], v3 = pp[(long long)(s + 24) * st];
-          a0 += (double)v0 + (double)v1;
-          a1 += (double)v2 + (double)v3;
+          neumaier(s0, c0, v0);
+          neumaier(s1, c1, v1);
+          neumaier(s0, c0, v2);
+          neumaier(s1, c1, v3);
         }
-        for (; s < splits; s += 8) a0 += (double)pp[(long long)s * st];
+        for (; s < splits; s += 8) neumaier(s0, c0, pp[(long long)s * st]);
       }
     }
-    red[w][lane] = a0 + a1;
+    red[w][lane] = ((double)s0 + (double)c0) + ((double)s1 + (double)c1);
     __syncthreads();
     if (w == 0 && pi >= 0) {
       const ProblemDev& Pb = P.problems[pi];
@@ -1091,11 +1101,6 @@ __device__ __noinline__ void z_string_block(const DevPlan& P, const DevRes& R, c
 // One operand entry as a float: FP32 as stored, or an int16 count sum times 1/shots.
 __device__ __forceinline__ float hub_elem(const float* A, float, long long i) { return A[i]; }
 __device__ __forceinline__ float hub_elem(const int16_t* A, float sc, long long i) { return (float)A[i] * sc; }
-__device__ __forceinline__ void neumaier(float& sum, float& comp, float p) {
-  const float t = sum + p;                     // keep the low part the sum loses
-  comp += fabsf(sum) >= fabsf(p) ? (sum - t) + p : (p - t) + sum;
-  sum = t;
-}
 
 // The first leaf of a slice, read from the hub operand in global memory:
 //   Y[r][x][m] = sum_g Q^T[kr(r) | kg(g)][m0 + m] T'[x][g]
