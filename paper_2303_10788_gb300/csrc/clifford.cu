@@ -1386,6 +1386,46 @@ __device__ __forceinline__ void hub_pair_out_packed(unsigned (&p)[16], const int
   }
 }
 
+// The same readout specialised on Q = the quantum outputs (2^Q bins, all
+// loaded; the Walsh-Hadamard transform has Q stages): whole-word adds, since
+// p = lo + 2^16 hi with |lo|, |hi| <= shots < 2^15 at every stage keeps both
+// lanes recoverable (the low lane's borrow is undone when the pair is
+// written), and the variant's sign masks (bits < Q) pick by a select tree.
+template <int Q>
+__device__ __forceinline__ void hub16_readout(const uint32_t* __restrict__ hist2, int m, int M, const int* s_czD,
+                                              const int* s_czS, int nz, float* QT, int16_t* QH, float inv) {
+  constexpr int NB = 1 << Q;
+  for (int o2 = threadIdx.x; o2 < (M >> 1); o2 += blockDim.x) {
+    const int o = 2 * o2;
+    unsigned p[NB];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) p[b] = hist2[((uint32_t)o | ((uint32_t)b << m)) >> 1];
+#pragma unroll
+    for (int h = 1; h < NB; h <<= 1)
+#pragma unroll
+      for (int b = 0; b < NB; ++b)
+        if (!(b & h)) {
+          const unsigned x = p[b], y = p[b | h];
+          p[b] = x + y;
+          p[b | h] = x - y;
+        }
+    for (int cz = 0; cz < (1 << nz); ++cz) {
+      const int sm = s_czS[cz];
+      unsigned t[NB];
+#pragma unroll
+      for (int b = 0; b < NB; ++b) t[b] = p[b];
+#pragma unroll
+      for (int lvl = 0; lvl < Q; ++lvl)
+#pragma unroll
+        for (int b = 0; b < (NB >> (lvl + 1)); ++b) t[b] = ((sm >> lvl) & 1) ? t[2 * b + 1] : t[2 * b];
+      const unsigned w = t[0] + ((t[0] & 0x8000u) << 1);      // the int16 pair (o, o+1)
+      const long long idx = (long long)s_czD[cz] * M + o;
+      if (QH) *reinterpret_cast<unsigned*>(QH + idx) = w;
+      else put2(QT, nullptr, idx, (int)(short)(w & 0xffffu), (int)(short)(w >> 16), inv);
+    }
+  }
+}
+
 }  // namespace
 
 // The operand rows a hub variant v owns: its preparation digits at the input
@@ -1512,12 +1552,12 @@ __global__ void __launch_bounds__(512) sample_hub_kernel(DevPlan P, DevRes R, Ev
       // an output's bins sum to at most the shots, so every transform value
       // fits a signed 16-bit lane: the counter word (outputs o, o+1) is
       // transformed as is, two outputs per SIMD add
-      for (int o2 = threadIdx.x; o2 < (M >> 1); o2 += blockDim.x) {
-        const int o = 2 * o2;
-        unsigned pk[16];
-#pragma unroll
-        for (int b = 0; b < 16; ++b) pk[b] = b < nb ? hist2[((uint32_t)o | ((uint32_t)b << m)) >> 1] : 0u;
-        hub_pair_out_packed(pk, s_czD, s_czS, nz, QT, QH, M, o, inv);
+      switch (F.qout) {
+        case 0: hub16_readout<0>(hist2, m, M, s_czD, s_czS, nz, QT, QH, inv); break;
+        case 1: hub16_readout<1>(hist2, m, M, s_czD, s_czS, nz, QT, QH, inv); break;
+        case 2: hub16_readout<2>(hist2, m, M, s_czD, s_czS, nz, QT, QH, inv); break;
+        case 3: hub16_readout<3>(hist2, m, M, s_czD, s_czS, nz, QT, QH, inv); break;
+        default: hub16_readout<4>(hist2, m, M, s_czD, s_czS, nz, QT, QH, inv); break;
       }
     } else
     for (int o2 = threadIdx.x; o2 < (M >> 1); o2 += blockDim.x) {
