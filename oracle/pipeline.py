@@ -4,8 +4,8 @@ Follows the paper's flow (Sec. V): cut the circuit (Sec. V-A), evaluate every
 variant of every fragment -- Clifford fragments by a stabilizer tableau,
 non-Clifford ones by an exact statevector (Sec. V-B) -- and rebuild the
 distribution of the uncut circuit by contracting the fragment tensors
-(Sec. V-C).  No maximum-likelihood correction is applied (the hot path keeps
-the raw fragment data).
+(Sec. V-C).  The maximum-likelihood correction of the fragment models is a
+separate step (``oracle.mlcorrect.ml_correct`` on ``OracleResult.tensors``).
 
 Modes: ``"exact"`` uses the closed-form 2^-rank distribution of each Clifford
 variant (strong simulation, Sec. V-C last paragraph); ``"sampled"`` draws
