@@ -293,6 +293,37 @@ int ccs_recombine(ccs_ctx ctx, ccs_plan plan, ccs_res res, const ccs_recomb_opts
 int ccs_recombine_noalloc(ccs_ctx ctx, ccs_plan plan, ccs_res res, int precision, double* marginal_out,
                           double* zexp_out);
 
+/* --- maximum-likelihood correction of fragment models (Sec. V-C) ----------- */
+#define CCS_ML_SAMPLED 0   /* the fragments estimated from shots: the Clifford fragments of a
+                              CCS_SAMPLED result (nothing to do for an exact result) */
+#define CCS_ML_ALL 1       /* every fragment; exactly evaluated ones are physical already and
+                              come back unchanged up to FP32 rounding */
+/* Before the contraction, turn the selected fragments' data into physical
+ * (self-consistent) fragment models, in place on the result (Sec. V-C:
+ * maximum-likelihood corrections that mitigate sampling error).  The
+ * paper names the step and its purpose only; the reading implemented:
+ * fragment f's model is its Choi form, one operator per outcome o of its
+ * marginal wires on its d cut slots (slot order),
+ *   J_o = 2^-d sum_P T_f(o, P) (x)_j s_j(P_j),
+ * s_j(P) = P^T where slot j is a quantum input and P where it is a quantum
+ * output; physical means every J_o positive semidefinite with
+ * sum_o Tr J_o = 2^{q_in}; the maximum-likelihood model under Gaussian shot
+ * noise of equal variance per T_f entry is the physical model nearest in
+ * Frobenius norm: all blocks' eigenvalues are projected together onto
+ * {lambda >= 0, sum = 2^{q_in}} and each block is rebuilt from its own
+ * eigenvectors (Smolin, Gambetta and Smith, PRL 108, 070502, 2012).  The
+ * Z-string values are exact in every mode and are left alone.
+ *
+ * Afterwards ccs_recombine contracts the corrected models, ccs_get_tensor
+ * returns them (hubs included) and ccs_get_operand the corrected operands
+ * (FP32); the next ccs_eval_variants replaces them with raw data again.
+ * Eigendecompositions run in FP32 (cyclic Jacobi), one CTA per block.
+ * Asynchronous on the context stream.  Errors: INVALID_ARG (bad arguments,
+ * a CCS_STITCH result), UNSUPPORTED (a selected fragment with more than 6
+ * cut slots; a host-only context), OOM (its scratch: 4 (N + N^2) bytes per
+ * block, N = 2^(d+1)), CUDA. */
+int ccs_ml_correct(ccs_ctx ctx, ccs_plan plan, ccs_res res, int which);
+
 /* --- learned cut scorer ------------------------------------------------------ */
 /* A message-passing network over a circuit's qubit interaction graph with a
  * candidate cut set applied predicts log(evaluation + recombination time);

@@ -16,7 +16,7 @@ SRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libccs.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "clifford.cu", "statevec.cu", "recomb.cu", "gemm_tc.cu", "mpnn.cu", "plan.cpp", "cutter.cpp", "features.cpp"]
+SOURCES = ["api.cu", "clifford.cu", "statevec.cu", "recomb.cu", "gemm_tc.cu", "mpnn.cu", "mlcorrect.cu", "plan.cpp", "cutter.cpp", "features.cpp"]
 
 
 def _nvcc():

@@ -21,6 +21,7 @@ ERRORS = {-1: "INVALID_ARG", -2: "UNSUPPORTED_GATE", -3: "TOO_MANY_CUTS", -4: "N
           -5: "OOM", -6: "CUDA", -7: "TIMEOUT", -8: "UNSUPPORTED", -9: "DEVICE_CHECK"}
 CCS_EXACT, CCS_SAMPLED, CCS_STITCH = 0, 1, 2
 CCS_FP32, CCS_BF16 = 0, 1
+CCS_ML_SAMPLED, CCS_ML_ALL = 0, 1
 
 # Every symbol include/ccs.h declares (checked by the ABI test).
 EXPORTS = ["ccs_version", "ccs_create", "ccs_destroy", "ccs_last_error", "ccs_build_fragments",
@@ -28,7 +29,7 @@ EXPORTS = ["ccs_version", "ccs_create", "ccs_destroy", "ccs_last_error", "ccs_bu
            "ccs_fragment_info_get", "ccs_plan_cuts", "ccs_fragment_wires", "ccs_get_tableau",
            "ccs_get_outcome_space", "ccs_get_counts", "ccs_get_dist", "ccs_get_zvals", "ccs_get_tensor",
            "ccs_set_profiling", "ccs_get_stage_times", "ccs_cut_candidates", "ccs_recombine_noalloc",
-           "ccs_get_tuning", "ccs_get_operand", "ccs_launch_count"]
+           "ccs_get_tuning", "ccs_get_operand", "ccs_launch_count", "ccs_ml_correct"]
 STAGES = ["clifford", "sample", "statevector", "fold", "recombine", "operands"]
 
 
@@ -126,6 +127,7 @@ def lib():
             "ccs_get_operand": ([P, P, C.c_int, C.c_int, P], C.c_int),
             "ccs_set_profiling": ([P, C.c_int], C.c_int),
             "ccs_recombine_noalloc": ([P, P, P, C.c_int, P, P], C.c_int),
+            "ccs_ml_correct": ([P, P, P, C.c_int], C.c_int),
             "ccs_get_tuning": ([P, P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                 C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
             "ccs_cut_candidates": ([P, C.POINTER(ccs_problem), C.POINTER(ccs_cut_opts), C.POINTER(ccs_cut),
@@ -451,6 +453,12 @@ def ccs_recombine_noalloc(ctx, plan, res, marginal_out, zexp_out=None, precision
                                           C.c_void_p(zexp_out.data_ptr() if zexp_out is not None else None)),
               "ccs_recombine_noalloc")
     return marginal_out, zexp_out
+
+
+def ccs_ml_correct(ctx, plan, res, which=CCS_ML_SAMPLED):
+    """Maximum-likelihood correction of the result's fragment models in place
+    (Sec. V-C); asynchronous on the context stream."""
+    ctx.check(lib().ccs_ml_correct(ctx.h, plan.h, res.h, which), "ccs_ml_correct")
 
 
 def ccs_get_tuning(ctx, res):

@@ -358,6 +358,19 @@ struct ccs_res_s {
   bool variant_path = false;  // autotuned: every variant simulates its whole circuit (small plans)
   float* scratch = nullptr;   // recombination: R operand + split-K partials
   uint16_t* rt_scratch = nullptr;   // bf16 R'^T of tensor-core-eligible problems
+  int eval_i16 = 0;           // hub_i16 of the last evaluation (the one its graph holds)
+  int ml_applied = 0;         // 1 + the fragment selection of ccs_ml_correct since the evaluation
+  struct MlCache {            // device records of the last ccs_ml_correct selection
+    int key = -1;
+    MlFrag* d_frags = nullptr;
+    int n_frags = 0;
+    std::vector<MlGroup> groups;
+    float* scratch = nullptr;
+    size_t scratch_len = 0;
+    double* theta = nullptr;
+    FoldSet leaves{nullptr, nullptr, 0, 0};   // corrected star leaves: T' is formed again
+    bool i16_hub = false;
+  } ml;
   ~ccs_res_s() {
     if (graph) cudaGraphExecDestroy(graph);
     if (rgraph) cudaGraphExecDestroy(rgraph);
@@ -1429,8 +1442,10 @@ int ccs_eval_variants(ccs_ctx c, ccs_plan p, const ccs_eval_opts* opts, ccs_res*
     r->ep = e;
     {   // sampled hubs keep exact 16-bit count sums (|sum| <= shots)
       const int i16 = (e.mode == CCS_SAMPLED && e.shots <= 32767u) ? 1 : 0;
-      if (i16 != r->dr.hub_i16) drop_graph();
-      r->dr.hub_i16 = i16;
+      if (i16 != r->eval_i16) drop_graph();
+      r->eval_i16 = i16;
+      r->dr.hub_i16 = i16;   // a maximum-likelihood correction may have left the operand in FP32
+      r->ml_applied = 0;
       r->dr.hub_scale = (float)e.inv_shots;
     }
     if (opts->autotune && !r->graph && opts->hub_sampler == 0) {
@@ -1750,17 +1765,108 @@ int ccs_get_operand(ccs_ctx c, ccs_res r, int problem, int fragment, float* out)
   });
 }
 
+int ccs_ml_correct(ccs_ctx c, ccs_plan p, ccs_res r, int which) {
+  return abi_guard([&](int code, const char* m) { return fail(c, code, m); }, [&]() -> int {
+    if (!c || !p || !r || r->plan != p) return fail(c, CCS_ERR_INVALID_ARG, "bad arguments");
+    if (c->host_only) return fail(c, CCS_ERR_UNSUPPORTED, "host-only context cannot correct fragment models");
+    if (which != CCS_ML_SAMPLED && which != CCS_ML_ALL) return fail(c, CCS_ERR_INVALID_ARG, "bad fragment selection");
+    if (r->ep.mode == CCS_STITCH)
+      return fail(c, CCS_ERR_INVALID_ARG, "a stitched result holds no fragment model to correct");
+    cudaSetDevice(c->device);
+    auto& mc = r->ml;
+    const int key = which * 4 + r->ep.mode * 2 + (r->dr.hub_i16 ? 1 : 0);
+    if (mc.key != key) {
+      std::vector<MlFrag> recs;
+      std::vector<int> leaf_idx;
+      std::vector<long long> leaf_pref{0};
+      std::vector<MlGroup> groups;
+      long long floats = 0;
+      bool i16_hub = false;
+      for (int dd = 0; dd <= kMlMaxSlots; ++dd) {
+        MlGroup G{dd, (int)recs.size(), 0, 0};
+        for (int g = 0; g < (int)p->fdev.size(); ++g) {
+          const FragDev& F = p->fdev[g];
+          const bool pick = which == CCS_ML_ALL || (F.clifford && r->ep.mode == CCS_SAMPLED);
+          if (!pick) continue;
+          if (F.n_slots > kMlMaxSlots)
+            return fail(c, CCS_ERR_UNSUPPORTED, "maximum-likelihood correction supports at most 6 cut slots per fragment");
+          if (F.n_slots != dd) continue;
+          const long long nb = 1ll << F.m, N = 2ll << dd;
+          MlFrag mf{};
+          mf.frag = g;
+          mf.d = dd;
+          mf.hub = F.role == 1 ? 1 : 0;
+          mf.i16 = (mf.hub && r->dr.hub_i16 && F.clifford) ? 1 : 0;
+          i16_hub = i16_hub || mf.i16;
+          mf.index = (int)recs.size();
+          mf.blk0 = G.blocks;
+          mf.ev_off = floats;
+          floats += nb * N;
+          mf.vec_off = floats;
+          floats += nb * N * N;
+          mf.total = 2.0 * (double)(1ll << F.qin);
+          recs.push_back(mf);
+          G.blocks += nb;
+          ++G.count;
+          if (F.role == 2) {
+            leaf_idx.push_back(g);
+            leaf_pref.push_back(leaf_pref.back() + (nb << (2 * dd)));
+          }
+        }
+        if (G.count) groups.push_back(G);
+      }
+      if (recs.empty()) {   // nothing estimated from shots: the models are exact
+        mc.key = key;
+        mc.n_frags = 0;
+        mc.groups.clear();
+        r->ml_applied = 1 + which;
+        return CCS_OK;
+      }
+      if ((size_t)floats > mc.scratch_len) {
+        mc.scratch = r->A.get<float>((size_t)floats);
+        mc.scratch_len = mc.scratch ? (size_t)floats : 0;
+        if (!mc.scratch) return fail(c, CCS_ERR_OOM, "correction scratch");
+      }
+      int* d_leaf = nullptr;
+      long long* d_pref = nullptr;
+      if (!upload(c, r->A, recs, &mc.d_frags) || !(mc.theta = r->A.get<double>(recs.size())) ||
+          !upload(c, r->A, leaf_idx, &d_leaf) || !upload(c, r->A, leaf_pref, &d_pref))
+        return fail(c, CCS_ERR_OOM, "correction records");
+      mc.n_frags = (int)recs.size();
+      mc.groups = groups;
+      mc.leaves = FoldSet{d_leaf, d_pref, (int)leaf_idx.size(), leaf_pref.back()};
+      mc.i16_hub = i16_hub;
+      mc.key = key;
+    }
+    if (mc.n_frags == 0) {
+      r->ml_applied = 1 + which;
+      return CCS_OK;
+    }
+    cudaError_t e = launch_ml_correct(p->dp, r->dr, mc.d_frags, mc.n_frags, mc.groups.data(), (int)mc.groups.size(),
+                                      mc.scratch, mc.theta, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "correction kernels");
+    if (mc.i16_hub) r->dr.hub_i16 = 0;   // the corrected hub operands are FP32 now
+    if (mc.leaves.nf &&
+        (e = launch_operands(p->dp, r->dr, r->ep, FoldSet{nullptr, nullptr, 0, 0}, mc.leaves, c->stream)) !=
+            cudaSuccess)
+      return cuda_fail(c, e, "leaf operands");
+    r->ml_applied = 1 + which;
+    return CCS_OK;
+  });
+}
+
 int ccs_get_tensor(ccs_ctx c, ccs_res r, int problem, int fragment, float* out) {
   return abi_guard([&](int code, const char* m) { return fail(c, code, m); }, [&]() -> int {
     const FragDev* d;
     int rc = locate(c, r, problem, fragment, -1, &d);
     if (rc) return rc;
     const long long cnt = (1ll << d->m) << (2 * d->n_slots);
-    if (d->role == 1 && d->clifford && r->ep.mode == CCS_SAMPLED && !r->ep.keep_tableaus)
+    const bool corrected = r->ml_applied && (d->clifford || r->ml_applied == 1 + CCS_ML_ALL);
+    if (d->role == 1 && !corrected && d->clifford && r->ep.mode == CCS_SAMPLED && !r->ep.keep_tableaus)
       return fail(c, CCS_ERR_INVALID_ARG, "a sampled hub's tensor needs its counts (keep_tableaus)");
     if (d->role == 1 && d->clifford && r->ep.mode == CCS_STITCH)
       return fail(c, CCS_ERR_INVALID_ARG, "a stitched hub forms no per-variant distribution (see ccs_get_operand)");
-    if (d->role == 1) {   // a hub's T is not formed on the hot path: fold it now
+    if (d->role == 1 && !corrected) {   // a hub's T is not formed on the hot path: fold it now
       const int g = (int)(d - r->plan->fdev.data());
       std::vector<int> fi{g};
       std::vector<long long> tp{0, cnt};

@@ -230,6 +230,31 @@ struct FoldSet {
 };
 cudaError_t launch_fold(const DevPlan& p, const DevRes& r, const EvalParams& e, const FoldSet& f,
                         cudaStream_t s);
+// Maximum-likelihood correction of fragment models (Sec. V-C).  One record
+// per fragment to correct; fragments with the same number of cut slots d
+// form a group (one launch of the per-block kernels).
+struct MlFrag {
+  int frag;                // FragDev index
+  int d;                   // cut slots (the Choi block's real embedding has N = 2^(d+1) rows)
+  int hub;                 // 1: a star hub (its operand Q^T is read and rewritten as well)
+  int i16;                 // the hub operand holds int16 count sums (value = sum x hub_scale)
+  int index;               // position in the launch's record list (its threshold)
+  long long blk0;          // first block (outcome 0) of the fragment within its group
+  long long ev_off;        // float index of its 2^m x N eigenvalues in the scratch
+  long long vec_off;       // float index of its 2^m x N x N eigenvector entries in the scratch
+  double total;            // trace of the doubled eigenvalue list: 2 x 2^qin
+};
+struct MlGroup {
+  int d, first, count;     // cut slots; range of MlFrag records
+  long long blocks;        // sum of 2^m over them
+};
+// Eigendecomposition of every block, the threshold per fragment, and the
+// rebuilt T_f (and hub operands); d <= 6.  `scratch` holds the eigenvalues
+// and eigenvectors, `theta` one double per record.
+cudaError_t launch_ml_correct(const DevPlan& p, const DevRes& r, const MlFrag* d_frags, int n_frags,
+                              const MlGroup* groups, int n_groups, float* scratch, double* theta, cudaStream_t s);
+constexpr int kMlMaxSlots = 6;
+
 // Contraction operands of star problems: Q of each hub from its variant data
 // (set `hubs`) and T' of every other fragment from its T (set `others`).
 cudaError_t launch_operands(const DevPlan& p, const DevRes& r, const EvalParams& e, const FoldSet& hubs,

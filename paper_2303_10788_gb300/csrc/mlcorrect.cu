@@ -1,0 +1,424 @@
+// Maximum-likelihood correction of fragment models (Sec. V-C: before the
+// contraction the fragment data become self-consistent fragment models,
+// which mitigates the sampling error of the Clifford fragments' shots).
+//
+// A fragment's model is its Choi form, one Hermitian operator per outcome o
+// of its marginal wires on its d cut slots:
+//   J_o = 2^-d sum_P T_f(o, P) (x)_j s_j(P_j),  s_j(P) = P^T at a quantum
+//   input, P at a quantum output;  T_f(o, P) = Tr[(x)_j s_j(P_j) J_o].
+// Physical: every J_o positive semidefinite, sum_o Tr J_o = 2^{q_in}.  The
+// maximum-likelihood model under Gaussian shot noise of equal variance per
+// T_f entry is the nearest physical one in Frobenius norm: all blocks'
+// eigenvalues projected together onto {lambda >= 0, sum = 2^{q_in}}, each
+// block rebuilt from its own eigenvectors (the eigenvalue projection of
+// Smolin, Gambetta and Smith, PRL 108, 070502, 2012).
+//
+// GPU form, three launches per group of fragments with the same d (d <= 6):
+//  1. ml_eig_kernel, one CTA per (fragment, outcome): the block's T_f row
+//     (a star hub's operand is stored by preparation at its inputs and is
+//     turned into Pauli digits first), the Choi block J_o as its real
+//     embedding [[Re J, -Im J], [Im J, Re J]] (N = 2^(d+1) rows: the same
+//     eigenvalues, each twice), and a cyclic Jacobi eigendecomposition in
+//     shared memory: N/2 disjoint rotations per round in the round-robin
+//     order, N - 1 rounds per sweep, sweeps until no rotation is left above
+//     2^-24 of the block's Frobenius norm (at most kMlMaxSweeps).  The
+//     eigenvalues and eigenvectors go to a scratch array.
+//  2. ml_threshold_kernel, one CTA per fragment: the threshold theta with
+//     sum max(lambda - theta, 0) = 2 x 2^{q_in} over the doubled eigenvalue
+//     list, by Michelot's finite algorithm (J. Optim. Theory Appl. 50, 1986):
+//     theta = (sum of the kept values - total) / (their count), keep the
+//     values above theta, repeat until the kept set stops changing.
+//  3. ml_rebuild_kernel, one CTA per (fragment, outcome): J'_o from the
+//     eigenvectors with eigenvalues max(lambda - theta, 0), then T'_f(o, P);
+//     written to T_f, and a hub's operand (by preparation at its inputs) is
+//     rewritten in FP32.
+#include "kernels.cuh"
+
+namespace ccs {
+
+namespace {
+
+constexpr int kMlMaxSweeps = 30;
+
+__device__ __forceinline__ int ml_find(const MlFrag* __restrict__ fr, int n, long long blk) {
+  int lo = 0, hi = n;      // fr[lo].blk0 <= blk < fr[hi].blk0
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (fr[mid].blk0 <= blk) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Sum over the CTA (every thread gets the result); red holds 32 entries.
+template <class T>
+__device__ T block_sum(T v, T* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[w] = v;
+  __syncthreads();
+  T s = 0;
+  for (int i = 0; i < nw; ++i) s += red[i];
+  return s;
+}
+
+// Entry [r][c] of the slot operator (x)_j s_j(P_j) for the Pauli digits of P
+// where the entry is nonzero: returns the power of i (0..3) of the entry
+// (its value is i^pw, a sign folded in as 2).  At slot j the entry needs
+// P_j in {I, Z} when r_j == c_j and in {X, Y} otherwise; Z contributes
+// (-1)^{r_j}; Y at an output contributes -i for r_j = 0 and +i for r_j = 1,
+// its transpose at an input the opposite.
+__device__ __forceinline__ int slot_entry_phase(int P, int r, int d, unsigned inmask) {
+  int pw = 0;
+  for (int j = 0; j < d; ++j) {
+    const int pj = (P >> (2 * j)) & 3, rj = (r >> j) & 1;
+    if (pj == 3) pw += 2 * rj;
+    else if (pj == 2) pw += 1 + 2 * ((rj ^ 1) ^ (int)((inmask >> j) & 1));
+  }
+  return pw & 3;
+}
+
+__device__ __forceinline__ unsigned input_mask(const FragDev& F) {
+  unsigned m = 0;
+  for (int j = 0; j < F.n_slots; ++j)
+    if ((F.slot_code[j] >> 8) == 0) m |= 1u << j;
+  return m;
+}
+
+}  // namespace
+
+// One CTA per (fragment, outcome o) of a group with d cut slots.
+__global__ void __launch_bounds__(256) ml_eig_kernel(DevPlan P, DevRes R, const MlFrag* __restrict__ fr, int nfr,
+                                                     int d, float* __restrict__ scratch) {
+  extern __shared__ float sm[];
+  const int D = 1 << d, N = 2 * D, KP = 1 << (2 * d), H = N / 2;
+  float* M = sm;                 // N x N
+  float* V = M + N * N;          // N x N
+  float* sT = V + N * N;         // the block's T_f row (4^d)
+  float* rc = sT + KP;           // per pair of the round: cosine, sine, tangent,
+  float* rs = rc + H;            // and the pair's entries before the rotation
+  float* rt = rs + H;
+  float* rpp = rt + H;
+  float* rqq = rpp + H;
+  float* rpq = rqq + H;
+  int* rp = reinterpret_cast<int*>(rpq + H);
+  int* rq = rp + H;
+  __shared__ float red[32];
+  __shared__ int any_rot;
+  const int tid = threadIdx.x, nt = blockDim.x;
+
+  const long long blk = blockIdx.x;
+  const MlFrag& mf = fr[ml_find(fr, nfr, blk)];
+  const FragDev& F = P.frags[mf.frag];
+  const int o = (int)(blk - mf.blk0);
+  const unsigned inmask = input_mask(F);
+
+  // 1. the block's row of T_f
+  if (!mf.hub) {
+    const float* src = R.T + F.T_off + ((long long)o << (2 * d));
+    for (int i = tid; i < KP; i += nt) sT[i] = src[i];
+  } else {   // hub operand Q^T[D][o]: preparation digit s at each input slot
+    const long long Mo = 1ll << F.m;
+    if (mf.i16) {
+      const int16_t* q = reinterpret_cast<const int16_t*>(R.TQ + F.T_off);
+      for (int i = tid; i < KP; i += nt) sT[i] = (float)q[(long long)i * Mo + o] * R.hub_scale;
+    } else {
+      for (int i = tid; i < KP; i += nt) sT[i] = R.TQ[F.T_off + (long long)i * Mo + o];
+    }
+    // T(P_j) = sum_s mu(P_j, s) Q(s): I = Q0 + Q1, X = 2 Q2 - Q0 - Q1,
+    // Y = 2 Q3 - Q0 - Q1, Z = Q0 - Q1 (the prepared states |0>,|1>,|+>,|+i>)
+    for (int j = 0; j < d; ++j) {
+      if (!((inmask >> j) & 1)) continue;
+      __syncthreads();
+      const int st = 1 << (2 * j);
+      for (int g = tid; g < KP / 4; g += nt) {
+        const int b = ((g >> (2 * j)) << (2 * j + 2)) | (g & (st - 1));
+        const float q0 = sT[b], q1 = sT[b + st], q2 = sT[b + 2 * st], q3 = sT[b + 3 * st];
+        sT[b] = q0 + q1;
+        sT[b + st] = 2.f * q2 - q0 - q1;
+        sT[b + 2 * st] = 2.f * q3 - q0 - q1;
+        sT[b + 3 * st] = q0 - q1;
+      }
+    }
+  }
+  __syncthreads();
+
+  // 2. J_o[r][c] = 2^-d sum over the 2^d Paulis whose slot operator is
+  //    nonzero at [r][c]; its real embedding and V = identity
+  const float scale = 1.f / (float)D;
+  float nrm = 0.f;
+  for (int e = tid; e < D * D; e += nt) {
+    const int r = e >> d, c = e & (D - 1), x = r ^ c;
+    float re = 0.f, im = 0.f;
+    for (int t = 0; t < D; ++t) {
+      int Pi = 0;
+      for (int j = 0; j < d; ++j) {
+        const int xj = (x >> j) & 1, tj = (t >> j) & 1;
+        Pi |= (xj ? (tj ? 2 : 1) : (tj ? 3 : 0)) << (2 * j);
+      }
+      const float v = sT[Pi];
+      switch (slot_entry_phase(Pi, r, d, inmask)) {
+        case 0: re += v; break;
+        case 1: im += v; break;
+        case 2: re -= v; break;
+        default: im -= v; break;
+      }
+    }
+    re *= scale;
+    im *= scale;
+    M[r * N + c] = re;
+    M[(r + D) * N + c + D] = re;
+    M[(r + D) * N + c] = im;
+    M[r * N + c + D] = -im;
+    nrm += 2.f * (re * re + im * im);
+  }
+  for (int e = tid; e < N * N; e += nt) V[e] = (e / N == e % N) ? 1.f : 0.f;
+  nrm = block_sum(nrm, red);
+  const float tol = sqrtf(nrm) * 5.9604645e-8f;   // 2^-24 of the Frobenius norm
+
+  // 3. cyclic Jacobi, round-robin pairs: round t pairs (N-1, t) and
+  //    ((t + i) mod (N-1), (t - i) mod (N-1)) for i = 1 .. N/2 - 1
+  if (nrm > 0.f) {
+    for (int sweep = 0; sweep < kMlMaxSweeps; ++sweep) {
+      if (tid == 0) any_rot = 0;
+      __syncthreads();
+      for (int t = 0; t < N - 1; ++t) {
+        if (tid < H) {
+          int a, b;
+          if (tid == 0) { a = N - 1; b = t; }
+          else { a = (t + tid) % (N - 1); b = (t - tid + N - 1) % (N - 1); }
+          const int p = min(a, b), q = max(a, b);
+          const float app = M[p * N + p], aqq = M[q * N + q], apq = M[p * N + q];
+          float c = 1.f, s = 0.f, tt = 0.f;
+          if (fabsf(apq) > tol) {   // Golub & Van Loan's symmetric Schur 2x2 rotation
+            const float tau = (aqq - app) / (2.f * apq);
+            tt = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+            c = 1.f / sqrtf(1.f + tt * tt);
+            s = tt * c;
+            if (tt != 0.f) any_rot = 1;
+          }
+          rp[tid] = p; rq[tid] = q;
+          rc[tid] = c; rs[tid] = s; rt[tid] = tt;
+          rpp[tid] = app; rqq[tid] = aqq; rpq[tid] = apq;
+        }
+        __syncthreads();
+        // rows p, q <- J^T M (consecutive threads along a row)
+        for (int w = tid; w < H * N; w += nt) {
+          const int i = w / N, k = w - i * N;
+          if (rt[i] == 0.f) continue;
+          const int p = rp[i], q = rq[i];
+          const float c = rc[i], s = rs[i];
+          const float mp = M[p * N + k], mq = M[q * N + k];
+          M[p * N + k] = c * mp - s * mq;
+          M[q * N + k] = s * mp + c * mq;
+        }
+        __syncthreads();
+        // columns p, q <- M J, and V <- V J (consecutive threads across pairs);
+        // the 2 x 2 block gets its exact rotated values
+        for (int w = tid; w < H * N; w += nt) {
+          const int k = w / H, i = w - k * H;
+          if (rt[i] == 0.f) continue;
+          const int p = rp[i], q = rq[i];
+          const float c = rc[i], s = rs[i];
+          if (k == p) {
+            M[p * N + p] = rpp[i] - rt[i] * rpq[i];
+            M[p * N + q] = 0.f;
+          } else if (k == q) {
+            M[q * N + q] = rqq[i] + rt[i] * rpq[i];
+            M[q * N + p] = 0.f;
+          } else {
+            const float mp = M[k * N + p], mq = M[k * N + q];
+            M[k * N + p] = c * mp - s * mq;
+            M[k * N + q] = s * mp + c * mq;
+          }
+          const float vp = V[k * N + p], vq = V[k * N + q];
+          V[k * N + p] = c * vp - s * vq;
+          V[k * N + q] = s * vp + c * vq;
+        }
+        __syncthreads();
+      }
+      const int more = any_rot;
+      __syncthreads();
+      if (!more) break;
+    }
+  }
+
+  // 4. eigenvalues (the diagonal) and eigenvectors (the columns of V)
+  float* ev = scratch + mf.ev_off + (long long)o * N;
+  float* vec = scratch + mf.vec_off + (long long)o * N * N;
+  for (int i = tid; i < N; i += nt) ev[i] = M[i * N + i];
+  for (int e = tid; e < N * N; e += nt) vec[e] = V[e];
+}
+
+// One CTA per fragment: theta over its doubled eigenvalue list.
+__global__ void __launch_bounds__(256) ml_threshold_kernel(DevPlan P, const MlFrag* __restrict__ fr,
+                                                           const float* __restrict__ scratch,
+                                                           double* __restrict__ theta_out) {
+  __shared__ double redd[32];
+  __shared__ long long redc[32];
+  const MlFrag& mf = fr[blockIdx.x];
+  const FragDev& F = P.frags[mf.frag];
+  const long long n = (1ll << F.m) * (2ll << mf.d);
+  const float* ev = scratch + mf.ev_off;
+  double theta = -1e300;
+  long long prev = -1;
+  // the kept set only shrinks, so at most n + 1 passes; the cap bounds the
+  // loop should rounding ever make it oscillate
+  for (long long it = 0; it <= n + 1 && it < 4096; ++it) {
+    double s = 0.0;
+    long long cnt = 0;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+      const double v = ev[i];
+      if (v > theta) { s += v; ++cnt; }
+    }
+    s = block_sum(s, redd);
+    cnt = block_sum(cnt, redc);
+    if (cnt == prev || cnt == 0) break;
+    prev = cnt;
+    const double th = (s - mf.total) / (double)cnt;
+    theta = th > theta ? th : theta;
+  }
+  if (threadIdx.x == 0) theta_out[blockIdx.x] = theta;
+}
+
+// One CTA per (fragment, outcome o): the corrected block and T'_f row.
+__global__ void __launch_bounds__(256) ml_rebuild_kernel(DevPlan P, DevRes R, const MlFrag* __restrict__ fr,
+                                                         int nfr, int d, const float* __restrict__ scratch,
+                                                         const double* __restrict__ theta) {
+  extern __shared__ float sm[];
+  const int D = 1 << d, N = 2 * D, KP = 1 << (2 * d);
+  float* V = sm;                 // N x N
+  float* lam = V + N * N;        // N clipped eigenvalues
+  float* Are = lam + N;          // D x D: Re J'
+  float* Aim = Are + D * D;      // D x D: Im J'
+  float* sT = Aim + D * D;       // 4^d
+  int* live = reinterpret_cast<int*>(sT + KP);   // indices of the nonzero eigenvalues
+  __shared__ int n_live;
+  const int tid = threadIdx.x, nt = blockDim.x;
+
+  const long long blk = blockIdx.x;
+  const int fi = ml_find(fr, nfr, blk);
+  const MlFrag& mf = fr[fi];
+  const FragDev& F = P.frags[mf.frag];
+  const int o = (int)(blk - mf.blk0);
+  const unsigned inmask = input_mask(F);
+  const float th = (float)theta[mf.index];
+  const float* ev = scratch + mf.ev_off + (long long)o * N;
+  const float* vec = scratch + mf.vec_off + (long long)o * N * N;
+  for (int e = tid; e < N * N; e += nt) V[e] = vec[e];
+  for (int i = tid; i < N; i += nt) lam[i] = fmaxf(ev[i] - th, 0.f);
+  __syncthreads();
+  if (tid == 0) {
+    int k = 0;
+    for (int i = 0; i < N; ++i)
+      if (lam[i] > 0.f) live[k++] = i;
+    n_live = k;
+  }
+  __syncthreads();
+  const int nl = n_live;
+  // M' = V diag(lam) V^T; Re J' is its top-left (= bottom-right) block and
+  // Im J' its bottom-left (= minus top-right) block, each taken as the mean
+  // of its two copies
+  for (int e = tid; e < D * D; e += nt) {
+    const int r = e >> d, c = e & (D - 1);
+    float a1 = 0.f, a2 = 0.f, b1 = 0.f, b2 = 0.f;
+    for (int t = 0; t < nl; ++t) {
+      const int k = live[t];
+      const float l = lam[k];
+      const float vr = V[r * N + k], vc = V[c * N + k], vr2 = V[(r + D) * N + k], vc2 = V[(c + D) * N + k];
+      a1 += vr * l * vc;
+      a2 += vr2 * l * vc2;
+      b1 += vr2 * l * vc;
+      b2 += vr * l * vc2;
+    }
+    Are[e] = 0.5f * (a1 + a2);
+    Aim[e] = 0.5f * (b1 - b2);
+  }
+  __syncthreads();
+  // T'(P) = Re Tr[S_P J'] = sum_r Re(S_P[r][c] J'[c][r]), c = r xor x(P)
+  for (int Pi = tid; Pi < KP; Pi += nt) {
+    int x = 0;
+    for (int j = 0; j < d; ++j) {
+      const int pj = (Pi >> (2 * j)) & 3;
+      if (pj == 1 || pj == 2) x |= 1 << j;
+    }
+    float acc = 0.f;
+    for (int r = 0; r < D; ++r) {
+      const int c = r ^ x;
+      const float re = Are[c * D + r], im = Aim[c * D + r];
+      switch (slot_entry_phase(Pi, r, d, inmask)) {   // Re(i^pw (re + i im))
+        case 0: acc += re; break;
+        case 1: acc -= im; break;
+        case 2: acc -= re; break;
+        default: acc += im; break;
+      }
+    }
+    sT[Pi] = acc;
+  }
+  __syncthreads();
+  float* dst = R.T + F.T_off + ((long long)o << (2 * d));
+  for (int i = tid; i < KP; i += nt) dst[i] = sT[i];
+  if (!mf.hub) return;
+  // the hub's operand by preparation at its inputs: Q(s) = Tr[E(rho_s) ...]
+  // = (T_I + T_Z)/2, (T_I - T_Z)/2, (T_I + T_X)/2, (T_I + T_Y)/2
+  for (int j = 0; j < d; ++j) {
+    if (!((inmask >> j) & 1)) continue;
+    __syncthreads();
+    const int st = 1 << (2 * j);
+    for (int g = tid; g < KP / 4; g += nt) {
+      const int b = ((g >> (2 * j)) << (2 * j + 2)) | (g & (st - 1));
+      const float tI = sT[b], tX = sT[b + st], tY = sT[b + 2 * st], tZ = sT[b + 3 * st];
+      sT[b] = 0.5f * (tI + tZ);
+      sT[b + st] = 0.5f * (tI - tZ);
+      sT[b + 2 * st] = 0.5f * (tI + tX);
+      sT[b + 3 * st] = 0.5f * (tI + tY);
+    }
+  }
+  __syncthreads();
+  const long long Mo = 1ll << F.m;
+  for (int i = tid; i < KP; i += nt) R.TQ[F.T_off + (long long)i * Mo + o] = sT[i];
+}
+
+size_t ml_eig_smem(int d) {
+  const size_t D = 1u << d, N = 2 * D, KP = 1u << (2 * d);
+  return (2 * N * N + KP + 8 * (N / 2)) * sizeof(float);
+}
+size_t ml_rebuild_smem(int d) {
+  const size_t D = 1u << d, N = 2 * D, KP = 1u << (2 * d);
+  return (N * N + N + 2 * D * D + KP + N) * sizeof(float);
+}
+
+cudaError_t launch_ml_correct(const DevPlan& p, const DevRes& r, const MlFrag* d_frags, int n_frags,
+                              const MlGroup* groups, int n_groups, float* scratch, double* theta, cudaStream_t s) {
+  cudaError_t err;
+  for (int g = 0; g < n_groups; ++g) {
+    const MlGroup& G = groups[g];
+    const size_t sm = ml_eig_smem(G.d);
+    if ((err = cudaFuncSetAttribute(ml_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) !=
+        cudaSuccess)
+      return err;
+    const int threads = G.d >= 4 ? 256 : 64;
+    ml_eig_kernel<<<(unsigned)G.blocks, threads, sm, s>>>(p, r, d_frags + G.first, G.count, G.d, scratch);
+    note_launch();
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  }
+  ml_threshold_kernel<<<n_frags, 256, 0, s>>>(p, d_frags, scratch, theta);
+  note_launch();
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  for (int g = 0; g < n_groups; ++g) {
+    const MlGroup& G = groups[g];
+    const size_t sm = ml_rebuild_smem(G.d);
+    if ((err = cudaFuncSetAttribute(ml_rebuild_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) !=
+        cudaSuccess)
+      return err;
+    const int threads = G.d >= 4 ? 256 : 64;
+    ml_rebuild_kernel<<<(unsigned)G.blocks, threads, sm, s>>>(p, r, d_frags + G.first, G.count, G.d, scratch,
+                                                               theta);
+    note_launch();
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace ccs
