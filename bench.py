@@ -705,6 +705,25 @@ def run_ours(args, rank, world, local_rank):
                             "variants_per_s": n_cliff_var * k2 * world / ts,
                             "mode": "Clifford-specific stitching (exact; no shots; zero Pauli rows skipped)"}
         del res_s
+        # maximum-likelihood correction of the sampled fragment models (Sec. V-C)
+        # between evaluation and contraction, on the same result
+        wide = max(i["n_slots"] for i in infos if i["clifford"]) if n_cliff_var else 0
+        if wide > 6:
+            line["ml"] = {"unsupported": f"a Clifford fragment with {wide} cut slots (the correction takes <= 6)"}
+        elif n_cliff_var:
+            def ml_step():
+                ccs.ccs_eval_variants(ctx, plan, use_graph=graph, res=res, **ev)
+                ccs.ccs_ml_correct(ctx, plan, res)
+                ccs.ccs_recombine(ctx, plan, res, precision=ccs.CCS_FP32, marginal_out=marg, zexp_out=zexp,
+                                  use_graph=graph)
+
+            for _ in range(2):
+                ml_step()
+            tm = max_over_ranks(timed(ml_step, k2), dist, device="cuda")
+            line["ml"] = {"ms_per_step": 1e3 * tm / k2, "circuits_per_s": world * len(ws) * k2 / tm,
+                          "value": units_per_step * k2 * world / tm,
+                          "form": "sampled evaluation, maximum-likelihood correction of the Clifford fragment "
+                                  "models, FP32 contraction"}
         ev_p = dict(ev, per_variant_body=True)
         res_p = ccs.ccs_eval_variants(ctx, plan, **ev_p)
 

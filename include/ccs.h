@@ -317,11 +317,11 @@ int ccs_recombine_noalloc(ccs_ctx ctx, ccs_plan plan, ccs_res res, int precision
  * Afterwards ccs_recombine contracts the corrected models, ccs_get_tensor
  * returns them (hubs included) and ccs_get_operand the corrected operands
  * (FP32); the next ccs_eval_variants replaces them with raw data again.
- * Eigendecompositions run in FP32 (cyclic Jacobi), one CTA per block.
+ * Eigendecompositions run in complex64 (cyclic Jacobi), one CTA per block.
  * Asynchronous on the context stream.  Errors: INVALID_ARG (bad arguments,
  * a CCS_STITCH result), UNSUPPORTED (a selected fragment with more than 6
- * cut slots; a host-only context), OOM (its scratch: 4 (N + N^2) bytes per
- * block, N = 2^(d+1)), CUDA. */
+ * cut slots; a host-only context), OOM (its scratch: 4 D + 8 D^2 bytes per
+ * block, D = 2^d), CUDA. */
 int ccs_ml_correct(ccs_ctx ctx, ccs_plan plan, ccs_res res, int which);
 
 /* --- learned cut scorer ------------------------------------------------------ */

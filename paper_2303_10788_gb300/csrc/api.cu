@@ -1791,7 +1791,7 @@ int ccs_ml_correct(ccs_ctx c, ccs_plan p, ccs_res r, int which) {
           if (F.n_slots > kMlMaxSlots)
             return fail(c, CCS_ERR_UNSUPPORTED, "maximum-likelihood correction supports at most 6 cut slots per fragment");
           if (F.n_slots != dd) continue;
-          const long long nb = 1ll << F.m, N = 2ll << dd;
+          const long long nb = 1ll << F.m, Dm = 1ll << dd;
           MlFrag mf{};
           mf.frag = g;
           mf.d = dd;
@@ -1801,10 +1801,10 @@ int ccs_ml_correct(ccs_ctx c, ccs_plan p, ccs_res r, int which) {
           mf.index = (int)recs.size();
           mf.blk0 = G.blocks;
           mf.ev_off = floats;
-          floats += nb * N;
+          floats += nb * Dm;
           mf.vec_off = floats;
-          floats += nb * N * N;
-          mf.total = 2.0 * (double)(1ll << F.qin);
+          floats += nb * 2 * Dm * Dm;   // complex64 eigenvectors
+          mf.total = (double)(1ll << F.qin);
           recs.push_back(mf);
           G.blocks += nb;
           ++G.count;

@@ -235,14 +235,14 @@ cudaError_t launch_fold(const DevPlan& p, const DevRes& r, const EvalParams& e, 
 // form a group (one launch of the per-block kernels).
 struct MlFrag {
   int frag;                // FragDev index
-  int d;                   // cut slots (the Choi block's real embedding has N = 2^(d+1) rows)
+  int d;                   // cut slots (the Choi block has D = 2^d rows)
   int hub;                 // 1: a star hub (its operand Q^T is read and rewritten as well)
   int i16;                 // the hub operand holds int16 count sums (value = sum x hub_scale)
   int index;               // position in the launch's record list (its threshold)
   long long blk0;          // first block (outcome 0) of the fragment within its group
-  long long ev_off;        // float index of its 2^m x N eigenvalues in the scratch
-  long long vec_off;       // float index of its 2^m x N x N eigenvector entries in the scratch
-  double total;            // trace of the doubled eigenvalue list: 2 x 2^qin
+  long long ev_off;        // float index of its 2^m x D eigenvalues in the scratch
+  long long vec_off;       // float index of its 2^m x D x D complex64 eigenvector entries
+  double total;            // the eigenvalues' sum after the correction: 2^qin
 };
 struct MlGroup {
   int d, first, count;     // cut slots; range of MlFrag records

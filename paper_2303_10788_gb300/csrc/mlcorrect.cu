@@ -16,16 +16,18 @@
 // GPU form, three launches per group of fragments with the same d (d <= 6):
 //  1. ml_eig_kernel, one CTA per (fragment, outcome): the block's T_f row
 //     (a star hub's operand is stored by preparation at its inputs and is
-//     turned into Pauli digits first), the Choi block J_o as its real
-//     embedding [[Re J, -Im J], [Im J, Re J]] (N = 2^(d+1) rows: the same
-//     eigenvalues, each twice), and a cyclic Jacobi eigendecomposition in
-//     shared memory: N/2 disjoint rotations per round in the round-robin
-//     order, N - 1 rounds per sweep, sweeps until no rotation is left above
-//     2^-24 of the block's Frobenius norm (at most kMlMaxSweeps).  The
-//     eigenvalues and eigenvectors go to a scratch array.
+//     turned into Pauli digits first), the Choi block J_o (D = 2^d rows,
+//     complex64, rows padded to D + 1 so that row and column sweeps are free
+//     of bank conflicts), and a cyclic complex Jacobi eigendecomposition in
+//     shared memory: D/2 disjoint rotations per round in the round-robin
+//     order, D - 1 rounds per sweep, sweeps until no rotation is left above
+//     2^-24 of the block's Frobenius norm (at most kMlMaxSweeps).  Each
+//     rotation is a phase that makes the pair's off-diagonal entry real
+//     followed by the real symmetric 2 x 2 Schur rotation (Golub & Van Loan,
+//     Sec. 8.5).  The eigenvalues and eigenvectors go to a scratch array.
 //  2. ml_threshold_kernel, one CTA per fragment: the threshold theta with
-//     sum max(lambda - theta, 0) = 2 x 2^{q_in} over the doubled eigenvalue
-//     list, by Michelot's finite algorithm (J. Optim. Theory Appl. 50, 1986):
+//     sum max(lambda - theta, 0) = 2^{q_in} over its eigenvalue list, by
+//     Michelot's finite algorithm (J. Optim. Theory Appl. 50, 1986):
 //     theta = (sum of the kept values - total) / (their count), keep the
 //     values above theta, repeat until the kept set stops changing.
 //  3. ml_rebuild_kernel, one CTA per (fragment, outcome): J'_o from the
@@ -89,21 +91,15 @@ __device__ __forceinline__ unsigned input_mask(const FragDev& F) {
 }  // namespace
 
 // One CTA per (fragment, outcome o) of a group with d cut slots.
-__global__ void __launch_bounds__(256) ml_eig_kernel(DevPlan P, DevRes R, const MlFrag* __restrict__ fr, int nfr,
-                                                     int d, float* __restrict__ scratch) {
-  extern __shared__ float sm[];
-  const int D = 1 << d, N = 2 * D, KP = 1 << (2 * d), H = N / 2;
-  float* M = sm;                 // N x N
-  float* V = M + N * N;          // N x N
-  float* sT = V + N * N;         // the block's T_f row (4^d)
-  float* rc = sT + KP;           // per pair of the round: cosine, sine, tangent,
-  float* rs = rc + H;            // and the pair's entries before the rotation
-  float* rt = rs + H;
-  float* rpp = rt + H;
-  float* rqq = rpp + H;
-  float* rpq = rqq + H;
-  int* rp = reinterpret_cast<int*>(rpq + H);
-  int* rq = rp + H;
+__global__ void __launch_bounds__(256, 3) ml_eig_kernel(DevPlan P, DevRes R, const MlFrag* __restrict__ fr,
+                                                        int nfr, int d, float* __restrict__ scratch) {
+  extern __shared__ float2 smc[];
+  const int D = 1 << d, LD = D + 1, KP = 1 << (2 * d), H = D / 2;
+  float2* A = smc;               // D x LD: the Choi block, then its rotations
+  float2* V = A + D * LD;        // D x LD: the accumulated unitary
+  float* sT = reinterpret_cast<float*>(V);   // the block's T_f row (4^d), before V is set up
+  float* prm = reinterpret_cast<float*>(V + D * LD);   // per pair: c, s, t, w (2), a_pp, a_qq, |a_pq|
+  int* pq = reinterpret_cast<int*>(prm + 8 * H);       // per pair: p, q
   __shared__ float red[32];
   __shared__ int any_rot;
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -145,7 +141,7 @@ __global__ void __launch_bounds__(256) ml_eig_kernel(DevPlan P, DevRes R, const 
   __syncthreads();
 
   // 2. J_o[r][c] = 2^-d sum over the 2^d Paulis whose slot operator is
-  //    nonzero at [r][c]; its real embedding and V = identity
+  //    nonzero at [r][c]
   const float scale = 1.f / (float)D;
   float nrm = 0.f;
   for (int e = tid; e < D * D; e += nt) {
@@ -167,74 +163,90 @@ __global__ void __launch_bounds__(256) ml_eig_kernel(DevPlan P, DevRes R, const 
     }
     re *= scale;
     im *= scale;
-    M[r * N + c] = re;
-    M[(r + D) * N + c + D] = re;
-    M[(r + D) * N + c] = im;
-    M[r * N + c + D] = -im;
-    nrm += 2.f * (re * re + im * im);
+    A[r * LD + c] = make_float2(re, im);
+    nrm += re * re + im * im;
   }
-  for (int e = tid; e < N * N; e += nt) V[e] = (e / N == e % N) ? 1.f : 0.f;
-  nrm = block_sum(nrm, red);
+  nrm = block_sum(nrm, red);     // its barriers also end the reads of sT
+  for (int e = tid; e < D * D; e += nt) {
+    const int r = e >> d, c = e & (D - 1);
+    V[r * LD + c] = make_float2(r == c ? 1.f : 0.f, 0.f);
+  }
   const float tol = sqrtf(nrm) * 5.9604645e-8f;   // 2^-24 of the Frobenius norm
 
-  // 3. cyclic Jacobi, round-robin pairs: round t pairs (N-1, t) and
-  //    ((t + i) mod (N-1), (t - i) mod (N-1)) for i = 1 .. N/2 - 1
-  if (nrm > 0.f) {
+  // 3. cyclic Jacobi, round-robin pairs: round t pairs (D-1, t) and
+  //    ((t + i) mod (D-1), (t - i) mod (D-1)) for i = 1 .. D/2 - 1.  With
+  //    a_pq = |a_pq| w, the rotation U = [[c, s], [-s conj(w), c conj(w)]]
+  //    on columns (p, q) zeroes a_pq: rows become c row_p - s w row_q and
+  //    s row_p + c w row_q, columns c col_p - s conj(w) col_q and
+  //    s col_p + c conj(w) col_q, and the pair's diagonal a_pp - t |a_pq|,
+  //    a_qq + t |a_pq|.
+  if (nrm > 0.f && D > 1) {
     for (int sweep = 0; sweep < kMlMaxSweeps; ++sweep) {
       if (tid == 0) any_rot = 0;
       __syncthreads();
-      for (int t = 0; t < N - 1; ++t) {
+      for (int t = 0; t < D - 1; ++t) {
         if (tid < H) {
           int a, b;
-          if (tid == 0) { a = N - 1; b = t; }
-          else { a = (t + tid) % (N - 1); b = (t - tid + N - 1) % (N - 1); }
+          if (tid == 0) { a = D - 1; b = t; }
+          else { a = (t + tid) % (D - 1); b = (t - tid + D - 1) % (D - 1); }
           const int p = min(a, b), q = max(a, b);
-          const float app = M[p * N + p], aqq = M[q * N + q], apq = M[p * N + q];
-          float c = 1.f, s = 0.f, tt = 0.f;
-          if (fabsf(apq) > tol) {   // Golub & Van Loan's symmetric Schur 2x2 rotation
-            const float tau = (aqq - app) / (2.f * apq);
+          const float app = A[p * LD + p].x, aqq = A[q * LD + q].x;
+          const float2 apq = A[p * LD + q];
+          const float mag = sqrtf(apq.x * apq.x + apq.y * apq.y);
+          float c = 1.f, s = 0.f, tt = 0.f, wr = 1.f, wi = 0.f;
+          if (mag > tol) {
+            const float tau = (aqq - app) / (2.f * mag);
             tt = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
             c = 1.f / sqrtf(1.f + tt * tt);
             s = tt * c;
+            wr = apq.x / mag;
+            wi = apq.y / mag;
             if (tt != 0.f) any_rot = 1;
           }
-          rp[tid] = p; rq[tid] = q;
-          rc[tid] = c; rs[tid] = s; rt[tid] = tt;
-          rpp[tid] = app; rqq[tid] = aqq; rpq[tid] = apq;
+          float* pr = prm + 8 * tid;
+          pr[0] = c; pr[1] = s; pr[2] = tt; pr[3] = wr; pr[4] = wi; pr[5] = app; pr[6] = aqq; pr[7] = mag;
+          pq[2 * tid] = p;
+          pq[2 * tid + 1] = q;
         }
         __syncthreads();
-        // rows p, q <- J^T M (consecutive threads along a row)
-        for (int w = tid; w < H * N; w += nt) {
-          const int i = w / N, k = w - i * N;
-          if (rt[i] == 0.f) continue;
-          const int p = rp[i], q = rq[i];
-          const float c = rc[i], s = rs[i];
-          const float mp = M[p * N + k], mq = M[q * N + k];
-          M[p * N + k] = c * mp - s * mq;
-          M[q * N + k] = s * mp + c * mq;
+        // rows p, q <- U^H A (consecutive threads along a row)
+        for (int w = tid; w < H * D; w += nt) {
+          const int i = w >> d, k = w & (D - 1);
+          const float* pr = prm + 8 * i;
+          if (pr[2] == 0.f) continue;
+          const int p = pq[2 * i], q = pq[2 * i + 1];
+          const float c = pr[0], s = pr[1], wr = pr[3], wi = pr[4];
+          const float2 xp = A[p * LD + k], xq = A[q * LD + k];
+          const float2 wq = make_float2(wr * xq.x - wi * xq.y, wr * xq.y + wi * xq.x);   // w a_qk
+          A[p * LD + k] = make_float2(c * xp.x - s * wq.x, c * xp.y - s * wq.y);
+          A[q * LD + k] = make_float2(s * xp.x + c * wq.x, s * xp.y + c * wq.y);
         }
         __syncthreads();
-        // columns p, q <- M J, and V <- V J (consecutive threads across pairs);
-        // the 2 x 2 block gets its exact rotated values
-        for (int w = tid; w < H * N; w += nt) {
-          const int k = w / H, i = w - k * H;
-          if (rt[i] == 0.f) continue;
-          const int p = rp[i], q = rq[i];
-          const float c = rc[i], s = rs[i];
+        // columns p, q <- A U and V <- V U (consecutive threads down a
+        // column: the padded row stride spreads them over the banks); the
+        // pair's 2 x 2 block gets its exact rotated values
+        for (int w = tid; w < H * D; w += nt) {
+          const int i = w >> d, k = w & (D - 1);
+          const float* pr = prm + 8 * i;
+          if (pr[2] == 0.f) continue;
+          const int p = pq[2 * i], q = pq[2 * i + 1];
+          const float c = pr[0], s = pr[1], wr = pr[3], wi = -pr[4];   // conj(w)
           if (k == p) {
-            M[p * N + p] = rpp[i] - rt[i] * rpq[i];
-            M[p * N + q] = 0.f;
+            A[p * LD + p] = make_float2(pr[5] - pr[2] * pr[7], 0.f);
+            A[p * LD + q] = make_float2(0.f, 0.f);
           } else if (k == q) {
-            M[q * N + q] = rqq[i] + rt[i] * rpq[i];
-            M[q * N + p] = 0.f;
+            A[q * LD + q] = make_float2(pr[6] + pr[2] * pr[7], 0.f);
+            A[q * LD + p] = make_float2(0.f, 0.f);
           } else {
-            const float mp = M[k * N + p], mq = M[k * N + q];
-            M[k * N + p] = c * mp - s * mq;
-            M[k * N + q] = s * mp + c * mq;
+            const float2 xp = A[k * LD + p], xq = A[k * LD + q];
+            const float2 wq = make_float2(wr * xq.x - wi * xq.y, wr * xq.y + wi * xq.x);
+            A[k * LD + p] = make_float2(c * xp.x - s * wq.x, c * xp.y - s * wq.y);
+            A[k * LD + q] = make_float2(s * xp.x + c * wq.x, s * xp.y + c * wq.y);
           }
-          const float vp = V[k * N + p], vq = V[k * N + q];
-          V[k * N + p] = c * vp - s * vq;
-          V[k * N + q] = s * vp + c * vq;
+          const float2 vp = V[k * LD + p], vq = V[k * LD + q];
+          const float2 wv = make_float2(wr * vq.x - wi * vq.y, wr * vq.y + wi * vq.x);
+          V[k * LD + p] = make_float2(c * vp.x - s * wv.x, c * vp.y - s * wv.y);
+          V[k * LD + q] = make_float2(s * vp.x + c * wv.x, s * vp.y + c * wv.y);
         }
         __syncthreads();
       }
@@ -243,15 +255,17 @@ __global__ void __launch_bounds__(256) ml_eig_kernel(DevPlan P, DevRes R, const 
       if (!more) break;
     }
   }
+  __syncthreads();
 
-  // 4. eigenvalues (the diagonal) and eigenvectors (the columns of V)
-  float* ev = scratch + mf.ev_off + (long long)o * N;
-  float* vec = scratch + mf.vec_off + (long long)o * N * N;
-  for (int i = tid; i < N; i += nt) ev[i] = M[i * N + i];
-  for (int e = tid; e < N * N; e += nt) vec[e] = V[e];
+  // 4. eigenvalues (the real diagonal) and eigenvectors (the columns of V,
+  //    stored row-major D x D complex)
+  float* ev = scratch + mf.ev_off + (long long)o * D;
+  float2* vec = reinterpret_cast<float2*>(scratch + mf.vec_off) + (long long)o * D * D;
+  for (int i = tid; i < D; i += nt) ev[i] = A[i * LD + i].x;
+  for (int e = tid; e < D * D; e += nt) vec[e] = V[(e >> d) * LD + (e & (D - 1))];
 }
 
-// One CTA per fragment: theta over its doubled eigenvalue list.
+// One CTA per fragment: theta over its eigenvalue list.
 __global__ void __launch_bounds__(256) ml_threshold_kernel(DevPlan P, const MlFrag* __restrict__ fr,
                                                            const float* __restrict__ scratch,
                                                            double* __restrict__ theta_out) {
@@ -259,7 +273,7 @@ __global__ void __launch_bounds__(256) ml_threshold_kernel(DevPlan P, const MlFr
   __shared__ long long redc[32];
   const MlFrag& mf = fr[blockIdx.x];
   const FragDev& F = P.frags[mf.frag];
-  const long long n = (1ll << F.m) * (2ll << mf.d);
+  const long long n = (1ll << F.m) << mf.d;
   const float* ev = scratch + mf.ev_off;
   double theta = -1e300;
   long long prev = -1;
@@ -286,54 +300,47 @@ __global__ void __launch_bounds__(256) ml_threshold_kernel(DevPlan P, const MlFr
 __global__ void __launch_bounds__(256) ml_rebuild_kernel(DevPlan P, DevRes R, const MlFrag* __restrict__ fr,
                                                          int nfr, int d, const float* __restrict__ scratch,
                                                          const double* __restrict__ theta) {
-  extern __shared__ float sm[];
-  const int D = 1 << d, N = 2 * D, KP = 1 << (2 * d);
-  float* V = sm;                 // N x N
-  float* lam = V + N * N;        // N clipped eigenvalues
-  float* Are = lam + N;          // D x D: Re J'
-  float* Aim = Are + D * D;      // D x D: Im J'
-  float* sT = Aim + D * D;       // 4^d
-  int* live = reinterpret_cast<int*>(sT + KP);   // indices of the nonzero eigenvalues
+  extern __shared__ float2 smc[];
+  const int D = 1 << d, LD = D + 1, KP = 1 << (2 * d);
+  float2* V = smc;               // D x LD eigenvectors (columns)
+  float2* J = V + D * LD;        // D x LD: J'
+  float* lam = reinterpret_cast<float*>(J + D * LD);   // D clipped eigenvalues
+  float* sT = lam + D;           // 4^d
+  int* live = reinterpret_cast<int*>(sT + KP);          // indices of the nonzero eigenvalues
   __shared__ int n_live;
   const int tid = threadIdx.x, nt = blockDim.x;
 
   const long long blk = blockIdx.x;
-  const int fi = ml_find(fr, nfr, blk);
-  const MlFrag& mf = fr[fi];
+  const MlFrag& mf = fr[ml_find(fr, nfr, blk)];
   const FragDev& F = P.frags[mf.frag];
   const int o = (int)(blk - mf.blk0);
   const unsigned inmask = input_mask(F);
   const float th = (float)theta[mf.index];
-  const float* ev = scratch + mf.ev_off + (long long)o * N;
-  const float* vec = scratch + mf.vec_off + (long long)o * N * N;
-  for (int e = tid; e < N * N; e += nt) V[e] = vec[e];
-  for (int i = tid; i < N; i += nt) lam[i] = fmaxf(ev[i] - th, 0.f);
+  const float* ev = scratch + mf.ev_off + (long long)o * D;
+  const float2* vec = reinterpret_cast<const float2*>(scratch + mf.vec_off) + (long long)o * D * D;
+  for (int e = tid; e < D * D; e += nt) V[(e >> d) * LD + (e & (D - 1))] = vec[e];
+  for (int i = tid; i < D; i += nt) lam[i] = fmaxf(ev[i] - th, 0.f);
   __syncthreads();
   if (tid == 0) {
     int k = 0;
-    for (int i = 0; i < N; ++i)
+    for (int i = 0; i < D; ++i)
       if (lam[i] > 0.f) live[k++] = i;
     n_live = k;
   }
   __syncthreads();
   const int nl = n_live;
-  // M' = V diag(lam) V^T; Re J' is its top-left (= bottom-right) block and
-  // Im J' its bottom-left (= minus top-right) block, each taken as the mean
-  // of its two copies
+  // J'[r][c] = sum_k V[r][k] lam_k conj(V[c][k])
   for (int e = tid; e < D * D; e += nt) {
     const int r = e >> d, c = e & (D - 1);
-    float a1 = 0.f, a2 = 0.f, b1 = 0.f, b2 = 0.f;
+    float re = 0.f, im = 0.f;
     for (int t = 0; t < nl; ++t) {
       const int k = live[t];
       const float l = lam[k];
-      const float vr = V[r * N + k], vc = V[c * N + k], vr2 = V[(r + D) * N + k], vc2 = V[(c + D) * N + k];
-      a1 += vr * l * vc;
-      a2 += vr2 * l * vc2;
-      b1 += vr2 * l * vc;
-      b2 += vr * l * vc2;
+      const float2 a = V[r * LD + k], b = V[c * LD + k];
+      re += l * (a.x * b.x + a.y * b.y);
+      im += l * (a.y * b.x - a.x * b.y);
     }
-    Are[e] = 0.5f * (a1 + a2);
-    Aim[e] = 0.5f * (b1 - b2);
+    J[r * LD + c] = make_float2(re, im);
   }
   __syncthreads();
   // T'(P) = Re Tr[S_P J'] = sum_r Re(S_P[r][c] J'[c][r]), c = r xor x(P)
@@ -345,13 +352,12 @@ __global__ void __launch_bounds__(256) ml_rebuild_kernel(DevPlan P, DevRes R, co
     }
     float acc = 0.f;
     for (int r = 0; r < D; ++r) {
-      const int c = r ^ x;
-      const float re = Are[c * D + r], im = Aim[c * D + r];
+      const float2 v = J[(r ^ x) * LD + r];
       switch (slot_entry_phase(Pi, r, d, inmask)) {   // Re(i^pw (re + i im))
-        case 0: acc += re; break;
-        case 1: acc -= im; break;
-        case 2: acc -= re; break;
-        default: acc += im; break;
+        case 0: acc += v.x; break;
+        case 1: acc -= v.y; break;
+        case 2: acc -= v.x; break;
+        default: acc += v.y; break;
       }
     }
     sT[Pi] = acc;
@@ -381,12 +387,14 @@ __global__ void __launch_bounds__(256) ml_rebuild_kernel(DevPlan P, DevRes R, co
 }
 
 size_t ml_eig_smem(int d) {
-  const size_t D = 1u << d, N = 2 * D, KP = 1u << (2 * d);
-  return (2 * N * N + KP + 8 * (N / 2)) * sizeof(float);
+  const size_t D = 1u << d, LD = D + 1, KP = 1u << (2 * d);
+  const size_t v_floats = 2 * D * LD > KP ? 2 * D * LD : KP;   // V shares its space with the T_f row
+  return 2 * D * LD * sizeof(float) + v_floats * sizeof(float) + 8 * (D / 2 + 1) * sizeof(float) +
+         2 * (D / 2 + 1) * sizeof(int);
 }
 size_t ml_rebuild_smem(int d) {
-  const size_t D = 1u << d, N = 2 * D, KP = 1u << (2 * d);
-  return (N * N + N + 2 * D * D + KP + N) * sizeof(float);
+  const size_t D = 1u << d, LD = D + 1, KP = 1u << (2 * d);
+  return (4 * D * LD + D + KP + D) * sizeof(float);
 }
 
 cudaError_t launch_ml_correct(const DevPlan& p, const DevRes& r, const MlFrag* d_frags, int n_frags,
