@@ -579,10 +579,14 @@ def run_ours(args, rank, world, local_rank):
     # buffers, the host waiting for it one step later).  Plans are built on
     # E2E_BUILDERS host threads (each with its own context and stream) up to
     # that many steps ahead of the device, the way a serving loop overlaps
-    # host work with the GPU.
+    # host work with the GPU.  These contexts use the library's own
+    # stream-ordered device allocator (the C ABI default): an allocator that
+    # calls back into Python would serialise the builders on the interpreter
+    # lock.
     import threading
     from concurrent.futures import ThreadPoolExecutor
     packed = ccs.pack_problems(ws_in)
+    ectx = ccs.ccs_create(local_rank, torch_allocator=False)
     tls, ctxs = threading.local(), []
 
     def build():
@@ -591,7 +595,7 @@ def run_ours(args, rank, world, local_rank):
             # plan uploads never wait for the evaluation on the main stream)
             tls.stream = torch.cuda.Stream(local_rank)
             torch.cuda.set_stream(tls.stream)
-            tls.ctx = ccs.ccs_create(local_rank)
+            tls.ctx = ccs.ccs_create(local_rank, torch_allocator=False)
             ctxs.append(tls.ctx)
         return ccs.ccs_build_fragments(tls.ctx, packed)
 
@@ -629,8 +633,8 @@ def run_ours(args, rank, world, local_rank):
             p2 = futs.pop(0).result()
             if i + depth < args.steps:
                 futs.append(ex.submit(build))
-            r2 = ccs.ccs_eval_variants(ctx, p2, autotune=tune, **ev)
-            ccs.ccs_recombine(ctx, p2, r2, precision=prec, marginal_out=dev_out[k][0], zexp_out=dev_out[k][1])
+            r2 = ccs.ccs_eval_variants(ectx, p2, autotune=tune, **ev)
+            ccs.ccs_recombine(ectx, p2, r2, precision=prec, marginal_out=dev_out[k][0], zexp_out=dev_out[k][1])
             host_out[k][0].copy_(dev_out[k][0], non_blocking=True)
             host_out[k][1].copy_(dev_out[k][1], non_blocking=True)
             done[k].record()
@@ -675,7 +679,8 @@ def run_ours(args, rank, world, local_rank):
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "pipeline": f"plans built on {E2E_BUILDERS} host threads up to {E2E_BUILDERS} steps ahead "
                                 "of the device; each step's result read back to pinned host memory "
-                                "asynchronously and waited for one step later"},
+                                "asynchronously and waited for one step later; contexts on the library's "
+                                "stream-ordered allocator"},
             "gpu_launches": launches, "clocks": clocks}
 
     # --- the same run's other forms: BF16 tensor-core contraction, plain GPU form

@@ -162,6 +162,10 @@ typedef struct {
  * upload, not for other work on the context's stream. */
 int ccs_build_fragments(ccs_ctx ctx, const ccs_problem* problems, int n_problems,
                         const ccs_cut_opts* opts, ccs_plan* out);
+/* Free a plan.  Its device memory goes back to the allocator of the context
+ * that built it, on that context's stream (stream-ordered with the default
+ * allocator): work that reads the plan on other streams must be complete
+ * first. */
 void ccs_plan_free(ccs_plan plan);
 
 /* Candidate cut sets of one problem from the cut search (its cuts field is
@@ -228,6 +232,7 @@ typedef struct {
  * buffers are reused (same plan only).  The call is asynchronous on the
  * context stream; getters synchronise. */
 int ccs_eval_variants(ccs_ctx ctx, ccs_plan plan, const ccs_eval_opts* opts, ccs_res* res);
+/* Free a result (its device memory goes back on the context's stream). */
 void ccs_res_free(ccs_res res);
 /* Launch shape in use for a result (after autotuning, if any): threads per
  * tableau CTA, 64-row words of one fused op per thread, shots per sampling

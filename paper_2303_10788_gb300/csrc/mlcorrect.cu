@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(256, 3) ml_eig_kernel(DevPlan P, DevRes R, con
   extern __shared__ float2 smc[];
   const int D = 1 << d, LD = D + 1, KP = 1 << (2 * d), H = D / 2;
   float2* A = smc;               // D x LD: the Choi block, then its rotations
-  float2* V = A + D * LD;        // D x LD: the accumulated unitary
+  float2* V = A + D * LD;        // D x LD: the accumulated unitary, transposed (row k = column k of V)
   float* sT = reinterpret_cast<float*>(V);   // the block's T_f row (4^d), before V is set up
   float* prm = reinterpret_cast<float*>(V + D * LD);   // per pair: c, s, t, w (2), a_pp, a_qq, |a_pq|
   int* pq = reinterpret_cast<int*>(prm + 8 * H);       // per pair: p, q
@@ -176,11 +176,16 @@ __global__ void __launch_bounds__(256, 3) ml_eig_kernel(DevPlan P, DevRes R, con
   // 3. cyclic Jacobi, round-robin pairs: round t pairs (D-1, t) and
   //    ((t + i) mod (D-1), (t - i) mod (D-1)) for i = 1 .. D/2 - 1.  With
   //    a_pq = |a_pq| w, the rotation U = [[c, s], [-s conj(w), c conj(w)]]
-  //    on columns (p, q) zeroes a_pq: rows become c row_p - s w row_q and
-  //    s row_p + c w row_q, columns c col_p - s conj(w) col_q and
-  //    s col_p + c conj(w) col_q, and the pair's diagonal a_pp - t |a_pq|,
-  //    a_qq + t |a_pq|.
+  //    on columns (p, q) zeroes a_pq and leaves a_pp - t |a_pq|,
+  //    a_qq + t |a_pq| on the diagonal.  All of a round's rotations are
+  //    applied at once, A <- U^H A U block by block: the 2 x 2 block of pairs
+  //    (i, j), i < j, becomes U_i^H B U_j and its mirror block the conjugate
+  //    transpose (so A stays exactly Hermitian); V^T's rows p, q take the
+  //    column update of V <- V U.
   if (nrm > 0.f && D > 1) {
+    const int nblk = H * (H + 1) / 2;
+    const int lg_tpp = max(0, (31 - __clz(nt)) - (d - 1));   // threads per pair in the V^T update
+    const int vi = tid >> lg_tpp, vl = tid & ((1 << lg_tpp) - 1);
     for (int sweep = 0; sweep < kMlMaxSweeps; ++sweep) {
       if (tid == 0) any_rot = 0;
       __syncthreads();
@@ -209,44 +214,65 @@ __global__ void __launch_bounds__(256, 3) ml_eig_kernel(DevPlan P, DevRes R, con
           pq[2 * tid + 1] = q;
         }
         __syncthreads();
-        // rows p, q <- U^H A (consecutive threads along a row)
-        for (int w = tid; w < H * D; w += nt) {
-          const int i = w >> d, k = w & (D - 1);
-          const float* pr = prm + 8 * i;
-          if (pr[2] == 0.f) continue;
+        // A: one 2 x 2 block per pair of pairs (i <= j)
+        for (int e = tid; e < nblk; e += nt) {
+          int j = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+          while (j * (j + 1) / 2 > e) --j;
+          while ((j + 1) * (j + 2) / 2 <= e) ++j;
+          const int i = e - j * (j + 1) / 2;
+          const float* pi_ = prm + 8 * i;
+          const float* pj_ = prm + 8 * j;
+          const bool ri = pi_[2] != 0.f, rj = pj_[2] != 0.f;
+          if (!ri && !rj) continue;
           const int p = pq[2 * i], q = pq[2 * i + 1];
-          const float c = pr[0], s = pr[1], wr = pr[3], wi = pr[4];
-          const float2 xp = A[p * LD + k], xq = A[q * LD + k];
-          const float2 wq = make_float2(wr * xq.x - wi * xq.y, wr * xq.y + wi * xq.x);   // w a_qk
-          A[p * LD + k] = make_float2(c * xp.x - s * wq.x, c * xp.y - s * wq.y);
-          A[q * LD + k] = make_float2(s * xp.x + c * wq.x, s * xp.y + c * wq.y);
-        }
-        __syncthreads();
-        // columns p, q <- A U and V <- V U (consecutive threads down a
-        // column: the padded row stride spreads them over the banks); the
-        // pair's 2 x 2 block gets its exact rotated values
-        for (int w = tid; w < H * D; w += nt) {
-          const int i = w >> d, k = w & (D - 1);
-          const float* pr = prm + 8 * i;
-          if (pr[2] == 0.f) continue;
-          const int p = pq[2 * i], q = pq[2 * i + 1];
-          const float c = pr[0], s = pr[1], wr = pr[3], wi = -pr[4];   // conj(w)
-          if (k == p) {
-            A[p * LD + p] = make_float2(pr[5] - pr[2] * pr[7], 0.f);
+          if (i == j) {
+            A[p * LD + p] = make_float2(pi_[5] - pi_[2] * pi_[7], 0.f);
+            A[q * LD + q] = make_float2(pi_[6] + pi_[2] * pi_[7], 0.f);
             A[p * LD + q] = make_float2(0.f, 0.f);
-          } else if (k == q) {
-            A[q * LD + q] = make_float2(pr[6] + pr[2] * pr[7], 0.f);
             A[q * LD + p] = make_float2(0.f, 0.f);
-          } else {
-            const float2 xp = A[k * LD + p], xq = A[k * LD + q];
-            const float2 wq = make_float2(wr * xq.x - wi * xq.y, wr * xq.y + wi * xq.x);
-            A[k * LD + p] = make_float2(c * xp.x - s * wq.x, c * xp.y - s * wq.y);
-            A[k * LD + q] = make_float2(s * xp.x + c * wq.x, s * xp.y + c * wq.y);
+            continue;
           }
-          const float2 vp = V[k * LD + p], vq = V[k * LD + q];
-          const float2 wv = make_float2(wr * vq.x - wi * vq.y, wr * vq.y + wi * vq.x);
-          V[k * LD + p] = make_float2(c * vp.x - s * wv.x, c * vp.y - s * wv.y);
-          V[k * LD + q] = make_float2(s * vp.x + c * wv.x, s * vp.y + c * wv.y);
+          const int u = pq[2 * j], v = pq[2 * j + 1];
+          float2 b00 = A[p * LD + u], b01 = A[p * LD + v], b10 = A[q * LD + u], b11 = A[q * LD + v];
+          if (rj) {   // B <- B U_j: columns c b0 - s conj(w) b1, s b0 + c conj(w) b1
+            const float c = pj_[0], s = pj_[1], wr = pj_[3], wi = -pj_[4];
+            const float2 y0 = make_float2(wr * b01.x - wi * b01.y, wr * b01.y + wi * b01.x);
+            const float2 y1 = make_float2(wr * b11.x - wi * b11.y, wr * b11.y + wi * b11.x);
+            const float2 n00 = make_float2(c * b00.x - s * y0.x, c * b00.y - s * y0.y);
+            const float2 n01 = make_float2(s * b00.x + c * y0.x, s * b00.y + c * y0.y);
+            const float2 n10 = make_float2(c * b10.x - s * y1.x, c * b10.y - s * y1.y);
+            const float2 n11 = make_float2(s * b10.x + c * y1.x, s * b10.y + c * y1.y);
+            b00 = n00; b01 = n01; b10 = n10; b11 = n11;
+          }
+          if (ri) {   // B <- U_i^H B: rows c r0 - s w r1, s r0 + c w r1
+            const float c = pi_[0], s = pi_[1], wr = pi_[3], wi = pi_[4];
+            const float2 y0 = make_float2(wr * b10.x - wi * b10.y, wr * b10.y + wi * b10.x);
+            const float2 y1 = make_float2(wr * b11.x - wi * b11.y, wr * b11.y + wi * b11.x);
+            const float2 n00 = make_float2(c * b00.x - s * y0.x, c * b00.y - s * y0.y);
+            const float2 n01 = make_float2(c * b01.x - s * y1.x, c * b01.y - s * y1.y);
+            const float2 n10 = make_float2(s * b00.x + c * y0.x, s * b00.y + c * y0.y);
+            const float2 n11 = make_float2(s * b01.x + c * y1.x, s * b01.y + c * y1.y);
+            b00 = n00; b01 = n01; b10 = n10; b11 = n11;
+          }
+          A[p * LD + u] = b00; A[p * LD + v] = b01; A[q * LD + u] = b10; A[q * LD + v] = b11;
+          A[u * LD + p] = make_float2(b00.x, -b00.y);
+          A[v * LD + p] = make_float2(b01.x, -b01.y);
+          A[u * LD + q] = make_float2(b10.x, -b10.y);
+          A[v * LD + q] = make_float2(b11.x, -b11.y);
+        }
+        // V^T rows p, q (one pair per group of threads, its rotation in registers)
+        if (vi < H) {
+          const float* pr = prm + 8 * vi;
+          if (pr[2] != 0.f) {
+            const int p = pq[2 * vi], q = pq[2 * vi + 1];
+            const float c = pr[0], s = pr[1], wr = pr[3], wi = -pr[4];
+            for (int r = vl; r < D; r += (1 << lg_tpp)) {
+              const float2 vp = V[p * LD + r], vq = V[q * LD + r];
+              const float2 y = make_float2(wr * vq.x - wi * vq.y, wr * vq.y + wi * vq.x);
+              V[p * LD + r] = make_float2(c * vp.x - s * y.x, c * vp.y - s * y.y);
+              V[q * LD + r] = make_float2(s * vp.x + c * y.x, s * vp.y + c * y.y);
+            }
+          }
         }
         __syncthreads();
       }
@@ -257,8 +283,8 @@ __global__ void __launch_bounds__(256, 3) ml_eig_kernel(DevPlan P, DevRes R, con
   }
   __syncthreads();
 
-  // 4. eigenvalues (the real diagonal) and eigenvectors (the columns of V,
-  //    stored row-major D x D complex)
+  // 4. eigenvalues (the real diagonal) and eigenvectors (the rows of V^T,
+  //    stored row-major D x D complex: entry [k][r] = component r of vector k)
   float* ev = scratch + mf.ev_off + (long long)o * D;
   float2* vec = reinterpret_cast<float2*>(scratch + mf.vec_off) + (long long)o * D * D;
   for (int i = tid; i < D; i += nt) ev[i] = A[i * LD + i].x;
@@ -302,7 +328,7 @@ __global__ void __launch_bounds__(256) ml_rebuild_kernel(DevPlan P, DevRes R, co
                                                          const double* __restrict__ theta) {
   extern __shared__ float2 smc[];
   const int D = 1 << d, LD = D + 1, KP = 1 << (2 * d);
-  float2* V = smc;               // D x LD eigenvectors (columns)
+  float2* V = smc;               // D x LD eigenvectors (row k = vector k)
   float2* J = V + D * LD;        // D x LD: J'
   float* lam = reinterpret_cast<float*>(J + D * LD);   // D clipped eigenvalues
   float* sT = lam + D;           // 4^d
@@ -329,14 +355,14 @@ __global__ void __launch_bounds__(256) ml_rebuild_kernel(DevPlan P, DevRes R, co
   }
   __syncthreads();
   const int nl = n_live;
-  // J'[r][c] = sum_k V[r][k] lam_k conj(V[c][k])
+  // J'[r][c] = sum_k lam_k v_k[r] conj(v_k[c])
   for (int e = tid; e < D * D; e += nt) {
     const int r = e >> d, c = e & (D - 1);
     float re = 0.f, im = 0.f;
     for (int t = 0; t < nl; ++t) {
       const int k = live[t];
       const float l = lam[k];
-      const float2 a = V[r * LD + k], b = V[c * LD + k];
+      const float2 a = V[k * LD + r], b = V[k * LD + c];
       re += l * (a.x * b.x + a.y * b.y);
       im += l * (a.y * b.x - a.x * b.y);
     }
