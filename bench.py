@@ -15,15 +15,18 @@ value   Clifford variant-shots/s, plan resident on the device, one CUDA-graph
         flushed between steps (outside the step events); the FP32
         contraction (the precision gated at 1e-5 against the FP64 oracle).
 e2e     the same metric through the public C ABI from host buffers: plan build
-        (host compile + upload), evaluation, recombination into host memory,
-        every step; plans are built on two host threads up to two steps ahead
-        of the device.
+        (host compile + upload), evaluation, recombination, read-back to host
+        memory, every step; steps are served by eight host worker threads, one
+        step at a time each, on their own contexts and streams.
 plain   the plain GPU form in the same run: per-variant simulation of every
         variant's whole circuit, stream launches, FP32, no tuning.
 bf16    the same steps with the contraction in BF16 on the tensor cores.
 stitched
         the same circuits in the Clifford-specific stitching mode (exact: no
         shots, each hub operand row in closed form, vanishing rows skipped).
+ml      the same sampled steps with the maximum-likelihood correction of the
+        Clifford fragment models between evaluation and contraction (or the
+        reason it does not apply: a fragment with more than 6 cut slots).
 
 With --gpus N (torchrun, or N spawned ranks when started plainly) every rank
 runs its own batch of the workload (other Philox seeds; other circuits for
@@ -372,7 +375,7 @@ def _ncu_traffic(kernel, workload):
     return None
 
 
-E2E_BUILDERS = 4    # host threads building plans ahead of the device in the end-to-end loop
+E2E_WORKERS = 8     # host threads serving end-to-end steps, one step at a time each
 
 
 def stage_kernel(st, precision, tuning=None, ws=None, prob_infos=None):
@@ -575,77 +578,61 @@ def run_ours(args, rank, world, local_rank):
     # the host inputs are the C-ABI problem structs, marshalled once (with
     # the cut search inside the timed build where the workload has no cut
     # set).  Every step builds and uploads its plan, evaluates, recombines
-    # and reads the result back to host memory (asynchronously into pinned
-    # buffers, the host waiting for it one step later).  Plans are built on
-    # E2E_BUILDERS host threads (each with its own context and stream) up to
-    # that many steps ahead of the device, the way a serving loop overlaps
-    # host work with the GPU.  These contexts use the library's own
-    # stream-ordered device allocator (the C ABI default): an allocator that
-    # calls back into Python would serialise the builders on the interpreter
-    # lock.
+    # and reads the result back to pinned host memory.  Steps are served by
+    # E2E_WORKERS host threads, the way a serving frontend takes requests:
+    # each worker runs one step at a time start to finish on its own context
+    # and stream, so host work overlaps across steps and the device work of
+    # different steps may overlap too.  The contexts use the library's own
+    # stream-ordered pool (the C ABI default): an allocator that calls back
+    # into Python would serialise the workers on the interpreter lock.
     import threading
     from concurrent.futures import ThreadPoolExecutor
     packed = ccs.pack_problems(ws_in)
-    ectx = ccs.ccs_create(local_rank, torch_allocator=False)
     tls, ctxs = threading.local(), []
+    nm = sum(1 << len(x.marginal) for x in ws)
+    nzs = max(1, sum(len(x.zstrings) for x in ws))
 
-    def build():
+    def e2e_step(_=None):
         if not hasattr(tls, "ctx"):
-            # each builder on a stream of its own (a non-blocking stream: its
-            # plan uploads never wait for the evaluation on the main stream)
             tls.stream = torch.cuda.Stream(local_rank)
             torch.cuda.set_stream(tls.stream)
             tls.ctx = ccs.ccs_create(local_rank, torch_allocator=False)
             ctxs.append(tls.ctx)
-        return ccs.ccs_build_fragments(tls.ctx, packed)
+            tls.dev = (torch.empty(nm, dtype=torch.float64, device="cuda"),
+                       torch.empty(nzs, dtype=torch.float64, device="cuda"))
+            tls.host = (torch.empty(nm, dtype=torch.float64, pin_memory=True),
+                        torch.empty(nzs, dtype=torch.float64, pin_memory=True))
+            tls.done = torch.cuda.Event()
+        tls.keep = None                                  # the previous step's plan and result
+        p2 = ccs.ccs_build_fragments(tls.ctx, packed)
+        r2 = ccs.ccs_eval_variants(tls.ctx, p2, autotune=tune, **ev)
+        ccs.ccs_recombine(tls.ctx, p2, r2, precision=prec, marginal_out=tls.dev[0], zexp_out=tls.dev[1])
+        tls.host[0].copy_(tls.dev[0], non_blocking=True)
+        tls.host[1].copy_(tls.dev[1], non_blocking=True)
+        tls.done.record(tls.stream)
+        tls.done.synchronize()                           # the step's result is in host memory
+        tls.keep = (p2, r2)
 
-    depth, built = E2E_BUILDERS, []
-    with ThreadPoolExecutor(depth) as ex:
-        gate = threading.Barrier(depth)
+    with ThreadPoolExecutor(E2E_WORKERS) as ex:
+        gate = threading.Barrier(E2E_WORKERS)
 
-        def warm():                                # every builder's context, outside the timed region
-            gate.wait()
-            return build()
+        def on_every_worker(fn):
+            def once():
+                gate.wait()
+                fn()
+            for f in [ex.submit(once) for _ in range(E2E_WORKERS)]:
+                f.result()
 
-        for f in [ex.submit(warm) for _ in range(depth)]:
-            f.result()
-        # two output slots: step i's marginal and Z values go device -> pinned
-        # host memory asynchronously, and the host waits for them one step
-        # later (before the slot is reused), so the next step's launches
-        # overlap this step's device work
-        nm = sum(1 << len(x.marginal) for x in ws)
-        nzs = max(1, sum(len(x.zstrings) for x in ws))
-        dev_out = [(torch.empty(nm, dtype=torch.float64, device="cuda"),
-                    torch.empty(nzs, dtype=torch.float64, device="cuda")) for _ in range(2)]
-        host_out = [(torch.empty(nm, dtype=torch.float64, pin_memory=True),
-                     torch.empty(nzs, dtype=torch.float64, pin_memory=True)) for _ in range(2)]
-        done = [torch.cuda.Event() for _ in range(2)]
-        inflight = [None, None]       # (plan, result) whose outputs occupy the slot
+        on_every_worker(e2e_step)          # contexts, buffers and autotuned shapes, outside the clock
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        futs = [ex.submit(build) for _ in range(min(depth, args.steps))]
-        for i in range(args.steps):
-            k = i % 2
-            if inflight[k] is not None:   # step i-2's result is on the host
-                done[k].synchronize()
-                built.append(inflight[k][0])   # plans are released after the loop, away from the builders
-                inflight[k] = None
-            p2 = futs.pop(0).result()
-            if i + depth < args.steps:
-                futs.append(ex.submit(build))
-            r2 = ccs.ccs_eval_variants(ectx, p2, autotune=tune, **ev)
-            ccs.ccs_recombine(ectx, p2, r2, precision=prec, marginal_out=dev_out[k][0], zexp_out=dev_out[k][1])
-            host_out[k][0].copy_(dev_out[k][0], non_blocking=True)
-            host_out[k][1].copy_(dev_out[k][1], non_blocking=True)
-            done[k].record()
-            inflight[k] = (p2, r2)
-        for k in range(2):
-            if inflight[k] is not None:
-                done[k].synchronize()
-                built.append(inflight[k][0])
-                inflight[k] = None
+        list(ex.map(e2e_step, range(args.steps)))
         e2e_local = (time.perf_counter() - t0) / args.steps
-    del built
+
+        def drop():
+            tls.keep = None
+        on_every_worker(drop)              # plans and results go on their own threads
+    torch.cuda.synchronize()
     e2e_s = max_over_ranks(e2e_local, dist, device="cuda")
     h2d = sum(24 * len(x.circuit.gates) + 8 * len(x.cuts or []) + 4 * len(x.marginal) +
               4 * sum(len(z) + 1 for z in x.zstrings) for x in ws)
@@ -677,10 +664,10 @@ def run_ours(args, rank, world, local_rank):
             "stage_ms": stage, "roofline": roof, "stage_roofline": roofs,
             "e2e": {"value": units_per_step * world / e2e_s, "unit": UNIT, "circuits_per_s": world * len(ws) / e2e_s,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "pipeline": f"plans built on {E2E_BUILDERS} host threads up to {E2E_BUILDERS} steps ahead "
-                                "of the device; each step's result read back to pinned host memory "
-                                "asynchronously and waited for one step later; contexts on the library's "
-                                "stream-ordered allocator"},
+                    "pipeline": f"{E2E_WORKERS} host worker threads, each serving one step at a time "
+                                "(build, upload, evaluation, recombination, read-back to pinned host "
+                                "memory) on its own context and stream; contexts on the library's "
+                                "stream-ordered pool"},
             "gpu_launches": launches, "clocks": clocks}
 
     # --- the same run's other forms: BF16 tensor-core contraction, plain GPU form

@@ -129,7 +129,11 @@ typedef struct {
  * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).
  * device < 0 creates a host-only context: plans can be built and inspected
  * (fragments, cuts, variant counts) without a GPU; ccs_eval_variants and
- * ccs_recombine then return CCS_ERR_UNSUPPORTED. */
+ * ccs_recombine then return CCS_ERR_UNSUPPORTED.  Without an allocator the
+ * context takes device memory from a stream-ordered pool the library keeps
+ * per device (shared by all such contexts): freed memory stays in the pool
+ * for the next plan or result, and ccs_destroy hands the unused part back
+ * to the driver. */
 int ccs_create(ccs_ctx* out, int device, void* cuda_stream, const ccs_allocator* alloc);
 void ccs_destroy(ccs_ctx ctx);
 const char* ccs_last_error(ccs_ctx ctx);

@@ -79,13 +79,41 @@ int cuda_fail(ccs_ctx c, cudaError_t e, const char* where) {
   return fail(c, CCS_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
+// Device memory of contexts created without an allocator: one stream-ordered
+// pool per device shared by them, which keeps freed memory for reuse
+// (release threshold unlimited) instead of handing it back to the driver at
+// every synchronisation as the device's default pool does, so that plans and
+// results made every step reuse their memory.  ccs_destroy trims it.
+constexpr int kMaxPoolDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[kMaxPoolDevices] = {};
+
+cudaMemPool_t lib_pool(int device) {
+  if (device < 0 || device >= kMaxPoolDevices) return nullptr;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_pools[device]) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    cudaMemPool_t pool;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) return nullptr;
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_pools[device] = pool;
+  }
+  return g_pools[device];
+}
+
 void* dalloc(ccs_ctx c, size_t bytes) {
   if (bytes == 0) bytes = 16;
   bytes = (bytes + 255) & ~size_t(255);
   if (!c->own_alloc) return c->alloc.alloc(bytes, (void*)c->stream, c->alloc.user);
   void* p = nullptr;
-  if (cudaMallocAsync(&p, bytes, c->stream) != cudaSuccess) return nullptr;
-  return p;
+  cudaMemPool_t pool = lib_pool(c->device);
+  const cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, bytes, pool, c->stream) : cudaMallocAsync(&p, bytes, c->stream);
+  return e == cudaSuccess ? p : nullptr;
 }
 
 void dfree(ccs_ctx c, void* p, size_t bytes) {
@@ -513,6 +541,10 @@ void ccs_destroy(ccs_ctx c) {
   if (c->side) cudaStreamDestroy(c->side);
   if (c->pinned) cudaFreeHost(c->pinned);
   if (c->upload_ev) cudaEventDestroy(c->upload_ev);
+  if (c->own_alloc && !c->host_only && c->device >= 0 && c->device < kMaxPoolDevices) {
+    std::lock_guard<std::mutex> lk(g_pool_mu);   // hand the pool's unused memory back
+    if (g_pools[c->device]) cudaMemPoolTrimTo(g_pools[c->device], 0);
+  }
   delete c;
 }
 
