@@ -74,6 +74,8 @@ def workloads_for(name, rank=0):
         return [W.config3()]
     if name == "config4":
         return W.config4(256, seed_offset=rank)
+    if name == "config4x16":          # 16 circuits of the same population (profiling captures)
+        return W.config4(16, seed_offset=rank)
     # the paper's own benchmark shapes (Sec. VI-B, 5000 shots per sampled
     # distribution as in Sec. VI-A); cut sets are searched by the library
     if name == "hwea300":
