@@ -150,25 +150,57 @@ void mix_rows(int op, double param, cd* u0, cd* u1, int n) {
   }
 }
 
-// A fused op: statevector fragments keep the gate word (for the unitary);
-// Clifford fragments apply each gate to the op's 16-pattern planes as it
-// arrives, so no word is stored.
-struct Fused {
+// A fused op of a Clifford fragment: each gate is applied to the op's
+// 16-pattern planes as it arrives, so no gate word is stored.
+struct PlaneOp {
   int a, b;                                   // b < 0: one-qubit op
-  std::vector<WordGate> word;                 // statevector fragments only
-  uint32_t px[2] = {kPX0, kPX1}, pz[2] = {kPZ0, kPZ1}, pf = 0;
-  bool dead = false;
-  void add(int op, int ra, int rb, bool planes, double param) {
-    if (planes) chp_planes(op, ra, rb < 0 ? 1 - ra : rb, px, pz, pf);
-    else word.push_back({op, ra, rb, param});
-  }
+  uint32_t px[2], pz[2], pf;
+  bool dead;
+  PlaneOp(int qa, int qb) : a(qa), b(qb), px{kPX0, kPX1}, pz{kPZ0, kPZ1}, pf(0), dead(false) {}
+  void add(int op, int ra, int rb, double) { chp_planes(op, ra, rb < 0 ? 1 - ra : rb, px, pz, pf); }
 };
+// A fused op of a statevector fragment keeps its gate word (for the unitary).
+struct WordOp {
+  int a, b;
+  std::vector<WordGate> word;
+  bool dead = false;
+  WordOp(int qa, int qb) : a(qa), b(qb) {}
+  void add(int op, int ra, int rb, double param) { word.push_back({op, ra, rb, param}); }
+};
+
+// The op made of a trailing one-qubit op on each side (either may be
+// absent) followed by the two-qubit gate's roles.
+inline void absorb(PlaneOp& nf, const PlaneOp* g0, const PlaneOp* g1) {
+  if (!g0 && !g1) return;
+  // A one-qubit op's planes hold its images of the patterns w = 0..3 in
+  // bits 0..3.  Role 0 reads w from bits 0-1 of the two-qubit pattern v
+  // (the 4-bit image repeated in every nibble), role 1 from bits 2-3
+  // (bit k of the image filling nibble k).
+  auto rep = [](uint32_t t) { t &= 0xfu; return t * 0x1111u; };
+  auto spread = [](uint32_t t) {
+    return ((t & 1u) ? 0x000fu : 0u) | ((t & 2u) ? 0x00f0u : 0u) | ((t & 4u) ? 0x0f00u : 0u) |
+           ((t & 8u) ? 0xf000u : 0u);
+  };
+  nf.px[0] = g0 ? rep(g0->px[0]) : kPX0;
+  nf.pz[0] = g0 ? rep(g0->pz[0]) : kPZ0;
+  nf.px[1] = g1 ? spread(g1->px[0]) : kPX1;
+  nf.pz[1] = g1 ? spread(g1->pz[0]) : kPZ1;
+  nf.pf = (g0 ? rep(g0->pf) : 0u) ^ (g1 ? spread(g1->pf) : 0u);
+}
+inline void absorb(WordOp& nf, WordOp* g0, WordOp* g1) {
+  for (int side = 0; side < 2; ++side) {
+    WordOp* g = side == 0 ? g0 : g1;
+    if (!g) continue;
+    for (auto& w : g->word) nf.word.push_back({w.op, side, -1, w.param});
+    g->word.clear();
+  }
+}
 
 // Fuse consecutive gates per qubit (pair) and assign ASAP moments: on return
 // order[start[L] .. start[L+1]) are the live ops of moment L (indices into
 // ops, in creation order).
-void fuse_and_layer(const Frag& f, std::vector<Fused>& ops, bool planes, std::vector<int>& order,
-                    std::vector<int>& start) {
+template <class Op>
+void fuse_and_layer(const Frag& f, std::vector<Op>& ops, std::vector<int>& order, std::vector<int>& start) {
   const int n = f.n();
   std::vector<int> last(n, -1);
   for (size_t gi = 0; gi < f.gates.size(); ++gi) {
@@ -177,59 +209,40 @@ void fuse_and_layer(const Frag& f, std::vector<Fused>& ops, bool planes, std::ve
     const double prm = f.gparam.empty() ? 0.0 : f.gparam[gi];
     if (!is_two_qubit(op)) {
       if (last[a] >= 0) {
-        Fused& F = ops[last[a]];
-        F.add(op, F.a == a ? 0 : 1, -1, planes, prm);
+        Op& F = ops[last[a]];
+        F.add(op, F.a == a ? 0 : 1, -1, prm);
       } else {
-        ops.push_back(Fused{a, -1});
-        ops.back().add(op, 0, -1, planes, prm);
+        ops.emplace_back(a, -1);
+        ops.back().add(op, 0, -1, prm);
         last[a] = (int)ops.size() - 1;
       }
       continue;
     }
-    int la = last[a], lb = last[b];
+    const int la = last[a], lb = last[b];
     if (la >= 0 && la == lb) {
-      Fused& F = ops[la];
-      int ra = F.a == a ? 0 : 1;
-      F.add(op, ra, 1 - ra, planes, 0.0);
+      Op& F = ops[la];
+      const int ra = F.a == a ? 0 : 1;
+      F.add(op, ra, 1 - ra, 0.0);
       continue;
     }
-    Fused nf{a, b};
-    const Fused* g1[2] = {nullptr, nullptr};
+    Op* g1[2] = {nullptr, nullptr};
     for (int side = 0; side < 2; ++side) {
-      int lq = side == 0 ? la : lb;
+      const int lq = side == 0 ? la : lb;
       if (lq >= 0 && ops[lq].b < 0) {     // absorb a trailing one-qubit op
-        if (!planes)
-          for (auto& w : ops[lq].word) nf.word.push_back({w.op, side, -1, w.param});
         g1[side] = &ops[lq];
         ops[lq].dead = true;
       }
     }
-    if (planes && (g1[0] || g1[1])) {   // nf = (g1[0] on role 0) x (g1[1] on role 1), then the gate
-      // A one-qubit op's planes hold its images of the patterns w = 0..3 in
-      // bits 0..3.  Role 0 reads w from bits 0-1 of the two-qubit pattern v
-      // (the 4-bit image repeated in every nibble), role 1 from bits 2-3
-      // (bit k of the image filling nibble k).
-      auto rep = [](uint32_t t) { t &= 0xfu; return t * 0x1111u; };
-      auto spread = [](uint32_t t) {
-        return ((t & 1u) ? 0x000fu : 0u) | ((t & 2u) ? 0x00f0u : 0u) | ((t & 4u) ? 0x0f00u : 0u) |
-               ((t & 8u) ? 0xf000u : 0u);
-      };
-      nf.px[0] = g1[0] ? rep(g1[0]->px[0]) : kPX0;
-      nf.pz[0] = g1[0] ? rep(g1[0]->pz[0]) : kPZ0;
-      nf.px[1] = g1[1] ? spread(g1[1]->px[0]) : kPX1;
-      nf.pz[1] = g1[1] ? spread(g1[1]->pz[0]) : kPZ1;
-      nf.pf = (g1[0] ? rep(g1[0]->pf) : 0u) ^ (g1[1] ? spread(g1[1]->pf) : 0u);
-    }
-    for (int side = 0; side < 2; ++side)
-      if (g1[side]) const_cast<Fused*>(g1[side])->word.clear();
-    nf.add(op, 0, 1, planes, 0.0);
-    ops.push_back(std::move(nf));
+    ops.emplace_back(a, b);                  // capacity reserved: g1 stays valid
+    Op& nf = ops.back();
+    absorb(nf, g1[0], g1[1]);
+    nf.add(op, 0, 1, 0.0);
     last[a] = last[b] = (int)ops.size() - 1;
   }
   std::vector<int> layer_of_q(n, -1), lay(ops.size(), -1);
   int nl = 0;
   for (size_t i = 0; i < ops.size(); ++i) {
-    const Fused& F = ops[i];
+    const Op& F = ops[i];
     if (F.dead) continue;
     int L = layer_of_q[F.a];
     if (F.b >= 0) L = std::max(L, layer_of_q[F.b]);
@@ -291,14 +304,6 @@ int fragment_problem(Problem& p, int pi, std::vector<Frag>& out, std::string& er
   const int n = (int)p.n_qubits;
   const int ng = (int)p.gates.size();
   if (!p.gparam.empty() && (int)p.gparam.size() != ng) { err = "gate exponent list size"; return CCS_ERR_INVALID_ARG; }
-  for (int gi = 0; gi < ng; ++gi) {
-    auto& g = p.gates[gi];
-    if (g[0] < 0 || (g[0] > CCS_ZPOW && g[0] != kOpI)) { err = "unknown gate opcode"; return CCS_ERR_UNSUPPORTED_GATE; }
-    if (g[1] < 0 || g[1] >= n) { err = "gate qubit out of range"; return CCS_ERR_INVALID_ARG; }
-    if (is_two_qubit(g[0]) && (g[2] < 0 || g[2] >= n || g[2] == g[1])) {
-      err = "bad two-qubit gate operands"; return CCS_ERR_INVALID_ARG;
-    }
-  }
   for (auto& c : p.cuts)
     if ((int)c.qubit >= n || (int)c.gate_index > ng) { err = "cut out of range"; return CCS_ERR_INVALID_ARG; }
   std::sort(p.cuts.begin(), p.cuts.end(), [](const ccs_cut& x, const ccs_cut& y) {
@@ -334,10 +339,26 @@ int fragment_problem(Problem& p, int pi, std::vector<Frag>& out, std::string& er
       visit(gi, g, segcur[g[1]], is_two_qubit(g[0]) ? segcur[g[2]] : -1);
     }
   };
+  // first pass: check each gate, join the segments a two-qubit gate touches
+  // and count the gates per segment (a gate belongs to its first operand's)
   UF uf(base[n]);
-  walk([&](int, const std::array<int, 3>&, int sa, int sb) {
-    if (sb >= 0) uf.join(sa, sb);
-  });
+  std::vector<int> seg_gates(base[n], 0);
+  {
+    segcur.assign(base.begin(), base.end() - 1);
+    size_t nc = 0;
+    for (int gi = 0; gi < ng; ++gi) {
+      while (nc < p.cuts.size() && (int)p.cuts[nc].gate_index <= gi) ++segcur[p.cuts[nc++].qubit];
+      const auto& g = p.gates[gi];
+      if (g[0] < 0 || (g[0] > CCS_ZPOW && g[0] != kOpI)) { err = "unknown gate opcode"; return CCS_ERR_UNSUPPORTED_GATE; }
+      if (g[1] < 0 || g[1] >= n) { err = "gate qubit out of range"; return CCS_ERR_INVALID_ARG; }
+      const int sa = segcur[g[1]];
+      ++seg_gates[sa];
+      if (is_two_qubit(g[0])) {
+        if (g[2] < 0 || g[2] >= n || g[2] == g[1]) { err = "bad two-qubit gate operands"; return CCS_ERR_INVALID_ARG; }
+        uf.join(sa, segcur[g[2]]);
+      }
+    }
+  }
   // fragments ordered by first wire; wires by (qubit, segment) = segment id
   std::vector<int> root_to_frag(base[n], -1);
   std::vector<std::pair<int, int>> where(base[n]);
@@ -358,7 +379,7 @@ int fragment_problem(Problem& p, int pi, std::vector<Frag>& out, std::string& er
     }
   {
     std::vector<int> count(out.size() - first, 0);
-    walk([&](int, const std::array<int, 3>&, int sa, int) { count[where[sa].first - first]++; });
+    for (int s = 0; s < base[n]; ++s) count[where[s].first - first] += seg_gates[s];
     for (size_t fi = 0; fi < count.size(); ++fi) {
       out[first + fi].gates.reserve(count[fi]);
       if (!p.gparam.empty()) out[first + fi].gparam.reserve(count[fi]);
@@ -441,8 +462,9 @@ int fragment_problem(Problem& p, int pi, std::vector<Frag>& out, std::string& er
 namespace {
 // Scratch of one host thread, kept between fragments and plan builds (the
 // pool's threads persist), so compiling does not fault in fresh pages.
+template <class Op>
 struct CompileScratch {
-  std::vector<Fused> ops;
+  std::vector<Op> ops;
   std::vector<int> order, start;
   void reset(size_t gates) {
     ops.clear();
@@ -452,9 +474,9 @@ struct CompileScratch {
 }  // namespace
 
 void compile_clifford(Frag& f) {
-  thread_local CompileScratch cs;
+  thread_local CompileScratch<PlaneOp> cs;
   cs.reset(f.gates.size());
-  fuse_and_layer(f, cs.ops, true, cs.order, cs.start);
+  fuse_and_layer(f, cs.ops, cs.order, cs.start);
   const int nl = (int)cs.start.size() - 1;
   f.cops.clear();
   f.cops.reserve(cs.order.size());
@@ -463,7 +485,7 @@ void compile_clifford(Frag& f) {
   const uint16_t dummy = (uint16_t)f.n();
   for (int L = 0; L < nl; ++L) {
     for (int k = cs.start[L]; k < cs.start[L + 1]; ++k) {
-      const Fused& F = cs.ops[cs.order[k]];
+      const PlaneOp& F = cs.ops[cs.order[k]];
       CliffordOp op = clifford_from_planes(F.px, F.pz, F.pf);
       op.qa = (uint16_t)F.a;
       op.qb = F.b >= 0 ? (uint16_t)F.b : dummy;
@@ -474,15 +496,15 @@ void compile_clifford(Frag& f) {
 }
 
 void compile_nc(Frag& f) {
-  thread_local CompileScratch cs;
+  thread_local CompileScratch<WordOp> cs;
   cs.reset(f.gates.size());
-  fuse_and_layer(f, cs.ops, false, cs.order, cs.start);
+  fuse_and_layer(f, cs.ops, cs.order, cs.start);
   const int nl = (int)cs.start.size() - 1;
   f.nops.clear();
   f.moment_start.assign(1, 0);
   for (int L = 0; L < nl; ++L) {
     for (int k = cs.start[L]; k < cs.start[L + 1]; ++k) {
-      const Fused* F = &cs.ops[cs.order[k]];
+      const WordOp* F = &cs.ops[cs.order[k]];
       NCOp o{};
       o.a = F->a;
       o.b = F->b;
