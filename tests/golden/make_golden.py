@@ -9,11 +9,18 @@ with these values; nothing here reads the library.
     python tests/golden/make_golden.py config3 [--procs 8]
     python tests/golden/make_golden.py config4 [--procs 8] [--circuits 0,1,...]
     python tests/golden/make_golden.py exact [--procs 8]
+    python tests/golden/make_golden.py ml [--procs 8]
 
 ``exact`` (after the two above) writes the exact-mode marginals (strong
 simulation, Sec. V-C: each Clifford variant's distribution is 2^-rank on its
 outcome space) of the same circuits from the stored oracle outcome spaces,
 so no tableau is simulated again.
+
+``ml`` (after ``config4``) writes the sampled-mode marginals of the stored
+config-4 circuits with every Clifford fragment's model corrected by maximum
+likelihood (Sec. V-C; ``oracle.mlcorrect``) before the contraction: the
+shot counts are drawn again from the stored outcome spaces with the same
+Philox stream, folded, corrected and contracted.
 
 config3 (500-qubit body, 20736 variants, 2^14 shots, 4^8 cut terms) takes
 about 5 CPU-hours; it is spread over ``--procs`` spawned processes.  Each
@@ -214,6 +221,48 @@ def _c4_exact_one(ci):
     return ci, recombine(frags, tensors, len(cuts), len(w.marginal))
 
 
+def _c4_ml_one(ci):
+    from workloads import config4
+    from oracle import statevector as sv
+    from oracle.cutting import fragment_circuit, fold, recombine
+    from oracle.mlcorrect import ml_correct
+    from oracle.pipeline import sample_counts
+    w = config4(256)[ci]
+    frags, cuts = fragment_circuit(w.circuit, w.cuts, w.marginal)
+    rows = np.load(os.path.join(HERE, "config4_sampled.npz"))[f"spaces_{ci}"]
+    by = {(int(r[0]), int(r[1])): r[2:] for r in rows}
+    tensors = []
+    for fi, fr in enumerate(frags):
+        if fr.clifford:
+            dists = []
+            for v in range(fr.n_variants):
+                row = by[(fi, v)]
+                rank, off = int(row[0]), int(row[1])
+                c = sample_counts(off, [int(b) for b in row[2:2 + rank]], len(fr.A), w.shots, v, fi, ci,
+                                  SEED[0], SEED[1])
+                dists.append(c / float(w.shots))
+            tensors.append(ml_correct(fr, fold(fr, dists))[0])
+        else:
+            dists = [sv.marginal(sv.run(fr.n, fr.variant_gates(v)), fr.n, fr.A) for v in range(fr.n_variants)]
+            tensors.append(fold(fr, dists))
+    return ci, recombine(frags, tensors, len(cuts), len(w.marginal))
+
+
+def make_ml(procs):
+    t0 = time.time()
+    g4 = np.load(os.path.join(HERE, "config4_sampled.npz"))
+    circuits = [int(c) for c in g4["circuits"]]
+    m = {}
+    with mp.get_context("spawn").Pool(procs) as pool:
+        for ci, mc in pool.imap_unordered(_c4_ml_one, circuits):
+            m[ci] = mc
+            print(f"circuit {ci}: {time.time() - t0:.0f} s", flush=True)
+    out = os.path.join(HERE, "ml_marginals.npz")
+    np.savez_compressed(out, config4_circuits=np.array(circuits, np.int64),
+                        config4=np.stack([m[c] for c in circuits]), seed=np.array(SEED, np.uint64))
+    print("wrote", out)
+
+
 def make_exact(procs):
     from oracle import statevector as sv
     from oracle.cutting import fold, recombine
@@ -245,7 +294,7 @@ def make_exact(procs):
 
 if __name__ == "__main__":
     ap = argparse.ArgumentParser()
-    ap.add_argument("which", choices=["config3", "config4", "exact"])
+    ap.add_argument("which", choices=["config3", "config4", "exact", "ml"])
     ap.add_argument("--procs", type=int, default=os.cpu_count() or 1)
     ap.add_argument("--circuits", default="0,1,2,3,4,5,6,7")
     a = ap.parse_args()
@@ -253,5 +302,7 @@ if __name__ == "__main__":
         make_config3(a.procs, out=os.path.join(HERE, "config3_sampled.npz"))
     elif a.which == "config4":
         make_config4(a.procs, [int(c) for c in a.circuits.split(",")])
+    elif a.which == "ml":
+        make_ml(a.procs)
     else:
         make_exact(a.procs)

@@ -13,6 +13,10 @@ variant's canonical outcome space (off, reduced basis).
 Bars: outcome spaces bit-exact; FP32 marginal within 1e-5 absolute (the
 spec bound); the BF16 tensor-core contraction's error against the FP64
 oracle is printed and held under 2e-4 (its operands carry 8 significant bits).
+The same config-4 run with every Clifford fragment's model corrected by
+maximum likelihood (Sec. V-C) before the contraction is held to 1e-5 against
+the oracle's corrected contraction, and no entry of any of the 256 corrected
+marginals is negative.
 """
 import os
 
@@ -26,6 +30,7 @@ pytestmark = pytest.mark.gpu
 HERE = os.path.dirname(os.path.abspath(__file__))
 GOLD3 = os.path.join(HERE, "golden", "config3_sampled.npz")
 GOLD4 = os.path.join(HERE, "golden", "config4_sampled.npz")
+GOLDML = os.path.join(HERE, "golden", "ml_marginals.npz")
 
 
 @pytest.fixture(scope="module")
@@ -92,3 +97,19 @@ def test_config4_default_path_matches_oracle(ctx):
     print(f"config4 circuits {list(g['circuits'])} vs FP64 oracle: max|err| fp32 {worst32:.2e}, bf16 {worst16:.2e}")
     assert worst32 < 1e-5
     assert worst16 < 2e-4
+
+
+def test_config4_ml_correction_matches_oracle(ctx):
+    g = np.load(GOLDML)
+    ws = config4(256)
+    plan, res = _bench_eval(ctx, ws, g["seed"])
+    ccs.ccs_ml_correct(ctx, plan, res, ccs.CCS_ML_SAMPLED)
+    m, _ = ccs.ccs_recombine(ctx, plan, res, precision=ccs.CCS_FP32, use_graph=True)
+    offs = np.concatenate([[0], np.cumsum([1 << len(w.marginal) for w in ws])])
+    worst = 0.0
+    for i, ci in enumerate(g["config4_circuits"]):
+        ci = int(ci)
+        worst = max(worst, np.abs(m[offs[ci]:offs[ci + 1]] - g["config4"][i]).max())
+    print(f"config4 ML-corrected vs FP64 oracle: max|err| {worst:.2e}; min entry over 256 circuits {m.min():.2e}")
+    assert worst < 1e-5
+    assert m.min() > -1e-5
