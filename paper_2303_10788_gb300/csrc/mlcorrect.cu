@@ -65,6 +65,18 @@ __device__ T block_sum(T v, T* red) {
   return s;
 }
 
+// Largest value over the CTA (every thread gets it); red holds 32 entries.
+__device__ float block_max(float v, float* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[w] = v;
+  __syncthreads();
+  float m = 0.f;
+  for (int i = 0; i < nw; ++i) m = fmaxf(m, red[i]);
+  return m;
+}
+
 // Entry [r][c] of the slot operator (x)_j s_j(P_j) for the Pauli digits of P
 // where the entry is nonzero: returns the power of i (0..3) of the entry
 // (its value is i^pw, a sign folded in as 2).  At slot j the entry needs
@@ -93,13 +105,14 @@ __device__ __forceinline__ unsigned input_mask(const FragDev& F) {
 // One CTA per (fragment, outcome o) of a group with d cut slots.
 __global__ void __launch_bounds__(256, 3) ml_eig_kernel(DevPlan P, DevRes R, const MlFrag* __restrict__ fr,
                                                         int nfr, int d, float* __restrict__ scratch) {
-  extern __shared__ float2 smc[];
+  extern __shared__ __align__(16) float2 smc[];
   const int D = 1 << d, LD = D + 1, KP = 1 << (2 * d), H = D / 2;
   float2* A = smc;               // D x LD: the Choi block, then its rotations
   float2* V = A + D * LD;        // D x LD: the accumulated unitary, transposed (row k = column k of V)
   float* sT = reinterpret_cast<float*>(V);   // the block's T_f row (4^d), before V is set up
-  float* prm = reinterpret_cast<float*>(V + D * LD);   // per pair: c, s, t, w (2), a_pp, a_qq, |a_pq|
-  int* pq = reinterpret_cast<int*>(prm + 8 * H);       // per pair: p, q
+  float4* prm = reinterpret_cast<float4*>(V + D * LD);   // per pair: (c, s, t, Re w), (Im w, a_pp, a_qq, |a_pq|)
+  int2* pq = reinterpret_cast<int2*>(prm + 2 * H);        // per pair: p, q
+  int* blk_ij = reinterpret_cast<int*>(pq + H);           // pair blocks i <= j of a round: i | j << 16
   __shared__ float red[32];
   __shared__ int any_rot;
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -172,6 +185,8 @@ __global__ void __launch_bounds__(256, 3) ml_eig_kernel(DevPlan P, DevRes R, con
     V[r * LD + c] = make_float2(r == c ? 1.f : 0.f, 0.f);
   }
   const float tol = sqrtf(nrm) * 5.9604645e-8f;   // 2^-24 of the Frobenius norm
+  for (int j = tid; j < H; j += nt)
+    for (int i = 0; i <= j; ++i) blk_ij[j * (j + 1) / 2 + i] = i | (j << 16);
 
   // 3. cyclic Jacobi, round-robin pairs: round t pairs (D-1, t) and
   //    ((t + i) mod (D-1), (t - i) mod (D-1)) for i = 1 .. D/2 - 1.  With
@@ -208,34 +223,33 @@ __global__ void __launch_bounds__(256, 3) ml_eig_kernel(DevPlan P, DevRes R, con
             wi = apq.y / mag;
             if (tt != 0.f) any_rot = 1;
           }
-          float* pr = prm + 8 * tid;
-          pr[0] = c; pr[1] = s; pr[2] = tt; pr[3] = wr; pr[4] = wi; pr[5] = app; pr[6] = aqq; pr[7] = mag;
-          pq[2 * tid] = p;
-          pq[2 * tid + 1] = q;
+          prm[2 * tid] = make_float4(c, s, tt, wr);
+          prm[2 * tid + 1] = make_float4(wi, app, aqq, mag);
+          pq[tid] = make_int2(p, q);
         }
         __syncthreads();
         // A: one 2 x 2 block per pair of pairs (i <= j)
         for (int e = tid; e < nblk; e += nt) {
-          int j = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
-          while (j * (j + 1) / 2 > e) --j;
-          while ((j + 1) * (j + 2) / 2 <= e) ++j;
-          const int i = e - j * (j + 1) / 2;
-          const float* pi_ = prm + 8 * i;
-          const float* pj_ = prm + 8 * j;
-          const bool ri = pi_[2] != 0.f, rj = pj_[2] != 0.f;
+          const int ij = blk_ij[e], i = ij & 0xffff, j = ij >> 16;
+          const float4 pi0 = prm[2 * i], pj0 = prm[2 * j];
+          const bool ri = pi0.z != 0.f, rj = pj0.z != 0.f;
           if (!ri && !rj) continue;
-          const int p = pq[2 * i], q = pq[2 * i + 1];
+          const float4 pi1 = prm[2 * i + 1];
+          const int2 pqi = pq[i];
+          const int p = pqi.x, q = pqi.y;
           if (i == j) {
-            A[p * LD + p] = make_float2(pi_[5] - pi_[2] * pi_[7], 0.f);
-            A[q * LD + q] = make_float2(pi_[6] + pi_[2] * pi_[7], 0.f);
+            A[p * LD + p] = make_float2(pi1.y - pi0.z * pi1.w, 0.f);
+            A[q * LD + q] = make_float2(pi1.z + pi0.z * pi1.w, 0.f);
             A[p * LD + q] = make_float2(0.f, 0.f);
             A[q * LD + p] = make_float2(0.f, 0.f);
             continue;
           }
-          const int u = pq[2 * j], v = pq[2 * j + 1];
+          const float4 pj1 = prm[2 * j + 1];
+          const int2 pqj = pq[j];
+          const int u = pqj.x, v = pqj.y;
           float2 b00 = A[p * LD + u], b01 = A[p * LD + v], b10 = A[q * LD + u], b11 = A[q * LD + v];
           if (rj) {   // B <- B U_j: columns c b0 - s conj(w) b1, s b0 + c conj(w) b1
-            const float c = pj_[0], s = pj_[1], wr = pj_[3], wi = -pj_[4];
+            const float c = pj0.x, s = pj0.y, wr = pj0.w, wi = -pj1.x;
             const float2 y0 = make_float2(wr * b01.x - wi * b01.y, wr * b01.y + wi * b01.x);
             const float2 y1 = make_float2(wr * b11.x - wi * b11.y, wr * b11.y + wi * b11.x);
             const float2 n00 = make_float2(c * b00.x - s * y0.x, c * b00.y - s * y0.y);
@@ -245,7 +259,7 @@ __global__ void __launch_bounds__(256, 3) ml_eig_kernel(DevPlan P, DevRes R, con
             b00 = n00; b01 = n01; b10 = n10; b11 = n11;
           }
           if (ri) {   // B <- U_i^H B: rows c r0 - s w r1, s r0 + c w r1
-            const float c = pi_[0], s = pi_[1], wr = pi_[3], wi = pi_[4];
+            const float c = pi0.x, s = pi0.y, wr = pi0.w, wi = pi1.x;
             const float2 y0 = make_float2(wr * b10.x - wi * b10.y, wr * b10.y + wi * b10.x);
             const float2 y1 = make_float2(wr * b11.x - wi * b11.y, wr * b11.y + wi * b11.x);
             const float2 n00 = make_float2(c * b00.x - s * y0.x, c * b00.y - s * y0.y);
@@ -262,10 +276,11 @@ __global__ void __launch_bounds__(256, 3) ml_eig_kernel(DevPlan P, DevRes R, con
         }
         // V^T rows p, q (one pair per group of threads, its rotation in registers)
         if (vi < H) {
-          const float* pr = prm + 8 * vi;
-          if (pr[2] != 0.f) {
-            const int p = pq[2 * vi], q = pq[2 * vi + 1];
-            const float c = pr[0], s = pr[1], wr = pr[3], wi = -pr[4];
+          const float4 pr0 = prm[2 * vi];
+          if (pr0.z != 0.f) {
+            const int2 pqv = pq[vi];
+            const int p = pqv.x, q = pqv.y;
+            const float c = pr0.x, s = pr0.y, wr = pr0.w, wi = -prm[2 * vi + 1].x;
             for (int r = vl; r < D; r += (1 << lg_tpp)) {
               const float2 vp = V[p * LD + r], vq = V[q * LD + r];
               const float2 y = make_float2(wr * vq.x - wi * vq.y, wr * vq.y + wi * vq.x);
@@ -276,9 +291,20 @@ __global__ void __launch_bounds__(256, 3) ml_eig_kernel(DevPlan P, DevRes R, con
         }
         __syncthreads();
       }
+      // stop once no off-diagonal entry exceeds the tolerance (the next
+      // sweep would rotate nothing)
+      float off = 0.f;
+      for (int e2 = tid; e2 < D * D; e2 += nt) {
+        const int r = e2 >> d, c = e2 & (D - 1);
+        if (r != c) {
+          const float2 x = A[r * LD + c];
+          off = fmaxf(off, x.x * x.x + x.y * x.y);
+        }
+      }
+      off = block_max(off, red);
       const int more = any_rot;
       __syncthreads();
-      if (!more) break;
+      if (!more || off <= tol * tol) break;
     }
   }
   __syncthreads();
@@ -413,10 +439,10 @@ __global__ void __launch_bounds__(256) ml_rebuild_kernel(DevPlan P, DevRes R, co
 }
 
 size_t ml_eig_smem(int d) {
-  const size_t D = 1u << d, LD = D + 1, KP = 1u << (2 * d);
+  const size_t D = 1u << d, LD = D + 1, KP = 1u << (2 * d), H = D / 2;
   const size_t v_floats = 2 * D * LD > KP ? 2 * D * LD : KP;   // V shares its space with the T_f row
-  return 2 * D * LD * sizeof(float) + v_floats * sizeof(float) + 8 * (D / 2 + 1) * sizeof(float) +
-         2 * (D / 2 + 1) * sizeof(int);
+  return 2 * D * LD * sizeof(float) + v_floats * sizeof(float) + 8 * (H + 1) * sizeof(float) +
+         2 * (H + 1) * sizeof(int) + (H * (H + 1) / 2 + 1) * sizeof(int);
 }
 size_t ml_rebuild_smem(int d) {
   const size_t D = 1u << d, LD = D + 1, KP = 1u << (2 * d);
