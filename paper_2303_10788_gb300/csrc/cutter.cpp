@@ -278,14 +278,23 @@ double plan_cost(const Problem& p, const std::vector<ccs_cut>& cuts_in, bool* ok
   }
   std::vector<int> base(n + 1, 0);
   for (int q = 0; q < n; ++q) base[q + 1] = base[q] + cnt[q] + 1;
-  auto seg = [&](int q, int g) {
-    return base[q] + (int)(std::upper_bound(pos.begin() + start[q], pos.begin() + start[q] + cnt[q], g) -
-                           (pos.begin() + start[q]));
-  };
+  // one pass over the gates: each qubit's current segment follows a cursor
+  // over the cuts (sorted by gate index); two-qubit gates join segments, and
+  // every segment counts its gates (a gate belongs to its first operand's)
+  // and whether one of them is non-Clifford
   UF uf(base[n]);
-  for (int gi = 0; gi < ng; ++gi) {
-    const auto& g = p.gates[gi];
-    if (two_qubit(g[0])) uf.join(seg(g[1], gi), seg(g[2], gi));
+  std::vector<int> seg_gates(base[n], 0), segcur(base.begin(), base.end() - 1);
+  std::vector<char> seg_nc(base[n], 0);
+  {
+    size_t nc = 0;
+    for (int gi = 0; gi < ng; ++gi) {
+      while (nc < cuts.size() && (int)cuts[nc].gate_index <= gi) ++segcur[cuts[nc++].qubit];
+      const auto& g = p.gates[gi];
+      const int sa = segcur[g[1]];
+      ++seg_gates[sa];
+      if (two_qubit(g[0])) uf.join(sa, segcur[g[2]]);
+      else if (is_nonclifford_op(g[0])) seg_nc[sa] = 1;
+    }
   }
   std::vector<int> fid(base[n], -1), of_seg(base[n]);
   int nf = 0;
@@ -296,12 +305,10 @@ double plan_cost(const Problem& p, const std::vector<ccs_cut>& cuts_in, bool* ok
   }
   std::vector<int> wires(nf, 0), gates(nf, 0), qin(nf, 0), qout(nf, 0), marg(nf, 0);
   std::vector<char> cliff(nf, 1);
-  for (int s = 0; s < base[n]; ++s) wires[of_seg[s]]++;
-  for (int gi = 0; gi < ng; ++gi) {
-    const auto& g = p.gates[gi];
-    const int f = of_seg[seg(g[1], gi)];
-    gates[f]++;
-    if (!two_qubit(g[0]) && is_nonclifford_op(g[0])) cliff[f] = 0;
+  for (int s = 0; s < base[n]; ++s) {
+    wires[of_seg[s]]++;
+    gates[of_seg[s]] += seg_gates[s];
+    if (seg_nc[s]) cliff[of_seg[s]] = 0;
   }
   for (auto& c : cuts) {
     const int q = (int)c.qubit;
