@@ -89,6 +89,11 @@ def test_ml_correction_matches_oracle(ctx, name):
     assert m.min() > -1e-5                                  # no negative quasi-probability left
     mb, _ = ccs.ccs_recombine(ctx, plan, res, precision=ccs.CCS_BF16)
     assert np.abs(mb - want_m).max() < 1e-2
+    # a second correction reads the corrected (FP32) operands: the corrected
+    # models are physical, so it leaves them where they are
+    ccs.ccs_ml_correct(ctx, plan, res, ccs.CCS_ML_SAMPLED)
+    m2, _ = ccs.ccs_recombine(ctx, plan, res, use_graph=True)
+    assert np.abs(m2 - want_m).max() < 1e-5
     # the next evaluation brings back the raw data (and the int16 hub operand)
     res = ccs.ccs_eval_variants(ctx, plan, mode=ccs.CCS_SAMPLED, shots=shots, seed_lo=SEED[0], seed_hi=SEED[1],
                                 use_graph=True, res=res)
