@@ -39,6 +39,30 @@ void chp_planes(int op, int ra, int rb, uint32_t x[2], uint32_t z[2], uint32_t& 
   }
 }
 
+// The one-qubit Cliffords of the gate set as plane updates without a branch:
+// x' = (x & P) ^ (z & Q), z' = (x & R) ^ (z & S),
+// flip ^= (x & z & A) ^ (x & B) ^ (z & C)   (all-ones or zero masks;
+// the same rules as chp_planes: H swaps x and z, S and S^dagger add x to z,
+// the Paulis only flip signs).  Row = opcode H..Z, then the identity.
+struct OneQubitRule { uint32_t P, Q, R, S, A, B, C; };
+constexpr uint32_t kOnes = 0xffffu;
+constexpr OneQubitRule kOneQubit[7] = {
+    {0, kOnes, kOnes, 0, kOnes, 0, 0},          // H
+    {kOnes, 0, kOnes, kOnes, kOnes, 0, 0},      // S
+    {kOnes, 0, kOnes, kOnes, kOnes, kOnes, 0},  // S^dagger: flip ^= x & ~z
+    {kOnes, 0, 0, kOnes, 0, 0, kOnes},          // X
+    {kOnes, 0, 0, kOnes, 0, kOnes, kOnes},      // Y
+    {kOnes, 0, 0, kOnes, 0, kOnes, 0},          // Z
+    {kOnes, 0, 0, kOnes, 0, 0, 0},              // identity
+};
+inline void one_qubit_planes(int op, uint32_t& x, uint32_t& z, uint32_t& flip) {
+  const OneQubitRule& r = kOneQubit[op == kOpI ? 6 : op];
+  flip ^= (x & z & r.A) ^ (x & r.B) ^ (z & r.C);
+  const uint32_t nx = (x & r.P) ^ (z & r.Q), nz = (x & r.R) ^ (z & r.S);
+  x = nx;
+  z = nz;
+}
+
 // Identity planes: pattern v has x_a = bit 0, z_a = bit 1, x_b = bit 2, z_b = bit 3 of v.
 constexpr uint32_t kPX0 = 0xaaaau, kPX1 = 0xf0f0u, kPZ0 = 0xccccu, kPZ1 = 0xff00u;
 
@@ -157,7 +181,11 @@ struct PlaneOp {
   uint32_t px[2], pz[2], pf;
   bool dead;
   PlaneOp(int qa, int qb) : a(qa), b(qb), px{kPX0, kPX1}, pz{kPZ0, kPZ1}, pf(0), dead(false) {}
-  void add(int op, int ra, int rb, double) { chp_planes(op, ra, rb < 0 ? 1 - ra : rb, px, pz, pf); }
+  void add(int op, int ra, int rb, double) {
+    if (rb < 0 && op <= CCS_Z) one_qubit_planes(op, px[ra], pz[ra], pf);
+    else if (rb < 0 && op == kOpI) return;
+    else chp_planes(op, ra, rb < 0 ? 1 - ra : rb, px, pz, pf);
+  }
 };
 // A fused op of a statevector fragment keeps its gate word (for the unitary).
 struct WordOp {
@@ -377,25 +405,28 @@ int fragment_problem(Problem& p, int pi, std::vector<Frag>& out, std::string& er
       where[s] = {root_to_frag[r], f.n()};
       f.wires.push_back({(uint32_t)q, (uint32_t)(s - base[q])});
     }
+  // second pass: every gate written to its fragment's pre-sized list
+  const int nfr = (int)out.size() - first;
+  std::vector<std::array<int, 3>*> gdst(nfr);
+  std::vector<double*> pdst(nfr, nullptr);
   {
-    std::vector<int> count(out.size() - first, 0);
+    std::vector<int> count(nfr, 0);
     for (int s = 0; s < base[n]; ++s) count[where[s].first - first] += seg_gates[s];
-    for (size_t fi = 0; fi < count.size(); ++fi) {
-      out[first + fi].gates.reserve(count[fi]);
-      if (!p.gparam.empty()) out[first + fi].gparam.reserve(count[fi]);
+    for (int fi = 0; fi < nfr; ++fi) {
+      out[first + fi].gates.resize(count[fi]);
+      gdst[fi] = out[first + fi].gates.data();
+      if (!p.gparam.empty()) {
+        out[first + fi].gparam.resize(count[fi]);
+        pdst[fi] = out[first + fi].gparam.data();
+      }
     }
   }
   walk([&](int gi, const std::array<int, 3>& g, int sa, int sb) {
     const auto wa = where[sa];
-    Frag& f = out[wa.first];
-    if (sb >= 0) {
-      f.gates.push_back({g[0], wa.second, where[sb].second});
-      if (!p.gparam.empty()) f.gparam.push_back(0.0);
-    } else {
-      f.gates.push_back({g[0], wa.second, -1});
-      if (!p.gparam.empty()) f.gparam.push_back(p.gparam[gi]);
-      if (!is_clifford_op(g[0])) f.clifford = false;
-    }
+    const int fl = wa.first - first;
+    *gdst[fl]++ = {g[0], wa.second, sb >= 0 ? where[sb].second : -1};
+    if (pdst[fl]) *pdst[fl]++ = sb >= 0 ? 0.0 : p.gparam[gi];
+    if (sb < 0 && !is_clifford_op(g[0])) out[wa.first].clifford = false;
   });
   for (int ci = 0; ci < (int)p.cuts.size(); ++ci) {
     int q = p.cuts[ci].qubit;
