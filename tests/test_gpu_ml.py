@@ -16,7 +16,7 @@ import numpy as np
 import pytest
 
 from paper_2303_10788_gb300 import ccs
-from workloads import Workload, Region, brickwork_star, small_star, config1, config2, tree_circuit
+from workloads import Workload, Region, brickwork_star, small_star, config1, config2, tree_circuit, t_to_s
 from oracle.cutting import recombine
 from oracle.mlcorrect import ml_correct, is_physical
 from oracle.pipeline import evaluate
@@ -151,3 +151,25 @@ def test_ml_rejections(ctx):
     res3 = ccs.ccs_eval_variants(ctx, plan3, mode=ccs.CCS_SAMPLED, shots=256)
     with pytest.raises(ccs.CCSError, match="UNSUPPORTED"):     # the hub has 8 cut slots
         ccs.ccs_ml_correct(ctx, plan3, res3)
+
+
+def test_cut_free_fragment(ctx):
+    """A Clifford circuit without cuts: one fragment, no cut slots, 1 x 1
+    Choi blocks (its sampled marginal, already a probability vector), so the
+    correction leaves it unchanged; with a cut-bearing problem beside it in
+    the same plan the blocks of both slot counts are corrected in one call."""
+    w0 = small_star()
+    w = Workload("cliff", t_to_s(w0.circuit), [], w0.marginal, [], 256, 1)
+    ws = [w, small_star(seed=3, shots=256)]
+    plan = ccs.ccs_build_fragments(ctx, ws)
+    res = ccs.ccs_eval_variants(ctx, plan, mode=ccs.CCS_SAMPLED, shots=256, seed_lo=SEED[0], seed_hi=SEED[1])
+    raw, _ = ccs.ccs_recombine(ctx, plan, res)
+    ccs.ccs_ml_correct(ctx, plan, res)
+    m, _ = ccs.ccs_recombine(ctx, plan, res)
+    n0 = 1 << len(w.marginal)
+    assert np.abs(m[:n0] - raw[:n0]).max() < 1e-6
+    orc = evaluate(ws[1].circuit, ws[1].cuts, ws[1].marginal, (), mode="sampled", shots=256, seed_lo=SEED[0],
+                   seed_hi=SEED[1], circuit_id=1)
+    want = [ml_correct(f, T)[0] if f.clifford else T for f, T in zip(orc.fragments, orc.tensors)]
+    want_m = recombine(orc.fragments, want, orc.meta["k"], len(ws[1].marginal))
+    assert np.abs(m[n0:] - want_m).max() < 1e-5

@@ -172,3 +172,15 @@ def test_correction_removes_negative_quasi_probabilities():
         fid_ml.append(np.sum(np.sqrt(p_ml * bf)) ** 2)
     assert raw_neg > 0
     assert np.mean(fid_ml) > np.mean(fid_raw)
+
+
+def test_cut_free_fragment_is_the_simplex_projection():
+    """A fragment without cut slots has 1 x 1 Choi blocks (its marginal
+    distribution): the correction is the plain Euclidean projection of that
+    vector onto the probability simplex (total 2^0 = 1)."""
+    f = Fragment(wires=[(0, 0), (1, 0)], gates=[], qin=[], qout=[], marg=[(0, 0), (1, 1)], slots=[])
+    T = np.array([[0.6], [0.5], [-0.1], [0.0]])
+    Tc, info = ml_correct(f, T)
+    want, theta = project_simplex(T[:, 0], 1.0)
+    assert np.abs(Tc[:, 0] - want).max() < 1e-15 and abs(info["theta"] - theta) < 1e-15
+    assert np.allclose(Tc[:, 0], [0.55, 0.45, 0.0, 0.0])
