@@ -1893,7 +1893,10 @@ int ccs_get_tensor(ccs_ctx c, ccs_res r, int problem, int fragment, float* out) 
     int rc = locate(c, r, problem, fragment, -1, &d);
     if (rc) return rc;
     const long long cnt = (1ll << d->m) << (2 * d->n_slots);
-    const bool corrected = r->ml_applied && (d->clifford || r->ml_applied == 1 + CCS_ML_ALL);
+    // corrected by ccs_ml_correct since the evaluation: every fragment under
+    // CCS_ML_ALL, the Clifford fragments of a sampled result otherwise
+    const bool corrected = r->ml_applied && (r->ml_applied == 1 + CCS_ML_ALL ||
+                                             (d->clifford && r->ep.mode == CCS_SAMPLED));
     if (d->role == 1 && !corrected && d->clifford && r->ep.mode == CCS_SAMPLED && !r->ep.keep_tableaus)
       return fail(c, CCS_ERR_INVALID_ARG, "a sampled hub's tensor needs its counts (keep_tableaus)");
     if (d->role == 1 && d->clifford && r->ep.mode == CCS_STITCH)

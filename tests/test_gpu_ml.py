@@ -110,6 +110,11 @@ def test_exact_models_are_fixed_points(ctx, name):
     plan = ccs.ccs_build_fragments(ctx, [w])
     res = ccs.ccs_eval_variants(ctx, plan, mode=ccs.CCS_EXACT)
     before, _ = ccs.ccs_recombine(ctx, plan, res)
+    # the default selection has nothing to correct in an exact result: every
+    # tensor (the hub's folded on request) stays the evaluation's
+    ccs.ccs_ml_correct(ctx, plan, res, ccs.CCS_ML_SAMPLED)
+    for fi, (f, T) in enumerate(zip(orc.fragments, orc.tensors)):
+        assert np.abs(ccs.ccs_get_tensor(ctx, res, 0, fi) - T).max() / max(1.0, np.abs(T).max()) < 1e-5
     ccs.ccs_ml_correct(ctx, plan, res, ccs.CCS_ML_ALL)
     for fi, (f, T) in enumerate(zip(orc.fragments, orc.tensors)):
         got = ccs.ccs_get_tensor(ctx, res, 0, fi)
