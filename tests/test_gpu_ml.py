@@ -3,14 +3,15 @@ against the FP64 oracle (``oracle.mlcorrect``) on the same Philox shots.
 
 Per fragment the corrected tensor T'_f must match the oracle's element by
 element, and the recombined marginal of the corrected models the oracle's
-contraction of its corrected tensors.  Bars (FP32 Jacobi against FP64
+contraction of its corrected tensors.  Bars (complex64 Jacobi against FP64
 ``eigh``): T'_f within 4 N 2^-24 of the oracle relative to max(1, max |T_f|),
-N = 2^(d+1) the rows of the real embedding of a Choi block (the rounding of
-an N-row FP32 eigendecomposition and of the rebuild grows like N eps times
-the block's norm: 2e-6 at d = 2, 3e-5 at d = 6); marginals within 1e-5.  Cases cover fragments with 1, 2,
-3, 4 and 6 cut slots: stars (the hub operand stored by preparation at its
-inputs, as int16 count sums) and a branched tree (general contraction, T_f
-read directly).
+N = 2^(d+1) the real dimension of a 2^d x 2^d complex Choi block (the
+rounding of an FP32 eigendecomposition and of the rebuild grows like N eps
+times the block's norm: 2e-6 at d = 2, 3e-5 at d = 6); marginals within
+1e-5.  Cases cover fragments with 1 to 6 cut slots: stars (the hub operand
+stored by preparation at its inputs, as int16 count sums; one hub with 5
+slots, one with 6) and a branched tree (general contraction, T_f read
+directly).
 """
 import numpy as np
 import pytest
@@ -36,6 +37,14 @@ def three_region_star():
     return Workload("star3x", c, cuts, [0, 7, 15, 3, 5, 10, 12], [], 256, 77, regs)
 
 
+def five_slot_star():
+    """A hub with five cut slots: the third region runs to the circuit's end
+    (an input cut only)."""
+    regs = [Region([0], 1, 2, 6, [0, 1], 1), Region([7], 8, 3, 7, [7, 8], 1), Region([15], 14, 2, 10, [15, 14], 1)]
+    c, cuts = brickwork_star(16, 10, regs, 78)
+    return Workload("star5s", c, cuts, [0, 7, 15, 3, 5, 10, 12], [], 256, 78, regs)
+
+
 def tree4():
     c, cuts = tree_circuit([0, 1, 1], 12, 2, seed=4)
     return Workload("tree4", c, cuts, [0, 2, 4, 6, c.n_qubits - 1], [], 128, 4)
@@ -46,9 +55,10 @@ CASES = {
     "config1": config1,
     "config2": config2,
     "star3x": three_region_star,
+    "star5s": five_slot_star,
     "tree4": tree4,
 }
-SHOTS = {"star8": 64, "config1": 96, "config2": 128, "star3x": 256, "tree4": 128}
+SHOTS = {"star8": 64, "config1": 96, "config2": 128, "star3x": 256, "star5s": 256, "tree4": 128}
 
 
 @pytest.fixture(scope="module")
